@@ -1,0 +1,151 @@
+/*
+ * fb.h -- C ABI of libfb.so, a B300 (sm_103a) implementation of the hot path of
+ * FastBlend (Duan et al., "FastBlend: a Powerful Model-Free Toolkit Making Video
+ * Stylization Easier", arXiv 2311.09265): patch-match NNF search between guide frames
+ * (Sec. 3.2, Alg. 1, Eq. 1), NNF-driven remapping of style frames (Sec. 3.3, Alg. 2),
+ * sliding-window blending (Sec. 3.4, Eq. 2) and two-keyframe interpolation
+ * (Sec. 3.5.2, the linear keyframe combination).
+ *
+ * Equations are numbered in order of appearance in the paper: Eq. 1 patch loss,
+ * Eq. 2 window blend, ..., Eq. 9 the linear two-keyframe combination.
+ *
+ * Conventions shared by every entry point
+ *   Images     H x W x 3 uint8, row-major, channel-fastest (HWC), contiguous.
+ *              Frame stacks are N such images back to back.
+ *   NNF        H x W x 2 int32: entry x = (row, col) of the SOURCE patch centre matched
+ *              to TARGET pixel x (the paper's F(i, j) = (x, y), Sec. 3.2).
+ *   Errors     H x W uint32, Eq. 1 evaluated at the returned NNF.
+ *   Outputs    float32 in [0, 1] (value / 255), same HWC layout as the inputs.
+ *   Patch      k = 2p+1 pixels per side, odd, 3 <= k <= 9; reads outside an image
+ *              take the nearest edge pixel (clamp-to-edge).
+ *   Sizes      k <= H, W <= 32767.  Frame counts 1 <= N <= 65535.
+ *   Memory     Unless an entry point says otherwise, every data pointer is a DEVICE
+ *              pointer on the context's device, owned by the caller, and must stay
+ *              valid until the work enqueued on `stream` has finished.
+ *   Streams    `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *              stream).  Calls enqueue asynchronously and return at once, except
+ *              where an entry point says it is synchronous.
+ *   Errors     Every call returns an fb_status.  Arguments are validated before any
+ *              work is enqueued; on FB_ERR_ARG nothing was launched.  On any error
+ *              fb_last_error() holds a message.  A context owns its scratch memory
+ *              and is NOT thread-safe; distinct contexts may be used concurrently.
+ *   Determinism  Results are a pure function of the inputs and fb_params: integer
+ *              patch distances, counter-based random numbers, one IEEE float
+ *              division per output value.
+ */
+#ifndef FB_H
+#define FB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define FB_API_VERSION 1
+
+typedef enum fb_status {
+    FB_OK = 0,
+    FB_ERR_ARG = 1,          /* invalid argument; nothing was enqueued          */
+    FB_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed      */
+    FB_ERR_OOM = 3,          /* device or pinned-host scratch allocation failed  */
+    FB_ERR_TIMEOUT = 4,      /* a bounded device-side wait expired               */
+    FB_ERR_UNSUPPORTED = 5   /* valid request this build does not implement      */
+} fb_status;
+
+typedef struct fb_ctx fb_ctx;
+
+/* Parameters of Alg. 1 (Sec. 3.2). */
+typedef struct fb_params {
+    int32_t patch;     /* k = 2p+1 (odd, 3..9)                                         */
+    int32_t iters;     /* n: iterations per pyramid level, 0..65534                    */
+    int32_t levels;    /* pyramid levels, 1..16; level l has ceil(H/2^l) x ceil(W/2^l)  */
+    int32_t r0;        /* first random-search radius; 0 => max(H', W') at each level   */
+    uint64_t seed;     /* key of the Philox-4x32-10 stream                             */
+    uint32_t pair_tag; /* fb_nnf only: stream id of this pair; fb_pair_tag(j, i) makes  */
+                       /* fb_nnf reproduce the NNF that the blend/interpolation calls   */
+                       /* compute for source frame j -> target frame i                  */
+    uint32_t flags;    /* reserved, must be 0                                           */
+} fb_params;
+
+/* Create a context on CUDA device `device` (made current for the call).  The context
+ * allocates scratch lazily and keeps it for reuse until fb_ctx_destroy. */
+int fb_ctx_create(fb_ctx **out, int device);
+
+/* Free the context and its scratch.  Synchronises the device first.  NULL is a no-op. */
+int fb_ctx_destroy(fb_ctx *ctx);
+
+/* Wait for `stream`, then report any error a kernel of this context recorded on the
+ * device (FB_ERR_TIMEOUT for an expired bounded wait) and clear it. */
+int fb_ctx_sync(fb_ctx *ctx, void *stream);
+
+/* Message for the last failing call on this context ("" if none).  Valid until the
+ * next call on the context.  ctx may be NULL (then: last argument error seen by a
+ * call made with ctx == NULL). */
+const char *fb_last_error(const fb_ctx *ctx);
+
+/* Static name of a status code. */
+const char *fb_status_string(int status);
+
+/* Number of kernels this context has launched since creation (diagnostics). */
+uint64_t fb_ctx_launches(const fb_ctx *ctx);
+
+/* Device scratch currently held by the context, in bytes. */
+size_t fb_ctx_scratch_bytes(const fb_ctx *ctx);
+
+/* Philox stream id of the ordered pair (source frame j -> target frame i), as used
+ * by fb_blend_window and fb_interpolate: (j << 16) | i. */
+uint32_t fb_pair_tag(int j, int i);
+
+/* NNF(S, T) by Alg. 1 (Sec. 3.2) with the Eq. 1 loss, for one source guide
+ * `src_guide` and one target guide `tgt_guide`, both H x W x 3.
+ *   init_nnf  NULL => Philox random initialisation at the coarsest level; else an
+ *             H x W x 2 int32 initial field (requires p->levels == 1; entries are
+ *             clamped into the image).
+ *   nnf_out   H x W x 2 int32 (written).     err_out  H x W uint32 or NULL.
+ * Schedule: every iteration updates all pixels from a snapshot of the previous
+ * iteration (Sec. 3.2, parallel update); per pixel the candidates are the four
+ * propagation candidates F(x+d) - d, d = (-1,0), (1,0), (0,-1), (0,1), then the random
+ * search candidates best + U[-r, r]^2 for r = r0, r0/2, ..., 1; a candidate wins only
+ * with a strictly smaller error.  Async on `stream`. */
+int fb_nnf(fb_ctx *ctx, const uint8_t *src_guide, const uint8_t *tgt_guide, int H, int W,
+           const fb_params *p, const int32_t *init_nnf, int32_t *nnf_out, uint32_t *err_out,
+           void *stream);
+
+/* Alg. 2 (Sec. 3.3), memory-efficient remap of `src_style` (H x W x 3) through `nnf`
+ * (H x W x 2 int32, entries clamped into the image):
+ *   out(x) = sum over the k x k neighbours q of x of S(F(q^) - (q^ - x)) / (255 k^2),
+ * with q^ = q clamped into the image and the source index clamped into the image.
+ * out: H x W x 3 float32.  No patch tensor is formed: O(HW) memory.  Async. */
+int fb_remap(fb_ctx *ctx, const uint8_t *src_style, const int32_t *nnf, int H, int W,
+             int patch, float *out, void *stream);
+
+/* Eq. 2 (Sec. 3.4): sliding-window blend of N style frames guided by N guide frames.
+ * For each frame i the window [i-M, i+M], M = (window-1)/2, is truncated to the clip;
+ *   out_i = (S_i + sum_{j in window, j != i} (S_j -> S_i)) / (frames in window),
+ * where (S_j -> S_i) is the Alg. 2 remap of S_j through NNF(G_j, G_i) computed by
+ * Alg. 1 with pair tag fb_pair_tag(j, i).  window must be odd and >= 1.
+ *   guides, styles: N x H x W x 3 uint8;  out: N x H x W x 3 float32.
+ * Pointers are either all device pointers (async) or all host pointers; with host
+ * pointers the call stages the data through the context and returns when `out` is
+ * filled (pinned host memory makes the copies faster; pageable memory works). */
+int fb_blend_window(fb_ctx *ctx, const uint8_t *guides, const uint8_t *styles, int N, int H,
+                    int W, int window, const fb_params *p, float *out, void *stream);
+
+/* Sec. 3.5.2: render every frame of an N-frame guide video from stylised keyframes.
+ *   key_idx     HOST array of n_keys strictly increasing frame indices in [0, N).
+ *   key_styles  n_keys x H x W x 3 uint8, keyframe m's style at key_idx[m].
+ * For l < i < r consecutive keys:
+ *   out_i = ((r - i)(S_l -> G_i) + (i - l)(S_r -> G_i)) / (r - l);
+ * keyframes are output unchanged (S/255); frames before the first / after the last
+ * key use that key alone.  n_keys == 1 renders the whole video from one frame.
+ * Memory rules as fb_blend_window (device => async, host => synchronous). */
+int fb_interpolate(fb_ctx *ctx, const uint8_t *guides, int N, int H, int W,
+                   const int32_t *key_idx, const uint8_t *key_styles, int n_keys,
+                   const fb_params *p, float *out, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FB_H */

@@ -1,0 +1,266 @@
+"""CPU oracle for the FastBlend hot path (arXiv 2311.09265) -- ctypes front end.
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, ``__graft_entry__.smoke()`` and the
+CPU-baseline / reference leg of ``bench.py`` may import this package.  The CUDA
+library never calls it and shares no code with it; ``fbref.c`` restates the paper's
+algorithms (Alg. 1, Eq. 1, Alg. 2, Eq. 2, Sec. 3.5.2) with plain loops.
+
+All arrays are numpy: images ``(H, W, 3) uint8``, stacks ``(N, H, W, 3) uint8``,
+NNFs ``(H, W, 2) int32`` holding (row, col), errors ``(H, W) uint32``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+_DIR = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_DIR, "fbref.c")
+_HDR = os.path.join(_DIR, "fbref.h")
+LIB_PATH = os.path.join(_DIR, "libfbref.so")
+
+_lib = None
+
+
+def build(force: bool = False) -> str:
+    """Compile fbref.c into libfbref.so (gcc, -O2, OpenMP, IEEE float: no fast-math)."""
+    stale = (not os.path.exists(LIB_PATH)
+             or os.path.getmtime(LIB_PATH) < max(os.path.getmtime(_SRC), os.path.getmtime(_HDR)))
+    if force or stale:
+        tmp = LIB_PATH + f".tmp{os.getpid()}"
+        subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11",
+                        "-fno-fast-math", "-o", tmp, _SRC], check=True)
+        os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("patch", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("r0", ctypes.c_int32),
+                ("seed", ctypes.c_uint64)]
+
+
+_u8p = ctypes.POINTER(ctypes.c_uint8)
+_i32p = ctypes.POINTER(ctypes.c_int32)
+_u32p = ctypes.POINTER(ctypes.c_uint32)
+_f32p = ctypes.POINTER(ctypes.c_float)
+_P = ctypes.POINTER(Params)
+
+
+def lib() -> ctypes.CDLL:
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB_PATH)
+        L.fbref_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
+        L.fbref_ssd.argtypes = [_u8p, _u8p] + [ctypes.c_int] * 7
+        L.fbref_ssd.restype = ctypes.c_uint32
+        L.fbref_downsample.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, _u8p]
+        L.fbref_rs_offset.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                      ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      _i32p, _i32p]
+        L.fbref_nnf.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
+                                _i32p, _i32p, _u32p]
+        L.fbref_nnf_trace.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int, _P,
+                                      ctypes.c_uint32, _i32p, _i32p, _u32p]
+        L.fbref_nnf_bruteforce.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                           _i32p, _u32p]
+        L.fbref_remap_sum.argtypes = [_u8p, _i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u32p]
+        L.fbref_remap.argtypes = [_u8p, _i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _f32p]
+        L.fbref_blend_window.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _P, _f32p]
+        L.fbref_blend_frame.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, _P, ctypes.c_int, _f32p]
+        L.fbref_interpolate.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _i32p,
+                                        _u8p, ctypes.c_int, _P, _f32p]
+        L.fbref_interpolate_frame.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              _i32p, _u8p, ctypes.c_int, _P, ctypes.c_int, _f32p]
+        L.fbref_pair_tag.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.fbref_pair_tag.restype = ctypes.c_uint32
+        L.fbref_num_threads.restype = ctypes.c_int
+        L.fbref_set_num_threads.argtypes = [ctypes.c_int]
+        for name in ("fbref_nnf", "fbref_nnf_trace", "fbref_blend_window", "fbref_blend_frame",
+                     "fbref_interpolate", "fbref_interpolate_frame"):
+            getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _ptr(a: np.ndarray, ctype):
+    assert a.flags["C_CONTIGUOUS"], "oracle arrays must be C-contiguous"
+    return a.ctypes.data_as(ctype)
+
+
+def _u8(a) -> np.ndarray:
+    a = np.ascontiguousarray(a)
+    assert a.dtype == np.uint8, a.dtype
+    return a
+
+
+def params(patch: int, iters: int, levels: int = 1, r0: int = 0, seed: int = 0) -> Params:
+    return Params(patch, iters, levels, r0, seed & 0xFFFFFFFFFFFFFFFF)
+
+
+def num_threads() -> int:
+    return lib().fbref_num_threads()
+
+
+def set_num_threads(n: int) -> None:
+    lib().fbref_set_num_threads(int(n))
+
+
+def pair_tag(j: int, i: int) -> int:
+    return lib().fbref_pair_tag(j, i)
+
+
+def philox4x32_10(ctr, key) -> np.ndarray:
+    c = np.ascontiguousarray(ctr, dtype=np.uint32)
+    k = np.ascontiguousarray(key, dtype=np.uint32)
+    out = np.zeros(4, np.uint32)
+    lib().fbref_philox4x32_10(_ptr(c, _u32p), _ptr(k, _u32p), _ptr(out, _u32p))
+    return out
+
+
+def ssd(src, tgt, k: int, u, x) -> int:
+    src, tgt = _u8(src), _u8(tgt)
+    H, W = src.shape[:2]
+    return int(lib().fbref_ssd(_ptr(src, _u8p), _ptr(tgt, _u8p), H, W, k,
+                               int(u[0]), int(u[1]), int(x[0]), int(x[1])))
+
+
+def downsample(img) -> np.ndarray:
+    img = _u8(img)
+    H, W = img.shape[:2]
+    out = np.zeros(((H + 1) // 2, (W + 1) // 2, 3), np.uint8)
+    lib().fbref_downsample(_ptr(img, _u8p), H, W, _ptr(out, _u8p))
+    return out
+
+
+def rs_offset(seed: int, pix: int, tag: int, level: int, it: int, t: int, r: int):
+    dr, dc = ctypes.c_int32(), ctypes.c_int32()
+    lib().fbref_rs_offset(seed, pix, tag, level, it, t, r, ctypes.byref(dr), ctypes.byref(dc))
+    return dr.value, dc.value
+
+
+def nnf(src, tgt, patch: int, iters: int, levels: int = 1, r0: int = 0, seed: int = 0,
+        pair_tag: int = 0, init=None):
+    """Alg. 1 for one pair; returns (F (H,W,2) int32, E (H,W) uint32)."""
+    src, tgt = _u8(src), _u8(tgt)
+    H, W = src.shape[:2]
+    F = np.zeros((H, W, 2), np.int32)
+    E = np.zeros((H, W), np.uint32)
+    p = params(patch, iters, levels, r0, seed)
+    ip = None
+    if init is not None:
+        init = np.ascontiguousarray(init, dtype=np.int32)
+        ip = _ptr(init, _i32p)
+    rc = lib().fbref_nnf(_ptr(src, _u8p), _ptr(tgt, _u8p), H, W, ctypes.byref(p), pair_tag, ip,
+                         _ptr(F, _i32p), _ptr(E, _u32p))
+    if rc != 0:
+        raise ValueError("fbref_nnf: bad arguments")
+    return F, E
+
+
+def nnf_trace(src, tgt, patch: int, iters: int, r0: int = 0, seed: int = 0, pair_tag: int = 0,
+              init=None):
+    """Alg. 1 (one level) returning F and E after each iteration: (iters+1, H, W)."""
+    src, tgt = _u8(src), _u8(tgt)
+    H, W = src.shape[:2]
+    F = np.zeros((H, W, 2), np.int32)
+    T = np.zeros((iters + 1, H, W), np.uint32)
+    p = params(patch, iters, 1, r0, seed)
+    ip = None
+    if init is not None:
+        init = np.ascontiguousarray(init, dtype=np.int32)
+        ip = _ptr(init, _i32p)
+    rc = lib().fbref_nnf_trace(_ptr(src, _u8p), _ptr(tgt, _u8p), H, W, ctypes.byref(p), pair_tag,
+                               ip, _ptr(F, _i32p), _ptr(T, _u32p))
+    if rc != 0:
+        raise ValueError("fbref_nnf_trace: bad arguments")
+    return F, T
+
+
+def nnf_bruteforce(src, tgt, patch: int):
+    src, tgt = _u8(src), _u8(tgt)
+    H, W = src.shape[:2]
+    F = np.zeros((H, W, 2), np.int32)
+    E = np.zeros((H, W), np.uint32)
+    lib().fbref_nnf_bruteforce(_ptr(src, _u8p), _ptr(tgt, _u8p), H, W, patch,
+                               _ptr(F, _i32p), _ptr(E, _u32p))
+    return F, E
+
+
+def remap_sum(style, F, patch: int) -> np.ndarray:
+    style = _u8(style)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    H, W = style.shape[:2]
+    V = np.zeros((H, W, 3), np.uint32)
+    lib().fbref_remap_sum(_ptr(style, _u8p), _ptr(F, _i32p), H, W, patch, _ptr(V, _u32p))
+    return V
+
+
+def remap(style, F, patch: int) -> np.ndarray:
+    style = _u8(style)
+    F = np.ascontiguousarray(F, dtype=np.int32)
+    H, W = style.shape[:2]
+    out = np.zeros((H, W, 3), np.float32)
+    lib().fbref_remap(_ptr(style, _u8p), _ptr(F, _i32p), H, W, patch, _ptr(out, _f32p))
+    return out
+
+
+def blend_window(guides, styles, window: int, patch: int, iters: int, levels: int = 1,
+                 r0: int = 0, seed: int = 0) -> np.ndarray:
+    guides, styles = _u8(guides), _u8(styles)
+    N, H, W = guides.shape[:3]
+    out = np.zeros((N, H, W, 3), np.float32)
+    p = params(patch, iters, levels, r0, seed)
+    rc = lib().fbref_blend_window(_ptr(guides, _u8p), _ptr(styles, _u8p), N, H, W, window,
+                                  ctypes.byref(p), _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_blend_window: bad arguments")
+    return out
+
+
+def blend_frame(guides, styles, window: int, i: int, patch: int, iters: int, levels: int = 1,
+                r0: int = 0, seed: int = 0) -> np.ndarray:
+    guides, styles = _u8(guides), _u8(styles)
+    N, H, W = guides.shape[:3]
+    out = np.zeros((H, W, 3), np.float32)
+    p = params(patch, iters, levels, r0, seed)
+    rc = lib().fbref_blend_frame(_ptr(guides, _u8p), _ptr(styles, _u8p), N, H, W, window,
+                                 ctypes.byref(p), i, _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_blend_frame: bad arguments")
+    return out
+
+
+def interpolate(guides, key_idx, key_styles, patch: int, iters: int, levels: int = 1,
+                r0: int = 0, seed: int = 0) -> np.ndarray:
+    guides, key_styles = _u8(guides), _u8(key_styles)
+    keys = np.ascontiguousarray(key_idx, dtype=np.int32)
+    N, H, W = guides.shape[:3]
+    out = np.zeros((N, H, W, 3), np.float32)
+    p = params(patch, iters, levels, r0, seed)
+    rc = lib().fbref_interpolate(_ptr(guides, _u8p), N, H, W, _ptr(keys, _i32p),
+                                 _ptr(key_styles, _u8p), len(keys), ctypes.byref(p),
+                                 _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_interpolate: bad arguments")
+    return out
+
+
+def interpolate_frame(guides, key_idx, key_styles, i: int, patch: int, iters: int,
+                      levels: int = 1, r0: int = 0, seed: int = 0) -> np.ndarray:
+    guides, key_styles = _u8(guides), _u8(key_styles)
+    keys = np.ascontiguousarray(key_idx, dtype=np.int32)
+    N, H, W = guides.shape[:3]
+    out = np.zeros((H, W, 3), np.float32)
+    p = params(patch, iters, levels, r0, seed)
+    rc = lib().fbref_interpolate_frame(_ptr(guides, _u8p), N, H, W, _ptr(keys, _i32p),
+                                       _ptr(key_styles, _u8p), len(keys), ctypes.byref(p), i,
+                                       _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_interpolate_frame: bad arguments")
+    return out

@@ -1,0 +1,485 @@
+/*
+ * fbref.c -- CPU oracle for the FastBlend hot path (arXiv 2311.09265).
+ *
+ * TEST INFRASTRUCTURE ONLY: used by the test suite, the package smoke check and the
+ * timed CPU baseline.  Never called by the product path.  Plain loops, integer
+ * arithmetic, one IEEE float division per output value; no blocking, fusion or
+ * reordering beyond the definitions cited at each function.  OpenMP only splits the
+ * independent per-pixel loops (Sec. 3.2 updates every position independently).
+ *
+ * What pins each part (tests/test_oracle_*.py):
+ *   Philox-4x32-10  known-answer vectors of Salmon et al. (tests/golden).
+ *   SSD (Eq. 1)     hand-derived values on tiny images (tests/golden), closed forms
+ *                   for constant images, brute-force agreement.
+ *   NNF (Alg. 1)    brute-force exhaustive NNF on tiny inputs (E_pm >= E_bf, equality
+ *                   after many iterations), known-shift fixed points, per-pixel
+ *                   monotone energy, propagation fixing a single wrong match.
+ *   Remap (Alg. 2)  identity NNF => identity, integer-shift NNF => shifted image,
+ *                   a hand-derived border example (tests/golden).
+ *   Blend (Eq. 2)   constant style => constant, identical frames => that frame,
+ *                   closed form on known-shift clips, linearity, window truncation.
+ *   Combine (Sec. 3.5.2)  keys copied, endpoint weights, weights sum to one,
+ *                   closed form on known-shift clips.
+ * Parity unpinned: none of the functions above; end-to-end visual quality against
+ * the paper's human study cannot be pinned (no data).
+ */
+#include "fbref.h"
+
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------------ */
+/* Philox-4x32-10, written from its definition in Salmon, Moraes, Dror and Shaw,   */
+/* "Parallel random numbers: as easy as 1, 2, 3" (SC'11): each of the 10 rounds    */
+/* multiplies counter words 0 and 2 by two fixed odd constants, swaps the 32-bit   */
+/* halves into a new 4-word block xor-ed with the round key and the untouched       */
+/* words; the 2-word key is advanced by the Weyl increments between rounds.        */
+/* ------------------------------------------------------------------------------ */
+#define PHILOX_MUL_A 0xD2511F53u
+#define PHILOX_MUL_B 0xCD9E8D57u
+#define PHILOX_WEYL_A 0x9E3779B9u
+#define PHILOX_WEYL_B 0xBB67AE85u
+
+void fbref_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t x0 = ctr[0], x1 = ctr[1], x2 = ctr[2], x3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int round = 0; round < 10; ++round) {
+        if (round > 0) {
+            k0 += PHILOX_WEYL_A;
+            k1 += PHILOX_WEYL_B;
+        }
+        uint64_t pa = (uint64_t)PHILOX_MUL_A * x0;
+        uint64_t pb = (uint64_t)PHILOX_MUL_B * x2;
+        uint32_t pa_hi = (uint32_t)(pa >> 32), pa_lo = (uint32_t)pa;
+        uint32_t pb_hi = (uint32_t)(pb >> 32), pb_lo = (uint32_t)pb;
+        uint32_t y0 = pb_hi ^ x1 ^ k0;
+        uint32_t y1 = pb_lo;
+        uint32_t y2 = pa_hi ^ x3 ^ k1;
+        uint32_t y3 = pa_lo;
+        x0 = y0; x1 = y1; x2 = y2; x3 = y3;
+    }
+    out[0] = x0; out[1] = x1; out[2] = x2; out[3] = x3;
+}
+
+/* ------------------------------------------------------------------------------ */
+static int clampi(int v, int lo, int hi) { return v < lo ? lo : (v > hi ? hi : v); }
+
+static uint8_t px(const uint8_t *img, int W, int r, int c, int ch)
+{
+    return img[((size_t)r * W + c) * 3 + ch];
+}
+
+/* Eq. 1, Sec. 3.2: || S[u] - T[x] ||_2^2 over the (2p+1)^2 RGB patch.  Patch reads
+ * outside the image take the nearest edge pixel (clamp-to-edge on both images). */
+uint32_t fbref_ssd(const uint8_t *src, const uint8_t *tgt, int H, int W, int k,
+                   int ur, int uc, int xr, int xc)
+{
+    int p = k / 2;
+    uint32_t acc = 0;
+    for (int a = -p; a <= p; ++a) {
+        for (int b = -p; b <= p; ++b) {
+            int sr = clampi(ur + a, 0, H - 1), sc = clampi(uc + b, 0, W - 1);
+            int tr = clampi(xr + a, 0, H - 1), tc = clampi(xc + b, 0, W - 1);
+            for (int ch = 0; ch < 3; ++ch) {
+                int d = (int)px(src, W, sr, sc, ch) - (int)px(tgt, W, tr, tc, ch);
+                acc += (uint32_t)(d * d);
+            }
+        }
+    }
+    return acc;
+}
+
+/* Alg. 1, "resize images S, T": one pyramid step, 2x2 box mean, round half up. */
+void fbref_downsample(const uint8_t *img, int H, int W, uint8_t *out)
+{
+    int h2 = (H + 1) / 2, w2 = (W + 1) / 2;
+    for (int r = 0; r < h2; ++r) {
+        for (int c = 0; c < w2; ++c) {
+            int r0 = 2 * r, r1 = clampi(2 * r + 1, 0, H - 1);
+            int c0 = 2 * c, c1 = clampi(2 * c + 1, 0, W - 1);
+            for (int ch = 0; ch < 3; ++ch) {
+                int s = px(img, W, r0, c0, ch) + px(img, W, r0, c1, ch) +
+                        px(img, W, r1, c0, ch) + px(img, W, r1, c1, ch);
+                out[((size_t)r * w2 + c) * 3 + ch] = (uint8_t)((s + 2) >> 2);
+            }
+        }
+    }
+}
+
+uint32_t fbref_pair_tag(int j, int i) { return ((uint32_t)j << 16) | (uint32_t)i; }
+
+int fbref_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+void fbref_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+}
+
+/* Uniform integer in [0, n) from one 32-bit Philox word: floor(u * n / 2^32). */
+static int32_t uniform_below(uint32_t u, uint32_t n)
+{
+    return (int32_t)(((uint64_t)u * n) >> 32);
+}
+
+/* Random search, Sec. 3.2: the offset (dr, dc) for radius r, each axis uniform on
+ * [-r, r].  Candidates t = 2m and 2m+1 share one Philox block: t even takes words
+ * 0,1 and t odd takes words 2,3 of counter (pix, pair_tag, level<<24 | (it+1)<<8 | m, 0). */
+void fbref_rs_offset(uint64_t seed, uint32_t pix, uint32_t pair_tag, int level, int it,
+                     int t, int r, int32_t *dr, int32_t *dc)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {pix, pair_tag,
+                       ((uint32_t)level << 24) | ((uint32_t)(it + 1) << 8) | (uint32_t)(t >> 1),
+                       0u};
+    uint32_t u[4];
+    fbref_philox4x32_10(ctr, key, u);
+    int w = 2 * (t & 1);
+    *dr = uniform_below(u[w], (uint32_t)(2 * r + 1)) - r;
+    *dc = uniform_below(u[w + 1], (uint32_t)(2 * r + 1)) - r;
+}
+
+/* Random initialisation of F, Alg. 1 first line: row uniform in [0, H'), column
+ * uniform in [0, W') from words 0,1 of counter (pix, pair_tag, level<<24, 0). */
+static void random_match(uint64_t seed, uint32_t pix, uint32_t pair_tag, int level, int H,
+                         int W, int32_t *r, int32_t *c)
+{
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t ctr[4] = {pix, pair_tag, (uint32_t)level << 24, 0u};
+    uint32_t u[4];
+    fbref_philox4x32_10(ctr, key, u);
+    *r = uniform_below(u[0], (uint32_t)H);
+    *c = uniform_below(u[1], (uint32_t)W);
+}
+
+static int params_ok(const fbref_params *p, int H, int W)
+{
+    if (!p) return 0;
+    if (p->patch < 3 || p->patch > 9 || (p->patch & 1) == 0) return 0;
+    if (p->iters < 0 || p->iters > 65534) return 0;
+    if (p->levels < 1 || p->levels > 16) return 0;
+    if (p->r0 < 0) return 0;
+    if (H < 1 || W < 1 || H > 32767 || W > 32767) return 0;
+    return 1;
+}
+
+/* Alg. 1 for one ordered pair (source `src`, target `tgt`).  Schedule: Sec. 3.2
+ * drops the scan-order update for a parallel one in which all positions are updated
+ * independently, so every iteration reads a snapshot (F, E) taken at its start and
+ * writes a new (F, E); within one pixel the updating sequence is applied candidate
+ * by candidate:
+ *   propagation  F'(x) = F(x + d) - d for d = (-1,0), (1,0), (0,-1), (0,1), using the
+ *                snapshot, skipping neighbours outside the target, clamping into
+ *                the source;
+ *   random search F'(x) = F(x) + (dr, dc), centred on the current best, r = r0 >> t
+ *                for t = 0, 1, ... while r >= 1 (exponential decay to zero), clamped;
+ * a candidate replaces the incumbent only if its error is strictly smaller (the
+ * masked update of Alg. 1), so ties keep the earlier match. */
+static int nnf_impl(const uint8_t *src, const uint8_t *tgt, int H, int W,
+                    const fbref_params *p, uint32_t tag, const int32_t *init,
+                    int32_t *nnf_out, uint32_t *err_out, uint32_t *err_trace)
+{
+    if (!params_ok(p, H, W) || !src || !tgt || !nnf_out) return -1;
+    if (init && p->levels != 1) return -1;
+    const int k = p->patch, L = p->levels;
+
+    /* Image pyramid (Alg. 1, outer loop): level 0 is full resolution. */
+    const uint8_t **ps = (const uint8_t **)calloc((size_t)L, sizeof(*ps));
+    const uint8_t **pt = (const uint8_t **)calloc((size_t)L, sizeof(*pt));
+    int *hs = (int *)calloc((size_t)L, sizeof(int)), *ws = (int *)calloc((size_t)L, sizeof(int));
+    ps[0] = src; pt[0] = tgt; hs[0] = H; ws[0] = W;
+    for (int l = 1; l < L; ++l) {
+        hs[l] = (hs[l - 1] + 1) / 2;
+        ws[l] = (ws[l - 1] + 1) / 2;
+        uint8_t *a = (uint8_t *)malloc((size_t)hs[l] * ws[l] * 3);
+        uint8_t *b = (uint8_t *)malloc((size_t)hs[l] * ws[l] * 3);
+        fbref_downsample(ps[l - 1], hs[l - 1], ws[l - 1], a);
+        fbref_downsample(pt[l - 1], hs[l - 1], ws[l - 1], b);
+        ps[l] = a; pt[l] = b;
+    }
+
+    size_t npx0 = (size_t)H * W;
+    int32_t *F = (int32_t *)malloc(npx0 * 2 * sizeof(int32_t));
+    int32_t *Fn = (int32_t *)malloc(npx0 * 2 * sizeof(int32_t));
+    uint32_t *E = (uint32_t *)malloc(npx0 * sizeof(uint32_t));
+    uint32_t *En = (uint32_t *)malloc(npx0 * sizeof(uint32_t));
+
+    for (int l = L - 1; l >= 0; --l) {
+        const int h = hs[l], w = ws[l];
+        const uint8_t *S = ps[l], *T = pt[l];
+        if (l == L - 1) {
+            for (int r = 0; r < h; ++r)
+                for (int c = 0; c < w; ++c) {
+                    size_t x = (size_t)r * w + c;
+                    if (init) {
+                        F[2 * x] = clampi(init[2 * x], 0, h - 1);
+                        F[2 * x + 1] = clampi(init[2 * x + 1], 0, w - 1);
+                    } else {
+                        random_match(p->seed, (uint32_t)x, tag, l, h, w, &F[2 * x], &F[2 * x + 1]);
+                    }
+                }
+        } else {
+            /* Alg. 1, "upsample F": the coarse match of x>>1, doubled, plus x's parity. */
+            const int wc = ws[l + 1];
+            for (int r = 0; r < h; ++r)
+                for (int c = 0; c < w; ++c) {
+                    size_t xc = (size_t)(r >> 1) * wc + (c >> 1);
+                    size_t x = (size_t)r * w + c;
+                    Fn[2 * x] = clampi(2 * F[2 * xc] + (r & 1), 0, h - 1);
+                    Fn[2 * x + 1] = clampi(2 * F[2 * xc + 1] + (c & 1), 0, w - 1);
+                }
+            int32_t *t = F; F = Fn; Fn = t;
+        }
+        /* Alg. 1, "initialize error matrix E". */
+#pragma omp parallel for schedule(static)
+        for (int r = 0; r < h; ++r)
+            for (int c = 0; c < w; ++c) {
+                size_t x = (size_t)r * w + c;
+                E[x] = fbref_ssd(S, T, h, w, k, F[2 * x], F[2 * x + 1], r, c);
+            }
+        if (err_trace && l == 0) memcpy(err_trace, E, npx0 * sizeof(uint32_t));
+
+        const int r0 = p->r0 > 0 ? p->r0 : (h > w ? h : w);
+        static const int dirs[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+        for (int it = 0; it < p->iters; ++it) {
+#pragma omp parallel for schedule(static)
+            for (int r = 0; r < h; ++r) {
+                for (int c = 0; c < w; ++c) {
+                    size_t x = (size_t)r * w + c;
+                    int32_t br = F[2 * x], bc = F[2 * x + 1];
+                    uint32_t be = E[x];
+                    for (int d = 0; d < 4; ++d) {
+                        int nr = r + dirs[d][0], nc = c + dirs[d][1];
+                        if (nr < 0 || nr >= h || nc < 0 || nc >= w) continue;
+                        size_t n = (size_t)nr * w + nc;
+                        int cr = clampi(F[2 * n] - dirs[d][0], 0, h - 1);
+                        int cc = clampi(F[2 * n + 1] - dirs[d][1], 0, w - 1);
+                        uint32_t e = fbref_ssd(S, T, h, w, k, cr, cc, r, c);
+                        if (e < be) { be = e; br = cr; bc = cc; }
+                    }
+                    for (int t = 0; (r0 >> t) >= 1; ++t) {
+                        int rad = r0 >> t;
+                        int32_t dr, dc;
+                        fbref_rs_offset(p->seed, (uint32_t)x, tag, l, it, t, rad, &dr, &dc);
+                        int cr = clampi(br + dr, 0, h - 1);
+                        int cc = clampi(bc + dc, 0, w - 1);
+                        uint32_t e = fbref_ssd(S, T, h, w, k, cr, cc, r, c);
+                        if (e < be) { be = e; br = cr; bc = cc; }
+                    }
+                    Fn[2 * x] = br; Fn[2 * x + 1] = bc; En[x] = be;
+                }
+            }
+            int32_t *tf = F; F = Fn; Fn = tf;
+            uint32_t *te = E; E = En; En = te;
+            if (err_trace && l == 0) memcpy(err_trace + (size_t)(it + 1) * npx0, E, npx0 * sizeof(uint32_t));
+        }
+    }
+
+    memcpy(nnf_out, F, npx0 * 2 * sizeof(int32_t));
+    if (err_out) memcpy(err_out, E, npx0 * sizeof(uint32_t));
+    free(F); free(Fn); free(E); free(En);
+    for (int l = 1; l < L; ++l) { free((void *)ps[l]); free((void *)pt[l]); }
+    free(ps); free(pt); free(hs); free(ws);
+    return 0;
+}
+
+int fbref_nnf(const uint8_t *src, const uint8_t *tgt, int H, int W, const fbref_params *p,
+              uint32_t pair_tag, const int32_t *init_nnf, int32_t *nnf_out, uint32_t *err_out)
+{
+    return nnf_impl(src, tgt, H, W, p, pair_tag, init_nnf, nnf_out, err_out, NULL);
+}
+
+int fbref_nnf_trace(const uint8_t *src, const uint8_t *tgt, int H, int W, const fbref_params *p,
+                    uint32_t pair_tag, const int32_t *init_nnf, int32_t *nnf_out,
+                    uint32_t *err_trace)
+{
+    return nnf_impl(src, tgt, H, W, p, pair_tag, init_nnf, nnf_out, NULL, err_trace);
+}
+
+/* The exact nearest-neighbour field of Eq. 1, by exhaustive search. */
+void fbref_nnf_bruteforce(const uint8_t *src, const uint8_t *tgt, int H, int W, int k,
+                          int32_t *nnf_out, uint32_t *err_out)
+{
+#pragma omp parallel for schedule(dynamic)
+    for (int r = 0; r < H; ++r) {
+        for (int c = 0; c < W; ++c) {
+            uint32_t be = 0xFFFFFFFFu;
+            int br = 0, bc = 0;
+            for (int ur = 0; ur < H; ++ur)
+                for (int uc = 0; uc < W; ++uc) {
+                    uint32_t e = fbref_ssd(src, tgt, H, W, k, ur, uc, r, c);
+                    if (e < be) { be = e; br = ur; bc = uc; }
+                }
+            size_t x = (size_t)r * W + c;
+            nnf_out[2 * x] = br; nnf_out[2 * x + 1] = bc;
+            if (err_out) err_out[x] = be;
+        }
+    }
+}
+
+/* Alg. 2 (Sec. 3.3) without the division: for each neighbour q of x in the k x k
+ * window, q is first clamped into the image (q^), then the source pixel
+ * F(q^) - (q^ - x), clamped into the source, is added.  NNF entries outside the
+ * image are clamped into it before use. */
+void fbref_remap_sum(const uint8_t *style, const int32_t *nnf, int H, int W, int k,
+                     uint32_t *v_out)
+{
+    int p = k / 2;
+#pragma omp parallel for schedule(static)
+    for (int r = 0; r < H; ++r) {
+        for (int c = 0; c < W; ++c) {
+            uint32_t acc[3] = {0, 0, 0};
+            for (int a = -p; a <= p; ++a) {
+                for (int b = -p; b <= p; ++b) {
+                    int qr = clampi(r + a, 0, H - 1), qc = clampi(c + b, 0, W - 1);
+                    size_t q = (size_t)qr * W + qc;
+                    int fr = clampi(nnf[2 * q], 0, H - 1), fc = clampi(nnf[2 * q + 1], 0, W - 1);
+                    int sr = clampi(fr - (qr - r), 0, H - 1);
+                    int sc = clampi(fc - (qc - c), 0, W - 1);
+                    for (int ch = 0; ch < 3; ++ch) acc[ch] += px(style, W, sr, sc, ch);
+                }
+            }
+            size_t x = (size_t)r * W + c;
+            for (int ch = 0; ch < 3; ++ch) v_out[3 * x + ch] = acc[ch];
+        }
+    }
+}
+
+void fbref_remap(const uint8_t *style, const int32_t *nnf, int H, int W, int k, float *out)
+{
+    size_t n = (size_t)H * W * 3;
+    uint32_t *v = (uint32_t *)malloc(n * sizeof(uint32_t));
+    fbref_remap_sum(style, nnf, H, W, k, v);
+    float den = (float)(255 * k * k);
+    for (size_t i = 0; i < n; ++i) out[i] = (float)v[i] / den;
+    free(v);
+}
+
+/* Remap the style frame `style` onto guide frame i through NNF(G_j, G_i), adding
+ * weight * V into acc. */
+static int add_remapped(const uint8_t *gj, const uint8_t *gi, const uint8_t *style, int H, int W,
+                        const fbref_params *p, uint32_t tag, uint32_t weight, uint32_t *acc)
+{
+    size_t npx = (size_t)H * W;
+    int32_t *F = (int32_t *)malloc(npx * 2 * sizeof(int32_t));
+    uint32_t *V = (uint32_t *)malloc(npx * 3 * sizeof(uint32_t));
+    int rc = fbref_nnf(gj, gi, H, W, p, tag, NULL, F, NULL);
+    if (rc == 0) {
+        fbref_remap_sum(style, F, H, W, p->patch, V);
+        for (size_t t = 0; t < npx * 3; ++t) acc[t] += weight * V[t];
+    }
+    free(F); free(V);
+    return rc;
+}
+
+/* Eq. 2 (Sec. 3.4) for output frame i.  The window [i-M, i+M] is truncated to the
+ * clip and the sum is divided by the number of frames actually in it; the j = i term
+ * is S_i itself (an identity remap).  Result = (k^2 S_i + sum_j V_{j->i}) /
+ * (255 k^2 c_i), one IEEE float division per value. */
+int fbref_blend_frame(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                      int window, const fbref_params *p, int i, float *out)
+{
+    if (!params_ok(p, H, W) || N < 1 || N > 65535 || window < 1 || (window & 1) == 0 || i < 0 || i >= N)
+        return -1;
+    const int k = p->patch, M = (window - 1) / 2;
+    size_t npx = (size_t)H * W, fsz = npx * 3;
+    uint32_t *acc = (uint32_t *)calloc(fsz, sizeof(uint32_t));
+    for (size_t t = 0; t < fsz; ++t) acc[t] = (uint32_t)(k * k) * styles[(size_t)i * fsz + t];
+    int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
+    int rc = 0;
+    for (int j = lo; j <= hi && rc == 0; ++j) {
+        if (j == i) continue;
+        rc = add_remapped(guides + (size_t)j * fsz, guides + (size_t)i * fsz,
+                          styles + (size_t)j * fsz, H, W, p, fbref_pair_tag(j, i), 1u, acc);
+    }
+    float den = (float)(255 * k * k * (hi - lo + 1));
+    for (size_t t = 0; t < fsz; ++t) out[t] = (float)acc[t] / den;
+    free(acc);
+    return rc;
+}
+
+int fbref_blend_window(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                       int window, const fbref_params *p, float *out)
+{
+    size_t fsz = (size_t)H * W * 3;
+    for (int i = 0; i < N; ++i) {
+        int rc = fbref_blend_frame(guides, styles, N, H, W, window, p, i, out + (size_t)i * fsz);
+        if (rc) return rc;
+    }
+    return 0;
+}
+
+/* Sec. 3.5.2: between keyframes l < i < r,
+ *   S~_i = (r - i)/(r - l) (S_l -> S_i) + (i - l)/(r - l) (S_r -> S_i),
+ * computed as ((r-i) V_l + (i-l) V_r) / (255 k^2 (r-l)).  Keyframes are output
+ * unchanged (S/255).  Frames before the first or after the last keyframe take the
+ * nearest keyframe alone (weight one). */
+int fbref_interpolate_frame(const uint8_t *guides, int N, int H, int W, const int32_t *key_idx,
+                            const uint8_t *key_styles, int n_keys, const fbref_params *p,
+                            int i, float *out)
+{
+    if (!params_ok(p, H, W) || N < 1 || N > 65535 || n_keys < 1 || i < 0 || i >= N) return -1;
+    for (int m = 0; m < n_keys; ++m) {
+        if (key_idx[m] < 0 || key_idx[m] >= N) return -1;
+        if (m > 0 && key_idx[m] <= key_idx[m - 1]) return -1;
+    }
+    const int k = p->patch;
+    size_t npx = (size_t)H * W, fsz = npx * 3;
+    uint32_t *acc = (uint32_t *)calloc(fsz, sizeof(uint32_t));
+    uint32_t den_int;
+    int rc = 0, key_here = -1, ml = -1, mr = -1;
+    for (int m = 0; m < n_keys; ++m) {
+        if (key_idx[m] == i) key_here = m;
+        if (key_idx[m] < i) ml = m;
+        if (key_idx[m] > i && mr < 0) mr = m;
+    }
+    const uint8_t *gi = guides + (size_t)i * fsz;
+    if (key_here >= 0) {
+        for (size_t t = 0; t < fsz; ++t) acc[t] = (uint32_t)(k * k) * key_styles[(size_t)key_here * fsz + t];
+        den_int = (uint32_t)(255 * k * k);
+    } else if (ml >= 0 && mr >= 0) {
+        int l = key_idx[ml], r = key_idx[mr];
+        rc = add_remapped(guides + (size_t)l * fsz, gi, key_styles + (size_t)ml * fsz, H, W, p,
+                          fbref_pair_tag(l, i), (uint32_t)(r - i), acc);
+        if (rc == 0)
+            rc = add_remapped(guides + (size_t)r * fsz, gi, key_styles + (size_t)mr * fsz, H, W, p,
+                              fbref_pair_tag(r, i), (uint32_t)(i - l), acc);
+        den_int = (uint32_t)(255 * k * k * (r - l));
+    } else {
+        int m = ml >= 0 ? ml : mr;
+        int l = key_idx[m];
+        rc = add_remapped(guides + (size_t)l * fsz, gi, key_styles + (size_t)m * fsz, H, W, p,
+                          fbref_pair_tag(l, i), 1u, acc);
+        den_int = (uint32_t)(255 * k * k);
+    }
+    float den = (float)den_int;
+    for (size_t t = 0; t < fsz; ++t) out[t] = (float)acc[t] / den;
+    free(acc);
+    return rc;
+}
+
+int fbref_interpolate(const uint8_t *guides, int N, int H, int W, const int32_t *key_idx,
+                      const uint8_t *key_styles, int n_keys, const fbref_params *p, float *out)
+{
+    size_t fsz = (size_t)H * W * 3;
+    for (int i = 0; i < N; ++i) {
+        int rc = fbref_interpolate_frame(guides, N, H, W, key_idx, key_styles, n_keys, p, i,
+                                         out + (size_t)i * fsz);
+        if (rc) return rc;
+    }
+    return 0;
+}
