@@ -1,0 +1,363 @@
+#!/usr/bin/env python3
+"""Throughput of the FastBlend hot path (arXiv 2311.09265) on B300.
+
+Default workload: Eq. 2 all-pairs sliding-window blend of a 60-frame 512x512 RGB clip,
+patch 5x5, window 15, 6 patch-match iterations (784 NNFs per step), synthetic guides
+under smooth random affine motion and LUT+noise style frames.  One step = one
+fb_blend_window call over the whole clip (pair set-up, NNF init, all iterations,
+remap, blend, normalise).
+
+Prints ONE JSON line (rank 0):
+  value      blended frames/s, device-resident inputs, CUDA events, max over ranks
+  e2e        the same through the C ABI with pinned HOST buffers (copies inside)
+  roofline   dominant kernel (the Alg. 1 Jacobi iteration) against the dp4a ALU bound
+  cpu_baseline  the CPU oracle on a bounded sample of the same workload
+
+--impl reference times the CPU oracle (the only reference: the paper ships no code).
+Multi-GPU (torchrun): every rank blends its own clip (weak scaling, no data-path
+collective); a gloo barrier and a max-reduce bracket the timed region.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "blended frames/s at 512² w=15; NNF candidate-evals/s vs integer/HBM roofline"
+L2_BYTES = 126 * 1024 * 1024
+FLUSH_BYTES = 512 * 1024 * 1024
+SM_COUNT_NOMINAL = 148
+SM_MAX_MHZ_NOMINAL = 2032.0
+
+
+def parse_args(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("fastblend", "reference"), default="fastblend")
+    ap.add_argument("--workload", default="blend_512", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-frames", type=int, default=1)
+    return ap.parse_args(argv)
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def shard_seed(workload_seed: int, rank: int) -> int:
+    """Rank r blends its own clip; rank 0 blends the named workload itself."""
+    return workload_seed + 7919 * rank
+
+
+def aggregate(n_frames_per_rank: int, steps: int, world: int, max_total_ms: float) -> float:
+    """Whole-job frames/s: every rank's frames over the slowest rank's time."""
+    return world * n_frames_per_rank * steps / (max_total_ms / 1e3)
+
+
+def make_inputs(w: synth.Workload, seed: int):
+    if seed == w.seed:
+        return synth.make_clip(next(k for k, v in synth.WORKLOADS.items() if v is w))
+    if w.motion == "shift":
+        g, _ = synth.shift_clip(w.N, w.H, w.W, seed)
+        s = synth.colour_matrix_styles(g, seed)
+    else:
+        g, _ = synth.affine_clip(w.N, w.H, w.W, seed)
+        s = synth.lut_styles(g, seed)
+    if w.mode == "interpolate":
+        s = s[list(w.keys)].copy()
+    return g, s
+
+
+# ----------------------------------------------------------------------------------
+# clocks during the timed region
+# ----------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.dev = device_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.f, stderr=subprocess.DEVNULL)
+            time.sleep(0.3)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as f:
+            for line in f:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 9:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v.lower() == "active"})
+        power = [float(r[3]) for r in rows if r[3].replace(".", "").isdigit()]
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows),
+                "power_w_median": statistics.median(power) if power else None}
+
+
+# ----------------------------------------------------------------------------------
+# CPU oracle (cpu_baseline and the reference arm)
+# ----------------------------------------------------------------------------------
+def oracle_frame_seconds(w: synth.Workload, g, s, frames):
+    import oracle
+    t0 = time.perf_counter()
+    for i in frames:
+        if w.mode == "blend":
+            oracle.blend_frame(g, s, w.window, i, w.patch, w.iters, seed=w.seed)
+        else:
+            oracle.interpolate_frame(g, list(w.keys), s, i, w.patch, w.iters, seed=w.seed)
+    return time.perf_counter() - t0
+
+
+def sample_frames(w: synth.Workload, n: int):
+    """Interior frames whose window is full (the typical, not the cheapest, frames)."""
+    mid = w.N // 2
+    return [mid + d for d in range(n)]
+
+
+def cpu_baseline(w: synth.Workload, g, s, n_frames: int):
+    import oracle
+    frames = sample_frames(w, n_frames)
+    secs = oracle_frame_seconds(w, g, s, frames)
+    return {"value": len(frames) / secs, "unit": "frames/s", "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{len(frames)} of {w.N} output frames ({frames}) of the same clip, each "
+                      f"with its full window of NNFs; C oracle, OpenMP, {secs:.1f} s"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    w = synth.WORKLOADS[args.workload]
+    g, s = make_inputs(w, w.seed)
+    frames = sample_frames(w, 1)
+    for _ in range(args.warmup):
+        oracle_frame_seconds(w, g, s, frames)
+    total = 0.0
+    for _ in range(args.steps):
+        total += oracle_frame_seconds(w, g, s, frames)
+    value = args.steps * len(frames) / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u8", "data": "synthetic",
+        "config": {"workload": w.name, "frames": w.N, "height": w.H, "width": w.W,
+                   "patch": w.patch, "window": w.window, "iters": w.iters,
+                   "step": "one output frame of the clip (bounded CPU sample)"},
+        "cpu_baseline": {"value": value, "unit": "frames/s", "cores": oracle.num_threads(),
+                         "kind": "oracle",
+                         "sample": f"each step blends output frame {frames[0]} of {w.N}"},
+        "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------------
+# GPU arm
+# ----------------------------------------------------------------------------------
+def iter_ops_per_launch(w: synth.Workload) -> int:
+    """Algorithmic byte-pair ops of one Jacobi-iteration launch (levels = 1): every
+    pair, every pixel, 4 propagation + R random-search candidates, 3k^2 byte pairs."""
+    return w.pairs() * w.H * w.W * (4 + w.random_search_radii()) * 3 * w.patch * w.patch
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    import paper_2311_09265_b300 as fbp
+
+    rank, world, local = dist_env()
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    fbp.build()
+    w = synth.WORKLOADS[args.workload]
+    g, s = make_inputs(w, shard_seed(w.seed, rank))
+    ctx = fbp.Context(local)
+    params = fbp.Params.make(w.patch, w.iters, w.levels, 0, w.seed)
+    g_d = torch.from_numpy(g).cuda()
+    s_d = torch.from_numpy(s).cuda()
+    out = torch.empty((w.N, w.H, w.W, 3), dtype=torch.float32, device="cuda")
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+
+    def step(gg, ss, oo):
+        if w.mode == "blend":
+            return fbp.fb_blend_window(ctx, gg, ss, w.window, params, out=oo)
+        return fbp.fb_interpolate(ctx, gg, list(w.keys), ss, params, out=oo)
+
+    for _ in range(max(args.warmup, 0)):
+        step(g_d, s_d, out)
+    torch.cuda.synchronize()
+
+    # ---- timed region: device-resident inputs ----
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ctx.profile(True)
+    launches0 = ctx.launches
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()                       # evict L2 between steps
+            starts[k].record()
+            step(g_d, s_d, out)
+            ends[k].record()
+        torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    launches = ctx.launches - launches0
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = sum(step_ms)
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = aggregate(w.N, args.steps, world, total_ms)
+    clocks = clk.summary()
+
+    # ---- end to end through the C ABI with pinned host buffers ----
+    e2e = None
+    if not args.no_e2e:
+        g_h = torch.from_numpy(g).pin_memory()
+        s_h = torch.from_numpy(s).pin_memory()
+        o_h = torch.empty((w.N, w.H, w.W, 3), dtype=torch.float32).pin_memory()
+        step(g_h, s_h, o_h)                     # warm (staging buffers)
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            step(g_h, s_h, o_h)                 # synchronous: returns with o_h filled
+        t_e2e = time.perf_counter() - t0
+        if world > 1:
+            t = torch.tensor([t_e2e], dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            t_e2e = float(t.item())
+        e2e = {"value": world * w.N * args.steps / t_e2e, "unit": "frames/s",
+               "h2d_bytes_per_step": int(g_h.numel() + s_h.numel()),
+               "d2h_bytes_per_step": int(o_h.numel() * 4)}
+
+    # ---- roofline of the dominant kernel ----
+    rate, _ = ctx.probe_dp4a()
+    iter_ms, iter_n = prof["iter"]
+    kernel_total_ms = sum(v[0] for v in prof.values())
+    ops = iter_ops_per_launch(w) if w.levels == 1 else None
+    roof = None
+    if iter_n and ops:
+        avg_s = iter_ms / iter_n / 1e3
+        achieved = ops / avg_s / 1e12
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        per_clk_sm = None
+        if clocks.get("sm_mhz"):
+            per_clk_sm = rate / (sms * clocks["sm_mhz"] * 1e6)
+        peak = 4.0 * rate / 1e12
+        peak_basis = "probe at the sampled clock"
+        if per_clk_sm:
+            # dp4a per SM per clock from the probe, x SMs x max clock x 4 byte pairs
+            peak = 4.0 * round(per_clk_sm) * SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+            peak_basis = (f"{round(per_clk_sm)} dp4a/clk/SM (probe) x {SM_COUNT_NOMINAL} SMs x "
+                          f"{SM_MAX_MHZ_NOMINAL:.0f} MHz x 4 byte pairs")
+        roof = {"bound": "alu", "kernel": "nnf_iter (Alg. 1 Jacobi iteration)",
+                "achieved": achieved, "peak": peak, "unit": "T byte-pair ops/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_basis": peak_basis,
+                "avg_launch_ms": iter_ms / iter_n, "launches": iter_n,
+                "share_of_kernel_time": iter_ms / kernel_total_ms if kernel_total_ms else None,
+                "candidate_evals_per_s": w.candidate_evals() * args.steps * world / (total_ms / 1e3),
+                "probe_dp4a_per_s": rate}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": w.name, "frames": w.N, "height": w.H, "width": w.W,
+                   "patch": w.patch, "window": w.window, "iters": w.iters, "levels": w.levels,
+                   "nnfs_per_step": w.pairs(), "candidate_evals_per_step": w.candidate_evals(),
+                   "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"{world} independent clip(s), one per GPU"},
+        "roofline": roof,
+        "e2e": e2e,
+        "gpu_launches": launches,
+        "kernel_ms": {k: v[0] / args.steps for k, v in prof.items() if v[1]},
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(w, g, s, args.cpu_sample_frames)
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -94,6 +94,35 @@ uint64_t fb_ctx_launches(const fb_ctx *ctx);
 /* Device scratch currently held by the context, in bytes. */
 size_t fb_ctx_scratch_bytes(const fb_ctx *ctx);
 
+/* Kernel families, for fb_ctx_profile_read. */
+typedef enum fb_kernel_kind {
+    FB_K_PREP = 0,      /* guide frame -> row patches + patch energies           */
+    FB_K_DOWNSAMPLE,    /* pyramid step                                          */
+    FB_K_STYLE,         /* style frame -> 4-byte pixels                          */
+    FB_K_INIT,          /* initial NNF and its Eq. 1 errors                      */
+    FB_K_ITER,          /* one Jacobi iteration of Alg. 1 (propagation + search) */
+    FB_K_UNPACK,        /* packed NNF -> int32 (row, col)                        */
+    FB_K_PACK,          /* int32 (row, col) -> packed NNF                        */
+    FB_K_COMBINE,       /* Alg. 2 remap fused with Eq. 2 / keyframe weights      */
+    FB_K_COUNT
+} fb_kernel_kind;
+
+/* Diagnostics: enable = 1 clears and starts recording a CUDA event pair around every
+ * kernel this context launches (on the caller's stream); enable = 0 stops.  Costs
+ * two event records per launch while on. */
+int fb_ctx_profile(fb_ctx *ctx, int enable);
+
+/* Waits for the recorded events and writes, per fb_kernel_kind, the summed device
+ * time in milliseconds (ms[FB_K_COUNT]) and the number of launches
+ * (launches[FB_K_COUNT]) recorded since profiling was last enabled. */
+int fb_ctx_profile_read(fb_ctx *ctx, double *ms, uint64_t *launches);
+
+/* Diagnostics: measures the device's throughput of dp4a (four byte products summed
+ * into a 32-bit accumulator, the instruction that evaluates Eq. 1) with a
+ * register-only kernel on every SM.  Writes dp4a instructions per second and the
+ * kernel's duration.  Synchronous.  Not part of the method. */
+int fb_probe_dp4a(fb_ctx *ctx, double *dp4a_per_s, double *ms);
+
 /* Philox stream id of the ordered pair (source frame j -> target frame i), as used
  * by fb_blend_window and fb_interpolate: (j << 16) | i. */
 uint32_t fb_pair_tag(int j, int i);

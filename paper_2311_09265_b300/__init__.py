@@ -1,0 +1,260 @@
+"""FastBlend hot path (arXiv 2311.09265) on B300 -- Python binding of libfb.so.
+
+This module only marshals arguments: every step of the path (patch matching, remap,
+blend, interpolation) runs in the CUDA kernels of libfb.so behind the C ABI declared
+in include/fb.h.  PyTorch supplies device memory and streams.  There is no CPU
+fallback: if libfb.so is missing or cannot load, every call raises.
+
+Names follow the C ABI: fb_nnf, fb_remap, fb_blend_window, fb_interpolate, plus
+Context (fb_ctx_*) and Params (fb_params).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional, Sequence
+
+import torch
+
+from ._build import LIB_PATH, build  # noqa: F401  (build is re-exported)
+
+FB_OK, FB_ERR_ARG, FB_ERR_CUDA, FB_ERR_OOM, FB_ERR_TIMEOUT, FB_ERR_UNSUPPORTED = range(6)
+
+HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_error",
+                    "fb_status_string", "fb_ctx_launches", "fb_ctx_scratch_bytes",
+                    "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a", "fb_pair_tag",
+                    "fb_nnf", "fb_remap", "fb_blend_window", "fb_interpolate")
+
+# fb_kernel_kind, in header order.
+KERNEL_KINDS = ("prep", "downsample", "style", "init", "iter", "unpack", "pack", "combine")
+
+
+class Params(ctypes.Structure):
+    """fb_params: Alg. 1 parameters (patch k, iterations, pyramid levels, r0, seed)."""
+    _fields_ = [("patch", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("levels", ctypes.c_int32), ("r0", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("pair_tag", ctypes.c_uint32),
+                ("flags", ctypes.c_uint32)]
+
+    @classmethod
+    def make(cls, patch: int, iters: int, levels: int = 1, r0: int = 0, seed: int = 0,
+             pair_tag: int = 0) -> "Params":
+        return cls(patch, iters, levels, r0, seed & 0xFFFFFFFFFFFFFFFF, pair_tag & 0xFFFFFFFF, 0)
+
+
+class FastBlendError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{_STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_STATUS_NAMES = {0: "FB_OK", 1: "FB_ERR_ARG", 2: "FB_ERR_CUDA", 3: "FB_ERR_OOM",
+                 4: "FB_ERR_TIMEOUT", 5: "FB_ERR_UNSUPPORTED"}
+
+_lib: Optional[ctypes.CDLL] = None
+_vp = ctypes.c_void_p
+
+
+def lib() -> ctypes.CDLL:
+    """Load libfb.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with __graft_entry__.build() "
+                               "or python -m paper_2311_09265_b300._build")
+        L = ctypes.CDLL(LIB_PATH)
+        L.fb_ctx_create.argtypes = [ctypes.POINTER(_vp), ctypes.c_int]
+        L.fb_ctx_destroy.argtypes = [_vp]
+        L.fb_ctx_sync.argtypes = [_vp, _vp]
+        L.fb_last_error.argtypes = [_vp]
+        L.fb_last_error.restype = ctypes.c_char_p
+        L.fb_status_string.argtypes = [ctypes.c_int]
+        L.fb_status_string.restype = ctypes.c_char_p
+        L.fb_ctx_launches.argtypes = [_vp]
+        L.fb_ctx_launches.restype = ctypes.c_uint64
+        L.fb_ctx_scratch_bytes.argtypes = [_vp]
+        L.fb_ctx_scratch_bytes.restype = ctypes.c_size_t
+        L.fb_ctx_profile.argtypes = [_vp, ctypes.c_int]
+        L.fb_ctx_profile_read.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
+                                          ctypes.POINTER(ctypes.c_uint64)]
+        L.fb_probe_dp4a.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
+                                    ctypes.POINTER(ctypes.c_double)]
+        L.fb_probe_dp4a.restype = ctypes.c_int
+        L.fb_pair_tag.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.fb_pair_tag.restype = ctypes.c_uint32
+        P = ctypes.POINTER(Params)
+        L.fb_nnf.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp, _vp, _vp]
+        L.fb_remap.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
+        L.fb_blend_window.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                      ctypes.c_int, P, _vp, _vp]
+        L.fb_interpolate.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
+                                     _vp, ctypes.c_int, P, _vp, _vp]
+        for f in ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_ctx_profile",
+                  "fb_ctx_profile_read", "fb_nnf", "fb_remap",
+                  "fb_blend_window", "fb_interpolate"):
+            getattr(L, f).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def fb_pair_tag(j: int, i: int) -> int:
+    return lib().fb_pair_tag(j, i)
+
+
+class Context:
+    """fb_ctx: owns device scratch for one CUDA device.  Not thread-safe."""
+
+    def __init__(self, device: int = 0):
+        h = _vp()
+        rc = lib().fb_ctx_create(ctypes.byref(h), device)
+        if rc != FB_OK:
+            raise FastBlendError(rc, lib().fb_last_error(None).decode())
+        self._h = h
+        self.device = device
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().fb_ctx_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover - best effort
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def check(self, rc: int) -> None:
+        if rc != FB_OK:
+            raise FastBlendError(rc, lib().fb_last_error(self._h).decode())
+
+    @property
+    def launches(self) -> int:
+        return int(lib().fb_ctx_launches(self._h))
+
+    @property
+    def scratch_bytes(self) -> int:
+        return int(lib().fb_ctx_scratch_bytes(self._h))
+
+    def profile(self, enable: bool) -> None:
+        """Start (clearing earlier records) or stop per-launch CUDA-event timing."""
+        self.check(lib().fb_ctx_profile(self._h, 1 if enable else 0))
+
+    def profile_read(self) -> dict:
+        """{kernel kind: (total ms, launches)} recorded since profiling was enabled."""
+        n = len(KERNEL_KINDS)
+        ms = (ctypes.c_double * n)()
+        cnt = (ctypes.c_uint64 * n)()
+        self.check(lib().fb_ctx_profile_read(self._h, ms, cnt))
+        return {k: (float(ms[i]), int(cnt[i])) for i, k in enumerate(KERNEL_KINDS)}
+
+    def probe_dp4a(self):
+        """(dp4a instructions per second, kernel ms) of a register-only probe."""
+        rate, ms = ctypes.c_double(), ctypes.c_double()
+        self.check(lib().fb_probe_dp4a(self._h, ctypes.byref(rate), ctypes.byref(ms)))
+        return rate.value, ms.value
+
+    def sync(self, stream: Optional[torch.cuda.Stream] = None) -> None:
+        self.check(lib().fb_ctx_sync(self._h, _stream_handle(stream, self.device)))
+
+
+def _stream_handle(stream, device) -> int:
+    if stream is None:
+        stream = torch.cuda.current_stream(device)
+    return stream.cuda_stream
+
+
+def _ptr(t: Optional[torch.Tensor], dtype: torch.dtype, name: str):
+    if t is None:
+        return None
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t.data_ptr()
+
+
+def _shape(t: torch.Tensor, want: Sequence[int], name: str) -> None:
+    if tuple(t.shape) != tuple(want):
+        raise ValueError(f"{name} must have shape {tuple(want)}, got {tuple(t.shape)}")
+
+
+def fb_nnf(ctx: Context, src_guide: torch.Tensor, tgt_guide: torch.Tensor, params: Params,
+           init_nnf: Optional[torch.Tensor] = None, nnf_out: Optional[torch.Tensor] = None,
+           err_out: Optional[torch.Tensor] = None, stream=None):
+    """Alg. 1 NNF(src -> tgt) for one pair of H x W x 3 uint8 CUDA tensors.
+    Returns (nnf (H,W,2) int32, err (H,W) int32 holding uint32 values)."""
+    H, W = int(src_guide.shape[0]), int(src_guide.shape[1])
+    _shape(src_guide, (H, W, 3), "src_guide")
+    _shape(tgt_guide, (H, W, 3), "tgt_guide")
+    dev = src_guide.device
+    if nnf_out is None:
+        nnf_out = torch.empty((H, W, 2), dtype=torch.int32, device=dev)
+    if err_out is None:
+        err_out = torch.empty((H, W), dtype=torch.int32, device=dev)
+    if init_nnf is not None:
+        _shape(init_nnf, (H, W, 2), "init_nnf")
+    rc = lib().fb_nnf(ctx.handle, _ptr(src_guide, torch.uint8, "src_guide"),
+                      _ptr(tgt_guide, torch.uint8, "tgt_guide"), H, W, ctypes.byref(params),
+                      _ptr(init_nnf, torch.int32, "init_nnf"),
+                      _ptr(nnf_out, torch.int32, "nnf_out"), _ptr(err_out, torch.int32, "err_out"),
+                      _stream_handle(stream, ctx.device))
+    ctx.check(rc)
+    return nnf_out, err_out
+
+
+def fb_remap(ctx: Context, src_style: torch.Tensor, nnf: torch.Tensor, patch: int,
+             out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Alg. 2 remap of an H x W x 3 uint8 style through an (H,W,2) int32 NNF."""
+    H, W = int(src_style.shape[0]), int(src_style.shape[1])
+    _shape(src_style, (H, W, 3), "src_style")
+    _shape(nnf, (H, W, 2), "nnf")
+    if out is None:
+        out = torch.empty((H, W, 3), dtype=torch.float32, device=src_style.device)
+    rc = lib().fb_remap(ctx.handle, _ptr(src_style, torch.uint8, "src_style"),
+                        _ptr(nnf, torch.int32, "nnf"), H, W, patch,
+                        _ptr(out, torch.float32, "out"), _stream_handle(stream, ctx.device))
+    ctx.check(rc)
+    return out
+
+
+def fb_blend_window(ctx: Context, guides: torch.Tensor, styles: torch.Tensor, window: int,
+                    params: Params, out: Optional[torch.Tensor] = None,
+                    stream=None) -> torch.Tensor:
+    """Eq. 2 window blend.  guides/styles (N,H,W,3) uint8, both CUDA (async) or both
+    CPU (the library stages them; synchronous).  Returns (N,H,W,3) float32."""
+    N, H, W = (int(s) for s in guides.shape[:3])
+    _shape(guides, (N, H, W, 3), "guides")
+    _shape(styles, (N, H, W, 3), "styles")
+    if out is None:
+        out = torch.empty((N, H, W, 3), dtype=torch.float32, device=guides.device,
+                          pin_memory=(not guides.is_cuda))
+    rc = lib().fb_blend_window(ctx.handle, _ptr(guides, torch.uint8, "guides"),
+                               _ptr(styles, torch.uint8, "styles"), N, H, W, window,
+                               ctypes.byref(params), _ptr(out, torch.float32, "out"),
+                               _stream_handle(stream, ctx.device))
+    ctx.check(rc)
+    return out
+
+
+def fb_interpolate(ctx: Context, guides: torch.Tensor, key_idx: Sequence[int],
+                   key_styles: torch.Tensor, params: Params, out: Optional[torch.Tensor] = None,
+                   stream=None) -> torch.Tensor:
+    """Sec. 3.5.2 keyframe interpolation.  guides (N,H,W,3) uint8, key_styles
+    (n_keys,H,W,3) uint8, key_idx a host sequence of increasing frame indices."""
+    N, H, W = (int(s) for s in guides.shape[:3])
+    _shape(guides, (N, H, W, 3), "guides")
+    keys = (ctypes.c_int32 * len(key_idx))(*[int(k) for k in key_idx])
+    _shape(key_styles, (len(key_idx), H, W, 3), "key_styles")
+    if out is None:
+        out = torch.empty((N, H, W, 3), dtype=torch.float32, device=guides.device,
+                          pin_memory=(not guides.is_cuda))
+    rc = lib().fb_interpolate(ctx.handle, _ptr(guides, torch.uint8, "guides"), N, H, W,
+                              ctypes.cast(keys, _vp), _ptr(key_styles, torch.uint8, "key_styles"),
+                              len(key_idx), ctypes.byref(params), _ptr(out, torch.float32, "out"),
+                              _stream_handle(stream, ctx.device))
+    ctx.check(rc)
+    return out

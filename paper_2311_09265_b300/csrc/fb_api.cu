@@ -1,0 +1,724 @@
+// fb_api.cu -- the C ABI of libfb.so (declared in include/fb.h): argument checks,
+// the per-call plan (pairs, output jobs, scratch layout), the scratch arena and the
+// launch sequence of the FastBlend hot path.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fb.h"
+#include "fb_internal.h"
+
+struct fb_ctx {
+    int device = 0;
+    char* arena = nullptr;          // device scratch, grown on demand
+    size_t arena_cap = 0;
+    char* pinned = nullptr;         // pinned host staging for the pair/job tables
+    size_t pinned_cap = 0;
+    cudaEvent_t upload_done = nullptr;
+    bool upload_pending = false;
+    uint64_t launches = 0;
+    int* dev_status = nullptr;      // device-side error word written by bounded waits
+    std::string err;
+    // Optional per-launch CUDA-event timing (fb_ctx_profile).
+    bool profiling = false;
+    std::vector<cudaEvent_t> ev_pool;
+    size_t ev_used = 0;
+    struct Rec {
+        int kind;
+        cudaEvent_t a, b;
+    };
+    std::vector<Rec> recs;
+};
+
+namespace {
+
+using fb::JobDesc;
+using fb::LevelGeom;
+using fb::PairDesc;
+
+thread_local std::string g_null_ctx_err;
+
+// Bytes of F/E ping-pong scratch one chunk of pairs may use.
+constexpr size_t kPairBudgetBytes = size_t(8) << 30;
+constexpr int kMaxChunkPairs = 65535;  // grid.y limit
+
+int fail(fb_ctx* ctx, int status, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    if (ctx)
+        ctx->err = buf;
+    else
+        g_null_ctx_err = buf;
+    return status;
+}
+
+#define FB_CUDA(ctx, expr)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? FB_ERR_OOM : FB_ERR_CUDA,    \
+                        "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_), __FILE__, __LINE__); \
+    } while (0)
+
+cudaEvent_t next_event(fb_ctx* ctx) {
+    if (ctx->ev_used == ctx->ev_pool.size()) {
+        cudaEvent_t e = nullptr;
+        if (cudaEventCreate(&e) != cudaSuccess) {
+            cudaGetLastError();
+            return nullptr;
+        }
+        ctx->ev_pool.push_back(e);
+    }
+    return ctx->ev_pool[ctx->ev_used++];
+}
+
+// Launch through `expr`; with profiling on, bracket it with an event pair on `st`.
+#define FB_LAUNCH(ctx, st, kind, expr)                                        \
+    do {                                                                      \
+        cudaEvent_t ea_ = nullptr, eb_ = nullptr;                             \
+        if ((ctx)->profiling) {                                               \
+            ea_ = next_event(ctx);                                            \
+            eb_ = next_event(ctx);                                            \
+            if (ea_ && eb_) FB_CUDA(ctx, cudaEventRecord(ea_, st));           \
+        }                                                                     \
+        FB_CUDA(ctx, (expr));                                                 \
+        ++(ctx)->launches;                                                    \
+        if (ea_ && eb_) {                                                     \
+            FB_CUDA(ctx, cudaEventRecord(eb_, st));                           \
+            (ctx)->recs.push_back(fb_ctx::Rec{(kind), ea_, eb_});             \
+        }                                                                     \
+    } while (0)
+
+// Restores the caller's current device on scope exit.
+struct DeviceGuard {
+    int prev = -1;
+    bool ok = false;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        ok = cudaSetDevice(dev) == cudaSuccess;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+// Bump allocator over the arena.  With base == nullptr it only measures.
+struct Carver {
+    char* base;
+    size_t off = 0;
+    explicit Carver(char* b) : base(b) {}
+    template <class T>
+    T* take(size_t n) {
+        off = align_up(off, 256);
+        T* p = base ? reinterpret_cast<T*>(base + off) : nullptr;
+        off += n * sizeof(T);
+        return p;
+    }
+};
+
+int ensure_arena(fb_ctx* ctx, size_t bytes) {
+    if (bytes <= ctx->arena_cap) return FB_OK;
+    // Work already enqueued may still use the old block.
+    FB_CUDA(ctx, cudaDeviceSynchronize());
+    if (ctx->arena) {
+        cudaFree(ctx->arena);
+        ctx->arena = nullptr;
+        ctx->arena_cap = 0;
+    }
+    const size_t want = align_up(bytes + bytes / 8, size_t(1) << 20);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&ctx->arena), want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        ctx->arena = nullptr;
+        return fail(ctx, FB_ERR_OOM, "device scratch of %zu bytes: %s", want, cudaGetErrorString(e));
+    }
+    ctx->arena_cap = want;
+    return FB_OK;
+}
+
+int ensure_pinned(fb_ctx* ctx, size_t bytes) {
+    if (ctx->upload_pending) {
+        FB_CUDA(ctx, cudaEventSynchronize(ctx->upload_done));
+        ctx->upload_pending = false;
+    }
+    if (bytes <= ctx->pinned_cap) return FB_OK;
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    ctx->pinned = nullptr;
+    ctx->pinned_cap = 0;
+    const size_t want = align_up(bytes, size_t(1) << 16);
+    cudaError_t e = cudaMallocHost(reinterpret_cast<void**>(&ctx->pinned), want);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, FB_ERR_OOM, "pinned staging of %zu bytes: %s", want, cudaGetErrorString(e));
+    }
+    ctx->pinned_cap = want;
+    return FB_OK;
+}
+
+enum class Mem { Device, Host, Invalid };
+
+Mem classify(const fb_ctx* ctx, const void* p) {
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return Mem::Host;
+    }
+    if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged)
+        return a.device == ctx->device ? Mem::Device : Mem::Invalid;
+    return Mem::Host;
+}
+
+int check_params(fb_ctx* ctx, const fb_params* p, int H, int W) {
+    if (!p) return fail(ctx, FB_ERR_ARG, "params is NULL");
+    if (p->patch < 3 || p->patch > 9 || (p->patch & 1) == 0)
+        return fail(ctx, FB_ERR_ARG, "patch must be odd in [3, 9], got %d", p->patch);
+    if (p->iters < 0 || p->iters > 65534)
+        return fail(ctx, FB_ERR_ARG, "iters must be in [0, 65534], got %d", p->iters);
+    if (p->levels < 1 || p->levels > 16)
+        return fail(ctx, FB_ERR_ARG, "levels must be in [1, 16], got %d", p->levels);
+    if (p->r0 < 0 || p->r0 > (1 << 20))
+        return fail(ctx, FB_ERR_ARG, "r0 must be in [0, 2^20], got %d", p->r0);
+    if (p->flags != 0) return fail(ctx, FB_ERR_ARG, "flags must be 0");
+    if (H < p->patch || W < p->patch || H > 32767 || W > 32767)
+        return fail(ctx, FB_ERR_ARG, "image %dx%d outside [patch, 32767]", H, W);
+    return FB_OK;
+}
+
+struct Levels {
+    int n;
+    int h[16], w[16];
+};
+
+Levels level_dims(int H, int W, int levels) {
+    Levels L;
+    L.n = levels;
+    L.h[0] = H;
+    L.w[0] = W;
+    for (int l = 1; l < levels; ++l) {
+        L.h[l] = (L.h[l - 1] + 1) / 2;
+        L.w[l] = (L.w[l - 1] + 1) / 2;
+    }
+    return L;
+}
+
+// Device buffers of one call.
+struct Buffers {
+    uint8_t* raw[16] = {};       // downsampled guides, levels >= 1
+    uint32_t* rp[16] = {};
+    uint32_t* en[16] = {};
+    uint32_t* styles = nullptr;
+    uint32_t *FA = nullptr, *FB = nullptr, *EA = nullptr, *EB = nullptr;
+    PairDesc* pairs = nullptr;
+    JobDesc* jobs = nullptr;
+    uint8_t* in_guides = nullptr;  // host-staging copies
+    uint8_t* in_styles = nullptr;
+    float* in_out = nullptr;
+};
+
+void carve(Carver& cv, Buffers& b, const Levels& L, int k, int n_guides, int n_styles,
+           size_t chunk_pairs, size_t n_pairs, size_t n_jobs, bool staging, size_t guide_bytes,
+           size_t style_bytes, size_t out_floats) {
+    const int rpw = fb::rowpatch_words(k);
+    for (int l = 0; l < L.n; ++l) {
+        const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];
+        if (l > 0) b.raw[l] = cv.take<uint8_t>(static_cast<size_t>(n_guides) * npx * 3);
+        b.rp[l] = cv.take<uint32_t>(static_cast<size_t>(n_guides) * npx * rpw);
+        b.en[l] = cv.take<uint32_t>(static_cast<size_t>(n_guides) * npx);
+    }
+    const size_t npx0 = static_cast<size_t>(L.h[0]) * L.w[0];
+    b.styles = cv.take<uint32_t>(static_cast<size_t>(n_styles) * npx0);
+    b.FA = cv.take<uint32_t>(chunk_pairs * npx0);
+    b.FB = cv.take<uint32_t>(chunk_pairs * npx0);
+    b.EA = cv.take<uint32_t>(chunk_pairs * npx0);
+    b.EB = cv.take<uint32_t>(chunk_pairs * npx0);
+    b.pairs = cv.take<PairDesc>(n_pairs > 0 ? n_pairs : 1);
+    b.jobs = cv.take<JobDesc>(n_jobs > 0 ? n_jobs : 1);
+    if (staging) {
+        b.in_guides = cv.take<uint8_t>(guide_bytes);
+        b.in_styles = cv.take<uint8_t>(style_bytes);
+        b.in_out = cv.take<float>(out_floats);
+    }
+}
+
+int upload_tables(fb_ctx* ctx, const std::vector<PairDesc>& pairs, const std::vector<JobDesc>& jobs,
+                  Buffers& b, cudaStream_t st) {
+    const size_t pb = pairs.size() * sizeof(PairDesc), jb = jobs.size() * sizeof(JobDesc);
+    if (pb + jb == 0) return FB_OK;
+    int rc = ensure_pinned(ctx, pb + jb + 256);
+    if (rc) return rc;
+    if (pb) std::memcpy(ctx->pinned, pairs.data(), pb);
+    if (jb) std::memcpy(ctx->pinned + align_up(pb, 256), jobs.data(), jb);
+    if (pb) FB_CUDA(ctx, cudaMemcpyAsync(b.pairs, ctx->pinned, pb, cudaMemcpyHostToDevice, st));
+    if (jb)
+        FB_CUDA(ctx, cudaMemcpyAsync(b.jobs, ctx->pinned + align_up(pb, 256), jb,
+                                     cudaMemcpyHostToDevice, st));
+    FB_CUDA(ctx, cudaEventRecord(ctx->upload_done, st));
+    ctx->upload_pending = true;
+    return FB_OK;
+}
+
+// Guide frames (n of them, contiguous at `frames`) -> row patches + energies at every
+// pyramid level, into guide slots [slot0, slot0 + n).
+int prep_guides(fb_ctx* ctx, const Buffers& b, const Levels& L, int k, const uint8_t* frames,
+                int n, int slot0, cudaStream_t st) {
+    const int rpw = fb::rowpatch_words(k);
+    const uint8_t* cur = frames;
+    for (int l = 0; l < L.n; ++l) {
+        const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];
+        if (l > 0) {
+            uint8_t* dst = b.raw[l] + static_cast<size_t>(slot0) * npx * 3;
+            FB_LAUNCH(ctx, st, FB_K_DOWNSAMPLE, fb::launch_downsample(cur, n, L.h[l - 1], L.w[l - 1], dst, st));
+            cur = dst;
+        }
+        FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(k, cur, n, L.h[l], L.w[l],
+                                              b.rp[l] + static_cast<size_t>(slot0) * npx * rpw,
+                                              b.en[l] + static_cast<size_t>(slot0) * npx, st));
+    }
+    return FB_OK;
+}
+
+// Alg. 1 for pairs [pair0, pair0 + n) of the uploaded table.  The final level-0
+// field and errors are returned in *F_out / *E_out (one of the ping-pong buffers).
+int run_nnf(fb_ctx* ctx, const Buffers& b, const Levels& L, const fb_params* p, int pair0, int n,
+            const int32_t* user_init, cudaStream_t st, uint32_t** F_out, uint32_t** E_out) {
+    const int k = p->patch;
+    uint32_t *Fc = b.FA, *Ec = b.EA, *Fo = b.FB, *Eo = b.EB;
+    for (int l = L.n - 1; l >= 0; --l) {
+        LevelGeom g{L.h[l], L.w[l], b.rp[l], b.en[l]};
+        if (l == L.n - 1) {
+            FB_LAUNCH(ctx, st, FB_K_INIT, fb::launch_nnf_init(k, b.pairs, pair0, n, g, user_init ? 2 : 0, nullptr,
+                                               0, 0, user_init, p->seed, l, Fc, Ec, st));
+        } else {
+            FB_LAUNCH(ctx, st, FB_K_INIT, fb::launch_nnf_init(k, b.pairs, pair0, n, g, 1, Fc, L.h[l + 1],
+                                               L.w[l + 1], nullptr, p->seed, l, Fo, Eo, st));
+            std::swap(Fc, Fo);
+            std::swap(Ec, Eo);
+        }
+        const int r0 = p->r0 > 0 ? p->r0 : (L.h[l] > L.w[l] ? L.h[l] : L.w[l]);
+        for (int it = 0; it < p->iters; ++it) {
+            FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_nnf_iter(k, b.pairs, pair0, n, g, r0, p->seed, l, it, Fc, Ec,
+                                               Fo, Eo, st));
+            std::swap(Fc, Fo);
+            std::swap(Ec, Eo);
+        }
+    }
+    *F_out = Fc;
+    *E_out = Ec;
+    return FB_OK;
+}
+
+// Group consecutive output jobs into chunks whose pairs fit the F/E budget.
+struct Chunk {
+    int job0, n_jobs, pair0, n_pairs;
+};
+
+int make_chunks(fb_ctx* ctx, const std::vector<JobDesc>& jobs, size_t npx0,
+                std::vector<Chunk>& chunks, size_t& max_pairs) {
+    const size_t per_pair = npx0 * 4 * sizeof(uint32_t);
+    size_t cap = kPairBudgetBytes / per_pair;
+    if (cap > static_cast<size_t>(kMaxChunkPairs)) cap = kMaxChunkPairs;
+    if (cap < 1) cap = 1;
+    max_pairs = 0;
+    Chunk cur{0, 0, jobs.empty() ? 0 : jobs[0].first_pair, 0};
+    for (size_t j = 0; j < jobs.size(); ++j) {
+        const size_t np = static_cast<size_t>(jobs[j].n_pairs);
+        if (np > cap)
+            return fail(ctx, FB_ERR_OOM, "output frame needs %zu NNFs; the pair budget holds %zu",
+                        np, cap);
+        if (cur.n_pairs + np > cap && cur.n_jobs > 0) {
+            chunks.push_back(cur);
+            cur = Chunk{static_cast<int>(j), 0, jobs[j].first_pair, 0};
+        }
+        cur.n_jobs += 1;
+        cur.n_pairs += static_cast<int>(np);
+    }
+    if (cur.n_jobs > 0) chunks.push_back(cur);
+    for (const Chunk& c : chunks)
+        if (static_cast<size_t>(c.n_pairs) > max_pairs) max_pairs = c.n_pairs;
+    return FB_OK;
+}
+
+// Shared driver of fb_blend_window and fb_interpolate: N guide frames, a style stack,
+// a pair table and one job per output frame.
+int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const uint8_t* styles,
+                 int n_styles, const std::vector<PairDesc>& pairs, const std::vector<JobDesc>& jobs,
+                 const fb_params* p, float* out, cudaStream_t st) {
+    const int k = p->patch;
+    const Levels L = level_dims(H, W, p->levels);
+    const size_t npx0 = static_cast<size_t>(H) * W;
+
+    const Mem mg = classify(ctx, guides), ms = classify(ctx, styles), mo = classify(ctx, out);
+    if (mg == Mem::Invalid || ms == Mem::Invalid || mo == Mem::Invalid)
+        return fail(ctx, FB_ERR_ARG, "a device pointer belongs to another device");
+    if (!(mg == ms && ms == mo))
+        return fail(ctx, FB_ERR_ARG, "guides, styles and out must all be device or all host memory");
+    const bool staging = mg == Mem::Host;
+
+    std::vector<Chunk> chunks;
+    size_t max_pairs = 0;
+    int rc = make_chunks(ctx, jobs, npx0, chunks, max_pairs);
+    if (rc) return rc;
+
+    const size_t guide_bytes = static_cast<size_t>(N) * npx0 * 3;
+    const size_t style_bytes = static_cast<size_t>(n_styles) * npx0 * 3;
+    const size_t out_floats = static_cast<size_t>(N) * npx0 * 3;
+    Buffers b;
+    Carver measure(nullptr);
+    carve(measure, b, L, k, N, n_styles, max_pairs, pairs.size(), jobs.size(), staging, guide_bytes,
+          style_bytes, out_floats);
+    rc = ensure_arena(ctx, measure.off);
+    if (rc) return rc;
+    Carver cv(ctx->arena);
+    carve(cv, b, L, k, N, n_styles, max_pairs, pairs.size(), jobs.size(), staging, guide_bytes,
+          style_bytes, out_floats);
+
+    rc = upload_tables(ctx, pairs, jobs, b, st);
+    if (rc) return rc;
+    const uint8_t* g_dev = guides;
+    const uint8_t* s_dev = styles;
+    float* o_dev = out;
+    if (staging) {
+        FB_CUDA(ctx, cudaMemcpyAsync(b.in_guides, guides, guide_bytes, cudaMemcpyHostToDevice, st));
+        FB_CUDA(ctx, cudaMemcpyAsync(b.in_styles, styles, style_bytes, cudaMemcpyHostToDevice, st));
+        g_dev = b.in_guides;
+        s_dev = b.in_styles;
+        o_dev = b.in_out;
+    }
+
+    rc = prep_guides(ctx, b, L, k, g_dev, N, 0, st);
+    if (rc) return rc;
+    FB_LAUNCH(ctx, st, FB_K_STYLE, fb::launch_style_rgbx(s_dev, static_cast<size_t>(n_styles) * npx0, b.styles, st));
+
+    for (const Chunk& c : chunks) {
+        uint32_t *F = nullptr, *E = nullptr;
+        if (c.n_pairs > 0) {
+            rc = run_nnf(ctx, b, L, p, c.pair0, c.n_pairs, nullptr, st, &F, &E);
+            if (rc) return rc;
+        }
+        FB_LAUNCH(ctx, st, FB_K_COMBINE, fb::launch_combine(k, b.jobs, c.job0, c.n_jobs, b.pairs, c.pair0, F,
+                                          b.styles, H, W, o_dev, st));
+    }
+
+    if (staging) {
+        FB_CUDA(ctx, cudaMemcpyAsync(out, o_dev, out_floats * sizeof(float), cudaMemcpyDeviceToHost,
+                                     st));
+        FB_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    return FB_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fb_ctx_create(fb_ctx** out, int device) {
+    if (!out) return fail(nullptr, FB_ERR_ARG, "out is NULL");
+    *out = nullptr;
+    int n = 0;
+    cudaError_t e = cudaGetDeviceCount(&n);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(nullptr, FB_ERR_CUDA, "cudaGetDeviceCount: %s", cudaGetErrorString(e));
+    }
+    if (device < 0 || device >= n)
+        return fail(nullptr, FB_ERR_ARG, "device %d out of range (%d devices)", device, n);
+    DeviceGuard dg(device);
+    if (!dg.ok) return fail(nullptr, FB_ERR_CUDA, "cudaSetDevice(%d) failed", device);
+    fb_ctx* ctx = new fb_ctx();
+    ctx->device = device;
+    if (cudaEventCreateWithFlags(&ctx->upload_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&ctx->dev_status), sizeof(int)) != cudaSuccess ||
+        cudaMemset(ctx->dev_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaGetLastError();
+        if (ctx->upload_done) cudaEventDestroy(ctx->upload_done);
+        if (ctx->dev_status) cudaFree(ctx->dev_status);
+        delete ctx;
+        return fail(nullptr, FB_ERR_CUDA, "context set-up failed on device %d", device);
+    }
+    *out = ctx;
+    return FB_OK;
+}
+
+int fb_ctx_destroy(fb_ctx* ctx) {
+    if (!ctx) return FB_OK;
+    DeviceGuard dg(ctx->device);
+    cudaDeviceSynchronize();
+    if (ctx->arena) cudaFree(ctx->arena);
+    if (ctx->pinned) cudaFreeHost(ctx->pinned);
+    if (ctx->upload_done) cudaEventDestroy(ctx->upload_done);
+    if (ctx->dev_status) cudaFree(ctx->dev_status);
+    for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    delete ctx;
+    return FB_OK;
+}
+
+int fb_ctx_sync(fb_ctx* ctx, void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg(ctx->device);
+    FB_CUDA(ctx, cudaStreamSynchronize(static_cast<cudaStream_t>(stream)));
+    int status = 0;
+    FB_CUDA(ctx, cudaMemcpy(&status, ctx->dev_status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (status != 0) {
+        FB_CUDA(ctx, cudaMemset(ctx->dev_status, 0, sizeof(int)));
+        return fail(ctx, FB_ERR_TIMEOUT, "a bounded device wait expired (code %d)", status);
+    }
+    return FB_OK;
+}
+
+const char* fb_last_error(const fb_ctx* ctx) {
+    return ctx ? ctx->err.c_str() : g_null_ctx_err.c_str();
+}
+
+const char* fb_status_string(int status) {
+    switch (status) {
+        case FB_OK: return "FB_OK";
+        case FB_ERR_ARG: return "FB_ERR_ARG";
+        case FB_ERR_CUDA: return "FB_ERR_CUDA";
+        case FB_ERR_OOM: return "FB_ERR_OOM";
+        case FB_ERR_TIMEOUT: return "FB_ERR_TIMEOUT";
+        case FB_ERR_UNSUPPORTED: return "FB_ERR_UNSUPPORTED";
+        default: return "FB_ERR_UNKNOWN";
+    }
+}
+
+uint64_t fb_ctx_launches(const fb_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int fb_ctx_profile(fb_ctx* ctx, int enable) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    DeviceGuard dg(ctx->device);
+    if (enable) {
+        // Events of an earlier record may still be pending; wait before reusing them.
+        for (const fb_ctx::Rec& r : ctx->recs) FB_CUDA(ctx, cudaEventSynchronize(r.b));
+        ctx->recs.clear();
+        ctx->ev_used = 0;
+    }
+    ctx->profiling = enable != 0;
+    return FB_OK;
+}
+
+int fb_ctx_profile_read(fb_ctx* ctx, double* ms, uint64_t* launches) {
+    if (!ctx || !ms || !launches) return fail(ctx, FB_ERR_ARG, "NULL argument");
+    DeviceGuard dg(ctx->device);
+    for (int k = 0; k < FB_K_COUNT; ++k) {
+        ms[k] = 0.0;
+        launches[k] = 0;
+    }
+    for (const fb_ctx::Rec& r : ctx->recs) {
+        FB_CUDA(ctx, cudaEventSynchronize(r.b));
+        float t = 0.f;
+        FB_CUDA(ctx, cudaEventElapsedTime(&t, r.a, r.b));
+        ms[r.kind] += t;
+        launches[r.kind] += 1;
+    }
+    return FB_OK;
+}
+
+size_t fb_ctx_scratch_bytes(const fb_ctx* ctx) { return ctx ? ctx->arena_cap : 0; }
+
+int fb_probe_dp4a(fb_ctx* ctx, double* dp4a_per_s, double* ms) {
+    if (!ctx || !dp4a_per_s || !ms) return fail(ctx, FB_ERR_ARG, "NULL argument");
+    DeviceGuard dg(ctx->device);
+    int sms = 0;
+    FB_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int blocks = sms * 8, iters = 1 << 16;
+    Carver measure(nullptr);
+    measure.take<uint32_t>(blocks);
+    int rc = ensure_arena(ctx, measure.off);
+    if (rc) return rc;
+    cudaEvent_t a = nullptr, b = nullptr;
+    FB_CUDA(ctx, cudaEventCreate(&a));
+    FB_CUDA(ctx, cudaEventCreate(&b));
+    uint32_t* sink = reinterpret_cast<uint32_t*>(ctx->arena);
+    FB_CUDA(ctx, fb::launch_dp4a_probe(blocks, iters / 16, sink, nullptr));  // warm-up
+    FB_CUDA(ctx, cudaEventRecord(a, nullptr));
+    FB_CUDA(ctx, fb::launch_dp4a_probe(blocks, iters, sink, nullptr));
+    FB_CUDA(ctx, cudaEventRecord(b, nullptr));
+    FB_CUDA(ctx, cudaEventSynchronize(b));
+    float t = 0.f;
+    FB_CUDA(ctx, cudaEventElapsedTime(&t, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->launches += 2;
+    *ms = t;
+    *dp4a_per_s = static_cast<double>(blocks) * 256.0 * iters * fb::kDp4aProbeChains / (t * 1e-3);
+    return FB_OK;
+}
+
+uint32_t fb_pair_tag(int j, int i) {
+    return (static_cast<uint32_t>(j) << 16) | static_cast<uint32_t>(i & 0xFFFF);
+}
+
+int fb_nnf(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int H, int W,
+           const fb_params* p, const int32_t* init_nnf, int32_t* nnf_out, uint32_t* err_out,
+           void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->err.clear();
+    int rc = check_params(ctx, p, H, W);
+    if (rc) return rc;
+    if (!src_guide || !tgt_guide || !nnf_out)
+        return fail(ctx, FB_ERR_ARG, "src_guide, tgt_guide and nnf_out must be non-NULL");
+    if (init_nnf && p->levels != 1)
+        return fail(ctx, FB_ERR_ARG, "an initial NNF requires levels == 1");
+    DeviceGuard dg(ctx->device);
+    for (const void* q : {static_cast<const void*>(src_guide), static_cast<const void*>(tgt_guide),
+                          static_cast<const void*>(nnf_out), static_cast<const void*>(init_nnf),
+                          static_cast<const void*>(err_out)})
+        if (q && classify(ctx, q) != Mem::Device)
+            return fail(ctx, FB_ERR_ARG, "fb_nnf takes device pointers of the context's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Levels L = level_dims(H, W, p->levels);
+    const size_t npx0 = static_cast<size_t>(H) * W;
+
+    Buffers b;
+    Carver measure(nullptr);
+    carve(measure, b, L, p->patch, 2, 0, 1, 1, 0, false, 0, 0, 0);
+    rc = ensure_arena(ctx, measure.off);
+    if (rc) return rc;
+    Carver cv(ctx->arena);
+    carve(cv, b, L, p->patch, 2, 0, 1, 1, 0, false, 0, 0, 0);
+
+    std::vector<PairDesc> pairs(1);
+    pairs[0] = PairDesc{0, 1, p->pair_tag, 0, 1u, {0, 0, 0}};
+    rc = upload_tables(ctx, pairs, {}, b, st);
+    if (rc) return rc;
+    rc = prep_guides(ctx, b, L, p->patch, src_guide, 1, 0, st);
+    if (rc) return rc;
+    rc = prep_guides(ctx, b, L, p->patch, tgt_guide, 1, 1, st);
+    if (rc) return rc;
+    uint32_t *F = nullptr, *E = nullptr;
+    rc = run_nnf(ctx, b, L, p, 0, 1, init_nnf, st, &F, &E);
+    if (rc) return rc;
+    FB_LAUNCH(ctx, st, FB_K_UNPACK, fb::launch_nnf_unpack(F, E, npx0, nnf_out, err_out, st));
+    return FB_OK;
+}
+
+int fb_remap(fb_ctx* ctx, const uint8_t* src_style, const int32_t* nnf, int H, int W, int patch,
+             float* out, void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->err.clear();
+    if (patch < 3 || patch > 9 || (patch & 1) == 0)
+        return fail(ctx, FB_ERR_ARG, "patch must be odd in [3, 9], got %d", patch);
+    if (H < patch || W < patch || H > 32767 || W > 32767)
+        return fail(ctx, FB_ERR_ARG, "image %dx%d outside [patch, 32767]", H, W);
+    if (!src_style || !nnf || !out)
+        return fail(ctx, FB_ERR_ARG, "src_style, nnf and out must be non-NULL");
+    DeviceGuard dg(ctx->device);
+    for (const void* q : {static_cast<const void*>(src_style), static_cast<const void*>(nnf),
+                          static_cast<const void*>(out)})
+        if (classify(ctx, q) != Mem::Device)
+            return fail(ctx, FB_ERR_ARG, "fb_remap takes device pointers of the context's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Levels L = level_dims(H, W, 1);
+    const size_t npx = static_cast<size_t>(H) * W;
+
+    Buffers b;
+    Carver measure(nullptr);
+    carve(measure, b, L, patch, 0, 1, 1, 1, 1, false, 0, 0, 0);
+    int rc = ensure_arena(ctx, measure.off);
+    if (rc) return rc;
+    Carver cv(ctx->arena);
+    carve(cv, b, L, patch, 0, 1, 1, 1, 1, false, 0, 0, 0);
+
+    std::vector<PairDesc> pairs(1);
+    pairs[0] = PairDesc{0, 0, 0u, 0, 1u, {0, 0, 0}};
+    std::vector<JobDesc> jobs(1);
+    jobs[0] = JobDesc{0, -1, 0u, 0, 1, static_cast<uint32_t>(255 * patch * patch), {0, 0}};
+    rc = upload_tables(ctx, pairs, jobs, b, st);
+    if (rc) return rc;
+    FB_LAUNCH(ctx, st, FB_K_STYLE, fb::launch_style_rgbx(src_style, npx, b.styles, st));
+    FB_LAUNCH(ctx, st, FB_K_PACK, fb::launch_nnf_pack(nnf, H, W, b.FA, st));
+    FB_LAUNCH(ctx, st, FB_K_COMBINE, fb::launch_combine(patch, b.jobs, 0, 1, b.pairs, 0, b.FA, b.styles, H, W, out, st));
+    return FB_OK;
+}
+
+int fb_blend_window(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles, int N, int H, int W,
+                    int window, const fb_params* p, float* out, void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->err.clear();
+    int rc = check_params(ctx, p, H, W);
+    if (rc) return rc;
+    if (N < 1 || N > 65535) return fail(ctx, FB_ERR_ARG, "N must be in [1, 65535], got %d", N);
+    if (window < 1 || (window & 1) == 0)
+        return fail(ctx, FB_ERR_ARG, "window must be odd and >= 1, got %d", window);
+    if (!guides || !styles || !out)
+        return fail(ctx, FB_ERR_ARG, "guides, styles and out must be non-NULL");
+    const int k = p->patch, M = (window - 1) / 2;
+
+    // Eq. 2: one job per output frame; its pairs are (j -> i) for j in the truncated
+    // window, j != i, in increasing j.
+    std::vector<PairDesc> pairs;
+    std::vector<JobDesc> jobs(N);
+    for (int i = 0; i < N; ++i) {
+        const int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
+        jobs[i] = JobDesc{i, i, 1u, static_cast<int32_t>(pairs.size()), hi - lo,
+                          static_cast<uint32_t>(255 * k * k * (hi - lo + 1)), {0, 0}};
+        for (int j = lo; j <= hi; ++j)
+            if (j != i) pairs.push_back(PairDesc{j, i, fb_pair_tag(j, i), j, 1u, {0, 0, 0}});
+    }
+    DeviceGuard dg(ctx->device);
+    return run_pipeline(ctx, guides, N, H, W, styles, N, pairs, jobs, p, out,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int fb_interpolate(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const int32_t* key_idx,
+                   const uint8_t* key_styles, int n_keys, const fb_params* p, float* out,
+                   void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->err.clear();
+    int rc = check_params(ctx, p, H, W);
+    if (rc) return rc;
+    if (N < 1 || N > 65535) return fail(ctx, FB_ERR_ARG, "N must be in [1, 65535], got %d", N);
+    if (!guides || !key_idx || !key_styles || !out)
+        return fail(ctx, FB_ERR_ARG, "guides, key_idx, key_styles and out must be non-NULL");
+    if (n_keys < 1 || n_keys > N)
+        return fail(ctx, FB_ERR_ARG, "n_keys must be in [1, N], got %d", n_keys);
+    for (int m = 0; m < n_keys; ++m) {
+        if (key_idx[m] < 0 || key_idx[m] >= N)
+            return fail(ctx, FB_ERR_ARG, "key_idx[%d] = %d outside [0, %d)", m, key_idx[m], N);
+        if (m > 0 && key_idx[m] <= key_idx[m - 1])
+            return fail(ctx, FB_ERR_ARG, "key_idx must be strictly increasing");
+    }
+    const int k = p->patch;
+    const uint32_t kk255 = static_cast<uint32_t>(255 * k * k);
+
+    // Sec. 3.5.2: keys are copied; between keys l < i < r the weights are (r - i) for
+    // S_l and (i - l) for S_r over (r - l); outside the key range the nearest key alone.
+    std::vector<PairDesc> pairs;
+    std::vector<JobDesc> jobs(N);
+    int m_left = -1;  // last key index < i
+    int next = 0;     // first key with frame >= i
+    for (int i = 0; i < N; ++i) {
+        while (next < n_keys && key_idx[next] < i) m_left = next++;
+        const bool is_key = next < n_keys && key_idx[next] == i;
+        const int m_right = is_key ? (next + 1 < n_keys ? next + 1 : -1) : (next < n_keys ? next : -1);
+        JobDesc j{i, -1, 0u, static_cast<int32_t>(pairs.size()), 0, kk255, {0, 0}};
+        if (is_key) {
+            j.self_style = next;
+            j.self_w = 1u;
+        } else if (m_left >= 0 && m_right >= 0) {
+            const int l = key_idx[m_left], r = key_idx[m_right];
+            pairs.push_back(PairDesc{l, i, fb_pair_tag(l, i), m_left, static_cast<uint32_t>(r - i), {0, 0, 0}});
+            pairs.push_back(PairDesc{r, i, fb_pair_tag(r, i), m_right, static_cast<uint32_t>(i - l), {0, 0, 0}});
+            j.n_pairs = 2;
+            j.den = kk255 * static_cast<uint32_t>(r - l);
+        } else {
+            const int m = m_left >= 0 ? m_left : m_right;
+            const int l = key_idx[m];
+            pairs.push_back(PairDesc{l, i, fb_pair_tag(l, i), m, 1u, {0, 0, 0}});
+            j.n_pairs = 1;
+        }
+        jobs[i] = j;
+    }
+    DeviceGuard dg(ctx->device);
+    return run_pipeline(ctx, guides, N, H, W, key_styles, n_keys, pairs, jobs, p, out,
+                        static_cast<cudaStream_t>(stream));
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// fb_internal.h -- host-side declarations shared by the kernels and the C-ABI layer
+// of libfb.so.  Not part of the public interface (that is include/fb.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+namespace fb {
+
+// NNF entries on the device are packed (row << 16) | col; H, W <= 32767.
+// Guide frames are pre-laid out as "row patches": for pixel (r, c) the k
+// horizontally adjacent RGB pixels (r, clamp(c-p .. c+p)) as 3k bytes in
+// rowpatch_words(k) 32-bit words (zero padded), so one patch row of Eq. 1 is one
+// aligned 16- or 32-byte load.  energy(r, c) = sum of squares of the k x k x 3
+// clamped patch at (r, c); Eq. 1 is then energy_s(u) + energy_t(x) - 2 <s_u, t_x>.
+inline int rowpatch_used_words(int k) { return (3 * k + 3) / 4; }
+inline int rowpatch_words(int k) { return (rowpatch_used_words(k) + 3) / 4 * 4; }
+
+// One ordered pair (source guide frame -> target guide frame) and how its remap
+// enters the output.
+struct PairDesc {
+    int32_t src;       // guide slot of the source frame (G_j)
+    int32_t tgt;       // guide slot of the target frame (G_i)
+    uint32_t tag;      // Philox stream id of the pair
+    int32_t style;     // style slot remapped through this pair's NNF
+    uint32_t weight;   // integer weight of the remapped style in the output numerator
+    int32_t pad[3];
+};
+
+// One output frame: out = (self_w * S_self * k^2 / k^2 ... ) see combine kernel.
+struct JobDesc {
+    int32_t out_frame;   // index of the output frame
+    int32_t self_style;  // style slot added with weight self_w * k^2, or -1
+    uint32_t self_w;     // weight of the un-remapped self style (before the k^2 factor)
+    int32_t first_pair;  // first pair (global index) of this output frame
+    int32_t n_pairs;     // number of consecutive pairs
+    uint32_t den;        // integer denominator (255 k^2 * total weight)
+    int32_t pad[2];
+};
+
+struct LevelGeom {
+    int H, W;
+    const uint32_t* rp;      // [n_guides][H*W][RPW]
+    const uint32_t* energy;  // [n_guides][H*W]
+};
+
+// ---- launchers (fb_kernels.cu); each returns the cudaError_t of the launch ------
+cudaError_t launch_prep_guides(int k, const uint8_t* frames, int n_frames, int H, int W,
+                               uint32_t* rp, uint32_t* energy, cudaStream_t st);
+cudaError_t launch_downsample(const uint8_t* in, int n_frames, int H, int W, uint8_t* out,
+                              cudaStream_t st);
+cudaError_t launch_style_rgbx(const uint8_t* in, size_t n_px, uint32_t* out, cudaStream_t st);
+
+// mode 0: Philox random init; 1: upsample from the coarse field; 2: user int32 field.
+cudaError_t launch_nnf_init(int k, const PairDesc* pairs, int pair0, int n_pairs,
+                            const LevelGeom& g, int mode, const uint32_t* coarse_F, int Hc,
+                            int Wc, const int32_t* user_init, uint64_t seed, int level,
+                            uint32_t* F, uint32_t* E, cudaStream_t st);
+cudaError_t launch_nnf_iter(int k, const PairDesc* pairs, int pair0, int n_pairs,
+                            const LevelGeom& g, int r0, uint64_t seed, int level, int it,
+                            const uint32_t* Fp, const uint32_t* Ep, uint32_t* Fn, uint32_t* En,
+                            cudaStream_t st);
+cudaError_t launch_nnf_unpack(const uint32_t* F, const uint32_t* E, size_t npx, int32_t* nnf_out,
+                              uint32_t* err_out, cudaStream_t st);
+cudaError_t launch_nnf_pack(const int32_t* nnf, int H, int W, uint32_t* F, cudaStream_t st);
+cudaError_t launch_combine(int k, const JobDesc* jobs, int job0, int n_jobs,
+                           const PairDesc* pairs, int pair0, const uint32_t* F,
+                           const uint32_t* styles, int H, int W, float* out, cudaStream_t st);
+
+// dp4a throughput probe (fb_calib.cu): blocks x 256 threads x iters x 8 dp4a.
+cudaError_t launch_dp4a_probe(int blocks, int iters, uint32_t* sink, cudaStream_t st);
+constexpr int kDp4aProbeChains = 8;
+
+}  // namespace fb

@@ -1,0 +1,246 @@
+"""Parity of the CUDA path (through the C ABI) with the CPU oracle.
+
+NNFs and patch errors must be bit-exact; blended / interpolated pixels must agree to
+0.5/255 in float32 (the path is exact integer arithmetic plus one IEEE division per
+value, so in practice they agree bit for bit, which is also checked).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 0.5 / 255.0
+
+
+@pytest.fixture(scope="module")
+def fbp():
+    import paper_2311_09265_b300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def ctx(fbp):
+    import torch
+    assert torch.cuda.is_available(), "GPU tests need CUDA"
+    c = fbp.Context(0)
+    yield c
+    c.close()
+
+
+def cuda(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def host(t):
+    import torch
+    torch.cuda.synchronize()
+    return t.cpu().numpy()
+
+
+def gpu_nnf(fbp, ctx, s, t, patch, iters, levels=1, r0=0, seed=0, tag=0, init=None):
+    p = fbp.Params.make(patch, iters, levels, r0, seed, tag)
+    F, E = fbp.fb_nnf(ctx, cuda(s), cuda(t), p, init_nnf=None if init is None else cuda(init))
+    return host(F), host(E).view(np.uint32)
+
+
+# ----------------------------------------------------------------------------------
+# Alg. 1 NNF: bit-exact F and E
+# ----------------------------------------------------------------------------------
+NNF_CASES = [
+    # H, W, k, iters, levels, r0, motion
+    (37, 53, 5, 0, 1, 0, "shift"),
+    (37, 53, 5, 1, 1, 0, "shift"),
+    (96, 96, 5, 4, 1, 0, "shift"),
+    (64, 70, 3, 3, 1, 0, "affine"),
+    (41, 45, 7, 2, 1, 0, "affine"),
+    (30, 33, 9, 2, 1, 0, "affine"),
+    (61, 77, 5, 2, 2, 0, "shift"),
+    (50, 47, 5, 2, 3, 0, "affine"),
+    (40, 44, 5, 3, 1, 4, "affine"),
+    (9, 9, 9, 3, 1, 0, "affine"),     # smallest image for the largest patch
+    (5, 300, 5, 2, 1, 0, "affine"),   # one tile row, ragged width
+]
+
+
+@pytest.mark.parametrize("H,W,k,iters,levels,r0,motion", NNF_CASES)
+def test_nnf_bit_exact(fbp, ctx, H, W, k, iters, levels, r0, motion):
+    g, _ = synth.small_clip(3, H, W, seed=H * 1000 + W + k, motion=motion)
+    tag = oracle.pair_tag(2, 0)
+    Fg, Eg = gpu_nnf(fbp, ctx, g[2], g[0], k, iters, levels, r0, seed=1234, tag=tag)
+    Fo, Eo = oracle.nnf(g[2], g[0], k, iters, levels=levels, r0=r0, seed=1234, pair_tag=tag)
+    assert (Fg == Fo).all(), np.argwhere((Fg != Fo).any(-1))[:5]
+    assert (Eg == Eo).all()
+
+
+def test_nnf_bit_exact_with_user_init(fbp, ctx):
+    g, sh = synth.shift_clip(2, 48, 52, seed=5)
+    rng = np.random.default_rng(0)
+    init = np.stack([rng.integers(-5, 60, (48, 52)), rng.integers(-5, 60, (48, 52))], -1).astype(np.int32)
+    Fg, Eg = gpu_nnf(fbp, ctx, g[0], g[1], 5, 2, seed=9, tag=77, init=init)
+    Fo, Eo = oracle.nnf(g[0], g[1], 5, 2, seed=9, pair_tag=77, init=init)
+    assert (Fg == Fo).all() and (Eg == Eo).all()
+
+
+def test_nnf_seed_and_tag_change_the_stream(fbp, ctx):
+    g, _ = synth.small_clip(2, 32, 32, seed=3)
+    a = gpu_nnf(fbp, ctx, g[0], g[1], 5, 1, seed=1, tag=1)[0]
+    b = gpu_nnf(fbp, ctx, g[0], g[1], 5, 1, seed=1, tag=2)[0]
+    c = gpu_nnf(fbp, ctx, g[0], g[1], 5, 1, seed=1, tag=1)[0]
+    assert (a != b).any() and (a == c).all()
+
+
+# ----------------------------------------------------------------------------------
+# Alg. 2 remap
+# ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W,k", [(33, 47, 3), (64, 64, 5), (29, 71, 7), (18, 19, 9)])
+def test_remap_bit_exact(fbp, ctx, H, W, k):
+    rng = np.random.default_rng(H + W + k)
+    S = rng.integers(0, 256, (H, W, 3), dtype=np.uint8)
+    F = np.stack([rng.integers(-3, H + 3, (H, W)), rng.integers(-3, W + 3, (H, W))], -1).astype(np.int32)
+    out = host(fbp.fb_remap(ctx, cuda(S), cuda(F), k))
+    ref = oracle.remap(S, F, k)
+    assert np.abs(out - ref).max() <= TOL
+    assert (out == ref).all()
+
+
+# ----------------------------------------------------------------------------------
+# Eq. 2 window blend
+# ----------------------------------------------------------------------------------
+BLEND_CASES = [
+    # N, H, W, k, window, iters, levels, motion
+    (8, 96, 96, 5, 3, 4, 1, "shift"),      # the 8-frame 96x96 workload
+    (7, 45, 61, 3, 5, 2, 1, "affine"),
+    (5, 40, 36, 7, 3, 2, 1, "affine"),
+    (6, 50, 42, 5, 7, 2, 2, "shift"),      # window larger than the clip, 2 levels
+    (4, 33, 35, 9, 3, 1, 1, "affine"),
+    (1, 20, 20, 5, 3, 2, 1, "shift"),      # single frame: no pairs
+    (5, 20, 24, 5, 1, 2, 1, "shift"),      # window 1: output = style
+]
+
+
+@pytest.mark.parametrize("N,H,W,k,window,iters,levels,motion", BLEND_CASES)
+def test_blend_window_matches_oracle(fbp, ctx, N, H, W, k, window, iters, levels, motion):
+    g, s = synth.small_clip(N, H, W, seed=N * 100 + H + W, motion=motion)
+    p = fbp.Params.make(k, iters, levels, 0, 4242)
+    out = host(fbp.fb_blend_window(ctx, cuda(g), cuda(s), window, p))
+    ref = oracle.blend_window(g, s, window, k, iters, levels=levels, seed=4242)
+    assert np.abs(out - ref).max() <= TOL
+    assert (out == ref).all()
+
+
+def test_blend_window_host_buffers_equal_device_buffers(fbp, ctx):
+    import torch
+    g, s = synth.small_clip(6, 40, 52, seed=8)
+    p = fbp.Params.make(5, 2, 1, 0, 11)
+    dev = host(fbp.fb_blend_window(ctx, cuda(g), cuda(s), 3, p))
+    gh = torch.from_numpy(g).pin_memory()
+    sh = torch.from_numpy(s).pin_memory()
+    hst = fbp.fb_blend_window(ctx, gh, sh, 3, p).numpy()
+    assert (dev == hst).all()
+    # pageable host memory works too
+    assert (fbp.fb_blend_window(ctx, torch.from_numpy(g.copy()), torch.from_numpy(s.copy()), 3,
+                                p).numpy() == dev).all()
+
+
+def test_blend_window_is_deterministic_and_counts_launches(fbp, ctx):
+    g, s = synth.small_clip(5, 32, 32, seed=2)
+    p = fbp.Params.make(5, 3, 1, 0, 3)
+    n0 = ctx.launches
+    a = host(fbp.fb_blend_window(ctx, cuda(g), cuda(s), 3, p))
+    n1 = ctx.launches
+    b = host(fbp.fb_blend_window(ctx, cuda(g), cuda(s), 3, p))
+    assert (a == b).all()
+    # prep + style + init + 3 iterations + combine
+    assert n1 - n0 == 1 + 1 + 1 + 3 + 1
+
+
+# ----------------------------------------------------------------------------------
+# Sec. 3.5.2 interpolation
+# ----------------------------------------------------------------------------------
+INTERP_CASES = [
+    # N, H, W, k, keys, iters
+    (9, 50, 40, 5, (0, 8), 3),
+    (10, 36, 44, 7, (2, 5, 7), 2),
+    (6, 30, 30, 5, (3,), 2),
+    (5, 28, 31, 3, (0, 1, 2, 3, 4), 1),     # every frame a key
+    (7, 33, 29, 9, (6,), 1),                # before the only key
+]
+
+
+@pytest.mark.parametrize("N,H,W,k,keys,iters", INTERP_CASES)
+def test_interpolate_matches_oracle(fbp, ctx, N, H, W, k, keys, iters):
+    g, s = synth.small_clip(N, H, W, seed=N + H * W, motion="affine")
+    ks = np.ascontiguousarray(s[list(keys)])
+    p = fbp.Params.make(k, iters, 1, 0, 99)
+    out = host(fbp.fb_interpolate(ctx, cuda(g), list(keys), cuda(ks), p))
+    ref = oracle.interpolate(g, list(keys), ks, k, iters, seed=99)
+    assert np.abs(out - ref).max() <= TOL
+    assert (out == ref).all()
+
+
+# ----------------------------------------------------------------------------------
+# Argument errors: FB_ERR_ARG before any launch
+# ----------------------------------------------------------------------------------
+def test_argument_errors(fbp, ctx):
+    import torch
+    g = torch.zeros((4, 16, 16, 3), dtype=torch.uint8, device="cuda")
+    n0 = ctx.launches
+    bad = [
+        lambda: fbp.fb_blend_window(ctx, g, g, 3, fbp.Params.make(4, 2)),     # even patch
+        lambda: fbp.fb_blend_window(ctx, g, g, 3, fbp.Params.make(11, 2)),    # patch > 9
+        lambda: fbp.fb_blend_window(ctx, g, g, 2, fbp.Params.make(5, 2)),     # even window
+        lambda: fbp.fb_blend_window(ctx, g, g, 3, fbp.Params.make(5, -1)),    # iters < 0
+        lambda: fbp.fb_blend_window(ctx, g, g, 3, fbp.Params.make(5, 2, 0)),  # levels 0
+        lambda: fbp.fb_interpolate(ctx, g, [2, 1], g[:2], fbp.Params.make(5, 2)),  # unsorted
+        lambda: fbp.fb_interpolate(ctx, g, [0, 4], g[:2], fbp.Params.make(5, 2)),  # out of range
+        lambda: fbp.fb_nnf(ctx, g[0], g[1], fbp.Params.make(5, 2, 2),
+                           init_nnf=torch.zeros((16, 16, 2), dtype=torch.int32, device="cuda")),
+        lambda: fbp.fb_nnf(ctx, g[0].cpu(), g[1], fbp.Params.make(5, 2)),       # host pointer
+        lambda: fbp.fb_blend_window(ctx, g, g.cpu(), 3, fbp.Params.make(5, 2)),  # mixed memory
+        lambda: fbp.fb_nnf(ctx, g[0, :3, :3].contiguous(), g[1, :3, :3].contiguous(),
+                           fbp.Params.make(5, 2)),                               # H < patch
+    ]
+    for f in bad:
+        with pytest.raises(fbp.FastBlendError) as ei:
+            f()
+        assert ei.value.status == fbp.FB_ERR_ARG
+    assert ctx.launches == n0
+
+
+# ----------------------------------------------------------------------------------
+# Full-size workloads in the launch configuration bench.py times, checked on samples
+# the oracle can compute one by one.
+# ----------------------------------------------------------------------------------
+@pytest.mark.slow
+def test_blend_512_full_size_sampled_frames(fbp, ctx):
+    w = synth.WORKLOADS["blend_512"]
+    g, s = synth.make_clip("blend_512")
+    seed = w.seed
+    p = fbp.Params.make(w.patch, w.iters, 1, 0, seed)
+    out = host(fbp.fb_blend_window(ctx, cuda(g), cuda(s), w.window, p))
+    for i in (0, 31):
+        ref = oracle.blend_frame(g, s, w.window, i, w.patch, w.iters, seed=seed)
+        assert np.abs(out[i] - ref).max() <= TOL
+        assert (out[i] == ref).all()
+    # one pair's NNF, bit-exact, through fb_nnf with that pair's tag
+    tag = oracle.pair_tag(33, 31)
+    Fg, Eg = gpu_nnf(fbp, ctx, g[33], g[31], w.patch, w.iters, seed=seed, tag=tag)
+    Fo, Eo = oracle.nnf(g[33], g[31], w.patch, w.iters, seed=seed, pair_tag=tag)
+    assert (Fg == Fo).all() and (Eg == Eo).all()
+
+
+@pytest.mark.slow
+def test_interp_1024x576_full_size_sampled_frame(fbp, ctx):
+    w = synth.WORKLOADS["interp_1024x576"]
+    g, ks = synth.make_clip("interp_1024x576")
+    p = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed)
+    out = host(fbp.fb_interpolate(ctx, cuda(g), list(w.keys), cuda(ks), p))
+    for i in (0, 23):
+        ref = oracle.interpolate_frame(g, list(w.keys), ks, i, w.patch, w.iters, seed=w.seed)
+        assert np.abs(out[i] - ref).max() <= TOL
+        assert (out[i] == ref).all()
