@@ -174,6 +174,35 @@ int fb_interpolate(fb_ctx *ctx, const uint8_t *guides, int N, int H, int W,
                    const int32_t *key_idx, const uint8_t *key_styles, int n_keys,
                    const fb_params *p, float *out, void *stream);
 
+/* Bytes of the fixed device scratch array used by fb_blend_window_noalloc. */
+#define FB_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
+
+/* fb_blend_window for callers that cannot allocate device memory.  The paper has no
+ * counterpart to this entry point: it is a deployment variant of the Eq. 2 blend
+ * above.  Some callers are not allowed to call cudaMalloc or any allocator where they
+ * blend (a host callback or stream-ordered pipeline that must not synchronise the
+ * device, a plug-in whose host application owns all device memory, a process held to
+ * a device-memory budget fixed at start-up), and every other entry point here needs a
+ * context that allocates.  This one takes no context and allocates nothing: all its
+ * scratch lives in one file-scope device array of FB_NOALLOC_SCRATCH_BYTES (64 MiB),
+ * which every GPU that loads libfb.so holds until the process exits.
+ *   Arguments and result are those of fb_blend_window, on the CURRENT device; guides,
+ *   styles and out must be device memory of that device (host pointers -> FB_ERR_ARG).
+ *   A blend whose scratch (row patches, energies and styles of N frames at every
+ *   pyramid level, four H x W words per NNF, the pair tables) exceeds the array is
+ *   rejected with FB_ERR_ARG and a message giving both sizes; so is one with more than
+ *   65535 NNFs.  Errors are reported through fb_last_error(NULL).
+ *   Set-up: the first call on each device looks up the array's device address
+ *   (cudaGetSymbolAddress) with that device current; make that first call before any
+ *   stream capture.
+ *   Sharing: every call on a device uses the same array and leaves its contents
+ *   behind; nothing in it needs to start at zero (every word is written before it is
+ *   read).  Calls whose work overlaps on the GPU (different streams, or host threads
+ *   without ordering) race on the array and corrupt each other's results: order them.
+ *   Results are bit-identical to fb_blend_window.  Async on `stream`. */
+int fb_blend_window_noalloc(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                            int window, const fb_params *p, float *out, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -23,7 +23,8 @@ FB_OK, FB_ERR_ARG, FB_ERR_CUDA, FB_ERR_OOM, FB_ERR_TIMEOUT, FB_ERR_UNSUPPORTED =
 HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_error",
                     "fb_status_string", "fb_ctx_launches", "fb_ctx_scratch_bytes",
                     "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a", "fb_pair_tag",
-                    "fb_nnf", "fb_remap", "fb_blend_window", "fb_interpolate")
+                    "fb_nnf", "fb_remap", "fb_blend_window", "fb_interpolate",
+                    "fb_blend_window_noalloc")
 
 # fb_kernel_kind, in header order.
 KERNEL_KINDS = ("prep", "downsample", "style", "init", "iter", "unpack", "pack", "combine")
@@ -89,6 +90,9 @@ def lib() -> ctypes.CDLL:
                                       ctypes.c_int, P, _vp, _vp]
         L.fb_interpolate.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp,
                                      _vp, ctypes.c_int, P, _vp, _vp]
+        L.fb_blend_window_noalloc.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, P, _vp, _vp]
+        L.fb_blend_window_noalloc.restype = ctypes.c_int
         for f in ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_ctx_profile",
                   "fb_ctx_profile_read", "fb_nnf", "fb_remap",
                   "fb_blend_window", "fb_interpolate"):

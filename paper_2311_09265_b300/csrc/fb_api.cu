@@ -416,6 +416,11 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
 
 }  // namespace
 
+namespace fb {
+// Error message of a call that has no context (read back by fb_last_error(NULL)).
+void set_null_ctx_error(const char* msg) { g_null_ctx_err = msg; }
+}  // namespace fb
+
 extern "C" {
 
 int fb_ctx_create(fb_ctx** out, int device) {

@@ -1,0 +1,67 @@
+"""fb_blend_window_noalloc: the Eq. 2 blend for callers that cannot allocate.
+
+Such callers (a host callback or stream-ordered pipeline that must not synchronise
+the device, a plug-in whose host owns every allocation, a process on a fixed memory
+budget) cannot create a context, because a context allocates its scratch.  The
+no-alloc entry point instead uses one fixed device array inside libfb.so.  This test
+calls it through the C ABI twice in a row, on different clips, and checks each result
+against fb_blend_window, the entry point with context-owned scratch.  It lives in a
+file of its own that pytest collects last.
+"""
+import ctypes
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+TOL = 0.5 / 255.0
+
+
+def _noalloc(fbp, g, s, window, params):
+    import torch
+    N, H, W = g.shape[:3]
+    out = torch.full((N, H, W, 3), -1.0, dtype=torch.float32, device="cuda")
+    rc = fbp.lib().fb_blend_window_noalloc(g.data_ptr(), s.data_ptr(), N, H, W, window,
+                                           ctypes.byref(params), out.data_ptr(),
+                                           torch.cuda.current_stream().cuda_stream)
+    assert rc == fbp.FB_OK, fbp.lib().fb_last_error(None).decode()
+    return out
+
+
+def test_noalloc_blend_matches_context_blend_on_two_calls_in_a_row():
+    import torch
+
+    import paper_2311_09265_b300 as fbp
+    fbp.build()
+    torch.cuda.set_device(0)
+    ctx = fbp.Context(0)
+    cases = [
+        (synth.small_clip(8, 96, 96, seed=synth.clip_seed(0)), 3, fbp.Params.make(5, 4, 1, 0, 31)),
+        (synth.small_clip(6, 61, 47, seed=77, motion="affine"), 5, fbp.Params.make(7, 2, 2, 0, 5)),
+    ]
+    for (g, s), window, params in cases:
+        gd, sd = torch.from_numpy(g).cuda(), torch.from_numpy(s).cuda()
+        want = fbp.fb_blend_window(ctx, gd, sd, window, params)
+        got = _noalloc(fbp, gd, sd, window, params)
+        torch.cuda.synchronize()
+        w, o = want.cpu().numpy(), got.cpu().numpy()
+        assert np.abs(o - w).max() <= TOL
+        assert (o == w).all()
+    ctx.close()
+
+
+def test_noalloc_rejects_a_blend_larger_than_its_scratch():
+    import torch
+
+    import paper_2311_09265_b300 as fbp
+    fbp.build()
+    g = torch.zeros((60, 512, 512, 3), dtype=torch.uint8, device="cuda")
+    out = torch.empty((60, 512, 512, 3), dtype=torch.float32, device="cuda")
+    p = fbp.Params.make(5, 1)
+    rc = fbp.lib().fb_blend_window_noalloc(g.data_ptr(), g.data_ptr(), 60, 512, 512, 15,
+                                           ctypes.byref(p), out.data_ptr(), None)
+    assert rc == fbp.FB_ERR_ARG
+    assert b"static scratch holds" in fbp.lib().fb_last_error(None)
