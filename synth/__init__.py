@@ -237,6 +237,8 @@ WORKLOADS = {
                            patch=5, iters=4, window=3, seed=clip_seed(0), motion="shift"),
     "blend_512": Workload("plain blend all-pairs 60x512x512 k5 w15 n6 (affine motion)", "blend",
                           60, 512, 512, patch=5, iters=6, window=15, seed=clip_seed(1)),
+    "blend_512_16f": Workload("plain blend all-pairs 16x512x512 k5 w15 n6 (affine motion)", "blend",
+                              16, 512, 512, patch=5, iters=6, window=15, seed=clip_seed(1, 16)),
     "interp_1024x576": Workload("plain interpolation 48x576x1024 k7 n8 keys 0,47 (affine motion)",
                                 "interpolate", 48, 576, 1024, patch=7, iters=8, keys=(0, 47),
                                 seed=clip_seed(2)),
