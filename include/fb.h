@@ -96,7 +96,7 @@ size_t fb_ctx_scratch_bytes(const fb_ctx *ctx);
 
 /* Kernel families, for fb_ctx_profile_read. */
 typedef enum fb_kernel_kind {
-    FB_K_PREP = 0,      /* guide frame -> row patches + patch energies           */
+    FB_K_PREP = 0,      /* guide frame -> row patches                            */
     FB_K_DOWNSAMPLE,    /* pyramid step                                          */
     FB_K_STYLE,         /* style frame -> 4-byte pixels                          */
     FB_K_INIT,          /* initial NNF and its Eq. 1 errors                      */
@@ -188,7 +188,7 @@ int fb_interpolate(fb_ctx *ctx, const uint8_t *guides, int N, int H, int W,
  * which every GPU that loads libfb.so holds until the process exits.
  *   Arguments and result are those of fb_blend_window, on the CURRENT device; guides,
  *   styles and out must be device memory of that device (host pointers -> FB_ERR_ARG).
- *   A blend whose scratch (row patches, energies and styles of N frames at every
+ *   A blend whose scratch (row patches and styles of N frames at every
  *   pyramid level, four H x W words per NNF, the pair tables) exceeds the array is
  *   rejected with FB_ERR_ARG and a message giving both sizes; so is one with more than
  *   65535 NNFs.  Errors are reported through fb_last_error(NULL).

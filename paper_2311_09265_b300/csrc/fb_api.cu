@@ -211,8 +211,7 @@ Levels level_dims(int H, int W, int levels) {
 // Device buffers of one call.
 struct Buffers {
     uint8_t* raw[16] = {};       // downsampled guides, levels >= 1
-    uint32_t* rp[16] = {};
-    uint32_t* en[16] = {};
+    uint32_t* rec[16] = {};   // patch records per level
     uint32_t* styles = nullptr;
     uint32_t *FA = nullptr, *FB = nullptr, *EA = nullptr, *EB = nullptr;
     PairDesc* pairs = nullptr;
@@ -225,12 +224,11 @@ struct Buffers {
 void carve(Carver& cv, Buffers& b, const Levels& L, int k, int n_guides, int n_styles,
            size_t chunk_pairs, size_t n_pairs, size_t n_jobs, bool staging, size_t guide_bytes,
            size_t style_bytes, size_t out_floats) {
-    const int rpw = fb::rowpatch_words(k);
+    const int recw = fb::patch_record_words(k);
     for (int l = 0; l < L.n; ++l) {
         const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];
         if (l > 0) b.raw[l] = cv.take<uint8_t>(static_cast<size_t>(n_guides) * npx * 3);
-        b.rp[l] = cv.take<uint32_t>(static_cast<size_t>(n_guides) * npx * rpw);
-        b.en[l] = cv.take<uint32_t>(static_cast<size_t>(n_guides) * npx);
+        b.rec[l] = cv.take<uint32_t>(static_cast<size_t>(n_guides) * npx * recw);
     }
     const size_t npx0 = static_cast<size_t>(L.h[0]) * L.w[0];
     b.styles = cv.take<uint32_t>(static_cast<size_t>(n_styles) * npx0);
@@ -264,11 +262,11 @@ int upload_tables(fb_ctx* ctx, const std::vector<PairDesc>& pairs, const std::ve
     return FB_OK;
 }
 
-// Guide frames (n of them, contiguous at `frames`) -> row patches + energies at every
+// Guide frames (n of them, contiguous at `frames`) -> row patches at every
 // pyramid level, into guide slots [slot0, slot0 + n).
 int prep_guides(fb_ctx* ctx, const Buffers& b, const Levels& L, int k, const uint8_t* frames,
                 int n, int slot0, cudaStream_t st) {
-    const int rpw = fb::rowpatch_words(k);
+    const int recw = fb::patch_record_words(k);
     const uint8_t* cur = frames;
     for (int l = 0; l < L.n; ++l) {
         const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];
@@ -278,8 +276,7 @@ int prep_guides(fb_ctx* ctx, const Buffers& b, const Levels& L, int k, const uin
             cur = dst;
         }
         FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(k, cur, n, L.h[l], L.w[l],
-                                              b.rp[l] + static_cast<size_t>(slot0) * npx * rpw,
-                                              b.en[l] + static_cast<size_t>(slot0) * npx, st));
+                                              b.rec[l] + static_cast<size_t>(slot0) * npx * recw, st));
     }
     return FB_OK;
 }
@@ -291,7 +288,7 @@ int run_nnf(fb_ctx* ctx, const Buffers& b, const Levels& L, const fb_params* p, 
     const int k = p->patch;
     uint32_t *Fc = b.FA, *Ec = b.EA, *Fo = b.FB, *Eo = b.EB;
     for (int l = L.n - 1; l >= 0; --l) {
-        LevelGeom g{L.h[l], L.w[l], b.rp[l], b.en[l]};
+        LevelGeom g{L.h[l], L.w[l], b.rec[l]};
         if (l == L.n - 1) {
             FB_LAUNCH(ctx, st, FB_K_INIT, fb::launch_nnf_init(k, b.pairs, pair0, n, g, user_init ? 2 : 0, nullptr,
                                                0, 0, user_init, p->seed, l, Fc, Ec, st));
@@ -532,7 +529,7 @@ int fb_probe_dp4a(fb_ctx* ctx, double* dp4a_per_s, double* ms) {
     DeviceGuard dg(ctx->device);
     int sms = 0;
     FB_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
-    const int blocks = sms * 8, iters = 1 << 16;
+    const int blocks = sms * 8, iters = 1 << 14;
     Carver measure(nullptr);
     measure.take<uint32_t>(blocks);
     int rc = ensure_arena(ctx, measure.off);

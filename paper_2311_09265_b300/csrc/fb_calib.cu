@@ -6,7 +6,7 @@
 namespace fb {
 namespace {
 
-constexpr int kChains = 8;  // independent accumulators per thread (hides latency)
+constexpr int kChains = kDp4aProbeChains;  // independent accumulators per thread
 
 __global__ void __launch_bounds__(256) dp4a_probe_kernel(uint32_t seed, int iters,
                                                          uint32_t* __restrict__ sink) {

@@ -10,13 +10,10 @@
 namespace fb {
 
 // NNF entries on the device are packed (row << 16) | col; H, W <= 32767.
-// Guide frames are pre-laid out as "row patches": for pixel (r, c) the k
-// horizontally adjacent RGB pixels (r, clamp(c-p .. c+p)) as 3k bytes in
-// rowpatch_words(k) 32-bit words (zero padded), so one patch row of Eq. 1 is one
-// aligned 16- or 32-byte load.  energy(r, c) = sum of squares of the k x k x 3
-// clamped patch at (r, c); Eq. 1 is then energy_s(u) + energy_t(x) - 2 <s_u, t_x>.
-inline int rowpatch_used_words(int k) { return (3 * k + 3) / 4; }
-inline int rowpatch_words(int k) { return (rowpatch_used_words(k) + 3) / 4 * 4; }
+// Guide frames are pre-laid out as one "patch record" per pixel: the three channel
+// sums of its clamped k x k patch (two words), then the patch's 3k^2 bytes, padded to
+// whole 32-byte sectors (patch_record_words(k) 32-bit words).
+inline int patch_record_words(int k) { return (2 + (3 * k * k + 3) / 4 + 7) / 8 * 8; }
 
 // One ordered pair (source guide frame -> target guide frame) and how its remap
 // enters the output.
@@ -42,13 +39,12 @@ struct JobDesc {
 
 struct LevelGeom {
     int H, W;
-    const uint32_t* rp;      // [n_guides][H*W][RPW]
-    const uint32_t* energy;  // [n_guides][H*W]
+    const uint32_t* rec;     // [n_guides][H*W][patch_record_words(k)]
 };
 
 // ---- launchers (fb_kernels.cu); each returns the cudaError_t of the launch ------
 cudaError_t launch_prep_guides(int k, const uint8_t* frames, int n_frames, int H, int W,
-                               uint32_t* rp, uint32_t* energy, cudaStream_t st);
+                               uint32_t* rec, cudaStream_t st);
 cudaError_t launch_downsample(const uint8_t* in, int n_frames, int H, int W, uint8_t* out,
                               cudaStream_t st);
 cudaError_t launch_style_rgbx(const uint8_t* in, size_t n_px, uint32_t* out, cudaStream_t st);
@@ -69,8 +65,8 @@ cudaError_t launch_combine(int k, const JobDesc* jobs, int job0, int n_jobs,
                            const PairDesc* pairs, int pair0, const uint32_t* F,
                            const uint32_t* styles, int H, int W, float* out, cudaStream_t st);
 
-// dp4a throughput probe (fb_calib.cu): blocks x 256 threads x iters x 8 dp4a.
+// dp4a throughput probe (fb_calib.cu): blocks x 256 threads x iters x chains dp4a.
+constexpr int kDp4aProbeChains = 32;
 cudaError_t launch_dp4a_probe(int blocks, int iters, uint32_t* sink, cudaStream_t st);
-constexpr int kDp4aProbeChains = 8;
 
 }  // namespace fb

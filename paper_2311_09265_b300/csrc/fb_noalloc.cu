@@ -135,7 +135,7 @@ extern "C" int fb_blend_window_noalloc(const uint8_t* guides, const uint8_t* sty
     if (!on_device(guides, device) || !on_device(styles, device) || !on_device(out, device))
         return report(FB_ERR_ARG, "guides, styles and out must be device memory of the current device");
 
-    const int k = p->patch, M = (window - 1) / 2, rpw = fb::rowpatch_words(k);
+    const int k = p->patch, M = (window - 1) / 2, recw = fb::patch_record_words(k);
     int hs[16], ws[16];
     hs[0] = H;
     ws[0] = W;
@@ -149,12 +149,11 @@ extern "C" int fb_blend_window_noalloc(const uint8_t* guides, const uint8_t* sty
     const size_t npx0 = static_cast<size_t>(H) * W;
 
     // Layout of the static scratch (256-byte aligned pieces).
-    size_t off = 0, o_raw[16] = {}, o_rp[16], o_en[16];
+    size_t off = 0, o_raw[16] = {}, o_rec[16];
     for (int l = 0; l < p->levels; ++l) {
         const size_t npx = static_cast<size_t>(hs[l]) * ws[l];
         if (l > 0) { o_raw[l] = off; off = align256(off + static_cast<size_t>(N) * npx * 3); }
-        o_rp[l] = off; off = align256(off + static_cast<size_t>(N) * npx * rpw * 4);
-        o_en[l] = off; off = align256(off + static_cast<size_t>(N) * npx * 4);
+        o_rec[l] = off; off = align256(off + static_cast<size_t>(N) * npx * recw * 4);
     }
     const size_t o_sty = off; off = align256(off + static_cast<size_t>(N) * npx0 * 4);
     size_t o_fe[4];
@@ -189,7 +188,7 @@ extern "C" int fb_blend_window_noalloc(const uint8_t* guides, const uint8_t* sty
             NA_CHECK(fb::launch_downsample(cur, N, hs[l - 1], ws[l - 1], dst, st));
             cur = dst;
         }
-        NA_CHECK(fb::launch_prep_guides(k, cur, N, hs[l], ws[l], u32(o_rp[l]), u32(o_en[l]), st));
+        NA_CHECK(fb::launch_prep_guides(k, cur, N, hs[l], ws[l], u32(o_rec[l]), st));
     }
     NA_CHECK(fb::launch_style_rgbx(styles, static_cast<size_t>(N) * npx0, u32(o_sty), st));
 
@@ -198,7 +197,7 @@ extern "C" int fb_blend_window_noalloc(const uint8_t* guides, const uint8_t* sty
         const int np = static_cast<int>(n_pairs);
         uint32_t *Fc = u32(o_fe[0]), *Ec = u32(o_fe[1]), *Fo = u32(o_fe[2]), *Eo = u32(o_fe[3]);
         for (int l = p->levels - 1; l >= 0; --l) {
-            LevelGeom g{hs[l], ws[l], u32(o_rp[l]), u32(o_en[l])};
+            LevelGeom g{hs[l], ws[l], u32(o_rec[l])};
             if (l == p->levels - 1) {
                 NA_CHECK(fb::launch_nnf_init(k, pairs, 0, np, g, 0, nullptr, 0, 0, nullptr, p->seed, l,
                                              Fc, Ec, st));
