@@ -211,7 +211,7 @@ Levels level_dims(int H, int W, int levels) {
 // Device buffers of one call.
 struct Buffers {
     uint8_t* raw[16] = {};       // downsampled guides, levels >= 1
-    uint32_t* rec[16] = {};   // patch records per level
+    uint32_t* rec[16] = {};   // row patches per level
     uint32_t* styles = nullptr;
     uint32_t *FA = nullptr, *FB = nullptr, *EA = nullptr, *EB = nullptr;
     PairDesc* pairs = nullptr;
@@ -224,7 +224,7 @@ struct Buffers {
 void carve(Carver& cv, Buffers& b, const Levels& L, int k, int n_guides, int n_styles,
            size_t chunk_pairs, size_t n_pairs, size_t n_jobs, bool staging, size_t guide_bytes,
            size_t style_bytes, size_t out_floats) {
-    const int recw = fb::patch_record_words(k);
+    const int recw = fb::rowpatch_words(k);
     for (int l = 0; l < L.n; ++l) {
         const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];
         if (l > 0) b.raw[l] = cv.take<uint8_t>(static_cast<size_t>(n_guides) * npx * 3);
@@ -266,7 +266,7 @@ int upload_tables(fb_ctx* ctx, const std::vector<PairDesc>& pairs, const std::ve
 // pyramid level, into guide slots [slot0, slot0 + n).
 int prep_guides(fb_ctx* ctx, const Buffers& b, const Levels& L, int k, const uint8_t* frames,
                 int n, int slot0, cudaStream_t st) {
-    const int recw = fb::patch_record_words(k);
+    const int recw = fb::rowpatch_words(k);
     const uint8_t* cur = frames;
     for (int l = 0; l < L.n; ++l) {
         const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];

@@ -10,10 +10,10 @@
 namespace fb {
 
 // NNF entries on the device are packed (row << 16) | col; H, W <= 32767.
-// Guide frames are pre-laid out as one "patch record" per pixel: the three channel
-// sums of its clamped k x k patch (two words), then the patch's 3k^2 bytes, padded to
-// whole 32-byte sectors (patch_record_words(k) 32-bit words).
-inline int patch_record_words(int k) { return (2 + (3 * k * k + 3) / 4 + 7) / 8 * 8; }
+// Guide frames are pre-laid out as "row patches": slot (r, c) holds the k pixels
+// (r, clamp(c-p .. c+p)) as 3k bytes in rowpatch_words(k) 32-bit words (zero padded),
+// so one patch row of Eq. 1 is one aligned 16- or 32-byte load.
+inline int rowpatch_words(int k) { return ((3 * k + 3) / 4 + 3) / 4 * 4; }
 
 // One ordered pair (source guide frame -> target guide frame) and how its remap
 // enters the output.
@@ -39,12 +39,12 @@ struct JobDesc {
 
 struct LevelGeom {
     int H, W;
-    const uint32_t* rec;     // [n_guides][H*W][patch_record_words(k)]
+    const uint32_t* rp;      // [n_guides][H*W][rowpatch_words(k)]
 };
 
 // ---- launchers (fb_kernels.cu); each returns the cudaError_t of the launch ------
 cudaError_t launch_prep_guides(int k, const uint8_t* frames, int n_frames, int H, int W,
-                               uint32_t* rec, cudaStream_t st);
+                               uint32_t* rp, cudaStream_t st);
 cudaError_t launch_downsample(const uint8_t* in, int n_frames, int H, int W, uint8_t* out,
                               cudaStream_t st);
 cudaError_t launch_style_rgbx(const uint8_t* in, size_t n_px, uint32_t* out, cudaStream_t st);

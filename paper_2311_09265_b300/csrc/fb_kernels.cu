@@ -1,6 +1,6 @@
 // fb_kernels.cu -- sm_103a kernels of the FastBlend hot path (arXiv 2311.09265).
 //
-//   prep_guides   guide frame -> one patch record per pixel (Eq. 1 operands)
+//   prep_guides   guide frame -> row-patch layout (Eq. 1 operands)
 //   downsample    one pyramid step (Alg. 1, "resize images")
 //   style_rgbx    style frame -> 4-byte pixels for single-load gathers
 //   nnf_init      random / upsampled / user initial field and its Eq. 1 error
@@ -9,17 +9,17 @@
 //                 Eq. 2 window sum (or the Sec. 3.5.2 keyframe weights) and the
 //                 final division
 //
-// Everything on the NNF path is integer: Eq. 1 is evaluated one 32-byte sector of the
-// candidate's patch record at a time as |s|^2 + |t|^2 - 2 <s, t> with dp4a, which is
-// exactly the clamp-to-edge sum of squared byte differences; a candidate stops loading
-// once an exact lower bound or its running sum reaches the incumbent's error.
+// Everything on the NNF path is integer: Eq. 1 is evaluated one patch row at a time as
+// |s|^2 + |t|^2 - 2 <s, t> with dp4a, which is exactly the clamp-to-edge sum of squared
+// byte differences; a candidate stops loading rows once its running sum reaches the
+// incumbent's error.
 #include "fb_internal.h"
 
 namespace fb {
 namespace {
 
 #ifndef FB_ITER_MIN_BLOCKS
-#define FB_ITER_MIN_BLOCKS 5  // resident 256-thread blocks per SM the iteration kernel is built for
+#define FB_ITER_MIN_BLOCKS 5  // resident 256-thread blocks per SM the k=5 iteration kernel is built for
 #endif
 #ifndef FB_TILE_H
 #define FB_TILE_H 8
@@ -53,68 +53,45 @@ __device__ __forceinline__ uint4 philox4x32_10(uint4 v, uint32_t k0, uint32_t k1
     return v;
 }
 
-// Patch record of a guide pixel u (the acceleration structure of the NNF search):
-//   word 0      sum of channel 0 | sum of channel 1 << 16 over the clamped k x k patch
-//   word 1      sum of channel 2
-//   words 2..   the 3k^2 bytes of the clamped patch, row-major, RGB, zero padded
-// padded to whole 32-byte sectors, so that one 256-bit load fetches one sector.
 template <int K>
-struct Rec {
+struct Geo {
     static constexpr int P = K / 2;
-    static constexpr int PATCH_BYTES = 3 * K * K;
-    static constexpr int PATCH_WORDS = (PATCH_BYTES + 3) / 4;
-    static constexpr int HEAD = 2;
-    static constexpr int WORDS = (HEAD + PATCH_WORDS + 7) / 8 * 8;
-    static constexpr int SECTORS = WORDS / 8;
+    static constexpr int NW = (3 * K + 3) / 4;    // 32-bit words holding one 3K-byte patch row
+    static constexpr int RPW = (NW + 3) / 4 * 4;  // row-patch slot stride: 16-byte aligned
 };
 
-__device__ __forceinline__ void ld256_nc(const uint32_t* p, uint32_t (&w)[8]) {
-    asm volatile("ld.global.nc.v8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
-                   "=r"(w[6]), "=r"(w[7])
-                 : "l"(p));
-}
-
 // ---------------------------------------------------------------------------------
-// Guide preparation: one patch record per pixel.
+// Guide preparation: "row patches".  Slot (r, c) holds the k pixels
+// (r, clamp(c-p .. c+p)) as 3k bytes in RPW words (zero padded), so one patch row of
+// Eq. 1 is one aligned 16- or 32-byte load and row clamping is an index clamp.
 // ---------------------------------------------------------------------------------
 template <int K>
 __global__ void __launch_bounds__(256) prep_guides_kernel(const uint8_t* __restrict__ frames,
                                                           int H, int W,
-                                                          uint32_t* __restrict__ rec) {
-    using R = Rec<K>;
+                                                          uint32_t* __restrict__ rp) {
+    using G = Geo<K>;
     const size_t npx = static_cast<size_t>(H) * W;
     const size_t pix = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (pix >= npx) return;
     const size_t f = blockIdx.y;
     const int r = static_cast<int>(pix / W), c = static_cast<int>(pix % W);
     const uint8_t* img = frames + f * npx * 3;
-
-    uint32_t words[R::WORDS];
+    uint32_t words[G::RPW];
 #pragma unroll
-    for (int w = 0; w < R::WORDS; ++w) words[w] = 0;
-    uint32_t sum[3] = {0u, 0u, 0u};
+    for (int w = 0; w < G::RPW; ++w) words[w] = 0;
 #pragma unroll
-    for (int a = 0; a < K; ++a) {
-        const int rr = clampi(r - R::P + a, 0, H - 1);
+    for (int m = 0; m < K; ++m) {
+        const int cc = clampi(c - G::P + m, 0, W - 1);
+        const uint8_t* q = img + (static_cast<size_t>(r) * W + cc) * 3;
 #pragma unroll
-        for (int b = 0; b < K; ++b) {
-            const int cc = clampi(c - R::P + b, 0, W - 1);
-            const uint8_t* q = img + (static_cast<size_t>(rr) * W + cc) * 3;
-#pragma unroll
-            for (int ch = 0; ch < 3; ++ch) {
-                const uint32_t v = q[ch];
-                const int idx = 3 * (a * K + b) + ch;
-                words[R::HEAD + (idx >> 2)] |= v << (8 * (idx & 3));
-                sum[ch] += v;
-            }
+        for (int ch = 0; ch < 3; ++ch) {
+            const int idx = 3 * m + ch;
+            words[idx >> 2] |= static_cast<uint32_t>(q[ch]) << (8 * (idx & 3));
         }
     }
-    words[0] = sum[0] | (sum[1] << 16);
-    words[1] = sum[2];
-    uint4* dst = reinterpret_cast<uint4*>(rec + (f * npx + pix) * R::WORDS);
+    uint4* dst = reinterpret_cast<uint4*>(rp + (f * npx + pix) * G::RPW);
 #pragma unroll
-    for (int v = 0; v < R::WORDS / 4; ++v)
+    for (int v = 0; v < G::RPW / 4; ++v)
         dst[v] = make_uint4(words[4 * v], words[4 * v + 1], words[4 * v + 2], words[4 * v + 3]);
 }
 
@@ -149,129 +126,85 @@ __global__ void __launch_bounds__(256) style_rgbx_kernel(const uint8_t* __restri
 }
 
 // ---------------------------------------------------------------------------------
-// Patch distance (Eq. 1) against a target record held in shared memory
+// Patch distance (Eq. 1)
 // ---------------------------------------------------------------------------------
-// Each thread keeps its own target record in shared memory (registers stay free for
-// occupancy): sector s as two 16-byte halves, plane-major so a warp's accesses are
-// contiguous, plus each sector's sum of squares over its patch words.
 template <int K>
-struct TargetSmem {
-    uint4* w;      // [SECTORS][2][TILE_THREADS]
-    uint32_t* e;   // [SECTORS][TILE_THREADS]
-    int tid;
-    uint32_t sum01, sum2;  // channel sums of the target patch
-    __device__ __forceinline__ uint4 half(int s, int h) const {
-        return w[(s * 2 + h) * TILE_THREADS + tid];
+__device__ __forceinline__ void load_row(const uint32_t* __restrict__ p,
+                                         uint32_t (&out)[Geo<K>::NW]) {
+    constexpr int NW = Geo<K>::NW;
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int v = 0; v < NW / 4; ++v) {
+        const uint4 t = __ldg(q + v);
+        out[4 * v] = t.x;
+        out[4 * v + 1] = t.y;
+        out[4 * v + 2] = t.z;
+        out[4 * v + 3] = t.w;
     }
-    __device__ __forceinline__ uint32_t energy(int s) const { return e[s * TILE_THREADS + tid]; }
+    constexpr int rem = NW % 4;
+    if constexpr (rem == 2) {
+        const uint2 t = __ldg(reinterpret_cast<const uint2*>(p + NW - 2));
+        out[NW - 2] = t.x;
+        out[NW - 1] = t.y;
+    } else if constexpr (rem == 3) {
+        const uint4 t = __ldg(q + NW / 4);
+        out[NW - 3] = t.x;
+        out[NW - 2] = t.y;
+        out[NW - 1] = t.z;
+    } else if constexpr (rem == 1) {
+        out[NW - 1] = __ldg(p + NW - 1);
+    }
+}
+
+template <int K>
+struct TargetPatch {
+    uint32_t w[K][Geo<K>::NW];  // the k rows of the target patch
+    uint32_t row_e[K];          // sum of squares of each row
 };
 
 template <int K>
-constexpr size_t target_smem_bytes() {
-    return static_cast<size_t>(Rec<K>::SECTORS) * TILE_THREADS * (2 * sizeof(uint4) + sizeof(uint32_t));
-}
-
-template <int K>
-__device__ __forceinline__ TargetSmem<K> stage_target(const uint32_t* __restrict__ rec_t,
-                                                      size_t xpix, unsigned char* smem) {
-    using R = Rec<K>;
-    TargetSmem<K> t;
-    t.w = reinterpret_cast<uint4*>(smem);
-    t.e = reinterpret_cast<uint32_t*>(smem + static_cast<size_t>(R::SECTORS) * 2 * TILE_THREADS * sizeof(uint4));
-    t.tid = threadIdx.y * TILE_W + threadIdx.x;
-    const uint32_t* p = rec_t + xpix * R::WORDS;
+__device__ __forceinline__ void load_target(const uint32_t* __restrict__ rpt, int H, int W,
+                                            int r, int c, TargetPatch<K>& t) {
+    using G = Geo<K>;
 #pragma unroll
-    for (int s = 0; s < R::SECTORS; ++s) {
-        uint32_t w[8];
-        ld256_nc(p + 8 * s, w);
-        if (s == 0) {
-            t.sum01 = w[0];
-            t.sum2 = w[1];
-        }
+    for (int a = 0; a < K; ++a) {
+        const int rr = clampi(r - G::P + a, 0, H - 1);
+        load_row<K>(rpt + (static_cast<size_t>(rr) * W + c) * G::RPW, t.w[a]);
         uint32_t e = 0;
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            const int wi = 8 * s + q;
-            if (wi >= R::HEAD && wi < R::HEAD + R::PATCH_WORDS) e = __dp4a(w[q], w[q], e);
-        }
-        t.w[(s * 2 + 0) * TILE_THREADS + t.tid] = make_uint4(w[0], w[1], w[2], w[3]);
-        t.w[(s * 2 + 1) * TILE_THREADS + t.tid] = make_uint4(w[4], w[5], w[6], w[7]);
-        t.e[s * TILE_THREADS + t.tid] = e;
+        for (int w = 0; w < G::NW; ++w) e = __dp4a(t.w[a][w], t.w[a][w], e);
+        t.row_e[a] = e;
     }
-    return t;
 }
 
-// Eq. 1 error of the source patch whose record starts at `src`, against target t.
-// The error is accumulated one 32-byte sector at a time as the exact non-negative sum
-// |s|^2 + |t|^2 - 2 <s, t> over that sector's patch bytes (dp4a, four byte pairs per
-// instruction).  Rejection is exact and only skips work:
-//   * with `use_bound`, the first sector's channel sums give the Cauchy-Schwarz bound
-//     k^2 * SSD >= sum_ch (sum_s,ch - sum_t,ch)^2, so a candidate whose bound reaches
-//     `bound` cannot be strictly better than the incumbent;
-//   * after each sector, a running sum that reaches `bound` stops the work.
-// The loads of CHUNK consecutive sectors are issued together before any is used:
-// CHUNK = 1 saves bytes for candidates that are usually rejected at once, a larger
-// CHUNK saves dependent round trips for candidates that usually need every sector.
-// Returns true, with the full error in *e, only when the error is below `bound`.
-template <int K, int CHUNK>
-__device__ __forceinline__ bool patch_error_below(const uint32_t* __restrict__ src,
-                                                  const TargetSmem<K>& t, uint32_t bound,
-                                                  bool use_bound, uint32_t* e) {
-    using R = Rec<K>;
+// Eq. 1 error of source patch u = (ur, uc) against target t, accumulated row by row as
+// the exact non-negative terms |s_a|^2 + |t_a|^2 - 2 <s_a, t_a> (dp4a, four byte pairs
+// per instruction).  Once the running sum reaches `bound` the candidate cannot be
+// strictly better than the incumbent and its remaining rows are not loaded (returns
+// false).  Otherwise returns true with the full error in *e.
+template <int K>
+__device__ __forceinline__ bool patch_error_below(const uint32_t* __restrict__ rps, int H, int W,
+                                                  int ur, int uc, const TargetPatch<K>& t,
+                                                  uint32_t bound, uint32_t* e) {
+    using G = Geo<K>;
     uint32_t acc = 0;
 #pragma unroll
-    for (int s0 = 0; s0 < R::SECTORS; s0 += CHUNK) {
-        uint32_t w[CHUNK][8];
+    for (int a = 0; a < K; ++a) {
+        const int rr = clampi(ur - G::P + a, 0, H - 1);
+        uint32_t s[G::NW];
+        load_row<K>(rps + (static_cast<size_t>(rr) * W + uc) * G::RPW, s);
+        uint32_t dot = 0, ss = 0;
 #pragma unroll
-        for (int j = 0; j < CHUNK; ++j)
-            if (s0 + j < R::SECTORS) ld256_nc(src + 8 * (s0 + j), w[j]);
-#pragma unroll
-        for (int j = 0; j < CHUNK; ++j) {
-            const int s = s0 + j;
-            if (s >= R::SECTORS) break;
-            if (s == 0 && use_bound) {
-                const int d0 = static_cast<int>(w[j][0] & 0xFFFFu) - static_cast<int>(t.sum01 & 0xFFFFu);
-                const int d1 = static_cast<int>(w[j][0] >> 16) - static_cast<int>(t.sum01 >> 16);
-                const int d2 = static_cast<int>(w[j][1]) - static_cast<int>(t.sum2);
-                const uint64_t lb = static_cast<uint64_t>(d0 * d0) + static_cast<uint64_t>(d1 * d1) +
-                                    static_cast<uint64_t>(d2 * d2);
-                if (lb >= static_cast<uint64_t>(bound) * (K * K)) return false;
-            }
-            const uint4 ta = t.half(s, 0), tb = t.half(s, 1);
-            const uint32_t tv[8] = {ta.x, ta.y, ta.z, ta.w, tb.x, tb.y, tb.z, tb.w};
-            uint32_t dot = 0, ss = 0;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const int wi = 8 * s + q;
-                if (wi >= R::HEAD && wi < R::HEAD + R::PATCH_WORDS) {
-                    dot = __dp4a(w[j][q], tv[q], dot);
-                    ss = __dp4a(w[j][q], w[j][q], ss);
-                }
-            }
-            acc += ss + t.energy(s) - 2u * dot;
-            if (acc >= bound) return false;
+        for (int w = 0; w < G::NW; ++w) {
+            dot = __dp4a(s[w], t.w[a][w], dot);
+            ss = __dp4a(s[w], s[w], ss);
         }
+        acc += ss + t.row_e[a] - 2u * dot;
+        if (acc >= bound) return false;
     }
     *e = acc;
     return true;
 }
-
-#ifndef FB_PROP_CHUNK
-#define FB_PROP_CHUNK 4       // sectors loaded together for propagation candidates
-#endif
-#ifndef FB_NEAR_CHUNK
-#define FB_NEAR_CHUNK 4       // ... for random-search candidates with radius <= FB_NEAR_RADIUS
-#endif
-#ifndef FB_FAR_CHUNK
-#define FB_FAR_CHUNK 1        // ... for random-search candidates with a larger radius
-#endif
-#ifndef FB_NEAR_RADIUS
-#define FB_NEAR_RADIUS 16
-#endif
-template <int K, int C>
-struct Chunk {
-    static constexpr int value = C < Rec<K>::SECTORS ? C : Rec<K>::SECTORS;
-};
 
 struct TileCoord {
     int r, c;
@@ -290,20 +223,17 @@ __device__ __forceinline__ TileCoord tile_coord(int W) {
 template <int K>
 __global__ void __launch_bounds__(TILE_THREADS)
     nnf_init_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
-                    const uint32_t* __restrict__ rec, int mode,
+                    const uint32_t* __restrict__ rp, int mode,
                     const uint32_t* __restrict__ coarse_F, int Hc, int Wc,
                     const int32_t* __restrict__ user_init, uint32_t key0, uint32_t key1,
                     uint32_t level_word, uint32_t* __restrict__ F, uint32_t* __restrict__ E) {
-    using R = Rec<K>;
-    extern __shared__ __align__(16) unsigned char smem[];
+    using G = Geo<K>;
     const TileCoord tc = tile_coord(W);
     if (tc.r >= H || tc.c >= W) return;
     const int pl = blockIdx.y;
     const PairDesc pd = pairs[pair0 + pl];
     const size_t npx = static_cast<size_t>(H) * W;
     const size_t x = static_cast<size_t>(tc.r) * W + tc.c;
-    const TargetSmem<K> t =
-        stage_target<K>(rec + static_cast<size_t>(pd.tgt) * npx * R::WORDS, x, smem);
 
     int ur, uc;
     if (mode == 0) {
@@ -320,13 +250,21 @@ __global__ void __launch_bounds__(TILE_THREADS)
         ur = clampi(user_init[2 * x], 0, H - 1);
         uc = clampi(user_init[2 * x + 1], 0, W - 1);
     }
-    const uint32_t* recs = rec + static_cast<size_t>(pd.src) * npx * R::WORDS;
+    TargetPatch<K> t;
+    load_target<K>(rp + static_cast<size_t>(pd.tgt) * npx * G::RPW, H, W, tc.r, tc.c, t);
     uint32_t e = 0;
-    patch_error_below<K, Chunk<K, 4>::value>(recs + (static_cast<size_t>(ur) * W + uc) * R::WORDS,
-                                             t, 0xFFFFFFFFu, false, &e);
+    patch_error_below<K>(rp + static_cast<size_t>(pd.src) * npx * G::RPW, H, W, ur, uc, t,
+                         0xFFFFFFFFu, &e);
     F[static_cast<size_t>(pl) * npx + x] = pack_rc(ur, uc);
     E[static_cast<size_t>(pl) * npx + x] = e;
 }
+
+// Resident 256-thread blocks per SM the iteration kernel is compiled for: larger
+// patches hold more target words in registers.
+template <int K>
+struct IterOccupancy {
+    static constexpr int value = K <= 3 ? 6 : K <= 5 ? FB_ITER_MIN_BLOCKS : K <= 7 ? 3 : 2;
+};
 
 // ---------------------------------------------------------------------------------
 // Alg. 1: one Jacobi iteration (Sec. 3.2 parallel update).  Reads the snapshot
@@ -336,14 +274,13 @@ __global__ void __launch_bounds__(TILE_THREADS)
 // skipped: its error equals the incumbent's, so it could not win.
 // ---------------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(TILE_THREADS, FB_ITER_MIN_BLOCKS * 256 / TILE_THREADS)
+__global__ void __launch_bounds__(TILE_THREADS, IterOccupancy<K>::value * 256 / TILE_THREADS)
     nnf_iter_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
-                    const uint32_t* __restrict__ rec, int r0,
+                    const uint32_t* __restrict__ rp, int r0,
                     uint32_t key0, uint32_t key1, uint32_t ctr_word,
                     const uint32_t* __restrict__ Fp, const uint32_t* __restrict__ Ep,
                     uint32_t* __restrict__ Fn, uint32_t* __restrict__ En) {
-    using R = Rec<K>;
-    extern __shared__ __align__(16) unsigned char smem[];
+    using G = Geo<K>;
     const TileCoord tc = tile_coord(W);
     if (tc.r >= H || tc.c >= W) return;
     const int r = tc.r, c = tc.c;
@@ -351,44 +288,41 @@ __global__ void __launch_bounds__(TILE_THREADS, FB_ITER_MIN_BLOCKS * 256 / TILE_
     const PairDesc pd = pairs[pair0 + pl];
     const size_t npx = static_cast<size_t>(H) * W;
     const size_t x = static_cast<size_t>(r) * W + c;
-    const uint32_t* __restrict__ recs = rec + static_cast<size_t>(pd.src) * npx * R::WORDS;
+    const uint32_t* __restrict__ rps = rp + static_cast<size_t>(pd.src) * npx * G::RPW;
     const uint32_t* __restrict__ Fpp = Fp + static_cast<size_t>(pl) * npx;
-    const TargetSmem<K> t =
-        stage_target<K>(rec + static_cast<size_t>(pd.tgt) * npx * R::WORDS, x, smem);
+
+    TargetPatch<K> t;
+    load_target<K>(rp + static_cast<size_t>(pd.tgt) * npx * G::RPW, H, W, r, c, t);
 
     uint32_t bf = Fpp[x];
     uint32_t be = Ep[static_cast<size_t>(pl) * npx + x];
 
-    auto consider = [&](int cr, int cc, auto chunk) {
+    auto consider = [&](int cr, int cc) {
         const uint32_t f = pack_rc(cr, cc);
         if (f == bf) return;
         uint32_t e;
-        if (patch_error_below<K, decltype(chunk)::value>(
-                recs + (static_cast<size_t>(cr) * W + cc) * R::WORDS, t, be, true, &e)) {
+        if (patch_error_below<K>(rps, H, W, cr, cc, t, be, &e)) {
             be = e;
             bf = f;
         }
     };
-    const Chunk<K, FB_PROP_CHUNK> prop_chunk;
-    const Chunk<K, FB_NEAR_CHUNK> near_chunk;
-    const Chunk<K, FB_FAR_CHUNK> far_chunk;
 
     // Propagation: F'(x) = F(x + d) - d.
     if (r > 0) {
         const uint32_t f = Fpp[x - W];
-        consider(min(row_of(f) + 1, H - 1), col_of(f), prop_chunk);
+        consider(min(row_of(f) + 1, H - 1), col_of(f));
     }
     if (r < H - 1) {
         const uint32_t f = Fpp[x + W];
-        consider(max(row_of(f) - 1, 0), col_of(f), prop_chunk);
+        consider(max(row_of(f) - 1, 0), col_of(f));
     }
     if (c > 0) {
         const uint32_t f = Fpp[x - 1];
-        consider(row_of(f), min(col_of(f) + 1, W - 1), prop_chunk);
+        consider(row_of(f), min(col_of(f) + 1, W - 1));
     }
     if (c < W - 1) {
         const uint32_t f = Fpp[x + 1];
-        consider(row_of(f), max(col_of(f) - 1, 0), prop_chunk);
+        consider(row_of(f), max(col_of(f) - 1, 0));
     }
 
     // Random search: F'(x) = F(x) + U[-r, r]^2, r = r0 >> t, t = 0, 1, ... while r >= 1.
@@ -402,11 +336,7 @@ __global__ void __launch_bounds__(TILE_THREADS, FB_ITER_MIN_BLOCKS * 256 / TILE_
         const uint32_t span = static_cast<uint32_t>(2 * rad + 1);
         const int dr = static_cast<int>(__umulhi((tt & 1) ? u.z : u.x, span)) - rad;
         const int dc = static_cast<int>(__umulhi((tt & 1) ? u.w : u.y, span)) - rad;
-        const int cr = clampi(row_of(bf) + dr, 0, H - 1), cc = clampi(col_of(bf) + dc, 0, W - 1);
-        if (rad <= FB_NEAR_RADIUS)
-            consider(cr, cc, near_chunk);
-        else
-            consider(cr, cc, far_chunk);
+        consider(clampi(row_of(bf) + dr, 0, H - 1), clampi(col_of(bf) + dc, 0, W - 1));
     }
 
     Fn[static_cast<size_t>(pl) * npx + x] = bf;
@@ -492,14 +422,6 @@ __global__ void __launch_bounds__(TILE_THREADS)
     o[2] = __fdiv_rn(__uint2float_rn(a2), den);
 }
 
-// Opt a kernel in to the dynamic shared memory it needs (once per kernel).
-template <class Kernel>
-inline void prepare_smem(Kernel kernel, size_t bytes) {
-    if (bytes > 48 * 1024)
-        cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(bytes));
-}
-
 inline dim3 tile_grid(int H, int W, int n) {
     const unsigned tiles = static_cast<unsigned>(((W + TILE_W - 1) / TILE_W) *
                                                  ((H + TILE_H - 1) / TILE_H));
@@ -521,10 +443,10 @@ inline unsigned blocks_for(size_t n, unsigned per) {
 }  // namespace
 
 cudaError_t launch_prep_guides(int k, const uint8_t* frames, int n_frames, int H, int W,
-                               uint32_t* rec, cudaStream_t st) {
+                               uint32_t* rp, cudaStream_t st) {
     if (n_frames <= 0) return cudaSuccess;
     const dim3 grid(blocks_for(static_cast<size_t>(H) * W, 256), static_cast<unsigned>(n_frames));
-    FB_DISPATCH_K(k, (prep_guides_kernel<KK><<<grid, 256, 0, st>>>(frames, H, W, rec)));
+    FB_DISPATCH_K(k, (prep_guides_kernel<KK><<<grid, 256, 0, st>>>(frames, H, W, rp)));
     return cudaGetLastError();
 }
 
@@ -551,9 +473,8 @@ cudaError_t launch_nnf_init(int k, const PairDesc* pairs, int pair0, int n_pairs
     const dim3 grid = tile_grid(g.H, g.W, n_pairs);
     const dim3 block(TILE_W, TILE_H);
     const uint32_t level_word = static_cast<uint32_t>(level) << 24;
-    FB_DISPATCH_K(k, (prepare_smem(nnf_init_kernel<KK>, target_smem_bytes<KK>()),
-                      nnf_init_kernel<KK><<<grid, block, target_smem_bytes<KK>(), st>>>(
-                         pairs, pair0, g.H, g.W, g.rec, mode, coarse_F, Hc, Wc, user_init,
+    FB_DISPATCH_K(k, (nnf_init_kernel<KK><<<grid, block, 0, st>>>(
+                         pairs, pair0, g.H, g.W, g.rp, mode, coarse_F, Hc, Wc, user_init,
                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32),
                          level_word, F, E)));
     return cudaGetLastError();
@@ -568,9 +489,8 @@ cudaError_t launch_nnf_iter(int k, const PairDesc* pairs, int pair0, int n_pairs
     const dim3 block(TILE_W, TILE_H);
     const uint32_t ctr_word = (static_cast<uint32_t>(level) << 24) |
                               (static_cast<uint32_t>(it + 1) << 8);
-    FB_DISPATCH_K(k, (prepare_smem(nnf_iter_kernel<KK>, target_smem_bytes<KK>()),
-                      nnf_iter_kernel<KK><<<grid, block, target_smem_bytes<KK>(), st>>>(
-                         pairs, pair0, g.H, g.W, g.rec, r0,
+    FB_DISPATCH_K(k, (nnf_iter_kernel<KK><<<grid, block, 0, st>>>(
+                         pairs, pair0, g.H, g.W, g.rp, r0,
                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32),
                          ctr_word, Fp, Ep, Fn, En)));
     return cudaGetLastError();

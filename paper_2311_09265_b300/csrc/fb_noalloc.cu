@@ -135,7 +135,7 @@ extern "C" int fb_blend_window_noalloc(const uint8_t* guides, const uint8_t* sty
     if (!on_device(guides, device) || !on_device(styles, device) || !on_device(out, device))
         return report(FB_ERR_ARG, "guides, styles and out must be device memory of the current device");
 
-    const int k = p->patch, M = (window - 1) / 2, recw = fb::patch_record_words(k);
+    const int k = p->patch, M = (window - 1) / 2, recw = fb::rowpatch_words(k);
     int hs[16], ws[16];
     hs[0] = H;
     ws[0] = W;
