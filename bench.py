@@ -40,6 +40,10 @@ L2_BYTES = 126 * 1024 * 1024
 FLUSH_BYTES = 512 * 1024 * 1024
 SM_COUNT_NOMINAL = 148
 SM_MAX_MHZ_NOMINAL = 2032.0
+DP4A_PER_CLK_SM = 64        # integer dot-product (dp4a) issue rate per SM per clock
+# dram__bytes_read.sum + dram__bytes_write.sum of one nnf_iter launch, from an ncu capture
+# of the current kernel, scaled to the workload (see profiles/); None when not captured.
+TRAFFIC_PER_LAUNCH = {"blend_512": 5.81e9}
 
 
 def parse_args(argv=None):
@@ -51,7 +55,7 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="blend_512", choices=sorted(synth.WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--cpu-sample-frames", type=int, default=1)
+    ap.add_argument("--cpu-sample-frames", type=int, default=5)
     return ap.parse_args(argv)
 
 
@@ -232,8 +236,8 @@ def run_gpu(args):
     g, s = make_inputs(w, shard_seed(w.seed, rank))
     ctx = fbp.Context(local)
     params = fbp.Params.make(w.patch, w.iters, w.levels, 0, w.seed)
-    g_d = torch.from_numpy(g).cuda()
-    s_d = torch.from_numpy(s).cuda()
+    g_d = torch.tensor(g, device="cuda")
+    s_d = torch.tensor(s, device="cuda")
     out = torch.empty((w.N, w.H, w.W, 3), dtype=torch.float32, device="cuda")
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
@@ -278,8 +282,8 @@ def run_gpu(args):
     # ---- end to end through the C ABI with pinned host buffers ----
     e2e = None
     if not args.no_e2e:
-        g_h = torch.from_numpy(g).pin_memory()
-        s_h = torch.from_numpy(s).pin_memory()
+        g_h = torch.tensor(g).pin_memory()
+        s_h = torch.tensor(s).pin_memory()
         o_h = torch.empty((w.N, w.H, w.W, 3), dtype=torch.float32).pin_memory()
         step(g_h, s_h, o_h)                     # warm (staging buffers)
         if world > 1:
@@ -307,20 +311,15 @@ def run_gpu(args):
         avg_s = iter_ms / iter_n / 1e3
         achieved = ops / avg_s / 1e12
         sms = torch.cuda.get_device_properties(local).multi_processor_count
-        per_clk_sm = None
-        if clocks.get("sm_mhz"):
-            per_clk_sm = rate / (sms * clocks["sm_mhz"] * 1e6)
-        peak = 4.0 * rate / 1e12
-        peak_basis = "probe at the sampled clock"
-        if per_clk_sm:
-            # dp4a per SM per clock from the probe, x SMs x max clock x 4 byte pairs
-            peak = 4.0 * round(per_clk_sm) * SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-            peak_basis = (f"{round(per_clk_sm)} dp4a/clk/SM (probe) x {SM_COUNT_NOMINAL} SMs x "
-                          f"{SM_MAX_MHZ_NOMINAL:.0f} MHz x 4 byte pairs")
+        probe_per_clk = rate / (sms * clocks["sm_mhz"] * 1e6) if clocks.get("sm_mhz") else None
+        peak = DP4A_PER_CLK_SM * 4 * SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": "nnf_iter (Alg. 1 Jacobi iteration)",
                 "achieved": achieved, "peak": peak, "unit": "T byte-pair ops/s",
-                "frac": achieved / peak, "traffic": None,
-                "peak_basis": peak_basis,
+                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
+                "peak_basis": (f"{DP4A_PER_CLK_SM} dp4a/clk/SM x {SM_COUNT_NOMINAL} SMs x "
+                               f"{SM_MAX_MHZ_NOMINAL:.0f} MHz x 4 byte pairs (derived; the live "
+                               f"register-only probe measured {probe_per_clk:.1f} dp4a/clk/SM)"
+                               if probe_per_clk else "derived"),
                 "avg_launch_ms": iter_ms / iter_n, "launches": iter_n,
                 "share_of_kernel_time": iter_ms / kernel_total_ms if kernel_total_ms else None,
                 "candidate_evals_per_s": w.candidate_evals() * args.steps * world / (total_ms / 1e3),
