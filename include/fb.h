@@ -174,6 +174,54 @@ int fb_interpolate(fb_ctx *ctx, const uint8_t *guides, int N, int H, int W,
                    const int32_t *key_idx, const uint8_t *key_styles, int n_keys,
                    const fb_params *p, float *out, void *stream);
 
+/* One clip of a batched submission (fb_blend_batch).  All pointers are device
+ * pointers of the context's device, owned by the caller. */
+typedef struct fb_clip_desc {
+    const uint8_t *guides;  /* N x H x W x 3 guide frames                        */
+    const uint8_t *styles;  /* N x H x W x 3 style frames                        */
+    float *out;             /* N x H x W x 3 output, float32 in [0, 1]           */
+    int32_t N, H, W;        /* 1 <= N <= 65535; patch <= H, W <= 32767            */
+    int32_t window;         /* odd, >= 1 (Eq. 2, truncated at the clip ends)     */
+    int32_t patch;          /* odd, 3..9                                         */
+    int32_t reserved;       /* must be 0                                         */
+} fb_clip_desc;
+
+#define FB_BATCH_NO_GRAPH 0x1u            /* launch directly, do not capture/replay */
+#define FB_BATCH_VARIANT(v) (((uint32_t)(v) + 1u) << 8)  /* force tile variant v (0..3) */
+
+/* Eq. 2 window blends of n_clips clips of uneven size, window and patch in one
+ * submission.  This batched, persistent form is not in the paper; the paper only
+ * notes that images are processed in batches (Sec. 3.2) and that a task manager
+ * schedules the NNF tasks (Sec. 3.4.1).  Each clip's output is bit-identical to
+ * fb_blend_window on that clip with the same fb_params (p->patch is ignored: every
+ * clip carries its own patch; p->levels must be 1).
+ *   clips  HOST array of n_clips descriptors (copied; need not outlive the call).
+ * Mechanics: all NNFs of all clips are cut into 32-column tiles and processed by
+ * persistent kernels (grid = SMs x resident blocks) that walk a flattened work list,
+ * one launch per Jacobi iteration and patch size, in chunks whose NNF buffers fit the
+ * pair budget.  The first submission of a given manifest (pointers, shapes, params)
+ * tunes the tile shape / occupancy per patch size on its first iteration (all variants
+ * give identical results), then captures the whole submission into a CUDA graph that
+ * later submissions with the same manifest replay (FB_BATCH_NO_GRAPH: direct
+ * launches).  The context keeps the tables, scratch and graph of the two most recent
+ * manifests.  Async on `stream`; do not call it while `stream` is being captured. */
+int fb_blend_batch(fb_ctx *ctx, const fb_clip_desc *clips, int n_clips, const fb_params *p,
+                   uint32_t flags, void *stream);
+
+/* Host-only planning of a batch (no CUDA calls): number of NNFs, persistent-kernel work
+ * items per iteration (32x8 tiles) and chunks under a pair budget of budget_bytes of
+ * NNF scratch (0 = the library's default). */
+int fb_batch_plan(const fb_clip_desc *clips, int n_clips, const fb_params *p, size_t budget_bytes,
+                  uint64_t *n_pairs, uint64_t *n_items, int *n_chunks);
+
+/* Bytes of NNF scratch (four H x W words per NNF) one chunk of pairs may use in this
+ * context's blend, interpolation and batch calls (0 = the default, 8 GiB; minimum
+ * 1 MiB).  Larger inputs run in more chunks; results do not depend on it. */
+int fb_ctx_set_pair_budget(fb_ctx *ctx, size_t bytes);
+
+/* Tile variant the autotuner chose for patch size k in this context, or -1. */
+int fb_ctx_batch_variant(const fb_ctx *ctx, int patch);
+
 /* Bytes of the fixed device scratch array used by fb_blend_window_noalloc. */
 #define FB_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 

@@ -24,7 +24,15 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_status_string", "fb_ctx_launches", "fb_ctx_scratch_bytes",
                     "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a", "fb_pair_tag",
                     "fb_nnf", "fb_remap", "fb_blend_window", "fb_interpolate",
-                    "fb_blend_window_noalloc")
+                    "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan",
+                    "fb_ctx_batch_variant", "fb_ctx_set_pair_budget")
+
+FB_BATCH_NO_GRAPH = 0x1
+
+
+def FB_BATCH_VARIANT(v: int) -> int:
+    """Flag that forces tile variant v (0..3) of the batched path."""
+    return (v + 1) << 8
 
 # fb_kernel_kind, in header order.
 KERNEL_KINDS = ("prep", "downsample", "style", "init", "iter", "unpack", "pack", "combine")
@@ -41,6 +49,14 @@ class Params(ctypes.Structure):
     def make(cls, patch: int, iters: int, levels: int = 1, r0: int = 0, seed: int = 0,
              pair_tag: int = 0) -> "Params":
         return cls(patch, iters, levels, r0, seed & 0xFFFFFFFFFFFFFFFF, pair_tag & 0xFFFFFFFF, 0)
+
+
+class ClipDesc(ctypes.Structure):
+    """fb_clip_desc: one clip of a batched submission (device pointers)."""
+    _fields_ = [("guides", ctypes.c_void_p), ("styles", ctypes.c_void_p),
+                ("out", ctypes.c_void_p), ("N", ctypes.c_int32), ("H", ctypes.c_int32),
+                ("W", ctypes.c_int32), ("window", ctypes.c_int32), ("patch", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class FastBlendError(RuntimeError):
@@ -93,6 +109,17 @@ def lib() -> ctypes.CDLL:
         L.fb_blend_window_noalloc.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, P, _vp, _vp]
         L.fb_blend_window_noalloc.restype = ctypes.c_int
+        CP = ctypes.POINTER(ClipDesc)
+        L.fb_blend_batch.argtypes = [_vp, CP, ctypes.c_int, P, ctypes.c_uint32, _vp]
+        L.fb_blend_batch.restype = ctypes.c_int
+        L.fb_batch_plan.argtypes = [CP, ctypes.c_int, P, ctypes.c_size_t,
+                                    ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
+                                    ctypes.POINTER(ctypes.c_int)]
+        L.fb_batch_plan.restype = ctypes.c_int
+        L.fb_ctx_set_pair_budget.argtypes = [_vp, ctypes.c_size_t]
+        L.fb_ctx_set_pair_budget.restype = ctypes.c_int
+        L.fb_ctx_batch_variant.argtypes = [_vp, ctypes.c_int]
+        L.fb_ctx_batch_variant.restype = ctypes.c_int
         for f in ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_ctx_profile",
                   "fb_ctx_profile_read", "fb_nnf", "fb_remap",
                   "fb_blend_window", "fb_interpolate"):
@@ -160,6 +187,10 @@ class Context:
         rate, ms = ctypes.c_double(), ctypes.c_double()
         self.check(lib().fb_probe_dp4a(self._h, ctypes.byref(rate), ctypes.byref(ms)))
         return rate.value, ms.value
+
+    def set_pair_budget(self, nbytes: int) -> None:
+        """Bytes of NNF scratch per chunk of pairs (0 = library default)."""
+        self.check(lib().fb_ctx_set_pair_budget(self._h, int(nbytes)))
 
     def sync(self, stream: Optional[torch.cuda.Stream] = None) -> None:
         self.check(lib().fb_ctx_sync(self._h, _stream_handle(stream, self.device)))
@@ -262,3 +293,44 @@ def fb_interpolate(ctx: Context, guides: torch.Tensor, key_idx: Sequence[int],
                               _stream_handle(stream, ctx.device))
     ctx.check(rc)
     return out
+
+
+def fb_blend_batch(ctx: Context, clips, params: Params, flags: int = 0, stream=None):
+    """Eq. 2 blends of several clips in one submission.  `clips` is a sequence of
+    (guides, styles, window, patch[, out]) with (N,H,W,3) uint8 CUDA tensors; returns
+    the list of (N,H,W,3) float32 outputs (bit-identical to fb_blend_window per clip)."""
+    descs = (ClipDesc * len(clips))()
+    outs, keep = [], []
+    for i, c in enumerate(clips):
+        g, s, window, patch = c[0], c[1], int(c[2]), int(c[3])
+        N, H, W = (int(v) for v in g.shape[:3])
+        _shape(g, (N, H, W, 3), "guides")
+        _shape(s, (N, H, W, 3), "styles")
+        out = c[4] if len(c) > 4 and c[4] is not None else torch.empty(
+            (N, H, W, 3), dtype=torch.float32, device=g.device)
+        descs[i] = ClipDesc(_ptr(g, torch.uint8, "guides"), _ptr(s, torch.uint8, "styles"),
+                            _ptr(out, torch.float32, "out"), N, H, W, window, patch, 0)
+        outs.append(out)
+        keep += [g, s]
+    rc = lib().fb_blend_batch(ctx.handle, descs, len(clips), ctypes.byref(params), flags,
+                              _stream_handle(stream, ctx.device))
+    ctx.check(rc)
+    return outs
+
+
+def fb_batch_plan(shapes, params: Params, budget_bytes: int = 0):
+    """Host-only plan of a batch given (N, H, W, window, patch) tuples:
+    (number of NNFs, work items of 32x8 tiles per iteration, chunks)."""
+    descs = (ClipDesc * len(shapes))()
+    for i, (N, H, W, window, patch) in enumerate(shapes):
+        descs[i] = ClipDesc(None, None, None, N, H, W, window, patch, 0)
+    n_pairs, n_items, n_chunks = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_int()
+    rc = lib().fb_batch_plan(descs, len(shapes), ctypes.byref(params), budget_bytes,
+                             ctypes.byref(n_pairs), ctypes.byref(n_items), ctypes.byref(n_chunks))
+    if rc != FB_OK:
+        raise FastBlendError(rc, lib().fb_last_error(None).decode())
+    return n_pairs.value, n_items.value, n_chunks.value
+
+
+def fb_ctx_batch_variant(ctx: Context, patch: int) -> int:
+    return int(lib().fb_ctx_batch_variant(ctx.handle, patch))

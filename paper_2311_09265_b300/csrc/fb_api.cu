@@ -3,7 +3,10 @@
 // launch sequence of the FastBlend hot path.
 #include <cstdarg>
 #include <cstdio>
+#include <algorithm>
+#include <array>
 #include <cstring>
+#include <functional>
 #include <string>
 #include <vector>
 
@@ -30,6 +33,22 @@ struct fb_ctx {
         cudaEvent_t a, b;
     };
     std::vector<Rec> recs;
+    // Batched submissions: tuned tile variant per patch size, and the cached manifests.
+    int tuned_variant[10] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+    size_t pair_budget = 0;  // bytes of NNF scratch per chunk; 0 = kPairBudgetBytes
+    struct BatchEntry;
+    std::vector<BatchEntry*> batch_cache;  // most recent last
+};
+
+// One cached batch manifest: its key, device tables and scratch, and its graph.
+struct fb_ctx::BatchEntry {
+    std::vector<uint8_t> key;
+    char* dev = nullptr;
+    size_t bytes = 0;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches_per_run = 0;
+    std::vector<std::function<cudaError_t(cudaStream_t)>> steps;  // the submission's launches
+    std::vector<int> step_kind;
 };
 
 namespace {
@@ -316,10 +335,14 @@ struct Chunk {
     int job0, n_jobs, pair0, n_pairs;
 };
 
+size_t pair_budget(const fb_ctx* ctx) {
+    return ctx && ctx->pair_budget ? ctx->pair_budget : kPairBudgetBytes;
+}
+
 int make_chunks(fb_ctx* ctx, const std::vector<JobDesc>& jobs, size_t npx0,
                 std::vector<Chunk>& chunks, size_t& max_pairs) {
     const size_t per_pair = npx0 * 4 * sizeof(uint32_t);
-    size_t cap = kPairBudgetBytes / per_pair;
+    size_t cap = pair_budget(ctx) / per_pair;
     if (cap > static_cast<size_t>(kMaxChunkPairs)) cap = kMaxChunkPairs;
     if (cap < 1) cap = 1;
     max_pairs = 0;
@@ -418,6 +441,451 @@ namespace fb {
 void set_null_ctx_error(const char* msg) { g_null_ctx_err = msg; }
 }  // namespace fb
 
+
+// ---------------------------------------------------------------------------------
+// Batched submissions (fb_blend_batch)
+// ---------------------------------------------------------------------------------
+namespace {
+
+using fb::BatchClip;
+using fb::BatchJob;
+using fb::BatchPair;
+
+struct HostChunk {
+    int k = 0;
+    std::vector<BatchPair> pairs;
+    std::vector<BatchJob> jobs;
+    size_t fe_elems = 0;  // sum of H*W over the chunk's pairs
+};
+
+int check_clips(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* p, bool pointers) {
+    if (!clips || n < 1) return fail(ctx, FB_ERR_ARG, "clips must be a non-empty host array");
+    if (!p) return fail(ctx, FB_ERR_ARG, "params is NULL");
+    if (p->levels != 1) return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use levels == 1");
+    for (int c = 0; c < n; ++c) {
+        const fb_clip_desc& d = clips[c];
+        fb_params q = *p;
+        q.patch = d.patch;
+        int rc = check_params(ctx, &q, d.H, d.W);
+        if (rc) return rc;
+        if (d.N < 1 || d.N > 65535) return fail(ctx, FB_ERR_ARG, "clip %d: N = %d outside [1, 65535]", c, d.N);
+        if (d.window < 1 || (d.window & 1) == 0)
+            return fail(ctx, FB_ERR_ARG, "clip %d: window must be odd and >= 1", c);
+        if (d.reserved != 0) return fail(ctx, FB_ERR_ARG, "clip %d: reserved must be 0", c);
+        if (pointers) {
+            if (!d.guides || !d.styles || !d.out)
+                return fail(ctx, FB_ERR_ARG, "clip %d: NULL pointer", c);
+            if (classify(ctx, d.guides) != Mem::Device || classify(ctx, d.styles) != Mem::Device ||
+                classify(ctx, d.out) != Mem::Device)
+                return fail(ctx, FB_ERR_ARG, "clip %d: pointers must be device memory of the context's device", c);
+        }
+    }
+    return FB_OK;
+}
+
+// Clips in patch-size order; per patch size, output frames in clip order grouped into
+// chunks whose F/E ping-pong (4 words per pixel and pair) fits budget_bytes.
+int plan_chunks(fb_ctx* ctx, const fb_clip_desc* clips, int n, size_t budget_bytes,
+                std::vector<HostChunk>& chunks) {
+    const size_t budget_elems = budget_bytes / (4 * sizeof(uint32_t));
+    for (int k = 3; k <= 9; k += 2) {
+        HostChunk cur;
+        cur.k = k;
+        for (int c = 0; c < n; ++c) {
+            const fb_clip_desc& d = clips[c];
+            if (d.patch != k) continue;
+            const size_t npx = static_cast<size_t>(d.H) * d.W;
+            const int M = (d.window - 1) / 2;
+            for (int i = 0; i < d.N; ++i) {
+                const int lo = i - M < 0 ? 0 : i - M, hi = i + M > d.N - 1 ? d.N - 1 : i + M;
+                const size_t need = static_cast<size_t>(hi - lo) * npx;
+                if (need > budget_elems)
+                    return fail(ctx, FB_ERR_OOM, "clip %d frame %d needs %zu NNF words; the budget holds %zu",
+                                c, i, need, budget_elems);
+                if (cur.fe_elems + need > budget_elems || cur.pairs.size() + (hi - lo) > 0x7FFFFFFF) {
+                    chunks.push_back(std::move(cur));
+                    cur = HostChunk();
+                    cur.k = k;
+                }
+                BatchJob j{};
+                j.clip = c;
+                j.frame = i;
+                j.first_pair = static_cast<int32_t>(cur.pairs.size());
+                j.n_pairs = hi - lo;
+                j.den = static_cast<uint32_t>(255 * k * k * (hi - lo + 1));
+                cur.jobs.push_back(j);
+                for (int jj = lo; jj <= hi; ++jj) {
+                    if (jj == i) continue;
+                    BatchPair bp{};
+                    bp.clip = c;
+                    bp.src = jj;
+                    bp.tgt = i;
+                    bp.style = jj;
+                    bp.tag = fb_pair_tag(jj, i);
+                    bp.weight = 1u;
+                    bp.fe_off = cur.fe_elems;
+                    cur.pairs.push_back(bp);
+                    cur.fe_elems += npx;
+                }
+            }
+        }
+        if (!cur.jobs.empty()) chunks.push_back(std::move(cur));
+    }
+    return FB_OK;
+}
+
+size_t tiles_of(int H, int W, int th) {
+    return static_cast<size_t>((W + 31) / 32) * static_cast<size_t>((H + th - 1) / th);
+}
+
+void item_maps(const HostChunk& ch, const fb_clip_desc* clips, int th, std::vector<int32_t>& ip,
+               std::vector<int32_t>& it) {
+    ip.clear();
+    it.clear();
+    for (size_t p = 0; p < ch.pairs.size(); ++p) {
+        const fb_clip_desc& d = clips[ch.pairs[p].clip];
+        const size_t nt = tiles_of(d.H, d.W, th);
+        for (size_t t = 0; t < nt; ++t) {
+            ip.push_back(static_cast<int32_t>(p));
+            it.push_back(static_cast<int32_t>(t));
+        }
+    }
+}
+
+void job_maps(const HostChunk& ch, const fb_clip_desc* clips, std::vector<int32_t>& ij,
+              std::vector<int32_t>& it) {
+    ij.clear();
+    it.clear();
+    for (size_t j = 0; j < ch.jobs.size(); ++j) {
+        const fb_clip_desc& d = clips[ch.jobs[j].clip];
+        const size_t nt = tiles_of(d.H, d.W, 8);
+        for (size_t t = 0; t < nt; ++t) {
+            ij.push_back(static_cast<int32_t>(j));
+            it.push_back(static_cast<int32_t>(t));
+        }
+    }
+}
+
+std::vector<uint8_t> manifest_key(const fb_clip_desc* clips, int n, const fb_params* p,
+                                  uint32_t flags) {
+    std::vector<uint8_t> key(sizeof(fb_clip_desc) * n + sizeof(fb_params) + sizeof(flags));
+    std::memcpy(key.data(), clips, sizeof(fb_clip_desc) * n);
+    fb_params q = *p;
+    q.patch = 0;
+    q.pair_tag = 0;
+    std::memcpy(key.data() + sizeof(fb_clip_desc) * n, &q, sizeof(q));
+    std::memcpy(key.data() + sizeof(fb_clip_desc) * n + sizeof(q), &flags, sizeof(flags));
+    return key;
+}
+
+void drop_entry(fb_ctx::BatchEntry* be) {
+    if (be->exec) cudaGraphExecDestroy(be->exec);
+    if (be->dev) cudaFree(be->dev);
+    delete be;
+}
+
+int forced_variant(uint32_t flags) {
+    const uint32_t v = (flags >> 8) & 0xFFu;
+    return v == 0 ? -1 : static_cast<int>(v) - 1;
+}
+
+// Builds a cache entry: device tables and scratch, tuning, the list of launches and,
+// unless FB_BATCH_NO_GRAPH, the instantiated graph of the whole submission.
+int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* p, uint32_t flags,
+                cudaStream_t st, fb_ctx::BatchEntry* be) {
+    std::vector<HostChunk> chunks;
+    int rc = plan_chunks(ctx, clips, n, pair_budget(ctx), chunks);
+    if (rc) return rc;
+    int sms = 0;
+    FB_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+
+    // ---- device layout ----
+    Carver cv(nullptr);
+    struct ClipBufs { uint32_t* rp; uint32_t* sty; };
+    auto layout = [&](Carver& c, BatchClip** d_clips, std::vector<ClipBufs>& cb,
+                      uint32_t** fe, std::vector<std::array<void*, 6>>& tabs) {
+        *d_clips = c.take<BatchClip>(n);
+        cb.assign(n, ClipBufs{});
+        for (int i = 0; i < n; ++i) {
+            const size_t npx = static_cast<size_t>(clips[i].H) * clips[i].W;
+            cb[i].rp = c.take<uint32_t>(static_cast<size_t>(clips[i].N) * npx * fb::rowpatch_words(clips[i].patch));
+            cb[i].sty = c.take<uint32_t>(static_cast<size_t>(clips[i].N) * npx);
+        }
+        size_t max_fe = 1;
+        for (const HostChunk& ch : chunks) max_fe = std::max(max_fe, ch.fe_elems);
+        for (int q = 0; q < 4; ++q) fe[q] = c.take<uint32_t>(max_fe);
+        tabs.assign(chunks.size(), {});
+        for (size_t ci = 0; ci < chunks.size(); ++ci) {
+            const HostChunk& ch = chunks[ci];
+            size_t max_items = 0;  // the 32x4 variant has the most tiles
+            for (const BatchPair& bp : ch.pairs) max_items += tiles_of(clips[bp.clip].H, clips[bp.clip].W, 4);
+            size_t job_items = 0;
+            for (const BatchJob& j : ch.jobs) job_items += tiles_of(clips[j.clip].H, clips[j.clip].W, 8);
+            tabs[ci][0] = c.take<BatchPair>(std::max<size_t>(ch.pairs.size(), 1));
+            tabs[ci][1] = c.take<int32_t>(std::max<size_t>(max_items, 1));
+            tabs[ci][2] = c.take<int32_t>(std::max<size_t>(max_items, 1));
+            tabs[ci][3] = c.take<BatchJob>(std::max<size_t>(ch.jobs.size(), 1));
+            tabs[ci][4] = c.take<int32_t>(std::max<size_t>(job_items, 1));
+            tabs[ci][5] = c.take<int32_t>(std::max<size_t>(job_items, 1));
+        }
+    };
+    BatchClip* d_clips = nullptr;
+    std::vector<ClipBufs> cb;
+    uint32_t* fe[4] = {};
+    std::vector<std::array<void*, 6>> tabs;
+    layout(cv, &d_clips, cb, fe, tabs);
+    be->bytes = align_up(cv.off, 1 << 20);
+    cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&be->dev), be->bytes);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        be->dev = nullptr;
+        return fail(ctx, FB_ERR_OOM, "batch scratch of %zu bytes: %s", be->bytes, cudaGetErrorString(e));
+    }
+    Carver real(be->dev);
+    layout(real, &d_clips, cb, fe, tabs);
+
+    // ---- static tables ----
+    std::vector<BatchClip> hclips(n);
+    for (int i = 0; i < n; ++i) {
+        const int r0 = p->r0 > 0 ? p->r0 : std::max(clips[i].H, clips[i].W);
+        hclips[i] = BatchClip{clips[i].H, clips[i].W, clips[i].N, r0, cb[i].rp, cb[i].sty, clips[i].out};
+    }
+    FB_CUDA(ctx, cudaMemcpy(d_clips, hclips.data(), sizeof(BatchClip) * n, cudaMemcpyHostToDevice));
+    std::vector<int32_t> m0, m1;
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        const HostChunk& ch = chunks[ci];
+        if (!ch.pairs.empty())
+            FB_CUDA(ctx, cudaMemcpy(tabs[ci][0], ch.pairs.data(), sizeof(BatchPair) * ch.pairs.size(),
+                                    cudaMemcpyHostToDevice));
+        FB_CUDA(ctx, cudaMemcpy(tabs[ci][3], ch.jobs.data(), sizeof(BatchJob) * ch.jobs.size(),
+                                cudaMemcpyHostToDevice));
+        job_maps(ch, clips, m0, m1);
+        FB_CUDA(ctx, cudaMemcpy(tabs[ci][4], m0.data(), sizeof(int32_t) * m0.size(), cudaMemcpyHostToDevice));
+        FB_CUDA(ctx, cudaMemcpy(tabs[ci][5], m1.data(), sizeof(int32_t) * m1.size(), cudaMemcpyHostToDevice));
+    }
+
+    // ---- the launches of one submission ----
+    std::vector<std::function<cudaError_t(cudaStream_t)>> prep;
+    for (int i = 0; i < n; ++i) {
+        const fb_clip_desc d = clips[i];
+        const ClipBufs b = cb[i];
+        be->steps.push_back([d, b](cudaStream_t s) {
+            return fb::launch_prep_guides(d.patch, d.guides, d.N, d.H, d.W, b.rp, s);
+        });
+        be->step_kind.push_back(FB_K_PREP);
+        be->steps.push_back([d, b](cudaStream_t s) {
+            return fb::launch_style_rgbx(d.styles, static_cast<size_t>(d.N) * d.H * d.W, b.sty, s);
+        });
+        be->step_kind.push_back(FB_K_STYLE);
+    }
+    // Tile variant per patch size: forced, tuned earlier in this context, or tuned now on
+    // the first iteration of the size's first chunk.
+    int variant_of[10];
+    for (int k = 0; k < 10; ++k) variant_of[k] = forced_variant(flags) >= 0 ? forced_variant(flags) : ctx->tuned_variant[k];
+    bool prepped = false;
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        const HostChunk& ch = chunks[ci];
+        if (variant_of[ch.k] >= 0 || ch.pairs.empty()) continue;
+        if (!prepped) {
+            for (size_t q = 0; q < 2 * static_cast<size_t>(n); ++q) FB_CUDA(ctx, be->steps[q](st));
+            prepped = true;
+        }
+        const BatchPair* d_pairs = static_cast<const BatchPair*>(tabs[ci][0]);
+        int32_t* d_ip = static_cast<int32_t*>(tabs[ci][1]);
+        int32_t* d_it = static_cast<int32_t*>(tabs[ci][2]);
+        float best = 0.f;
+        int best_v = 0;
+        cudaEvent_t a = nullptr, b = nullptr;
+        FB_CUDA(ctx, cudaEventCreate(&a));
+        FB_CUDA(ctx, cudaEventCreate(&b));
+        for (int v = 0; v < fb::kBatchVariants; ++v) {
+            item_maps(ch, clips, fb::batch_variant_tile_h(v), m0, m1);
+            FB_CUDA(ctx, cudaMemcpyAsync(d_ip, m0.data(), sizeof(int32_t) * m0.size(), cudaMemcpyHostToDevice, st));
+            FB_CUDA(ctx, cudaMemcpyAsync(d_it, m1.data(), sizeof(int32_t) * m1.size(), cudaMemcpyHostToDevice, st));
+            const int grid = sms * fb::batch_iter_blocks_per_sm(ch.k, v);
+            FB_CUDA(ctx, fb::launch_batch_init(ch.k, v, d_pairs, d_clips, d_ip, d_it, static_cast<int>(m0.size()),
+                                               p->seed, fe[0], fe[1], grid, st));
+            FB_CUDA(ctx, cudaEventRecord(a, st));
+            FB_CUDA(ctx, fb::launch_batch_iter(ch.k, v, d_pairs, d_clips, d_ip, d_it, static_cast<int>(m0.size()),
+                                               p->seed, 0, fe[0], fe[1], fe[2], fe[3], grid, st));
+            FB_CUDA(ctx, cudaEventRecord(b, st));
+            FB_CUDA(ctx, cudaEventSynchronize(b));
+            float ms = 0.f;
+            FB_CUDA(ctx, cudaEventElapsedTime(&ms, a, b));
+            ctx->launches += 2;
+            if (v == 0 || ms < best) {
+                best = ms;
+                best_v = v;
+            }
+        }
+        cudaEventDestroy(a);
+        cudaEventDestroy(b);
+        variant_of[ch.k] = best_v;
+        if (forced_variant(flags) < 0) ctx->tuned_variant[ch.k] = best_v;
+    }
+    for (size_t ci = 0; ci < chunks.size(); ++ci) {
+        const HostChunk& ch = chunks[ci];
+        const int v = variant_of[ch.k] >= 0 ? variant_of[ch.k] : 0;
+        item_maps(ch, clips, fb::batch_variant_tile_h(v), m0, m1);
+        if (!m0.empty()) {
+            FB_CUDA(ctx, cudaMemcpyAsync(tabs[ci][1], m0.data(), sizeof(int32_t) * m0.size(), cudaMemcpyHostToDevice, st));
+            FB_CUDA(ctx, cudaMemcpyAsync(tabs[ci][2], m1.data(), sizeof(int32_t) * m1.size(), cudaMemcpyHostToDevice, st));
+        }
+        FB_CUDA(ctx, cudaStreamSynchronize(st));  // host vectors are reused
+        const int n_items = static_cast<int>(m0.size());
+        size_t job_items = 0;
+        for (const BatchJob& j : ch.jobs) job_items += tiles_of(clips[j.clip].H, clips[j.clip].W, 8);
+        const int k = ch.k;
+        const uint64_t seed = p->seed;
+        const int iters = p->iters;
+        const int grid = sms * fb::batch_iter_blocks_per_sm(k, v);
+        const int cgrid = sms * 8;
+        const BatchPair* d_pairs = static_cast<const BatchPair*>(tabs[ci][0]);
+        const int32_t* d_ip = static_cast<const int32_t*>(tabs[ci][1]);
+        const int32_t* d_it = static_cast<const int32_t*>(tabs[ci][2]);
+        const BatchJob* d_jobs = static_cast<const BatchJob*>(tabs[ci][3]);
+        const int32_t* d_ij = static_cast<const int32_t*>(tabs[ci][4]);
+        const int32_t* d_ijt = static_cast<const int32_t*>(tabs[ci][5]);
+        uint32_t *Fc = fe[0], *Ec = fe[1], *Fo = fe[2], *Eo = fe[3];
+        if (n_items > 0) {
+            be->steps.push_back([=](cudaStream_t s) {
+                return fb::launch_batch_init(k, v, d_pairs, d_clips, d_ip, d_it, n_items, seed, Fc, Ec, grid, s);
+            });
+            be->step_kind.push_back(FB_K_INIT);
+            for (int it = 0; it < iters; ++it) {
+                uint32_t *a = Fc, *ea = Ec, *b = Fo, *eb = Eo;
+                be->steps.push_back([=](cudaStream_t s) {
+                    return fb::launch_batch_iter(k, v, d_pairs, d_clips, d_ip, d_it, n_items, seed, it, a, ea, b, eb, grid, s);
+                });
+                be->step_kind.push_back(FB_K_ITER);
+                std::swap(Fc, Fo);
+                std::swap(Ec, Eo);
+            }
+        }
+        const uint32_t* Ffinal = Fc;
+        const int jn = static_cast<int>(job_items);
+        be->steps.push_back([=](cudaStream_t s) {
+            return fb::launch_batch_combine(k, d_jobs, d_pairs, d_clips, d_ij, d_ijt, jn, Ffinal, cgrid, s);
+        });
+        be->step_kind.push_back(FB_K_COMBINE);
+    }
+    be->launches_per_run = be->steps.size();
+
+    if (!(flags & FB_BATCH_NO_GRAPH)) {
+        // Capture on a private stream (the legacy default stream cannot be captured);
+        // nothing runs during capture.  The graph is launched on the caller's stream.
+        cudaStream_t cap = nullptr;
+        FB_CUDA(ctx, cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+        cudaGraph_t g = nullptr;
+        cudaError_t be_ = cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal);
+        if (be_ != cudaSuccess) {
+            cudaStreamDestroy(cap);
+            return fail(ctx, FB_ERR_CUDA, "cudaStreamBeginCapture: %s", cudaGetErrorString(be_));
+        }
+        cudaError_t le = cudaSuccess;
+        for (auto& f : be->steps)
+            if (le == cudaSuccess) le = f(cap);
+        cudaError_t ce = cudaStreamEndCapture(cap, &g);
+        cudaStreamDestroy(cap);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (g) cudaGraphDestroy(g);
+            cudaGetLastError();
+            return fail(ctx, FB_ERR_CUDA, "graph capture of the batch failed: %s",
+                        cudaGetErrorString(le != cudaSuccess ? le : ce));
+        }
+        e = cudaGraphInstantiate(&be->exec, g, 0);
+        cudaGraphDestroy(g);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            be->exec = nullptr;
+            return fail(ctx, FB_ERR_CUDA, "graph instantiation failed: %s", cudaGetErrorString(e));
+        }
+    }
+    return FB_OK;
+}
+
+}  // namespace
+
+extern "C" int fb_batch_plan(const fb_clip_desc* clips, int n_clips, const fb_params* p,
+                             size_t budget_bytes, uint64_t* n_pairs, uint64_t* n_items,
+                             int* n_chunks) {
+    int rc = check_clips(nullptr, clips, n_clips, p, false);
+    if (rc) return rc;
+    std::vector<HostChunk> chunks;
+    rc = plan_chunks(nullptr, clips, n_clips, budget_bytes ? budget_bytes : kPairBudgetBytes, chunks);
+    if (rc) return rc;
+    uint64_t np = 0, ni = 0;
+    for (const HostChunk& ch : chunks) {
+        np += ch.pairs.size();
+        for (const BatchPair& bp : ch.pairs) ni += tiles_of(clips[bp.clip].H, clips[bp.clip].W, 8);
+    }
+    if (n_pairs) *n_pairs = np;
+    if (n_items) *n_items = ni;
+    if (n_chunks) *n_chunks = static_cast<int>(chunks.size());
+    return FB_OK;
+}
+
+extern "C" int fb_ctx_set_pair_budget(fb_ctx* ctx, size_t bytes) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    if (bytes != 0 && bytes < (size_t(1) << 20))
+        return fail(ctx, FB_ERR_ARG, "pair budget below 1 MiB");
+    ctx->pair_budget = bytes;
+    return FB_OK;
+}
+
+extern "C" int fb_ctx_batch_variant(const fb_ctx* ctx, int patch) {
+    if (!ctx || patch < 0 || patch > 9) return -1;
+    return ctx->tuned_variant[patch];
+}
+
+extern "C" int fb_blend_batch(fb_ctx* ctx, const fb_clip_desc* clips, int n_clips,
+                              const fb_params* p, uint32_t flags, void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->err.clear();
+    if (flags & ~(FB_BATCH_NO_GRAPH | 0xFF00u)) return fail(ctx, FB_ERR_ARG, "unknown flags 0x%x", flags);
+    if (forced_variant(flags) >= fb::kBatchVariants)
+        return fail(ctx, FB_ERR_ARG, "tile variant %d outside [0, %d)", forced_variant(flags), fb::kBatchVariants);
+    DeviceGuard dg(ctx->device);
+    int rc = check_clips(ctx, clips, n_clips, p, true);
+    if (rc) return rc;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const std::vector<uint8_t> key = manifest_key(clips, n_clips, p, flags);
+    fb_ctx::BatchEntry* be = nullptr;
+    for (size_t i = 0; i < ctx->batch_cache.size(); ++i) {
+        if (ctx->batch_cache[i]->key == key) {
+            be = ctx->batch_cache[i];
+            ctx->batch_cache.erase(ctx->batch_cache.begin() + i);
+            ctx->batch_cache.push_back(be);
+            break;
+        }
+    }
+    if (!be) {
+        FB_CUDA(ctx, cudaStreamSynchronize(st));
+        while (ctx->batch_cache.size() >= 2) {
+            drop_entry(ctx->batch_cache.front());
+            ctx->batch_cache.erase(ctx->batch_cache.begin());
+        }
+        be = new fb_ctx::BatchEntry();
+        be->key = key;
+        rc = build_entry(ctx, clips, n_clips, p, flags, st, be);
+        if (rc) {
+            drop_entry(be);
+            return rc;
+        }
+        ctx->batch_cache.push_back(be);
+    }
+    if (be->exec) {
+        FB_CUDA(ctx, cudaGraphLaunch(be->exec, st));
+        ctx->launches += be->launches_per_run;
+    } else {
+        for (size_t i = 0; i < be->steps.size(); ++i) {
+            const int kind = be->step_kind[i];
+            FB_LAUNCH(ctx, st, kind, be->steps[i](st));
+        }
+    }
+    return FB_OK;
+}
+
 extern "C" {
 
 int fb_ctx_create(fb_ctx** out, int device) {
@@ -457,6 +925,11 @@ int fb_ctx_destroy(fb_ctx* ctx) {
     if (ctx->upload_done) cudaEventDestroy(ctx->upload_done);
     if (ctx->dev_status) cudaFree(ctx->dev_status);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (fb_ctx::BatchEntry* be : ctx->batch_cache) {
+        if (be->exec) cudaGraphExecDestroy(be->exec);
+        if (be->dev) cudaFree(be->dev);
+        delete be;
+    }
     delete ctx;
     return FB_OK;
 }

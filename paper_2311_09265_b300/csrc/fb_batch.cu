@@ -1,0 +1,234 @@
+// fb_batch.cu -- persistent kernels of the batched submission (fb_blend_batch): many
+// clips of uneven size, window and patch in one pass.  Every pair of every clip is cut
+// into 32-column tiles; a kernel of SMs x resident-blocks CTAs walks the flattened
+// work list (item -> pair, tile), so clips of different shapes share one launch per
+// Jacobi iteration.  The per-pixel work is the same code as the per-call kernels
+// (fb_device.cuh), so results are identical to fb_blend_window whatever tile shape the
+// autotuner picks.
+#include <type_traits>
+
+#include "fb_device.cuh"
+
+namespace fb {
+namespace {
+
+using namespace dev;
+
+// Variant v: tile height and the resident 32 x TH-thread blocks per SM the iteration
+// kernel is compiled for (the same ~1280 threads per SM for k = 5).
+template <int V>
+struct Variant;
+template <> struct Variant<0> { static constexpr int TH = 8, MINB = 5; };   // 32x8,  5 blocks
+template <> struct Variant<1> { static constexpr int TH = 4, MINB = 10; };  // 32x4, 10 blocks
+template <> struct Variant<2> { static constexpr int TH = 16, MINB = 2; };  // 32x16, 2 blocks
+template <> struct Variant<3> { static constexpr int TH = 8, MINB = 4; };   // 32x8,  4 blocks
+
+// Larger patches keep more target words in registers: scale the block count down.
+template <int K, int V>
+struct BatchOcc {
+    static constexpr int base = Variant<V>::MINB;
+    static constexpr int value = K <= 5 ? base : K <= 7 ? (base * 3 + 4) / 5 : (base * 2 + 4) / 5;
+};
+
+template <int K, int V>
+__global__ void __launch_bounds__(32 * Variant<V>::TH, BatchOcc<K, V>::value)
+    batch_iter_kernel(const BatchPair* __restrict__ pairs, const BatchClip* __restrict__ clips,
+                      const int32_t* __restrict__ item_pair, const int32_t* __restrict__ item_tile,
+                      int n_items, uint32_t key0, uint32_t key1, uint32_t ctr_word,
+                      const uint32_t* __restrict__ Fp, const uint32_t* __restrict__ Ep,
+                      uint32_t* __restrict__ Fn, uint32_t* __restrict__ En) {
+    using G = Geo<K>;
+    constexpr int TH = Variant<V>::TH;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const BatchPair bp = pairs[item_pair[item]];
+        const BatchClip cl = clips[bp.clip];
+        const int tiles_x = (cl.W + 31) / 32;
+        const int tile = item_tile[item];
+        const int r = (tile / tiles_x) * TH + static_cast<int>(threadIdx.y);
+        const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
+        if (r >= cl.H || c >= cl.W) continue;
+        const size_t npx = static_cast<size_t>(cl.H) * cl.W;
+        iterate_pixel<K>(cl.rp + static_cast<size_t>(bp.src) * npx * G::RPW,
+                         cl.rp + static_cast<size_t>(bp.tgt) * npx * G::RPW, cl.H, cl.W, r, c,
+                         bp.tag, cl.r0, key0, key1, ctr_word, Fp + bp.fe_off, Ep + bp.fe_off,
+                         Fn + bp.fe_off, En + bp.fe_off);
+    }
+}
+
+template <int K, int V>
+__global__ void __launch_bounds__(32 * Variant<V>::TH)
+    batch_init_kernel(const BatchPair* __restrict__ pairs, const BatchClip* __restrict__ clips,
+                      const int32_t* __restrict__ item_pair, const int32_t* __restrict__ item_tile,
+                      int n_items, uint32_t key0, uint32_t key1, uint32_t* __restrict__ F,
+                      uint32_t* __restrict__ E) {
+    using G = Geo<K>;
+    constexpr int TH = Variant<V>::TH;
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const BatchPair bp = pairs[item_pair[item]];
+        const BatchClip cl = clips[bp.clip];
+        const int tiles_x = (cl.W + 31) / 32;
+        const int tile = item_tile[item];
+        const int r = (tile / tiles_x) * TH + static_cast<int>(threadIdx.y);
+        const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
+        if (r >= cl.H || c >= cl.W) continue;
+        const size_t npx = static_cast<size_t>(cl.H) * cl.W;
+        init_pixel<K>(cl.rp + static_cast<size_t>(bp.src) * npx * G::RPW,
+                      cl.rp + static_cast<size_t>(bp.tgt) * npx * G::RPW, cl.H, cl.W, r, c, bp.tag,
+                      0, nullptr, 0, 0, nullptr, key0, key1, 0u, F + bp.fe_off, E + bp.fe_off);
+    }
+}
+
+// Alg. 2 + Eq. 2 for the output frames of a chunk: items are (job, 32x8 tile).
+template <int K>
+__global__ void __launch_bounds__(256)
+    batch_combine_kernel(const BatchJob* __restrict__ jobs, const BatchPair* __restrict__ pairs,
+                         const BatchClip* __restrict__ clips, const int32_t* __restrict__ item_job,
+                         const int32_t* __restrict__ item_tile, int n_items,
+                         const uint32_t* __restrict__ F) {
+    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+        const BatchJob job = jobs[item_job[item]];
+        const BatchClip cl = clips[job.clip];
+        const int tiles_x = (cl.W + 31) / 32;
+        const int tile = item_tile[item];
+        const int r = (tile / tiles_x) * 8 + static_cast<int>(threadIdx.y);
+        const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
+        if (r >= cl.H || c >= cl.W) continue;
+        const size_t npx = static_cast<size_t>(cl.H) * cl.W;
+        const size_t x = static_cast<size_t>(r) * cl.W + c;
+        const uint32_t s = __ldg(cl.styles + static_cast<size_t>(job.frame) * npx + x);
+        const uint32_t w = static_cast<uint32_t>(K * K);
+        uint32_t a0 = w * (s & 0xFFu), a1 = w * ((s >> 8) & 0xFFu), a2 = w * ((s >> 16) & 0xFFu);
+        for (int p = 0; p < job.n_pairs; ++p) {
+            const BatchPair bp = pairs[job.first_pair + p];
+            uint32_t v0, v1, v2;
+            remap_votes<K>(F + bp.fe_off, cl.styles + static_cast<size_t>(bp.style) * npx, cl.H,
+                           cl.W, r, c, v0, v1, v2);
+            a0 += bp.weight * v0;
+            a1 += bp.weight * v1;
+            a2 += bp.weight * v2;
+        }
+        write_output(cl.out + (static_cast<size_t>(job.frame) * npx + x) * 3, a0, a1, a2, job.den);
+    }
+}
+
+template <int K, int V>
+cudaError_t launch_iter_kv(const BatchPair* pairs, const BatchClip* clips, const int32_t* ip,
+                           const int32_t* it_, int n, uint32_t k0, uint32_t k1, uint32_t cw,
+                           const uint32_t* Fp, const uint32_t* Ep, uint32_t* Fn, uint32_t* En,
+                           int grid, cudaStream_t st) {
+    batch_iter_kernel<K, V><<<grid, dim3(32, Variant<V>::TH), 0, st>>>(pairs, clips, ip, it_, n, k0,
+                                                                       k1, cw, Fp, Ep, Fn, En);
+    return cudaGetLastError();
+}
+
+template <int K, int V>
+cudaError_t launch_init_kv(const BatchPair* pairs, const BatchClip* clips, const int32_t* ip,
+                           const int32_t* it_, int n, uint32_t k0, uint32_t k1, uint32_t* F,
+                           uint32_t* E, int grid, cudaStream_t st) {
+    batch_init_kernel<K, V><<<grid, dim3(32, Variant<V>::TH), 0, st>>>(pairs, clips, ip, it_, n, k0,
+                                                                       k1, F, E);
+    return cudaGetLastError();
+}
+
+template <int K>
+int occupancy_k(int v) {
+    int nb = 0;
+    switch (v) {
+        case 0: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_iter_kernel<K, 0>, 32 * Variant<0>::TH, 0); break;
+        case 1: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_iter_kernel<K, 1>, 32 * Variant<1>::TH, 0); break;
+        case 2: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_iter_kernel<K, 2>, 32 * Variant<2>::TH, 0); break;
+        default: cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_iter_kernel<K, 3>, 32 * Variant<3>::TH, 0); break;
+    }
+    cudaGetLastError();
+    return nb > 0 ? nb : 1;
+}
+
+#define FB_BATCH_DISPATCH(k, v, CALL)                                                     \
+    switch ((k) * 10 + (v)) {                                                              \
+        case 30: { constexpr int KK = 3, VV = 0; return CALL; }                            \
+        case 31: { constexpr int KK = 3, VV = 1; return CALL; }                            \
+        case 32: { constexpr int KK = 3, VV = 2; return CALL; }                            \
+        case 33: { constexpr int KK = 3, VV = 3; return CALL; }                            \
+        case 50: { constexpr int KK = 5, VV = 0; return CALL; }                            \
+        case 51: { constexpr int KK = 5, VV = 1; return CALL; }                            \
+        case 52: { constexpr int KK = 5, VV = 2; return CALL; }                            \
+        case 53: { constexpr int KK = 5, VV = 3; return CALL; }                            \
+        case 70: { constexpr int KK = 7, VV = 0; return CALL; }                            \
+        case 71: { constexpr int KK = 7, VV = 1; return CALL; }                            \
+        case 72: { constexpr int KK = 7, VV = 2; return CALL; }                            \
+        case 73: { constexpr int KK = 7, VV = 3; return CALL; }                            \
+        case 90: { constexpr int KK = 9, VV = 0; return CALL; }                            \
+        case 91: { constexpr int KK = 9, VV = 1; return CALL; }                            \
+        case 92: { constexpr int KK = 9, VV = 2; return CALL; }                            \
+        case 93: { constexpr int KK = 9, VV = 3; return CALL; }                            \
+        default: return cudaErrorInvalidValue;                                             \
+    }
+
+}  // namespace
+
+const char* batch_variant_name(int v) {
+    switch (v) {
+        case 0: return "tile 32x8, 5 blocks/SM";
+        case 1: return "tile 32x4, 10 blocks/SM";
+        case 2: return "tile 32x16, 2 blocks/SM";
+        case 3: return "tile 32x8, 4 blocks/SM";
+        default: return "?";
+    }
+}
+
+int batch_variant_tile_h(int variant) {
+    switch (variant) {
+        case 1: return Variant<1>::TH;
+        case 2: return Variant<2>::TH;
+        case 3: return Variant<3>::TH;
+        default: return Variant<0>::TH;
+    }
+}
+
+int batch_iter_blocks_per_sm(int k, int variant) {
+    switch (k) {
+        case 3: return occupancy_k<3>(variant);
+        case 5: return occupancy_k<5>(variant);
+        case 7: return occupancy_k<7>(variant);
+        case 9: return occupancy_k<9>(variant);
+        default: return 1;
+    }
+}
+
+cudaError_t launch_batch_iter(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
+                              const int32_t* item_pair, const int32_t* item_tile, int n_items,
+                              uint64_t seed, int it, const uint32_t* Fp, const uint32_t* Ep,
+                              uint32_t* Fn, uint32_t* En, int grid, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    const uint32_t cw = static_cast<uint32_t>(it + 1) << 8;  // level 0
+    FB_BATCH_DISPATCH(k, variant, (launch_iter_kv<KK, VV>(pairs, clips, item_pair, item_tile, n_items,
+                                                         k0, k1, cw, Fp, Ep, Fn, En, grid, st)));
+}
+
+cudaError_t launch_batch_init(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
+                              const int32_t* item_pair, const int32_t* item_tile, int n_items,
+                              uint64_t seed, uint32_t* F, uint32_t* E, int grid, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+    FB_BATCH_DISPATCH(k, variant, (launch_init_kv<KK, VV>(pairs, clips, item_pair, item_tile, n_items,
+                                                         k0, k1, F, E, grid, st)));
+}
+
+cudaError_t launch_batch_combine(int k, const BatchJob* jobs, const BatchPair* pairs,
+                                 const BatchClip* clips, const int32_t* item_job,
+                                 const int32_t* item_tile, int n_items, const uint32_t* F,
+                                 int grid, cudaStream_t st) {
+    if (n_items <= 0) return cudaSuccess;
+    const dim3 block(32, 8);
+    switch (k) {
+        case 3: batch_combine_kernel<3><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, F); break;
+        case 5: batch_combine_kernel<5><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, F); break;
+        case 7: batch_combine_kernel<7><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, F); break;
+        case 9: batch_combine_kernel<9><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, F); break;
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+}  // namespace fb

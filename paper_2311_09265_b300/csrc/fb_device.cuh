@@ -1,0 +1,257 @@
+// fb_device.cuh -- per-pixel device code of the FastBlend hot path, shared by the
+// per-call kernels (fb_kernels.cu) and the batched persistent kernels (fb_batch.cu).
+#pragma once
+
+#include <cstdint>
+
+#include "fb_internal.h"
+
+namespace fb {
+namespace dev {
+
+__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
+__device__ __forceinline__ uint32_t pack_rc(int r, int c) {
+    return (static_cast<uint32_t>(r) << 16) | static_cast<uint32_t>(c);
+}
+__device__ __forceinline__ int row_of(uint32_t f) { return static_cast<int>(f >> 16); }
+__device__ __forceinline__ int col_of(uint32_t f) { return static_cast<int>(f & 0xFFFFu); }
+
+// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
+// multiplies whose halves are recombined with the round key; the key advances by
+// the two Weyl constants between rounds.
+__device__ __forceinline__ uint4 philox4x32_10(uint4 v, uint32_t k0, uint32_t k1) {
+#pragma unroll
+    for (int round = 0; round < 10; ++round) {
+        if (round) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo_a = 0xD2511F53u * v.x, hi_a = __umulhi(0xD2511F53u, v.x);
+        const uint32_t lo_b = 0xCD9E8D57u * v.z, hi_b = __umulhi(0xCD9E8D57u, v.z);
+        v = make_uint4(hi_b ^ v.y ^ k0, lo_b, hi_a ^ v.w ^ k1, lo_a);
+    }
+    return v;
+}
+
+template <int K>
+struct Geo {
+    static constexpr int P = K / 2;
+    static constexpr int NW = (3 * K + 3) / 4;    // 32-bit words holding one 3K-byte patch row
+    static constexpr int RPW = (NW + 3) / 4 * 4;  // row-patch slot stride: 16-byte aligned
+};
+
+template <int K>
+__device__ __forceinline__ void load_row(const uint32_t* __restrict__ p,
+                                         uint32_t (&out)[Geo<K>::NW]) {
+    constexpr int NW = Geo<K>::NW;
+    const uint4* q = reinterpret_cast<const uint4*>(p);
+#pragma unroll
+    for (int v = 0; v < NW / 4; ++v) {
+        const uint4 t = __ldg(q + v);
+        out[4 * v] = t.x;
+        out[4 * v + 1] = t.y;
+        out[4 * v + 2] = t.z;
+        out[4 * v + 3] = t.w;
+    }
+    constexpr int rem = NW % 4;
+    if constexpr (rem == 2) {
+        const uint2 t = __ldg(reinterpret_cast<const uint2*>(p + NW - 2));
+        out[NW - 2] = t.x;
+        out[NW - 1] = t.y;
+    } else if constexpr (rem == 3) {
+        const uint4 t = __ldg(q + NW / 4);
+        out[NW - 3] = t.x;
+        out[NW - 2] = t.y;
+        out[NW - 1] = t.z;
+    } else if constexpr (rem == 1) {
+        out[NW - 1] = __ldg(p + NW - 1);
+    }
+}
+
+template <int K>
+struct TargetPatch {
+    uint32_t w[K][Geo<K>::NW];  // the k rows of the target patch
+    uint32_t row_e[K];          // sum of squares of each row
+};
+
+template <int K>
+__device__ __forceinline__ void load_target(const uint32_t* __restrict__ rpt, int H, int W,
+                                            int r, int c, TargetPatch<K>& t) {
+    using G = Geo<K>;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+        const int rr = clampi(r - G::P + a, 0, H - 1);
+        load_row<K>(rpt + (static_cast<size_t>(rr) * W + c) * G::RPW, t.w[a]);
+        uint32_t e = 0;
+#pragma unroll
+        for (int w = 0; w < G::NW; ++w) e = __dp4a(t.w[a][w], t.w[a][w], e);
+        t.row_e[a] = e;
+    }
+}
+
+// Eq. 1 error of source patch u = (ur, uc) against target t, accumulated row by row as
+// the exact non-negative terms |s_a|^2 + |t_a|^2 - 2 <s_a, t_a> (dp4a, four byte pairs
+// per instruction).  Once the running sum reaches `bound` the candidate cannot be
+// strictly better than the incumbent and its remaining rows are not loaded (returns
+// false).  Otherwise returns true with the full error in *e.
+template <int K>
+__device__ __forceinline__ bool patch_error_below(const uint32_t* __restrict__ rps, int H, int W,
+                                                  int ur, int uc, const TargetPatch<K>& t,
+                                                  uint32_t bound, uint32_t* e) {
+    using G = Geo<K>;
+    uint32_t acc = 0;
+#pragma unroll
+    for (int a = 0; a < K; ++a) {
+        const int rr = clampi(ur - G::P + a, 0, H - 1);
+        uint32_t s[G::NW];
+        load_row<K>(rps + (static_cast<size_t>(rr) * W + uc) * G::RPW, s);
+        uint32_t dot = 0, ss = 0;
+#pragma unroll
+        for (int w = 0; w < G::NW; ++w) {
+            dot = __dp4a(s[w], t.w[a][w], dot);
+            ss = __dp4a(s[w], s[w], ss);
+        }
+        acc += ss + t.row_e[a] - 2u * dot;
+        if (acc >= bound) return false;
+    }
+    *e = acc;
+    return true;
+}
+
+// One Jacobi iteration of Alg. 1 (Sec. 3.2 parallel update) for target pixel (r, c) of
+// one pair: reads the pair's snapshot (Fp, Ep), writes (Fn, En).  Propagation from the
+// four neighbours in the order (-1,0), (1,0), (0,-1), (0,1), then random search around
+// the running best with radius r0 >> t; strict improvement only.  A candidate equal to
+// the running best is skipped: its error equals the incumbent's, so it could not win.
+template <int K>
+__device__ __forceinline__ void iterate_pixel(const uint32_t* __restrict__ rps,
+                                              const uint32_t* __restrict__ rpt, int H, int W,
+                                              int r, int c, uint32_t tag, int r0, uint32_t key0,
+                                              uint32_t key1, uint32_t ctr_word,
+                                              const uint32_t* __restrict__ Fpp,
+                                              const uint32_t* __restrict__ Epp,
+                                              uint32_t* __restrict__ Fnp,
+                                              uint32_t* __restrict__ Enp) {
+    const size_t x = static_cast<size_t>(r) * W + c;
+    TargetPatch<K> t;
+    load_target<K>(rpt, H, W, r, c, t);
+
+    uint32_t bf = Fpp[x];
+    uint32_t be = Epp[x];
+
+    auto consider = [&](int cr, int cc) {
+        const uint32_t f = pack_rc(cr, cc);
+        if (f == bf) return;
+        uint32_t e;
+        if (patch_error_below<K>(rps, H, W, cr, cc, t, be, &e)) {
+            be = e;
+            bf = f;
+        }
+    };
+
+    // Propagation: F'(x) = F(x + d) - d.
+    if (r > 0) {
+        const uint32_t f = Fpp[x - W];
+        consider(min(row_of(f) + 1, H - 1), col_of(f));
+    }
+    if (r < H - 1) {
+        const uint32_t f = Fpp[x + W];
+        consider(max(row_of(f) - 1, 0), col_of(f));
+    }
+    if (c > 0) {
+        const uint32_t f = Fpp[x - 1];
+        consider(row_of(f), min(col_of(f) + 1, W - 1));
+    }
+    if (c < W - 1) {
+        const uint32_t f = Fpp[x + 1];
+        consider(row_of(f), max(col_of(f) - 1, 0));
+    }
+
+    // Random search: F'(x) = F(x) + U[-r, r]^2, r = r0 >> t, t = 0, 1, ... while r >= 1.
+    uint4 u = make_uint4(0u, 0u, 0u, 0u);
+    for (int tt = 0; (r0 >> tt) >= 1; ++tt) {
+        const int rad = r0 >> tt;
+        if ((tt & 1) == 0)
+            u = philox4x32_10(make_uint4(static_cast<uint32_t>(x), tag,
+                                         ctr_word | static_cast<uint32_t>(tt >> 1), 0u),
+                              key0, key1);
+        const uint32_t span = static_cast<uint32_t>(2 * rad + 1);
+        const int dr = static_cast<int>(__umulhi((tt & 1) ? u.z : u.x, span)) - rad;
+        const int dc = static_cast<int>(__umulhi((tt & 1) ? u.w : u.y, span)) - rad;
+        consider(clampi(row_of(bf) + dr, 0, H - 1), clampi(col_of(bf) + dc, 0, W - 1));
+    }
+
+    Fnp[x] = bf;
+    Enp[x] = be;
+}
+
+// Initial field of Alg. 1 for target pixel (r, c) of one pair and its Eq. 1 error.
+// mode 0: Philox random match; 1: the coarse level's match, doubled, plus the pixel's
+// parity; 2: the caller's field (clamped into the image).
+template <int K>
+__device__ __forceinline__ void init_pixel(const uint32_t* __restrict__ rps,
+                                           const uint32_t* __restrict__ rpt, int H, int W, int r,
+                                           int c, uint32_t tag, int mode,
+                                           const uint32_t* __restrict__ coarse_Fp, int Hc, int Wc,
+                                           const int32_t* __restrict__ user_init, uint32_t key0,
+                                           uint32_t key1, uint32_t level_word,
+                                           uint32_t* __restrict__ Fp, uint32_t* __restrict__ Ep) {
+    const size_t x = static_cast<size_t>(r) * W + c;
+    int ur, uc;
+    if (mode == 0) {
+        const uint4 u = philox4x32_10(make_uint4(static_cast<uint32_t>(x), tag, level_word, 0u),
+                                      key0, key1);
+        ur = static_cast<int>(__umulhi(u.x, static_cast<uint32_t>(H)));
+        uc = static_cast<int>(__umulhi(u.y, static_cast<uint32_t>(W)));
+    } else if (mode == 1) {
+        const uint32_t fc = coarse_Fp[static_cast<size_t>(r >> 1) * Wc + (c >> 1)];
+        ur = clampi(2 * row_of(fc) + (r & 1), 0, H - 1);
+        uc = clampi(2 * col_of(fc) + (c & 1), 0, W - 1);
+    } else {
+        ur = clampi(user_init[2 * x], 0, H - 1);
+        uc = clampi(user_init[2 * x + 1], 0, W - 1);
+    }
+    TargetPatch<K> t;
+    load_target<K>(rpt, H, W, r, c, t);
+    uint32_t e = 0;
+    patch_error_below<K>(rps, H, W, ur, uc, t, 0xFFFFFFFFu, &e);
+    Fp[x] = pack_rc(ur, uc);
+    Ep[x] = e;
+}
+
+// Alg. 2 remap of one pair's style through its NNF at output pixel (r, c): the k^2
+// votes S(clamp(F(q^) - (q^ - x))), q^ = clamp(q), summed per channel.
+template <int K>
+__device__ __forceinline__ void remap_votes(const uint32_t* __restrict__ Fq,
+                                            const uint32_t* __restrict__ S, int H, int W, int r,
+                                            int c, uint32_t& v0, uint32_t& v1, uint32_t& v2) {
+    constexpr int P = K / 2;
+    v0 = v1 = v2 = 0;
+#pragma unroll
+    for (int a = -P; a <= P; ++a) {
+        const int qr = clampi(r + a, 0, H - 1);
+#pragma unroll
+        for (int b = -P; b <= P; ++b) {
+            const int qc = clampi(c + b, 0, W - 1);
+            const uint32_t f = __ldg(Fq + static_cast<size_t>(qr) * W + qc);
+            const int sr = clampi(row_of(f) - (qr - r), 0, H - 1);
+            const int sc = clampi(col_of(f) - (qc - c), 0, W - 1);
+            const uint32_t s = __ldg(S + static_cast<size_t>(sr) * W + sc);
+            v0 += s & 0xFFu;
+            v1 += (s >> 8) & 0xFFu;
+            v2 += (s >> 16) & 0xFFu;
+        }
+    }
+}
+
+// Output value of one pixel: num / den per channel with one IEEE division.
+__device__ __forceinline__ void write_output(float* __restrict__ o, uint32_t a0, uint32_t a1,
+                                             uint32_t a2, uint32_t den_u) {
+    const float den = __uint2float_rn(den_u);
+    o[0] = __fdiv_rn(__uint2float_rn(a0), den);
+    o[1] = __fdiv_rn(__uint2float_rn(a1), den);
+    o[2] = __fdiv_rn(__uint2float_rn(a2), den);
+}
+
+}  // namespace dev
+}  // namespace fb

@@ -65,6 +65,47 @@ cudaError_t launch_combine(int k, const JobDesc* jobs, int job0, int n_jobs,
                            const PairDesc* pairs, int pair0, const uint32_t* F,
                            const uint32_t* styles, int H, int W, float* out, cudaStream_t st);
 
+// ---- batched persistent path (fb_batch.cu) --------------------------------------
+// One clip of a batch submission (device table).
+struct BatchClip {
+    int32_t H, W, N, r0;     // r0: first random-search radius for this clip
+    const uint32_t* rp;      // row patches of the clip's N guide frames
+    const uint32_t* styles;  // RGBX styles of the clip's N frames
+    float* out;              // the caller's N x H x W x 3 output
+};
+// One NNF of a chunk: pair (src -> tgt) of clip `clip`, its F/E plane at fe_off.
+struct BatchPair {
+    int32_t clip, src, tgt, style;
+    uint32_t tag, weight;
+    uint64_t fe_off;
+};
+// One output frame of a chunk; its pairs are [first_pair, first_pair + n_pairs).
+struct BatchJob {
+    int32_t clip, frame, first_pair, n_pairs;
+    uint32_t den;
+    int32_t pad[3];
+};
+
+// Tile shapes / occupancies the autotuner chooses among (same results for all).
+constexpr int kBatchVariants = 4;
+const char* batch_variant_name(int v);
+// Work items: item_pair[i] = pair of item i, item_tile[i] = tile index within the pair.
+cudaError_t launch_batch_init(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
+                              const int32_t* item_pair, const int32_t* item_tile, int n_items,
+                              uint64_t seed, uint32_t* F, uint32_t* E, int grid, cudaStream_t st);
+cudaError_t launch_batch_iter(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
+                              const int32_t* item_pair, const int32_t* item_tile, int n_items,
+                              uint64_t seed, int it, const uint32_t* Fp, const uint32_t* Ep,
+                              uint32_t* Fn, uint32_t* En, int grid, cudaStream_t st);
+cudaError_t launch_batch_combine(int k, const BatchJob* jobs, const BatchPair* pairs,
+                                 const BatchClip* clips, const int32_t* item_job,
+                                 const int32_t* item_tile, int n_items, const uint32_t* F,
+                                 int grid, cudaStream_t st);
+// Rows per tile of a variant (tiles are 32 columns wide).
+int batch_variant_tile_h(int variant);
+// Resident blocks per SM of the variant's iteration kernel for patch k (occupancy API).
+int batch_iter_blocks_per_sm(int k, int variant);
+
 // dp4a throughput probe (fb_calib.cu): blocks x 256 threads x iters x chains dp4a.
 constexpr int kDp4aProbeChains = 32;
 cudaError_t launch_dp4a_probe(int blocks, int iters, uint32_t* sink, cudaStream_t st);

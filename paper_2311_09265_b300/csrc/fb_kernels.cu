@@ -13,10 +13,12 @@
 // |s|^2 + |t|^2 - 2 <s, t> with dp4a, which is exactly the clamp-to-edge sum of squared
 // byte differences; a candidate stops loading rows once its running sum reaches the
 // incumbent's error.
-#include "fb_internal.h"
+#include "fb_device.cuh"
 
 namespace fb {
 namespace {
+
+using namespace dev;
 
 #ifndef FB_ITER_MIN_BLOCKS
 #define FB_ITER_MIN_BLOCKS 5  // resident 256-thread blocks per SM the k=5 iteration kernel is built for
@@ -28,37 +30,6 @@ namespace {
 constexpr int TILE_W = 32;
 constexpr int TILE_H = FB_TILE_H;
 constexpr int TILE_THREADS = TILE_W * TILE_H;
-
-__device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
-__device__ __forceinline__ uint32_t pack_rc(int r, int c) {
-    return (static_cast<uint32_t>(r) << 16) | static_cast<uint32_t>(c);
-}
-__device__ __forceinline__ int row_of(uint32_t f) { return static_cast<int>(f >> 16); }
-__device__ __forceinline__ int col_of(uint32_t f) { return static_cast<int>(f & 0xFFFFu); }
-
-// Philox-4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two 32x32->64
-// multiplies whose halves are recombined with the round key; the key advances by
-// the two Weyl constants between rounds.
-__device__ __forceinline__ uint4 philox4x32_10(uint4 v, uint32_t k0, uint32_t k1) {
-#pragma unroll
-    for (int round = 0; round < 10; ++round) {
-        if (round) {
-            k0 += 0x9E3779B9u;
-            k1 += 0xBB67AE85u;
-        }
-        const uint32_t lo_a = 0xD2511F53u * v.x, hi_a = __umulhi(0xD2511F53u, v.x);
-        const uint32_t lo_b = 0xCD9E8D57u * v.z, hi_b = __umulhi(0xCD9E8D57u, v.z);
-        v = make_uint4(hi_b ^ v.y ^ k0, lo_b, hi_a ^ v.w ^ k1, lo_a);
-    }
-    return v;
-}
-
-template <int K>
-struct Geo {
-    static constexpr int P = K / 2;
-    static constexpr int NW = (3 * K + 3) / 4;    // 32-bit words holding one 3K-byte patch row
-    static constexpr int RPW = (NW + 3) / 4 * 4;  // row-patch slot stride: 16-byte aligned
-};
 
 // ---------------------------------------------------------------------------------
 // Guide preparation: "row patches".  Slot (r, c) holds the k pixels
@@ -128,84 +99,9 @@ __global__ void __launch_bounds__(256) style_rgbx_kernel(const uint8_t* __restri
 // ---------------------------------------------------------------------------------
 // Patch distance (Eq. 1)
 // ---------------------------------------------------------------------------------
-template <int K>
-__device__ __forceinline__ void load_row(const uint32_t* __restrict__ p,
-                                         uint32_t (&out)[Geo<K>::NW]) {
-    constexpr int NW = Geo<K>::NW;
-    const uint4* q = reinterpret_cast<const uint4*>(p);
-#pragma unroll
-    for (int v = 0; v < NW / 4; ++v) {
-        const uint4 t = __ldg(q + v);
-        out[4 * v] = t.x;
-        out[4 * v + 1] = t.y;
-        out[4 * v + 2] = t.z;
-        out[4 * v + 3] = t.w;
-    }
-    constexpr int rem = NW % 4;
-    if constexpr (rem == 2) {
-        const uint2 t = __ldg(reinterpret_cast<const uint2*>(p + NW - 2));
-        out[NW - 2] = t.x;
-        out[NW - 1] = t.y;
-    } else if constexpr (rem == 3) {
-        const uint4 t = __ldg(q + NW / 4);
-        out[NW - 3] = t.x;
-        out[NW - 2] = t.y;
-        out[NW - 1] = t.z;
-    } else if constexpr (rem == 1) {
-        out[NW - 1] = __ldg(p + NW - 1);
-    }
-}
-
-template <int K>
-struct TargetPatch {
-    uint32_t w[K][Geo<K>::NW];  // the k rows of the target patch
-    uint32_t row_e[K];          // sum of squares of each row
-};
-
-template <int K>
-__device__ __forceinline__ void load_target(const uint32_t* __restrict__ rpt, int H, int W,
-                                            int r, int c, TargetPatch<K>& t) {
-    using G = Geo<K>;
-#pragma unroll
-    for (int a = 0; a < K; ++a) {
-        const int rr = clampi(r - G::P + a, 0, H - 1);
-        load_row<K>(rpt + (static_cast<size_t>(rr) * W + c) * G::RPW, t.w[a]);
-        uint32_t e = 0;
-#pragma unroll
-        for (int w = 0; w < G::NW; ++w) e = __dp4a(t.w[a][w], t.w[a][w], e);
-        t.row_e[a] = e;
-    }
-}
-
-// Eq. 1 error of source patch u = (ur, uc) against target t, accumulated row by row as
-// the exact non-negative terms |s_a|^2 + |t_a|^2 - 2 <s_a, t_a> (dp4a, four byte pairs
-// per instruction).  Once the running sum reaches `bound` the candidate cannot be
-// strictly better than the incumbent and its remaining rows are not loaded (returns
-// false).  Otherwise returns true with the full error in *e.
-template <int K>
-__device__ __forceinline__ bool patch_error_below(const uint32_t* __restrict__ rps, int H, int W,
-                                                  int ur, int uc, const TargetPatch<K>& t,
-                                                  uint32_t bound, uint32_t* e) {
-    using G = Geo<K>;
-    uint32_t acc = 0;
-#pragma unroll
-    for (int a = 0; a < K; ++a) {
-        const int rr = clampi(ur - G::P + a, 0, H - 1);
-        uint32_t s[G::NW];
-        load_row<K>(rps + (static_cast<size_t>(rr) * W + uc) * G::RPW, s);
-        uint32_t dot = 0, ss = 0;
-#pragma unroll
-        for (int w = 0; w < G::NW; ++w) {
-            dot = __dp4a(s[w], t.w[a][w], dot);
-            ss = __dp4a(s[w], s[w], ss);
-        }
-        acc += ss + t.row_e[a] - 2u * dot;
-        if (acc >= bound) return false;
-    }
-    *e = acc;
-    return true;
-}
-
+// ---------------------------------------------------------------------------------
+// Per-call kernels (one pair table / job table per call)
+// ---------------------------------------------------------------------------------
 struct TileCoord {
     int r, c;
 };
@@ -233,30 +129,11 @@ __global__ void __launch_bounds__(TILE_THREADS)
     const int pl = blockIdx.y;
     const PairDesc pd = pairs[pair0 + pl];
     const size_t npx = static_cast<size_t>(H) * W;
-    const size_t x = static_cast<size_t>(tc.r) * W + tc.c;
-
-    int ur, uc;
-    if (mode == 0) {
-        const uint4 u = philox4x32_10(make_uint4(static_cast<uint32_t>(x), pd.tag, level_word, 0u),
-                                      key0, key1);
-        ur = static_cast<int>(__umulhi(u.x, static_cast<uint32_t>(H)));
-        uc = static_cast<int>(__umulhi(u.y, static_cast<uint32_t>(W)));
-    } else if (mode == 1) {
-        const uint32_t fc = coarse_F[static_cast<size_t>(pl) * Hc * Wc +
-                                     static_cast<size_t>(tc.r >> 1) * Wc + (tc.c >> 1)];
-        ur = clampi(2 * row_of(fc) + (tc.r & 1), 0, H - 1);
-        uc = clampi(2 * col_of(fc) + (tc.c & 1), 0, W - 1);
-    } else {
-        ur = clampi(user_init[2 * x], 0, H - 1);
-        uc = clampi(user_init[2 * x + 1], 0, W - 1);
-    }
-    TargetPatch<K> t;
-    load_target<K>(rp + static_cast<size_t>(pd.tgt) * npx * G::RPW, H, W, tc.r, tc.c, t);
-    uint32_t e = 0;
-    patch_error_below<K>(rp + static_cast<size_t>(pd.src) * npx * G::RPW, H, W, ur, uc, t,
-                         0xFFFFFFFFu, &e);
-    F[static_cast<size_t>(pl) * npx + x] = pack_rc(ur, uc);
-    E[static_cast<size_t>(pl) * npx + x] = e;
+    init_pixel<K>(rp + static_cast<size_t>(pd.src) * npx * G::RPW,
+                  rp + static_cast<size_t>(pd.tgt) * npx * G::RPW, H, W, tc.r, tc.c, pd.tag, mode,
+                  coarse_F ? coarse_F + static_cast<size_t>(pl) * Hc * Wc : nullptr, Hc, Wc,
+                  user_init, key0, key1,
+                  level_word, F + static_cast<size_t>(pl) * npx, E + static_cast<size_t>(pl) * npx);
 }
 
 // Resident 256-thread blocks per SM the iteration kernel is compiled for: larger
@@ -287,60 +164,12 @@ __global__ void __launch_bounds__(TILE_THREADS, IterOccupancy<K>::value * 256 / 
     const int pl = blockIdx.y;
     const PairDesc pd = pairs[pair0 + pl];
     const size_t npx = static_cast<size_t>(H) * W;
-    const size_t x = static_cast<size_t>(r) * W + c;
     const uint32_t* __restrict__ rps = rp + static_cast<size_t>(pd.src) * npx * G::RPW;
     const uint32_t* __restrict__ Fpp = Fp + static_cast<size_t>(pl) * npx;
 
-    TargetPatch<K> t;
-    load_target<K>(rp + static_cast<size_t>(pd.tgt) * npx * G::RPW, H, W, r, c, t);
-
-    uint32_t bf = Fpp[x];
-    uint32_t be = Ep[static_cast<size_t>(pl) * npx + x];
-
-    auto consider = [&](int cr, int cc) {
-        const uint32_t f = pack_rc(cr, cc);
-        if (f == bf) return;
-        uint32_t e;
-        if (patch_error_below<K>(rps, H, W, cr, cc, t, be, &e)) {
-            be = e;
-            bf = f;
-        }
-    };
-
-    // Propagation: F'(x) = F(x + d) - d.
-    if (r > 0) {
-        const uint32_t f = Fpp[x - W];
-        consider(min(row_of(f) + 1, H - 1), col_of(f));
-    }
-    if (r < H - 1) {
-        const uint32_t f = Fpp[x + W];
-        consider(max(row_of(f) - 1, 0), col_of(f));
-    }
-    if (c > 0) {
-        const uint32_t f = Fpp[x - 1];
-        consider(row_of(f), min(col_of(f) + 1, W - 1));
-    }
-    if (c < W - 1) {
-        const uint32_t f = Fpp[x + 1];
-        consider(row_of(f), max(col_of(f) - 1, 0));
-    }
-
-    // Random search: F'(x) = F(x) + U[-r, r]^2, r = r0 >> t, t = 0, 1, ... while r >= 1.
-    uint4 u = make_uint4(0u, 0u, 0u, 0u);
-    for (int tt = 0; (r0 >> tt) >= 1; ++tt) {
-        const int rad = r0 >> tt;
-        if ((tt & 1) == 0)
-            u = philox4x32_10(make_uint4(static_cast<uint32_t>(x), pd.tag,
-                                         ctr_word | static_cast<uint32_t>(tt >> 1), 0u),
-                              key0, key1);
-        const uint32_t span = static_cast<uint32_t>(2 * rad + 1);
-        const int dr = static_cast<int>(__umulhi((tt & 1) ? u.z : u.x, span)) - rad;
-        const int dc = static_cast<int>(__umulhi((tt & 1) ? u.w : u.y, span)) - rad;
-        consider(clampi(row_of(bf) + dr, 0, H - 1), clampi(col_of(bf) + dc, 0, W - 1));
-    }
-
-    Fn[static_cast<size_t>(pl) * npx + x] = bf;
-    En[static_cast<size_t>(pl) * npx + x] = be;
+    iterate_pixel<K>(rps, rp + static_cast<size_t>(pd.tgt) * npx * G::RPW, H, W, r, c, pd.tag, r0,
+                     key0, key1, ctr_word, Fpp, Ep + static_cast<size_t>(pl) * npx,
+                     Fn + static_cast<size_t>(pl) * npx, En + static_cast<size_t>(pl) * npx);
 }
 
 __global__ void __launch_bounds__(256) nnf_unpack_kernel(const uint32_t* __restrict__ F,
@@ -374,7 +203,6 @@ __global__ void __launch_bounds__(TILE_THREADS)
     combine_kernel(const JobDesc* __restrict__ jobs, int job0, const PairDesc* __restrict__ pairs,
                    int pair0, const uint32_t* __restrict__ F, const uint32_t* __restrict__ styles,
                    int H, int W, float* __restrict__ out) {
-    constexpr int P = K / 2;
     const TileCoord tc = tile_coord(W);
     if (tc.r >= H || tc.c >= W) return;
     const int r = tc.r, c = tc.c;
@@ -393,33 +221,14 @@ __global__ void __launch_bounds__(TILE_THREADS)
     for (int p = 0; p < job.n_pairs; ++p) {
         const int gp = job.first_pair + p;
         const PairDesc pd = pairs[gp];
-        const uint32_t* __restrict__ Fq = F + static_cast<size_t>(gp - pair0) * npx;
-        const uint32_t* __restrict__ S = styles + static_cast<size_t>(pd.style) * npx;
-        uint32_t v0 = 0, v1 = 0, v2 = 0;
-#pragma unroll
-        for (int a = -P; a <= P; ++a) {
-            const int qr = clampi(r + a, 0, H - 1);
-#pragma unroll
-            for (int b = -P; b <= P; ++b) {
-                const int qc = clampi(c + b, 0, W - 1);
-                const uint32_t f = __ldg(Fq + static_cast<size_t>(qr) * W + qc);
-                const int sr = clampi(row_of(f) - (qr - r), 0, H - 1);
-                const int sc = clampi(col_of(f) - (qc - c), 0, W - 1);
-                const uint32_t s = __ldg(S + static_cast<size_t>(sr) * W + sc);
-                v0 += s & 0xFFu;
-                v1 += (s >> 8) & 0xFFu;
-                v2 += (s >> 16) & 0xFFu;
-            }
-        }
+        uint32_t v0, v1, v2;
+        remap_votes<K>(F + static_cast<size_t>(gp - pair0) * npx,
+                       styles + static_cast<size_t>(pd.style) * npx, H, W, r, c, v0, v1, v2);
         a0 += pd.weight * v0;
         a1 += pd.weight * v1;
         a2 += pd.weight * v2;
     }
-    const float den = __uint2float_rn(job.den);
-    float* o = out + (static_cast<size_t>(job.out_frame) * npx + x) * 3;
-    o[0] = __fdiv_rn(__uint2float_rn(a0), den);
-    o[1] = __fdiv_rn(__uint2float_rn(a1), den);
-    o[2] = __fdiv_rn(__uint2float_rn(a2), den);
+    write_output(out + (static_cast<size_t>(job.out_frame) * npx + x) * 3, a0, a1, a2, job.den);
 }
 
 inline dim3 tile_grid(int H, int W, int n) {

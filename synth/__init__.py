@@ -270,3 +270,30 @@ def small_clip(N: int, H: int, W: int, seed: int, motion: str = "shift"):
         return g, colour_matrix_styles(g, seed)
     g, _ = affine_clip(N, H, W, seed)
     return g, lut_styles(g, seed)
+
+
+# ----------------------------------------------------------------------------------
+# Batched submission manifest: clips of uneven size, length, window and patch
+# ----------------------------------------------------------------------------------
+def batch_manifest(n_clips: int = 32, seed: int = clip_seed(3), sizes=(256, 1024),
+                   frames=(16, 120), windows=(5, 31), patches=(5, 7)):
+    """Seeded list of (N, H, W, window, patch): H, W multiples of 64 in [sizes],
+    N uniform in [frames], odd windows uniform in [windows], patch from `patches`."""
+    rng = np.random.default_rng(seed)
+    out = []
+    lo, hi = sizes[0] // 64, sizes[1] // 64
+    for _ in range(n_clips):
+        H = int(rng.integers(lo, hi + 1)) * 64
+        W = int(rng.integers(lo, hi + 1)) * 64
+        N = int(rng.integers(frames[0], frames[1] + 1))
+        window = int(rng.integers(windows[0] // 2, windows[1] // 2 + 1)) * 2 + 1
+        patch = int(rng.choice(patches))
+        out.append((N, H, W, window, patch))
+    return out
+
+
+def batch_clip(N: int, H: int, W: int, seed: int):
+    """Guides and styles of one manifest clip: the shift-clip recipe (cheap to draw at
+    any size) with the colour-matrix flicker style."""
+    g, _ = shift_clip(N, H, W, seed, max_step=2)
+    return g, colour_matrix_styles(g, seed)

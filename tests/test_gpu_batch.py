@@ -1,0 +1,115 @@
+"""The batched persistent path (fb_blend_batch): every clip bit-identical to
+fb_blend_window, for every tile variant, with and without graph replay, across chunks."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+SHAPES = [(5, 40, 52, 3, 5), (6, 33, 64, 5, 7), (4, 64, 48, 7, 3), (3, 48, 48, 1, 5),
+          (7, 37, 45, 5, 5)]
+
+
+@pytest.fixture(scope="module")
+def fbp():
+    import paper_2311_09265_b300 as m
+    m.build()
+    return m
+
+
+@pytest.fixture(scope="module")
+def clips():
+    import torch
+    out = []
+    for n, (N, H, W, window, patch) in enumerate(SHAPES):
+        g, s = synth.small_clip(N, H, W, seed=900 + n, motion="affine" if n % 2 else "shift")
+        out.append((torch.tensor(g, device="cuda"), torch.tensor(s, device="cuda"), window, patch))
+    return out
+
+
+def per_clip(fbp, ctx, clips, params):
+    res = []
+    for g, s, window, patch in clips:
+        p = fbp.Params.make(patch, params.iters, 1, params.r0, params.seed)
+        res.append(fbp.fb_blend_window(ctx, g, s, window, p).cpu().numpy())
+    return res
+
+
+def test_batch_matches_per_clip_blend_and_oracle(fbp, clips):
+    ctx = fbp.Context(0)
+    params = fbp.Params.make(5, 3, 1, 0, 2024)
+    want = per_clip(fbp, ctx, clips, params)
+    got = [o.cpu().numpy() for o in fbp.fb_blend_batch(ctx, clips, params)]
+    for w, g in zip(want, got):
+        assert (w == g).all()
+    g0 = clips[0][0].cpu().numpy()
+    s0 = clips[0][1].cpu().numpy()
+    ref = oracle.blend_window(g0, s0, SHAPES[0][3], SHAPES[0][4], 3, seed=2024)
+    assert (got[0] == ref).all()
+    for k in (3, 5, 7):
+        assert 0 <= fbp.fb_ctx_batch_variant(ctx, k) < 4
+    ctx.close()
+
+
+def test_graph_replay_follows_new_input_contents(fbp, clips):
+    import torch
+    ctx = fbp.Context(0)
+    params = fbp.Params.make(5, 2, 1, 0, 7)
+    outs = [torch.empty(g.shape, dtype=torch.float32, device="cuda") for g, _, _, _ in clips]
+    spec = [(g, s, w, k, o) for (g, s, w, k), o in zip(clips, outs)]
+    first = [o.cpu().numpy().copy() for o in fbp.fb_blend_batch(ctx, spec, params)]
+    n0 = ctx.launches
+    again = [o.cpu().numpy().copy() for o in fbp.fb_blend_batch(ctx, spec, params)]
+    assert all((a == b).all() for a, b in zip(first, again))
+    assert ctx.launches > n0                      # replay counted its kernels
+    saved = [s.clone() for _, s, _, _ in clips]
+    for _, s, _, _ in clips:                      # new style contents, same pointers
+        s.copy_(torch.flip(s, dims=[0]))
+    replay = [o.cpu().numpy().copy() for o in fbp.fb_blend_batch(ctx, spec, params)]
+    want = per_clip(fbp, ctx, clips, params)
+    assert all((a == b).all() for a, b in zip(replay, want))
+    for (_, s, _, _), s0 in zip(clips, saved):
+        s.copy_(s0)
+    ctx.close()
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+def test_every_tile_variant_gives_identical_results(fbp, clips, variant):
+    ctx = fbp.Context(0)
+    params = fbp.Params.make(5, 2, 1, 0, 99)
+    want = per_clip(fbp, ctx, clips, params)
+    for flags in (fbp.FB_BATCH_VARIANT(variant), fbp.FB_BATCH_VARIANT(variant) | fbp.FB_BATCH_NO_GRAPH):
+        got = [o.cpu().numpy() for o in fbp.fb_blend_batch(ctx, clips, params, flags=flags)]
+        assert all((a == b).all() for a, b in zip(want, got))
+    ctx.close()
+
+
+def test_chunked_batch_equals_single_chunk(fbp, clips):
+    ctx = fbp.Context(0)
+    params = fbp.Params.make(5, 2, 1, 0, 5)
+    want = per_clip(fbp, ctx, clips, params)
+    ctx.set_pair_budget(1 << 20)                 # forces many chunks
+    got = [o.cpu().numpy() for o in fbp.fb_blend_batch(ctx, clips, params)]
+    assert all((a == b).all() for a, b in zip(want, got))
+    # the per-call blend honours the budget too
+    again = per_clip(fbp, ctx, clips, params)
+    assert all((a == b).all() for a, b in zip(want, again))
+    ctx.close()
+
+
+def test_batch_argument_errors(fbp, clips):
+    import torch
+    ctx = fbp.Context(0)
+    g, s, _, _ = clips[0]
+    with pytest.raises(fbp.FastBlendError) as e:
+        fbp.fb_blend_batch(ctx, [(g, s, 4, 5)], fbp.Params.make(5, 2))
+    assert e.value.status == fbp.FB_ERR_ARG
+    with pytest.raises(fbp.FastBlendError) as e:
+        fbp.fb_blend_batch(ctx, [(g.cpu(), s, 3, 5)], fbp.Params.make(5, 2))
+    assert e.value.status == fbp.FB_ERR_ARG
+    with pytest.raises(fbp.FastBlendError) as e:
+        fbp.fb_blend_batch(ctx, [(g, s, 3, 5)], fbp.Params.make(5, 2), flags=fbp.FB_BATCH_VARIANT(7))
+    assert e.value.status == fbp.FB_ERR_ARG
+    ctx.close()
