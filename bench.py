@@ -52,7 +52,8 @@ def parse_args(argv=None):
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("fastblend", "reference"), default="fastblend")
-    ap.add_argument("--workload", default="blend_512", choices=sorted(synth.WORKLOADS))
+    ap.add_argument("--workload", default="blend_512",
+                    choices=sorted(synth.WORKLOADS) + ["batch_32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=5)
@@ -184,8 +185,15 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    w = synth.WORKLOADS[args.workload]
-    g, s = make_inputs(w, w.seed)
+    if args.workload == "batch_32":
+        N, H, W, window, patch = synth.batch_manifest(seed=BATCH_SEED)[0]
+        g, s = synth.batch_clip(N, H, W, seed=BATCH_SEED)
+        w = synth.Workload("batched persistent submission of 32 uneven clips (sample: clip 0)",
+                           "blend", N, H, W, patch=patch, iters=BATCH_ITERS, window=window,
+                           seed=BATCH_SEED)
+    else:
+        w = synth.WORKLOADS[args.workload]
+        g, s = make_inputs(w, w.seed)
     frames = sample_frames(w, 1)
     for _ in range(args.warmup):
         oracle_frame_seconds(w, g, s, frames)
@@ -351,10 +359,168 @@ def run_gpu(args):
     return 0
 
 
+# ----------------------------------------------------------------------------------
+# Batched submission: 32 clips of uneven size, length, window and patch
+# ----------------------------------------------------------------------------------
+BATCH_SEED = synth.clip_seed(3)
+BATCH_ITERS = 6
+
+
+def batch_iter_ops(manifest) -> int:
+    """Algorithmic byte-pair ops of all Jacobi-iteration launches of one submission."""
+    tot = 0
+    for N, H, W, window, patch in manifest:
+        M = (window - 1) // 2
+        pairs = sum(min(N - 1, i + M) - max(0, i - M) for i in range(N))
+        R = int(math.floor(math.log2(max(H, W)))) + 1
+        tot += pairs * H * W * (4 + R) * 3 * patch * patch
+    return tot * BATCH_ITERS
+
+
+def batch_candidate_evals(manifest) -> int:
+    tot = 0
+    for N, H, W, window, patch in manifest:
+        M = (window - 1) // 2
+        pairs = sum(min(N - 1, i + M) - max(0, i - M) for i in range(N))
+        R = int(math.floor(math.log2(max(H, W)))) + 1
+        tot += pairs * H * W * (1 + BATCH_ITERS * (4 + R))
+    return tot
+
+
+def run_gpu_batch(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2311_09265_b300 as fbp
+
+    rank, world, local = dist_env()
+    if world > 1:
+        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+        dist.init_process_group("gloo", rank=rank, world_size=world)
+    torch.cuda.set_device(local)
+    fbp.build()
+    manifest = synth.batch_manifest(seed=shard_seed(BATCH_SEED, rank))
+    clips, host = [], []
+    for n, (N, H, W, window, patch) in enumerate(manifest):
+        g, s = synth.batch_clip(N, H, W, seed=shard_seed(BATCH_SEED, rank) + n)
+        host.append((g, s))
+        clips.append((torch.tensor(g, device="cuda"), torch.tensor(s, device="cuda"), window, patch,
+                      torch.empty((N, H, W, 3), dtype=torch.float32, device="cuda")))
+    frames = sum(m[0] for m in manifest)
+    ctx = fbp.Context(local)
+    params = fbp.Params.make(5, BATCH_ITERS, 1, 0, BATCH_SEED)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    t_build = time.perf_counter()
+    for _ in range(max(args.warmup, 1)):          # the first call tunes and captures
+        fbp.fb_blend_batch(ctx, clips, params)
+    torch.cuda.synchronize()
+    t_build = time.perf_counter() - t_build
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launches
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record()
+            fbp.fb_blend_batch(ctx, clips, params)   # graph replay
+            ends[k].record()
+        torch.cuda.synchronize()
+    launches = ctx.launches - launches0
+    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = aggregate(frames, args.steps, world, total_ms)
+    clocks = clk.summary()
+
+    # Kernel breakdown: one untimed submission with direct launches and event timing.
+    ctx.profile(True)
+    fbp.fb_blend_batch(ctx, clips, params, flags=fbp.FB_BATCH_NO_GRAPH)
+    prof = ctx.profile_read()
+    ctx.profile(False)
+    iter_ms, iter_n = prof["iter"]
+    kernel_total_ms = sum(v[0] for v in prof.values())
+    peak = DP4A_PER_CLK_SM * 4 * SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
+    achieved = batch_iter_ops(manifest) / (iter_ms / 1e3) / 1e12 if iter_ms else None
+    roof = {"bound": "alu", "kernel": "batch_iter (persistent Alg. 1 Jacobi iteration)",
+            "achieved": achieved, "peak": peak, "unit": "T byte-pair ops/s",
+            "frac": achieved / peak if achieved else None, "traffic": None,
+            "peak_basis": f"{DP4A_PER_CLK_SM} dp4a/clk/SM x {SM_COUNT_NOMINAL} SMs x "
+                          f"{SM_MAX_MHZ_NOMINAL:.0f} MHz x 4 byte pairs (derived)",
+            "avg_launch_ms": iter_ms / iter_n if iter_n else None, "launches": iter_n,
+            "share_of_kernel_time": iter_ms / kernel_total_ms if kernel_total_ms else None,
+            "candidate_evals_per_s": batch_candidate_evals(manifest) * args.steps * world
+            / (total_ms / 1e3)}
+    variants = {k: fbp.batch_variant_name(fbp.fb_ctx_batch_variant(ctx, k)) for k in (5, 7)}
+
+    e2e = None
+    if not args.no_e2e:
+        # End to end: pinned host inputs copied in, outputs copied out, every step.
+        hg = [torch.tensor(g).pin_memory() for g, _ in host]
+        hs = [torch.tensor(s).pin_memory() for _, s in host]
+        ho = [torch.empty(c[4].shape, dtype=torch.float32).pin_memory() for c in clips]
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            for (g, s, _, _, _), a, b in zip(clips, hg, hs):
+                g.copy_(a, non_blocking=True)
+                s.copy_(b, non_blocking=True)
+            fbp.fb_blend_batch(ctx, clips, params)
+            for c, o in zip(clips, ho):
+                o.copy_(c[4], non_blocking=True)
+            torch.cuda.synchronize()
+        t_e2e = time.perf_counter() - t0
+        e2e = {"value": world * frames * args.steps / t_e2e, "unit": "frames/s",
+               "h2d_bytes_per_step": int(sum(a.numel() + b.numel() for a, b in zip(hg, hs))),
+               "d2h_bytes_per_step": int(sum(o.numel() * 4 for o in ho))}
+
+    line = {
+        "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+        "data": "synthetic",
+        "config": {"workload": "batched persistent submission of 32 uneven clips "
+                               "(256-1024 px, 16-120 frames, windows 5-31, patch 5/7, n=6)",
+                   "frames_per_step": frames, "clips": len(manifest),
+                   "nnfs_per_step": sum(sum(min(N - 1, i + (w - 1) // 2) - max(0, i - (w - 1) // 2)
+                                            for i in range(N)) for N, H, W, w, k in manifest),
+                   "candidate_evals_per_step": batch_candidate_evals(manifest),
+                   "tuned_variants": variants, "first_call_s": t_build,
+                   "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"{world} independent batch(es), one per GPU"},
+        "roofline": roof, "e2e": e2e, "gpu_launches": launches,
+        "kernel_ms": {k: v[0] for k, v in prof.items() if v[1]}, "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        N, H, W, window, patch = manifest[0]
+        g, s = host[0]
+        t0 = time.perf_counter()
+        oracle.blend_frame(g, s, window, N // 2, patch, BATCH_ITERS, seed=BATCH_SEED)
+        secs = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": 1.0 / secs, "unit": "frames/s",
+                                "cores": oracle.num_threads(), "kind": "oracle",
+                                "sample": f"output frame {N // 2} of clip 0 ({N}x{H}x{W}, window "
+                                          f"{window}, patch {patch}); {secs:.1f} s"}
+    if rank == 0:
+        print(json.dumps(line))
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "batch_32":
+        return run_gpu_batch(args)
     return run_gpu(args)
 
 

@@ -334,3 +334,11 @@ def fb_batch_plan(shapes, params: Params, budget_bytes: int = 0):
 
 def fb_ctx_batch_variant(ctx: Context, patch: int) -> int:
     return int(lib().fb_ctx_batch_variant(ctx.handle, patch))
+
+
+BATCH_VARIANT_NAMES = ("tile 32x8, 5 blocks/SM", "tile 32x4, 10 blocks/SM",
+                       "tile 32x16, 2 blocks/SM", "tile 32x8, 4 blocks/SM")
+
+
+def batch_variant_name(v: int) -> str:
+    return BATCH_VARIANT_NAMES[v] if 0 <= v < len(BATCH_VARIANT_NAMES) else "untuned"

@@ -602,8 +602,11 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     // ---- device layout ----
     Carver cv(nullptr);
     struct ClipBufs { uint32_t* rp; uint32_t* sty; };
+    size_t n_counters = 2;  // tuning launches
+    for (const HostChunk& ch : chunks) n_counters += 2 + static_cast<size_t>(p->iters);
     auto layout = [&](Carver& c, BatchClip** d_clips, std::vector<ClipBufs>& cb,
-                      uint32_t** fe, std::vector<std::array<void*, 6>>& tabs) {
+                      uint32_t** fe, std::vector<std::array<void*, 6>>& tabs, int** counters) {
+        *counters = c.take<int>(n_counters);
         *d_clips = c.take<BatchClip>(n);
         cb.assign(n, ClipBufs{});
         for (int i = 0; i < n; ++i) {
@@ -633,7 +636,8 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     std::vector<ClipBufs> cb;
     uint32_t* fe[4] = {};
     std::vector<std::array<void*, 6>> tabs;
-    layout(cv, &d_clips, cb, fe, tabs);
+    int* counters = nullptr;
+    layout(cv, &d_clips, cb, fe, tabs, &counters);
     be->bytes = align_up(cv.off, 1 << 20);
     cudaError_t e = cudaMalloc(reinterpret_cast<void**>(&be->dev), be->bytes);
     if (e != cudaSuccess) {
@@ -642,7 +646,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         return fail(ctx, FB_ERR_OOM, "batch scratch of %zu bytes: %s", be->bytes, cudaGetErrorString(e));
     }
     Carver real(be->dev);
-    layout(real, &d_clips, cb, fe, tabs);
+    layout(real, &d_clips, cb, fe, tabs, &counters);
 
     // ---- static tables ----
     std::vector<BatchClip> hclips(n);
@@ -665,7 +669,11 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     }
 
     // ---- the launches of one submission ----
-    std::vector<std::function<cudaError_t(cudaStream_t)>> prep;
+    // First the work counters of the persistent launches are zeroed (kind -1: not a kernel).
+    be->steps.push_back([counters, n_counters](cudaStream_t s) {
+        return cudaMemsetAsync(counters, 0, n_counters * sizeof(int), s);
+    });
+    be->step_kind.push_back(-1);
     for (int i = 0; i < n; ++i) {
         const fb_clip_desc d = clips[i];
         const ClipBufs b = cb[i];
@@ -687,7 +695,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         const HostChunk& ch = chunks[ci];
         if (variant_of[ch.k] >= 0 || ch.pairs.empty()) continue;
         if (!prepped) {
-            for (size_t q = 0; q < 2 * static_cast<size_t>(n); ++q) FB_CUDA(ctx, be->steps[q](st));
+            for (size_t q = 0; q < 1 + 2 * static_cast<size_t>(n); ++q) FB_CUDA(ctx, be->steps[q](st));
             prepped = true;
         }
         const BatchPair* d_pairs = static_cast<const BatchPair*>(tabs[ci][0]);
@@ -703,11 +711,12 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
             FB_CUDA(ctx, cudaMemcpyAsync(d_ip, m0.data(), sizeof(int32_t) * m0.size(), cudaMemcpyHostToDevice, st));
             FB_CUDA(ctx, cudaMemcpyAsync(d_it, m1.data(), sizeof(int32_t) * m1.size(), cudaMemcpyHostToDevice, st));
             const int grid = sms * fb::batch_iter_blocks_per_sm(ch.k, v);
+            FB_CUDA(ctx, cudaMemsetAsync(counters, 0, 2 * sizeof(int), st));
             FB_CUDA(ctx, fb::launch_batch_init(ch.k, v, d_pairs, d_clips, d_ip, d_it, static_cast<int>(m0.size()),
-                                               p->seed, fe[0], fe[1], grid, st));
+                                               counters, p->seed, fe[0], fe[1], grid, st));
             FB_CUDA(ctx, cudaEventRecord(a, st));
             FB_CUDA(ctx, fb::launch_batch_iter(ch.k, v, d_pairs, d_clips, d_ip, d_it, static_cast<int>(m0.size()),
-                                               p->seed, 0, fe[0], fe[1], fe[2], fe[3], grid, st));
+                                               counters + 1, p->seed, 0, fe[0], fe[1], fe[2], fe[3], grid, st));
             FB_CUDA(ctx, cudaEventRecord(b, st));
             FB_CUDA(ctx, cudaEventSynchronize(b));
             float ms = 0.f;
@@ -723,6 +732,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         variant_of[ch.k] = best_v;
         if (forced_variant(flags) < 0) ctx->tuned_variant[ch.k] = best_v;
     }
+    int* next_counter = counters + 2;
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const HostChunk& ch = chunks[ci];
         const int v = variant_of[ch.k] >= 0 ? variant_of[ch.k] : 0;
@@ -748,14 +758,16 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         const int32_t* d_ijt = static_cast<const int32_t*>(tabs[ci][5]);
         uint32_t *Fc = fe[0], *Ec = fe[1], *Fo = fe[2], *Eo = fe[3];
         if (n_items > 0) {
+            int* cnt = next_counter++;
             be->steps.push_back([=](cudaStream_t s) {
-                return fb::launch_batch_init(k, v, d_pairs, d_clips, d_ip, d_it, n_items, seed, Fc, Ec, grid, s);
+                return fb::launch_batch_init(k, v, d_pairs, d_clips, d_ip, d_it, n_items, cnt, seed, Fc, Ec, grid, s);
             });
             be->step_kind.push_back(FB_K_INIT);
             for (int it = 0; it < iters; ++it) {
                 uint32_t *a = Fc, *ea = Ec, *b = Fo, *eb = Eo;
+                int* cnt_it = next_counter++;
                 be->steps.push_back([=](cudaStream_t s) {
-                    return fb::launch_batch_iter(k, v, d_pairs, d_clips, d_ip, d_it, n_items, seed, it, a, ea, b, eb, grid, s);
+                    return fb::launch_batch_iter(k, v, d_pairs, d_clips, d_ip, d_it, n_items, cnt_it, seed, it, a, ea, b, eb, grid, s);
                 });
                 be->step_kind.push_back(FB_K_ITER);
                 std::swap(Fc, Fo);
@@ -764,12 +776,14 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         }
         const uint32_t* Ffinal = Fc;
         const int jn = static_cast<int>(job_items);
+        int* cnt_c = next_counter++;
         be->steps.push_back([=](cudaStream_t s) {
-            return fb::launch_batch_combine(k, d_jobs, d_pairs, d_clips, d_ij, d_ijt, jn, Ffinal, cgrid, s);
+            return fb::launch_batch_combine(k, d_jobs, d_pairs, d_clips, d_ij, d_ijt, jn, cnt_c, Ffinal, cgrid, s);
         });
         be->step_kind.push_back(FB_K_COMBINE);
     }
-    be->launches_per_run = be->steps.size();
+    be->launches_per_run = 0;
+    for (int kind : be->step_kind) be->launches_per_run += kind >= 0 ? 1 : 0;
 
     if (!(flags & FB_BATCH_NO_GRAPH)) {
         // Capture on a private stream (the legacy default stream cannot be captured);
@@ -880,7 +894,10 @@ extern "C" int fb_blend_batch(fb_ctx* ctx, const fb_clip_desc* clips, int n_clip
     } else {
         for (size_t i = 0; i < be->steps.size(); ++i) {
             const int kind = be->step_kind[i];
-            FB_LAUNCH(ctx, st, kind, be->steps[i](st));
+            if (kind < 0)
+                FB_CUDA(ctx, be->steps[i](st));
+            else
+                FB_LAUNCH(ctx, st, kind, be->steps[i](st));
         }
     }
     return FB_OK;

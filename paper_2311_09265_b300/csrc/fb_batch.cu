@@ -1,8 +1,8 @@
 // fb_batch.cu -- persistent kernels of the batched submission (fb_blend_batch): many
 // clips of uneven size, window and patch in one pass.  Every pair of every clip is cut
-// into 32-column tiles; a kernel of SMs x resident-blocks CTAs walks the flattened
-// work list (item -> pair, tile), so clips of different shapes share one launch per
-// Jacobi iteration.  The per-pixel work is the same code as the per-call kernels
+// into 32-column tiles; a kernel of SMs x resident-blocks CTAs claims items of the
+// flattened work list (item -> pair, tile) from a counter, so clips of different shapes
+// share one launch per Jacobi iteration.  The per-pixel work is the same code as the per-call kernels
 // (fb_device.cuh), so results are identical to fb_blend_window whatever tile shape the
 // autotuner picks.
 #include <type_traits>
@@ -23,6 +23,34 @@ template <> struct Variant<1> { static constexpr int TH = 4, MINB = 10; };  // 3
 template <> struct Variant<2> { static constexpr int TH = 16, MINB = 2; };  // 32x16, 2 blocks
 template <> struct Variant<3> { static constexpr int TH = 8, MINB = 4; };   // 32x8,  4 blocks
 
+// Work distribution: every CTA claims the next unprocessed item from a counter that is
+// zeroed before the launch, so items (pair-major) are processed close to their global
+// order and only about one resident wave of pairs shares the L2 at a time (a static
+// round-robin lets fast and slow CTAs drift apart and spreads the working set).  The
+// claim for the following item is issued before the current one is processed, so its
+// latency is hidden behind the work.
+struct ItemQueue {
+    int* counter;
+    int* slot;    // shared: [2]
+    int buf = 0;
+    int pending = 0;
+    __device__ __forceinline__ bool lead() const { return threadIdx.x == 0 && threadIdx.y == 0; }
+    __device__ __forceinline__ int first() {
+        if (lead()) slot[0] = atomicAdd(counter, 1);
+        __syncthreads();
+        return slot[0];
+    }
+    __device__ __forceinline__ void prefetch() {
+        if (lead()) pending = atomicAdd(counter, 1);
+    }
+    __device__ __forceinline__ int next() {
+        if (lead()) slot[buf ^ 1] = pending;
+        __syncthreads();  // the claim is visible and every thread is done with the item
+        buf ^= 1;
+        return slot[buf];
+    }
+};
+
 // Larger patches keep more target words in registers: scale the block count down.
 template <int K, int V>
 struct BatchOcc {
@@ -34,19 +62,23 @@ template <int K, int V>
 __global__ void __launch_bounds__(32 * Variant<V>::TH, BatchOcc<K, V>::value)
     batch_iter_kernel(const BatchPair* __restrict__ pairs, const BatchClip* __restrict__ clips,
                       const int32_t* __restrict__ item_pair, const int32_t* __restrict__ item_tile,
-                      int n_items, uint32_t key0, uint32_t key1, uint32_t ctr_word,
-                      const uint32_t* __restrict__ Fp, const uint32_t* __restrict__ Ep,
-                      uint32_t* __restrict__ Fn, uint32_t* __restrict__ En) {
+                      int n_items, int* __restrict__ counter, uint32_t key0, uint32_t key1,
+                      uint32_t ctr_word, const uint32_t* __restrict__ Fp,
+                      const uint32_t* __restrict__ Ep, uint32_t* __restrict__ Fn,
+                      uint32_t* __restrict__ En) {
     using G = Geo<K>;
     constexpr int TH = Variant<V>::TH;
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    __shared__ int s_slot[2];
+    ItemQueue q{counter, s_slot};
+    for (int item = q.first(); item < n_items; item = q.next()) {
+        q.prefetch();
         const BatchPair bp = pairs[item_pair[item]];
         const BatchClip cl = clips[bp.clip];
         const int tiles_x = (cl.W + 31) / 32;
         const int tile = item_tile[item];
         const int r = (tile / tiles_x) * TH + static_cast<int>(threadIdx.y);
         const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
-        if (r >= cl.H || c >= cl.W) continue;
+        if (r >= cl.H || c >= cl.W) continue;  // no barrier below: a skipped thread rejoins at q.next()
         const size_t npx = static_cast<size_t>(cl.H) * cl.W;
         iterate_pixel<K>(cl.rp + static_cast<size_t>(bp.src) * npx * G::RPW,
                          cl.rp + static_cast<size_t>(bp.tgt) * npx * G::RPW, cl.H, cl.W, r, c,
@@ -59,11 +91,14 @@ template <int K, int V>
 __global__ void __launch_bounds__(32 * Variant<V>::TH)
     batch_init_kernel(const BatchPair* __restrict__ pairs, const BatchClip* __restrict__ clips,
                       const int32_t* __restrict__ item_pair, const int32_t* __restrict__ item_tile,
-                      int n_items, uint32_t key0, uint32_t key1, uint32_t* __restrict__ F,
-                      uint32_t* __restrict__ E) {
+                      int n_items, int* __restrict__ counter, uint32_t key0, uint32_t key1,
+                      uint32_t* __restrict__ F, uint32_t* __restrict__ E) {
     using G = Geo<K>;
     constexpr int TH = Variant<V>::TH;
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+    __shared__ int s_slot[2];
+    ItemQueue q{counter, s_slot};
+    for (int item = q.first(); item < n_items; item = q.next()) {
+        q.prefetch();
         const BatchPair bp = pairs[item_pair[item]];
         const BatchClip cl = clips[bp.clip];
         const int tiles_x = (cl.W + 31) / 32;
@@ -84,8 +119,11 @@ __global__ void __launch_bounds__(256)
     batch_combine_kernel(const BatchJob* __restrict__ jobs, const BatchPair* __restrict__ pairs,
                          const BatchClip* __restrict__ clips, const int32_t* __restrict__ item_job,
                          const int32_t* __restrict__ item_tile, int n_items,
-                         const uint32_t* __restrict__ F) {
-    for (int item = blockIdx.x; item < n_items; item += gridDim.x) {
+                         int* __restrict__ counter, const uint32_t* __restrict__ F) {
+    __shared__ int s_slot[2];
+    ItemQueue q{counter, s_slot};
+    for (int item = q.first(); item < n_items; item = q.next()) {
+        q.prefetch();
         const BatchJob job = jobs[item_job[item]];
         const BatchClip cl = clips[job.clip];
         const int tiles_x = (cl.W + 31) / 32;
@@ -113,20 +151,20 @@ __global__ void __launch_bounds__(256)
 
 template <int K, int V>
 cudaError_t launch_iter_kv(const BatchPair* pairs, const BatchClip* clips, const int32_t* ip,
-                           const int32_t* it_, int n, uint32_t k0, uint32_t k1, uint32_t cw,
-                           const uint32_t* Fp, const uint32_t* Ep, uint32_t* Fn, uint32_t* En,
-                           int grid, cudaStream_t st) {
-    batch_iter_kernel<K, V><<<grid, dim3(32, Variant<V>::TH), 0, st>>>(pairs, clips, ip, it_, n, k0,
-                                                                       k1, cw, Fp, Ep, Fn, En);
+                           const int32_t* it_, int n, int* counter, uint32_t k0, uint32_t k1,
+                           uint32_t cw, const uint32_t* Fp, const uint32_t* Ep, uint32_t* Fn,
+                           uint32_t* En, int grid, cudaStream_t st) {
+    batch_iter_kernel<K, V><<<grid, dim3(32, Variant<V>::TH), 0, st>>>(pairs, clips, ip, it_, n, counter,
+                                                                       k0, k1, cw, Fp, Ep, Fn, En);
     return cudaGetLastError();
 }
 
 template <int K, int V>
 cudaError_t launch_init_kv(const BatchPair* pairs, const BatchClip* clips, const int32_t* ip,
-                           const int32_t* it_, int n, uint32_t k0, uint32_t k1, uint32_t* F,
-                           uint32_t* E, int grid, cudaStream_t st) {
-    batch_init_kernel<K, V><<<grid, dim3(32, Variant<V>::TH), 0, st>>>(pairs, clips, ip, it_, n, k0,
-                                                                       k1, F, E);
+                           const int32_t* it_, int n, int* counter, uint32_t k0, uint32_t k1,
+                           uint32_t* F, uint32_t* E, int grid, cudaStream_t st) {
+    batch_init_kernel<K, V><<<grid, dim3(32, Variant<V>::TH), 0, st>>>(pairs, clips, ip, it_, n, counter,
+                                                                       k0, k1, F, E);
     return cudaGetLastError();
 }
 
@@ -197,35 +235,37 @@ int batch_iter_blocks_per_sm(int k, int variant) {
 
 cudaError_t launch_batch_iter(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
                               const int32_t* item_pair, const int32_t* item_tile, int n_items,
-                              uint64_t seed, int it, const uint32_t* Fp, const uint32_t* Ep,
-                              uint32_t* Fn, uint32_t* En, int grid, cudaStream_t st) {
+                              int* counter, uint64_t seed, int it, const uint32_t* Fp,
+                              const uint32_t* Ep, uint32_t* Fn, uint32_t* En, int grid,
+                              cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
     const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
     const uint32_t cw = static_cast<uint32_t>(it + 1) << 8;  // level 0
     FB_BATCH_DISPATCH(k, variant, (launch_iter_kv<KK, VV>(pairs, clips, item_pair, item_tile, n_items,
-                                                         k0, k1, cw, Fp, Ep, Fn, En, grid, st)));
+                                                         counter, k0, k1, cw, Fp, Ep, Fn, En, grid, st)));
 }
 
 cudaError_t launch_batch_init(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
                               const int32_t* item_pair, const int32_t* item_tile, int n_items,
-                              uint64_t seed, uint32_t* F, uint32_t* E, int grid, cudaStream_t st) {
+                              int* counter, uint64_t seed, uint32_t* F, uint32_t* E, int grid,
+                              cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
     const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
     FB_BATCH_DISPATCH(k, variant, (launch_init_kv<KK, VV>(pairs, clips, item_pair, item_tile, n_items,
-                                                         k0, k1, F, E, grid, st)));
+                                                         counter, k0, k1, F, E, grid, st)));
 }
 
 cudaError_t launch_batch_combine(int k, const BatchJob* jobs, const BatchPair* pairs,
                                  const BatchClip* clips, const int32_t* item_job,
-                                 const int32_t* item_tile, int n_items, const uint32_t* F,
-                                 int grid, cudaStream_t st) {
+                                 const int32_t* item_tile, int n_items, int* counter,
+                                 const uint32_t* F, int grid, cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
     const dim3 block(32, 8);
     switch (k) {
-        case 3: batch_combine_kernel<3><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, F); break;
-        case 5: batch_combine_kernel<5><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, F); break;
-        case 7: batch_combine_kernel<7><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, F); break;
-        case 9: batch_combine_kernel<9><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, F); break;
+        case 3: batch_combine_kernel<3><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, counter, F); break;
+        case 5: batch_combine_kernel<5><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, counter, F); break;
+        case 7: batch_combine_kernel<7><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, counter, F); break;
+        case 9: batch_combine_kernel<9><<<grid, block, 0, st>>>(jobs, pairs, clips, item_job, item_tile, n_items, counter, F); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -90,17 +90,20 @@ struct BatchJob {
 constexpr int kBatchVariants = 4;
 const char* batch_variant_name(int v);
 // Work items: item_pair[i] = pair of item i, item_tile[i] = tile index within the pair.
+// `counter` must be zero when the launch starts (one int per launch).
 cudaError_t launch_batch_init(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
                               const int32_t* item_pair, const int32_t* item_tile, int n_items,
-                              uint64_t seed, uint32_t* F, uint32_t* E, int grid, cudaStream_t st);
+                              int* counter, uint64_t seed, uint32_t* F, uint32_t* E, int grid,
+                              cudaStream_t st);
 cudaError_t launch_batch_iter(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
                               const int32_t* item_pair, const int32_t* item_tile, int n_items,
-                              uint64_t seed, int it, const uint32_t* Fp, const uint32_t* Ep,
-                              uint32_t* Fn, uint32_t* En, int grid, cudaStream_t st);
+                              int* counter, uint64_t seed, int it, const uint32_t* Fp,
+                              const uint32_t* Ep, uint32_t* Fn, uint32_t* En, int grid,
+                              cudaStream_t st);
 cudaError_t launch_batch_combine(int k, const BatchJob* jobs, const BatchPair* pairs,
                                  const BatchClip* clips, const int32_t* item_job,
-                                 const int32_t* item_tile, int n_items, const uint32_t* F,
-                                 int grid, cudaStream_t st);
+                                 const int32_t* item_tile, int n_items, int* counter,
+                                 const uint32_t* F, int grid, cudaStream_t st);
 // Rows per tile of a variant (tiles are 32 columns wide).
 int batch_variant_tile_h(int variant);
 // Resident blocks per SM of the variant's iteration kernel for patch k (occupancy API).
