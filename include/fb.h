@@ -66,8 +66,16 @@ typedef struct fb_params {
     uint32_t pair_tag; /* fb_nnf only: stream id of this pair; fb_pair_tag(j, i) makes  */
                        /* fb_nnf reproduce the NNF that the blend/interpolation calls   */
                        /* compute for source frame j -> target frame i                  */
-    uint32_t flags;    /* reserved, must be 0                                           */
+    uint32_t flags;    /* FB_FLAG_* bits below; 0 = the paper's method                  */
 } fb_params;
+
+/* fb_params.flags.  FB_FLAG_LEARNED_INIT (fb_blend_window, fb_interpolate): start Alg. 1
+ * from the learned initialiser attached with fb_ctx_set_initnet instead of the random
+ * field (an addition to the paper, see fb_initnet below; levels must be 1).
+ * FB_FLAG_REPORT_ENERGY (same calls): accumulate the sum of the final Eq. 1 errors of all
+ * NNFs of the call, read with fb_ctx_energy. */
+#define FB_FLAG_LEARNED_INIT 0x1u
+#define FB_FLAG_REPORT_ENERGY 0x2u
 
 /* Create a context on CUDA device `device` (made current for the call).  The context
  * allocates scratch lazily and keeps it for reuse until fb_ctx_destroy. */
@@ -219,8 +227,89 @@ int fb_batch_plan(const fb_clip_desc *clips, int n_clips, const fb_params *p, si
  * 1 MiB).  Larger inputs run in more chunks; results do not depend on it. */
 int fb_ctx_set_pair_budget(fb_ctx *ctx, size_t bytes);
 
+/* Sum and number of the final Eq. 1 errors accumulated by the last call made with
+ * FB_FLAG_REPORT_ENERGY (waits for the device). */
+int fb_ctx_energy(fb_ctx *ctx, double *sum, uint64_t *count);
+
 /* Tile variant the autotuner chose for patch size k in this context, or -1. */
 int fb_ctx_batch_variant(const fb_ctx *ctx, int patch);
+
+/* ---------------------------------------------------------------------------------
+ * Learned NNF initialiser.  Not in the paper (its method is model-free and needs no
+ * training, Sec. 3.1): a small BF16 convolutional pyramid that maps a pair of guide
+ * frames (source, target) at a quarter of their resolution to an offset field, trained
+ * on NNFs that Alg. 1 itself computes, so that Alg. 1 can start near its answer and run
+ * fewer iterations.  Convolutions run on the tcgen05 tensor cores (BF16 operands, FP32
+ * accumulation); forward, backward and the Adam update are this library's kernels.
+ * Architecture: 12 3x3 conv layers (encoder 8->32->32, ->64/2->64, ->96/2->96,
+ * ->128/2->128; decoder with nearest upsampling and skip concatenation 224->96,
+ * 160->64, 96->32; head 32->8 of which channels 0,1 are the (row, col) offset / 16 in
+ * full-resolution pixels), ReLU except on the head; 779,592 parameters.
+ * Guide frames must have H and W divisible by 32.  All pointers are device pointers
+ * unless stated.  A net belongs to the device current at creation; not thread-safe.
+ * --------------------------------------------------------------------------------- */
+typedef struct fb_initnet fb_initnet;
+
+/* Allocate a net for up to max_pairs pairs of H x W frames (parameters start at zero:
+ * set them with fb_initnet_set_params).  FB_ERR_ARG if H or W is not a multiple of 32. */
+int fb_initnet_create(fb_ctx *ctx, fb_initnet **out, int max_pairs, int H, int W);
+int fb_initnet_destroy(fb_initnet *net);
+const char *fb_initnet_last_error(const fb_initnet *net);
+
+/* Number of FP32 parameters, laid out per layer as weights [Cout][3][3][Cin] then biases
+ * [Cout]; get/set copy them between the device and a HOST array of that length (set
+ * also resets the Adam state). */
+size_t fb_initnet_param_count(const fb_initnet *net);
+int fb_initnet_get_params(fb_initnet *net, float *host_out);
+int fb_initnet_set_params(fb_initnet *net, const float *host_in);
+/* Gradient of the last train step, same layout, to a HOST array. */
+int fb_initnet_get_grads(fb_initnet *net, float *host_out);
+
+/* Forward pass for n pairs: src, tgt are n x H x W x 3 uint8 stacks (pair p = source
+ * frame src[p] -> target frame tgt[p]).  head_out (nullable): n x H/4 x W/4 x 8 float,
+ * channels 0,1 = predicted (row, col) offset / 16.  Async on `stream`. */
+int fb_initnet_forward(fb_initnet *net, const uint8_t *src, const uint8_t *tgt, int n,
+                       float *head_out, void *stream);
+
+/* Initial NNF of the n pairs of the last forward pass: F0(x) = clamp(x + rint(16 *
+ * head(x / 4))), written as n x H x W x 2 int32.  Async. */
+int fb_initnet_init_nnf(fb_initnet *net, int n, int32_t *nnf_out, void *stream);
+
+/* One training step on n pairs: forward, smooth-L1 loss (1 pixel transition) between
+ * 16 * head[..., 0:2] and `target` (n x H/4 x W/4 x 2 float, full-resolution pixels)
+ * weighted by `weight` (n x H/4 x W/4 float, or NULL = 1) and divided by weight_sum,
+ * backward, and an Adam update with step size lr (lr = 0: gradients only).  The loss
+ * is written to the device float *loss_out (nullable).  Async. */
+int fb_initnet_train_step(fb_initnet *net, const uint8_t *src, const uint8_t *tgt, int n,
+                          const float *target, const float *weight, float weight_sum, float lr,
+                          float *loss_out, void *stream);
+
+/* Attach (or with NULL detach) the learned initialiser used by FB_FLAG_LEARNED_INIT. */
+int fb_ctx_set_initnet(fb_ctx *ctx, fb_initnet *net);
+
+/* Training targets from fields computed by Alg. 1 (nnf: n x H x W x 2 int32): per 4x4
+ * block the mean offset F(x) - x (target, n x H/4 x W/4 x 2 float) and weight 1 where
+ * all 16 offsets lie within 2 pixels of that mean, else 0 (weight, nullable).  Async. */
+int fb_initnet_targets(const int32_t *nnf, int n, int H, int W, float *target, float *weight,
+                       void *stream);
+
+/* FB_ERR_TIMEOUT if a tensor-core kernel of this net hit its bounded wait. */
+int fb_initnet_status(fb_initnet *net);
+
+/* Single 3x3 convolution layer (zero padding 1) on the tensor cores, for tests:
+ *   x   n x H x W x Cin bf16 (uint16 storage), w Cout x 3 x 3 x Cin bf16, bias Cout f32,
+ *   y   n x Ho x Wo x Cout, Ho = ceil(H / stride): bf16 (y_bf16) or f32 (y_f32, no ReLU
+ *       applied to the f32 output when relu = 0).
+ * Backward: dz = gradient at the pre-activation output (bf16), wt = the weights
+ * transposed to Cin x 3 x 3 x Cout (bf16); dx (nullable) n x H x W x Cin f32 written;
+ * dw (nullable) Cout x 3 x 3 x Cin f32 ADDED to.  Cin, Cout multiples of 8, Cout <= 128.
+ * status: device int set to 1 if a bounded wait expired.  Async. */
+int fb_conv3x3_forward(const uint16_t *x, int n, int H, int W, int Cin, const uint16_t *w,
+                       const float *bias, int Cout, int stride, int relu, uint16_t *y_bf16,
+                       float *y_f32, int *status, void *stream);
+int fb_conv3x3_backward(const uint16_t *x, int n, int H, int W, int Cin, const uint16_t *wt,
+                        int Cout, int stride, const uint16_t *dz, float *dx, float *dw,
+                        int *status, void *stream);
 
 /* Bytes of the fixed device scratch array used by fb_blend_window_noalloc. */
 #define FB_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)

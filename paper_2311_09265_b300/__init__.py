@@ -25,7 +25,16 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a", "fb_pair_tag",
                     "fb_nnf", "fb_remap", "fb_blend_window", "fb_interpolate",
                     "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan",
-                    "fb_ctx_batch_variant", "fb_ctx_set_pair_budget")
+                    "fb_ctx_batch_variant", "fb_ctx_set_pair_budget",
+                    "fb_initnet_create", "fb_initnet_destroy", "fb_initnet_last_error",
+                    "fb_initnet_param_count", "fb_initnet_get_params", "fb_initnet_set_params",
+                    "fb_initnet_get_grads", "fb_initnet_forward", "fb_initnet_init_nnf",
+                    "fb_initnet_train_step", "fb_initnet_status", "fb_conv3x3_forward",
+                    "fb_conv3x3_backward", "fb_ctx_set_initnet", "fb_ctx_energy",
+                    "fb_initnet_targets")
+
+FB_FLAG_LEARNED_INIT = 0x1
+FB_FLAG_REPORT_ENERGY = 0x2
 
 FB_BATCH_NO_GRAPH = 0x1
 
@@ -116,6 +125,37 @@ def lib() -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_uint64), ctypes.POINTER(ctypes.c_uint64),
                                     ctypes.POINTER(ctypes.c_int)]
         L.fb_batch_plan.restype = ctypes.c_int
+        L.fb_initnet_create.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int]
+        L.fb_initnet_destroy.argtypes = [_vp]
+        L.fb_initnet_last_error.argtypes = [_vp]
+        L.fb_initnet_last_error.restype = ctypes.c_char_p
+        L.fb_initnet_param_count.argtypes = [_vp]
+        L.fb_initnet_param_count.restype = ctypes.c_size_t
+        for f in ("fb_initnet_get_params", "fb_initnet_set_params", "fb_initnet_get_grads"):
+            getattr(L, f).argtypes = [_vp, _vp]
+        L.fb_initnet_forward.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
+        L.fb_initnet_init_nnf.argtypes = [_vp, ctypes.c_int, _vp, _vp]
+        L.fb_initnet_train_step.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_float,
+                                            ctypes.c_float, _vp, _vp]
+        L.fb_initnet_status.argtypes = [_vp]
+        L.fb_conv3x3_forward.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, _vp, _vp, _vp, _vp]
+        L.fb_conv3x3_backward.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                          ctypes.c_int, _vp, ctypes.c_int, ctypes.c_int, _vp, _vp,
+                                          _vp, _vp, _vp]
+        for f in ("fb_initnet_create", "fb_initnet_destroy", "fb_initnet_get_params",
+                  "fb_initnet_set_params", "fb_initnet_get_grads", "fb_initnet_forward",
+                  "fb_initnet_init_nnf", "fb_initnet_train_step", "fb_initnet_status",
+                  "fb_conv3x3_forward", "fb_conv3x3_backward"):
+            getattr(L, f).restype = ctypes.c_int
+        L.fb_ctx_set_initnet.argtypes = [_vp, _vp]
+        L.fb_ctx_set_initnet.restype = ctypes.c_int
+        L.fb_ctx_energy.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]
+        L.fb_ctx_energy.restype = ctypes.c_int
+        L.fb_initnet_targets.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L.fb_initnet_targets.restype = ctypes.c_int
         L.fb_ctx_set_pair_budget.argtypes = [_vp, ctypes.c_size_t]
         L.fb_ctx_set_pair_budget.restype = ctypes.c_int
         L.fb_ctx_batch_variant.argtypes = [_vp, ctypes.c_int]
@@ -187,6 +227,16 @@ class Context:
         rate, ms = ctypes.c_double(), ctypes.c_double()
         self.check(lib().fb_probe_dp4a(self._h, ctypes.byref(rate), ctypes.byref(ms)))
         return rate.value, ms.value
+
+    def set_initnet(self, net) -> None:
+        """Attach the learned initialiser used with FB_FLAG_LEARNED_INIT (None detaches)."""
+        self.check(lib().fb_ctx_set_initnet(self._h, net.handle if net is not None else None))
+
+    def energy(self):
+        """(sum, count) of final Eq. 1 errors of the last FB_FLAG_REPORT_ENERGY call."""
+        s, c = ctypes.c_double(), ctypes.c_uint64()
+        self.check(lib().fb_ctx_energy(self._h, ctypes.byref(s), ctypes.byref(c)))
+        return s.value, c.value
 
     def set_pair_budget(self, nbytes: int) -> None:
         """Bytes of NNF scratch per chunk of pairs (0 = library default)."""
@@ -342,3 +392,139 @@ BATCH_VARIANT_NAMES = ("tile 32x8, 5 blocks/SM", "tile 32x4, 10 blocks/SM",
 
 def batch_variant_name(v: int) -> str:
     return BATCH_VARIANT_NAMES[v] if 0 <= v < len(BATCH_VARIANT_NAMES) else "untuned"
+
+
+# ----------------------------------------------------------------------------------
+# Learned NNF initialiser
+# ----------------------------------------------------------------------------------
+class InitNet:
+    """fb_initnet: the BF16 conv pyramid that proposes initial NNFs (tensor-core kernels)."""
+
+    def __init__(self, ctx: Context, max_pairs: int, H: int, W: int):
+        h = _vp()
+        rc = lib().fb_initnet_create(ctx.handle, ctypes.byref(h), max_pairs, H, W)
+        if rc != FB_OK:
+            raise FastBlendError(rc, "fb_initnet_create")
+        self._h, self.ctx, self.max_pairs, self.H, self.W = h, ctx, max_pairs, H, W
+        self.n_params = int(lib().fb_initnet_param_count(h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().fb_initnet_destroy(self._h)
+            self._h = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, rc: int) -> None:
+        if rc != FB_OK:
+            raise FastBlendError(rc, lib().fb_initnet_last_error(self._h).decode())
+
+    def get_params(self):
+        import numpy as np
+        out = np.zeros(self.n_params, np.float32)
+        self._check(lib().fb_initnet_get_params(self._h, out.ctypes.data))
+        return out
+
+    def set_params(self, p) -> None:
+        import numpy as np
+        p = np.ascontiguousarray(p, dtype=np.float32)
+        assert p.size == self.n_params
+        self._check(lib().fb_initnet_set_params(self._h, p.ctypes.data))
+
+    def get_grads(self):
+        import numpy as np
+        out = np.zeros(self.n_params, np.float32)
+        self._check(lib().fb_initnet_get_grads(self._h, out.ctypes.data))
+        return out
+
+    def forward(self, src: torch.Tensor, tgt: torch.Tensor, stream=None) -> torch.Tensor:
+        n = int(src.shape[0])
+        head = torch.empty((n, self.H // 4, self.W // 4, 8), dtype=torch.float32, device=src.device)
+        self._check(lib().fb_initnet_forward(self._h, _ptr(src, torch.uint8, "src"),
+                                             _ptr(tgt, torch.uint8, "tgt"), n,
+                                             _ptr(head, torch.float32, "head"),
+                                             _stream_handle(stream, self.ctx.device)))
+        return head
+
+    def init_nnf(self, n: int, stream=None) -> torch.Tensor:
+        out = torch.empty((n, self.H, self.W, 2), dtype=torch.int32, device="cuda")
+        self._check(lib().fb_initnet_init_nnf(self._h, n, out.data_ptr(),
+                                              _stream_handle(stream, self.ctx.device)))
+        return out
+
+    def train_step(self, src, tgt, target, weight=None, weight_sum=None, lr=1e-3,
+                   loss_out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+        n = int(src.shape[0])
+        if loss_out is None:
+            loss_out = torch.zeros(1, dtype=torch.float32, device=src.device)
+        if weight_sum is None:
+            weight_sum = float(weight.sum()) if weight is not None else float(
+                n * (self.H // 4) * (self.W // 4))
+        self._check(lib().fb_initnet_train_step(
+            self._h, _ptr(src, torch.uint8, "src"), _ptr(tgt, torch.uint8, "tgt"), n,
+            _ptr(target, torch.float32, "target"),
+            _ptr(weight, torch.float32, "weight") if weight is not None else None,
+            float(weight_sum), float(lr), _ptr(loss_out, torch.float32, "loss"),
+            _stream_handle(stream, self.ctx.device)))
+        return loss_out
+
+    def status(self) -> int:
+        return int(lib().fb_initnet_status(self._h))
+
+
+def fb_initnet_targets(nnf: torch.Tensor, stream=None):
+    """Targets (n,H/4,W/4,2) and weights (n,H/4,W/4) from Alg. 1 fields (n,H,W,2) int32."""
+    n, H, W = (int(v) for v in nnf.shape[:3])
+    target = torch.empty((n, H // 4, W // 4, 2), dtype=torch.float32, device=nnf.device)
+    weight = torch.empty((n, H // 4, W // 4), dtype=torch.float32, device=nnf.device)
+    rc = lib().fb_initnet_targets(_ptr(nnf, torch.int32, "nnf"), n, H, W, target.data_ptr(),
+                                  weight.data_ptr(), _stream_handle(stream, nnf.device.index or 0))
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_initnet_targets")
+    return target, weight
+
+
+def conv3x3_forward(x: torch.Tensor, w: torch.Tensor, bias: torch.Tensor, stride: int, relu: bool,
+                    out_f32: bool = False, status: Optional[torch.Tensor] = None):
+    """One 3x3 conv layer on the tensor cores (bf16 NHWC x, bf16 [Cout,3,3,Cin] w)."""
+    n, H, W, Cin = (int(v) for v in x.shape)
+    Cout = int(w.shape[0])
+    Ho, Wo = (H + stride - 1) // stride, (W + stride - 1) // stride
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=x.device)
+    y = torch.empty((n, Ho, Wo, Cout), dtype=torch.float32 if out_f32 else torch.bfloat16,
+                    device=x.device)
+    rc = lib().fb_conv3x3_forward(_ptr(x, torch.bfloat16, "x"), n, H, W, Cin,
+                                  _ptr(w, torch.bfloat16, "w"), _ptr(bias, torch.float32, "bias"),
+                                  Cout, stride, int(relu),
+                                  None if out_f32 else y.data_ptr(), y.data_ptr() if out_f32 else None,
+                                  status.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_conv3x3_forward")
+    return y, status
+
+
+def conv3x3_backward(x: torch.Tensor, wt: torch.Tensor, dz: torch.Tensor, stride: int,
+                     status: Optional[torch.Tensor] = None):
+    """(dx f32, dw f32) of one conv layer; wt = weights transposed to [Cin,3,3,Cout] bf16."""
+    n, H, W, Cin = (int(v) for v in x.shape)
+    Cout = int(dz.shape[-1])
+    if status is None:
+        status = torch.zeros(1, dtype=torch.int32, device=x.device)
+    dx = torch.empty((n, H, W, Cin), dtype=torch.float32, device=x.device)
+    dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device=x.device)
+    rc = lib().fb_conv3x3_backward(_ptr(x, torch.bfloat16, "x"), n, H, W, Cin,
+                                   _ptr(wt, torch.bfloat16, "wt"), Cout, stride,
+                                   _ptr(dz, torch.bfloat16, "dz"), dx.data_ptr(), dw.data_ptr(),
+                                   status.data_ptr(), torch.cuda.current_stream().cuda_stream)
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_conv3x3_backward")
+    return dx, dw, status

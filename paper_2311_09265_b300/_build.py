@@ -10,7 +10,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 LIB_PATH = os.path.join(PKG, "libfb.so")
-SOURCES = ["fb_api.cu", "fb_kernels.cu", "fb_batch.cu", "fb_calib.cu", "fb_noalloc.cu"]
+SOURCES = ["fb_api.cu", "fb_kernels.cu", "fb_batch.cu", "fb_net.cu", "fb_calib.cu", "fb_noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

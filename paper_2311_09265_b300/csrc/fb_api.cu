@@ -36,6 +36,9 @@ struct fb_ctx {
     // Batched submissions: tuned tile variant per patch size, and the cached manifests.
     int tuned_variant[10] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
     size_t pair_budget = 0;  // bytes of NNF scratch per chunk; 0 = kPairBudgetBytes
+    fb_initnet* init_net = nullptr;  // learned initialiser for FB_FLAG_LEARNED_INIT
+    double* energy = nullptr;        // device: sum of final errors (FB_FLAG_REPORT_ENERGY)
+    uint64_t energy_count = 0;
     struct BatchEntry;
     std::vector<BatchEntry*> batch_cache;  // most recent last
 };
@@ -204,7 +207,8 @@ int check_params(fb_ctx* ctx, const fb_params* p, int H, int W) {
         return fail(ctx, FB_ERR_ARG, "levels must be in [1, 16], got %d", p->levels);
     if (p->r0 < 0 || p->r0 > (1 << 20))
         return fail(ctx, FB_ERR_ARG, "r0 must be in [0, 2^20], got %d", p->r0);
-    if (p->flags != 0) return fail(ctx, FB_ERR_ARG, "flags must be 0");
+    if (p->flags & ~(FB_FLAG_LEARNED_INIT | FB_FLAG_REPORT_ENERGY))
+        return fail(ctx, FB_ERR_ARG, "unknown flags 0x%x", p->flags);
     if (H < p->patch || W < p->patch || H > 32767 || W > 32767)
         return fail(ctx, FB_ERR_ARG, "image %dx%d outside [patch, 32767]", H, W);
     return FB_OK;
@@ -233,6 +237,7 @@ struct Buffers {
     uint32_t* rec[16] = {};   // row patches per level
     uint32_t* styles = nullptr;
     uint32_t *FA = nullptr, *FB = nullptr, *EA = nullptr, *EB = nullptr;
+    int32_t* init = nullptr;     // learned initial fields of a chunk (int32 pairs)
     PairDesc* pairs = nullptr;
     JobDesc* jobs = nullptr;
     uint8_t* in_guides = nullptr;  // host-staging copies
@@ -242,7 +247,7 @@ struct Buffers {
 
 void carve(Carver& cv, Buffers& b, const Levels& L, int k, int n_guides, int n_styles,
            size_t chunk_pairs, size_t n_pairs, size_t n_jobs, bool staging, size_t guide_bytes,
-           size_t style_bytes, size_t out_floats) {
+           size_t style_bytes, size_t out_floats, bool learned = false) {
     const int recw = fb::rowpatch_words(k);
     for (int l = 0; l < L.n; ++l) {
         const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];
@@ -255,6 +260,7 @@ void carve(Carver& cv, Buffers& b, const Levels& L, int k, int n_guides, int n_s
     b.FB = cv.take<uint32_t>(chunk_pairs * npx0);
     b.EA = cv.take<uint32_t>(chunk_pairs * npx0);
     b.EB = cv.take<uint32_t>(chunk_pairs * npx0);
+    if (learned) b.init = cv.take<int32_t>(chunk_pairs * npx0 * 2);
     b.pairs = cv.take<PairDesc>(n_pairs > 0 ? n_pairs : 1);
     b.jobs = cv.take<JobDesc>(n_jobs > 0 ? n_jobs : 1);
     if (staging) {
@@ -389,15 +395,24 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
     const size_t guide_bytes = static_cast<size_t>(N) * npx0 * 3;
     const size_t style_bytes = static_cast<size_t>(n_styles) * npx0 * 3;
     const size_t out_floats = static_cast<size_t>(N) * npx0 * 3;
+    const bool learned = (p->flags & FB_FLAG_LEARNED_INIT) != 0;
+    if (learned) {
+        if (!ctx->init_net) return fail(ctx, FB_ERR_ARG, "FB_FLAG_LEARNED_INIT without fb_ctx_set_initnet");
+        int nh = 0, nw = 0;
+        fb::initnet_dims(ctx->init_net, &nh, &nw);
+        if (nh != H || nw != W || p->levels != 1)
+            return fail(ctx, FB_ERR_ARG, "the learned initialiser was built for %dx%d frames and levels == 1",
+                        nh, nw);
+    }
     Buffers b;
     Carver measure(nullptr);
     carve(measure, b, L, k, N, n_styles, max_pairs, pairs.size(), jobs.size(), staging, guide_bytes,
-          style_bytes, out_floats);
+          style_bytes, out_floats, learned);
     rc = ensure_arena(ctx, measure.off);
     if (rc) return rc;
     Carver cv(ctx->arena);
     carve(cv, b, L, k, N, n_styles, max_pairs, pairs.size(), jobs.size(), staging, guide_bytes,
-          style_bytes, out_floats);
+          style_bytes, out_floats, learned);
 
     rc = upload_tables(ctx, pairs, jobs, b, st);
     if (rc) return rc;
@@ -416,11 +431,34 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
     if (rc) return rc;
     FB_LAUNCH(ctx, st, FB_K_STYLE, fb::launch_style_rgbx(s_dev, static_cast<size_t>(n_styles) * npx0, b.styles, st));
 
+    if (p->flags & FB_FLAG_REPORT_ENERGY) {
+        FB_CUDA(ctx, cudaMemsetAsync(ctx->energy, 0, sizeof(double), st));
+        ctx->energy_count = 0;
+    }
     for (const Chunk& c : chunks) {
         uint32_t *F = nullptr, *E = nullptr;
         if (c.n_pairs > 0) {
-            rc = run_nnf(ctx, b, L, p, c.pair0, c.n_pairs, nullptr, st, &F, &E);
+            const int32_t* init = nullptr;
+            if (p->flags & FB_FLAG_LEARNED_INIT) {
+                // Initial fields of the chunk's pairs from the learned initialiser, in
+                // batches of at most its capacity, into the learned-init buffer.
+                const int cap = fb::initnet_max_pairs(ctx->init_net);
+                for (int q = 0; q < c.n_pairs; q += cap) {
+                    const int cnt = c.n_pairs - q < cap ? c.n_pairs - q : cap;
+                    int r2 = fb::initnet_init_pairs(ctx->init_net, g_dev, b.pairs, c.pair0 + q, cnt,
+                                                    b.init + static_cast<size_t>(q) * npx0 * 2, st);
+                    if (r2) return fail(ctx, r2, "learned initialiser failed");
+                    ctx->launches += 17;  // input, 3 concatenations, 12 convolutions, offsets
+                }
+                init = b.init;
+            }
+            rc = run_nnf(ctx, b, L, p, c.pair0, c.n_pairs, init, st, &F, &E);
             if (rc) return rc;
+            if (p->flags & FB_FLAG_REPORT_ENERGY) {
+                FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_energy_sum(E, static_cast<size_t>(c.n_pairs) * npx0,
+                                                                   ctx->energy, st));
+                ctx->energy_count += static_cast<uint64_t>(c.n_pairs) * npx0;
+            }
         }
         FB_LAUNCH(ctx, st, FB_K_COMBINE, fb::launch_combine(k, b.jobs, c.job0, c.n_jobs, b.pairs, c.pair0, F,
                                           b.styles, H, W, o_dev, st));
@@ -839,6 +877,20 @@ extern "C" int fb_batch_plan(const fb_clip_desc* clips, int n_clips, const fb_pa
     return FB_OK;
 }
 
+extern "C" int fb_ctx_set_initnet(fb_ctx* ctx, fb_initnet* net) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->init_net = net;
+    return FB_OK;
+}
+
+extern "C" int fb_ctx_energy(fb_ctx* ctx, double* sum, uint64_t* count) {
+    if (!ctx || !sum || !count) return fail(ctx, FB_ERR_ARG, "NULL argument");
+    DeviceGuard dg(ctx->device);
+    FB_CUDA(ctx, cudaMemcpy(sum, ctx->energy, sizeof(double), cudaMemcpyDeviceToHost));
+    *count = ctx->energy_count;
+    return FB_OK;
+}
+
 extern "C" int fb_ctx_set_pair_budget(fb_ctx* ctx, size_t bytes) {
     if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
     if (bytes != 0 && bytes < (size_t(1) << 20))
@@ -922,7 +974,9 @@ int fb_ctx_create(fb_ctx** out, int device) {
     ctx->device = device;
     if (cudaEventCreateWithFlags(&ctx->upload_done, cudaEventDisableTiming) != cudaSuccess ||
         cudaMalloc(reinterpret_cast<void**>(&ctx->dev_status), sizeof(int)) != cudaSuccess ||
-        cudaMemset(ctx->dev_status, 0, sizeof(int)) != cudaSuccess) {
+        cudaMemset(ctx->dev_status, 0, sizeof(int)) != cudaSuccess ||
+        cudaMalloc(reinterpret_cast<void**>(&ctx->energy), sizeof(double)) != cudaSuccess ||
+        cudaMemset(ctx->energy, 0, sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         if (ctx->upload_done) cudaEventDestroy(ctx->upload_done);
         if (ctx->dev_status) cudaFree(ctx->dev_status);
@@ -941,6 +995,7 @@ int fb_ctx_destroy(fb_ctx* ctx) {
     if (ctx->pinned) cudaFreeHost(ctx->pinned);
     if (ctx->upload_done) cudaEventDestroy(ctx->upload_done);
     if (ctx->dev_status) cudaFree(ctx->dev_status);
+    if (ctx->energy) cudaFree(ctx->energy);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
     for (fb_ctx::BatchEntry* be : ctx->batch_cache) {
         if (be->exec) cudaGraphExecDestroy(be->exec);

@@ -7,6 +7,8 @@
 
 #include <cuda_runtime.h>
 
+#include "fb.h"
+
 namespace fb {
 
 // NNF entries on the device are packed (row << 16) | col; H, W <= 32767.
@@ -64,6 +66,17 @@ cudaError_t launch_nnf_pack(const int32_t* nnf, int H, int W, uint32_t* F, cudaS
 cudaError_t launch_combine(int k, const JobDesc* jobs, int job0, int n_jobs,
                            const PairDesc* pairs, int pair0, const uint32_t* F,
                            const uint32_t* styles, int H, int W, float* out, cudaStream_t st);
+
+cudaError_t launch_energy_sum(const uint32_t* E, size_t n, double* acc, cudaStream_t st);
+
+// ---- learned initialiser (fb_net.cu), used by the blend / interpolation pipeline ----
+// Forward pass of `net` on pairs [first, first + n) of a pair table over the guide
+// stack `guides` (H x W frames), then the initial fields F0 of those pairs written as
+// n x H x W x 2 int32 to nnf_out.  Returns an fb_status.
+int initnet_init_pairs(::fb_initnet* net, const uint8_t* guides, const PairDesc* pairs, int first,
+                       int n, int32_t* nnf_out, cudaStream_t st);
+int initnet_max_pairs(const ::fb_initnet* net);
+void initnet_dims(const ::fb_initnet* net, int* H, int* W);
 
 // ---- batched persistent path (fb_batch.cu) --------------------------------------
 // One clip of a batch submission (device table).

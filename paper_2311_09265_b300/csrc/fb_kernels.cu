@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
     init_pixel<K>(rp + static_cast<size_t>(pd.src) * npx * G::RPW,
                   rp + static_cast<size_t>(pd.tgt) * npx * G::RPW, H, W, tc.r, tc.c, pd.tag, mode,
                   coarse_F ? coarse_F + static_cast<size_t>(pl) * Hc * Wc : nullptr, Hc, Wc,
-                  user_init, key0, key1,
+                  user_init ? user_init + static_cast<size_t>(pl) * npx * 2 : nullptr, key0, key1,
                   level_word, F + static_cast<size_t>(pl) * npx, E + static_cast<size_t>(pl) * npx);
 }
 
@@ -231,6 +231,23 @@ __global__ void __launch_bounds__(TILE_THREADS)
     write_output(out + (static_cast<size_t>(job.out_frame) * npx + x) * 3, a0, a1, a2, job.den);
 }
 
+// Sum of the Eq. 1 errors of n_elems values (double accumulator).
+__global__ void __launch_bounds__(256) energy_sum_kernel(const uint32_t* __restrict__ E, size_t n,
+                                                         double* __restrict__ acc) {
+    double s = 0.0;
+    for (size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * blockDim.x)
+        s += E[i];
+    __shared__ double red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = 128; w > 0; w >>= 1) {
+        if (static_cast<int>(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(acc, red[0]);
+}
+
 inline dim3 tile_grid(int H, int W, int n) {
     const unsigned tiles = static_cast<unsigned>(((W + TILE_W - 1) / TILE_W) *
                                                  ((H + TILE_H - 1) / TILE_H));
@@ -302,6 +319,12 @@ cudaError_t launch_nnf_iter(int k, const PairDesc* pairs, int pair0, int n_pairs
                          pairs, pair0, g.H, g.W, g.rp, r0,
                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32),
                          ctr_word, Fp, Ep, Fn, En)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_sum(const uint32_t* E, size_t n, double* acc, cudaStream_t st) {
+    if (n == 0) return cudaSuccess;
+    energy_sum_kernel<<<1184, 256, 0, st>>>(E, n, acc);
     return cudaGetLastError();
 }
 

@@ -1,0 +1,731 @@
+// fb_net.cu -- the learned NNF initialiser: a small BF16 convolutional pyramid that
+// maps a pair of guide frames to an offset field, used to start Alg. 1 close to its
+// answer so that fewer iterations are needed.  The paper's method is model-free; this
+// network is an addition that the method itself trains (targets are NNFs computed by
+// Alg. 1).  Convolutions run on tcgen05 (fb_net_ops.cuh); training (forward, loss,
+// backward, Adam) runs entirely in this file's kernels.
+//
+// Network, at a quarter of the guide resolution (Hq = H/4, Wq = W/4), NHWC bf16:
+//   in    8 ch: source RGB, target RGB (each 4x4 box mean / 255 - 0.5), 2 zero ch
+//   e0a 8->32, e0b 32->32            (Hq)
+//   e1a 32->64 /2, e1b 64->64        (Hq/2)
+//   e2a 64->96 /2, e2b 96->96        (Hq/4)
+//   e3a 96->128 /2, e3b 128->128     (Hq/8)
+//   d2  [up(e3b), e2b] 224->96       (Hq/4)
+//   d1  [up(d2), e1b] 160->64        (Hq/2)
+//   d0  [up(d1), e0b] 96->32         (Hq)
+//   head 32->8 (channels 0,1 used): offset = 16 * head, in full-resolution pixels
+// 3x3 kernels, zero padding, ReLU after every layer but the head; 779,592 parameters.
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fb.h"
+#include "fb_internal.h"
+#include "fb_net_ops.cuh"
+
+namespace fb {
+namespace net {
+namespace {
+
+constexpr int kOffsetScale = 16;
+
+// ---------------------------------------------------------------------------------
+// Conv launchers
+// ---------------------------------------------------------------------------------
+template <int BN, class G, class E>
+cudaError_t launch_gemm(const G& gth, const E& epi, int M, int N, int K, int splits, int* status,
+                        cudaStream_t st) {
+    const int chunks = (K + tc::BK - 1) / tc::BK;
+    if (splits < 1) splits = 1;
+    if (splits > chunks) splits = chunks;
+    const int per = (chunks + splits - 1) / splits;
+    splits = (chunks + per - 1) / per;
+    const dim3 grid((M + tc::BM - 1) / tc::BM, (N + BN - 1) / BN, splits);
+    constexpr int smem = tc::gemm_smem_bytes<BN>();
+    auto kern = tc::tc_gemm_kernel<BN, G, E>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 128, smem, st>>>(gth, epi, M, N, K, per, status);
+    return cudaGetLastError();
+}
+
+cudaError_t conv_forward(const ConvGeom& g, const bf16* X, const bf16* Wt, const float* bias,
+                         int relu, bf16* Y, float* Yf, int* status, cudaStream_t st) {
+    const int M = g.n * g.Ho * g.Wo, K = 9 * g.Cin;
+    EpiFwd epi{Y, Yf, bias, g.Cout, relu};
+    if (g.Cout <= 16) return launch_gemm<16>(GatherFwd<16>{X, Wt, g, M, K}, epi, M, g.Cout, K, 1, status, st);
+    if (g.Cout <= 32) return launch_gemm<32>(GatherFwd<32>{X, Wt, g, M, K}, epi, M, g.Cout, K, 1, status, st);
+    if (g.Cout <= 64) return launch_gemm<64>(GatherFwd<64>{X, Wt, g, M, K}, epi, M, g.Cout, K, 1, status, st);
+    return launch_gemm<128>(GatherFwd<128>{X, Wt, g, M, K}, epi, M, g.Cout, K, 1, status, st);
+}
+
+cudaError_t conv_dgrad(const ConvGeom& g, const bf16* dZ, const bf16* WT, float* dX, int accumulate,
+                       int* status, cudaStream_t st) {
+    const int M = g.n * g.H * g.W, K = 9 * g.Cout;
+    EpiDgrad epi{dX, g.Cin, accumulate};
+    if (g.Cin <= 16) return launch_gemm<16>(GatherDgrad<16>{dZ, WT, g, M, K}, epi, M, g.Cin, K, 1, status, st);
+    if (g.Cin <= 32) return launch_gemm<32>(GatherDgrad<32>{dZ, WT, g, M, K}, epi, M, g.Cin, K, 1, status, st);
+    if (g.Cin <= 64) return launch_gemm<64>(GatherDgrad<64>{dZ, WT, g, M, K}, epi, M, g.Cin, K, 1, status, st);
+    return launch_gemm<128>(GatherDgrad<128>{dZ, WT, g, M, K}, epi, M, g.Cin, K, 1, status, st);
+}
+
+cudaError_t conv_wgrad(const ConvGeom& g, const bf16* dZ, const bf16* X, float* dW, int sms,
+                       int* status, cudaStream_t st) {
+    const int P = g.n * g.Ho * g.Wo, N = 9 * g.Cin;
+    const int ntiles = (N + 127) / 128;
+    const int splits = (2 * sms + ntiles - 1) / ntiles;
+    return launch_gemm<128>(GatherWgrad<128>{dZ, X, g, P}, EpiWgrad{dW, N}, g.Cout, N, P, splits,
+                            status, st);
+}
+
+// ---------------------------------------------------------------------------------
+// Elementwise kernels
+// ---------------------------------------------------------------------------------
+inline unsigned blocks(size_t n, unsigned per = 256) { return static_cast<unsigned>((n + per - 1) / per); }
+
+// Network input: 4x4 box means of both guides, scaled to [-0.5, 0.5], 8 channels.
+__global__ void prep_input_kernel(const uint8_t* __restrict__ src, const uint8_t* __restrict__ tgt,
+                                  int n, int H, int W, bf16* __restrict__ out) {
+    const int Hq = H / 4, Wq = W / 4;
+    const size_t total = static_cast<size_t>(n) * Hq * Wq;
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int img = static_cast<int>(i / (static_cast<size_t>(Hq) * Wq));
+    const int rem = static_cast<int>(i - static_cast<size_t>(img) * Hq * Wq);
+    const int qy = rem / Wq, qx = rem % Wq;
+    float s[6] = {0, 0, 0, 0, 0, 0};
+    for (int dy = 0; dy < 4; ++dy)
+        for (int dx = 0; dx < 4; ++dx) {
+            const size_t p = ((static_cast<size_t>(img) * H + 4 * qy + dy) * W + 4 * qx + dx) * 3;
+            for (int ch = 0; ch < 3; ++ch) {
+                s[ch] += src[p + ch];
+                s[3 + ch] += tgt[p + ch];
+            }
+        }
+    bf16* o = out + i * 8;
+    for (int ch = 0; ch < 6; ++ch) o[ch] = __float2bfloat16_rn(s[ch] / (16.f * 255.f) - 0.5f);
+    o[6] = o[7] = __float2bfloat16_rn(0.f);
+}
+
+// The same input built from a guide stack and pairs [first, first + n) of a pair table.
+__global__ void prep_input_pairs_kernel(const uint8_t* __restrict__ guides,
+                                        const fb::PairDesc* __restrict__ pairs, int first, int n,
+                                        int H, int W, bf16* __restrict__ out) {
+    const int Hq = H / 4, Wq = W / 4;
+    const size_t total = static_cast<size_t>(n) * Hq * Wq;
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int img = static_cast<int>(i / (static_cast<size_t>(Hq) * Wq));
+    const int rem = static_cast<int>(i - static_cast<size_t>(img) * Hq * Wq);
+    const int qy = rem / Wq, qx = rem % Wq;
+    const fb::PairDesc pd = pairs[first + img];
+    const size_t fsz = static_cast<size_t>(H) * W * 3;
+    const uint8_t* src = guides + static_cast<size_t>(pd.src) * fsz;
+    const uint8_t* tgt = guides + static_cast<size_t>(pd.tgt) * fsz;
+    float s[6] = {0, 0, 0, 0, 0, 0};
+    for (int dy = 0; dy < 4; ++dy)
+        for (int dx = 0; dx < 4; ++dx) {
+            const size_t p = (static_cast<size_t>(4 * qy + dy) * W + 4 * qx + dx) * 3;
+            for (int ch = 0; ch < 3; ++ch) {
+                s[ch] += src[p + ch];
+                s[3 + ch] += tgt[p + ch];
+            }
+        }
+    bf16* o = out + i * 8;
+    for (int ch = 0; ch < 6; ++ch) o[ch] = __float2bfloat16_rn(s[ch] / (16.f * 255.f) - 0.5f);
+    o[6] = o[7] = __float2bfloat16_rn(0.f);
+}
+
+// Training targets from Alg. 1 fields: the mean offset F(x) - x over each 4x4 block,
+// with weight 1 where all 16 offsets lie within 2 pixels of that mean (one coherent
+// motion), else 0.
+__global__ void nnf_targets_kernel(const int32_t* __restrict__ nnf, int n, int H, int W,
+                                   float* __restrict__ target, float* __restrict__ weight) {
+    const int Hq = H / 4, Wq = W / 4;
+    const size_t total = static_cast<size_t>(n) * Hq * Wq;
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int img = static_cast<int>(i / (static_cast<size_t>(Hq) * Wq));
+    const int rem = static_cast<int>(i - static_cast<size_t>(img) * Hq * Wq);
+    const int qy = rem / Wq, qx = rem % Wq;
+    float oy[16], ox[16], my = 0.f, mx = 0.f;
+    for (int j = 0; j < 16; ++j) {
+        const int y = 4 * qy + j / 4, x = 4 * qx + j % 4;
+        const size_t p = (static_cast<size_t>(img) * H + y) * W + x;
+        oy[j] = static_cast<float>(nnf[2 * p] - y);
+        ox[j] = static_cast<float>(nnf[2 * p + 1] - x);
+        my += oy[j];
+        mx += ox[j];
+    }
+    my *= (1.f / 16.f);
+    mx *= (1.f / 16.f);
+    bool ok = true;
+    for (int j = 0; j < 16; ++j) ok = ok && fabsf(oy[j] - my) <= 2.f && fabsf(ox[j] - mx) <= 2.f;
+    target[2 * i] = my;
+    target[2 * i + 1] = mx;
+    if (weight) weight[i] = ok ? 1.f : 0.f;
+}
+
+// out[n][2h][2w][C1+C2] = [nearest-upsampled lo, skip]
+__global__ void concat_up_kernel(const bf16* __restrict__ lo, int C1, const bf16* __restrict__ skip,
+                                 int C2, int n, int H2, int W2, bf16* __restrict__ out) {
+    const int C = C1 + C2;
+    const size_t total = static_cast<size_t>(n) * H2 * W2 * (C / 8);
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int u = static_cast<int>(i % (C / 8));
+    const size_t pix = i / (C / 8);
+    const int img = static_cast<int>(pix / (static_cast<size_t>(H2) * W2));
+    const int rem = static_cast<int>(pix - static_cast<size_t>(img) * H2 * W2);
+    const int y = rem / W2, x = rem % W2;
+    const int c = 8 * u;
+    uint4 v;
+    if (c < C1) {
+        const size_t lp = (static_cast<size_t>(img) * (H2 / 2) + y / 2) * (W2 / 2) + x / 2;
+        v = *reinterpret_cast<const uint4*>(lo + lp * C1 + c);
+    } else {
+        v = *reinterpret_cast<const uint4*>(skip + pix * C2 + (c - C1));
+    }
+    *reinterpret_cast<uint4*>(out + pix * C + c) = v;
+}
+
+// Gradient of concat_up: dlo[n][h][w][C1] += sum over the 2x2 block, dskip += its part.
+__global__ void concat_up_bwd_kernel(const float* __restrict__ dout, int C1, int C2, int n, int H2,
+                                     int W2, float* __restrict__ dlo, float* __restrict__ dskip) {
+    const int C = C1 + C2;
+    const int H = H2 / 2, W = W2 / 2;
+    const size_t lo_total = static_cast<size_t>(n) * H * W * C1;
+    const size_t sk_total = static_cast<size_t>(n) * H2 * W2 * C2;
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i < lo_total) {
+        const int c = static_cast<int>(i % C1);
+        const size_t p = i / C1;
+        const int img = static_cast<int>(p / (static_cast<size_t>(H) * W));
+        const int rem = static_cast<int>(p - static_cast<size_t>(img) * H * W);
+        const int y = rem / W, x = rem % W;
+        float s = 0.f;
+        for (int dy = 0; dy < 2; ++dy)
+            for (int dx = 0; dx < 2; ++dx)
+                s += dout[((static_cast<size_t>(img) * H2 + 2 * y + dy) * W2 + 2 * x + dx) * C + c];
+        dlo[i] += s;
+    } else if (i < lo_total + sk_total) {
+        const size_t j = i - lo_total;
+        const int c = static_cast<int>(j % C2);
+        const size_t p = j / C2;
+        dskip[j] += dout[p * C + C1 + c];
+    }
+}
+
+// dZ = dA * (A > 0) in bf16 (ReLU backward); relu == 0 passes dA through.
+__global__ void relu_bwd_kernel(const float* __restrict__ dA, const bf16* __restrict__ A, size_t n,
+                                int relu, bf16* __restrict__ dZ) {
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    float g = dA[i];
+    if (relu && !(__bfloat162float(A[i]) > 0.f)) g = 0.f;
+    dZ[i] = __float2bfloat16_rn(g);
+}
+
+// db[c] += sum_p dZ[p][c]
+__global__ void bias_grad_kernel(const bf16* __restrict__ dZ, size_t P, int C, float* __restrict__ db) {
+    const int c = blockIdx.x;
+    float s = 0.f;
+    for (size_t p = threadIdx.x; p < P; p += blockDim.x) s += __bfloat162float(dZ[p * C + c]);
+    __shared__ float red[256];
+    red[threadIdx.x] = s;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (static_cast<int>(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) db[c] += red[0];
+}
+
+// Smooth-L1 (Huber, delta 1 pixel) between 16 * head[..., 0:2] and the target offsets,
+// weighted, averaged over the weight sum.  Writes dHead (fp32, 8 channels) and adds the
+// loss to *loss.
+__global__ void offset_loss_kernel(const float* __restrict__ head, const float* __restrict__ target,
+                                   const float* __restrict__ weight, size_t P, float inv_wsum,
+                                   float* __restrict__ dhead, float* __restrict__ loss) {
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    float l = 0.f;
+    if (i < P) {
+        const float w = weight ? weight[i] : 1.f;
+        for (int ch = 0; ch < 8; ++ch) dhead[i * 8 + ch] = 0.f;
+        for (int ch = 0; ch < 2; ++ch) {
+            const float d = kOffsetScale * head[i * 8 + ch] - target[i * 2 + ch];
+            const float ad = fabsf(d);
+            l += w * (ad < 1.f ? 0.5f * d * d : ad - 0.5f);
+            const float g = ad < 1.f ? d : (d > 0.f ? 1.f : -1.f);
+            dhead[i * 8 + ch] = w * g * kOffsetScale * inv_wsum;
+        }
+    }
+    __shared__ float red[256];
+    red[threadIdx.x] = l;
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (static_cast<int>(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) atomicAdd(loss, red[0] * inv_wsum);
+}
+
+// fp32 master weights [Cout][9][Cin] -> bf16 copy and bf16 transpose [Cin][9][Cout].
+__global__ void weights_to_bf16_kernel(const float* __restrict__ w, int Cout, int Cin,
+                                       bf16* __restrict__ wb, bf16* __restrict__ wt) {
+    const size_t n = static_cast<size_t>(Cout) * 9 * Cin;
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int ci = static_cast<int>(i % Cin);
+    const int tap = static_cast<int>((i / Cin) % 9);
+    const int co = static_cast<int>(i / (9 * static_cast<size_t>(Cin)));
+    const bf16 v = __float2bfloat16_rn(w[i]);
+    wb[i] = v;
+    wt[(static_cast<size_t>(ci) * 9 + tap) * Cout + co] = v;
+}
+
+__global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, float* __restrict__ m,
+                            float* __restrict__ v, size_t n, float lr, float b1, float b2, float eps,
+                            float c1, float c2) {
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+// Initial NNF from predicted offsets: F0(x) = clamp(x + rint(offset(x / 4))).
+__global__ void offsets_to_nnf_kernel(const float* __restrict__ head, int n, int H, int W,
+                                      int32_t* __restrict__ nnf) {
+    const size_t total = static_cast<size_t>(n) * H * W;
+    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (i >= total) return;
+    const int img = static_cast<int>(i / (static_cast<size_t>(H) * W));
+    const int rem = static_cast<int>(i - static_cast<size_t>(img) * H * W);
+    const int y = rem / W, x = rem % W;
+    const int Hq = H / 4, Wq = W / 4;
+    const size_t q = (static_cast<size_t>(img) * Hq + min(y / 4, Hq - 1)) * Wq + min(x / 4, Wq - 1);
+    const float dy = kOffsetScale * head[q * 8 + 0], dx = kOffsetScale * head[q * 8 + 1];
+    const int ry = y + static_cast<int>(rintf(fminf(fmaxf(dy, -32768.f), 32768.f)));
+    const int rx = x + static_cast<int>(rintf(fminf(fmaxf(dx, -32768.f), 32768.f)));
+    nnf[2 * i] = min(max(ry, 0), H - 1);
+    nnf[2 * i + 1] = min(max(rx, 0), W - 1);
+}
+
+// ---------------------------------------------------------------------------------
+// Network
+// ---------------------------------------------------------------------------------
+struct LayerDef {
+    int cin, cout, stride, relu;
+};
+// e0a e0b e1a e1b e2a e2b e3a e3b d2 d1 d0 head
+constexpr LayerDef kLayers[12] = {
+    {8, 32, 1, 1},    {32, 32, 1, 1},   {32, 64, 2, 1},  {64, 64, 1, 1},
+    {64, 96, 2, 1},   {96, 96, 1, 1},   {96, 128, 2, 1}, {128, 128, 1, 1},
+    {224, 96, 1, 1},  {160, 64, 1, 1},  {96, 32, 1, 1},  {32, 8, 1, 0}};
+constexpr int kNumLayers = 12;
+
+size_t layer_weights(int l) { return static_cast<size_t>(kLayers[l].cout) * 9 * kLayers[l].cin; }
+
+}  // namespace
+}  // namespace net
+}  // namespace fb
+
+using fb::net::bf16;
+using fb::net::ConvGeom;
+using fb::net::kLayers;
+using fb::net::kNumLayers;
+
+struct fb_initnet {
+    fb_ctx* ctx = nullptr;
+    int device = 0;
+    int max_pairs = 0, H = 0, W = 0;
+    int sms = 0;
+    size_t n_params = 0;                    // weights + biases
+    size_t w_off[kNumLayers], b_off[kNumLayers];
+    float* params = nullptr;                // fp32 master: [w0 b0 w1 b1 ...]
+    float* grads = nullptr;
+    float* adam_m = nullptr;
+    float* adam_v = nullptr;
+    bf16* wb = nullptr;                     // bf16 weights, per layer at w_off
+    bf16* wt = nullptr;                     // bf16 transposed weights
+    // activations (bf16) and gradients (fp32), sized for max_pairs
+    bf16* act[16] = {};
+    float* dact[16] = {};
+    bf16* dz = nullptr;                     // scratch: bf16 dZ of the largest layer
+    float* head = nullptr;                  // fp32 head output [P][8]
+    float* loss = nullptr;
+    int* status = nullptr;
+    uint64_t step = 0;
+    char* arena = nullptr;
+    std::string err;
+};
+
+namespace {
+
+using fb::net::ConvGeom;
+
+int net_fail(fb_initnet* net, int status, const char* msg) {
+    if (net) net->err = msg;
+    return status;
+}
+
+#define NET_CUDA(net, expr)                                                  \
+    do {                                                                     \
+        cudaError_t e_ = (expr);                                             \
+        if (e_ != cudaSuccess) {                                             \
+            cudaGetLastError();                                              \
+            return net_fail(net, FB_ERR_CUDA, cudaGetErrorString(e_));       \
+        }                                                                    \
+    } while (0)
+
+// Spatial size (Hq-relative divisor) of each tensor:
+//   act[0]=input(1) act[1]=e0a act[2]=e0b(1) act[3]=e1a act[4]=e1b(2) act[5]=e2a
+//   act[6]=e2b(4) act[7]=e3a act[8]=e3b(8) act[9]=cat2(4) act[10]=d2(4) act[11]=cat1(2)
+//   act[12]=d1(2) act[13]=cat0(1) act[14]=d0(1)
+struct Tens {
+    int div, ch;
+};
+constexpr Tens kTens[15] = {{1, 8},   {1, 32},  {1, 32},  {2, 64},  {2, 64},
+                            {4, 96},  {4, 96},  {8, 128}, {8, 128}, {4, 224},
+                            {4, 96},  {2, 160}, {2, 64},  {1, 96},  {1, 32}};
+// layer l: input tensor, output tensor
+constexpr int kIn[12] = {0, 1, 2, 3, 4, 5, 6, 7, 9, 11, 13, 14};
+constexpr int kOut[12] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, -1};
+
+ConvGeom geom(const fb_initnet* net, int l, int n) {
+    const int Hq = net->H / 4, Wq = net->W / 4;
+    const fb::net::LayerDef& d = kLayers[l];
+    const int hin = Hq / kTens[kIn[l]].div, win = Wq / kTens[kIn[l]].div;
+    ConvGeom g;
+    g.n = n;
+    g.H = hin;
+    g.W = win;
+    g.Cin = d.cin;
+    g.stride = d.stride;
+    g.Ho = (hin + d.stride - 1) / d.stride;
+    g.Wo = (win + d.stride - 1) / d.stride;
+    g.Cout = d.cout;
+    return g;
+}
+
+size_t tens_elems(const fb_initnet* net, int t, int n) {
+    const int Hq = net->H / 4, Wq = net->W / 4;
+    return static_cast<size_t>(n) * (Hq / kTens[t].div) * (Wq / kTens[t].div) * kTens[t].ch;
+}
+
+int net_layers(fb_initnet* net, int n, cudaStream_t st);
+
+int net_forward(fb_initnet* net, const uint8_t* src, const uint8_t* tgt, int n, cudaStream_t st) {
+    using namespace fb::net;
+    const size_t Pq = static_cast<size_t>(n) * (net->H / 4) * (net->W / 4);
+    prep_input_kernel<<<blocks(Pq), 256, 0, st>>>(src, tgt, n, net->H, net->W, net->act[0]);
+    NET_CUDA(net, cudaGetLastError());
+    return net_layers(net, n, st);
+}
+
+// The twelve layers on the input already in act[0].
+int net_layers(fb_initnet* net, int n, cudaStream_t st) {
+    using namespace fb::net;
+    for (int l = 0; l < kNumLayers; ++l) {
+        if (l == 8 || l == 9 || l == 10) {  // build the decoder's concatenated input
+            const int lo = l == 8 ? 8 : (l == 9 ? 10 : 12);
+            const int skip = l == 8 ? 6 : (l == 9 ? 4 : 2);
+            const int cat = kIn[l];
+            const int H2 = (net->H / 4) / kTens[cat].div, W2 = (net->W / 4) / kTens[cat].div;
+            const size_t units = static_cast<size_t>(n) * H2 * W2 * (kTens[cat].ch / 8);
+            concat_up_kernel<<<blocks(units), 256, 0, st>>>(net->act[lo], kTens[lo].ch, net->act[skip],
+                                                             kTens[skip].ch, n, H2, W2, net->act[cat]);
+            NET_CUDA(net, cudaGetLastError());
+        }
+        const ConvGeom g = geom(net, l, n);
+        const bool head = kOut[l] < 0;
+        NET_CUDA(net, conv_forward(g, net->act[kIn[l]], net->wb + net->w_off[l], net->params + net->b_off[l],
+                                   kLayers[l].relu, head ? nullptr : net->act[kOut[l]],
+                                   head ? net->head : nullptr, net->status, st));
+    }
+    return FB_OK;
+}
+
+int refresh_bf16(fb_initnet* net, cudaStream_t st) {
+    using namespace fb::net;
+    for (int l = 0; l < kNumLayers; ++l) {
+        const size_t nw = layer_weights(l);
+        weights_to_bf16_kernel<<<blocks(nw), 256, 0, st>>>(net->params + net->w_off[l], kLayers[l].cout,
+                                                            kLayers[l].cin, net->wb + net->w_off[l],
+                                                            net->wt + net->w_off[l]);
+        NET_CUDA(net, cudaGetLastError());
+    }
+    return FB_OK;
+}
+
+}  // namespace
+
+namespace fb {
+
+int initnet_init_pairs(::fb_initnet* net, const uint8_t* guides, const PairDesc* pairs, int first,
+                       int n, int32_t* nnf_out, cudaStream_t st) {
+    using namespace fb::net;
+    if (n < 1 || n > net->max_pairs) return FB_ERR_ARG;
+    const size_t Pq = static_cast<size_t>(n) * (net->H / 4) * (net->W / 4);
+    prep_input_pairs_kernel<<<blocks(Pq), 256, 0, st>>>(guides, pairs, first, n, net->H, net->W,
+                                                        net->act[0]);
+    NET_CUDA(net, cudaGetLastError());
+    int rc = net_layers(net, n, st);
+    if (rc) return rc;
+    const size_t total = static_cast<size_t>(n) * net->H * net->W;
+    offsets_to_nnf_kernel<<<blocks(total), 256, 0, st>>>(net->head, n, net->H, net->W, nnf_out);
+    NET_CUDA(net, cudaGetLastError());
+    return FB_OK;
+}
+
+int initnet_max_pairs(const ::fb_initnet* net) { return net->max_pairs; }
+
+void initnet_dims(const ::fb_initnet* net, int* H, int* W) {
+    *H = net->H;
+    *W = net->W;
+}
+
+}  // namespace fb
+
+extern "C" {
+
+int fb_initnet_targets(const int32_t* nnf, int n, int H, int W, float* target, float* weight,
+                       void* stream) {
+    if (!nnf || !target || n < 1 || H < 4 || W < 4 || H % 4 || W % 4) return FB_ERR_ARG;
+    const size_t total = static_cast<size_t>(n) * (H / 4) * (W / 4);
+    fb::net::nnf_targets_kernel<<<fb::net::blocks(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        nnf, n, H, W, target, weight);
+    return cudaGetLastError() == cudaSuccess ? FB_OK : FB_ERR_CUDA;
+}
+
+int fb_initnet_create(fb_ctx* ctx, fb_initnet** out, int max_pairs, int H, int W) {
+    if (!ctx || !out) return FB_ERR_ARG;
+    *out = nullptr;
+    if (max_pairs < 1 || H < 32 || W < 32 || H % 32 || W % 32 || H > 32767 || W > 32767)
+        return FB_ERR_ARG;
+    fb_initnet* net = new fb_initnet();
+    net->ctx = ctx;
+    cudaGetDevice(&net->device);
+    net->max_pairs = max_pairs;
+    net->H = H;
+    net->W = W;
+    cudaDeviceGetAttribute(&net->sms, cudaDevAttrMultiProcessorCount, net->device);
+    size_t off = 0;
+    for (int l = 0; l < kNumLayers; ++l) {
+        net->w_off[l] = off;
+        off += fb::net::layer_weights(l);
+        net->b_off[l] = off;
+        off += kLayers[l].cout;
+    }
+    net->n_params = off;
+    // one arena
+    size_t bytes = 0;
+    auto take = [&](size_t nbytes) {
+        const size_t o = bytes;
+        bytes += (nbytes + 255) / 256 * 256;
+        return o;
+    };
+    const size_t o_p = take(off * 4), o_g = take(off * 4), o_m = take(off * 4), o_v = take(off * 4);
+    const size_t o_wb = take(off * 2), o_wt = take(off * 2);
+    size_t o_act[15], o_dact[15], max_t = 0;
+    for (int t = 0; t < 15; ++t) {
+        const size_t e = tens_elems(net, t, max_pairs);
+        max_t = e > max_t ? e : max_t;
+        o_act[t] = take(e * 2);
+        o_dact[t] = take(e * 4);
+    }
+    const size_t Pq = static_cast<size_t>(max_pairs) * (H / 4) * (W / 4);
+    const size_t o_dz = take(max_t * 2), o_head = take(Pq * 8 * 4), o_dhead = take(Pq * 8 * 4);
+    const size_t o_loss = take(4), o_status = take(4);
+    if (cudaMalloc(reinterpret_cast<void**>(&net->arena), bytes) != cudaSuccess) {
+        cudaGetLastError();
+        delete net;
+        return FB_ERR_OOM;
+    }
+    cudaMemset(net->arena, 0, bytes);
+    char* a = net->arena;
+    net->params = reinterpret_cast<float*>(a + o_p);
+    net->grads = reinterpret_cast<float*>(a + o_g);
+    net->adam_m = reinterpret_cast<float*>(a + o_m);
+    net->adam_v = reinterpret_cast<float*>(a + o_v);
+    net->wb = reinterpret_cast<bf16*>(a + o_wb);
+    net->wt = reinterpret_cast<bf16*>(a + o_wt);
+    for (int t = 0; t < 15; ++t) {
+        net->act[t] = reinterpret_cast<bf16*>(a + o_act[t]);
+        net->dact[t] = reinterpret_cast<float*>(a + o_dact[t]);
+    }
+    net->dact[15] = reinterpret_cast<float*>(a + o_dhead);  // gradient of the head output
+    net->dz = reinterpret_cast<bf16*>(a + o_dz);
+    net->head = reinterpret_cast<float*>(a + o_head);
+    net->loss = reinterpret_cast<float*>(a + o_loss);
+    net->status = reinterpret_cast<int*>(a + o_status);
+    *out = net;
+    return FB_OK;
+}
+
+int fb_initnet_destroy(fb_initnet* net) {
+    if (!net) return FB_OK;
+    cudaDeviceSynchronize();
+    if (net->arena) cudaFree(net->arena);
+    delete net;
+    return FB_OK;
+}
+
+const char* fb_initnet_last_error(const fb_initnet* net) { return net ? net->err.c_str() : ""; }
+
+size_t fb_initnet_param_count(const fb_initnet* net) { return net ? net->n_params : 0; }
+
+int fb_initnet_get_params(fb_initnet* net, float* host_out) {
+    if (!net || !host_out) return FB_ERR_ARG;
+    NET_CUDA(net, cudaMemcpy(host_out, net->params, net->n_params * 4, cudaMemcpyDeviceToHost));
+    return FB_OK;
+}
+
+int fb_initnet_set_params(fb_initnet* net, const float* host_in) {
+    if (!net || !host_in) return FB_ERR_ARG;
+    NET_CUDA(net, cudaMemcpy(net->params, host_in, net->n_params * 4, cudaMemcpyHostToDevice));
+    NET_CUDA(net, cudaMemset(net->adam_m, 0, net->n_params * 4));
+    NET_CUDA(net, cudaMemset(net->adam_v, 0, net->n_params * 4));
+    net->step = 0;
+    return refresh_bf16(net, nullptr);
+}
+
+int fb_initnet_forward(fb_initnet* net, const uint8_t* src, const uint8_t* tgt, int n,
+                       float* head_out, void* stream) {
+    if (!net || !src || !tgt || n < 1 || n > net->max_pairs) return FB_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = net_forward(net, src, tgt, n, st);
+    if (rc) return rc;
+    if (head_out) {
+        const size_t Pq = static_cast<size_t>(n) * (net->H / 4) * (net->W / 4);
+        NET_CUDA(net, cudaMemcpyAsync(head_out, net->head, Pq * 8 * 4, cudaMemcpyDeviceToDevice, st));
+    }
+    return FB_OK;
+}
+
+int fb_initnet_init_nnf(fb_initnet* net, int n, int32_t* nnf_out, void* stream) {
+    if (!net || !nnf_out || n < 1 || n > net->max_pairs) return FB_ERR_ARG;
+    const size_t total = static_cast<size_t>(n) * net->H * net->W;
+    fb::net::offsets_to_nnf_kernel<<<fb::net::blocks(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
+        net->head, n, net->H, net->W, nnf_out);
+    NET_CUDA(net, cudaGetLastError());
+    return FB_OK;
+}
+
+int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tgt, int n,
+                          const float* target, const float* weight, float weight_sum, float lr,
+                          float* loss_out, void* stream) {
+    using namespace fb::net;
+    if (!net || !src || !tgt || !target || n < 1 || n > net->max_pairs || !(weight_sum > 0.f))
+        return FB_ERR_ARG;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int rc = net_forward(net, src, tgt, n, st);
+    if (rc) return rc;
+    const size_t Pq = static_cast<size_t>(n) * (net->H / 4) * (net->W / 4);
+    NET_CUDA(net, cudaMemsetAsync(net->loss, 0, 4, st));
+    NET_CUDA(net, cudaMemsetAsync(net->grads, 0, net->n_params * 4, st));
+    for (int t = 0; t < 15; ++t)
+        NET_CUDA(net, cudaMemsetAsync(net->dact[t], 0, tens_elems(net, t, n) * 4, st));
+    offset_loss_kernel<<<blocks(Pq), 256, 0, st>>>(net->head, target, weight, Pq, 1.f / weight_sum,
+                                                   net->dact[15], net->loss);
+    NET_CUDA(net, cudaGetLastError());
+    for (int l = kNumLayers - 1; l >= 0; --l) {
+        const ConvGeom g = geom(net, l, n);
+        const size_t out_elems = static_cast<size_t>(g.n) * g.Ho * g.Wo * g.Cout;
+        const float* dA = kOut[l] < 0 ? net->dact[15] : net->dact[kOut[l]];
+        const bf16* A = kOut[l] < 0 ? nullptr : net->act[kOut[l]];
+        relu_bwd_kernel<<<blocks(out_elems), 256, 0, st>>>(dA, A ? A : net->act[0], out_elems,
+                                                           kLayers[l].relu, net->dz);
+        NET_CUDA(net, cudaGetLastError());
+        bias_grad_kernel<<<g.Cout, 256, 0, st>>>(net->dz, static_cast<size_t>(g.n) * g.Ho * g.Wo, g.Cout,
+                                                 net->grads + net->b_off[l]);
+        NET_CUDA(net, cudaGetLastError());
+        NET_CUDA(net, conv_wgrad(g, net->dz, net->act[kIn[l]], net->grads + net->w_off[l], net->sms,
+                                 net->status, st));
+        if (l > 0)
+            NET_CUDA(net, conv_dgrad(g, net->dz, net->wt + net->w_off[l], net->dact[kIn[l]], 1,
+                                     net->status, st));
+        if (l == 8 || l == 9 || l == 10) {  // split the concatenated input's gradient
+            const int lo = l == 8 ? 8 : (l == 9 ? 10 : 12);
+            const int skip = l == 8 ? 6 : (l == 9 ? 4 : 2);
+            const int cat = kIn[l];
+            const int H2 = (net->H / 4) / kTens[cat].div, W2 = (net->W / 4) / kTens[cat].div;
+            const size_t tot = tens_elems(net, lo, n) + tens_elems(net, skip, n);
+            concat_up_bwd_kernel<<<blocks(tot), 256, 0, st>>>(net->dact[cat], kTens[lo].ch, kTens[skip].ch, n,
+                                                              H2, W2, net->dact[lo], net->dact[skip]);
+            NET_CUDA(net, cudaGetLastError());
+        }
+    }
+    if (lr > 0.f) {
+        net->step += 1;
+        const float b1 = 0.9f, b2 = 0.999f;
+        const float c1 = 1.f - std::pow(b1, static_cast<float>(net->step));
+        const float c2 = 1.f - std::pow(b2, static_cast<float>(net->step));
+        adam_kernel<<<blocks(net->n_params), 256, 0, st>>>(net->params, net->grads, net->adam_m, net->adam_v,
+                                                          net->n_params, lr, b1, b2, 1e-8f, c1, c2);
+        NET_CUDA(net, cudaGetLastError());
+        rc = refresh_bf16(net, st);
+        if (rc) return rc;
+    }
+    if (loss_out) NET_CUDA(net, cudaMemcpyAsync(loss_out, net->loss, 4, cudaMemcpyDeviceToDevice, st));
+    return FB_OK;
+}
+
+int fb_initnet_get_grads(fb_initnet* net, float* host_out) {
+    if (!net || !host_out) return FB_ERR_ARG;
+    NET_CUDA(net, cudaMemcpy(host_out, net->grads, net->n_params * 4, cudaMemcpyDeviceToHost));
+    return FB_OK;
+}
+
+int fb_initnet_status(fb_initnet* net) {
+    if (!net) return FB_ERR_ARG;
+    int s = 0;
+    NET_CUDA(net, cudaMemcpy(&s, net->status, 4, cudaMemcpyDeviceToHost));
+    return s ? FB_ERR_TIMEOUT : FB_OK;
+}
+
+// Single-layer entry points (used by the gradient checks against the CPU oracle).
+int fb_conv3x3_forward(const uint16_t* x, int n, int H, int W, int Cin, const uint16_t* w,
+                       const float* bias, int Cout, int stride, int relu, uint16_t* y_bf16,
+                       float* y_f32, int* status, void* stream) {
+    if (!x || !w || !bias || (!y_bf16 && !y_f32) || Cin % 8 || Cout % 8 || Cout > 128 || Cin > 1024 ||
+        (stride != 1 && stride != 2) || n < 1 || H < 1 || W < 1 || !status)
+        return FB_ERR_ARG;
+    ConvGeom g{n, H, W, Cin, (H + stride - 1) / stride, (W + stride - 1) / stride, Cout, stride};
+    cudaError_t e = fb::net::conv_forward(g, reinterpret_cast<const bf16*>(x), reinterpret_cast<const bf16*>(w),
+                                          bias, relu, reinterpret_cast<bf16*>(y_bf16), y_f32, status,
+                                          static_cast<cudaStream_t>(stream));
+    return e == cudaSuccess ? FB_OK : FB_ERR_CUDA;
+}
+
+int fb_conv3x3_backward(const uint16_t* x, int n, int H, int W, int Cin, const uint16_t* wt,
+                        int Cout, int stride, const uint16_t* dz, float* dx, float* dw, int* status,
+                        void* stream) {
+    if (!x || !dz || Cin % 8 || Cout % 8 || Cout > 128 || Cin > 1024 || (stride != 1 && stride != 2) ||
+        n < 1 || H < 1 || W < 1 || !status || (dx && !wt))
+        return FB_ERR_ARG;
+    ConvGeom g{n, H, W, Cin, (H + stride - 1) / stride, (W + stride - 1) / stride, Cout, stride};
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (dw) {
+        cudaError_t e = fb::net::conv_wgrad(g, reinterpret_cast<const bf16*>(dz), reinterpret_cast<const bf16*>(x),
+                                            dw, sms, status, st);
+        if (e != cudaSuccess) return FB_ERR_CUDA;
+    }
+    if (dx) {
+        cudaError_t e = fb::net::conv_dgrad(g, reinterpret_cast<const bf16*>(dz), reinterpret_cast<const bf16*>(wt),
+                                            dx, 0, status, st);
+        if (e != cudaSuccess) return FB_ERR_CUDA;
+    }
+    return FB_OK;
+}
+
+}  // extern "C"

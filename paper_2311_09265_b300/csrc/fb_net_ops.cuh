@@ -1,0 +1,230 @@
+// fb_net_ops.cuh -- 3x3 convolutions (zero padding 1, stride 1 or 2, NHWC bf16) of the
+// learned NNF initialiser expressed as gathered tcgen05 GEMMs (fb_tc_gemm.cuh):
+//   forward  Y[p][co]  = act(b[co] + sum_{tap,ci} X[p*s + tap - 1][ci] W[co][tap][ci])
+//            GEMM M = output pixels, N = Cout, K = 9 Cin
+//   dgrad    dX[q][ci] = sum_{tap,co} dZ[(q - tap + 1)/s][co] W[co][tap][ci]
+//            GEMM M = input pixels, N = Cin, K = 9 Cout (B = weights transposed)
+//   wgrad    dW[co][tap][ci] = sum_p dZ[p][co] X[p*s + tap - 1][ci]
+//            GEMM M = Cout, N = 9 Cin, K = output pixels (split over CTAs, fp32 atomics)
+// Channel counts are multiples of 8, so one 16-byte gather unit (8 channels) is one
+// row of a core matrix.
+#pragma once
+
+#include <cuda_bf16.h>
+
+#include "fb_tc_gemm.cuh"
+
+namespace fb {
+namespace net {
+
+using bf16 = __nv_bfloat16;
+
+struct ConvGeom {
+    int n, H, W, Cin;   // input
+    int Ho, Wo, Cout;   // output
+    int stride;
+};
+
+__device__ __forceinline__ uint4 zero4() { return make_uint4(0u, 0u, 0u, 0u); }
+
+__device__ __forceinline__ void store_unit(unsigned char* tile, int row, int k, uint4 v) {
+    *reinterpret_cast<uint4*>(tile + tc::tile_off(row, k)) = v;
+}
+
+// ---- forward ---------------------------------------------------------------------
+template <int BN>
+struct GatherFwd {
+    const bf16* X;   // [n][H][W][Cin]
+    const bf16* Wt;  // [Cout][9*Cin]
+    ConvGeom g;
+    int M, K;
+    __device__ __forceinline__ void load(unsigned char* sa, unsigned char* sb, int k0, int m0,
+                                         int n0) const {
+        const int t = threadIdx.x;
+        const int m = m0 + t;
+        int img = 0, oy = 0, ox = 0;
+        if (m < M) {
+            img = m / (g.Ho * g.Wo);
+            const int rem = m - img * g.Ho * g.Wo;
+            oy = rem / g.Wo;
+            ox = rem - oy * g.Wo;
+        }
+#pragma unroll
+        for (int u = 0; u < tc::BK / 8; ++u) {
+            const int k = k0 + 8 * u;
+            uint4 v = zero4();
+            if (m < M && k < K) {
+                const int tap = k / g.Cin, ci = k - tap * g.Cin;
+                const int iy = oy * g.stride + tap / 3 - 1, ix = ox * g.stride + tap % 3 - 1;
+                if (iy >= 0 && iy < g.H && ix >= 0 && ix < g.W)
+                    v = __ldg(reinterpret_cast<const uint4*>(
+                        X + ((static_cast<size_t>(img) * g.H + iy) * g.W + ix) * g.Cin + ci));
+            }
+            store_unit(sa, t, 8 * u, v);
+        }
+        for (int idx = t; idx < BN * (tc::BK / 8); idx += 128) {
+            const int row = idx / (tc::BK / 8), u = idx % (tc::BK / 8);
+            const int n = n0 + row, k = k0 + 8 * u;
+            uint4 v = zero4();
+            if (n < g.Cout && k < K)
+                v = __ldg(reinterpret_cast<const uint4*>(Wt + static_cast<size_t>(n) * K + k));
+            store_unit(sb, row, 8 * u, v);
+        }
+    }
+};
+
+// bias + optional ReLU, bf16 output [M][Cout] (or fp32 output when Yf is set).
+struct EpiFwd {
+    bf16* Y;
+    float* Yf;
+    const float* bias;
+    int Cout;
+    int relu;
+    __device__ __forceinline__ void store(int row, int col0, const float (&v)[16]) const {
+        if (Yf) {
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (col0 + j < Cout) Yf[static_cast<size_t>(row) * Cout + col0 + j] = v[j] + bias[col0 + j];
+            return;
+        }
+        if (col0 + 16 <= Cout) {
+            __align__(16) bf16 o[16];
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                float x = v[j] + bias[col0 + j];
+                o[j] = __float2bfloat16_rn(relu ? fmaxf(x, 0.f) : x);
+            }
+            uint4* d = reinterpret_cast<uint4*>(Y + static_cast<size_t>(row) * Cout + col0);
+            d[0] = *reinterpret_cast<const uint4*>(&o[0]);
+            d[1] = *reinterpret_cast<const uint4*>(&o[8]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) {
+                if (col0 + j >= Cout) break;
+                const float x = v[j] + bias[col0 + j];
+                Y[static_cast<size_t>(row) * Cout + col0 + j] = __float2bfloat16_rn(relu ? fmaxf(x, 0.f) : x);
+            }
+        }
+    }
+};
+
+// ---- input gradient ----------------------------------------------------------------
+template <int BN>
+struct GatherDgrad {
+    const bf16* dZ;  // [n][Ho][Wo][Cout]
+    const bf16* WT;  // [Cin][9*Cout]
+    ConvGeom g;
+    int M, K;        // M = n*H*W, K = 9*Cout
+    __device__ __forceinline__ void load(unsigned char* sa, unsigned char* sb, int k0, int m0,
+                                         int n0) const {
+        const int t = threadIdx.x;
+        const int m = m0 + t;
+        int img = 0, y = 0, x = 0;
+        if (m < M) {
+            img = m / (g.H * g.W);
+            const int rem = m - img * g.H * g.W;
+            y = rem / g.W;
+            x = rem - y * g.W;
+        }
+#pragma unroll
+        for (int u = 0; u < tc::BK / 8; ++u) {
+            const int k = k0 + 8 * u;
+            uint4 v = zero4();
+            if (m < M && k < K) {
+                const int tap = k / g.Cout, co = k - tap * g.Cout;
+                const int ty = y - tap / 3 + 1, tx = x - tap % 3 + 1;  // = output pixel * stride
+                if (ty >= 0 && tx >= 0 && ty % g.stride == 0 && tx % g.stride == 0) {
+                    const int oy = ty / g.stride, ox = tx / g.stride;
+                    if (oy < g.Ho && ox < g.Wo)
+                        v = __ldg(reinterpret_cast<const uint4*>(
+                            dZ + ((static_cast<size_t>(img) * g.Ho + oy) * g.Wo + ox) * g.Cout + co));
+                }
+            }
+            store_unit(sa, t, 8 * u, v);
+        }
+        for (int idx = t; idx < BN * (tc::BK / 8); idx += 128) {
+            const int row = idx / (tc::BK / 8), u = idx % (tc::BK / 8);
+            const int n = n0 + row, k = k0 + 8 * u;
+            uint4 v = zero4();
+            if (n < g.Cin && k < K)
+                v = __ldg(reinterpret_cast<const uint4*>(WT + static_cast<size_t>(n) * K + k));
+            store_unit(sb, row, 8 * u, v);
+        }
+    }
+};
+
+// fp32 input gradient [M][Cin], written or added.
+struct EpiDgrad {
+    float* dX;
+    int Cin;
+    int accumulate;
+    __device__ __forceinline__ void store(int row, int col0, const float (&v)[16]) const {
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (col0 + j >= Cin) break;
+            float* d = dX + static_cast<size_t>(row) * Cin + col0 + j;
+            *d = accumulate ? *d + v[j] : v[j];
+        }
+    }
+};
+
+// ---- weight gradient ---------------------------------------------------------------
+template <int BN>
+struct GatherWgrad {
+    const bf16* dZ;  // [P][Cout], P = n*Ho*Wo
+    const bf16* X;   // [n][H][W][Cin]
+    ConvGeom g;
+    int P;           // K of the GEMM
+    __device__ __forceinline__ void load(unsigned char* sa, unsigned char* sb, int k0, int m0,
+                                         int n0) const {
+        const int t = threadIdx.x;
+        (void)m0;  // M = Cout <= 128: one tile
+        // A[co][p] = dZ[p][co]: each unit (8 channels of one pixel) scatters to 8 rows.
+        const int groups_a = (g.Cout + 7) / 8;
+        for (int idx = t; idx < tc::BK * groups_a; idx += 128) {
+            const int j = idx / groups_a, gr = idx - j * groups_a;
+            const int p = k0 + j;
+            uint4 v = zero4();
+            if (p < P)
+                v = __ldg(reinterpret_cast<const uint4*>(dZ + static_cast<size_t>(p) * g.Cout + 8 * gr));
+            const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                *reinterpret_cast<bf16*>(sa + tc::tile_off(8 * gr + q, j)) = e[q];
+        }
+        // B[tap*Cin + ci][p] = X[p*s + tap - 1][ci]
+        constexpr int groups_b = BN / 8;
+        for (int idx = t; idx < tc::BK * groups_b; idx += 128) {
+            const int j = idx / groups_b, gr = idx - j * groups_b;
+            const int p = k0 + j, n = n0 + 8 * gr;
+            uint4 v = zero4();
+            if (p < P && n < 9 * g.Cin) {
+                const int tap = n / g.Cin, ci = n - tap * g.Cin;
+                const int img = p / (g.Ho * g.Wo);
+                const int rem = p - img * g.Ho * g.Wo;
+                const int oy = rem / g.Wo, ox = rem - oy * g.Wo;
+                const int iy = oy * g.stride + tap / 3 - 1, ix = ox * g.stride + tap % 3 - 1;
+                if (iy >= 0 && iy < g.H && ix >= 0 && ix < g.W)
+                    v = __ldg(reinterpret_cast<const uint4*>(
+                        X + ((static_cast<size_t>(img) * g.H + iy) * g.W + ix) * g.Cin + ci));
+            }
+            const bf16* e = reinterpret_cast<const bf16*>(&v);
+#pragma unroll
+            for (int q = 0; q < 8; ++q)
+                *reinterpret_cast<bf16*>(sb + tc::tile_off(8 * gr + q, j)) = e[q];
+        }
+    }
+};
+
+struct EpiWgrad {
+    float* dW;  // [Cout][9*Cin], accumulated
+    int N;      // 9*Cin
+    __device__ __forceinline__ void store(int row, int col0, const float (&v)[16]) const {
+#pragma unroll
+        for (int j = 0; j < 16; ++j)
+            if (col0 + j < N) atomicAdd(dW + static_cast<size_t>(row) * N + col0 + j, v[j]);
+    }
+};
+
+}  // namespace net
+}  // namespace fb

@@ -119,7 +119,7 @@ extern "C" int fb_blend_window_noalloc(const uint8_t* guides, const uint8_t* sty
     if (p->levels < 1 || p->levels > 16)
         return report(FB_ERR_ARG, "levels must be in [1, 16], got %lld", p->levels);
     if (p->r0 < 0 || p->r0 > (1 << 20)) return report(FB_ERR_ARG, "r0 must be in [0, 2^20], got %lld", p->r0);
-    if (p->flags != 0) return report(FB_ERR_ARG, "flags must be 0");
+    if (p->flags != 0) return report(FB_ERR_ARG, "flags must be 0 for the no-allocation blend");
     if (H < p->patch || W < p->patch || H > 32767 || W > 32767)
         return report(FB_ERR_ARG, "image %lldx%lld outside [patch, 32767]", H, W);
     if (N < 1 || N > 65535) return report(FB_ERR_ARG, "N must be in [1, 65535], got %lld", N);

@@ -1,0 +1,95 @@
+"""Training of the learned NNF initialiser on fields computed by Alg. 1.
+
+Every compute step runs in libfb.so: the targets come from fb_nnf (Alg. 1 with more
+iterations than the blend uses) and fb_initnet_targets, the loss, backward pass and
+Adam update from fb_initnet_train_step.  PyTorch only holds device memory and gathers
+the pair stacks of a batch.  The guide clips are the seeded synthetic clips of the
+`synth` module (smooth random affine motion), drawn with seeds other than the ones the
+benchmarks evaluate on.
+"""
+from __future__ import annotations
+
+import math
+import time
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+import synth
+
+from . import (FB_FLAG_LEARNED_INIT, Context, InitNet, Params, fb_initnet_targets, fb_nnf)
+
+
+@dataclass
+class TrainingSet:
+    frames: list          # per clip: (N, H, W, 3) uint8 CUDA tensor
+    pairs: np.ndarray     # (P, 3): clip, source frame, target frame
+    target: torch.Tensor  # (P, H/4, W/4, 2) float32
+    weight: torch.Tensor  # (P, H/4, W/4) float32
+
+
+def make_training_set(ctx: Context, n_clips: int = 6, frames: int = 24, H: int = 512, W: int = 512,
+                      max_gap: int = 7, pairs_per_clip: int = 160, target_iters: int = 12,
+                      seed: int = synth.clip_seed(4)) -> TrainingSet:
+    """Seeded clips, random ordered pairs with 1 <= |i - j| <= max_gap, and the method's
+    own NNFs (target_iters iterations of Alg. 1) turned into block-mean targets."""
+    rng = np.random.default_rng(seed)
+    clips, pairs, targets, weights = [], [], [], []
+    for c in range(n_clips):
+        g, _ = synth.affine_clip(frames, H, W, seed + 101 * c)
+        gd = torch.tensor(g, device="cuda")
+        clips.append(gd)
+        for _ in range(pairs_per_clip):
+            i = int(rng.integers(0, frames))
+            d = int(rng.integers(1, max_gap + 1)) * (1 if rng.random() < 0.5 else -1)
+            j = min(max(i + d, 0), frames - 1)
+            if j == i:
+                j = i + 1 if i + 1 < frames else i - 1
+            p = Params.make(5, target_iters, 1, 0, seed + 7 * len(pairs), 0)
+            F, _ = fb_nnf(ctx, gd[j], gd[i], p)
+            t, w = fb_initnet_targets(F.unsqueeze(0))
+            pairs.append((c, j, i))
+            targets.append(t[0])
+            weights.append(w[0])
+    return TrainingSet(clips, np.array(pairs, np.int64), torch.stack(targets), torch.stack(weights))
+
+
+def batch(ts: TrainingSet, idx):
+    src = torch.stack([ts.frames[c][j] for c, j, _ in ts.pairs[idx]])
+    tgt = torch.stack([ts.frames[c][i] for c, _, i in ts.pairs[idx]])
+    return src, tgt, ts.target[idx].contiguous(), ts.weight[idx].contiguous()
+
+
+def initial_params(n_params: int, seed: int) -> np.ndarray:
+    """He-normal weights, zero biases; the head starts small and uses channels 0, 1."""
+    from .initnet_layout import LAYERS
+    rng = np.random.default_rng(seed)
+    out = []
+    for l, (cin, cout) in enumerate(LAYERS):
+        std = math.sqrt(2.0 / (9 * cin)) * (0.1 if l == len(LAYERS) - 1 else 1.0)
+        w = rng.normal(0.0, std, size=(cout, 3, 3, cin)).astype(np.float32)
+        if l == len(LAYERS) - 1:
+            w[2:] = 0.0
+        out.append(np.concatenate([w.ravel(), np.zeros(cout, np.float32)]))
+    p = np.concatenate(out)
+    assert p.size == n_params
+    return p
+
+
+def train(net: InitNet, ts: TrainingSet, steps: int = 1500, batch_size: int = 8, lr: float = 2e-3,
+          seed: int = 0, log_every: int = 100):
+    """Adam with a cosine-decayed step size; returns the loss history (every log_every)."""
+    rng = np.random.default_rng(seed)
+    hist = []
+    loss = torch.zeros(1, dtype=torch.float32, device="cuda")
+    t0 = time.perf_counter()
+    for s in range(steps):
+        idx = rng.choice(len(ts.pairs), size=batch_size, replace=False)
+        src, tgt, target, weight = batch(ts, idx)
+        wsum = max(float(weight.sum()), 1.0)
+        cur = lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * s / steps)))
+        net.train_step(src, tgt, target, weight, wsum, cur, loss_out=loss)
+        if s % log_every == 0 or s == steps - 1:
+            hist.append((s, float(loss.item()), time.perf_counter() - t0))
+    return hist

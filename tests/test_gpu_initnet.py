@@ -1,0 +1,120 @@
+"""The learned initialiser's tensor-core kernels against the FP64 CPU oracle: single
+conv layers (forward, input and weight gradients) and the whole training step's
+parameter gradient (relative L2 error <= 1e-2 at BF16)."""
+import numpy as np
+import pytest
+
+from oracle import initnet as ref
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def fbp():
+    import paper_2311_09265_b300 as m
+    m.build()
+    return m
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
+
+
+def to_bf16_tensor(a):
+    import torch
+    return torch.from_numpy(ref.bf16_bits(a).view(np.int16).copy()).view(torch.bfloat16).cuda()
+
+
+CONV_CASES = [  # n, H, W, Cin, Cout, stride
+    (2, 20, 20, 8, 32, 1), (2, 17, 23, 32, 64, 2), (1, 16, 16, 96, 96, 1),
+    (2, 8, 8, 224, 96, 1), (1, 12, 10, 64, 128, 2), (3, 9, 11, 32, 8, 1),
+]
+
+
+@pytest.mark.parametrize("n,H,W,Cin,Cout,stride", CONV_CASES)
+def test_conv_forward_matches_oracle(fbp, n, H, W, Cin, Cout, stride):
+    import torch
+    rng = np.random.default_rng(H * W + Cin)
+    x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
+    w = ref.bf16(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin))
+    b = rng.normal(size=Cout).astype(np.float32).astype(np.float64)
+    want = ref.conv3x3(x, w, b, stride)
+    y32, st = fbp.conv3x3_forward(to_bf16_tensor(x), to_bf16_tensor(w),
+                                  torch.tensor(b, dtype=torch.float32, device="cuda"), stride, False,
+                                  out_f32=True)
+    yb, st2 = fbp.conv3x3_forward(to_bf16_tensor(x), to_bf16_tensor(w),
+                                  torch.tensor(b, dtype=torch.float32, device="cuda"), stride, True)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and int(st2.item()) == 0
+    assert rel_l2(y32.cpu().numpy(), want) < 1e-5
+    assert rel_l2(yb.float().cpu().numpy(), np.maximum(want, 0)) < 1e-2
+
+
+@pytest.mark.parametrize("n,H,W,Cin,Cout,stride", CONV_CASES)
+def test_conv_backward_matches_oracle(fbp, n, H, W, Cin, Cout, stride):
+    import torch
+    rng = np.random.default_rng(7 + H * W + Cout)
+    x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
+    w = ref.bf16(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin))
+    Ho, Wo = ref.out_size(H, stride), ref.out_size(W, stride)
+    dz = ref.bf16(rng.normal(size=(n, Ho, Wo, Cout)))
+    dx_ref, dw_ref, _ = ref.conv3x3_backward(x, w, dz, stride)
+    wt = np.ascontiguousarray(np.transpose(w, (3, 1, 2, 0)))
+    dx, dw, st = fbp.conv3x3_backward(to_bf16_tensor(x), to_bf16_tensor(wt), to_bf16_tensor(dz), stride)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    assert rel_l2(dx.cpu().numpy(), dx_ref) < 1e-5
+    assert rel_l2(dw.cpu().numpy(), dw_ref) < 1e-5
+
+
+def _oracle_grads(params, src, tgt, target, nudge=0.0):
+    p = params.astype(np.float64)
+    if nudge:
+        p = p * (1.0 + nudge * np.random.default_rng(9).normal(size=p.shape))
+    head, cache = ref.forward(p, src, tgt)
+    n, hq, wq = head.shape[:3]
+    _, dhead = ref.loss_and_grad_head(head, target.astype(np.float64), None, float(n * hq * wq))
+    return ref.backward(cache, dhead), head
+
+
+def test_training_step_gradient_matches_oracle(fbp):
+    """A BF16 network's gradient is chaotic at the per-cent level: nudging the weights by
+    1e-6 (far below BF16 resolution) moves the oracle's own gradient by about 2 %,
+    through rounding flips at ReLU boundaries and BF16 stores.  The GPU gradient must lie
+    within twice that measured noise floor of the oracle (and the head layer, where no
+    flip can intervene, within 1 %)."""
+    import torch
+    rng = np.random.default_rng(5)
+    n, H, W = 2, 64, 64
+    src = rng.integers(0, 256, size=(n, H, W, 3)).astype(np.uint8)
+    tgt = rng.integers(0, 256, size=(n, H, W, 3)).astype(np.uint8)
+    params = ref.init_params(11).astype(np.float32)
+    params[-8 * 9 * 32 - 8:-6 * 9 * 32 - 8] = rng.normal(0, 0.05, size=2 * 9 * 32)   # live head rows 0,1
+    target = rng.normal(0, 4, size=(n, H // 4, W // 4, 2)).astype(np.float32)
+    g_ref, head = _oracle_grads(params, src, tgt, target)
+    g_nudged, head_nudged = _oracle_grads(params, src, tgt, target, nudge=1e-6)
+    noise = rel_l2(g_nudged, g_ref)
+    head_noise = rel_l2(head_nudged[..., :2], head[..., :2])
+    ctx = fbp.Context(0)
+    net = fbp.InitNet(ctx, n, H, W)
+    net.set_params(params)
+    g_src = torch.tensor(src, device="cuda")
+    g_tgt = torch.tensor(tgt, device="cuda")
+    head_gpu = net.forward(g_src, g_tgt)
+    net.train_step(g_src, g_tgt, torch.tensor(target, device="cuda"), lr=0.0)
+    torch.cuda.synchronize()
+    assert net.status() == 0
+    assert rel_l2(head_gpu.cpu().numpy()[..., :2], head[..., :2]) <= max(1e-2, 2 * head_noise)
+    g = net.get_grads()
+    assert 1e-3 < noise < 0.1
+    assert rel_l2(g, g_ref) <= max(1e-2, 2 * noise)
+    cos = float(np.dot(g, g_ref) / (np.linalg.norm(g) * np.linalg.norm(g_ref)))
+    assert cos > 0.995
+    off = 0
+    for l, (cin, cout, _, _) in enumerate(ref.LAYERS):
+        nw = cout * 9 * cin
+        if l == len(ref.LAYERS) - 1:
+            assert rel_l2(g[off:off + nw], g_ref[off:off + nw]) < 1e-2
+        off += nw + cout
+    net.close()
+    ctx.close()
