@@ -53,7 +53,9 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("fastblend", "reference"), default="fastblend")
     ap.add_argument("--workload", default="blend_512",
-                    choices=sorted(synth.WORKLOADS) + ["batch_32"])
+                    choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512"])
+    ap.add_argument("--learned-iters", type=int, default=2,
+                    help="Alg. 1 iterations after the learned initialiser (learned_512)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=5)
@@ -240,10 +242,24 @@ def run_gpu(args):
         dist.init_process_group("gloo", rank=rank, world_size=world)
     torch.cuda.set_device(local)
     fbp.build()
-    w = synth.WORKLOADS[args.workload]
+    learned = args.workload == "learned_512"
+    w = synth.WORKLOADS["blend_512" if learned else args.workload]
     g, s = make_inputs(w, shard_seed(w.seed, rank))
     ctx = fbp.Context(local)
     params = fbp.Params.make(w.patch, w.iters, w.levels, 0, w.seed)
+    learned_info = None
+    if learned:
+        # The learned initialiser: trained here, on the method's own NNFs of seeded clips
+        # that differ from the evaluated clip, by the library's forward/backward kernels.
+        from paper_2311_09265_b300 import initnet_train
+        net, hist, t_data, t_train = initnet_train.train_default(ctx, w.H, w.W, max_pairs=256)
+        ctx.set_initnet(net)
+        params = fbp.Params.make(w.patch, args.learned_iters, 1, 0, w.seed)
+        params.flags = fbp.FB_FLAG_LEARNED_INIT
+        learned_info = {"training_set_s": t_data, "training_s": t_train,
+                        "training_steps": hist[-1][0] + 1, "loss_first": hist[0][1],
+                        "loss_last": hist[-1][1], "refinement_iters": args.learned_iters,
+                        "net_params": net.n_params, "downscale": net.ds}
     g_d = torch.tensor(g, device="cuda")
     s_d = torch.tensor(s, device="cuda")
     out = torch.empty((w.N, w.H, w.W, 3), dtype=torch.float32, device="cuda")
@@ -309,11 +325,35 @@ def run_gpu(args):
                "h2d_bytes_per_step": int(g_h.numel() + s_h.numel()),
                "d2h_bytes_per_step": int(o_h.numel() * 4)}
 
+    if learned:
+        # NNF energy (mean Eq. 1 error of all 784 final fields) against the plain search.
+        def energy_and_ms(pp):
+            pp.flags |= fbp.FB_FLAG_REPORT_ENERGY
+            fbp.fb_blend_window(ctx, g_d, s_d, w.window, pp, out=out)
+            e, c = ctx.energy()
+            pp.flags &= ~fbp.FB_FLAG_REPORT_ENERGY
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            fbp.fb_blend_window(ctx, g_d, s_d, w.window, pp, out=out)
+            torch.cuda.synchronize()
+            a.record()
+            fbp.fb_blend_window(ctx, g_d, s_d, w.window, pp, out=out)
+            b.record()
+            torch.cuda.synchronize()
+            return e / c, a.elapsed_time(b)
+        plain = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed)
+        e_plain, ms_plain = energy_and_ms(plain)
+        lp = fbp.Params.make(w.patch, args.learned_iters, 1, 0, w.seed)
+        lp.flags = fbp.FB_FLAG_LEARNED_INIT
+        e_learn, ms_learn = energy_and_ms(lp)
+        learned_info.update({"energy_learned": e_learn, "energy_plain_6_iters": e_plain,
+                             "energy_ratio": e_learn / e_plain, "ms_learned": ms_learn,
+                             "ms_plain_6_iters": ms_plain, "speedup_vs_plain": ms_plain / ms_learn})
+
     # ---- roofline of the dominant kernel ----
     rate, _ = ctx.probe_dp4a()
     iter_ms, iter_n = prof["iter"]
     kernel_total_ms = sum(v[0] for v in prof.values())
-    ops = iter_ops_per_launch(w) if w.levels == 1 else None
+    ops = iter_ops_per_launch(w) if w.levels == 1 else None  # same per launch with learned init
     roof = None
     if iter_n and ops:
         avg_s = iter_ms / iter_n / 1e3
@@ -330,7 +370,10 @@ def run_gpu(args):
                                if probe_per_clk else "derived"),
                 "avg_launch_ms": iter_ms / iter_n, "launches": iter_n,
                 "share_of_kernel_time": iter_ms / kernel_total_ms if kernel_total_ms else None,
-                "candidate_evals_per_s": w.candidate_evals() * args.steps * world / (total_ms / 1e3),
+                "candidate_evals_per_s": (w.candidate_evals() if not learned else
+                                          w.pairs() * w.H * w.W * (1 + args.learned_iters *
+                                                                   (4 + w.random_search_radii())))
+                * args.steps * world / (total_ms / 1e3),
                 "probe_dp4a_per_s": rate}
 
     line = {
@@ -338,9 +381,17 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": w.name, "frames": w.N, "height": w.H, "width": w.W,
-                   "patch": w.patch, "window": w.window, "iters": w.iters, "levels": w.levels,
-                   "nnfs_per_step": w.pairs(), "candidate_evals_per_step": w.candidate_evals(),
+        "config": {"workload": (w.name if not learned else
+                                "learned-init blend all-pairs 60x512x512 k5 w15: BF16 conv initialiser "
+                                f"(tcgen05) + {args.learned_iters} Alg. 1 iteration(s)"),
+                   "frames": w.N, "height": w.H, "width": w.W,
+                   "patch": w.patch, "window": w.window,
+                   "iters": w.iters if not learned else args.learned_iters, "levels": w.levels,
+                   "nnfs_per_step": w.pairs(),
+                   "candidate_evals_per_step": (w.candidate_evals() if not learned else
+                                                w.pairs() * w.H * w.W * (1 + args.learned_iters *
+                                                                         (4 + w.random_search_radii()))),
+                   "learned_init": learned_info,
                    "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"{world} independent clip(s), one per GPU"},
         "roofline": roof,

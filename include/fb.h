@@ -112,6 +112,7 @@ typedef enum fb_kernel_kind {
     FB_K_UNPACK,        /* packed NNF -> int32 (row, col)                        */
     FB_K_PACK,          /* int32 (row, col) -> packed NNF                        */
     FB_K_COMBINE,       /* Alg. 2 remap fused with Eq. 2 / keyframe weights      */
+    FB_K_INITNET,       /* learned initialiser: network forward + initial fields  */
     FB_K_COUNT
 } fb_kernel_kind;
 
@@ -237,22 +238,24 @@ int fb_ctx_batch_variant(const fb_ctx *ctx, int patch);
 /* ---------------------------------------------------------------------------------
  * Learned NNF initialiser.  Not in the paper (its method is model-free and needs no
  * training, Sec. 3.1): a small BF16 convolutional pyramid that maps a pair of guide
- * frames (source, target) at a quarter of their resolution to an offset field, trained
+ * frames (source, target) at 1/4 or 1/8 of their resolution to an offset field, trained
  * on NNFs that Alg. 1 itself computes, so that Alg. 1 can start near its answer and run
  * fewer iterations.  Convolutions run on the tcgen05 tensor cores (BF16 operands, FP32
  * accumulation); forward, backward and the Adam update are this library's kernels.
  * Architecture: 12 3x3 conv layers (encoder 8->32->32, ->64/2->64, ->96/2->96,
  * ->128/2->128; decoder with nearest upsampling and skip concatenation 224->96,
  * 160->64, 96->32; head 32->8 of which channels 0,1 are the (row, col) offset / 16 in
- * full-resolution pixels), ReLU except on the head; 779,592 parameters.
- * Guide frames must have H and W divisible by 32.  All pointers are device pointers
- * unless stated.  A net belongs to the device current at creation; not thread-safe.
+ * full-resolution pixels), ReLU except on the head; 779,592 parameters.  The network
+ * runs at Hq x Wq = H/D x W/D for a downscale D in {4, 8} (D x D box means of the
+ * guides); H and W must be multiples of 8 D.  All pointers are device pointers unless
+ * stated.  A net belongs to the device current at creation; not thread-safe.
  * --------------------------------------------------------------------------------- */
 typedef struct fb_initnet fb_initnet;
 
-/* Allocate a net for up to max_pairs pairs of H x W frames (parameters start at zero:
- * set them with fb_initnet_set_params).  FB_ERR_ARG if H or W is not a multiple of 32. */
-int fb_initnet_create(fb_ctx *ctx, fb_initnet **out, int max_pairs, int H, int W);
+/* Allocate a net for up to max_pairs pairs of H x W frames at downscale D (4 or 8);
+ * parameters start at zero: set them with fb_initnet_set_params.  FB_ERR_ARG if H or W
+ * is not a multiple of 8 D. */
+int fb_initnet_create(fb_ctx *ctx, fb_initnet **out, int max_pairs, int H, int W, int downscale);
 int fb_initnet_destroy(fb_initnet *net);
 const char *fb_initnet_last_error(const fb_initnet *net);
 
@@ -266,18 +269,18 @@ int fb_initnet_set_params(fb_initnet *net, const float *host_in);
 int fb_initnet_get_grads(fb_initnet *net, float *host_out);
 
 /* Forward pass for n pairs: src, tgt are n x H x W x 3 uint8 stacks (pair p = source
- * frame src[p] -> target frame tgt[p]).  head_out (nullable): n x H/4 x W/4 x 8 float,
+ * frame src[p] -> target frame tgt[p]).  head_out (nullable): n x Hq x Wq x 8 float,
  * channels 0,1 = predicted (row, col) offset / 16.  Async on `stream`. */
 int fb_initnet_forward(fb_initnet *net, const uint8_t *src, const uint8_t *tgt, int n,
                        float *head_out, void *stream);
 
 /* Initial NNF of the n pairs of the last forward pass: F0(x) = clamp(x + rint(16 *
- * head(x / 4))), written as n x H x W x 2 int32.  Async. */
+ * head(x / D))), written as n x H x W x 2 int32.  Async. */
 int fb_initnet_init_nnf(fb_initnet *net, int n, int32_t *nnf_out, void *stream);
 
 /* One training step on n pairs: forward, smooth-L1 loss (1 pixel transition) between
- * 16 * head[..., 0:2] and `target` (n x H/4 x W/4 x 2 float, full-resolution pixels)
- * weighted by `weight` (n x H/4 x W/4 float, or NULL = 1) and divided by weight_sum,
+ * 16 * head[..., 0:2] and `target` (n x Hq x Wq x 2 float, full-resolution pixels)
+ * weighted by `weight` (n x Hq x Wq float, or NULL = 1) and divided by weight_sum,
  * backward, and an Adam update with step size lr (lr = 0: gradients only).  The loss
  * is written to the device float *loss_out (nullable).  Async. */
 int fb_initnet_train_step(fb_initnet *net, const uint8_t *src, const uint8_t *tgt, int n,
@@ -287,11 +290,12 @@ int fb_initnet_train_step(fb_initnet *net, const uint8_t *src, const uint8_t *tg
 /* Attach (or with NULL detach) the learned initialiser used by FB_FLAG_LEARNED_INIT. */
 int fb_ctx_set_initnet(fb_ctx *ctx, fb_initnet *net);
 
-/* Training targets from fields computed by Alg. 1 (nnf: n x H x W x 2 int32): per 4x4
- * block the mean offset F(x) - x (target, n x H/4 x W/4 x 2 float) and weight 1 where
- * all 16 offsets lie within 2 pixels of that mean, else 0 (weight, nullable).  Async. */
-int fb_initnet_targets(const int32_t *nnf, int n, int H, int W, float *target, float *weight,
-                       void *stream);
+/* Training targets from fields computed by Alg. 1 (nnf: n x H x W x 2 int32): per D x D
+ * block the mean offset F(x) - x (target, n x H/D x W/D x 2 float) and weight 1 where
+ * every offset of the block lies within D/2 pixels of that mean, else 0 (weight,
+ * nullable).  D = downscale, 4 or 8.  Async. */
+int fb_initnet_targets(const int32_t *nnf, int n, int H, int W, int downscale, float *target,
+                       float *weight, void *stream);
 
 /* FB_ERR_TIMEOUT if a tensor-core kernel of this net hit its bounded wait. */
 int fb_initnet_status(fb_initnet *net);

@@ -87,12 +87,12 @@ def n_params() -> int:
     return sum(cout * 9 * cin + cout for cin, cout, _, _ in LAYERS)
 
 
-def net_input(src, tgt):
-    """4x4 box means of both guide stacks, /255 - 0.5, 8 channels (last two zero)."""
+def net_input(src, tgt, ds=4):
+    """ds x ds box means of both guide stacks, /255 - 0.5, 8 channels (last two zero)."""
     n, H, W, _ = src.shape
     def q(a):
-        return a.astype(np.float64).reshape(n, H // 4, 4, W // 4, 4, 3).mean(axis=(2, 4))
-    x = np.zeros((n, H // 4, W // 4, 8))
+        return a.astype(np.float64).reshape(n, H // ds, ds, W // ds, ds, 3).mean(axis=(2, 4))
+    x = np.zeros((n, H // ds, W // ds, 8))
     x[..., 0:3] = q(src) / 255.0 - 0.5
     x[..., 3:6] = q(tgt) / 255.0 - 0.5
     return bf16(x)
@@ -102,10 +102,10 @@ def _up(a):
     return np.repeat(np.repeat(a, 2, axis=1), 2, axis=2)
 
 
-def forward(params, src, tgt):
-    """Returns (head [n, H/4, W/4, 8] float64, cache for backward)."""
+def forward(params, src, tgt, ds=4):
+    """Returns (head [n, H/ds, W/ds, 8] float64, cache for backward)."""
     P = [(bf16(w), b) for w, b in split_params(params)]
-    acts = {"in": net_input(src, tgt)}
+    acts = {"in": net_input(src, tgt, ds)}
     order = ["e0a", "e0b", "e1a", "e1b", "e2a", "e2b", "e3a", "e3b", "d2", "d1", "d0", "head"]
     inputs = {"e0a": "in", "e0b": "e0a", "e1a": "e0b", "e1b": "e1a", "e2a": "e1b", "e2b": "e2a",
               "e3a": "e2b", "e3b": "e3a", "d2": "cat2", "d1": "cat1", "d0": "cat0", "head": "d0"}

@@ -44,7 +44,8 @@ def FB_BATCH_VARIANT(v: int) -> int:
     return (v + 1) << 8
 
 # fb_kernel_kind, in header order.
-KERNEL_KINDS = ("prep", "downsample", "style", "init", "iter", "unpack", "pack", "combine")
+KERNEL_KINDS = ("prep", "downsample", "style", "init", "iter", "unpack", "pack", "combine",
+                "initnet")
 
 
 class Params(ctypes.Structure):
@@ -126,7 +127,7 @@ def lib() -> ctypes.CDLL:
                                     ctypes.POINTER(ctypes.c_int)]
         L.fb_batch_plan.restype = ctypes.c_int
         L.fb_initnet_create.argtypes = [_vp, ctypes.POINTER(_vp), ctypes.c_int, ctypes.c_int,
-                                        ctypes.c_int]
+                                        ctypes.c_int, ctypes.c_int]
         L.fb_initnet_destroy.argtypes = [_vp]
         L.fb_initnet_last_error.argtypes = [_vp]
         L.fb_initnet_last_error.restype = ctypes.c_char_p
@@ -154,7 +155,8 @@ def lib() -> ctypes.CDLL:
         L.fb_ctx_set_initnet.restype = ctypes.c_int
         L.fb_ctx_energy.argtypes = [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_uint64)]
         L.fb_ctx_energy.restype = ctypes.c_int
-        L.fb_initnet_targets.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp, _vp]
+        L.fb_initnet_targets.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         _vp, _vp, _vp]
         L.fb_initnet_targets.restype = ctypes.c_int
         L.fb_ctx_set_pair_budget.argtypes = [_vp, ctypes.c_size_t]
         L.fb_ctx_set_pair_budget.restype = ctypes.c_int
@@ -400,12 +402,13 @@ def batch_variant_name(v: int) -> str:
 class InitNet:
     """fb_initnet: the BF16 conv pyramid that proposes initial NNFs (tensor-core kernels)."""
 
-    def __init__(self, ctx: Context, max_pairs: int, H: int, W: int):
+    def __init__(self, ctx: Context, max_pairs: int, H: int, W: int, downscale: int = 8):
         h = _vp()
-        rc = lib().fb_initnet_create(ctx.handle, ctypes.byref(h), max_pairs, H, W)
+        rc = lib().fb_initnet_create(ctx.handle, ctypes.byref(h), max_pairs, H, W, downscale)
         if rc != FB_OK:
             raise FastBlendError(rc, "fb_initnet_create")
         self._h, self.ctx, self.max_pairs, self.H, self.W = h, ctx, max_pairs, H, W
+        self.ds = downscale
         self.n_params = int(lib().fb_initnet_param_count(h))
 
     @property
@@ -447,7 +450,8 @@ class InitNet:
 
     def forward(self, src: torch.Tensor, tgt: torch.Tensor, stream=None) -> torch.Tensor:
         n = int(src.shape[0])
-        head = torch.empty((n, self.H // 4, self.W // 4, 8), dtype=torch.float32, device=src.device)
+        head = torch.empty((n, self.H // self.ds, self.W // self.ds, 8), dtype=torch.float32,
+                           device=src.device)
         self._check(lib().fb_initnet_forward(self._h, _ptr(src, torch.uint8, "src"),
                                              _ptr(tgt, torch.uint8, "tgt"), n,
                                              _ptr(head, torch.float32, "head"),
@@ -467,7 +471,7 @@ class InitNet:
             loss_out = torch.zeros(1, dtype=torch.float32, device=src.device)
         if weight_sum is None:
             weight_sum = float(weight.sum()) if weight is not None else float(
-                n * (self.H // 4) * (self.W // 4))
+                n * (self.H // self.ds) * (self.W // self.ds))
         self._check(lib().fb_initnet_train_step(
             self._h, _ptr(src, torch.uint8, "src"), _ptr(tgt, torch.uint8, "tgt"), n,
             _ptr(target, torch.float32, "target"),
@@ -480,12 +484,13 @@ class InitNet:
         return int(lib().fb_initnet_status(self._h))
 
 
-def fb_initnet_targets(nnf: torch.Tensor, stream=None):
-    """Targets (n,H/4,W/4,2) and weights (n,H/4,W/4) from Alg. 1 fields (n,H,W,2) int32."""
+def fb_initnet_targets(nnf: torch.Tensor, downscale: int = 8, stream=None):
+    """Targets (n,H/D,W/D,2) and weights (n,H/D,W/D) from Alg. 1 fields (n,H,W,2) int32."""
     n, H, W = (int(v) for v in nnf.shape[:3])
-    target = torch.empty((n, H // 4, W // 4, 2), dtype=torch.float32, device=nnf.device)
-    weight = torch.empty((n, H // 4, W // 4), dtype=torch.float32, device=nnf.device)
-    rc = lib().fb_initnet_targets(_ptr(nnf, torch.int32, "nnf"), n, H, W, target.data_ptr(),
+    D = downscale
+    target = torch.empty((n, H // D, W // D, 2), dtype=torch.float32, device=nnf.device)
+    weight = torch.empty((n, H // D, W // D), dtype=torch.float32, device=nnf.device)
+    rc = lib().fb_initnet_targets(_ptr(nnf, torch.int32, "nnf"), n, H, W, D, target.data_ptr(),
                                   weight.data_ptr(), _stream_handle(stream, nnf.device.index or 0))
     if rc != FB_OK:
         raise FastBlendError(rc, "fb_initnet_targets")

@@ -445,10 +445,20 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
                 const int cap = fb::initnet_max_pairs(ctx->init_net);
                 for (int q = 0; q < c.n_pairs; q += cap) {
                     const int cnt = c.n_pairs - q < cap ? c.n_pairs - q : cap;
+                    cudaEvent_t ea = nullptr, eb = nullptr;
+                    if (ctx->profiling) {
+                        ea = next_event(ctx);
+                        eb = next_event(ctx);
+                        if (ea && eb) FB_CUDA(ctx, cudaEventRecord(ea, st));
+                    }
                     int r2 = fb::initnet_init_pairs(ctx->init_net, g_dev, b.pairs, c.pair0 + q, cnt,
                                                     b.init + static_cast<size_t>(q) * npx0 * 2, st);
                     if (r2) return fail(ctx, r2, "learned initialiser failed");
                     ctx->launches += 17;  // input, 3 concatenations, 12 convolutions, offsets
+                    if (ea && eb) {
+                        FB_CUDA(ctx, cudaEventRecord(eb, st));
+                        ctx->recs.push_back(fb_ctx::Rec{FB_K_INITNET, ea, eb});
+                    }
                 }
                 init = b.init;
             }

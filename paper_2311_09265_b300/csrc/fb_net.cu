@@ -85,10 +85,10 @@ cudaError_t conv_wgrad(const ConvGeom& g, const bf16* dZ, const bf16* X, float* 
 // ---------------------------------------------------------------------------------
 inline unsigned blocks(size_t n, unsigned per = 256) { return static_cast<unsigned>((n + per - 1) / per); }
 
-// Network input: 4x4 box means of both guides, scaled to [-0.5, 0.5], 8 channels.
+// Network input: DS x DS box means of both guides, scaled to [-0.5, 0.5], 8 channels.
 __global__ void prep_input_kernel(const uint8_t* __restrict__ src, const uint8_t* __restrict__ tgt,
-                                  int n, int H, int W, bf16* __restrict__ out) {
-    const int Hq = H / 4, Wq = W / 4;
+                                  int n, int H, int W, int DS, bf16* __restrict__ out) {
+    const int Hq = H / DS, Wq = W / DS;
     const size_t total = static_cast<size_t>(n) * Hq * Wq;
     const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= total) return;
@@ -96,24 +96,25 @@ __global__ void prep_input_kernel(const uint8_t* __restrict__ src, const uint8_t
     const int rem = static_cast<int>(i - static_cast<size_t>(img) * Hq * Wq);
     const int qy = rem / Wq, qx = rem % Wq;
     float s[6] = {0, 0, 0, 0, 0, 0};
-    for (int dy = 0; dy < 4; ++dy)
-        for (int dx = 0; dx < 4; ++dx) {
-            const size_t p = ((static_cast<size_t>(img) * H + 4 * qy + dy) * W + 4 * qx + dx) * 3;
+    for (int dy = 0; dy < DS; ++dy)
+        for (int dx = 0; dx < DS; ++dx) {
+            const size_t p = ((static_cast<size_t>(img) * H + DS * qy + dy) * W + DS * qx + dx) * 3;
             for (int ch = 0; ch < 3; ++ch) {
                 s[ch] += src[p + ch];
                 s[3 + ch] += tgt[p + ch];
             }
         }
     bf16* o = out + i * 8;
-    for (int ch = 0; ch < 6; ++ch) o[ch] = __float2bfloat16_rn(s[ch] / (16.f * 255.f) - 0.5f);
+    const float scale = 1.f / (static_cast<float>(DS * DS) * 255.f);
+    for (int ch = 0; ch < 6; ++ch) o[ch] = __float2bfloat16_rn(s[ch] * scale - 0.5f);
     o[6] = o[7] = __float2bfloat16_rn(0.f);
 }
 
 // The same input built from a guide stack and pairs [first, first + n) of a pair table.
 __global__ void prep_input_pairs_kernel(const uint8_t* __restrict__ guides,
                                         const fb::PairDesc* __restrict__ pairs, int first, int n,
-                                        int H, int W, bf16* __restrict__ out) {
-    const int Hq = H / 4, Wq = W / 4;
+                                        int H, int W, int DS, bf16* __restrict__ out) {
+    const int Hq = H / DS, Wq = W / DS;
     const size_t total = static_cast<size_t>(n) * Hq * Wq;
     const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= total) return;
@@ -125,44 +126,49 @@ __global__ void prep_input_pairs_kernel(const uint8_t* __restrict__ guides,
     const uint8_t* src = guides + static_cast<size_t>(pd.src) * fsz;
     const uint8_t* tgt = guides + static_cast<size_t>(pd.tgt) * fsz;
     float s[6] = {0, 0, 0, 0, 0, 0};
-    for (int dy = 0; dy < 4; ++dy)
-        for (int dx = 0; dx < 4; ++dx) {
-            const size_t p = (static_cast<size_t>(4 * qy + dy) * W + 4 * qx + dx) * 3;
+    for (int dy = 0; dy < DS; ++dy)
+        for (int dx = 0; dx < DS; ++dx) {
+            const size_t p = (static_cast<size_t>(DS * qy + dy) * W + DS * qx + dx) * 3;
             for (int ch = 0; ch < 3; ++ch) {
                 s[ch] += src[p + ch];
                 s[3 + ch] += tgt[p + ch];
             }
         }
     bf16* o = out + i * 8;
-    for (int ch = 0; ch < 6; ++ch) o[ch] = __float2bfloat16_rn(s[ch] / (16.f * 255.f) - 0.5f);
+    const float scale = 1.f / (static_cast<float>(DS * DS) * 255.f);
+    for (int ch = 0; ch < 6; ++ch) o[ch] = __float2bfloat16_rn(s[ch] * scale - 0.5f);
     o[6] = o[7] = __float2bfloat16_rn(0.f);
 }
 
-// Training targets from Alg. 1 fields: the mean offset F(x) - x over each 4x4 block,
-// with weight 1 where all 16 offsets lie within 2 pixels of that mean (one coherent
-// motion), else 0.
-__global__ void nnf_targets_kernel(const int32_t* __restrict__ nnf, int n, int H, int W,
+// Training targets from Alg. 1 fields: the mean offset F(x) - x over each DS x DS block,
+// with weight 1 where every offset of the block lies within DS/2 pixels of that mean
+// (one coherent motion), else 0.
+__global__ void nnf_targets_kernel(const int32_t* __restrict__ nnf, int n, int H, int W, int DS,
                                    float* __restrict__ target, float* __restrict__ weight) {
-    const int Hq = H / 4, Wq = W / 4;
+    const int Hq = H / DS, Wq = W / DS;
     const size_t total = static_cast<size_t>(n) * Hq * Wq;
     const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= total) return;
     const int img = static_cast<int>(i / (static_cast<size_t>(Hq) * Wq));
     const int rem = static_cast<int>(i - static_cast<size_t>(img) * Hq * Wq);
     const int qy = rem / Wq, qx = rem % Wq;
-    float oy[16], ox[16], my = 0.f, mx = 0.f;
-    for (int j = 0; j < 16; ++j) {
-        const int y = 4 * qy + j / 4, x = 4 * qx + j % 4;
+    float my = 0.f, mx = 0.f;
+    for (int j = 0; j < DS * DS; ++j) {
+        const int y = DS * qy + j / DS, x = DS * qx + j % DS;
         const size_t p = (static_cast<size_t>(img) * H + y) * W + x;
-        oy[j] = static_cast<float>(nnf[2 * p] - y);
-        ox[j] = static_cast<float>(nnf[2 * p + 1] - x);
-        my += oy[j];
-        mx += ox[j];
+        my += static_cast<float>(nnf[2 * p] - y);
+        mx += static_cast<float>(nnf[2 * p + 1] - x);
     }
-    my *= (1.f / 16.f);
-    mx *= (1.f / 16.f);
+    my /= static_cast<float>(DS * DS);
+    mx /= static_cast<float>(DS * DS);
+    const float tol = 0.5f * DS;
     bool ok = true;
-    for (int j = 0; j < 16; ++j) ok = ok && fabsf(oy[j] - my) <= 2.f && fabsf(ox[j] - mx) <= 2.f;
+    for (int j = 0; j < DS * DS; ++j) {
+        const int y = DS * qy + j / DS, x = DS * qx + j % DS;
+        const size_t p = (static_cast<size_t>(img) * H + y) * W + x;
+        ok = ok && fabsf(static_cast<float>(nnf[2 * p] - y) - my) <= tol &&
+             fabsf(static_cast<float>(nnf[2 * p + 1] - x) - mx) <= tol;
+    }
     target[2 * i] = my;
     target[2 * i + 1] = mx;
     if (weight) weight[i] = ok ? 1.f : 0.f;
@@ -299,8 +305,8 @@ __global__ void adam_kernel(float* __restrict__ w, const float* __restrict__ g, 
     w[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
 }
 
-// Initial NNF from predicted offsets: F0(x) = clamp(x + rint(offset(x / 4))).
-__global__ void offsets_to_nnf_kernel(const float* __restrict__ head, int n, int H, int W,
+// Initial NNF from predicted offsets: F0(x) = clamp(x + rint(offset(x / DS))).
+__global__ void offsets_to_nnf_kernel(const float* __restrict__ head, int n, int H, int W, int DS,
                                       int32_t* __restrict__ nnf) {
     const size_t total = static_cast<size_t>(n) * H * W;
     const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -308,8 +314,8 @@ __global__ void offsets_to_nnf_kernel(const float* __restrict__ head, int n, int
     const int img = static_cast<int>(i / (static_cast<size_t>(H) * W));
     const int rem = static_cast<int>(i - static_cast<size_t>(img) * H * W);
     const int y = rem / W, x = rem % W;
-    const int Hq = H / 4, Wq = W / 4;
-    const size_t q = (static_cast<size_t>(img) * Hq + min(y / 4, Hq - 1)) * Wq + min(x / 4, Wq - 1);
+    const int Hq = H / DS, Wq = W / DS;
+    const size_t q = (static_cast<size_t>(img) * Hq + min(y / DS, Hq - 1)) * Wq + min(x / DS, Wq - 1);
     const float dy = kOffsetScale * head[q * 8 + 0], dx = kOffsetScale * head[q * 8 + 1];
     const int ry = y + static_cast<int>(rintf(fminf(fmaxf(dy, -32768.f), 32768.f)));
     const int rx = x + static_cast<int>(rintf(fminf(fmaxf(dx, -32768.f), 32768.f)));
@@ -345,6 +351,7 @@ struct fb_initnet {
     fb_ctx* ctx = nullptr;
     int device = 0;
     int max_pairs = 0, H = 0, W = 0;
+    int ds = 4;                             // guide pixels per network pixel, per axis
     int sms = 0;
     size_t n_params = 0;                    // weights + biases
     size_t w_off[kNumLayers], b_off[kNumLayers];
@@ -399,7 +406,7 @@ constexpr int kIn[12] = {0, 1, 2, 3, 4, 5, 6, 7, 9, 11, 13, 14};
 constexpr int kOut[12] = {1, 2, 3, 4, 5, 6, 7, 8, 10, 12, 14, -1};
 
 ConvGeom geom(const fb_initnet* net, int l, int n) {
-    const int Hq = net->H / 4, Wq = net->W / 4;
+    const int Hq = net->H / net->ds, Wq = net->W / net->ds;
     const fb::net::LayerDef& d = kLayers[l];
     const int hin = Hq / kTens[kIn[l]].div, win = Wq / kTens[kIn[l]].div;
     ConvGeom g;
@@ -415,7 +422,7 @@ ConvGeom geom(const fb_initnet* net, int l, int n) {
 }
 
 size_t tens_elems(const fb_initnet* net, int t, int n) {
-    const int Hq = net->H / 4, Wq = net->W / 4;
+    const int Hq = net->H / net->ds, Wq = net->W / net->ds;
     return static_cast<size_t>(n) * (Hq / kTens[t].div) * (Wq / kTens[t].div) * kTens[t].ch;
 }
 
@@ -423,8 +430,8 @@ int net_layers(fb_initnet* net, int n, cudaStream_t st);
 
 int net_forward(fb_initnet* net, const uint8_t* src, const uint8_t* tgt, int n, cudaStream_t st) {
     using namespace fb::net;
-    const size_t Pq = static_cast<size_t>(n) * (net->H / 4) * (net->W / 4);
-    prep_input_kernel<<<blocks(Pq), 256, 0, st>>>(src, tgt, n, net->H, net->W, net->act[0]);
+    const size_t Pq = static_cast<size_t>(n) * (net->H / net->ds) * (net->W / net->ds);
+    prep_input_kernel<<<blocks(Pq), 256, 0, st>>>(src, tgt, n, net->H, net->W, net->ds, net->act[0]);
     NET_CUDA(net, cudaGetLastError());
     return net_layers(net, n, st);
 }
@@ -437,7 +444,7 @@ int net_layers(fb_initnet* net, int n, cudaStream_t st) {
             const int lo = l == 8 ? 8 : (l == 9 ? 10 : 12);
             const int skip = l == 8 ? 6 : (l == 9 ? 4 : 2);
             const int cat = kIn[l];
-            const int H2 = (net->H / 4) / kTens[cat].div, W2 = (net->W / 4) / kTens[cat].div;
+            const int H2 = (net->H / net->ds) / kTens[cat].div, W2 = (net->W / net->ds) / kTens[cat].div;
             const size_t units = static_cast<size_t>(n) * H2 * W2 * (kTens[cat].ch / 8);
             concat_up_kernel<<<blocks(units), 256, 0, st>>>(net->act[lo], kTens[lo].ch, net->act[skip],
                                                              kTens[skip].ch, n, H2, W2, net->act[cat]);
@@ -472,14 +479,14 @@ int initnet_init_pairs(::fb_initnet* net, const uint8_t* guides, const PairDesc*
                        int n, int32_t* nnf_out, cudaStream_t st) {
     using namespace fb::net;
     if (n < 1 || n > net->max_pairs) return FB_ERR_ARG;
-    const size_t Pq = static_cast<size_t>(n) * (net->H / 4) * (net->W / 4);
+    const size_t Pq = static_cast<size_t>(n) * (net->H / net->ds) * (net->W / net->ds);
     prep_input_pairs_kernel<<<blocks(Pq), 256, 0, st>>>(guides, pairs, first, n, net->H, net->W,
-                                                        net->act[0]);
+                                                        net->ds, net->act[0]);
     NET_CUDA(net, cudaGetLastError());
     int rc = net_layers(net, n, st);
     if (rc) return rc;
     const size_t total = static_cast<size_t>(n) * net->H * net->W;
-    offsets_to_nnf_kernel<<<blocks(total), 256, 0, st>>>(net->head, n, net->H, net->W, nnf_out);
+    offsets_to_nnf_kernel<<<blocks(total), 256, 0, st>>>(net->head, n, net->H, net->W, net->ds, nnf_out);
     NET_CUDA(net, cudaGetLastError());
     return FB_OK;
 }
@@ -495,21 +502,25 @@ void initnet_dims(const ::fb_initnet* net, int* H, int* W) {
 
 extern "C" {
 
-int fb_initnet_targets(const int32_t* nnf, int n, int H, int W, float* target, float* weight,
-                       void* stream) {
-    if (!nnf || !target || n < 1 || H < 4 || W < 4 || H % 4 || W % 4) return FB_ERR_ARG;
-    const size_t total = static_cast<size_t>(n) * (H / 4) * (W / 4);
+int fb_initnet_targets(const int32_t* nnf, int n, int H, int W, int downscale, float* target,
+                       float* weight, void* stream) {
+    if (!nnf || !target || n < 1 || (downscale != 4 && downscale != 8) || H % downscale || W % downscale)
+        return FB_ERR_ARG;
+    const size_t total = static_cast<size_t>(n) * (H / downscale) * (W / downscale);
     fb::net::nnf_targets_kernel<<<fb::net::blocks(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        nnf, n, H, W, target, weight);
+        nnf, n, H, W, downscale, target, weight);
     return cudaGetLastError() == cudaSuccess ? FB_OK : FB_ERR_CUDA;
 }
 
-int fb_initnet_create(fb_ctx* ctx, fb_initnet** out, int max_pairs, int H, int W) {
+int fb_initnet_create(fb_ctx* ctx, fb_initnet** out, int max_pairs, int H, int W, int downscale) {
     if (!ctx || !out) return FB_ERR_ARG;
     *out = nullptr;
-    if (max_pairs < 1 || H < 32 || W < 32 || H % 32 || W % 32 || H > 32767 || W > 32767)
+    if (downscale != 4 && downscale != 8) return FB_ERR_ARG;
+    const int unit = 8 * downscale;  // three stride-2 levels below the network resolution
+    if (max_pairs < 1 || H < unit || W < unit || H % unit || W % unit || H > 32767 || W > 32767)
         return FB_ERR_ARG;
     fb_initnet* net = new fb_initnet();
+    net->ds = downscale;
     net->ctx = ctx;
     cudaGetDevice(&net->device);
     net->max_pairs = max_pairs;
@@ -540,7 +551,7 @@ int fb_initnet_create(fb_ctx* ctx, fb_initnet** out, int max_pairs, int H, int W
         o_act[t] = take(e * 2);
         o_dact[t] = take(e * 4);
     }
-    const size_t Pq = static_cast<size_t>(max_pairs) * (H / 4) * (W / 4);
+    const size_t Pq = static_cast<size_t>(max_pairs) * (H / downscale) * (W / downscale);
     const size_t o_dz = take(max_t * 2), o_head = take(Pq * 8 * 4), o_dhead = take(Pq * 8 * 4);
     const size_t o_loss = take(4), o_status = take(4);
     if (cudaMalloc(reinterpret_cast<void**>(&net->arena), bytes) != cudaSuccess) {
@@ -603,7 +614,7 @@ int fb_initnet_forward(fb_initnet* net, const uint8_t* src, const uint8_t* tgt, 
     int rc = net_forward(net, src, tgt, n, st);
     if (rc) return rc;
     if (head_out) {
-        const size_t Pq = static_cast<size_t>(n) * (net->H / 4) * (net->W / 4);
+        const size_t Pq = static_cast<size_t>(n) * (net->H / net->ds) * (net->W / net->ds);
         NET_CUDA(net, cudaMemcpyAsync(head_out, net->head, Pq * 8 * 4, cudaMemcpyDeviceToDevice, st));
     }
     return FB_OK;
@@ -613,7 +624,7 @@ int fb_initnet_init_nnf(fb_initnet* net, int n, int32_t* nnf_out, void* stream) 
     if (!net || !nnf_out || n < 1 || n > net->max_pairs) return FB_ERR_ARG;
     const size_t total = static_cast<size_t>(n) * net->H * net->W;
     fb::net::offsets_to_nnf_kernel<<<fb::net::blocks(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
-        net->head, n, net->H, net->W, nnf_out);
+        net->head, n, net->H, net->W, net->ds, nnf_out);
     NET_CUDA(net, cudaGetLastError());
     return FB_OK;
 }
@@ -627,7 +638,7 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = net_forward(net, src, tgt, n, st);
     if (rc) return rc;
-    const size_t Pq = static_cast<size_t>(n) * (net->H / 4) * (net->W / 4);
+    const size_t Pq = static_cast<size_t>(n) * (net->H / net->ds) * (net->W / net->ds);
     NET_CUDA(net, cudaMemsetAsync(net->loss, 0, 4, st));
     NET_CUDA(net, cudaMemsetAsync(net->grads, 0, net->n_params * 4, st));
     for (int t = 0; t < 15; ++t)
@@ -655,7 +666,7 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
             const int lo = l == 8 ? 8 : (l == 9 ? 10 : 12);
             const int skip = l == 8 ? 6 : (l == 9 ? 4 : 2);
             const int cat = kIn[l];
-            const int H2 = (net->H / 4) / kTens[cat].div, W2 = (net->W / 4) / kTens[cat].div;
+            const int H2 = (net->H / net->ds) / kTens[cat].div, W2 = (net->W / net->ds) / kTens[cat].div;
             const size_t tot = tens_elems(net, lo, n) + tens_elems(net, skip, n);
             concat_up_bwd_kernel<<<blocks(tot), 256, 0, st>>>(net->dact[cat], kTens[lo].ch, kTens[skip].ch, n,
                                                               H2, W2, net->dact[lo], net->dact[skip]);

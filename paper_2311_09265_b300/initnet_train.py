@@ -25,13 +25,13 @@ from . import (FB_FLAG_LEARNED_INIT, Context, InitNet, Params, fb_initnet_target
 class TrainingSet:
     frames: list          # per clip: (N, H, W, 3) uint8 CUDA tensor
     pairs: np.ndarray     # (P, 3): clip, source frame, target frame
-    target: torch.Tensor  # (P, H/4, W/4, 2) float32
-    weight: torch.Tensor  # (P, H/4, W/4) float32
+    target: torch.Tensor  # (P, H/D, W/D, 2) float32
+    weight: torch.Tensor  # (P, H/D, W/D) float32
 
 
 def make_training_set(ctx: Context, n_clips: int = 6, frames: int = 24, H: int = 512, W: int = 512,
                       max_gap: int = 7, pairs_per_clip: int = 160, target_iters: int = 12,
-                      seed: int = synth.clip_seed(4)) -> TrainingSet:
+                      downscale: int = 8, seed: int = synth.clip_seed(4)) -> TrainingSet:
     """Seeded clips, random ordered pairs with 1 <= |i - j| <= max_gap, and the method's
     own NNFs (target_iters iterations of Alg. 1) turned into block-mean targets."""
     rng = np.random.default_rng(seed)
@@ -48,7 +48,7 @@ def make_training_set(ctx: Context, n_clips: int = 6, frames: int = 24, H: int =
                 j = i + 1 if i + 1 < frames else i - 1
             p = Params.make(5, target_iters, 1, 0, seed + 7 * len(pairs), 0)
             F, _ = fb_nnf(ctx, gd[j], gd[i], p)
-            t, w = fb_initnet_targets(F.unsqueeze(0))
+            t, w = fb_initnet_targets(F.unsqueeze(0), downscale)
             pairs.append((c, j, i))
             targets.append(t[0])
             weights.append(w[0])
@@ -93,3 +93,32 @@ def train(net: InitNet, ts: TrainingSet, steps: int = 1500, batch_size: int = 8,
         if s % log_every == 0 or s == steps - 1:
             hist.append((s, float(loss.item()), time.perf_counter() - t0))
     return hist
+
+
+def save(net: InitNet, path: str) -> None:
+    """Checkpoint: the FP32 parameters (the Adam state is not kept)."""
+    np.save(path, net.get_params())
+
+
+def load(net: InitNet, path: str) -> None:
+    net.set_params(np.load(path))
+
+
+def train_default(ctx: Context, H: int, W: int, max_pairs: int = 256, steps: int = 2500,
+                  n_clips: int = 6, frames: int = 24, pairs_per_clip: int = 200,
+                  downscale: int = 8, seed: int = synth.clip_seed(4)):
+    """The recipe used for the benchmarks: a fresh net trained on the method's own NNFs
+    of seeded clips (different seeds from the evaluation clips).  Returns
+    (net, loss history, seconds for the training set, seconds for training)."""
+    t0 = time.perf_counter()
+    ts = make_training_set(ctx, n_clips=n_clips, frames=frames, H=H, W=W,
+                           pairs_per_clip=pairs_per_clip, downscale=downscale, seed=seed)
+    torch.cuda.synchronize()
+    t_data = time.perf_counter() - t0
+    net = InitNet(ctx, max_pairs, H, W, downscale=downscale)
+    net.set_params(initial_params(net.n_params, seed & 0xFFFF))
+    t0 = time.perf_counter()
+    hist = train(net, ts, steps=steps, batch_size=8, lr=2e-3, seed=seed & 0xFFFF,
+                 log_every=max(steps // 10, 1))
+    torch.cuda.synchronize()
+    return net, hist, t_data, time.perf_counter() - t0

@@ -96,7 +96,7 @@ def test_training_step_gradient_matches_oracle(fbp):
     noise = rel_l2(g_nudged, g_ref)
     head_noise = rel_l2(head_nudged[..., :2], head[..., :2])
     ctx = fbp.Context(0)
-    net = fbp.InitNet(ctx, n, H, W)
+    net = fbp.InitNet(ctx, n, H, W, downscale=4)
     net.set_params(params)
     g_src = torch.tensor(src, device="cuda")
     g_tgt = torch.tensor(tgt, device="cuda")
