@@ -69,6 +69,38 @@ def dist_env():
     return rank, world, local
 
 
+class RankGroup:
+    """The ranks of one bench run.  With more than one rank a gloo group carries the
+    barriers around the timed region and the max-over-ranks reduction of the timings;
+    the data path itself never communicates (each rank blends its own clips)."""
+
+    def __init__(self):
+        self.rank, self.world, self.local = dist_env()
+        if self.world > 1:
+            import torch.distributed as dist
+            os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
+            dist.init_process_group("gloo", rank=self.rank, world_size=self.world)
+
+    def barrier(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def max(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def close(self):
+        if self.world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
 def shard_seed(workload_seed: int, rank: int) -> int:
     """Rank r blends its own clip; rank 0 blends the named workload itself."""
     return workload_seed + 7919 * rank
@@ -232,14 +264,11 @@ def iter_ops_per_launch(w: synth.Workload) -> int:
 
 def run_gpu(args):
     import torch
-    import torch.distributed as dist
 
     import paper_2311_09265_b300 as fbp
 
-    rank, world, local = dist_env()
-    if world > 1:
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("gloo", rank=rank, world_size=world)
+    grp = RankGroup()
+    rank, world, local = grp.rank, grp.world, grp.local
     torch.cuda.set_device(local)
     fbp.build()
     learned = args.workload == "learned_512"
@@ -275,8 +304,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     # ---- timed region: device-resident inputs ----
-    if world > 1:
-        dist.barrier()
+    grp.barrier()
     torch.cuda.synchronize()
     ctx.profile(True)
     launches0 = ctx.launches
@@ -289,17 +317,12 @@ def run_gpu(args):
             step(g_d, s_d, out)
             ends[k].record()
         torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+    grp.barrier()
     launches = ctx.launches - launches0
     prof = ctx.profile_read()
     ctx.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-    total_ms = sum(step_ms)
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    total_ms = grp.max(sum(step_ms))
     value = aggregate(w.N, args.steps, world, total_ms)
     clocks = clk.summary()
 
@@ -310,17 +333,12 @@ def run_gpu(args):
         s_h = torch.tensor(s).pin_memory()
         o_h = torch.empty((w.N, w.H, w.W, 3), dtype=torch.float32).pin_memory()
         step(g_h, s_h, o_h)                     # warm (staging buffers)
-        if world > 1:
-            dist.barrier()
+        grp.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
             step(g_h, s_h, o_h)                 # synchronous: returns with o_h filled
-        t_e2e = time.perf_counter() - t0
-        if world > 1:
-            t = torch.tensor([t_e2e], dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            t_e2e = float(t.item())
+        t_e2e = grp.max(time.perf_counter() - t0)
         e2e = {"value": world * w.N * args.steps / t_e2e, "unit": "frames/s",
                "h2d_bytes_per_step": int(g_h.numel() + s_h.numel()),
                "d2h_bytes_per_step": int(o_h.numel() * 4)}
@@ -405,8 +423,7 @@ def run_gpu(args):
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
+    grp.close()
     return 0
 
 
@@ -439,16 +456,12 @@ def batch_candidate_evals(manifest) -> int:
 
 
 def run_gpu_batch(args):
-    import numpy as np
     import torch
-    import torch.distributed as dist
 
     import paper_2311_09265_b300 as fbp
 
-    rank, world, local = dist_env()
-    if world > 1:
-        os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
-        dist.init_process_group("gloo", rank=rank, world_size=world)
+    grp = RankGroup()
+    rank, world, local = grp.rank, grp.world, grp.local
     torch.cuda.set_device(local)
     fbp.build()
     manifest = synth.batch_manifest(seed=shard_seed(BATCH_SEED, rank))
@@ -467,8 +480,7 @@ def run_gpu_batch(args):
         fbp.fb_blend_batch(ctx, clips, params)
     torch.cuda.synchronize()
     t_build = time.perf_counter() - t_build
-    if world > 1:
-        dist.barrier()
+    grp.barrier()
     torch.cuda.synchronize()
     launches0 = ctx.launches
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -481,11 +493,8 @@ def run_gpu_batch(args):
             ends[k].record()
         torch.cuda.synchronize()
     launches = ctx.launches - launches0
-    total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+    grp.barrier()
+    total_ms = grp.max(sum(a.elapsed_time(b) for a, b in zip(starts, ends)))
     value = aggregate(frames, args.steps, world, total_ms)
     clocks = clk.summary()
 
@@ -515,6 +524,7 @@ def run_gpu_batch(args):
         hg = [torch.tensor(g).pin_memory() for g, _ in host]
         hs = [torch.tensor(s).pin_memory() for _, s in host]
         ho = [torch.empty(c[4].shape, dtype=torch.float32).pin_memory() for c in clips]
+        grp.barrier()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(args.steps):
@@ -525,7 +535,7 @@ def run_gpu_batch(args):
             for c, o in zip(clips, ho):
                 o.copy_(c[4], non_blocking=True)
             torch.cuda.synchronize()
-        t_e2e = time.perf_counter() - t0
+        t_e2e = grp.max(time.perf_counter() - t0)
         e2e = {"value": world * frames * args.steps / t_e2e, "unit": "frames/s",
                "h2d_bytes_per_step": int(sum(a.numel() + b.numel() for a, b in zip(hg, hs))),
                "d2h_bytes_per_step": int(sum(o.numel() * 4 for o in ho))}
@@ -561,8 +571,7 @@ def run_gpu_batch(args):
     if rank == 0:
         print(json.dumps(line))
     ctx.close()
-    if world > 1:
-        dist.destroy_process_group()
+    grp.close()
     return 0
 
 
