@@ -209,10 +209,10 @@ typedef struct fb_clip_desc {
  * persistent kernels (grid = SMs x resident blocks) that walk a flattened work list,
  * one launch per Jacobi iteration and patch size, in chunks whose NNF buffers fit the
  * pair budget.  The first submission of a given manifest (pointers, shapes, params)
- * tunes the tile shape / occupancy per patch size on its first iteration (all variants
- * give identical results), then captures the whole submission into a CUDA graph that
- * later submissions with the same manifest replay (FB_BATCH_NO_GRAPH: direct
- * launches).  The context keeps the tables, scratch and graph of the two most recent
+ * tunes the tile shape / occupancy per patch size on a few iterations of the size's
+ * first chunk (all variants give identical results), then captures the whole
+ * submission into a CUDA graph that later submissions with the same manifest replay
+ * (FB_BATCH_NO_GRAPH: direct launches).  The context keeps the tables, scratch and graph of the two most recent
  * manifests.  Async on `stream`; do not call it while `stream` is being captured. */
 int fb_blend_batch(fb_ctx *ctx, const fb_clip_desc *clips, int n_clips, const fb_params *p,
                    uint32_t flags, void *stream);

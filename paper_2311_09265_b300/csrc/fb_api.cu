@@ -586,20 +586,24 @@ size_t tiles_of(int H, int W, int th) {
     return static_cast<size_t>((W + 31) / 32) * static_cast<size_t>((H + th - 1) / th);
 }
 
-void item_maps(const HostChunk& ch, const fb_clip_desc* clips, int th, std::vector<int32_t>& ip,
-               std::vector<int32_t>& it) {
+// Work units of the persistent kernels: runs of `per_claim` consecutive tiles (tile
+// height th) of one pair, pair-major.
+void item_maps(const HostChunk& ch, const fb_clip_desc* clips, int th, int per_claim,
+               std::vector<int32_t>& ip, std::vector<int32_t>& it) {
     ip.clear();
     it.clear();
     for (size_t p = 0; p < ch.pairs.size(); ++p) {
         const fb_clip_desc& d = clips[ch.pairs[p].clip];
         const size_t nt = tiles_of(d.H, d.W, th);
-        for (size_t t = 0; t < nt; ++t) {
+        for (size_t t = 0; t < nt; t += static_cast<size_t>(per_claim)) {
             ip.push_back(static_cast<int32_t>(p));
             it.push_back(static_cast<int32_t>(t));
         }
     }
 }
 
+// Work units of the combine kernel: runs of kCombineTilesPerClaim 32x8 tiles of one
+// output frame.
 void job_maps(const HostChunk& ch, const fb_clip_desc* clips, std::vector<int32_t>& ij,
               std::vector<int32_t>& it) {
     ij.clear();
@@ -607,7 +611,7 @@ void job_maps(const HostChunk& ch, const fb_clip_desc* clips, std::vector<int32_
     for (size_t j = 0; j < ch.jobs.size(); ++j) {
         const fb_clip_desc& d = clips[ch.jobs[j].clip];
         const size_t nt = tiles_of(d.H, d.W, 8);
-        for (size_t t = 0; t < nt; ++t) {
+        for (size_t t = 0; t < nt; t += static_cast<size_t>(fb::kCombineTilesPerClaim)) {
             ij.push_back(static_cast<int32_t>(j));
             it.push_back(static_cast<int32_t>(t));
         }
@@ -653,7 +657,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     size_t n_counters = 2;  // tuning launches
     for (const HostChunk& ch : chunks) n_counters += 2 + static_cast<size_t>(p->iters);
     auto layout = [&](Carver& c, BatchClip** d_clips, std::vector<ClipBufs>& cb,
-                      uint32_t** fe, std::vector<std::array<void*, 6>>& tabs, int** counters) {
+                      uint32_t** fe, std::vector<std::array<void*, 8>>& tabs, int** counters) {
         *counters = c.take<int>(n_counters);
         *d_clips = c.take<BatchClip>(n);
         cb.assign(n, ClipBufs{});
@@ -678,12 +682,14 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
             tabs[ci][3] = c.take<BatchJob>(std::max<size_t>(ch.jobs.size(), 1));
             tabs[ci][4] = c.take<int32_t>(std::max<size_t>(job_items, 1));
             tabs[ci][5] = c.take<int32_t>(std::max<size_t>(job_items, 1));
+            tabs[ci][6] = c.take<int32_t>(std::max<size_t>(max_items, 1));  // init units
+            tabs[ci][7] = c.take<int32_t>(std::max<size_t>(max_items, 1));
         }
     };
     BatchClip* d_clips = nullptr;
     std::vector<ClipBufs> cb;
     uint32_t* fe[4] = {};
-    std::vector<std::array<void*, 6>> tabs;
+    std::vector<std::array<void*, 8>> tabs;
     int* counters = nullptr;
     layout(cv, &d_clips, cb, fe, tabs, &counters);
     be->bytes = align_up(cv.off, 1 << 20);
@@ -704,6 +710,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     }
     FB_CUDA(ctx, cudaMemcpy(d_clips, hclips.data(), sizeof(BatchClip) * n, cudaMemcpyHostToDevice));
     std::vector<int32_t> m0, m1;
+    std::vector<int> job_units(chunks.size(), 0);
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const HostChunk& ch = chunks[ci];
         if (!ch.pairs.empty())
@@ -712,6 +719,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         FB_CUDA(ctx, cudaMemcpy(tabs[ci][3], ch.jobs.data(), sizeof(BatchJob) * ch.jobs.size(),
                                 cudaMemcpyHostToDevice));
         job_maps(ch, clips, m0, m1);
+        job_units[ci] = static_cast<int>(m0.size());
         FB_CUDA(ctx, cudaMemcpy(tabs[ci][4], m0.data(), sizeof(int32_t) * m0.size(), cudaMemcpyHostToDevice));
         FB_CUDA(ctx, cudaMemcpy(tabs[ci][5], m1.data(), sizeof(int32_t) * m1.size(), cudaMemcpyHostToDevice));
     }
@@ -735,7 +743,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         be->step_kind.push_back(FB_K_STYLE);
     }
     // Tile variant per patch size: forced, tuned earlier in this context, or tuned now on
-    // the first iteration of the size's first chunk.
+    // iterations 1-2 of the size's first chunk (after an untimed iteration 0).
     int variant_of[10];
     for (int k = 0; k < 10; ++k) variant_of[k] = forced_variant(flags) >= 0 ? forced_variant(flags) : ctx->tuned_variant[k];
     bool prepped = false;
@@ -749,27 +757,39 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         const BatchPair* d_pairs = static_cast<const BatchPair*>(tabs[ci][0]);
         int32_t* d_ip = static_cast<int32_t*>(tabs[ci][1]);
         int32_t* d_it = static_cast<int32_t*>(tabs[ci][2]);
+        int32_t* d_ip0 = static_cast<int32_t*>(tabs[ci][6]);
+        int32_t* d_it0 = static_cast<int32_t*>(tabs[ci][7]);
+        std::vector<int32_t> u0, u1;
         float best = 0.f;
         int best_v = 0;
         cudaEvent_t a = nullptr, b = nullptr;
         FB_CUDA(ctx, cudaEventCreate(&a));
         FB_CUDA(ctx, cudaEventCreate(&b));
         for (int v = 0; v < fb::kBatchVariants; ++v) {
-            item_maps(ch, clips, fb::batch_variant_tile_h(v), m0, m1);
+            item_maps(ch, clips, fb::batch_variant_tile_h(v), fb::kIterTilesPerClaim, m0, m1);
+            item_maps(ch, clips, fb::batch_variant_tile_h(v), fb::kInitTilesPerClaim, u0, u1);
             FB_CUDA(ctx, cudaMemcpyAsync(d_ip, m0.data(), sizeof(int32_t) * m0.size(), cudaMemcpyHostToDevice, st));
             FB_CUDA(ctx, cudaMemcpyAsync(d_it, m1.data(), sizeof(int32_t) * m1.size(), cudaMemcpyHostToDevice, st));
+            FB_CUDA(ctx, cudaMemcpyAsync(d_ip0, u0.data(), sizeof(int32_t) * u0.size(), cudaMemcpyHostToDevice, st));
+            FB_CUDA(ctx, cudaMemcpyAsync(d_it0, u1.data(), sizeof(int32_t) * u1.size(), cudaMemcpyHostToDevice, st));
             const int grid = sms * fb::batch_iter_blocks_per_sm(ch.k, v);
             FB_CUDA(ctx, cudaMemsetAsync(counters, 0, 2 * sizeof(int), st));
-            FB_CUDA(ctx, fb::launch_batch_init(ch.k, v, d_pairs, d_clips, d_ip, d_it, static_cast<int>(m0.size()),
+            FB_CUDA(ctx, fb::launch_batch_init(ch.k, v, d_pairs, d_clips, d_ip0, d_it0, static_cast<int>(u0.size()),
                                                counters, p->seed, fe[0], fe[1], grid, st));
-            FB_CUDA(ctx, cudaEventRecord(a, st));
-            FB_CUDA(ctx, fb::launch_batch_iter(ch.k, v, d_pairs, d_clips, d_ip, d_it, static_cast<int>(m0.size()),
-                                               counters + 1, p->seed, 0, fe[0], fe[1], fe[2], fe[3], grid, st));
+            // One untimed iteration, then two timed ones (ping-pong F/E; results discarded).
+            for (int it = 0; it < 3; ++it) {
+                if (it == 1) FB_CUDA(ctx, cudaEventRecord(a, st));
+                const int s0 = (it & 1) ? 2 : 0, s1 = (it & 1) ? 0 : 2;
+                FB_CUDA(ctx, cudaMemsetAsync(counters + 1, 0, sizeof(int), st));
+                FB_CUDA(ctx, fb::launch_batch_iter(ch.k, v, d_pairs, d_clips, d_ip, d_it, static_cast<int>(m0.size()),
+                                                   counters + 1, p->seed, it, fe[s0], fe[s0 + 1], fe[s1],
+                                                   fe[s1 + 1], grid, st));
+            }
             FB_CUDA(ctx, cudaEventRecord(b, st));
             FB_CUDA(ctx, cudaEventSynchronize(b));
             float ms = 0.f;
             FB_CUDA(ctx, cudaEventElapsedTime(&ms, a, b));
-            ctx->launches += 2;
+            ctx->launches += 4;
             if (v == 0 || ms < best) {
                 best = ms;
                 best_v = v;
@@ -784,15 +804,18 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const HostChunk& ch = chunks[ci];
         const int v = variant_of[ch.k] >= 0 ? variant_of[ch.k] : 0;
-        item_maps(ch, clips, fb::batch_variant_tile_h(v), m0, m1);
+        std::vector<int32_t> u0, u1;
+        item_maps(ch, clips, fb::batch_variant_tile_h(v), fb::kIterTilesPerClaim, m0, m1);
+        item_maps(ch, clips, fb::batch_variant_tile_h(v), fb::kInitTilesPerClaim, u0, u1);
         if (!m0.empty()) {
             FB_CUDA(ctx, cudaMemcpyAsync(tabs[ci][1], m0.data(), sizeof(int32_t) * m0.size(), cudaMemcpyHostToDevice, st));
             FB_CUDA(ctx, cudaMemcpyAsync(tabs[ci][2], m1.data(), sizeof(int32_t) * m1.size(), cudaMemcpyHostToDevice, st));
+            FB_CUDA(ctx, cudaMemcpyAsync(tabs[ci][6], u0.data(), sizeof(int32_t) * u0.size(), cudaMemcpyHostToDevice, st));
+            FB_CUDA(ctx, cudaMemcpyAsync(tabs[ci][7], u1.data(), sizeof(int32_t) * u1.size(), cudaMemcpyHostToDevice, st));
         }
         FB_CUDA(ctx, cudaStreamSynchronize(st));  // host vectors are reused
         const int n_items = static_cast<int>(m0.size());
-        size_t job_items = 0;
-        for (const BatchJob& j : ch.jobs) job_items += tiles_of(clips[j.clip].H, clips[j.clip].W, 8);
+        const int n_init_units = static_cast<int>(u0.size());
         const int k = ch.k;
         const uint64_t seed = p->seed;
         const int iters = p->iters;
@@ -801,6 +824,8 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         const BatchPair* d_pairs = static_cast<const BatchPair*>(tabs[ci][0]);
         const int32_t* d_ip = static_cast<const int32_t*>(tabs[ci][1]);
         const int32_t* d_it = static_cast<const int32_t*>(tabs[ci][2]);
+        const int32_t* d_ip0 = static_cast<const int32_t*>(tabs[ci][6]);
+        const int32_t* d_it0 = static_cast<const int32_t*>(tabs[ci][7]);
         const BatchJob* d_jobs = static_cast<const BatchJob*>(tabs[ci][3]);
         const int32_t* d_ij = static_cast<const int32_t*>(tabs[ci][4]);
         const int32_t* d_ijt = static_cast<const int32_t*>(tabs[ci][5]);
@@ -808,7 +833,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         if (n_items > 0) {
             int* cnt = next_counter++;
             be->steps.push_back([=](cudaStream_t s) {
-                return fb::launch_batch_init(k, v, d_pairs, d_clips, d_ip, d_it, n_items, cnt, seed, Fc, Ec, grid, s);
+                return fb::launch_batch_init(k, v, d_pairs, d_clips, d_ip0, d_it0, n_init_units, cnt, seed, Fc, Ec, grid, s);
             });
             be->step_kind.push_back(FB_K_INIT);
             for (int it = 0; it < iters; ++it) {
@@ -823,7 +848,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
             }
         }
         const uint32_t* Ffinal = Fc;
-        const int jn = static_cast<int>(job_items);
+        const int jn = job_units[ci];
         int* cnt_c = next_counter++;
         be->steps.push_back([=](cudaStream_t s) {
             return fb::launch_batch_combine(k, d_jobs, d_pairs, d_clips, d_ij, d_ijt, jn, cnt_c, Ffinal, cgrid, s);

@@ -1,8 +1,9 @@
 // fb_batch.cu -- persistent kernels of the batched submission (fb_blend_batch): many
 // clips of uneven size, window and patch in one pass.  Every pair of every clip is cut
-// into 32-column tiles; a kernel of SMs x resident-blocks CTAs claims items of the
-// flattened work list (item -> pair, tile) from a counter, so clips of different shapes
-// share one launch per Jacobi iteration.  The per-pixel work is the same code as the per-call kernels
+// into 32-column tiles, and runs of consecutive tiles of one pair form the work units;
+// a kernel of SMs x resident-blocks CTAs claims units of the flattened work list
+// (unit -> pair, first tile) from a counter, so clips of different shapes share one
+// launch per Jacobi iteration.  The per-pixel work is the same code as the per-call kernels
 // (fb_device.cuh), so results are identical to fb_blend_window whatever tile shape the
 // autotuner picks.
 #include <type_traits>
@@ -51,6 +52,22 @@ struct ItemQueue {
     }
 };
 
+// Block-uniform descriptor loads the compiler may not hoist out of a tile loop: every
+// thread re-reads them per tile (L1 broadcast hits), so they need not stay live in
+// registers across the pixel work, which would spill at 5 blocks per SM.
+__device__ __forceinline__ int4 ld_uniform(const void* p) {
+    int4 v;
+    asm volatile("ld.global.nc.v4.s32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+__device__ __forceinline__ const uint32_t* as_ptr(int lo, int hi) {
+    return reinterpret_cast<const uint32_t*>((static_cast<uint64_t>(static_cast<uint32_t>(hi)) << 32) |
+                                             static_cast<uint32_t>(lo));
+}
+
 // Larger patches keep more target words in registers: scale the block count down.
 template <int K, int V>
 struct BatchOcc {
@@ -72,18 +89,33 @@ __global__ void __launch_bounds__(32 * Variant<V>::TH, BatchOcc<K, V>::value)
     ItemQueue q{counter, s_slot};
     for (int item = q.first(); item < n_items; item = q.next()) {
         q.prefetch();
-        const BatchPair bp = pairs[item_pair[item]];
-        const BatchClip cl = clips[bp.clip];
-        const int tiles_x = (cl.W + 31) / 32;
-        const int tile = item_tile[item];
-        const int r = (tile / tiles_x) * TH + static_cast<int>(threadIdx.y);
-        const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
-        if (r >= cl.H || c >= cl.W) continue;  // no barrier below: a skipped thread rejoins at q.next()
-        const size_t npx = static_cast<size_t>(cl.H) * cl.W;
-        iterate_pixel<K>(cl.rp + static_cast<size_t>(bp.src) * npx * G::RPW,
-                         cl.rp + static_cast<size_t>(bp.tgt) * npx * G::RPW, cl.H, cl.W, r, c,
-                         bp.tag, cl.r0, key0, key1, ctr_word, Fp + bp.fe_off, Ep + bp.fe_off,
-                         Fn + bp.fe_off, En + bp.fe_off);
+        const int ip = item_pair[item];
+        const int t0 = item_tile[item];
+        int t1;
+        {
+            const int4 cg = ld_uniform(clips + ld_uniform(pairs + ip).x);  // H, W, N, r0
+            t1 = min(t0 + kIterTilesPerClaim, ((cg.y + 31) / 32) * ((cg.x + TH - 1) / TH));
+        }
+        // No barrier inside the unit: each thread runs through its pixels of the unit's
+        // tiles and rejoins the block at q.next().
+        for (int tile = t0; tile < t1; ++tile) {
+            const int4 p0 = ld_uniform(pairs + ip);              // clip, src, tgt, style
+            const int4 p1 = ld_uniform(&pairs[ip].tag);          // tag, weight, fe_off
+            const int4 cg = ld_uniform(clips + p0.x);            // H, W, N, r0
+            const int4 cp = ld_uniform(&clips[p0.x].rp);         // rp, styles
+            const int H = cg.x, W = cg.y, tiles_x = (W + 31) / 32;
+            const int r = (tile / tiles_x) * TH + static_cast<int>(threadIdx.y);
+            const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
+            if (r >= H || c >= W) continue;
+            const size_t npx = static_cast<size_t>(H) * W;
+            const uint32_t* rp = as_ptr(cp.x, cp.y);
+            const uint64_t fe = (static_cast<uint64_t>(static_cast<uint32_t>(p1.w)) << 32) |
+                                static_cast<uint32_t>(p1.z);
+            iterate_pixel<K>(rp + static_cast<size_t>(p0.y) * npx * G::RPW,
+                             rp + static_cast<size_t>(p0.z) * npx * G::RPW, H, W, r, c,
+                             static_cast<uint32_t>(p1.x), cg.w, key0, key1, ctr_word, Fp + fe,
+                             Ep + fe, Fn + fe, En + fe);
+        }
     }
 }
 
@@ -102,18 +134,23 @@ __global__ void __launch_bounds__(32 * Variant<V>::TH)
         const BatchPair bp = pairs[item_pair[item]];
         const BatchClip cl = clips[bp.clip];
         const int tiles_x = (cl.W + 31) / 32;
-        const int tile = item_tile[item];
-        const int r = (tile / tiles_x) * TH + static_cast<int>(threadIdx.y);
-        const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
-        if (r >= cl.H || c >= cl.W) continue;
+        const int t0 = item_tile[item];
+        const int t1 = min(t0 + kInitTilesPerClaim, tiles_x * ((cl.H + TH - 1) / TH));
         const size_t npx = static_cast<size_t>(cl.H) * cl.W;
-        init_pixel<K>(cl.rp + static_cast<size_t>(bp.src) * npx * G::RPW,
-                      cl.rp + static_cast<size_t>(bp.tgt) * npx * G::RPW, cl.H, cl.W, r, c, bp.tag,
-                      0, nullptr, 0, 0, nullptr, key0, key1, 0u, F + bp.fe_off, E + bp.fe_off);
+        for (int tile = t0; tile < t1; ++tile) {
+            const int r = (tile / tiles_x) * TH + static_cast<int>(threadIdx.y);
+            const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
+            if (r >= cl.H || c >= cl.W) continue;
+            init_pixel<K>(cl.rp + static_cast<size_t>(bp.src) * npx * G::RPW,
+                          cl.rp + static_cast<size_t>(bp.tgt) * npx * G::RPW, cl.H, cl.W, r, c,
+                          bp.tag, 0, nullptr, 0, 0, nullptr, key0, key1, 0u, F + bp.fe_off,
+                          E + bp.fe_off);
+        }
     }
 }
 
-// Alg. 2 + Eq. 2 for the output frames of a chunk: items are (job, 32x8 tile).
+// Alg. 2 + Eq. 2 for the output frames of a chunk: units are (job, kCombineTilesPerClaim
+// consecutive 32x8 tiles).
 template <int K>
 __global__ void __launch_bounds__(256)
     batch_combine_kernel(const BatchJob* __restrict__ jobs, const BatchPair* __restrict__ pairs,
@@ -124,28 +161,41 @@ __global__ void __launch_bounds__(256)
     ItemQueue q{counter, s_slot};
     for (int item = q.first(); item < n_items; item = q.next()) {
         q.prefetch();
-        const BatchJob job = jobs[item_job[item]];
-        const BatchClip cl = clips[job.clip];
-        const int tiles_x = (cl.W + 31) / 32;
-        const int tile = item_tile[item];
-        const int r = (tile / tiles_x) * 8 + static_cast<int>(threadIdx.y);
-        const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
-        if (r >= cl.H || c >= cl.W) continue;
-        const size_t npx = static_cast<size_t>(cl.H) * cl.W;
-        const size_t x = static_cast<size_t>(r) * cl.W + c;
-        const uint32_t s = __ldg(cl.styles + static_cast<size_t>(job.frame) * npx + x);
-        const uint32_t w = static_cast<uint32_t>(K * K);
-        uint32_t a0 = w * (s & 0xFFu), a1 = w * ((s >> 8) & 0xFFu), a2 = w * ((s >> 16) & 0xFFu);
-        for (int p = 0; p < job.n_pairs; ++p) {
-            const BatchPair bp = pairs[job.first_pair + p];
-            uint32_t v0, v1, v2;
-            remap_votes<K>(F + bp.fe_off, cl.styles + static_cast<size_t>(bp.style) * npx, cl.H,
-                           cl.W, r, c, v0, v1, v2);
-            a0 += bp.weight * v0;
-            a1 += bp.weight * v1;
-            a2 += bp.weight * v2;
+        const int ij = item_job[item];
+        const int t0 = item_tile[item];
+        int t1;
+        {
+            const int4 cg = ld_uniform(clips + ld_uniform(jobs + ij).x);  // H, W, N, r0
+            t1 = min(t0 + kCombineTilesPerClaim, ((cg.y + 31) / 32) * ((cg.x + 7) / 8));
         }
-        write_output(cl.out + (static_cast<size_t>(job.frame) * npx + x) * 3, a0, a1, a2, job.den);
+        for (int tile = t0; tile < t1; ++tile) {
+            const int4 j0 = ld_uniform(jobs + ij);        // clip, frame, first_pair, n_pairs
+            const int4 cg = ld_uniform(clips + j0.x);     // H, W, N, r0
+            const int H = cg.x, W = cg.y, tiles_x = (W + 31) / 32;
+            const int r = (tile / tiles_x) * 8 + static_cast<int>(threadIdx.y);
+            const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
+            if (r >= H || c >= W) continue;
+            const int4 cp = ld_uniform(&clips[j0.x].rp);  // rp, styles
+            const uint32_t* styles = as_ptr(cp.z, cp.w);
+            const size_t npx = static_cast<size_t>(H) * W;
+            const size_t x = static_cast<size_t>(r) * W + c;
+            const uint32_t s = __ldg(styles + static_cast<size_t>(j0.y) * npx + x);
+            const uint32_t w = static_cast<uint32_t>(K * K);
+            uint32_t a0 = w * (s & 0xFFu), a1 = w * ((s >> 8) & 0xFFu), a2 = w * ((s >> 16) & 0xFFu);
+            for (int p = 0; p < j0.w; ++p) {
+                const BatchPair bp = pairs[j0.z + p];
+                uint32_t v0, v1, v2;
+                remap_votes<K>(F + bp.fe_off, styles + static_cast<size_t>(bp.style) * npx, H, W, r,
+                               c, v0, v1, v2);
+                a0 += bp.weight * v0;
+                a1 += bp.weight * v1;
+                a2 += bp.weight * v2;
+            }
+            const BatchJob job = jobs[ij];
+            const BatchClip* cl = clips + job.clip;
+            write_output(cl->out + (static_cast<size_t>(job.frame) * npx + x) * 3, a0, a1, a2,
+                         job.den);
+        }
     }
 }
 

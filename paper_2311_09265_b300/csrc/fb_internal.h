@@ -80,30 +80,51 @@ void initnet_dims(const ::fb_initnet* net, int* H, int* W);
 
 // ---- batched persistent path (fb_batch.cu) --------------------------------------
 // One clip of a batch submission (device table).
-struct BatchClip {
+// Both descriptors are read by the batch kernels as 16-byte vectors (fb_batch.cu): keep
+// them 16-byte aligned with the field offsets asserted below.
+struct alignas(16) BatchClip {
     int32_t H, W, N, r0;     // r0: first random-search radius for this clip
     const uint32_t* rp;      // row patches of the clip's N guide frames
     const uint32_t* styles;  // RGBX styles of the clip's N frames
     float* out;              // the caller's N x H x W x 3 output
 };
 // One NNF of a chunk: pair (src -> tgt) of clip `clip`, its F/E plane at fe_off.
-struct BatchPair {
+struct alignas(16) BatchPair {
     int32_t clip, src, tgt, style;
     uint32_t tag, weight;
     uint64_t fe_off;
 };
+static_assert(sizeof(BatchClip) == 48 && offsetof(BatchClip, rp) == 16, "BatchClip layout");
+static_assert(sizeof(BatchPair) == 32 && offsetof(BatchPair, tag) == 16 &&
+                  offsetof(BatchPair, fe_off) == 24, "BatchPair layout");
 // One output frame of a chunk; its pairs are [first_pair, first_pair + n_pairs).
-struct BatchJob {
+struct alignas(16) BatchJob {
     int32_t clip, frame, first_pair, n_pairs;
     uint32_t den;
     int32_t pad[3];
 };
+static_assert(sizeof(BatchJob) == 32, "BatchJob layout");
 
 // Tile shapes / occupancies the autotuner chooses among (same results for all).
 constexpr int kBatchVariants = 4;
+// Consecutive tiles of one pair (or output frame) that one claim of a persistent batch
+// kernel covers: the claim's descriptor loads and block barrier are paid once per claim
+// instead of once per tile.  The remap reads F and styles around each pixel, so its
+// units stay one tile (neighbouring tiles then run side by side and share L1/L2 lines).  Work unit u of a launch is (unit_pair[u], first tile
+// unit_tile[u]) and covers tiles [first, min(first + per_claim, tiles of the pair)).
+#ifndef FB_ITER_TILES_PER_CLAIM
+#define FB_ITER_TILES_PER_CLAIM 4
+#endif
+#ifndef FB_COMBINE_TILES_PER_CLAIM
+#define FB_COMBINE_TILES_PER_CLAIM 1
+#endif
+constexpr int kIterTilesPerClaim = FB_ITER_TILES_PER_CLAIM;
+constexpr int kInitTilesPerClaim = 16;
+constexpr int kCombineTilesPerClaim = FB_COMBINE_TILES_PER_CLAIM;
 const char* batch_variant_name(int v);
-// Work items: item_pair[i] = pair of item i, item_tile[i] = tile index within the pair.
-// `counter` must be zero when the launch starts (one int per launch).
+// Work units: item_pair[u] = pair of unit u, item_tile[u] = its first tile within the
+// pair (claims of kIterTilesPerClaim / kInitTilesPerClaim tiles).  `counter` must be
+// zero when the launch starts (one int per launch).
 cudaError_t launch_batch_init(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
                               const int32_t* item_pair, const int32_t* item_tile, int n_items,
                               int* counter, uint64_t seed, uint32_t* F, uint32_t* E, int grid,
