@@ -248,11 +248,10 @@ struct Buffers {
 void carve(Carver& cv, Buffers& b, const Levels& L, int k, int n_guides, int n_styles,
            size_t chunk_pairs, size_t n_pairs, size_t n_jobs, bool staging, size_t guide_bytes,
            size_t style_bytes, size_t out_floats, bool learned = false) {
-    const int recw = fb::rowpatch_words(k);
     for (int l = 0; l < L.n; ++l) {
         const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];
         if (l > 0) b.raw[l] = cv.take<uint8_t>(static_cast<size_t>(n_guides) * npx * 3);
-        b.rec[l] = cv.take<uint32_t>(static_cast<size_t>(n_guides) * npx * recw);
+        b.rec[l] = cv.take<uint32_t>(static_cast<size_t>(n_guides) * fb::rowpatch_frame_words(k, L.h[l], L.w[l]));
     }
     const size_t npx0 = static_cast<size_t>(L.h[0]) * L.w[0];
     b.styles = cv.take<uint32_t>(static_cast<size_t>(n_styles) * npx0);
@@ -291,7 +290,6 @@ int upload_tables(fb_ctx* ctx, const std::vector<PairDesc>& pairs, const std::ve
 // pyramid level, into guide slots [slot0, slot0 + n).
 int prep_guides(fb_ctx* ctx, const Buffers& b, const Levels& L, int k, const uint8_t* frames,
                 int n, int slot0, cudaStream_t st) {
-    const int recw = fb::rowpatch_words(k);
     const uint8_t* cur = frames;
     for (int l = 0; l < L.n; ++l) {
         const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];
@@ -301,7 +299,8 @@ int prep_guides(fb_ctx* ctx, const Buffers& b, const Levels& L, int k, const uin
             cur = dst;
         }
         FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(k, cur, n, L.h[l], L.w[l],
-                                              b.rec[l] + static_cast<size_t>(slot0) * npx * recw, st));
+                                              b.rec[l] + static_cast<size_t>(slot0) *
+                                                             fb::rowpatch_frame_words(k, L.h[l], L.w[l]), st));
     }
     return FB_OK;
 }
@@ -663,7 +662,8 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         cb.assign(n, ClipBufs{});
         for (int i = 0; i < n; ++i) {
             const size_t npx = static_cast<size_t>(clips[i].H) * clips[i].W;
-            cb[i].rp = c.take<uint32_t>(static_cast<size_t>(clips[i].N) * npx * fb::rowpatch_words(clips[i].patch));
+            cb[i].rp = c.take<uint32_t>(static_cast<size_t>(clips[i].N) *
+                                        fb::rowpatch_frame_words(clips[i].patch, clips[i].H, clips[i].W));
             cb[i].sty = c.take<uint32_t>(static_cast<size_t>(clips[i].N) * npx);
         }
         size_t max_fe = 1;

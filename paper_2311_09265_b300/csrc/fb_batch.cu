@@ -107,12 +107,10 @@ __global__ void __launch_bounds__(32 * Variant<V>::TH, BatchOcc<K, V>::value)
             const int r = (tile / tiles_x) * TH + static_cast<int>(threadIdx.y);
             const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
             if (r >= H || c >= W) continue;
-            const size_t npx = static_cast<size_t>(H) * W;
             const uint32_t* rp = as_ptr(cp.x, cp.y);
             const uint64_t fe = (static_cast<uint64_t>(static_cast<uint32_t>(p1.w)) << 32) |
                                 static_cast<uint32_t>(p1.z);
-            iterate_pixel<K>(rp + static_cast<size_t>(p0.y) * npx * G::RPW,
-                             rp + static_cast<size_t>(p0.z) * npx * G::RPW, H, W, r, c,
+            iterate_pixel<K>(frame_rows<K>(rp, p0.y, H, W), frame_rows<K>(rp, p0.z, H, W), H, W, r, c,
                              static_cast<uint32_t>(p1.x), cg.w, key0, key1, ctr_word, Fp + fe,
                              Ep + fe, Fn + fe, En + fe);
         }
@@ -136,13 +134,12 @@ __global__ void __launch_bounds__(32 * Variant<V>::TH)
         const int tiles_x = (cl.W + 31) / 32;
         const int t0 = item_tile[item];
         const int t1 = min(t0 + kInitTilesPerClaim, tiles_x * ((cl.H + TH - 1) / TH));
-        const size_t npx = static_cast<size_t>(cl.H) * cl.W;
         for (int tile = t0; tile < t1; ++tile) {
             const int r = (tile / tiles_x) * TH + static_cast<int>(threadIdx.y);
             const int c = (tile % tiles_x) * 32 + static_cast<int>(threadIdx.x);
             if (r >= cl.H || c >= cl.W) continue;
-            init_pixel<K>(cl.rp + static_cast<size_t>(bp.src) * npx * G::RPW,
-                          cl.rp + static_cast<size_t>(bp.tgt) * npx * G::RPW, cl.H, cl.W, r, c,
+            init_pixel<K>(frame_rows<K>(cl.rp, bp.src, cl.H, cl.W),
+                          frame_rows<K>(cl.rp, bp.tgt, cl.H, cl.W), cl.H, cl.W, r, c,
                           bp.tag, 0, nullptr, 0, 0, nullptr, key0, key1, 0u, F + bp.fe_off,
                           E + bp.fe_off);
         }

@@ -38,7 +38,24 @@ struct Geo {
     static constexpr int P = K / 2;
     static constexpr int NW = (3 * K + 3) / 4;    // 32-bit words holding one 3K-byte patch row
     static constexpr int RPW = (NW + 3) / 4 * 4;  // row-patch slot stride: 16-byte aligned
+    static constexpr bool PAIRED = rowpatch_paired(K);  // k = 5: two rows per 32-byte slot
 };
+
+// One 32-byte slot of the paired layout (two row patches of 4 words).  A 256-bit load
+// is one request, like a 16-byte one, so the pair costs what one row did.  volatile:
+// the load must stay behind the early-exit test that guards it.
+__device__ __forceinline__ void load_slot(const uint32_t* __restrict__ p, uint32_t (&w)[8]) {
+    asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3]), "=r"(w[4]), "=r"(w[5]),
+                   "=r"(w[6]), "=r"(w[7])
+                 : "l"(p));
+}
+
+// Frame f of a guide stack laid out by prep_guides.
+template <int K>
+__device__ __forceinline__ const uint32_t* frame_rows(const uint32_t* rp, int f, int H, int W) {
+    return rp + static_cast<size_t>(f) * rowpatch_frame_words(K, H, W);
+}
 
 template <int K>
 __device__ __forceinline__ void load_row(const uint32_t* __restrict__ p,
@@ -78,10 +95,33 @@ template <int K>
 __device__ __forceinline__ void load_target(const uint32_t* __restrict__ rpt, int H, int W,
                                             int r, int c, TargetPatch<K>& t) {
     using G = Geo<K>;
+    if constexpr (G::PAIRED) {
+        // Rows r-2 .. r+2 are the clamped rows 2q-2 .. 2q-1 of slots q = r/2 + 0, 1, 2:
+        // for even r they are halves 0..4 of the three slots, for odd r halves 1..5.
+        const int odd = r & 1;
+        const size_t stride = static_cast<size_t>(W) * 8;
+        const uint32_t* base = rpt + (static_cast<size_t>(r >> 1) * W + c) * 8;
+        uint32_t h[3][8];
+#pragma unroll
+        for (int L = 0; L < 3; ++L) load_slot(base + L * stride, h[L]);
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t ev = h[a >> 1][4 * (a & 1) + w];
+                const uint32_t od = h[(a + 1) >> 1][4 * ((a + 1) & 1) + w];
+                t.w[a][w] = odd ? od : ev;
+            }
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            const int rr = clampi(r - G::P + a, 0, H - 1);
+            load_row<K>(rpt + (static_cast<size_t>(rr) * W + c) * G::RPW, t.w[a]);
+        }
+    }
 #pragma unroll
     for (int a = 0; a < K; ++a) {
-        const int rr = clampi(r - G::P + a, 0, H - 1);
-        load_row<K>(rpt + (static_cast<size_t>(rr) * W + c) * G::RPW, t.w[a]);
         uint32_t e = 0;
 #pragma unroll
         for (int w = 0; w < G::NW; ++w) e = __dp4a(t.w[a][w], t.w[a][w], e);
@@ -100,22 +140,59 @@ __device__ __forceinline__ bool patch_error_below(const uint32_t* __restrict__ r
                                                   uint32_t bound, uint32_t* e) {
     using G = Geo<K>;
     uint32_t acc = 0;
+    if constexpr (G::PAIRED) {
+        // Source rows ur-2 .. ur+2 sit in slots q = ur/2 + L (L = 0, 1, 2), whose halves
+        // are patch rows a = 2L - odd and 2L - odd + 1 (a outside 0..4 is not part of
+        // the patch and contributes zero).  The middle slot, always two patch rows, is
+        // tested first.
+        const int odd = ur & 1;
+        const size_t stride = static_cast<size_t>(W) * 8;
+        const uint32_t* base = rps + (static_cast<size_t>(ur >> 1) * W + uc) * 8;
 #pragma unroll
-    for (int a = 0; a < K; ++a) {
-        const int rr = clampi(ur - G::P + a, 0, H - 1);
-        uint32_t s[G::NW];
-        load_row<K>(rps + (static_cast<size_t>(rr) * W + uc) * G::RPW, s);
-        uint32_t dot = 0, ss = 0;
+        for (int i = 0; i < 3; ++i) {
+            const int L = i == 0 ? 1 : (i == 1 ? 0 : 2);
+            uint32_t s[8];
+            load_slot(base + L * stride, s);
+            uint32_t dot = 0, ss = 0, te = 0;
 #pragma unroll
-        for (int w = 0; w < G::NW; ++w) {
-            dot = __dp4a(s[w], t.w[a][w], dot);
-            ss = __dp4a(s[w], s[w], ss);
+            for (int half = 0; half < 2; ++half) {
+                const int a_ev = 2 * L + half;      // patch row of this half for even ur
+                const int a_od = 2 * L + half - 1;  // ... for odd ur
+                const bool v_ev = a_ev <= 4, v_od = a_od >= 0;
+                const bool valid = odd ? v_od : v_ev;
+                const int ae = v_ev ? a_ev : 0, ao = v_od ? a_od : 0;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const uint32_t tw = valid ? (odd ? t.w[ao][w] : t.w[ae][w]) : 0u;
+                    const uint32_t sw = valid ? s[4 * half + w] : 0u;
+                    dot = __dp4a(sw, tw, dot);
+                    ss = __dp4a(sw, sw, ss);
+                }
+                te += valid ? (odd ? t.row_e[ao] : t.row_e[ae]) : 0u;
+            }
+            acc += ss + te - 2u * dot;
+            if (acc >= bound) return false;
         }
-        acc += ss + t.row_e[a] - 2u * dot;
-        if (acc >= bound) return false;
+        *e = acc;
+        return true;
+    } else {
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            const int rr = clampi(ur - G::P + a, 0, H - 1);
+            uint32_t s[G::NW];
+            load_row<K>(rps + (static_cast<size_t>(rr) * W + uc) * G::RPW, s);
+            uint32_t dot = 0, ss = 0;
+#pragma unroll
+            for (int w = 0; w < G::NW; ++w) {
+                dot = __dp4a(s[w], t.w[a][w], dot);
+                ss = __dp4a(s[w], s[w], ss);
+            }
+            acc += ss + t.row_e[a] - 2u * dot;
+            if (acc >= bound) return false;
+        }
+        *e = acc;
+        return true;
     }
-    *e = acc;
-    return true;
 }
 
 // One Jacobi iteration of Alg. 1 (Sec. 3.2 parallel update) for target pixel (r, c) of

@@ -12,10 +12,21 @@
 namespace fb {
 
 // NNF entries on the device are packed (row << 16) | col; H, W <= 32767.
-// Guide frames are pre-laid out as "row patches": slot (r, c) holds the k pixels
-// (r, clamp(c-p .. c+p)) as 3k bytes in rowpatch_words(k) 32-bit words (zero padded),
-// so one patch row of Eq. 1 is one aligned 16- or 32-byte load.
-inline int rowpatch_words(int k) { return ((3 * k + 3) / 4 + 3) / 4 * 4; }
+// Guide frames are pre-laid out as "row patches": the row patch of (r, c) is the k
+// pixels (r, clamp(c-p .. c+p)) as 3k bytes in rowpatch_words(k) 32-bit words (zero
+// padded), so one patch row of Eq. 1 is one aligned 16- or 32-byte load.
+//   k = 5 ("paired"): one 32-byte slot per column c and row pair q = 0 .. (H+3)/2,
+//     holding the row patches of rows clamp(2q-2) and clamp(2q-1): the rows -2 .. H+1
+//     that a clamped 5x5 patch can touch are all present, and one load brings two rows.
+//   other k: one slot per pixel holding the row patch of (r, c).
+__host__ __device__ constexpr int rowpatch_words(int k) { return ((3 * k + 3) / 4 + 3) / 4 * 4; }
+__host__ __device__ constexpr bool rowpatch_paired(int k) { return k == 5; }
+__host__ __device__ constexpr int rowpatch_pair_rows(int H) { return (H + 5) / 2; }
+// 32-bit words of one guide frame's row patches.
+__host__ __device__ inline size_t rowpatch_frame_words(int k, int H, int W) {
+    return rowpatch_paired(k) ? static_cast<size_t>(rowpatch_pair_rows(H)) * W * 8
+                              : static_cast<size_t>(H) * W * rowpatch_words(k);
+}
 
 // One ordered pair (source guide frame -> target guide frame) and how its remap
 // enters the output.
@@ -41,7 +52,7 @@ struct JobDesc {
 
 struct LevelGeom {
     int H, W;
-    const uint32_t* rp;      // [n_guides][H*W][rowpatch_words(k)]
+    const uint32_t* rp;      // n_guides frames of rowpatch_frame_words(k, H, W) words
 };
 
 // ---- launchers (fb_kernels.cu); each returns the cudaError_t of the launch ------

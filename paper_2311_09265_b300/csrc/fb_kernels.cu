@@ -66,6 +66,40 @@ __global__ void __launch_bounds__(256) prep_guides_kernel(const uint8_t* __restr
         dst[v] = make_uint4(words[4 * v], words[4 * v + 1], words[4 * v + 2], words[4 * v + 3]);
 }
 
+// The paired k = 5 layout: thread (q, c) of frame f writes the 32-byte slot holding the
+// row patches of rows clamp(2q - 2) and clamp(2q - 1) at column c.
+__global__ void __launch_bounds__(256) prep_guides_paired_kernel(const uint8_t* __restrict__ frames,
+                                                                 int H, int W,
+                                                                 uint32_t* __restrict__ rp) {
+    constexpr int K = 5, P = 2;
+    const size_t n_slots = static_cast<size_t>(rowpatch_pair_rows(H)) * W;
+    const size_t idx = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (idx >= n_slots) return;
+    const size_t f = blockIdx.y;
+    const int q = static_cast<int>(idx / W), c = static_cast<int>(idx % W);
+    const uint8_t* img = frames + f * static_cast<size_t>(H) * W * 3;
+    uint32_t words[8];
+#pragma unroll
+    for (int w = 0; w < 8; ++w) words[w] = 0;
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int r = clampi(2 * q - 2 + half, 0, H - 1);
+#pragma unroll
+        for (int m = 0; m < K; ++m) {
+            const int cc = clampi(c - P + m, 0, W - 1);
+            const uint8_t* px = img + (static_cast<size_t>(r) * W + cc) * 3;
+#pragma unroll
+            for (int ch = 0; ch < 3; ++ch) {
+                const int b = 3 * m + ch;
+                words[4 * half + (b >> 2)] |= static_cast<uint32_t>(px[ch]) << (8 * (b & 3));
+            }
+        }
+    }
+    uint4* dst = reinterpret_cast<uint4*>(rp + f * rowpatch_frame_words(K, H, W) + idx * 8);
+    dst[0] = make_uint4(words[0], words[1], words[2], words[3]);
+    dst[1] = make_uint4(words[4], words[5], words[6], words[7]);
+}
+
 __global__ void __launch_bounds__(256) downsample_kernel(const uint8_t* __restrict__ in, int H,
                                                          int W, uint8_t* __restrict__ out) {
     const int h2 = (H + 1) / 2, w2 = (W + 1) / 2;
@@ -129,8 +163,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
     const int pl = blockIdx.y;
     const PairDesc pd = pairs[pair0 + pl];
     const size_t npx = static_cast<size_t>(H) * W;
-    init_pixel<K>(rp + static_cast<size_t>(pd.src) * npx * G::RPW,
-                  rp + static_cast<size_t>(pd.tgt) * npx * G::RPW, H, W, tc.r, tc.c, pd.tag, mode,
+    init_pixel<K>(frame_rows<K>(rp, pd.src, H, W), frame_rows<K>(rp, pd.tgt, H, W), H, W, tc.r,
+                  tc.c, pd.tag, mode,
                   coarse_F ? coarse_F + static_cast<size_t>(pl) * Hc * Wc : nullptr, Hc, Wc,
                   user_init ? user_init + static_cast<size_t>(pl) * npx * 2 : nullptr, key0, key1,
                   level_word, F + static_cast<size_t>(pl) * npx, E + static_cast<size_t>(pl) * npx);
@@ -164,10 +198,10 @@ __global__ void __launch_bounds__(TILE_THREADS, IterOccupancy<K>::value * 256 / 
     const int pl = blockIdx.y;
     const PairDesc pd = pairs[pair0 + pl];
     const size_t npx = static_cast<size_t>(H) * W;
-    const uint32_t* __restrict__ rps = rp + static_cast<size_t>(pd.src) * npx * G::RPW;
+    const uint32_t* __restrict__ rps = frame_rows<K>(rp, pd.src, H, W);
     const uint32_t* __restrict__ Fpp = Fp + static_cast<size_t>(pl) * npx;
 
-    iterate_pixel<K>(rps, rp + static_cast<size_t>(pd.tgt) * npx * G::RPW, H, W, r, c, pd.tag, r0,
+    iterate_pixel<K>(rps, frame_rows<K>(rp, pd.tgt, H, W), H, W, r, c, pd.tag, r0,
                      key0, key1, ctr_word, Fpp, Ep + static_cast<size_t>(pl) * npx,
                      Fn + static_cast<size_t>(pl) * npx, En + static_cast<size_t>(pl) * npx);
 }
@@ -272,6 +306,12 @@ cudaError_t launch_prep_guides(int k, const uint8_t* frames, int n_frames, int H
                                uint32_t* rp, cudaStream_t st) {
     if (n_frames <= 0) return cudaSuccess;
     const dim3 grid(blocks_for(static_cast<size_t>(H) * W, 256), static_cast<unsigned>(n_frames));
+    if (rowpatch_paired(k)) {
+        const size_t n_slots = static_cast<size_t>(rowpatch_pair_rows(H)) * W;
+        prep_guides_paired_kernel<<<dim3(blocks_for(n_slots, 256), static_cast<unsigned>(n_frames)), 256,
+                                    0, st>>>(frames, H, W, rp);
+        return cudaGetLastError();
+    }
     FB_DISPATCH_K(k, (prep_guides_kernel<KK><<<grid, 256, 0, st>>>(frames, H, W, rp)));
     return cudaGetLastError();
 }

@@ -135,7 +135,7 @@ extern "C" int fb_blend_window_noalloc(const uint8_t* guides, const uint8_t* sty
     if (!on_device(guides, device) || !on_device(styles, device) || !on_device(out, device))
         return report(FB_ERR_ARG, "guides, styles and out must be device memory of the current device");
 
-    const int k = p->patch, M = (window - 1) / 2, recw = fb::rowpatch_words(k);
+    const int k = p->patch, M = (window - 1) / 2;
     int hs[16], ws[16];
     hs[0] = H;
     ws[0] = W;
@@ -153,7 +153,7 @@ extern "C" int fb_blend_window_noalloc(const uint8_t* guides, const uint8_t* sty
     for (int l = 0; l < p->levels; ++l) {
         const size_t npx = static_cast<size_t>(hs[l]) * ws[l];
         if (l > 0) { o_raw[l] = off; off = align256(off + static_cast<size_t>(N) * npx * 3); }
-        o_rec[l] = off; off = align256(off + static_cast<size_t>(N) * npx * recw * 4);
+        o_rec[l] = off; off = align256(off + static_cast<size_t>(N) * fb::rowpatch_frame_words(k, hs[l], ws[l]) * 4);
     }
     const size_t o_sty = off; off = align256(off + static_cast<size_t>(N) * npx0 * 4);
     size_t o_fe[4];
