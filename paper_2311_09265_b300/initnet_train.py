@@ -77,9 +77,11 @@ def initial_params(n_params: int, seed: int) -> np.ndarray:
     return p
 
 
-def train(net: InitNet, ts: TrainingSet, steps: int = 1500, batch_size: int = 8, lr: float = 2e-3,
-          seed: int = 0, log_every: int = 100):
-    """Adam with a cosine-decayed step size; returns the loss history (every log_every)."""
+def train(net: InitNet, ts: TrainingSet, steps: int = 1500, batch_size: int = 8, lr: float = 1e-3,
+          warmup: int = 200, seed: int = 0, log_every: int = 100):
+    """Adam with a linear warm-up over `warmup` steps, then a cosine-decayed step size;
+    returns the loss history (every log_every).  Without the warm-up the first few
+    hundred steps swing widely and a run can stall on a plateau."""
     rng = np.random.default_rng(seed)
     hist = []
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
@@ -89,6 +91,8 @@ def train(net: InitNet, ts: TrainingSet, steps: int = 1500, batch_size: int = 8,
         src, tgt, target, weight = batch(ts, idx)
         wsum = max(float(weight.sum()), 1.0)
         cur = lr * (0.05 + 0.95 * 0.5 * (1.0 + math.cos(math.pi * s / steps)))
+        if warmup > 0:
+            cur *= min(1.0, (s + 1) / warmup)
         net.train_step(src, tgt, target, weight, wsum, cur, loss_out=loss)
         if s % log_every == 0 or s == steps - 1:
             hist.append((s, float(loss.item()), time.perf_counter() - t0))
@@ -118,7 +122,7 @@ def train_default(ctx: Context, H: int, W: int, max_pairs: int = 256, steps: int
     net = InitNet(ctx, max_pairs, H, W, downscale=downscale)
     net.set_params(initial_params(net.n_params, seed & 0xFFFF))
     t0 = time.perf_counter()
-    hist = train(net, ts, steps=steps, batch_size=8, lr=2e-3, seed=seed & 0xFFFF,
+    hist = train(net, ts, steps=steps, batch_size=8, lr=1e-3, warmup=200, seed=seed & 0xFFFF,
                  log_every=max(steps // 10, 1))
     torch.cuda.synchronize()
     return net, hist, t_data, time.perf_counter() - t0
