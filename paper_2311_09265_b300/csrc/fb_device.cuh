@@ -120,12 +120,14 @@ __device__ __forceinline__ void load_target(const uint32_t* __restrict__ rpt, in
             load_row<K>(rpt + (static_cast<size_t>(rr) * W + c) * G::RPW, t.w[a]);
         }
     }
+    if constexpr (!G::PAIRED) {  // the paired path recomputes |t_a|^2 per candidate
 #pragma unroll
-    for (int a = 0; a < K; ++a) {
-        uint32_t e = 0;
+        for (int a = 0; a < K; ++a) {
+            uint32_t e = 0;
 #pragma unroll
-        for (int w = 0; w < G::NW; ++w) e = __dp4a(t.w[a][w], t.w[a][w], e);
-        t.row_e[a] = e;
+            for (int w = 0; w < G::NW; ++w) e = __dp4a(t.w[a][w], t.w[a][w], e);
+            t.row_e[a] = e;
+        }
     }
 }
 
@@ -167,8 +169,8 @@ __device__ __forceinline__ bool patch_error_below(const uint32_t* __restrict__ r
                     const uint32_t sw = valid ? s[4 * half + w] : 0u;
                     dot = __dp4a(sw, tw, dot);
                     ss = __dp4a(sw, sw, ss);
+                    te = __dp4a(tw, tw, te);  // |t|^2 recomputed: five fewer live registers
                 }
-                te += valid ? (odd ? t.row_e[ao] : t.row_e[ae]) : 0u;
             }
             acc += ss + te - 2u * dot;
             if (acc >= bound) return false;
