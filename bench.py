@@ -53,7 +53,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("fastblend", "reference"), default="fastblend")
     ap.add_argument("--workload", default="blend_512",
-                    choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512"])
+                    choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512", "initnet_512"])
     ap.add_argument("--learned-iters", type=int, default=2,
                     help="Alg. 1 iterations after the learned initialiser (learned_512)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -577,12 +577,108 @@ def run_gpu_batch(args):
     return 0
 
 
+# ----------------------------------------------------------------------------------
+# learned initialiser alone: the forward pass of its convolution pyramid
+# ----------------------------------------------------------------------------------
+INITNET_PAIRS = 256
+INITNET_DIVISORS = [1, 1, 2, 2, 4, 4, 8, 8, 4, 2, 1, 1]  # grid of each layer: (H/ds)/divisor
+
+
+def initnet_flops_per_pair(H: int, W: int, ds: int) -> int:
+    """2 * outputs * Cout * 9 * Cin summed over the twelve 3x3 convolutions."""
+    from paper_2311_09265_b300.initnet_layout import LAYERS
+    hq, wq = H // ds, W // ds
+    return sum(2 * (hq // d) * (wq // d) * cout * 9 * cin
+               for (cin, cout), d in zip(LAYERS, INITNET_DIVISORS))
+
+
+def measured_peak(key: str, fallback: float):
+    """A peak from the measured MEASURED_PEAKS.json, else the recipe's fallback."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)[key]), "measured"
+    except (OSError, KeyError, ValueError):
+        return fallback, "fallback"
+
+
+def run_gpu_initnet(args):
+    """One step = the initialiser's forward (input box means, 12 convolutions on the
+    tensor cores, head) over 256 ordered pairs of the headline clip's 512x512 guides, with
+    He-initialised weights (the time does not depend on the weight values)."""
+    import numpy as np
+    import torch
+
+    import paper_2311_09265_b300 as fbp
+    from paper_2311_09265_b300 import initnet_train
+
+    grp = RankGroup()
+    rank, world, local = grp.rank, grp.world, grp.local
+    torch.cuda.set_device(local)
+    fbp.build()
+    w = synth.WORKLOADS["blend_512"]
+    g, _ = make_inputs(w, shard_seed(w.seed, rank))
+    rng = np.random.default_rng(shard_seed(w.seed, rank))
+    tgt_i = rng.integers(0, w.N, INITNET_PAIRS)
+    src_j = np.clip(tgt_i + rng.choice([-3, -2, -1, 1, 2, 3], INITNET_PAIRS), 0, w.N - 1)
+    g_d = torch.tensor(g, device="cuda")
+    src, tgt = g_d[torch.tensor(src_j)].contiguous(), g_d[torch.tensor(tgt_i)].contiguous()
+    ctx = fbp.Context(local)
+    net = fbp.InitNet(ctx, INITNET_PAIRS, w.H, w.W, downscale=8)
+    net.set_params(initnet_train.initial_params(net.n_params, 1))
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
+    for _ in range(max(args.warmup, 0)):
+        net.forward(src, tgt)
+    torch.cuda.synchronize()
+    grp.barrier()
+    launches0 = ctx.launches
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            starts[k].record()
+            net.forward(src, tgt)
+            ends[k].record()
+        torch.cuda.synchronize()
+    grp.barrier()
+    step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+    total_ms = grp.max(sum(step_ms))
+    flops = initnet_flops_per_pair(w.H, w.W, 8) * INITNET_PAIRS
+    peak, basis = measured_peak("bf16_tflops", 1800.0)
+    achieved = flops / (statistics.median(step_ms) / 1e3) / 1e12
+    line = {
+        "metric": "learned-initialiser forward: NNF pairs/s at 512x512 (64x64 grid)",
+        "value": world * INITNET_PAIRS * args.steps / (total_ms / 1e3), "unit": "pairs/s",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": total_ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {"workload": "learned-initialiser forward, 256 pairs of 512x512 guides, "
+                               "downscale 8, 12 conv layers (779,592 parameters)",
+                   "pairs_per_step": INITNET_PAIRS, "flops_per_pair": flops // INITNET_PAIRS,
+                   "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
+                   "parallelism": f"{world} independent replica(s), one per GPU"},
+        "roofline": {"bound": "tensor", "kernel": "whole forward (12 tc_gemm convolutions + "
+                     "input and head kernels)", "achieved": achieved, "peak": peak,
+                     "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
+                     "peak_basis": f"bf16 dense, {basis} (cuBLAS burst)"},
+        "e2e": None, "gpu_launches": ctx.launches - launches0, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line))
+    net.close()
+    ctx.close()
+    grp.close()
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "batch_32":
         return run_gpu_batch(args)
+    if args.workload == "initnet_512":
+        return run_gpu_initnet(args)
     return run_gpu(args)
 
 

@@ -912,6 +912,12 @@ extern "C" int fb_batch_plan(const fb_clip_desc* clips, int n_clips, const fb_pa
     return FB_OK;
 }
 
+namespace fb {
+void count_launches(fb_ctx* ctx, int n) {
+    if (ctx) ctx->launches += static_cast<uint64_t>(n);
+}
+}  // namespace fb
+
 extern "C" int fb_ctx_set_initnet(fb_ctx* ctx, fb_initnet* net) {
     if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
     ctx->init_net = net;

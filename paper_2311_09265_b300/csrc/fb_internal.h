@@ -55,6 +55,9 @@ struct LevelGeom {
     const uint32_t* rp;      // n_guides frames of rowpatch_frame_words(k, H, W) words
 };
 
+// Adds n kernel launches made on behalf of ctx to its launch counter (fb_api.cu).
+void count_launches(fb_ctx* ctx, int n);
+
 // ---- launchers (fb_kernels.cu); each returns the cudaError_t of the launch ------
 cudaError_t launch_prep_guides(int k, const uint8_t* frames, int n_frames, int H, int W,
                                uint32_t* rp, cudaStream_t st);

@@ -51,24 +51,46 @@ cudaError_t launch_gemm(const G& gth, const E& epi, int M, int N, int K, int spl
     return cudaGetLastError();
 }
 
+#ifndef FB_GEMM_STAGES
+#define FB_GEMM_STAGES 3
+#endif
+#ifndef FB_GEMM_LOOKAHEAD
+#define FB_GEMM_LOOKAHEAD (FB_GEMM_STAGES - 1)
+#endif
+constexpr int kStages = FB_GEMM_STAGES;
+constexpr int kLookahead = FB_GEMM_LOOKAHEAD;
+
+// Forward and input-gradient convolutions: the pipelined asynchronous-copy GEMM.
+template <int BN, class G, class E>
+cudaError_t launch_gemm_async(const G& gth, const E& epi, int M, int N, int K, int* status,
+                              cudaStream_t st) {
+    const dim3 grid((M + tc::BM - 1) / tc::BM, (N + BN - 1) / BN);
+    constexpr int smem = tc::gemm_async_smem_bytes<BN, kStages>();
+    auto kern = tc::tc_gemm_async_kernel<BN, kStages, G, E, kLookahead>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<grid, 128, smem, st>>>(gth, epi, M, N, K, status);
+    return cudaGetLastError();
+}
+
 cudaError_t conv_forward(const ConvGeom& g, const bf16* X, const bf16* Wt, const float* bias,
                          int relu, bf16* Y, float* Yf, int* status, cudaStream_t st) {
-    const int M = g.n * g.Ho * g.Wo, K = 9 * g.Cin;
+    const int M = g.n * g.Ho * g.Wo, K = 9 * g.Cin, ncb = (g.Cin + 63) / 64;
     EpiFwd epi{Y, Yf, bias, g.Cout, relu};
-    if (g.Cout <= 16) return launch_gemm<16>(GatherFwd<16>{X, Wt, g, M, K}, epi, M, g.Cout, K, 1, status, st);
-    if (g.Cout <= 32) return launch_gemm<32>(GatherFwd<32>{X, Wt, g, M, K}, epi, M, g.Cout, K, 1, status, st);
-    if (g.Cout <= 64) return launch_gemm<64>(GatherFwd<64>{X, Wt, g, M, K}, epi, M, g.Cout, K, 1, status, st);
-    return launch_gemm<128>(GatherFwd<128>{X, Wt, g, M, K}, epi, M, g.Cout, K, 1, status, st);
+    if (g.Cout <= 16) return launch_gemm_async<16>(GatherFwd<16>{X, Wt, g, M, K, ncb}, epi, M, g.Cout, K, status, st);
+    if (g.Cout <= 32) return launch_gemm_async<32>(GatherFwd<32>{X, Wt, g, M, K, ncb}, epi, M, g.Cout, K, status, st);
+    if (g.Cout <= 64) return launch_gemm_async<64>(GatherFwd<64>{X, Wt, g, M, K, ncb}, epi, M, g.Cout, K, status, st);
+    return launch_gemm_async<128>(GatherFwd<128>{X, Wt, g, M, K, ncb}, epi, M, g.Cout, K, status, st);
 }
 
 cudaError_t conv_dgrad(const ConvGeom& g, const bf16* dZ, const bf16* WT, float* dX, int accumulate,
                        int* status, cudaStream_t st) {
-    const int M = g.n * g.H * g.W, K = 9 * g.Cout;
+    const int M = g.n * g.H * g.W, K = 9 * g.Cout, ncb = (g.Cout + 63) / 64;
     EpiDgrad epi{dX, g.Cin, accumulate};
-    if (g.Cin <= 16) return launch_gemm<16>(GatherDgrad<16>{dZ, WT, g, M, K}, epi, M, g.Cin, K, 1, status, st);
-    if (g.Cin <= 32) return launch_gemm<32>(GatherDgrad<32>{dZ, WT, g, M, K}, epi, M, g.Cin, K, 1, status, st);
-    if (g.Cin <= 64) return launch_gemm<64>(GatherDgrad<64>{dZ, WT, g, M, K}, epi, M, g.Cin, K, 1, status, st);
-    return launch_gemm<128>(GatherDgrad<128>{dZ, WT, g, M, K}, epi, M, g.Cin, K, 1, status, st);
+    if (g.Cin <= 16) return launch_gemm_async<16>(GatherDgrad<16>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
+    if (g.Cin <= 32) return launch_gemm_async<32>(GatherDgrad<32>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
+    if (g.Cin <= 64) return launch_gemm_async<64>(GatherDgrad<64>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
+    return launch_gemm_async<128>(GatherDgrad<128>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
 }
 
 cudaError_t conv_wgrad(const ConvGeom& g, const bf16* dZ, const bf16* X, float* dW, int sms,
@@ -613,6 +635,7 @@ int fb_initnet_forward(fb_initnet* net, const uint8_t* src, const uint8_t* tgt, 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     int rc = net_forward(net, src, tgt, n, st);
     if (rc) return rc;
+    fb::count_launches(net->ctx, 16);  // input, 3 concatenations, 12 convolutions
     if (head_out) {
         const size_t Pq = static_cast<size_t>(n) * (net->H / net->ds) * (net->W / net->ds);
         NET_CUDA(net, cudaMemcpyAsync(head_out, net->head, Pq * 8 * 4, cudaMemcpyDeviceToDevice, st));
@@ -626,6 +649,7 @@ int fb_initnet_init_nnf(fb_initnet* net, int n, int32_t* nnf_out, void* stream) 
     fb::net::offsets_to_nnf_kernel<<<fb::net::blocks(total), 256, 0, static_cast<cudaStream_t>(stream)>>>(
         net->head, n, net->H, net->W, net->ds, nnf_out);
     NET_CUDA(net, cudaGetLastError());
+    fb::count_launches(net->ctx, 1);
     return FB_OK;
 }
 
@@ -685,6 +709,9 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
         if (rc) return rc;
     }
     if (loss_out) NET_CUDA(net, cudaMemcpyAsync(loss_out, net->loss, 4, cudaMemcpyDeviceToDevice, st));
+    // forward 16, loss 1, per layer ReLU/bias/weight gradients (36) and input gradients
+    // (11), 3 concatenation splits; with an update Adam 1 and the bf16 refresh 12.
+    fb::count_launches(net->ctx, 67 + (lr > 0.f ? 13 : 0));
     return FB_OK;
 }
 

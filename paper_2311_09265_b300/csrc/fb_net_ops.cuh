@@ -71,6 +71,57 @@ struct GatherFwd {
             store_unit(sb, row, 8 * u, v);
         }
     }
+    // Pipelined path (tc_gemm_async_kernel): K is walked tap-major in blocks of 64
+    // input channels, chunk c = (tap, channel block), so a chunk is 8 contiguous 16-byte
+    // copies per output pixel and the pixel is decoded once per thread.
+    int ncb;  // channel blocks: (Cin + 63) / 64
+    struct State {
+        long long base;  // element offset of the pixel's top-left tap (may be negative)
+        uint32_t ok;     // bits 0-2: tap rows inside the image, bits 3-5: tap columns
+    };
+    __device__ __forceinline__ State thread_state(int m0) const {
+        State st{0, 0u};
+        const int m = m0 + static_cast<int>(threadIdx.x);
+        if (m < M) {
+            const int img = m / (g.Ho * g.Wo);
+            const int rem = m - img * g.Ho * g.Wo;
+            const int oy = rem / g.Wo, ox = rem - (rem / g.Wo) * g.Wo;
+            const int y0 = oy * g.stride - 1, x0 = ox * g.stride - 1;
+            st.base = ((static_cast<long long>(img) * g.H + y0) * g.W + x0) * g.Cin;
+#pragma unroll
+            for (int d = 0; d < 3; ++d) {
+                if (y0 + d >= 0 && y0 + d < g.H) st.ok |= 1u << d;
+                if (x0 + d >= 0 && x0 + d < g.W) st.ok |= 1u << (3 + d);
+            }
+        }
+        return st;
+    }
+    __device__ __forceinline__ int chunks() const { return 9 * ncb; }
+    __device__ __forceinline__ int k_steps(int c) const {
+        const int cb = c - (c / ncb) * ncb;
+        return (min(64, g.Cin - 64 * cb) + 15) / 16;
+    }
+    __device__ __forceinline__ void load_async(const State& st, uint32_t sa, uint32_t sb, int c,
+                                               int n0) const {
+        const int t = threadIdx.x;
+        const int tap = c / ncb, cb = c - tap * ncb;
+        const int dy = (tap * 11) >> 5, dx = tap - 3 * dy;  // tap / 3, tap % 3 for tap < 9
+        const int c0 = 64 * cb;
+        const bool pix = ((st.ok >> dy) & (st.ok >> (3 + dx)) & 1u) != 0u;
+        const long long off = st.base + (static_cast<long long>(dy) * g.W + dx) * g.Cin + c0;
+#pragma unroll
+        for (int u = 0; u < tc::BK / 8; ++u) {
+            const bool v = pix && c0 + 8 * u < g.Cin;
+            tc::cp_async16(sa + tc::tile_off(t, 8 * u), v ? X + off + 8 * u : X, v ? 16u : 0u);
+        }
+        for (int idx = t; idx < BN * (tc::BK / 8); idx += 128) {
+            const int row = idx >> 3, u = idx & 7;
+            const int n = n0 + row, ci = c0 + 8 * u;
+            const bool v = n < g.Cout && ci < g.Cin;
+            tc::cp_async16(sb + tc::tile_off(row, 8 * u),
+                           v ? Wt + static_cast<size_t>(n) * K + tap * g.Cin + ci : Wt, v ? 16u : 0u);
+        }
+    }
 };
 
 // bias + optional ReLU, bf16 output [M][Cout] (or fp32 output when Yf is set).
@@ -149,6 +200,57 @@ struct GatherDgrad {
             if (n < g.Cin && k < K)
                 v = __ldg(reinterpret_cast<const uint4*>(WT + static_cast<size_t>(n) * K + k));
             store_unit(sb, row, 8 * u, v);
+        }
+    }
+    // Pipelined path: K walked tap-major in blocks of 64 output channels, as in GatherFwd.
+    int ncb;  // (Cout + 63) / 64
+    struct State {
+        int img, y1, x1;  // input pixel (y + 1, x + 1); img < 0 past the end
+    };
+    __device__ __forceinline__ State thread_state(int m0) const {
+        State st{-1, 0, 0};
+        const int m = m0 + static_cast<int>(threadIdx.x);
+        if (m < M) {
+            st.img = m / (g.H * g.W);
+            const int rem = m - st.img * g.H * g.W;
+            st.y1 = rem / g.W + 1;
+            st.x1 = rem - (rem / g.W) * g.W + 1;
+        }
+        return st;
+    }
+    __device__ __forceinline__ int chunks() const { return 9 * ncb; }
+    __device__ __forceinline__ int k_steps(int c) const {
+        const int cb = c - (c / ncb) * ncb;
+        return (min(64, g.Cout - 64 * cb) + 15) / 16;
+    }
+    __device__ __forceinline__ void load_async(const State& st, uint32_t sa, uint32_t sb, int c,
+                                               int n0) const {
+        const int t = threadIdx.x;
+        const int tap = c / ncb, cb = c - tap * ncb;
+        const int dy = (tap * 11) >> 5, dx = tap - 3 * dy;
+        const int c0 = 64 * cb;
+        // output pixel (ty, tx) / stride feeds input pixel (y, x) through tap (dy, dx)
+        const int ty = st.y1 - dy, tx = st.x1 - dx;
+        bool pix = st.img >= 0 && ty >= 0 && tx >= 0;
+        int oy = ty, ox = tx;
+        if (g.stride == 2) {
+            pix = pix && ((ty | tx) & 1) == 0;
+            oy = ty >> 1;
+            ox = tx >> 1;
+        }
+        pix = pix && oy < g.Ho && ox < g.Wo;
+        const size_t off = pix ? ((static_cast<size_t>(st.img) * g.Ho + oy) * g.Wo + ox) * g.Cout + c0 : 0;
+#pragma unroll
+        for (int u = 0; u < tc::BK / 8; ++u) {
+            const bool v = pix && c0 + 8 * u < g.Cout;
+            tc::cp_async16(sa + tc::tile_off(t, 8 * u), v ? dZ + off + 8 * u : dZ, v ? 16u : 0u);
+        }
+        for (int idx = t; idx < BN * (tc::BK / 8); idx += 128) {
+            const int row = idx >> 3, u = idx & 7;
+            const int n = n0 + row, co = c0 + 8 * u;
+            const bool v = n < g.Cin && co < g.Cout;
+            tc::cp_async16(sb + tc::tile_off(row, 8 * u),
+                           v ? WT + static_cast<size_t>(n) * K + tap * g.Cout + co : WT, v ? 16u : 0u);
         }
     }
 };

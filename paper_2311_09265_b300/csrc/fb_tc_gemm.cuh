@@ -188,5 +188,125 @@ constexpr int gemm_smem_bytes() {
     return 2 * (BM * BK * 2 + BN * BK * 2);
 }
 
+// ---- asynchronous-copy variant ------------------------------------------------------
+// 16-byte global -> shared copy that does not pass through registers (cp.async, L2 only);
+// src_bytes = 0 writes zeros (the convolution's padding) and reads nothing.
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src, uint32_t src_bytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(dst), "l"(src),
+                 "r"(src_bytes)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Same GEMM with an S-stage pipeline: the threads issue the asynchronous copies of the
+// chunks S-1 ahead of the one being multiplied, so several chunks of operand loads are
+// in flight while the tensor cores work.  The gather decides the K order:
+//   Gather::State st = gather.thread_state(m0)   per-thread set-up, once per CTA
+//   gather.chunks()                              number of K chunks
+//   gather.k_steps(c)                            K = 16 MMAs chunk c needs (1..4)
+//   gather.load_async(st, sa, sb, c, n0)         issues (without waiting) the copies of
+//                                                chunk c into shared addresses sa (A) /
+//                                                sb (B), tile_off() layout, zeros where
+//                                                the chunk has no data
+// Stage s is refilled only after the mbarrier of its previous MMAs has fired.  Waits are
+// bounded as above.
+template <int BN, int S, class Gather, class Epi, int LA = S - 1>
+__global__ void __launch_bounds__(128) tc_gemm_async_kernel(Gather gather, Epi epi, int M, int N,
+                                                            int K, int* status) {
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tile N");
+    static_assert(S >= 2 && S <= 8 && LA >= 1 && LA <= S - 1, "stages / lookahead");
+    constexpr int A_BYTES = BM * BK * 2;
+    constexpr int B_BYTES = BN * BK * 2;
+    constexpr int STAGE = A_BYTES + B_BYTES;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[S];
+    __shared__ uint32_t tmem_base;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const int n_chunks = gather.chunks();
+    (void)K;
+    const typename Gather::State gst = gather.thread_state(m0);
+
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) mbar_init(&bars[s]);
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TmemCols<BN>::value));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = instr_desc(BN);
+    const uint32_t s0 = smem_u32(smem);
+
+    // Chunks are loaded LA ahead; chunk i + LA reuses the stage of chunk i + LA - S,
+    // whose MMAs were issued S - LA iterations earlier.
+#pragma unroll
+    for (int i = 0; i < LA; ++i) {
+        if (i < n_chunks) gather.load_async(gst, s0 + i * STAGE, s0 + i * STAGE + A_BYTES, i, n0);
+        cp_async_commit();
+    }
+    bool ok = true;
+    for (int i = 0; i < n_chunks; ++i) {
+        const int s = i % S;
+        cp_async_wait<LA - 1>();  // this thread's copies of chunk i have landed
+        asm volatile("fence.proxy.async.shared::cta;");
+        __syncthreads();         // ... and every thread's
+        if (threadIdx.x == 0 && ok) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = s0 + s * STAGE, sb = sa + A_BYTES;
+            const int steps = gather.k_steps(i);
+            for (int j = 0; j < steps; ++j)
+                mma_bf16(tmem, smem_desc(sa + j * 2 * LBO), smem_desc(sb + j * 2 * LBO), idesc,
+                         (i > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&bars[s]);
+        }
+        const int nxt = i + LA;
+        const int prev = nxt - S;  // the chunk that last used nxt's stage
+        if (nxt < n_chunks) {
+            if (prev >= 0 && ok) ok = mbar_wait(&bars[prev % S], (prev / S) & 1);
+            if (ok) {
+                const uint32_t sa = s0 + (nxt % S) * STAGE;
+                gather.load_async(gst, sa, sa + A_BYTES, nxt, n0);
+            }
+        }
+        cp_async_commit();
+    }
+    cp_async_wait<0>();
+    if (n_chunks > 0 && ok) ok = mbar_wait(&bars[(n_chunks - 1) % S], ((n_chunks - 1) / S) & 1);
+    if (!ok && lane == 0) atomicExch(status, 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (ok && n_chunks > 0) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+            if (row < M && n0 + c0 < N) epi.store(row, n0 + c0, v);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TmemCols<BN>::value));
+}
+
+template <int BN, int S>
+constexpr int gemm_async_smem_bytes() {
+    return S * (BM * BK * 2 + BN * BK * 2);
+}
+
 }  // namespace tc
 }  // namespace fb
