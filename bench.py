@@ -43,7 +43,7 @@ SM_MAX_MHZ_NOMINAL = 2032.0
 DP4A_PER_CLK_SM = 64        # integer dot-product (dp4a) issue rate per SM per clock
 # dram__bytes_read.sum + dram__bytes_write.sum of one nnf_iter launch, from an ncu capture
 # of the current kernel, scaled to the workload (see profiles/); None when not captured.
-TRAFFIC_PER_LAUNCH = {"blend_512": 5.81e9}
+TRAFFIC_PER_LAUNCH = {"blend_512": 5.73e9}
 
 
 def parse_args(argv=None):
