@@ -263,6 +263,20 @@ def make_clip(key: str):
     return g, s
 
 
+def noise_pair(H: int, W: int, seed: int, shift=(1, 3)):
+    """Two (H, W, 3) uint8 frames for edge-case shapes (e.g. one side at the largest
+    supported size) where the smooth textures above are slow to synthesise: i.i.d.
+    uniform bytes, and the same texture translated by `shift` (row, col) with
+    edge-replicated borders."""
+    rng = np.random.default_rng(seed)
+    a = rng.integers(0, 256, (H, W, 3), dtype=np.uint8)
+    dr, dc = shift
+    rows = np.clip(np.arange(H) - dr, 0, H - 1)
+    cols = np.clip(np.arange(W) - dc, 0, W - 1)
+    b = a[rows][:, cols]
+    return np.stack([a, b])
+
+
 def small_clip(N: int, H: int, W: int, seed: int, motion: str = "shift"):
     """A small clip for parity tests: guides and styles (N,H,W,3) uint8."""
     if motion == "shift":

@@ -113,3 +113,30 @@ def test_batch_argument_errors(fbp, clips):
         fbp.fb_blend_batch(ctx, [(g, s, 3, 5)], fbp.Params.make(5, 2), flags=fbp.FB_BATCH_VARIANT(7))
     assert e.value.status == fbp.FB_ERR_ARG
     ctx.close()
+
+
+@pytest.mark.slow
+def test_full_manifest_in_the_bench_launch_configuration(fbp):
+    """The 32-clip manifest bench.py times (uneven shapes, windows 5-31, patch 5 and 7,
+    tuned tiles, graph capture), checked on one middle frame of the cheapest clip of each
+    patch size against the oracle, bit for bit."""
+    import torch
+    import bench
+    manifest = synth.batch_manifest(seed=bench.BATCH_SEED)
+    clips, host = [], []
+    for n, (N, H, W, window, patch) in enumerate(manifest):
+        g, s = synth.batch_clip(N, H, W, seed=bench.BATCH_SEED + n)
+        host.append((g, s))
+        clips.append((torch.tensor(g, device="cuda"), torch.tensor(s, device="cuda"), window, patch))
+    ctx = fbp.Context(0)
+    params = fbp.Params.make(5, bench.BATCH_ITERS, 1, 0, bench.BATCH_SEED)
+    fbp.fb_blend_batch(ctx, clips, params)            # tunes and captures
+    outs = fbp.fb_blend_batch(ctx, clips, params)     # graph replay, as timed
+    for k in (5, 7):
+        i = min((c for c in range(len(manifest)) if manifest[c][4] == k),
+                key=lambda c: manifest[c][1] * manifest[c][2] * manifest[c][3])
+        N, H, W, window, patch = manifest[i]
+        g, s = host[i]
+        ref = oracle.blend_frame(g, s, window, N // 2, patch, bench.BATCH_ITERS, seed=bench.BATCH_SEED)
+        assert (outs[i][N // 2].cpu().numpy() == ref).all(), (i, manifest[i])
+    ctx.close()

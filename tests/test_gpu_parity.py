@@ -216,6 +216,17 @@ def test_argument_errors(fbp, ctx):
 # Full-size workloads in the launch configuration bench.py times, checked on samples
 # the oracle can compute one by one.
 # ----------------------------------------------------------------------------------
+@pytest.mark.parametrize("H,W", [(9, 32767), (32767, 9)])
+def test_nnf_at_the_largest_image_side(fbp, ctx, H, W):
+    """The packed NNF entries (row << 16 | col) at the largest supported side, odd sizes
+    (the paired k = 5 row layout's last pair then holds a clamped row)."""
+    g = synth.noise_pair(H, W, seed=77)
+    Fg, Eg = gpu_nnf(fbp, ctx, g[0], g[1], 5, 1, seed=5, tag=oracle.pair_tag(0, 1))
+    Fo, Eo = oracle.nnf(g[0], g[1], 5, 1, seed=5, pair_tag=oracle.pair_tag(0, 1))
+    assert (Fg == Fo).all() and (Eg == Eo).all()
+    assert Fg[..., 0].max() <= H - 1 and Fg[..., 1].max() <= W - 1
+
+
 @pytest.mark.slow
 def test_blend_512_full_size_sampled_frames(fbp, ctx):
     w = synth.WORKLOADS["blend_512"]
