@@ -20,6 +20,9 @@ _DIR = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_DIR, "fbref.c")
 _HDR = os.path.join(_DIR, "fbref.h")
 LIB_PATH = os.path.join(_DIR, "libfbref.so")
+# tests/test_oracle_mutants.py runs the pins against deliberately broken builds of
+# fbref.c; this variable points the front end at such a build instead of LIB_PATH.
+_LIB_OVERRIDE = os.environ.get("FBREF_TEST_LIBRARY")
 
 _lib = None
 
@@ -52,8 +55,11 @@ _P = ctypes.POINTER(Params)
 def lib() -> ctypes.CDLL:
     global _lib
     if _lib is None:
-        build()
-        L = ctypes.CDLL(LIB_PATH)
+        if _LIB_OVERRIDE:
+            L = ctypes.CDLL(_LIB_OVERRIDE)
+        else:
+            build()
+            L = ctypes.CDLL(LIB_PATH)
         L.fbref_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.fbref_ssd.argtypes = [_u8p, _u8p] + [ctypes.c_int] * 7
         L.fbref_ssd.restype = ctypes.c_uint32
@@ -164,13 +170,15 @@ def nnf(src, tgt, patch: int, iters: int, levels: int = 1, r0: int = 0, seed: in
 
 
 def nnf_trace(src, tgt, patch: int, iters: int, r0: int = 0, seed: int = 0, pair_tag: int = 0,
-              init=None):
-    """Alg. 1 (one level) returning F and E after each iteration: (iters+1, H, W)."""
+              init=None, levels: int = 1):
+    """Alg. 1 returning the full-resolution E before the first and after each iteration
+    of level 0: (iters+1, H, W).  With levels > 1, T[0] is the error of the field
+    upsampled from the coarser level."""
     src, tgt = _u8(src), _u8(tgt)
     H, W = src.shape[:2]
     F = np.zeros((H, W, 2), np.int32)
     T = np.zeros((iters + 1, H, W), np.uint32)
-    p = params(patch, iters, 1, r0, seed)
+    p = params(patch, iters, levels, r0, seed)
     ip = None
     if init is not None:
         init = np.ascontiguousarray(init, dtype=np.int32)

@@ -184,6 +184,89 @@ def test_propagation_repairs_one_wrong_match_with_the_correct_sign():
     assert E[x0] == 0
 
 
+def test_propagation_repairs_runs_along_both_axes_with_the_correct_signs():
+    # A horizontal run of wrong matches can only be repaired from the rows above and
+    # below (d = (-1,0), (1,0)), a vertical run only from the columns beside it: each
+    # checks the sign of F(x+d) - d on its own axis (random search limited to radius 1).
+    g, sh = synth.shift_clip(2, 40, 40, seed=21)
+    d = sh[1] - sh[0]
+    Fstar = _true_field(40, 40, d)
+    init = Fstar.copy()
+    run_h = [(20, c) for c in range(10, 30)]
+    run_v = [(r, 8) for r in range(10, 30)]
+    for x in run_h:
+        init[x] = (min(39, Fstar[x][0] + 15), Fstar[x][1])
+    for x in run_v:
+        init[x] = (Fstar[x][0], min(39, Fstar[x][1] + 15))
+    F, E = oracle.nnf(g[0], g[1], 5, 1, r0=1, seed=2, init=init)
+    for x in run_h + run_v:
+        assert tuple(F[x]) == tuple(Fstar[x]) and E[x] == 0, x
+
+
+def test_ties_keep_the_incumbent():
+    # Alg. 1 updates only where the new error is strictly smaller.  On identical
+    # constant frames every candidate ties, so the random initial field never changes.
+    g = np.full((24, 28, 3), 77, np.uint8)
+    F0, _ = oracle.nnf(g, g, 5, 0, seed=12)
+    F3, E3 = oracle.nnf(g, g, 5, 3, seed=12)
+    assert (F3 == F0).all() and (E3 == 0).all()
+
+
+def test_random_init_rows_and_columns_are_independent():
+    # A match drawn uniformly over the source has independent row and column: the
+    # 8 x 8 grid of (row, column) cells is uniformly populated.
+    g = np.zeros((64, 64, 3), np.uint8)
+    F, _ = oracle.nnf(g, g, 3, 0, seed=31)
+    cells = (F[..., 0] // 8) * 8 + F[..., 1] // 8
+    counts = np.bincount(cells.ravel(), minlength=64)
+    expected = F.shape[0] * F.shape[1] / 64
+    chi2 = ((counts - expected) ** 2 / expected).sum()
+    assert chi2 < 120.0, chi2                       # 63 dof; p ~ 2e-5
+    assert abs(np.corrcoef(F[..., 0].ravel(), F[..., 1].ravel())[0, 1]) < 0.05
+
+
+def test_random_search_starts_at_radius_r0():
+    # Target = source moved one column left (match x + (0, 1)), identity start: the
+    # propagation candidates F(x+d) - d all equal the incumbent, so only the random
+    # search can move a pixel, and with r0 = 1 its single candidate (radius r0 >> 0 = 1)
+    # hits the match with probability 1/9 per pixel.
+    a, b = synth.noise_pair(48, 48, seed=5, shift=(0, -1))
+    ident = _true_field(48, 48, (0, 0))
+    F, E = oracle.nnf(a, b, 5, 1, r0=1, seed=8, init=ident)
+    inner = (slice(3, 45), slice(3, 44))
+    hit = (E[inner] == 0).mean()
+    assert 0.05 < hit < 0.2, hit
+
+
+def test_upsampled_field_keeps_the_pixel_parity():
+    # An even shift (2, 4) commutes with the 2x2 box mean, so the coarse level holds the
+    # exact half shift after enough iterations, and the upsampled field 2 F(x/2) + parity
+    # is the exact fine shift: zero error before the first fine iteration.
+    a, b = synth.noise_pair(40, 40, seed=6, shift=(2, 4))
+    F, T = oracle.nnf_trace(a, b, 5, 8, levels=2, seed=3)
+    inner = (slice(6, 34), slice(8, 32))
+    assert (T[0][inner] == 0).mean() > 0.9
+
+
+def test_random_search_is_centred_on_the_running_best():
+    # Smooth texture, known shift d.  Every pixel starts one column off (x + d + (0, 1))
+    # except a checkerboard of pixels that start 12 rows further away.  In one iteration
+    # those pixels take the off-by-one match from a neighbour by propagation, and the
+    # radius-1 random candidate around that running best hits the true match with
+    # probability 1/9; centred on the far start it could not.
+    H = W = 48
+    g, sh = synth.shift_clip(2, H, W, seed=21)
+    d = sh[1] - sh[0]
+    init = _true_field(H, W, (d[0], d[1] + 1))
+    rr, cc = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    far = (rr + cc) % 2 == 0
+    init[far, 0] = np.clip(rr[far] + d[0] + 12, 0, H - 1)
+    F, E = oracle.nnf(g[0], g[1], 5, 1, r0=1, seed=4, init=init)
+    sel = far & (rr >= 6) & (rr < H - 18) & (cc >= 6) & (cc < W - 8)
+    hit = (E[sel] == 0).mean()
+    assert 0.05 < hit < 0.2, hit
+
+
 def test_error_is_monotone_per_pixel_across_iterations():
     g, _ = synth.small_clip(2, 33, 29, seed=17, motion="affine")
     F, T = oracle.nnf_trace(g[0], g[1], 5, 6, seed=4)
