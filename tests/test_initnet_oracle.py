@@ -89,3 +89,62 @@ def test_network_gradient_matches_finite_differences_of_its_loss():
     finally:
         ref.bf16 = saved
     assert ref.n_params() == 779592
+
+
+def test_conv_and_its_gradients_equal_the_library_convolution():
+    """The special case that reduces to a library routine: oracle conv3x3 (NHWC, weights
+    [Cout][3][3][Cin]) equals torch's 2-D cross-correlation with zero padding 1 in float64,
+    and conv3x3_backward equals autograd's input, weight and bias gradients -- for an
+    asymmetric kernel (a transposed tap order or a mirrored offset would differ) at
+    strides 1 and 2 on odd sizes."""
+    import torch
+    import torch.nn.functional as TF
+    rng = np.random.default_rng(3)
+    for stride, (H, W) in ((1, (7, 9)), (2, (7, 9)), (2, (8, 6))):
+        x = rng.normal(size=(2, H, W, 8))
+        w = rng.normal(size=(16, 3, 3, 8))
+        b = rng.normal(size=16)
+        y = ref.conv3x3(x, w, b, stride)
+        xt = torch.tensor(x.transpose(0, 3, 1, 2), requires_grad=True)
+        wt = torch.tensor(w.transpose(0, 3, 1, 2), requires_grad=True)
+        bt = torch.tensor(b, requires_grad=True)
+        yt = TF.conv2d(xt, wt, bt, stride=stride, padding=1)
+        assert y.shape == tuple(yt.permute(0, 2, 3, 1).shape)
+        assert np.allclose(y, yt.detach().numpy().transpose(0, 2, 3, 1), atol=1e-10)
+        dz = rng.normal(size=y.shape)
+        yt.backward(torch.tensor(dz.transpose(0, 3, 1, 2)))
+        dx, dw, db = ref.conv3x3_backward(x, w, dz, stride)
+        assert np.allclose(dx, xt.grad.numpy().transpose(0, 2, 3, 1), atol=1e-10)
+        assert np.allclose(dw, wt.grad.numpy().transpose(0, 2, 3, 1), atol=1e-10)
+        assert np.allclose(db, bt.grad.numpy(), atol=1e-10)
+
+
+def test_network_input_closed_forms():
+    """Box means of constant images map 0 -> -0.5 and 255 -> +0.5; a 2x2 checkerboard of
+    0/255 averages to 127.5 -> 0 at downscale 4; the two spare channels are zero."""
+    n, H, W = 1, 16, 16
+    src = np.zeros((n, H, W, 3), np.uint8)
+    tgt = np.full((n, H, W, 3), 255, np.uint8)
+    x = ref.net_input(src, tgt, ds=4)
+    assert x.shape == (1, 4, 4, 8)
+    assert (x[..., 0:3] == -0.5).all() and (x[..., 3:6] == 0.5).all() and (x[..., 6:] == 0).all()
+    rr, cc = np.meshgrid(np.arange(H), np.arange(W), indexing="ij")
+    chk = np.repeat((((rr + cc) % 2) * 255).astype(np.uint8)[None, :, :, None], 3, axis=3)
+    x = ref.net_input(chk, chk, ds=4)
+    assert (x[..., :6] == 0).all()
+
+
+def test_offset_loss_closed_forms():
+    """Smooth-L1 (delta one pixel) of 16 * head against the target: zero at the target,
+    0.5 d^2 inside one pixel, |d| - 0.5 outside, weights and their sum applied."""
+    head = np.zeros((1, 2, 2, 8))
+    target = np.zeros((1, 2, 2, 2))
+    target[0, 0, 0] = (16.0, -32.0)          # head = target / 16 gives zero there
+    head[0, 0, 0, :2] = (1.0, -2.0)
+    target[0, 0, 1] = (0.5, 0.0)             # d = -0.5  -> 0.125
+    target[0, 1, 0] = (3.0, 0.0)             # d = -3    -> 2.5
+    weight = np.array([[[1.0, 1.0], [1.0, 0.0]]])
+    loss, g = ref.loss_and_grad_head(head, target, weight, 2.0)
+    assert np.isclose(loss, (0.0 + 0.125 + 2.5) / 2.0)
+    assert np.isclose(g[0, 0, 1, 0], -0.5 * 16 / 2.0) and np.isclose(g[0, 1, 0, 0], -1.0 * 16 / 2.0)
+    assert (g[0, 0, 0] == 0).all() and (g[..., 2:] == 0).all()
