@@ -132,6 +132,15 @@ int fb_ctx_profile_read(fb_ctx *ctx, double *ms, uint64_t *launches);
  * kernel's duration.  Synchronous.  Not part of the method. */
 int fb_probe_dp4a(fb_ctx *ctx, double *dp4a_per_s, double *ms);
 
+/* Diagnostics of debug builds: libfb_debug.so (compiled with FB_COUNT_EVALS) counts,
+ * in a device-global counter, every candidate the per-call NNF kernels consider -- one
+ * per pixel and level for the initial match, then per pixel and iteration one per
+ * propagation neighbour inside the image and one per random-search radius, duplicates
+ * of the running best included (Alg. 1).  Writes the count accumulated since the last
+ * reset and resets it if `reset` is non-zero; synchronous; device of the current
+ * context.  The product libfb.so returns FB_ERR_UNSUPPORTED. */
+int fb_debug_candidates_considered(uint64_t *count, int reset);
+
 /* Philox stream id of the ordered pair (source frame j -> target frame i), as used
  * by fb_blend_window and fb_interpolate: (j << 16) | i. */
 uint32_t fb_pair_tag(int j, int i);

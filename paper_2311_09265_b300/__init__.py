@@ -22,7 +22,8 @@ FB_OK, FB_ERR_ARG, FB_ERR_CUDA, FB_ERR_OOM, FB_ERR_TIMEOUT, FB_ERR_UNSUPPORTED =
 
 HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_error",
                     "fb_status_string", "fb_ctx_launches", "fb_ctx_scratch_bytes",
-                    "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a", "fb_pair_tag",
+                    "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a",
+                    "fb_debug_candidates_considered", "fb_pair_tag",
                     "fb_nnf", "fb_remap", "fb_blend_window", "fb_interpolate",
                     "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan",
                     "fb_ctx_batch_variant", "fb_ctx_set_pair_budget",
@@ -107,6 +108,8 @@ def lib() -> ctypes.CDLL:
         L.fb_probe_dp4a.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)]
         L.fb_probe_dp4a.restype = ctypes.c_int
+        L.fb_debug_candidates_considered.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
+        L.fb_debug_candidates_considered.restype = ctypes.c_int
         L.fb_pair_tag.argtypes = [ctypes.c_int, ctypes.c_int]
         L.fb_pair_tag.restype = ctypes.c_uint32
         P = ctypes.POINTER(Params)
@@ -168,6 +171,16 @@ def lib() -> ctypes.CDLL:
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def fb_debug_candidates_considered(reset: bool = False) -> int:
+    """Candidates considered by the per-call NNF kernels since the last reset (debug
+    builds, libfb_debug.so, only; the product library raises FB_ERR_UNSUPPORTED)."""
+    v = ctypes.c_uint64()
+    rc = lib().fb_debug_candidates_considered(ctypes.byref(v), 1 if reset else 0)
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_debug_candidates_considered")
+    return int(v.value)
 
 
 def fb_pair_tag(j: int, i: int) -> int:

@@ -33,21 +33,43 @@ def nvcc() -> str:
     return cand if os.path.exists(cand) else "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
-    """Compile every CUDA source of the package into libfb.so (skip if up to date)."""
-    if not force and not is_stale():
-        return LIB_PATH
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+DEBUG_LIB_PATH = os.path.join(PKG, "libfb_debug.so")
+
+
+def _compile(out: str, defines=(), verbose: bool = False, ptxas_info: bool = False) -> str:
+    tmp = out + f".tmp{os.getpid()}"
     cmd = [nvcc(), *ARCH, "-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC,-O2",
            "-shared", "-I", INCLUDE, "-I", CSRC, "-o", tmp]
+    cmd += [f"-D{d}" for d in defines]
     if ptxas_info:
         cmd += ["-Xptxas", "-v"]
     cmd += [os.path.join(CSRC, s) for s in SOURCES]
     if verbose:
         print(" ".join(cmd), file=sys.stderr)
     subprocess.run(cmd, check=True)
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, out)
+    return out
+
+
+def _stale(path: str) -> bool:
+    if not os.path.exists(path):
+        return True
+    t = os.path.getmtime(path)
+    return any(os.path.getmtime(f) > t for f in _inputs())
+
+
+def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) -> str:
+    """Compile every CUDA source of the package into libfb.so (skip if up to date)."""
+    if not force and not is_stale():
+        return LIB_PATH
+    return _compile(LIB_PATH, verbose=verbose, ptxas_info=ptxas_info)
+
+
+def build_debug(force: bool = False, verbose: bool = False) -> str:
+    """libfb_debug.so: the same sources with FB_COUNT_EVALS (candidate counter)."""
+    if not force and not _stale(DEBUG_LIB_PATH):
+        return DEBUG_LIB_PATH
+    return _compile(DEBUG_LIB_PATH, defines=("FB_COUNT_EVALS",), verbose=verbose)
 
 
 if __name__ == "__main__":

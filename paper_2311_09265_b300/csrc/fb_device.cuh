@@ -9,6 +9,17 @@
 namespace fb {
 namespace dev {
 
+// Debug builds (-DFB_COUNT_EVALS, libfb_debug.so) count every candidate a pixel
+// considers -- the initial match, each propagation neighbour inside the image and each
+// random-search radius, duplicates included -- so a test can hold the count against its
+// closed form.  Product builds compile the counting away.
+#ifdef FB_COUNT_EVALS
+static __device__ unsigned long long g_candidates_considered;
+#define FB_COUNT_CANDIDATES(n) atomicAdd(&::fb::dev::g_candidates_considered, (unsigned long long)(n))
+#else
+#define FB_COUNT_CANDIDATES(n) ((void)0)
+#endif
+
 __device__ __forceinline__ int clampi(int v, int lo, int hi) { return min(max(v, lo), hi); }
 __device__ __forceinline__ uint32_t pack_rc(int r, int c) {
     return (static_cast<uint32_t>(r) << 16) | static_cast<uint32_t>(c);
@@ -218,7 +229,13 @@ __device__ __forceinline__ void iterate_pixel(const uint32_t* __restrict__ rps,
     uint32_t bf = Fpp[x];
     uint32_t be = Epp[x];
 
+#ifdef FB_COUNT_EVALS
+    uint32_t n_considered = 0;
+#endif
     auto consider = [&](int cr, int cc) {
+#ifdef FB_COUNT_EVALS
+        ++n_considered;
+#endif
         const uint32_t f = pack_rc(cr, cc);
         if (f == bf) return;
         uint32_t e;
@@ -262,6 +279,9 @@ __device__ __forceinline__ void iterate_pixel(const uint32_t* __restrict__ rps,
 
     Fnp[x] = bf;
     Enp[x] = be;
+#ifdef FB_COUNT_EVALS
+    FB_COUNT_CANDIDATES(n_considered);
+#endif
 }
 
 // Initial field of Alg. 1 for target pixel (r, c) of one pair and its Eq. 1 error.
@@ -296,6 +316,7 @@ __device__ __forceinline__ void init_pixel(const uint32_t* __restrict__ rps,
     patch_error_below<K>(rps, H, W, ur, uc, t, 0xFFFFFFFFu, &e);
     Fp[x] = pack_rc(ur, uc);
     Ep[x] = e;
+    FB_COUNT_CANDIDATES(1);
 }
 
 // Alg. 2 remap of one pair's style through its NNF at output pixel (r, c): the k^2

@@ -391,3 +391,29 @@ cudaError_t launch_combine(int k, const JobDesc* jobs, int job0, int n_jobs,
 }
 
 }  // namespace fb
+
+// Debug counter of considered candidates (see fb_device.cuh); the product build reports
+// FB_ERR_UNSUPPORTED.
+extern "C" int fb_debug_candidates_considered(uint64_t* count, int reset) {
+#ifdef FB_COUNT_EVALS
+    if (!count) return FB_ERR_ARG;
+    unsigned long long v = 0;
+    if (cudaMemcpyFromSymbol(&v, fb::dev::g_candidates_considered, sizeof(v)) != cudaSuccess) {
+        cudaGetLastError();
+        return FB_ERR_CUDA;
+    }
+    *count = v;
+    if (reset) {
+        const unsigned long long zero = 0;
+        if (cudaMemcpyToSymbol(fb::dev::g_candidates_considered, &zero, sizeof(zero)) != cudaSuccess) {
+            cudaGetLastError();
+            return FB_ERR_CUDA;
+        }
+    }
+    return FB_OK;
+#else
+    (void)count;
+    (void)reset;
+    return FB_ERR_UNSUPPORTED;
+#endif
+}
