@@ -83,6 +83,18 @@ def lib() -> ctypes.CDLL:
                                         _u8p, ctypes.c_int, _P, _f32p]
         L.fbref_interpolate_frame.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               _i32p, _u8p, ctypes.c_int, _P, ctypes.c_int, _f32p]
+        L.fbref_shat.argtypes = [_u8p, _i32p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _u8p]
+        L.fbref_nnf_balanced.argtypes = [_u8p, _u8p, _u8p, ctypes.c_int, ctypes.c_int, _P,
+                                         ctypes.c_uint32, ctypes.c_uint32, _i32p, _i32p, _u32p, _u8p]
+        L.fbref_nnf_balanced.restype = ctypes.c_int
+        L.fbref_blend_frame_balanced.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
+                                                 ctypes.c_int, _f32p]
+        L.fbref_blend_frame_balanced.restype = ctypes.c_int
+        L.fbref_blend_window_balanced.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
+                                                  _f32p]
+        L.fbref_blend_window_balanced.restype = ctypes.c_int
         L.fbref_pair_tag.argtypes = [ctypes.c_int, ctypes.c_int]
         L.fbref_pair_tag.restype = ctypes.c_uint32
         L.fbref_num_threads.restype = ctypes.c_int
@@ -271,4 +283,64 @@ def interpolate_frame(guides, key_idx, key_styles, i: int, patch: int, iters: in
                                        _ptr(out, _f32p))
     if rc != 0:
         raise ValueError("fbref_interpolate_frame: bad arguments")
+    return out
+
+
+# ----------------------------------------------------------------------------------
+# Sec. 3.4 improved loss ("balanced mode")
+# ----------------------------------------------------------------------------------
+def shat(style, nnf, patch: int) -> np.ndarray:
+    """The remap (Alg. 2) of `style` through `nnf`, rounded to 8-bit values."""
+    style = _u8(style)
+    H, W = style.shape[:2]
+    nnf = np.ascontiguousarray(nnf, dtype=np.int32)
+    out = np.zeros((H, W, 3), np.uint8)
+    lib().fbref_shat(_ptr(style, _u8p), _ptr(nnf, _i32p), H, W, patch, _ptr(out, _u8p))
+    return out
+
+
+def nnf_balanced(src_guide, tgt_guide, src_style, patch: int, iters: int, alpha: int,
+                 r0: int = 0, seed: int = 0, pair_tag: int = 0, init=None):
+    """Alg. 1 under the improved loss; returns (F, E, S^ of the last iteration)."""
+    gs, gt, ss = _u8(src_guide), _u8(tgt_guide), _u8(src_style)
+    H, W = gs.shape[:2]
+    F = np.zeros((H, W, 2), np.int32)
+    E = np.zeros((H, W), np.uint32)
+    S = np.zeros((H, W, 3), np.uint8)
+    p = params(patch, iters, 1, r0, seed)
+    ip = None
+    if init is not None:
+        init = np.ascontiguousarray(init, dtype=np.int32)
+        ip = _ptr(init, _i32p)
+    rc = lib().fbref_nnf_balanced(_ptr(gs, _u8p), _ptr(gt, _u8p), _ptr(ss, _u8p), H, W,
+                                  ctypes.byref(p), alpha, pair_tag, ip, _ptr(F, _i32p),
+                                  _ptr(E, _u32p), _ptr(S, _u8p))
+    if rc != 0:
+        raise ValueError("fbref_nnf_balanced: bad arguments")
+    return F, E, S
+
+
+def blend_frame_balanced(guides, styles, window: int, i: int, patch: int, iters: int,
+                         alpha: int, seed: int = 0):
+    g, s = _u8(guides), _u8(styles)
+    N, H, W = g.shape[:3]
+    out = np.zeros((H, W, 3), np.float32)
+    p = params(patch, iters, 1, 0, seed)
+    rc = lib().fbref_blend_frame_balanced(_ptr(g, _u8p), _ptr(s, _u8p), N, H, W, window,
+                                          ctypes.byref(p), alpha, i, _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_blend_frame_balanced: bad arguments")
+    return out
+
+
+def blend_window_balanced(guides, styles, window: int, patch: int, iters: int, alpha: int,
+                          seed: int = 0):
+    g, s = _u8(guides), _u8(styles)
+    N, H, W = g.shape[:3]
+    out = np.zeros((N, H, W, 3), np.float32)
+    p = params(patch, iters, 1, 0, seed)
+    rc = lib().fbref_blend_window_balanced(_ptr(g, _u8p), _ptr(s, _u8p), N, H, W, window,
+                                           ctypes.byref(p), alpha, _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_blend_window_balanced: bad arguments")
     return out

@@ -483,3 +483,158 @@ int fbref_interpolate(const uint8_t *guides, int N, int H, int W, const int32_t 
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Sec. 3.4, improved blending loss ("balanced mode"):                               */
+/*   L(x) = alpha ||G_j[F(x)] - G_i[x]||^2 + ||S_j[F(x)] - S^_i[x]||^2                */
+/* over the k x k RGB patches of Eq. 1 (clamp-to-edge on every image).  S^_i is the  */
+/* remap (Alg. 2) of S_j through the current field, rounded to 8-bit values; it is   */
+/* refreshed once at the beginning of every iteration, and the incumbent's loss is   */
+/* re-evaluated against the refreshed S^_i before the iteration's candidates are     */
+/* compared with it.  alpha is an integer weight in [0, 255].                         */
+/* ------------------------------------------------------------------------------ */
+
+/* S^ = V / k^2 rounded half up per channel, V the Alg. 2 vote sum. */
+void fbref_shat(const uint8_t *style, const int32_t *nnf, int H, int W, int k, uint8_t *shat)
+{
+    size_t n = (size_t)H * W * 3;
+    uint32_t *v = (uint32_t *)malloc(n * sizeof(uint32_t));
+    fbref_remap_sum(style, nnf, H, W, k, v);
+    uint32_t kk = (uint32_t)(k * k);
+    for (size_t t = 0; t < n; ++t) shat[t] = (uint8_t)((v[t] + kk / 2) / kk);
+    free(v);
+}
+
+static uint32_t balanced_loss(const uint8_t *gs, const uint8_t *gt, const uint8_t *ss,
+                              const uint8_t *shat, int H, int W, int k, uint32_t alpha,
+                              int ur, int uc, int xr, int xc)
+{
+    return alpha * fbref_ssd(gs, gt, H, W, k, ur, uc, xr, xc) +
+           fbref_ssd(ss, shat, H, W, k, ur, uc, xr, xc);
+}
+
+/* Alg. 1 with the loss above, one level: the same Jacobi schedule, candidate order,
+ * random streams and strict acceptance as fbref_nnf.  shat_out (nullable) receives the
+ * S^ of the last iteration (of the initial field when iters = 0); err_out holds L with
+ * respect to it. */
+int fbref_nnf_balanced(const uint8_t *src_guide, const uint8_t *tgt_guide,
+                       const uint8_t *src_style, int H, int W, const fbref_params *p,
+                       uint32_t alpha, uint32_t tag, const int32_t *init, int32_t *nnf_out,
+                       uint32_t *err_out, uint8_t *shat_out)
+{
+    if (!params_ok(p, H, W) || p->levels != 1 || alpha > 255) return -1;
+    if (!src_guide || !tgt_guide || !src_style || !nnf_out) return -1;
+    const int k = p->patch, h = H, w = W;
+    size_t npx = (size_t)H * W;
+    int32_t *F = (int32_t *)malloc(npx * 2 * sizeof(int32_t));
+    int32_t *Fn = (int32_t *)malloc(npx * 2 * sizeof(int32_t));
+    uint32_t *E = (uint32_t *)malloc(npx * sizeof(uint32_t));
+    uint32_t *En = (uint32_t *)malloc(npx * sizeof(uint32_t));
+    uint8_t *shat = (uint8_t *)malloc(npx * 3);
+    for (int r = 0; r < h; ++r)
+        for (int c = 0; c < w; ++c) {
+            size_t x = (size_t)r * w + c;
+            if (init) {
+                F[2 * x] = clampi(init[2 * x], 0, h - 1);
+                F[2 * x + 1] = clampi(init[2 * x + 1], 0, w - 1);
+            } else {
+                random_match(p->seed, (uint32_t)x, tag, 0, h, w, &F[2 * x], &F[2 * x + 1]);
+            }
+        }
+    const int r0 = p->r0 > 0 ? p->r0 : (h > w ? h : w);
+    static const int dirs[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    const int rounds = p->iters > 0 ? p->iters : 1;
+    for (int it = 0; it < rounds; ++it) {
+        /* the beginning of the iteration: refresh S^ from the field, re-evaluate E */
+        fbref_shat(src_style, F, h, w, k, shat);
+#pragma omp parallel for schedule(static)
+        for (int r = 0; r < h; ++r)
+            for (int c = 0; c < w; ++c) {
+                size_t x = (size_t)r * w + c;
+                E[x] = balanced_loss(src_guide, tgt_guide, src_style, shat, h, w, k, alpha,
+                                     F[2 * x], F[2 * x + 1], r, c);
+            }
+        if (p->iters == 0) break;
+#pragma omp parallel for schedule(static)
+        for (int r = 0; r < h; ++r) {
+            for (int c = 0; c < w; ++c) {
+                size_t x = (size_t)r * w + c;
+                int32_t br = F[2 * x], bc = F[2 * x + 1];
+                uint32_t be = E[x];
+                for (int d = 0; d < 4; ++d) {
+                    int nr = r + dirs[d][0], nc = c + dirs[d][1];
+                    if (nr < 0 || nr >= h || nc < 0 || nc >= w) continue;
+                    size_t n = (size_t)nr * w + nc;
+                    int cr = clampi(F[2 * n] - dirs[d][0], 0, h - 1);
+                    int cc = clampi(F[2 * n + 1] - dirs[d][1], 0, w - 1);
+                    uint32_t e = balanced_loss(src_guide, tgt_guide, src_style, shat, h, w, k,
+                                               alpha, cr, cc, r, c);
+                    if (e < be) { be = e; br = cr; bc = cc; }
+                }
+                for (int t = 0; (r0 >> t) >= 1; ++t) {
+                    int rad = r0 >> t;
+                    int32_t dr, dc;
+                    fbref_rs_offset(p->seed, (uint32_t)x, tag, 0, it, t, rad, &dr, &dc);
+                    int cr = clampi(br + dr, 0, h - 1);
+                    int cc = clampi(bc + dc, 0, w - 1);
+                    uint32_t e = balanced_loss(src_guide, tgt_guide, src_style, shat, h, w, k,
+                                               alpha, cr, cc, r, c);
+                    if (e < be) { be = e; br = cr; bc = cc; }
+                }
+                Fn[2 * x] = br; Fn[2 * x + 1] = bc; En[x] = be;
+            }
+        }
+        int32_t *tf = F; F = Fn; Fn = tf;
+        uint32_t *te = E; E = En; En = te;
+    }
+    memcpy(nnf_out, F, npx * 2 * sizeof(int32_t));
+    if (err_out) memcpy(err_out, E, npx * sizeof(uint32_t));
+    if (shat_out) memcpy(shat_out, shat, npx * 3);
+    free(F); free(Fn); free(E); free(En); free(shat);
+    return 0;
+}
+
+/* Eq. 2 with the NNFs of the balanced mode: as fbref_blend_frame. */
+int fbref_blend_frame_balanced(const uint8_t *guides, const uint8_t *styles, int N, int H,
+                               int W, int window, const fbref_params *p, uint32_t alpha, int i,
+                               float *out)
+{
+    if (!params_ok(p, H, W) || p->levels != 1 || N < 1 || N > 65535 || window < 1 ||
+        (window & 1) == 0 || i < 0 || i >= N)
+        return -1;
+    const int k = p->patch, M = (window - 1) / 2;
+    size_t npx = (size_t)H * W, fsz = npx * 3;
+    uint32_t *acc = (uint32_t *)calloc(fsz, sizeof(uint32_t));
+    int32_t *F = (int32_t *)malloc(npx * 2 * sizeof(int32_t));
+    uint32_t *V = (uint32_t *)malloc(fsz * sizeof(uint32_t));
+    for (size_t t = 0; t < fsz; ++t) acc[t] = (uint32_t)(k * k) * styles[(size_t)i * fsz + t];
+    int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
+    int rc = 0;
+    for (int j = lo; j <= hi && rc == 0; ++j) {
+        if (j == i) continue;
+        rc = fbref_nnf_balanced(guides + (size_t)j * fsz, guides + (size_t)i * fsz,
+                                styles + (size_t)j * fsz, H, W, p, alpha, fbref_pair_tag(j, i),
+                                NULL, F, NULL, NULL);
+        if (rc == 0) {
+            fbref_remap_sum(styles + (size_t)j * fsz, F, H, W, k, V);
+            for (size_t t = 0; t < fsz; ++t) acc[t] += V[t];
+        }
+    }
+    float den = (float)(255 * k * k * (hi - lo + 1));
+    for (size_t t = 0; t < fsz; ++t) out[t] = (float)acc[t] / den;
+    free(acc); free(F); free(V);
+    return rc;
+}
+
+int fbref_blend_window_balanced(const uint8_t *guides, const uint8_t *styles, int N, int H,
+                                int W, int window, const fbref_params *p, uint32_t alpha,
+                                float *out)
+{
+    size_t fsz = (size_t)H * W * 3;
+    for (int i = 0; i < N; ++i) {
+        int rc = fbref_blend_frame_balanced(guides, styles, N, H, W, window, p, alpha, i,
+                                            out + (size_t)i * fsz);
+        if (rc) return rc;
+    }
+    return 0;
+}

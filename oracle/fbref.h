@@ -94,6 +94,19 @@ int fbref_interpolate_frame(const uint8_t *guides, int N, int H, int W, const in
  * Philox counter. */
 uint32_t fbref_pair_tag(int j, int i);
 
+/* Sec. 3.4 improved loss ("balanced mode"), one level: see fbref.c. */
+void fbref_shat(const uint8_t *style, const int32_t *nnf, int H, int W, int k, uint8_t *shat);
+int fbref_nnf_balanced(const uint8_t *src_guide, const uint8_t *tgt_guide,
+                       const uint8_t *src_style, int H, int W, const fbref_params *p,
+                       uint32_t alpha, uint32_t pair_tag, const int32_t *init_nnf,
+                       int32_t *nnf_out, uint32_t *err_out, uint8_t *shat_out);
+int fbref_blend_frame_balanced(const uint8_t *guides, const uint8_t *styles, int N, int H,
+                               int W, int window, const fbref_params *p, uint32_t alpha, int i,
+                               float *out);
+int fbref_blend_window_balanced(const uint8_t *guides, const uint8_t *styles, int N, int H,
+                                int W, int window, const fbref_params *p, uint32_t alpha,
+                                float *out);
+
 /* Number of OpenMP threads the oracle uses, and a setter (n <= 0 is ignored). */
 int fbref_num_threads(void);
 void fbref_set_num_threads(int n);
