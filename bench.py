@@ -41,6 +41,8 @@ FLUSH_BYTES = 512 * 1024 * 1024
 SM_COUNT_NOMINAL = 148
 SM_MAX_MHZ_NOMINAL = 2032.0
 DP4A_PER_CLK_SM = 64        # integer dot-product (dp4a) issue rate per SM per clock
+# Guide weight of the improved loss (Sec. 3.4) in the balanced workload.
+BALANCED_ALPHA = 10
 # dram__bytes_read.sum + dram__bytes_write.sum of one nnf_iter launch, from an ncu capture
 # of the current kernel, scaled to the workload (see profiles/); None when not captured.
 TRAFFIC_PER_LAUNCH = {"blend_512": 5.73e9}
@@ -53,7 +55,8 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("fastblend", "reference"), default="fastblend")
     ap.add_argument("--workload", default="blend_512",
-                    choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512", "initnet_512"])
+                    choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512", "initnet_512",
+                                                       "balanced_512"])
     ap.add_argument("--learned-iters", type=int, default=2,
                     help="Alg. 1 iterations after the learned initialiser (learned_512)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -187,11 +190,13 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------
 # CPU oracle (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------------
-def oracle_frame_seconds(w: synth.Workload, g, s, frames):
+def oracle_frame_seconds(w: synth.Workload, g, s, frames, alpha=None):
     import oracle
     t0 = time.perf_counter()
     for i in frames:
-        if w.mode == "blend":
+        if w.mode == "blend" and alpha is not None:
+            oracle.blend_frame_balanced(g, s, w.window, i, w.patch, w.iters, alpha, seed=w.seed)
+        elif w.mode == "blend":
             oracle.blend_frame(g, s, w.window, i, w.patch, w.iters, seed=w.seed)
         else:
             oracle.interpolate_frame(g, list(w.keys), s, i, w.patch, w.iters, seed=w.seed)
@@ -204,10 +209,10 @@ def sample_frames(w: synth.Workload, n: int):
     return [mid + d for d in range(n)]
 
 
-def cpu_baseline(w: synth.Workload, g, s, n_frames: int):
+def cpu_baseline(w: synth.Workload, g, s, n_frames: int, alpha=None):
     import oracle
     frames = sample_frames(w, n_frames)
-    secs = oracle_frame_seconds(w, g, s, frames)
+    secs = oracle_frame_seconds(w, g, s, frames, alpha)
     return {"value": len(frames) / secs, "unit": "frames/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"{len(frames)} of {w.N} output frames ({frames}) of the same clip, each "
@@ -226,14 +231,16 @@ def run_reference(args):
                            "blend", N, H, W, patch=patch, iters=BATCH_ITERS, window=window,
                            seed=BATCH_SEED)
     else:
-        w = synth.WORKLOADS[args.workload]
+        w = synth.WORKLOADS["blend_512" if args.workload in ("balanced_512", "learned_512",
+                                                             "initnet_512") else args.workload]
         g, s = make_inputs(w, w.seed)
+    alpha = BALANCED_ALPHA if args.workload == "balanced_512" else None
     frames = sample_frames(w, 1)
     for _ in range(args.warmup):
-        oracle_frame_seconds(w, g, s, frames)
+        oracle_frame_seconds(w, g, s, frames, alpha)
     total = 0.0
     for _ in range(args.steps):
-        total += oracle_frame_seconds(w, g, s, frames)
+        total += oracle_frame_seconds(w, g, s, frames, alpha)
     value = args.steps * len(frames) / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
@@ -272,10 +279,14 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     fbp.build()
     learned = args.workload == "learned_512"
-    w = synth.WORKLOADS["blend_512" if learned else args.workload]
+    balanced = args.workload == "balanced_512"
+    w = synth.WORKLOADS["blend_512" if learned or balanced else args.workload]
     g, s = make_inputs(w, shard_seed(w.seed, rank))
     ctx = fbp.Context(local)
     params = fbp.Params.make(w.patch, w.iters, w.levels, 0, w.seed)
+    if balanced:
+        params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_BALANCED,
+                                 alpha=BALANCED_ALPHA)
     learned_info = None
     if learned:
         # The learned initialiser: trained here, on the method's own NNFs of seeded clips
@@ -372,6 +383,8 @@ def run_gpu(args):
     iter_ms, iter_n = prof["iter"]
     kernel_total_ms = sum(v[0] for v in prof.values())
     ops = iter_ops_per_launch(w) if w.levels == 1 else None  # same per launch with learned init
+    if ops and balanced:
+        ops *= 2   # each candidate compares a guide patch and a style patch
     roof = None
     if iter_n and ops:
         avg_s = iter_ms / iter_n / 1e3
@@ -379,7 +392,9 @@ def run_gpu(args):
         sms = torch.cuda.get_device_properties(local).multi_processor_count
         probe_per_clk = rate / (sms * clocks["sm_mhz"] * 1e6) if clocks.get("sm_mhz") else None
         peak = DP4A_PER_CLK_SM * 4 * SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
-        roof = {"bound": "alu", "kernel": "nnf_iter (Alg. 1 Jacobi iteration)",
+        roof = {"bound": "alu", "kernel": ("nnf_iter_balanced (Alg. 1 Jacobi iteration, Sec. 3.4 "
+                                           "improved loss)" if balanced else
+                                           "nnf_iter (Alg. 1 Jacobi iteration)"),
                 "achieved": achieved, "peak": peak, "unit": "T byte-pair ops/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
                 "peak_basis": (f"{DP4A_PER_CLK_SM} dp4a/clk/SM x {SM_COUNT_NOMINAL} SMs x "
@@ -399,9 +414,11 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": (w.name if not learned else
-                                "learned-init blend all-pairs 60x512x512 k5 w15: BF16 conv initialiser "
-                                f"(tcgen05) + {args.learned_iters} Alg. 1 iteration(s)"),
+        "config": {"workload": ("learned-init blend all-pairs 60x512x512 k5 w15: BF16 conv "
+                                f"initialiser (tcgen05) + {args.learned_iters} Alg. 1 iteration(s)"
+                                if learned else
+                                "balanced blend all-pairs 60x512x512 k5 w15 n6: Sec. 3.4 improved "
+                                f"loss, alpha {BALANCED_ALPHA}" if balanced else w.name),
                    "frames": w.N, "height": w.H, "width": w.W,
                    "patch": w.patch, "window": w.window,
                    "iters": w.iters if not learned else args.learned_iters, "levels": w.levels,
@@ -419,7 +436,8 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(w, g, s, args.cpu_sample_frames)
+        line["cpu_baseline"] = cpu_baseline(w, g, s, args.cpu_sample_frames,
+                                            BALANCED_ALPHA if balanced else None)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

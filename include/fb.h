@@ -67,6 +67,8 @@ typedef struct fb_params {
                        /* fb_nnf reproduce the NNF that the blend/interpolation calls   */
                        /* compute for source frame j -> target frame i                  */
     uint32_t flags;    /* FB_FLAG_* bits below; 0 = the paper's method                  */
+    uint32_t alpha;    /* FB_FLAG_BALANCED / fb_nnf_balanced: integer weight of the      */
+                       /* guide term of the improved loss, 0..255; ignored otherwise    */
 } fb_params;
 
 /* fb_params.flags.  FB_FLAG_LEARNED_INIT (fb_blend_window, fb_interpolate): start Alg. 1
@@ -76,6 +78,11 @@ typedef struct fb_params {
  * NNFs of the call, read with fb_ctx_energy. */
 #define FB_FLAG_LEARNED_INIT 0x1u
 #define FB_FLAG_REPORT_ENERGY 0x2u
+/* FB_FLAG_BALANCED (fb_blend_window only): compute the NNFs with the improved loss of
+ * Sec. 3.4 instead of Eq. 1, as fb_nnf_balanced does for each pair (j -> i) with source
+ * style S_j; levels must be 1, p->alpha <= 255, not with FB_FLAG_LEARNED_INIT.  The
+ * energy that FB_FLAG_REPORT_ENERGY sums is then the improved loss. */
+#define FB_FLAG_BALANCED 0x4u
 
 /* Create a context on CUDA device `device` (made current for the call).  The context
  * allocates scratch lazily and keeps it for reuse until fb_ctx_destroy. */
@@ -113,6 +120,8 @@ typedef enum fb_kernel_kind {
     FB_K_PACK,          /* int32 (row, col) -> packed NNF                        */
     FB_K_COMBINE,       /* Alg. 2 remap fused with Eq. 2 / keyframe weights      */
     FB_K_INITNET,       /* learned initialiser: network forward + initial fields  */
+    FB_K_SHAT,          /* improved loss: remapped source style S^ of every pair  */
+    FB_K_ENERGY,        /* improved loss: incumbent's loss against the new S^      */
     FB_K_COUNT
 } fb_kernel_kind;
 
@@ -159,6 +168,23 @@ uint32_t fb_pair_tag(int j, int i);
 int fb_nnf(fb_ctx *ctx, const uint8_t *src_guide, const uint8_t *tgt_guide, int H, int W,
            const fb_params *p, const int32_t *init_nnf, int32_t *nnf_out, uint32_t *err_out,
            void *stream);
+
+/* Alg. 1 under the improved loss of Sec. 3.4 ("balanced mode") for one pair:
+ *   L(x) = alpha ||G_src[F(x)] - G_tgt[x]||^2 + ||S_src[F(x)] - S^[x]||^2
+ * over k x k RGB patches (clamp-to-edge), S^ = the Alg. 2 remap of src_style through the
+ * current field rounded half up to 8 bits, refreshed at the beginning of every
+ * iteration; the incumbent's loss is re-evaluated against the refreshed S^ before the
+ * iteration's candidates (same schedule, order, random stream and strict acceptance as
+ * fb_nnf) are compared with it.  With iters = 0, err_out is the loss of the initial
+ * field against the S^ it implies.
+ *   src_style  H x W x 3 uint8, the style frame that goes with src_guide (device).
+ *   p          levels must be 1; p->alpha in [0, 255]; p->flags ignored.
+ *   shat_out   H x W x 3 uint8 or NULL: the S^ of the last iteration.
+ * Other arguments and errors as fb_nnf.  Async on `stream`. */
+int fb_nnf_balanced(fb_ctx *ctx, const uint8_t *src_guide, const uint8_t *tgt_guide,
+                    const uint8_t *src_style, int H, int W, const fb_params *p,
+                    const int32_t *init_nnf, int32_t *nnf_out, uint32_t *err_out,
+                    uint8_t *shat_out, void *stream);
 
 /* Alg. 2 (Sec. 3.3), memory-efficient remap of `src_style` (H x W x 3) through `nnf`
  * (H x W x 2 int32, entries clamped into the image):

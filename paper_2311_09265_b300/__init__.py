@@ -24,7 +24,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_status_string", "fb_ctx_launches", "fb_ctx_scratch_bytes",
                     "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a",
                     "fb_debug_candidates_considered", "fb_pair_tag",
-                    "fb_nnf", "fb_remap", "fb_blend_window", "fb_interpolate",
+                    "fb_nnf", "fb_nnf_balanced", "fb_remap", "fb_blend_window", "fb_interpolate",
                     "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan",
                     "fb_ctx_batch_variant", "fb_ctx_set_pair_budget",
                     "fb_initnet_create", "fb_initnet_destroy", "fb_initnet_last_error",
@@ -36,6 +36,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
 
 FB_FLAG_LEARNED_INIT = 0x1
 FB_FLAG_REPORT_ENERGY = 0x2
+FB_FLAG_BALANCED = 0x4
 
 FB_BATCH_NO_GRAPH = 0x1
 
@@ -46,7 +47,7 @@ def FB_BATCH_VARIANT(v: int) -> int:
 
 # fb_kernel_kind, in header order.
 KERNEL_KINDS = ("prep", "downsample", "style", "init", "iter", "unpack", "pack", "combine",
-                "initnet")
+                "initnet", "shat", "energy")
 
 
 class Params(ctypes.Structure):
@@ -54,12 +55,13 @@ class Params(ctypes.Structure):
     _fields_ = [("patch", ctypes.c_int32), ("iters", ctypes.c_int32),
                 ("levels", ctypes.c_int32), ("r0", ctypes.c_int32),
                 ("seed", ctypes.c_uint64), ("pair_tag", ctypes.c_uint32),
-                ("flags", ctypes.c_uint32)]
+                ("flags", ctypes.c_uint32), ("alpha", ctypes.c_uint32)]
 
     @classmethod
     def make(cls, patch: int, iters: int, levels: int = 1, r0: int = 0, seed: int = 0,
-             pair_tag: int = 0) -> "Params":
-        return cls(patch, iters, levels, r0, seed & 0xFFFFFFFFFFFFFFFF, pair_tag & 0xFFFFFFFF, 0)
+             pair_tag: int = 0, flags: int = 0, alpha: int = 0) -> "Params":
+        return cls(patch, iters, levels, r0, seed & 0xFFFFFFFFFFFFFFFF, pair_tag & 0xFFFFFFFF,
+                   flags, alpha)
 
 
 class ClipDesc(ctypes.Structure):
@@ -114,6 +116,8 @@ def lib() -> ctypes.CDLL:
         L.fb_pair_tag.restype = ctypes.c_uint32
         P = ctypes.POINTER(Params)
         L.fb_nnf.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp, _vp, _vp]
+        L.fb_nnf_balanced.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp,
+                                      _vp, _vp, _vp]
         L.fb_remap.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
         L.fb_blend_window.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, P, _vp, _vp]
@@ -304,6 +308,32 @@ def fb_nnf(ctx: Context, src_guide: torch.Tensor, tgt_guide: torch.Tensor, param
                       _stream_handle(stream, ctx.device))
     ctx.check(rc)
     return nnf_out, err_out
+
+
+def fb_nnf_balanced(ctx: Context, src_guide: torch.Tensor, tgt_guide: torch.Tensor,
+                    src_style: torch.Tensor, params: Params, init_nnf: Optional[torch.Tensor] = None,
+                    stream=None):
+    """Alg. 1 under the improved loss of Sec. 3.4 for one pair (params.alpha weighs the
+    guide term).  Returns (nnf (H,W,2) int32, err (H,W) int32 holding uint32 values,
+    S^ of the last iteration (H,W,3) uint8)."""
+    H, W = int(src_guide.shape[0]), int(src_guide.shape[1])
+    _shape(src_guide, (H, W, 3), "src_guide")
+    _shape(tgt_guide, (H, W, 3), "tgt_guide")
+    _shape(src_style, (H, W, 3), "src_style")
+    dev = src_guide.device
+    nnf_out = torch.empty((H, W, 2), dtype=torch.int32, device=dev)
+    err_out = torch.empty((H, W), dtype=torch.int32, device=dev)
+    shat_out = torch.empty((H, W, 3), dtype=torch.uint8, device=dev)
+    if init_nnf is not None:
+        _shape(init_nnf, (H, W, 2), "init_nnf")
+    rc = lib().fb_nnf_balanced(ctx.handle, _ptr(src_guide, torch.uint8, "src_guide"),
+                               _ptr(tgt_guide, torch.uint8, "tgt_guide"),
+                               _ptr(src_style, torch.uint8, "src_style"), H, W, ctypes.byref(params),
+                               _ptr(init_nnf, torch.int32, "init_nnf"),
+                               _ptr(nnf_out, torch.int32, "nnf_out"), _ptr(err_out, torch.int32, "err_out"),
+                               _ptr(shat_out, torch.uint8, "shat_out"), _stream_handle(stream, ctx.device))
+    ctx.check(rc)
+    return nnf_out, err_out, shat_out
 
 
 def fb_remap(ctx: Context, src_style: torch.Tensor, nnf: torch.Tensor, patch: int,

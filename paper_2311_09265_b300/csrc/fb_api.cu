@@ -207,8 +207,14 @@ int check_params(fb_ctx* ctx, const fb_params* p, int H, int W) {
         return fail(ctx, FB_ERR_ARG, "levels must be in [1, 16], got %d", p->levels);
     if (p->r0 < 0 || p->r0 > (1 << 20))
         return fail(ctx, FB_ERR_ARG, "r0 must be in [0, 2^20], got %d", p->r0);
-    if (p->flags & ~(FB_FLAG_LEARNED_INIT | FB_FLAG_REPORT_ENERGY))
+    if (p->flags & ~(FB_FLAG_LEARNED_INIT | FB_FLAG_REPORT_ENERGY | FB_FLAG_BALANCED))
         return fail(ctx, FB_ERR_ARG, "unknown flags 0x%x", p->flags);
+    if (p->flags & FB_FLAG_BALANCED) {
+        if (p->levels != 1) return fail(ctx, FB_ERR_ARG, "FB_FLAG_BALANCED requires levels == 1");
+        if (p->alpha > 255) return fail(ctx, FB_ERR_ARG, "alpha must be in [0, 255], got %u", p->alpha);
+        if (p->flags & FB_FLAG_LEARNED_INIT)
+            return fail(ctx, FB_ERR_ARG, "FB_FLAG_BALANCED does not combine with FB_FLAG_LEARNED_INIT");
+    }
     if (H < p->patch || W < p->patch || H > 32767 || W > 32767)
         return fail(ctx, FB_ERR_ARG, "image %dx%d outside [patch, 32767]", H, W);
     return FB_OK;
@@ -236,6 +242,9 @@ struct Buffers {
     uint8_t* raw[16] = {};       // downsampled guides, levels >= 1
     uint32_t* rec[16] = {};   // row patches per level
     uint32_t* styles = nullptr;
+    uint32_t* srec = nullptr;      // improved loss: style row patches (level 0)
+    uint8_t* shat_img = nullptr;   // improved loss: S^ of a chunk's pairs, H x W x 3 each
+    uint32_t* shat_rec = nullptr;  // ... and their row patches
     uint32_t *FA = nullptr, *FB = nullptr, *EA = nullptr, *EB = nullptr;
     int32_t* init = nullptr;     // learned initial fields of a chunk (int32 pairs)
     PairDesc* pairs = nullptr;
@@ -247,7 +256,8 @@ struct Buffers {
 
 void carve(Carver& cv, Buffers& b, const Levels& L, int k, int n_guides, int n_styles,
            size_t chunk_pairs, size_t n_pairs, size_t n_jobs, bool staging, size_t guide_bytes,
-           size_t style_bytes, size_t out_floats, bool learned = false) {
+           size_t style_bytes, size_t out_floats, bool learned = false,
+           bool balanced = false) {
     for (int l = 0; l < L.n; ++l) {
         const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];
         if (l > 0) b.raw[l] = cv.take<uint8_t>(static_cast<size_t>(n_guides) * npx * 3);
@@ -260,6 +270,12 @@ void carve(Carver& cv, Buffers& b, const Levels& L, int k, int n_guides, int n_s
     b.EA = cv.take<uint32_t>(chunk_pairs * npx0);
     b.EB = cv.take<uint32_t>(chunk_pairs * npx0);
     if (learned) b.init = cv.take<int32_t>(chunk_pairs * npx0 * 2);
+    if (balanced) {
+        const size_t fw = fb::rowpatch_frame_words(k, L.h[0], L.w[0]);
+        b.srec = cv.take<uint32_t>(static_cast<size_t>(n_styles) * fw);
+        b.shat_img = cv.take<uint8_t>(chunk_pairs * npx0 * 3);
+        b.shat_rec = cv.take<uint32_t>(chunk_pairs * fw);
+    }
     b.pairs = cv.take<PairDesc>(n_pairs > 0 ? n_pairs : 1);
     b.jobs = cv.take<JobDesc>(n_jobs > 0 ? n_jobs : 1);
     if (staging) {
@@ -335,6 +351,40 @@ int run_nnf(fb_ctx* ctx, const Buffers& b, const Levels& L, const fb_params* p, 
     return FB_OK;
 }
 
+// Alg. 1 under the improved loss of Sec. 3.4 (level 0 only) for pairs [pair0, pair0 + n):
+// at the beginning of every iteration S^ is rebuilt from the fields (remap of the source
+// style, rounded, laid out as row patches); the Jacobi step then re-evaluates each
+// incumbent against it before comparing candidates.  With no iterations the loss of the
+// initial field is left in E.
+int run_nnf_balanced(fb_ctx* ctx, const Buffers& b, int H, int W, const fb_params* p, int pair0,
+                     int n, const int32_t* user_init, cudaStream_t st, uint32_t** F_out,
+                     uint32_t** E_out) {
+    const int k = p->patch;
+    const LevelGeom g{H, W, b.rec[0]};
+    uint32_t *Fc = b.FA, *Ec = b.EA, *Fo = b.FB, *Eo = b.EB;
+    FB_LAUNCH(ctx, st, FB_K_INIT, fb::launch_nnf_init(k, b.pairs, pair0, n, g, user_init ? 2 : 0, nullptr, 0, 0,
+                                                      user_init, p->seed, 0, Fc, Ec, st));
+    const int r0 = p->r0 > 0 ? p->r0 : (H > W ? H : W);
+    const int rounds = p->iters > 0 ? p->iters : 1;
+    for (int it = 0; it < rounds; ++it) {
+        FB_LAUNCH(ctx, st, FB_K_SHAT, fb::launch_shat(k, b.pairs, pair0, n, H, W, Fc, b.styles, b.shat_img, st));
+        FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(k, b.shat_img, n, H, W, b.shat_rec, st));
+        if (p->iters == 0) {
+            FB_LAUNCH(ctx, st, FB_K_ENERGY, fb::launch_energy_balanced(k, b.pairs, pair0, n, g, b.srec, b.shat_rec,
+                                                                       p->alpha, Fc, Ec, st));
+            break;
+        }
+        // the iteration kernel re-evaluates the incumbent against the new S^ itself
+        FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_nnf_iter_balanced(k, b.pairs, pair0, n, g, b.srec, b.shat_rec,
+                                                                   p->alpha, r0, p->seed, it, Fc, Fo, Eo, st));
+        std::swap(Fc, Fo);
+        std::swap(Ec, Eo);
+    }
+    *F_out = Fc;
+    *E_out = Ec;
+    return FB_OK;
+}
+
 // Group consecutive output jobs into chunks whose pairs fit the F/E budget.
 struct Chunk {
     int job0, n_jobs, pair0, n_pairs;
@@ -345,8 +395,8 @@ size_t pair_budget(const fb_ctx* ctx) {
 }
 
 int make_chunks(fb_ctx* ctx, const std::vector<JobDesc>& jobs, size_t npx0,
-                std::vector<Chunk>& chunks, size_t& max_pairs) {
-    const size_t per_pair = npx0 * 4 * sizeof(uint32_t);
+                std::vector<Chunk>& chunks, size_t& max_pairs, size_t extra_per_pair = 0) {
+    const size_t per_pair = npx0 * 4 * sizeof(uint32_t) + extra_per_pair;
     size_t cap = pair_budget(ctx) / per_pair;
     if (cap > static_cast<size_t>(kMaxChunkPairs)) cap = kMaxChunkPairs;
     if (cap < 1) cap = 1;
@@ -386,9 +436,12 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
         return fail(ctx, FB_ERR_ARG, "guides, styles and out must all be device or all host memory");
     const bool staging = mg == Mem::Host;
 
+    const bool balanced = (p->flags & FB_FLAG_BALANCED) != 0;
+    // the improved loss keeps each pair's S^ image and row patches next to its F/E
+    const size_t extra = balanced ? npx0 * 3 + fb::rowpatch_frame_words(k, H, W) * sizeof(uint32_t) : 0;
     std::vector<Chunk> chunks;
     size_t max_pairs = 0;
-    int rc = make_chunks(ctx, jobs, npx0, chunks, max_pairs);
+    int rc = make_chunks(ctx, jobs, npx0, chunks, max_pairs, extra);
     if (rc) return rc;
 
     const size_t guide_bytes = static_cast<size_t>(N) * npx0 * 3;
@@ -406,12 +459,12 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
     Buffers b;
     Carver measure(nullptr);
     carve(measure, b, L, k, N, n_styles, max_pairs, pairs.size(), jobs.size(), staging, guide_bytes,
-          style_bytes, out_floats, learned);
+          style_bytes, out_floats, learned, balanced);
     rc = ensure_arena(ctx, measure.off);
     if (rc) return rc;
     Carver cv(ctx->arena);
     carve(cv, b, L, k, N, n_styles, max_pairs, pairs.size(), jobs.size(), staging, guide_bytes,
-          style_bytes, out_floats, learned);
+          style_bytes, out_floats, learned, balanced);
 
     rc = upload_tables(ctx, pairs, jobs, b, st);
     if (rc) return rc;
@@ -429,6 +482,8 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
     rc = prep_guides(ctx, b, L, k, g_dev, N, 0, st);
     if (rc) return rc;
     FB_LAUNCH(ctx, st, FB_K_STYLE, fb::launch_style_rgbx(s_dev, static_cast<size_t>(n_styles) * npx0, b.styles, st));
+    if (balanced)
+        FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(k, s_dev, n_styles, H, W, b.srec, st));
 
     if (p->flags & FB_FLAG_REPORT_ENERGY) {
         FB_CUDA(ctx, cudaMemsetAsync(ctx->energy, 0, sizeof(double), st));
@@ -461,7 +516,8 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
                 }
                 init = b.init;
             }
-            rc = run_nnf(ctx, b, L, p, c.pair0, c.n_pairs, init, st, &F, &E);
+            rc = balanced ? run_nnf_balanced(ctx, b, H, W, p, c.pair0, c.n_pairs, init, st, &F, &E)
+                          : run_nnf(ctx, b, L, p, c.pair0, c.n_pairs, init, st, &F, &E);
             if (rc) return rc;
             if (p->flags & FB_FLAG_REPORT_ENERGY) {
                 FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_energy_sum(E, static_cast<size_t>(c.n_pairs) * npx0,
@@ -509,6 +565,8 @@ int check_clips(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     if (!clips || n < 1) return fail(ctx, FB_ERR_ARG, "clips must be a non-empty host array");
     if (!p) return fail(ctx, FB_ERR_ARG, "params is NULL");
     if (p->levels != 1) return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use levels == 1");
+    if (p->flags & FB_FLAG_BALANCED)
+        return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use the plain loss");
     for (int c = 0; c < n; ++c) {
         const fb_clip_desc& d = clips[c];
         fb_params q = *p;
@@ -1154,6 +1212,8 @@ int fb_nnf(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int 
         return fail(ctx, FB_ERR_ARG, "src_guide, tgt_guide and nnf_out must be non-NULL");
     if (init_nnf && p->levels != 1)
         return fail(ctx, FB_ERR_ARG, "an initial NNF requires levels == 1");
+    if (p->flags & FB_FLAG_BALANCED)
+        return fail(ctx, FB_ERR_ARG, "the improved loss needs the source style: use fb_nnf_balanced");
     DeviceGuard dg(ctx->device);
     for (const void* q : {static_cast<const void*>(src_guide), static_cast<const void*>(tgt_guide),
                           static_cast<const void*>(nnf_out), static_cast<const void*>(init_nnf),
@@ -1184,6 +1244,57 @@ int fb_nnf(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int 
     rc = run_nnf(ctx, b, L, p, 0, 1, init_nnf, st, &F, &E);
     if (rc) return rc;
     FB_LAUNCH(ctx, st, FB_K_UNPACK, fb::launch_nnf_unpack(F, E, npx0, nnf_out, err_out, st));
+    return FB_OK;
+}
+
+int fb_nnf_balanced(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide,
+                    const uint8_t* src_style, int H, int W, const fb_params* p,
+                    const int32_t* init_nnf, int32_t* nnf_out, uint32_t* err_out, uint8_t* shat_out,
+                    void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->err.clear();
+    if (!p) return fail(ctx, FB_ERR_ARG, "params is NULL");
+    fb_params q = *p;
+    q.flags = FB_FLAG_BALANCED;
+    int rc = check_params(ctx, &q, H, W);
+    if (rc) return rc;
+    if (!src_guide || !tgt_guide || !src_style || !nnf_out)
+        return fail(ctx, FB_ERR_ARG, "src_guide, tgt_guide, src_style and nnf_out must be non-NULL");
+    DeviceGuard dg(ctx->device);
+    for (const void* v : {static_cast<const void*>(src_guide), static_cast<const void*>(tgt_guide),
+                          static_cast<const void*>(src_style), static_cast<const void*>(nnf_out),
+                          static_cast<const void*>(init_nnf), static_cast<const void*>(err_out),
+                          static_cast<const void*>(shat_out)})
+        if (v && classify(ctx, v) != Mem::Device)
+            return fail(ctx, FB_ERR_ARG, "fb_nnf_balanced takes device pointers of the context's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Levels L = level_dims(H, W, 1);
+    const size_t npx0 = static_cast<size_t>(H) * W;
+
+    Buffers b;
+    Carver measure(nullptr);
+    carve(measure, b, L, q.patch, 2, 1, 1, 1, 0, false, 0, 0, 0, false, true);
+    rc = ensure_arena(ctx, measure.off);
+    if (rc) return rc;
+    Carver cv(ctx->arena);
+    carve(cv, b, L, q.patch, 2, 1, 1, 1, 0, false, 0, 0, 0, false, true);
+
+    std::vector<PairDesc> pairs(1);
+    pairs[0] = PairDesc{0, 1, q.pair_tag, 0, 1u, {0, 0, 0}};
+    rc = upload_tables(ctx, pairs, {}, b, st);
+    if (rc) return rc;
+    rc = prep_guides(ctx, b, L, q.patch, src_guide, 1, 0, st);
+    if (rc) return rc;
+    rc = prep_guides(ctx, b, L, q.patch, tgt_guide, 1, 1, st);
+    if (rc) return rc;
+    FB_LAUNCH(ctx, st, FB_K_STYLE, fb::launch_style_rgbx(src_style, npx0, b.styles, st));
+    FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(q.patch, src_style, 1, H, W, b.srec, st));
+    uint32_t *F = nullptr, *E = nullptr;
+    rc = run_nnf_balanced(ctx, b, H, W, &q, 0, 1, init_nnf, st, &F, &E);
+    if (rc) return rc;
+    FB_LAUNCH(ctx, st, FB_K_UNPACK, fb::launch_nnf_unpack(F, E, npx0, nnf_out, err_out, st));
+    if (shat_out)
+        FB_CUDA(ctx, cudaMemcpyAsync(shat_out, b.shat_img, npx0 * 3, cudaMemcpyDeviceToDevice, st));
     return FB_OK;
 }
 
@@ -1262,6 +1373,8 @@ int fb_interpolate(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, cons
     ctx->err.clear();
     int rc = check_params(ctx, p, H, W);
     if (rc) return rc;
+    if (p->flags & FB_FLAG_BALANCED)
+        return fail(ctx, FB_ERR_ARG, "FB_FLAG_BALANCED applies to fb_blend_window only");
     if (N < 1 || N > 65535) return fail(ctx, FB_ERR_ARG, "N must be in [1, 65535], got %d", N);
     if (!guides || !key_idx || !key_styles || !out)
         return fail(ctx, FB_ERR_ARG, "guides, key_idx, key_styles and out must be non-NULL");

@@ -208,26 +208,116 @@ __device__ __forceinline__ bool patch_error_below(const uint32_t* __restrict__ r
     }
 }
 
-// One Jacobi iteration of Alg. 1 (Sec. 3.2 parallel update) for target pixel (r, c) of
-// one pair: reads the pair's snapshot (Fp, Ep), writes (Fn, En).  Propagation from the
-// four neighbours in the order (-1,0), (1,0), (0,-1), (0,1), then random search around
-// the running best with radius r0 >> t; strict improvement only.  A candidate equal to
-// the running best is skipped: its error equals the incumbent's, so it could not win.
+// Improved loss of Sec. 3.4 for candidate u = (ur, uc):
+//   alpha * Eq.1(G_src at u, G_tgt at x) + Eq.1(S_src at u, S^ at x),
+// accumulated per row (per paired slot for k = 5) with the same exact early exit as
+// patch_error_below.  tg / ts: target guide and S^ patches of x; rpg / rpss: source
+// guide and style row patches.  alpha <= 255 keeps every partial sum in uint32.
 template <int K>
-__device__ __forceinline__ void iterate_pixel(const uint32_t* __restrict__ rps,
-                                              const uint32_t* __restrict__ rpt, int H, int W,
-                                              int r, int c, uint32_t tag, int r0, uint32_t key0,
-                                              uint32_t key1, uint32_t ctr_word,
-                                              const uint32_t* __restrict__ Fpp,
-                                              const uint32_t* __restrict__ Epp,
-                                              uint32_t* __restrict__ Fnp,
-                                              uint32_t* __restrict__ Enp) {
-    const size_t x = static_cast<size_t>(r) * W + c;
-    TargetPatch<K> t;
-    load_target<K>(rpt, H, W, r, c, t);
+__device__ __forceinline__ bool balanced_error_below(const uint32_t* __restrict__ rpg,
+                                                     const uint32_t* __restrict__ rpss, int H,
+                                                     int W, int ur, int uc,
+                                                     const TargetPatch<K>& tg,
+                                                     const TargetPatch<K>& ts, uint32_t alpha,
+                                                     uint32_t bound, uint32_t* e) {
+    using G = Geo<K>;
+    uint32_t acc = 0;
+    if constexpr (G::PAIRED) {
+        const int odd = ur & 1;
+        const size_t stride = static_cast<size_t>(W) * 8;
+        const size_t off = (static_cast<size_t>(ur >> 1) * W + uc) * 8;
+#pragma unroll
+        for (int i = 0; i < 3; ++i) {
+            const int L = i == 0 ? 1 : (i == 1 ? 0 : 2);
+            uint32_t sg[8], sst[8];
+            load_slot(rpg + off + L * stride, sg);
+            load_slot(rpss + off + L * stride, sst);
+            uint32_t gd = 0, gs = 0, gt = 0, sd = 0, ss = 0, st = 0;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int a_ev = 2 * L + half, a_od = 2 * L + half - 1;
+                const bool v_ev = a_ev <= 4, v_od = a_od >= 0;
+                const bool valid = odd ? v_od : v_ev;
+                const int ae = v_ev ? a_ev : 0, ao = v_od ? a_od : 0;
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const uint32_t tgw = valid ? (odd ? tg.w[ao][w] : tg.w[ae][w]) : 0u;
+                    const uint32_t tsw = valid ? (odd ? ts.w[ao][w] : ts.w[ae][w]) : 0u;
+                    const uint32_t a = valid ? sg[4 * half + w] : 0u;
+                    const uint32_t b = valid ? sst[4 * half + w] : 0u;
+                    gd = __dp4a(a, tgw, gd);
+                    gs = __dp4a(a, a, gs);
+                    gt = __dp4a(tgw, tgw, gt);
+                    sd = __dp4a(b, tsw, sd);
+                    ss = __dp4a(b, b, ss);
+                    st = __dp4a(tsw, tsw, st);
+                }
+            }
+            acc += alpha * (gs + gt - 2u * gd) + (ss + st - 2u * sd);
+            if (acc >= bound) return false;
+        }
+    } else {
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+            const int rr = clampi(ur - G::P + a, 0, H - 1);
+            uint32_t sg[G::NW], sst[G::NW];
+            load_row<K>(rpg + (static_cast<size_t>(rr) * W + uc) * G::RPW, sg);
+            load_row<K>(rpss + (static_cast<size_t>(rr) * W + uc) * G::RPW, sst);
+            uint32_t gd = 0, gs = 0, sd = 0, ss = 0;
+#pragma unroll
+            for (int w = 0; w < G::NW; ++w) {
+                gd = __dp4a(sg[w], tg.w[a][w], gd);
+                gs = __dp4a(sg[w], sg[w], gs);
+                sd = __dp4a(sst[w], ts.w[a][w], sd);
+                ss = __dp4a(sst[w], sst[w], ss);
+            }
+            acc += alpha * (gs + tg.row_e[a] - 2u * gd) + (ss + ts.row_e[a] - 2u * sd);
+            if (acc >= bound) return false;
+        }
+    }
+    *e = acc;
+    return true;
+}
 
-    uint32_t bf = Fpp[x];
-    uint32_t be = Epp[x];
+// Candidate-error functors of the two losses (bound: the incumbent's error).
+template <int K>
+struct PlainError {
+    const uint32_t* rps;
+    int H, W;
+    const TargetPatch<K>& t;
+    __device__ __forceinline__ bool operator()(int ur, int uc, uint32_t bound, uint32_t* e) const {
+        return patch_error_below<K>(rps, H, W, ur, uc, t, bound, e);
+    }
+};
+
+template <int K>
+struct BalancedError {
+    const uint32_t* rpg;
+    const uint32_t* rpss;
+    int H, W;
+    const TargetPatch<K>& tg;
+    const TargetPatch<K>& ts;
+    uint32_t alpha;
+    __device__ __forceinline__ bool operator()(int ur, int uc, uint32_t bound, uint32_t* e) const {
+        return balanced_error_below<K>(rpg, rpss, H, W, ur, uc, tg, ts, alpha, bound, e);
+    }
+};
+
+// One Jacobi iteration of Alg. 1 (Sec. 3.2 parallel update) for target pixel (r, c) of
+// one pair under the candidate error `err`: reads the pair's snapshot (Fp, Ep), writes
+// (Fn, En).  Propagation from the four neighbours in the order (-1,0), (1,0), (0,-1),
+// (0,1), then random search around the running best with radius r0 >> t; strict
+// improvement only.  A candidate equal to the running best is skipped: its error equals
+// the incumbent's, so it could not win.
+// (bf, be): the incumbent match and its error under `err`.
+template <int K, class Err>
+__device__ __forceinline__ void search_pixel(const Err& err, int H, int W, int r, int c,
+                                             uint32_t tag, int r0, uint32_t key0, uint32_t key1,
+                                             uint32_t ctr_word, const uint32_t* __restrict__ Fpp,
+                                             uint32_t bf, uint32_t be,
+                                             uint32_t* __restrict__ Fnp,
+                                             uint32_t* __restrict__ Enp) {
+    const size_t x = static_cast<size_t>(r) * W + c;
 
 #ifdef FB_COUNT_EVALS
     uint32_t n_considered = 0;
@@ -239,7 +329,7 @@ __device__ __forceinline__ void iterate_pixel(const uint32_t* __restrict__ rps,
         const uint32_t f = pack_rc(cr, cc);
         if (f == bf) return;
         uint32_t e;
-        if (patch_error_below<K>(rps, H, W, cr, cc, t, be, &e)) {
+        if (err(cr, cc, be, &e)) {
             be = e;
             bf = f;
         }
@@ -282,6 +372,42 @@ __device__ __forceinline__ void iterate_pixel(const uint32_t* __restrict__ rps,
 #ifdef FB_COUNT_EVALS
     FB_COUNT_CANDIDATES(n_considered);
 #endif
+}
+
+// The plain method: Eq. 1 on the guides.
+template <int K>
+__device__ __forceinline__ void iterate_pixel(const uint32_t* __restrict__ rps,
+                                              const uint32_t* __restrict__ rpt, int H, int W,
+                                              int r, int c, uint32_t tag, int r0, uint32_t key0,
+                                              uint32_t key1, uint32_t ctr_word,
+                                              const uint32_t* __restrict__ Fpp,
+                                              const uint32_t* __restrict__ Epp,
+                                              uint32_t* __restrict__ Fnp,
+                                              uint32_t* __restrict__ Enp) {
+    TargetPatch<K> t;
+    load_target<K>(rpt, H, W, r, c, t);
+    const size_t x = static_cast<size_t>(r) * W + c;
+    search_pixel<K>(PlainError<K>{rps, H, W, t}, H, W, r, c, tag, r0, key0, key1, ctr_word, Fpp,
+                    Fpp[x], Epp[x], Fnp, Enp);
+}
+
+// The improved loss of Sec. 3.4: the pair's S^ (rpshat, refreshed before the iteration)
+// is the style target; the incumbent's loss is evaluated here against that S^.
+template <int K>
+__device__ __forceinline__ void iterate_pixel_balanced(
+    const uint32_t* __restrict__ rpg_src, const uint32_t* __restrict__ rps_src,
+    const uint32_t* __restrict__ rpg_tgt, const uint32_t* __restrict__ rpshat, uint32_t alpha,
+    int H, int W, int r, int c, uint32_t tag, int r0, uint32_t key0, uint32_t key1,
+    uint32_t ctr_word, const uint32_t* __restrict__ Fpp, uint32_t* __restrict__ Fnp,
+    uint32_t* __restrict__ Enp) {
+    TargetPatch<K> tg, ts;
+    load_target<K>(rpg_tgt, H, W, r, c, tg);
+    load_target<K>(rpshat, H, W, r, c, ts);
+    const BalancedError<K> err{rpg_src, rps_src, H, W, tg, ts, alpha};
+    const uint32_t bf = Fpp[static_cast<size_t>(r) * W + c];
+    uint32_t be = 0;
+    err(row_of(bf), col_of(bf), 0xFFFFFFFFu, &be);
+    search_pixel<K>(err, H, W, r, c, tag, r0, key0, key1, ctr_word, Fpp, bf, be, Fnp, Enp);
 }
 
 // Initial field of Alg. 1 for target pixel (r, c) of one pair and its Eq. 1 error.

@@ -77,6 +77,19 @@ cudaError_t launch_nnf_iter(int k, const PairDesc* pairs, int pair0, int n_pairs
 cudaError_t launch_nnf_unpack(const uint32_t* F, const uint32_t* E, size_t npx, int32_t* nnf_out,
                               uint32_t* err_out, cudaStream_t st);
 cudaError_t launch_nnf_pack(const int32_t* nnf, int H, int W, uint32_t* F, cudaStream_t st);
+// Improved loss of Sec. 3.4: S^ images of a chunk's pairs (n_pairs x H x W x 3 bytes,
+// from the fields F and the RGBX styles), the loss of the current fields against their
+// S^ row patches (shat_rp: n_pairs frames; srp: the source styles' row patches), and the
+// Jacobi step under that loss (which evaluates the incumbent's loss itself).  Level 0.
+cudaError_t launch_shat(int k, const PairDesc* pairs, int pair0, int n_pairs, int H, int W,
+                       const uint32_t* F, const uint32_t* styles, uint8_t* shat, cudaStream_t st);
+cudaError_t launch_energy_balanced(int k, const PairDesc* pairs, int pair0, int n_pairs,
+                                   const LevelGeom& g, const uint32_t* srp, const uint32_t* shat_rp,
+                                   uint32_t alpha, const uint32_t* F, uint32_t* E, cudaStream_t st);
+cudaError_t launch_nnf_iter_balanced(int k, const PairDesc* pairs, int pair0, int n_pairs,
+                                     const LevelGeom& g, const uint32_t* srp, const uint32_t* shat_rp,
+                                     uint32_t alpha, int r0, uint64_t seed, int it, const uint32_t* Fp,
+                                     uint32_t* Fn, uint32_t* En, cudaStream_t st);
 cudaError_t launch_combine(int k, const JobDesc* jobs, int job0, int n_jobs,
                            const PairDesc* pairs, int pair0, const uint32_t* F,
                            const uint32_t* styles, int H, int W, float* out, cudaStream_t st);

@@ -206,6 +206,81 @@ __global__ void __launch_bounds__(TILE_THREADS, IterOccupancy<K>::value * 256 / 
                      Fn + static_cast<size_t>(pl) * npx, En + static_cast<size_t>(pl) * npx);
 }
 
+// ---------------------------------------------------------------------------------
+// Improved loss of Sec. 3.4 ("balanced mode").  Per iteration: S^ of every pair from its
+// current field (shat_kernel, then the guide row-patch layout), the incumbent's loss
+// against the new S^ (energy_balanced_kernel), then the Jacobi step under that loss.
+// ---------------------------------------------------------------------------------
+// S^(x) = the Alg. 2 remap of the pair's source style through F, rounded half up to 8 bits.
+template <int K>
+__global__ void __launch_bounds__(TILE_THREADS)
+    shat_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
+                const uint32_t* __restrict__ F, const uint32_t* __restrict__ styles,
+                uint8_t* __restrict__ shat) {
+    const TileCoord tc = tile_coord(W);
+    if (tc.r >= H || tc.c >= W) return;
+    const int pl = blockIdx.y;
+    const PairDesc pd = pairs[pair0 + pl];
+    const size_t npx = static_cast<size_t>(H) * W;
+    uint32_t v0, v1, v2;
+    remap_votes<K>(F + static_cast<size_t>(pl) * npx, styles + static_cast<size_t>(pd.style) * npx, H,
+                   W, tc.r, tc.c, v0, v1, v2);
+    constexpr uint32_t kk = static_cast<uint32_t>(K * K);
+    uint8_t* o = shat + (static_cast<size_t>(pl) * npx + static_cast<size_t>(tc.r) * W + tc.c) * 3;
+    o[0] = static_cast<uint8_t>((v0 + kk / 2) / kk);
+    o[1] = static_cast<uint8_t>((v1 + kk / 2) / kk);
+    o[2] = static_cast<uint8_t>((v2 + kk / 2) / kk);
+}
+
+// E(x) = the improved loss of the pair's current match against its current S^.
+template <int K>
+__global__ void __launch_bounds__(TILE_THREADS)
+    energy_balanced_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
+                           const uint32_t* __restrict__ rp, const uint32_t* __restrict__ srp,
+                           const uint32_t* __restrict__ shat_rp, uint32_t alpha,
+                           const uint32_t* __restrict__ F, uint32_t* __restrict__ E) {
+    const TileCoord tc = tile_coord(W);
+    if (tc.r >= H || tc.c >= W) return;
+    const int pl = blockIdx.y;
+    const PairDesc pd = pairs[pair0 + pl];
+    const size_t x = static_cast<size_t>(tc.r) * W + tc.c;
+    const size_t npx = static_cast<size_t>(H) * W;
+    TargetPatch<K> tg, ts;
+    load_target<K>(frame_rows<K>(rp, pd.tgt, H, W), H, W, tc.r, tc.c, tg);
+    load_target<K>(frame_rows<K>(shat_rp, pl, H, W), H, W, tc.r, tc.c, ts);
+    const uint32_t f = F[static_cast<size_t>(pl) * npx + x];
+    uint32_t e = 0;
+    balanced_error_below<K>(frame_rows<K>(rp, pd.src, H, W), frame_rows<K>(srp, pd.style, H, W), H, W,
+                            row_of(f), col_of(f), tg, ts, alpha, 0xFFFFFFFFu, &e);
+    E[static_cast<size_t>(pl) * npx + x] = e;
+}
+
+// Two target patches per thread: fewer resident blocks than the plain kernel.
+template <int K>
+struct BalancedOccupancy {
+    static constexpr int value = K <= 3 ? 4 : K <= 5 ? 3 : K <= 7 ? 2 : 1;
+};
+
+template <int K>
+__global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
+    nnf_iter_balanced_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
+                             const uint32_t* __restrict__ rp, const uint32_t* __restrict__ srp,
+                             const uint32_t* __restrict__ shat_rp, uint32_t alpha, int r0,
+                             uint32_t key0, uint32_t key1, uint32_t ctr_word,
+                             const uint32_t* __restrict__ Fp, uint32_t* __restrict__ Fn,
+                             uint32_t* __restrict__ En) {
+    const TileCoord tc = tile_coord(W);
+    if (tc.r >= H || tc.c >= W) return;
+    const int pl = blockIdx.y;
+    const PairDesc pd = pairs[pair0 + pl];
+    const size_t npx = static_cast<size_t>(H) * W;
+    iterate_pixel_balanced<K>(frame_rows<K>(rp, pd.src, H, W), frame_rows<K>(srp, pd.style, H, W),
+                              frame_rows<K>(rp, pd.tgt, H, W), frame_rows<K>(shat_rp, pl, H, W), alpha,
+                              H, W, tc.r, tc.c, pd.tag, r0, key0, key1, ctr_word,
+                              Fp + static_cast<size_t>(pl) * npx, Fn + static_cast<size_t>(pl) * npx,
+                              En + static_cast<size_t>(pl) * npx);
+}
+
 __global__ void __launch_bounds__(256) nnf_unpack_kernel(const uint32_t* __restrict__ F,
                                                          const uint32_t* __restrict__ E,
                                                          size_t npx, int32_t* __restrict__ nnf,
@@ -359,6 +434,41 @@ cudaError_t launch_nnf_iter(int k, const PairDesc* pairs, int pair0, int n_pairs
                          pairs, pair0, g.H, g.W, g.rp, r0,
                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32),
                          ctr_word, Fp, Ep, Fn, En)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_shat(int k, const PairDesc* pairs, int pair0, int n_pairs, int H, int W,
+                       const uint32_t* F, const uint32_t* styles, uint8_t* shat, cudaStream_t st) {
+    if (n_pairs <= 0) return cudaSuccess;
+    const dim3 grid = tile_grid(H, W, n_pairs);
+    const dim3 block(TILE_W, TILE_H);
+    FB_DISPATCH_K(k, (shat_kernel<KK><<<grid, block, 0, st>>>(pairs, pair0, H, W, F, styles, shat)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_energy_balanced(int k, const PairDesc* pairs, int pair0, int n_pairs,
+                                   const LevelGeom& g, const uint32_t* srp, const uint32_t* shat_rp,
+                                   uint32_t alpha, const uint32_t* F, uint32_t* E, cudaStream_t st) {
+    if (n_pairs <= 0) return cudaSuccess;
+    const dim3 grid = tile_grid(g.H, g.W, n_pairs);
+    const dim3 block(TILE_W, TILE_H);
+    FB_DISPATCH_K(k, (energy_balanced_kernel<KK><<<grid, block, 0, st>>>(pairs, pair0, g.H, g.W, g.rp, srp,
+                                                                       shat_rp, alpha, F, E)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nnf_iter_balanced(int k, const PairDesc* pairs, int pair0, int n_pairs,
+                                     const LevelGeom& g, const uint32_t* srp, const uint32_t* shat_rp,
+                                     uint32_t alpha, int r0, uint64_t seed, int it, const uint32_t* Fp,
+                                     uint32_t* Fn, uint32_t* En, cudaStream_t st) {
+    if (n_pairs <= 0) return cudaSuccess;
+    const dim3 grid = tile_grid(g.H, g.W, n_pairs);
+    const dim3 block(TILE_W, TILE_H);
+    const uint32_t ctr_word = static_cast<uint32_t>(it + 1) << 8;  // level 0
+    FB_DISPATCH_K(k, (nnf_iter_balanced_kernel<KK><<<grid, block, 0, st>>>(
+                         pairs, pair0, g.H, g.W, g.rp, srp, shat_rp, alpha, r0,
+                         static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), ctr_word,
+                         Fp, Fn, En)));
     return cudaGetLastError();
 }
 

@@ -82,4 +82,4 @@ def test_params_struct_matches_header_layout():
     body = re.search(r"typedef struct fb_params \{(.*?)\} fb_params;", text, re.S).group(1)
     fields = re.findall(r"(u?int\d+_t)\s+([a-z_0-9]+);", body)
     assert [f for _, f in fields] == [f for f, _ in fbp.Params._fields_]
-    assert ctypes.sizeof(fbp.Params) == 32
+    assert ctypes.sizeof(fbp.Params) == 40   # 36 bytes of fields, 8-byte aligned (seed)
