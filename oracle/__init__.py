@@ -95,6 +95,12 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
                                                   _f32p]
         L.fbref_blend_window_balanced.restype = ctypes.c_int
+        L.fbref_blend_frame_fast.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                             ctypes.c_int, _P, ctypes.c_int, _f32p]
+        L.fbref_blend_frame_fast.restype = ctypes.c_int
+        L.fbref_blend_window_fast.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                              ctypes.c_int, _P, _f32p]
+        L.fbref_blend_window_fast.restype = ctypes.c_int
         L.fbref_pair_tag.argtypes = [ctypes.c_int, ctypes.c_int]
         L.fbref_pair_tag.restype = ctypes.c_uint32
         L.fbref_num_threads.restype = ctypes.c_int
@@ -343,4 +349,31 @@ def blend_window_balanced(guides, styles, window: int, patch: int, iters: int, a
                                            ctypes.byref(p), alpha, _ptr(out, _f32p))
     if rc != 0:
         raise ValueError("fbref_blend_window_balanced: bad arguments")
+    return out
+
+
+# ----------------------------------------------------------------------------------
+# Sec. 3.4 fast mode (Algs. 3-5)
+# ----------------------------------------------------------------------------------
+def blend_frame_fast(guides, styles, window: int, i: int, patch: int, iters: int, seed: int = 0):
+    g, s = _u8(guides), _u8(styles)
+    N, H, W = g.shape[:3]
+    out = np.zeros((H, W, 3), np.float32)
+    p = params(patch, iters, 1, 0, seed)
+    rc = lib().fbref_blend_frame_fast(_ptr(g, _u8p), _ptr(s, _u8p), N, H, W, window,
+                                      ctypes.byref(p), i, _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_blend_frame_fast: bad arguments")
+    return out
+
+
+def blend_window_fast(guides, styles, window: int, patch: int, iters: int, seed: int = 0):
+    g, s = _u8(guides), _u8(styles)
+    N, H, W = g.shape[:3]
+    out = np.zeros((N, H, W, 3), np.float32)
+    p = params(patch, iters, 1, 0, seed)
+    rc = lib().fbref_blend_window_fast(_ptr(g, _u8p), _ptr(s, _u8p), N, H, W, window,
+                                       ctypes.byref(p), _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_blend_window_fast: bad arguments")
     return out

@@ -638,3 +638,140 @@ int fbref_blend_window_balanced(const uint8_t *guides, const uint8_t *styles, in
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Sec. 3.4, fast mode: remapping table (Alg. 3), blending table (Alg. 4) and the    */
+/* interval query (Alg. 5) over them, for output frame i.                            */
+/*   Alg. 3 adds (S_a -> S_j) to RemappingTable(j, L+1) for j = a | (2^(L+1) - 1)    */
+/*   whenever bit L of a is 0, i.e. for the 2^L sources a in [j - 2^(L+1) + 1,        */
+/*   j - 2^L]; RemappingTable(j, 0) = S_j.  Alg. 4 takes prefix sums over L, so       */
+/*   BlendingTable(j, L) = sum over a in [j - 2^L + 1, j] of (S_a -> S_j) (a = j: S_j). */
+/*   Alg. 5 walks i = r, r - 2^L, ... down to l, each time with the largest L whose   */
+/*   low L bits of i are set and whose entry stays inside [l, r], and adds            */
+/*   (BlendingTable(i, L) -> S_r) through NNF(G_i, G_r) (the identity when i = r).    */
+/* The window sum of Eq. 2 is the left query [lo, i] plus the query [i, hi] on the    */
+/* reversed clip (the symmetric table) minus S_i (the split identity of Sec. 3.4).   */
+/* All sums are exact integers: a remap contributes its k^2 votes, so the table       */
+/* entries carry k^2 and the query terms k^4 times the remapped values; the result    */
+/* is one division (in double, rounded once to float) by 255 k^4 (hi - lo + 1).       */
+/* ------------------------------------------------------------------------------ */
+
+/* Alg. 2 vote sums of a 3-channel uint32 image (an already-summed table entry). */
+static void remap_sum_u32(const uint32_t *img, const int32_t *nnf, int H, int W, int k,
+                          uint32_t *v_out)
+{
+    int p = k / 2;
+#pragma omp parallel for schedule(static)
+    for (int r = 0; r < H; ++r) {
+        for (int c = 0; c < W; ++c) {
+            uint32_t acc[3] = {0, 0, 0};
+            for (int a = -p; a <= p; ++a) {
+                for (int b = -p; b <= p; ++b) {
+                    int qr = clampi(r + a, 0, H - 1), qc = clampi(c + b, 0, W - 1);
+                    size_t q = (size_t)qr * W + qc;
+                    int fr = clampi(nnf[2 * q], 0, H - 1), fc = clampi(nnf[2 * q + 1], 0, W - 1);
+                    int sr = clampi(fr - (qr - r), 0, H - 1);
+                    int sc = clampi(fc - (qc - c), 0, W - 1);
+                    for (int ch = 0; ch < 3; ++ch) acc[ch] += img[((size_t)sr * W + sc) * 3 + ch];
+                }
+            }
+            size_t x = (size_t)r * W + c;
+            for (int ch = 0; ch < 3; ++ch) v_out[3 * x + ch] = acc[ch];
+        }
+    }
+}
+
+/* frame index of position t in the clip order (reversed for the symmetric table) */
+static int clip_frame(int t, int N, int rev) { return rev ? N - 1 - t : t; }
+
+/* BlendingTable(j, L) in table order `rev` (k^2-scaled): k^2 S_j plus the remaps
+ * (S_a -> S_j) through NNF(G_a, G_j) of the 2^L - 1 earlier positions a. */
+static int blending_entry(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                          const fbref_params *p, int rev, int j, int L, uint32_t *out)
+{
+    const int k = p->patch;
+    size_t npx = (size_t)H * W, fsz = npx * 3;
+    int fj = clip_frame(j, N, rev);
+    for (size_t t = 0; t < fsz; ++t) out[t] = (uint32_t)(k * k) * styles[(size_t)fj * fsz + t];
+    int32_t *F = (int32_t *)malloc(npx * 2 * sizeof(int32_t));
+    uint32_t *V = (uint32_t *)malloc(fsz * sizeof(uint32_t));
+    int rc = 0;
+    for (int a = j - (1 << L) + 1; a < j && rc == 0; ++a) {
+        int fa = clip_frame(a, N, rev);
+        rc = fbref_nnf(guides + (size_t)fa * fsz, guides + (size_t)fj * fsz, H, W, p,
+                       fbref_pair_tag(fa, fj), NULL, F, NULL);
+        if (rc == 0) {
+            fbref_remap_sum(styles + (size_t)fa * fsz, F, H, W, k, V);
+            for (size_t t = 0; t < fsz; ++t) out[t] += V[t];
+        }
+    }
+    free(F); free(V);
+    return rc;
+}
+
+/* Alg. 5 on the table of order `rev`: sum over the interval [l, r] (table positions) of
+ * (S_a -> S_r), k^4-scaled, added into acc. */
+static int query(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                 const fbref_params *p, int rev, int l, int r, uint32_t *acc)
+{
+    const int k = p->patch;
+    size_t npx = (size_t)H * W, fsz = npx * 3;
+    uint32_t *B = (uint32_t *)malloc(fsz * sizeof(uint32_t));
+    uint32_t *V = (uint32_t *)malloc(fsz * sizeof(uint32_t));
+    int32_t *F = (int32_t *)malloc(npx * 2 * sizeof(int32_t));
+    int fr = clip_frame(r, N, rev);
+    int rc = 0;
+    int i = r;
+    while (i >= l && rc == 0) {
+        int L = 0;
+        while (((i >> L) & 1) && i - (1 << (L + 1)) + 1 >= l) ++L;
+        rc = blending_entry(guides, styles, N, H, W, p, rev, i, L, B);
+        if (rc) break;
+        if (i == r) {
+            for (size_t t = 0; t < fsz; ++t) acc[t] += (uint32_t)(k * k) * B[t];  /* identity remap */
+        } else {
+            int fi = clip_frame(i, N, rev);
+            rc = fbref_nnf(guides + (size_t)fi * fsz, guides + (size_t)fr * fsz, H, W, p,
+                           fbref_pair_tag(fi, fr), NULL, F, NULL);
+            if (rc) break;
+            remap_sum_u32(B, F, H, W, k, V);
+            for (size_t t = 0; t < fsz; ++t) acc[t] += V[t];
+        }
+        i -= 1 << L;
+    }
+    free(B); free(V); free(F);
+    return rc;
+}
+
+int fbref_blend_frame_fast(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                           int window, const fbref_params *p, int i, float *out)
+{
+    if (!params_ok(p, H, W) || N < 1 || N > 65535 || window < 1 || (window & 1) == 0 || i < 0 || i >= N)
+        return -1;
+    const int k = p->patch, M = (window - 1) / 2;
+    size_t fsz = (size_t)H * W * 3;
+    int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
+    uint32_t *acc = (uint32_t *)calloc(fsz, sizeof(uint32_t));
+    int rc = query(guides, styles, N, H, W, p, 0, lo, i, acc);                     /* [lo, i] */
+    if (rc == 0)
+        rc = query(guides, styles, N, H, W, p, 1, N - 1 - hi, N - 1 - i, acc);    /* [i, hi] */
+    const uint32_t k4 = (uint32_t)(k * k * k * k);
+    double den = 255.0 * k4 * (double)(hi - lo + 1);
+    for (size_t t = 0; t < fsz; ++t) {
+        uint32_t num = acc[t] - k4 * styles[(size_t)i * fsz + t];   /* S_i was counted twice */
+        out[t] = (float)((double)num / den);
+    }
+    free(acc);
+    return rc;
+}
+
+int fbref_blend_window_fast(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                            int window, const fbref_params *p, float *out)
+{
+    size_t fsz = (size_t)H * W * 3;
+    for (int i = 0; i < N; ++i) {
+        int rc = fbref_blend_frame_fast(guides, styles, N, H, W, window, p, i, out + (size_t)i * fsz);
+        if (rc) return rc;
+    }
+    return 0;
+}

@@ -94,6 +94,12 @@ int fbref_interpolate_frame(const uint8_t *guides, int N, int H, int W, const in
  * Philox counter. */
 uint32_t fbref_pair_tag(int j, int i);
 
+/* Sec. 3.4 fast mode (Algs. 3-5 and the split identity): see fbref.c. */
+int fbref_blend_frame_fast(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                           int window, const fbref_params *p, int i, float *out);
+int fbref_blend_window_fast(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                            int window, const fbref_params *p, float *out);
+
 /* Sec. 3.4 improved loss ("balanced mode"), one level: see fbref.c. */
 void fbref_shat(const uint8_t *style, const int32_t *nnf, int H, int W, int k, uint8_t *shat);
 int fbref_nnf_balanced(const uint8_t *src_guide, const uint8_t *tgt_guide,

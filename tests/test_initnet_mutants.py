@@ -36,15 +36,31 @@ sys.exit(pytest.main(["-x", "-q", "-p", "no:cacheprovider", sys.argv[2]]))
 """
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(name, tmp_path):
+def run_mutant(name: str, workdir: str):
     old, new = MUTANTS[name]
     with open(SRC) as f:
         src = f.read()
     assert src.count(old) == 1, f"mutation site of {name} not unique: {old!r}"
-    mutant = tmp_path / "initnet_mutant.py"
-    mutant.write_text(src.replace(old, new))
-    res = subprocess.run([sys.executable, "-c", RUNNER, str(mutant),
+    mutant = os.path.join(workdir, f"{name}.py")
+    with open(mutant, "w") as f:
+        f.write(src.replace(old, new))
+    res = subprocess.run([sys.executable, "-c", RUNNER, mutant,
                           os.path.join(ROOT, "tests", "test_initnet_oracle.py")],
                          cwd=ROOT, capture_output=True, text=True, timeout=600)
-    assert res.returncode == 1, f"no pin failed for mutant {name}:\n{res.stdout[-1500:]}"
+    return res.returncode, res.stdout[-1500:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """All mutants, tested concurrently (each in its own process)."""
+    from concurrent.futures import ThreadPoolExecutor
+    workdir = str(tmp_path_factory.mktemp("initnet_mutants"))
+    with ThreadPoolExecutor(max_workers=max(2, min(8, os.cpu_count() or 2))) as ex:
+        futs = {name: ex.submit(run_mutant, name, workdir) for name in MUTANTS}
+        return {name: f.result() for name, f in futs.items()}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, outcomes):
+    code, out = outcomes[name]
+    assert code == 1, f"no pin failed for mutant {name}:\n{out}"

@@ -4,7 +4,7 @@ Each mutant below is a one-place edit of oracle/fbref.c of the kind a restatemen
 the paper can get wrong (a dropped term, a wrong sign, an index of the wrong axis, a
 non-strict acceptance, an off-by-one bound or constant).  It is compiled into a
 temporary directory and the pin suites (tests/test_oracle_pins.py,
-tests/test_oracle_balanced.py) are run against it:
+tests/test_oracle_balanced.py, tests/test_oracle_fast.py) are run against it:
 every mutant must make at least one pin fail.  The oracle's own source is not touched.
 """
 import os
@@ -43,10 +43,10 @@ MUTANTS = {
                                           "int cr = clampi(F[2 * x] + dr, 0, h - 1);\n                        int cc = clampi(F[2 * x + 1] + dc, 0, w - 1);", None),
     "upsample_drops_parity": ("Fn[2 * x] = clampi(2 * F[2 * xc] + (r & 1), 0, h - 1);",
                               "Fn[2 * x] = clampi(2 * F[2 * xc], 0, h - 1);", None),
-    "remap_offset_sign": ("int sr = clampi(fr - (qr - r), 0, H - 1);", "int sr = clampi(fr + (qr - r), 0, H - 1);", None),
-    "remap_unclamped_neighbour_offset": ("int sc = clampi(fc - (qc - c), 0, W - 1);", "int sc = clampi(fc - b, 0, W - 1);", None),
+    "remap_offset_sign": ("int sr = clampi(fr - (qr - r), 0, H - 1);", "int sr = clampi(fr + (qr - r), 0, H - 1);", 0),
+    "remap_unclamped_neighbour_offset": ("int sc = clampi(fc - (qc - c), 0, W - 1);", "int sc = clampi(fc - b, 0, W - 1);", 0),
     "remap_rows_and_columns_swapped": ("int fr = clampi(nnf[2 * q], 0, H - 1), fc = clampi(nnf[2 * q + 1], 0, W - 1);",
-                                       "int fr = clampi(nnf[2 * q + 1], 0, H - 1), fc = clampi(nnf[2 * q], 0, W - 1);", None),
+                                       "int fr = clampi(nnf[2 * q + 1], 0, H - 1), fc = clampi(nnf[2 * q], 0, W - 1);", 0),
     "remap_divisor_off_by_one": ("float den = (float)(255 * k * k);\n    for (size_t i = 0; i < n; ++i)",
                                  "float den = (float)(255 * k * k + 1);\n    for (size_t i = 0; i < n; ++i)", None),
     "downsample_drops_second_row": ("int r0 = 2 * r, r1 = clampi(2 * r + 1, 0, H - 1);",
@@ -62,6 +62,22 @@ MUTANTS = {
     "balanced_propagation_row_offset_sign": ("int cr = clampi(F[2 * n] - dirs[d][0], 0, h - 1);",
                                              "int cr = clampi(F[2 * n] + dirs[d][0], 0, h - 1);", 1),
     "balanced_random_search_skips_largest_radius": ("int rad = r0 >> t;", "int rad = r0 >> (t + 1);", 1),
+    "fast_table_remap_offset_sign": ("int sr = clampi(fr - (qr - r), 0, H - 1);", "int sr = clampi(fr + (qr - r), 0, H - 1);", 1),
+    "fast_walk_steps_twice_the_piece": ("        i -= 1 << L;", "        i -= 2 << L;", None),
+    "fast_identity_piece_unweighted": ("acc[t] += (uint32_t)(k * k) * B[t];  /* identity remap */",
+                                       "acc[t] += B[t];  /* identity remap */", None),
+    "fast_self_term_not_removed": ("uint32_t num = acc[t] - k4 * styles[(size_t)i * fsz + t];", "uint32_t num = acc[t];", None),
+    "fast_query_nnf_reversed": ("rc = fbref_nnf(guides + (size_t)fi * fsz, guides + (size_t)fr * fsz, H, W, p,\n                           fbref_pair_tag(fi, fr)",
+                                "rc = fbref_nnf(guides + (size_t)fr * fsz, guides + (size_t)fi * fsz, H, W, p,\n                           fbref_pair_tag(fr, fi)", None),
+    "fast_entry_nnf_reversed": ("rc = fbref_nnf(guides + (size_t)fa * fsz, guides + (size_t)fj * fsz, H, W, p,\n                       fbref_pair_tag(fa, fj)",
+                                "rc = fbref_nnf(guides + (size_t)fj * fsz, guides + (size_t)fa * fsz, H, W, p,\n                       fbref_pair_tag(fj, fa)", None),
+    "fast_right_side_not_reversed": ("rc = query(guides, styles, N, H, W, p, 1, N - 1 - hi, N - 1 - i, acc);",
+                                     "rc = query(guides, styles, N, H, W, p, 0, i, hi, acc);", None),
+    "fast_piece_may_leave_the_interval": ("while (((i >> L) & 1) && i - (1 << (L + 1)) + 1 >= l) ++L;",
+                                          "while (((i >> L) & 1) && i - (1 << (L + 1)) + 1 >= l - 1) ++L;", None),
+    "fast_entry_misses_a_source": ("for (int a = j - (1 << L) + 1; a < j && rc == 0; ++a) {",
+                                   "for (int a = j - (1 << L) + 2; a < j && rc == 0; ++a) {", None),
+    "fast_divisor_count": ("double den = 255.0 * k4 * (double)(hi - lo + 1);", "double den = 255.0 * k4 * (double)(hi - lo);", None),
     "blend_divisor_drops_self_term": ("float den = (float)(255 * k * k * (hi - lo + 1));",
                                       "float den = (float)(255 * k * k * (hi - lo));", 0),
     "blend_self_term_unweighted": ("for (size_t t = 0; t < fsz; ++t) acc[t] = (uint32_t)(k * k) * styles[(size_t)i * fsz + t];",
@@ -84,19 +100,39 @@ def mutate(src: str, old: str, new: str, which):
     return src[:pos] + new + src[pos + len(old):]
 
 
-@pytest.mark.parametrize("name", sorted(MUTANTS))
-def test_pins_catch_mutant(name, tmp_path):
+def run_mutant(name: str, workdir: str):
+    """Compile mutant `name` into workdir and run the pin suites against it; returns
+    (pytest exit code, tail of its output)."""
     old, new, which = MUTANTS[name]
     with open(SRC) as f:
         src = f.read()
-    mutant_c = tmp_path / "fbref_mutant.c"
-    mutant_c.write_text(mutate(src, old, new, which))
-    lib = tmp_path / "libfbref_mutant.so"
+    mutant_c = os.path.join(workdir, f"{name}.c")
+    with open(mutant_c, "w") as f:
+        f.write(mutate(src, old, new, which))
+    lib = os.path.join(workdir, f"lib{name}.so")
     subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
-                    "-I", os.path.join(ROOT, "oracle"), "-o", str(lib), str(mutant_c)], check=True)
-    env = dict(os.environ, FBREF_TEST_LIBRARY=str(lib), OMP_NUM_THREADS="4")
+                    "-I", os.path.join(ROOT, "oracle"), "-o", lib, mutant_c], check=True)
+    env = dict(os.environ, FBREF_TEST_LIBRARY=lib, OMP_NUM_THREADS="2")
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_balanced.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_balanced.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_fast.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
-    assert res.returncode == 1, f"no pin failed for mutant {name}:\n{res.stdout[-1500:]}"
+    return res.returncode, res.stdout[-1500:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """All mutants, compiled and tested concurrently (each in its own processes)."""
+    from concurrent.futures import ThreadPoolExecutor
+    workdir = str(tmp_path_factory.mktemp("oracle_mutants"))
+    workers = max(2, min(8, (os.cpu_count() or 2)))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futs = {name: ex.submit(run_mutant, name, workdir) for name in MUTANTS}
+        return {name: f.result() for name, f in futs.items()}
+
+
+@pytest.mark.parametrize("name", sorted(MUTANTS))
+def test_pins_catch_mutant(name, outcomes):
+    code, out = outcomes[name]
+    assert code == 1, f"no pin failed for mutant {name}:\n{out}"
