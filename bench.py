@@ -56,7 +56,9 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=("fastblend", "reference"), default="fastblend")
     ap.add_argument("--workload", default="blend_512",
                     choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512", "initnet_512",
-                                                       "balanced_512"])
+                                                       "balanced_512", "fast_512"])
+    ap.add_argument("--window", type=int, default=0,
+                    help="override the blend window of the headline-clip workloads (odd)")
     ap.add_argument("--learned-iters", type=int, default=2,
                     help="Alg. 1 iterations after the learned initialiser (learned_512)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -190,11 +192,13 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------
 # CPU oracle (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------------
-def oracle_frame_seconds(w: synth.Workload, g, s, frames, alpha=None):
+def oracle_frame_seconds(w: synth.Workload, g, s, frames, alpha=None, fast=False):
     import oracle
     t0 = time.perf_counter()
     for i in frames:
-        if w.mode == "blend" and alpha is not None:
+        if w.mode == "blend" and fast:
+            oracle.blend_frame_fast(g, s, w.window, i, w.patch, w.iters, seed=w.seed)
+        elif w.mode == "blend" and alpha is not None:
             oracle.blend_frame_balanced(g, s, w.window, i, w.patch, w.iters, alpha, seed=w.seed)
         elif w.mode == "blend":
             oracle.blend_frame(g, s, w.window, i, w.patch, w.iters, seed=w.seed)
@@ -209,10 +213,10 @@ def sample_frames(w: synth.Workload, n: int):
     return [mid + d for d in range(n)]
 
 
-def cpu_baseline(w: synth.Workload, g, s, n_frames: int, alpha=None):
+def cpu_baseline(w: synth.Workload, g, s, n_frames: int, alpha=None, fast=False):
     import oracle
     frames = sample_frames(w, n_frames)
-    secs = oracle_frame_seconds(w, g, s, frames, alpha)
+    secs = oracle_frame_seconds(w, g, s, frames, alpha, fast)
     return {"value": len(frames) / secs, "unit": "frames/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"{len(frames)} of {w.N} output frames ({frames}) of the same clip, each "
@@ -232,15 +236,20 @@ def run_reference(args):
                            seed=BATCH_SEED)
     else:
         w = synth.WORKLOADS["blend_512" if args.workload in ("balanced_512", "learned_512",
-                                                             "initnet_512") else args.workload]
+                                                             "initnet_512", "fast_512")
+                            else args.workload]
+        if args.window and w.mode == "blend":
+            import dataclasses
+            w = dataclasses.replace(w, window=args.window)
         g, s = make_inputs(w, w.seed)
     alpha = BALANCED_ALPHA if args.workload == "balanced_512" else None
+    fast = args.workload == "fast_512"
     frames = sample_frames(w, 1)
     for _ in range(args.warmup):
-        oracle_frame_seconds(w, g, s, frames, alpha)
+        oracle_frame_seconds(w, g, s, frames, alpha, fast)
     total = 0.0
     for _ in range(args.steps):
-        total += oracle_frame_seconds(w, g, s, frames, alpha)
+        total += oracle_frame_seconds(w, g, s, frames, alpha, fast)
     value = args.steps * len(frames) / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
@@ -280,13 +289,23 @@ def run_gpu(args):
     fbp.build()
     learned = args.workload == "learned_512"
     balanced = args.workload == "balanced_512"
-    w = synth.WORKLOADS["blend_512" if learned or balanced else args.workload]
+    fast = args.workload == "fast_512"
+    w = synth.WORKLOADS["blend_512" if learned or balanced or fast else args.workload]
+    if args.window and w.mode == "blend":
+        import dataclasses
+        w = dataclasses.replace(w, window=args.window)
     g, s = make_inputs(w, shard_seed(w.seed, rank))
     ctx = fbp.Context(local)
     params = fbp.Params.make(w.patch, w.iters, w.levels, 0, w.seed)
     if balanced:
         params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_BALANCED,
                                  alpha=BALANCED_ALPHA)
+    fast_info = None
+    if fast:
+        params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_FAST)
+        n_nnfs, n_entries, n_pieces = fbp.fb_fast_plan(w.N, w.window)
+        fast_info = {"nnfs": n_nnfs, "direct_nnfs": w.pairs(), "table_entries": n_entries,
+                     "query_pieces": n_pieces}
     learned_info = None
     if learned:
         # The learned initialiser: trained here, on the method's own NNFs of seeded clips
@@ -385,6 +404,20 @@ def run_gpu(args):
     ops = iter_ops_per_launch(w) if w.levels == 1 else None  # same per launch with learned init
     if ops and balanced:
         ops *= 2   # each candidate compares a guide patch and a style patch
+    if ops and fast:
+        ops = ops * fast_info["nnfs"] // w.pairs()   # the fast mode computes fewer NNFs
+    if fast:
+        # context: the direct window sum of the same clip and window, one untimed-by-the-
+        # contract measurement with CUDA events
+        direct = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed)
+        fbp.fb_blend_window(ctx, g_d, s_d, w.window, direct, out=out)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        fbp.fb_blend_window(ctx, g_d, s_d, w.window, direct, out=out)
+        b.record()
+        torch.cuda.synchronize()
+        fast_info["direct_ms_per_step"] = a.elapsed_time(b)
     roof = None
     if iter_n and ops:
         avg_s = iter_ms / iter_n / 1e3
@@ -403,7 +436,8 @@ def run_gpu(args):
                                if probe_per_clk else "derived"),
                 "avg_launch_ms": iter_ms / iter_n, "launches": iter_n,
                 "share_of_kernel_time": iter_ms / kernel_total_ms if kernel_total_ms else None,
-                "candidate_evals_per_s": (w.candidate_evals() if not learned else
+                "candidate_evals_per_s": (w.candidate_evals() * (fast_info["nnfs"] / w.pairs() if fast else 1)
+                                          if not learned else
                                           w.pairs() * w.H * w.W * (1 + args.learned_iters *
                                                                    (4 + w.random_search_radii())))
                 * args.steps * world / (total_ms / 1e3),
@@ -418,15 +452,18 @@ def run_gpu(args):
                                 f"initialiser (tcgen05) + {args.learned_iters} Alg. 1 iteration(s)"
                                 if learned else
                                 "balanced blend all-pairs 60x512x512 k5 w15 n6: Sec. 3.4 improved "
-                                f"loss, alpha {BALANCED_ALPHA}" if balanced else w.name),
+                                f"loss, alpha {BALANCED_ALPHA}" if balanced else
+                                f"fast-mode blend 60x512x512 k5 w{w.window} n6: Sec. 3.4 remapping / "
+                                "blending tables and interval queries (Algs. 3-5)" if fast else w.name),
                    "frames": w.N, "height": w.H, "width": w.W,
                    "patch": w.patch, "window": w.window,
                    "iters": w.iters if not learned else args.learned_iters, "levels": w.levels,
-                   "nnfs_per_step": w.pairs(),
+                   "nnfs_per_step": fast_info["nnfs"] if fast else w.pairs(),
                    "candidate_evals_per_step": (w.candidate_evals() if not learned else
                                                 w.pairs() * w.H * w.W * (1 + args.learned_iters *
                                                                          (4 + w.random_search_radii()))),
                    "learned_init": learned_info,
+                   "fast_mode": fast_info,
                    "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"{world} independent clip(s), one per GPU"},
         "roofline": roof,
@@ -437,7 +474,7 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, g, s, args.cpu_sample_frames,
-                                            BALANCED_ALPHA if balanced else None)
+                                            BALANCED_ALPHA if balanced else None, fast)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

@@ -83,6 +83,15 @@ typedef struct fb_params {
  * style S_j; levels must be 1, p->alpha <= 255, not with FB_FLAG_LEARNED_INIT.  The
  * energy that FB_FLAG_REPORT_ENERGY sums is then the improved loss. */
 #define FB_FLAG_BALANCED 0x4u
+/* FB_FLAG_FAST (fb_blend_window only): the fast mode of Sec. 3.4 -- the window sum of
+ * Eq. 2 from a remapping table (Alg. 3), its prefix sums (Alg. 4) and the interval query
+ * (Alg. 5) on the clip and on the reversed clip, joined by the split identity; O(N log N)
+ * NNFs instead of O(N M).  Each NNF is Alg. 1 with the pair tag of its (source, target)
+ * frames.  Results differ from the direct sum (remaps of remapped frames); sums are exact
+ * integers and each output value one double division rounded to float.  Not with
+ * FB_FLAG_BALANCED or FB_FLAG_LEARNED_INIT; all NNFs of the call are held at once
+ * (FB_ERR_UNSUPPORTED beyond the pair budget). */
+#define FB_FLAG_FAST 0x8u
 
 /* Create a context on CUDA device `device` (made current for the call).  The context
  * allocates scratch lazily and keeps it for reuse until fb_ctx_destroy. */
@@ -122,6 +131,7 @@ typedef enum fb_kernel_kind {
     FB_K_INITNET,       /* learned initialiser: network forward + initial fields  */
     FB_K_SHAT,          /* improved loss: remapped source style S^ of every pair  */
     FB_K_ENERGY,        /* improved loss: incumbent's loss against the new S^      */
+    FB_K_TABLE,         /* fast mode: blending-table entries                      */
     FB_K_COUNT
 } fb_kernel_kind;
 
@@ -251,6 +261,12 @@ typedef struct fb_clip_desc {
  * manifests.  Async on `stream`; do not call it while `stream` is being captured. */
 int fb_blend_batch(fb_ctx *ctx, const fb_clip_desc *clips, int n_clips, const fb_params *p,
                    uint32_t flags, void *stream);
+
+/* Host-only planning of the fast mode (FB_FLAG_FAST) for N frames and `window`: the
+ * number of distinct NNFs it computes, of blending-table entries it builds and of query
+ * pieces it remaps (the direct sum of Eq. 2 computes sum_i (window_i - 1) NNFs).  No CUDA
+ * calls; FB_ERR_ARG for N outside [1, 65535] or an even / non-positive window. */
+int fb_fast_plan(int N, int window, uint64_t *n_nnfs, uint64_t *n_entries, uint64_t *n_pieces);
 
 /* Host-only planning of a batch (no CUDA calls): number of NNFs, persistent-kernel work
  * items per iteration (32x8 tiles) and chunks under a pair budget of budget_bytes of

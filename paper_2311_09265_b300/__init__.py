@@ -25,7 +25,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a",
                     "fb_debug_candidates_considered", "fb_pair_tag",
                     "fb_nnf", "fb_nnf_balanced", "fb_remap", "fb_blend_window", "fb_interpolate",
-                    "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan",
+                    "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan", "fb_fast_plan",
                     "fb_ctx_batch_variant", "fb_ctx_set_pair_budget",
                     "fb_initnet_create", "fb_initnet_destroy", "fb_initnet_last_error",
                     "fb_initnet_param_count", "fb_initnet_get_params", "fb_initnet_set_params",
@@ -37,6 +37,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
 FB_FLAG_LEARNED_INIT = 0x1
 FB_FLAG_REPORT_ENERGY = 0x2
 FB_FLAG_BALANCED = 0x4
+FB_FLAG_FAST = 0x8
 
 FB_BATCH_NO_GRAPH = 0x1
 
@@ -47,7 +48,7 @@ def FB_BATCH_VARIANT(v: int) -> int:
 
 # fb_kernel_kind, in header order.
 KERNEL_KINDS = ("prep", "downsample", "style", "init", "iter", "unpack", "pack", "combine",
-                "initnet", "shat", "energy")
+                "initnet", "shat", "energy", "table")
 
 
 class Params(ctypes.Structure):
@@ -118,6 +119,7 @@ def lib() -> ctypes.CDLL:
         L.fb_nnf.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp, _vp, _vp]
         L.fb_nnf_balanced.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp,
                                       _vp, _vp, _vp]
+        L.fb_fast_plan.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.POINTER(ctypes.c_uint64)] * 3
         L.fb_remap.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
         L.fb_blend_window.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, P, _vp, _vp]
@@ -175,6 +177,15 @@ def lib() -> ctypes.CDLL:
             getattr(L, f).restype = ctypes.c_int
         _lib = L
     return _lib
+
+
+def fb_fast_plan(N: int, window: int):
+    """(distinct NNFs, blending-table entries, query pieces) of the fast mode (host only)."""
+    a, b, c = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    rc = lib().fb_fast_plan(N, window, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c))
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_fast_plan")
+    return int(a.value), int(b.value), int(c.value)
 
 
 def fb_debug_candidates_considered(reset: bool = False) -> int:

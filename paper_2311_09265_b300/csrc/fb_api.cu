@@ -8,6 +8,7 @@
 #include <cstring>
 #include <functional>
 #include <string>
+#include <map>
 #include <vector>
 
 #include "fb.h"
@@ -59,6 +60,8 @@ namespace {
 using fb::JobDesc;
 using fb::LevelGeom;
 using fb::PairDesc;
+using fb::FastEntry;
+using fb::FastJob;
 
 thread_local std::string g_null_ctx_err;
 
@@ -207,8 +210,10 @@ int check_params(fb_ctx* ctx, const fb_params* p, int H, int W) {
         return fail(ctx, FB_ERR_ARG, "levels must be in [1, 16], got %d", p->levels);
     if (p->r0 < 0 || p->r0 > (1 << 20))
         return fail(ctx, FB_ERR_ARG, "r0 must be in [0, 2^20], got %d", p->r0);
-    if (p->flags & ~(FB_FLAG_LEARNED_INIT | FB_FLAG_REPORT_ENERGY | FB_FLAG_BALANCED))
+    if (p->flags & ~(FB_FLAG_LEARNED_INIT | FB_FLAG_REPORT_ENERGY | FB_FLAG_BALANCED | FB_FLAG_FAST))
         return fail(ctx, FB_ERR_ARG, "unknown flags 0x%x", p->flags);
+    if ((p->flags & FB_FLAG_FAST) && (p->flags & (FB_FLAG_BALANCED | FB_FLAG_LEARNED_INIT)))
+        return fail(ctx, FB_ERR_ARG, "FB_FLAG_FAST does not combine with FB_FLAG_BALANCED or FB_FLAG_LEARNED_INIT");
     if (p->flags & FB_FLAG_BALANCED) {
         if (p->levels != 1) return fail(ctx, FB_ERR_ARG, "FB_FLAG_BALANCED requires levels == 1");
         if (p->alpha > 255) return fail(ctx, FB_ERR_ARG, "alpha must be in [0, 255], got %u", p->alpha);
@@ -537,6 +542,153 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
     return FB_OK;
 }
 
+// ---------------------------------------------------------------------------------
+// Fast mode of Sec. 3.4
+// ---------------------------------------------------------------------------------
+struct FastPlan {
+    std::vector<PairDesc> pairs;   // distinct NNFs (source frame -> target frame)
+    std::vector<FastEntry> entries;
+    std::vector<int32_t> src_pairs;
+    std::vector<FastJob> jobs;
+    std::vector<int2> pieces;
+};
+
+// Blending-table entries and queries of every output frame.  Positions t of the table
+// run over the clip (rev = 0) or the reversed clip (rev = 1, frame N - 1 - t).  Entry
+// (rev, j, L) sums the 2^L positions [j - 2^L + 1, j] remapped to position j; the query
+// for [l, r] walks t = r, r - 2^L, ... with the largest L whose low L bits of t are set
+// and whose entry stays in [l, r] (Alg. 5), each piece remapped to position r.
+void plan_fast(int N, int window, FastPlan& plan) {
+    const int M = (window - 1) / 2;
+    std::map<std::pair<int, int>, int> pair_of;
+    std::map<std::array<int, 3>, int> entry_of;
+    auto frame = [N](int rev, int t) { return rev ? N - 1 - t : t; };
+    auto get_pair = [&](int src, int tgt) {
+        auto it = pair_of.find({src, tgt});
+        if (it != pair_of.end()) return it->second;
+        const int id = static_cast<int>(plan.pairs.size());
+        plan.pairs.push_back(PairDesc{src, tgt, fb_pair_tag(src, tgt), src, 1u, {0, 0, 0}});
+        pair_of[{src, tgt}] = id;
+        return id;
+    };
+    auto get_entry = [&](int rev, int j, int L) {
+        const std::array<int, 3> key{rev, j, L};
+        auto it = entry_of.find(key);
+        if (it != entry_of.end()) return it->second;
+        FastEntry e{frame(rev, j), static_cast<int32_t>(plan.src_pairs.size()), 0, 0};
+        for (int a = j - (1 << L) + 1; a < j; ++a) plan.src_pairs.push_back(get_pair(frame(rev, a), frame(rev, j)));
+        e.n_src = static_cast<int32_t>(plan.src_pairs.size()) - e.first_src;
+        const int id = static_cast<int>(plan.entries.size());
+        plan.entries.push_back(e);
+        entry_of[key] = id;
+        return id;
+    };
+    for (int i = 0; i < N; ++i) {
+        const int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
+        FastJob job{i, static_cast<int32_t>(plan.pieces.size()), 0, hi - lo + 1};
+        const int spans[2][3] = {{0, lo, i}, {1, N - 1 - hi, N - 1 - i}};
+        for (const auto& sp : spans) {
+            const int rev = sp[0], l = sp[1], r = sp[2];
+            for (int t = r; t >= l;) {
+                int L = 0;
+                while (((t >> L) & 1) && t - (1 << (L + 1)) + 1 >= l) ++L;
+                const int e = get_entry(rev, t, L);
+                const int pr = t == r ? -1 : get_pair(frame(rev, t), frame(rev, r));
+                plan.pieces.push_back(make_int2(e, pr));
+                t -= 1 << L;
+            }
+        }
+        job.n_pieces = static_cast<int32_t>(plan.pieces.size()) - job.first_piece;
+        plan.jobs.push_back(job);
+    }
+}
+
+int run_fast_pipeline(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles, int N, int H, int W,
+                      const FastPlan& plan, const fb_params* p, float* out, cudaStream_t st) {
+    const int k = p->patch;
+    const Levels L = level_dims(H, W, p->levels);
+    const size_t npx0 = static_cast<size_t>(H) * W;
+    const Mem mg = classify(ctx, guides), ms = classify(ctx, styles), mo = classify(ctx, out);
+    if (mg == Mem::Invalid || ms == Mem::Invalid || mo == Mem::Invalid)
+        return fail(ctx, FB_ERR_ARG, "a device pointer belongs to another device");
+    if (!(mg == ms && ms == mo))
+        return fail(ctx, FB_ERR_ARG, "guides, styles and out must all be device or all host memory");
+    const bool staging = mg == Mem::Host;
+    const size_t n_pairs = plan.pairs.size(), n_entries = plan.entries.size();
+    if (n_pairs > static_cast<size_t>(kMaxChunkPairs) || n_pairs * npx0 * 16 > pair_budget(ctx) ||
+        n_entries > static_cast<size_t>(kMaxChunkPairs))
+        return fail(ctx, FB_ERR_UNSUPPORTED, "fast mode holds all %zu NNFs of the call at once; the pair budget does not",
+                    n_pairs);
+    const size_t fbytes = static_cast<size_t>(N) * npx0 * 3;
+
+    Buffers b;
+    FastEntry* d_entries = nullptr;
+    int32_t* d_src = nullptr;
+    FastJob* d_jobs = nullptr;
+    int2* d_pieces = nullptr;
+    uint4* d_table = nullptr;
+    auto layout = [&](Carver& c) {
+        carve(c, b, L, k, N, N, n_pairs, n_pairs > 0 ? n_pairs : 1, 0, staging, fbytes, fbytes, fbytes);
+        d_table = c.take<uint4>(n_entries * npx0);
+        d_entries = c.take<FastEntry>(n_entries);
+        d_src = c.take<int32_t>(plan.src_pairs.size() > 0 ? plan.src_pairs.size() : 1);
+        d_jobs = c.take<FastJob>(plan.jobs.size());
+        d_pieces = c.take<int2>(plan.pieces.size());
+    };
+    Carver measure(nullptr);
+    layout(measure);
+    int rc = ensure_arena(ctx, measure.off);
+    if (rc) return rc;
+    Carver cv(ctx->arena);
+    layout(cv);
+    rc = upload_tables(ctx, plan.pairs, {}, b, st);
+    if (rc) return rc;
+    FB_CUDA(ctx, cudaMemcpyAsync(d_entries, plan.entries.data(), n_entries * sizeof(FastEntry),
+                                 cudaMemcpyHostToDevice, st));
+    if (!plan.src_pairs.empty())
+        FB_CUDA(ctx, cudaMemcpyAsync(d_src, plan.src_pairs.data(), plan.src_pairs.size() * sizeof(int32_t),
+                                     cudaMemcpyHostToDevice, st));
+    FB_CUDA(ctx, cudaMemcpyAsync(d_jobs, plan.jobs.data(), plan.jobs.size() * sizeof(FastJob),
+                                 cudaMemcpyHostToDevice, st));
+    FB_CUDA(ctx, cudaMemcpyAsync(d_pieces, plan.pieces.data(), plan.pieces.size() * sizeof(int2),
+                                 cudaMemcpyHostToDevice, st));
+    const uint8_t* g_dev = guides;
+    const uint8_t* s_dev = styles;
+    float* o_dev = out;
+    if (staging) {
+        FB_CUDA(ctx, cudaMemcpyAsync(b.in_guides, guides, fbytes, cudaMemcpyHostToDevice, st));
+        FB_CUDA(ctx, cudaMemcpyAsync(b.in_styles, styles, fbytes, cudaMemcpyHostToDevice, st));
+        g_dev = b.in_guides;
+        s_dev = b.in_styles;
+        o_dev = b.in_out;
+    }
+    rc = prep_guides(ctx, b, L, k, g_dev, N, 0, st);
+    if (rc) return rc;
+    FB_LAUNCH(ctx, st, FB_K_STYLE, fb::launch_style_rgbx(s_dev, static_cast<size_t>(N) * npx0, b.styles, st));
+    if (p->flags & FB_FLAG_REPORT_ENERGY) {
+        FB_CUDA(ctx, cudaMemsetAsync(ctx->energy, 0, sizeof(double), st));
+        ctx->energy_count = 0;
+    }
+    uint32_t *F = b.FA, *E = b.EA;
+    if (n_pairs > 0) {
+        rc = run_nnf(ctx, b, L, p, 0, static_cast<int>(n_pairs), nullptr, st, &F, &E);
+        if (rc) return rc;
+        if (p->flags & FB_FLAG_REPORT_ENERGY) {
+            FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_energy_sum(E, n_pairs * npx0, ctx->energy, st));
+            ctx->energy_count += static_cast<uint64_t>(n_pairs) * npx0;
+        }
+    }
+    FB_LAUNCH(ctx, st, FB_K_TABLE, fb::launch_fast_table(k, d_entries, static_cast<int>(n_entries), d_src, b.pairs,
+                                                         F, b.styles, H, W, d_table, st));
+    FB_LAUNCH(ctx, st, FB_K_COMBINE, fb::launch_fast_combine(k, d_jobs, static_cast<int>(plan.jobs.size()),
+                                                             d_pieces, F, d_table, b.styles, H, W, o_dev, st));
+    if (staging) {
+        FB_CUDA(ctx, cudaMemcpyAsync(out, o_dev, fbytes * sizeof(float), cudaMemcpyDeviceToHost, st));
+        FB_CUDA(ctx, cudaStreamSynchronize(st));
+    }
+    return FB_OK;
+}
+
 }  // namespace
 
 namespace fb {
@@ -565,8 +717,8 @@ int check_clips(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     if (!clips || n < 1) return fail(ctx, FB_ERR_ARG, "clips must be a non-empty host array");
     if (!p) return fail(ctx, FB_ERR_ARG, "params is NULL");
     if (p->levels != 1) return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use levels == 1");
-    if (p->flags & FB_FLAG_BALANCED)
-        return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use the plain loss");
+    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST))
+        return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use the plain loss and the direct sum");
     for (int c = 0; c < n; ++c) {
         const fb_clip_desc& d = clips[c];
         fb_params q = *p;
@@ -976,6 +1128,17 @@ void count_launches(fb_ctx* ctx, int n) {
 }
 }  // namespace fb
 
+extern "C" int fb_fast_plan(int N, int window, uint64_t* n_nnfs, uint64_t* n_entries,
+                            uint64_t* n_pieces) {
+    if (N < 1 || N > 65535 || window < 1 || (window & 1) == 0) return FB_ERR_ARG;
+    FastPlan plan;
+    plan_fast(N, window, plan);
+    if (n_nnfs) *n_nnfs = plan.pairs.size();
+    if (n_entries) *n_entries = plan.entries.size();
+    if (n_pieces) *n_pieces = plan.pieces.size();
+    return FB_OK;
+}
+
 extern "C" int fb_ctx_set_initnet(fb_ctx* ctx, fb_initnet* net) {
     if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
     ctx->init_net = net;
@@ -1214,6 +1377,7 @@ int fb_nnf(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int 
         return fail(ctx, FB_ERR_ARG, "an initial NNF requires levels == 1");
     if (p->flags & FB_FLAG_BALANCED)
         return fail(ctx, FB_ERR_ARG, "the improved loss needs the source style: use fb_nnf_balanced");
+    if (p->flags & FB_FLAG_FAST) return fail(ctx, FB_ERR_ARG, "FB_FLAG_FAST applies to fb_blend_window only");
     DeviceGuard dg(ctx->device);
     for (const void* q : {static_cast<const void*>(src_guide), static_cast<const void*>(tgt_guide),
                           static_cast<const void*>(nnf_out), static_cast<const void*>(init_nnf),
@@ -1349,6 +1513,15 @@ int fb_blend_window(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles, i
     if (!guides || !styles || !out)
         return fail(ctx, FB_ERR_ARG, "guides, styles and out must be non-NULL");
     const int k = p->patch, M = (window - 1) / 2;
+    if (p->flags & FB_FLAG_FAST) {
+        const uint64_t k4 = static_cast<uint64_t>(k) * k * k * k;
+        if (k4 * 255u * static_cast<uint64_t>(window) >= (1ull << 32))
+            return fail(ctx, FB_ERR_ARG, "fast mode: window %d with patch %d overflows the exact sums", window, k);
+        FastPlan plan;
+        plan_fast(N, window, plan);
+        DeviceGuard dg(ctx->device);
+        return run_fast_pipeline(ctx, guides, styles, N, H, W, plan, p, out, static_cast<cudaStream_t>(stream));
+    }
 
     // Eq. 2: one job per output frame; its pairs are (j -> i) for j in the truncated
     // window, j != i, in increasing j.
@@ -1373,8 +1546,8 @@ int fb_interpolate(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, cons
     ctx->err.clear();
     int rc = check_params(ctx, p, H, W);
     if (rc) return rc;
-    if (p->flags & FB_FLAG_BALANCED)
-        return fail(ctx, FB_ERR_ARG, "FB_FLAG_BALANCED applies to fb_blend_window only");
+    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST))
+        return fail(ctx, FB_ERR_ARG, "FB_FLAG_BALANCED and FB_FLAG_FAST apply to fb_blend_window only");
     if (N < 1 || N > 65535) return fail(ctx, FB_ERR_ARG, "N must be in [1, 65535], got %d", N);
     if (!guides || !key_idx || !key_styles || !out)
         return fail(ctx, FB_ERR_ARG, "guides, key_idx, key_styles and out must be non-NULL");

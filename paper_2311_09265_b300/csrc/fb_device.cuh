@@ -470,6 +470,38 @@ __device__ __forceinline__ void remap_votes(const uint32_t* __restrict__ Fq,
     }
 }
 
+// Alg. 2 vote sums of a fast-mode table entry (three uint32 sums per 16-byte pixel).
+template <int K>
+__device__ __forceinline__ void remap_votes_u4(const uint32_t* __restrict__ Fq,
+                                               const uint4* __restrict__ T, int H, int W, int r,
+                                               int c, uint32_t& v0, uint32_t& v1, uint32_t& v2) {
+    constexpr int P = K / 2;
+    v0 = v1 = v2 = 0;
+#pragma unroll
+    for (int a = -P; a <= P; ++a) {
+        const int qr = clampi(r + a, 0, H - 1);
+#pragma unroll
+        for (int b = -P; b <= P; ++b) {
+            const int qc = clampi(c + b, 0, W - 1);
+            const uint32_t f = __ldg(Fq + static_cast<size_t>(qr) * W + qc);
+            const int sr = clampi(row_of(f) - (qr - r), 0, H - 1);
+            const int sc = clampi(col_of(f) - (qc - c), 0, W - 1);
+            const uint4 s = __ldg(T + static_cast<size_t>(sr) * W + sc);
+            v0 += s.x;
+            v1 += s.y;
+            v2 += s.z;
+        }
+    }
+}
+
+// Fast-mode output: num / den per channel, one IEEE double division rounded once to float.
+__device__ __forceinline__ void write_output_d(float* __restrict__ o, uint32_t a0, uint32_t a1,
+                                               uint32_t a2, double den) {
+    o[0] = __double2float_rn(__ddiv_rn(__uint2double_rn(a0), den));
+    o[1] = __double2float_rn(__ddiv_rn(__uint2double_rn(a1), den));
+    o[2] = __double2float_rn(__ddiv_rn(__uint2double_rn(a2), den));
+}
+
 // Output value of one pixel: num / den per channel with one IEEE division.
 __device__ __forceinline__ void write_output(float* __restrict__ o, uint32_t a0, uint32_t a1,
                                              uint32_t a2, uint32_t den_u) {

@@ -77,6 +77,24 @@ cudaError_t launch_nnf_iter(int k, const PairDesc* pairs, int pair0, int n_pairs
 cudaError_t launch_nnf_unpack(const uint32_t* F, const uint32_t* E, size_t npx, int32_t* nnf_out,
                               uint32_t* err_out, cudaStream_t st);
 cudaError_t launch_nnf_pack(const int32_t* nnf, int H, int W, uint32_t* F, cudaStream_t st);
+// Fast mode of Sec. 3.4 (Algs. 3-5).  A blending-table entry: the exact sum
+// k^2 S_frame + the Alg. 2 votes of its sources, each source one NNF pair (index into the
+// pair table; the pair's style is the source frame), stored as 16 bytes per pixel.
+struct FastEntry {
+    int32_t frame, first_src, n_src, pad;
+};
+// An output frame: the sum of its pieces (entry, NNF pair to the frame or -1 for the
+// identity), minus k^4 S_frame, over 255 k^4 count (the frames in its window).
+struct FastJob {
+    int32_t frame, first_piece, n_pieces, count;
+};
+cudaError_t launch_fast_table(int k, const FastEntry* entries, int n_entries, const int32_t* src_pairs,
+                              const PairDesc* pairs, const uint32_t* F, const uint32_t* styles, int H,
+                              int W, uint4* out, cudaStream_t st);
+cudaError_t launch_fast_combine(int k, const FastJob* jobs, int n_jobs, const int2* pieces,
+                                const uint32_t* F, const uint4* entries, const uint32_t* styles, int H,
+                                int W, float* out, cudaStream_t st);
+
 // Improved loss of Sec. 3.4: S^ images of a chunk's pairs (n_pairs x H x W x 3 bytes,
 // from the fields F and the RGBX styles), the loss of the current fields against their
 // S^ row patches (shat_rp: n_pairs frames; srp: the source styles' row patches), and the

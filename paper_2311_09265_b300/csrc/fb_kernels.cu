@@ -281,6 +281,73 @@ __global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
                               En + static_cast<size_t>(pl) * npx);
 }
 
+// ---------------------------------------------------------------------------------
+// Fast mode of Sec. 3.4: blending-table entries (Algs. 3-4) and the interval queries of
+// the output frames (Alg. 5 + the split identity), exact integer sums.
+// ---------------------------------------------------------------------------------
+template <int K>
+__global__ void __launch_bounds__(TILE_THREADS)
+    fast_table_kernel(const FastEntry* __restrict__ entries, const int32_t* __restrict__ src_pairs,
+                      const PairDesc* __restrict__ pairs, const uint32_t* __restrict__ F,
+                      const uint32_t* __restrict__ styles, int H, int W, uint4* __restrict__ out) {
+    const TileCoord tc = tile_coord(W);
+    if (tc.r >= H || tc.c >= W) return;
+    const FastEntry e = entries[blockIdx.y];
+    const size_t npx = static_cast<size_t>(H) * W;
+    const size_t x = static_cast<size_t>(tc.r) * W + tc.c;
+    const uint32_t s = __ldg(styles + static_cast<size_t>(e.frame) * npx + x);
+    constexpr uint32_t kk = static_cast<uint32_t>(K * K);
+    uint32_t a0 = kk * (s & 0xFFu), a1 = kk * ((s >> 8) & 0xFFu), a2 = kk * ((s >> 16) & 0xFFu);
+    for (int q = 0; q < e.n_src; ++q) {
+        const int p = src_pairs[e.first_src + q];
+        const PairDesc pd = pairs[p];
+        uint32_t v0, v1, v2;
+        remap_votes<K>(F + static_cast<size_t>(p) * npx, styles + static_cast<size_t>(pd.style) * npx, H,
+                       W, tc.r, tc.c, v0, v1, v2);
+        a0 += v0;
+        a1 += v1;
+        a2 += v2;
+    }
+    out[static_cast<size_t>(blockIdx.y) * npx + x] = make_uint4(a0, a1, a2, 0u);
+}
+
+template <int K>
+__global__ void __launch_bounds__(TILE_THREADS)
+    fast_combine_kernel(const FastJob* __restrict__ jobs, const int2* __restrict__ pieces,
+                        const uint32_t* __restrict__ F, const uint4* __restrict__ entries,
+                        const uint32_t* __restrict__ styles, int H, int W, float* __restrict__ out) {
+    const TileCoord tc = tile_coord(W);
+    if (tc.r >= H || tc.c >= W) return;
+    const FastJob job = jobs[blockIdx.y];
+    const size_t npx = static_cast<size_t>(H) * W;
+    const size_t x = static_cast<size_t>(tc.r) * W + tc.c;
+    constexpr uint32_t kk = static_cast<uint32_t>(K * K);
+    uint32_t a0 = 0, a1 = 0, a2 = 0;
+    for (int q = 0; q < job.n_pieces; ++q) {
+        const int2 pc = pieces[job.first_piece + q];
+        const uint4* T = entries + static_cast<size_t>(pc.x) * npx;
+        if (pc.y < 0) {  // the piece ends at the output frame: identity remap
+            const uint4 t = __ldg(T + x);
+            a0 += kk * t.x;
+            a1 += kk * t.y;
+            a2 += kk * t.z;
+        } else {
+            uint32_t v0, v1, v2;
+            remap_votes_u4<K>(F + static_cast<size_t>(pc.y) * npx, T, H, W, tc.r, tc.c, v0, v1, v2);
+            a0 += v0;
+            a1 += v1;
+            a2 += v2;
+        }
+    }
+    const uint32_t s = __ldg(styles + static_cast<size_t>(job.frame) * npx + x);
+    constexpr uint32_t k4 = kk * kk;  // S_frame is in both the left and the right query
+    a0 -= k4 * (s & 0xFFu);
+    a1 -= k4 * ((s >> 8) & 0xFFu);
+    a2 -= k4 * ((s >> 16) & 0xFFu);
+    const double den = 255.0 * static_cast<double>(k4) * static_cast<double>(job.count);
+    write_output_d(out + (static_cast<size_t>(job.frame) * npx + x) * 3, a0, a1, a2, den);
+}
+
 __global__ void __launch_bounds__(256) nnf_unpack_kernel(const uint32_t* __restrict__ F,
                                                          const uint32_t* __restrict__ E,
                                                          size_t npx, int32_t* __restrict__ nnf,
@@ -469,6 +536,28 @@ cudaError_t launch_nnf_iter_balanced(int k, const PairDesc* pairs, int pair0, in
                          pairs, pair0, g.H, g.W, g.rp, srp, shat_rp, alpha, r0,
                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), ctr_word,
                          Fp, Fn, En)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fast_table(int k, const FastEntry* entries, int n_entries, const int32_t* src_pairs,
+                              const PairDesc* pairs, const uint32_t* F, const uint32_t* styles, int H,
+                              int W, uint4* out, cudaStream_t st) {
+    if (n_entries <= 0) return cudaSuccess;
+    const dim3 grid = tile_grid(H, W, n_entries);
+    const dim3 block(TILE_W, TILE_H);
+    FB_DISPATCH_K(k, (fast_table_kernel<KK><<<grid, block, 0, st>>>(entries, src_pairs, pairs, F, styles, H,
+                                                                   W, out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fast_combine(int k, const FastJob* jobs, int n_jobs, const int2* pieces,
+                                const uint32_t* F, const uint4* entries, const uint32_t* styles, int H,
+                                int W, float* out, cudaStream_t st) {
+    if (n_jobs <= 0) return cudaSuccess;
+    const dim3 grid = tile_grid(H, W, n_jobs);
+    const dim3 block(TILE_W, TILE_H);
+    FB_DISPATCH_K(k, (fast_combine_kernel<KK><<<grid, block, 0, st>>>(jobs, pieces, F, entries, styles, H, W,
+                                                                     out)));
     return cudaGetLastError();
 }
 
