@@ -118,7 +118,8 @@ def aggregate(n_frames_per_rank: int, steps: int, world: int, max_total_ms: floa
 
 def make_inputs(w: synth.Workload, seed: int):
     if seed == w.seed:
-        return synth.make_clip(next(k for k, v in synth.WORKLOADS.items() if v is w))
+        # the named workload's own clip (a window override keeps the clip)
+        return synth.make_clip(next(k for k, v in synth.WORKLOADS.items() if v.name == w.name))
     if w.motion == "shift":
         g, _ = synth.shift_clip(w.N, w.H, w.W, seed)
         s = synth.colour_matrix_styles(g, seed)

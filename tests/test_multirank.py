@@ -82,3 +82,11 @@ def test_reference_arm_under_torchrun_prints_one_line():
     d = json.loads(lines[0])
     assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and d["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_window_override_keeps_the_named_clip():
+    import dataclasses
+    w = synth.WORKLOADS["blend_tiny"]
+    g0, s0 = bench.make_inputs(w, w.seed)
+    g1, s1 = bench.make_inputs(dataclasses.replace(w, window=5), w.seed)
+    assert np.array_equal(g0, g1) and np.array_equal(s0, s1)
