@@ -95,6 +95,14 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
                                                   _f32p]
         L.fbref_blend_window_balanced.restype = ctypes.c_int
+        L.fbref_blend_frame_accurate.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int,
+                                                 ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
+                                                 ctypes.c_int, _f32p, _u8p, _i32p]
+        L.fbref_blend_frame_accurate.restype = ctypes.c_int
+        L.fbref_blend_window_accurate.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
+                                                  _f32p]
+        L.fbref_blend_window_accurate.restype = ctypes.c_int
         L.fbref_blend_frame_fast.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                              ctypes.c_int, _P, ctypes.c_int, _f32p]
         L.fbref_blend_frame_fast.restype = ctypes.c_int
@@ -376,4 +384,40 @@ def blend_window_fast(guides, styles, window: int, patch: int, iters: int, seed:
                                        ctypes.byref(p), _ptr(out, _f32p))
     if rc != 0:
         raise ValueError("fbref_blend_window_fast: bad arguments")
+    return out
+
+
+# ----------------------------------------------------------------------------------
+# Sec. 3.4 quality improvement ("accurate mode")
+# ----------------------------------------------------------------------------------
+def blend_frame_accurate(guides, styles, window: int, i: int, patch: int, iters: int, alpha: int,
+                         seed: int = 0):
+    """Output frame i, the mean remapped frame Tbar_i of the last iteration and the final
+    fields of the pairs (j -> i), j ascending: (out, tbar, F (pairs, H, W, 2))."""
+    g, s = _u8(guides), _u8(styles)
+    N, H, W = g.shape[:3]
+    M = (window - 1) // 2
+    n_pairs = min(N - 1, i + M) - max(0, i - M)
+    out = np.zeros((H, W, 3), np.float32)
+    tbar = np.zeros((H, W, 3), np.uint8)
+    F = np.zeros((max(n_pairs, 1), H, W, 2), np.int32)
+    p = params(patch, iters, 1, 0, seed)
+    rc = lib().fbref_blend_frame_accurate(_ptr(g, _u8p), _ptr(s, _u8p), N, H, W, window,
+                                          ctypes.byref(p), alpha, i, _ptr(out, _f32p),
+                                          _ptr(tbar, _u8p), _ptr(F, _i32p))
+    if rc != 0:
+        raise ValueError("fbref_blend_frame_accurate: bad arguments")
+    return out, tbar, F[:n_pairs]
+
+
+def blend_window_accurate(guides, styles, window: int, patch: int, iters: int, alpha: int,
+                          seed: int = 0):
+    g, s = _u8(guides), _u8(styles)
+    N, H, W = g.shape[:3]
+    out = np.zeros((N, H, W, 3), np.float32)
+    p = params(patch, iters, 1, 0, seed)
+    rc = lib().fbref_blend_window_accurate(_ptr(g, _u8p), _ptr(s, _u8p), N, H, W, window,
+                                           ctypes.byref(p), alpha, _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_blend_window_accurate: bad arguments")
     return out

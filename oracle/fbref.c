@@ -775,3 +775,124 @@ int fbref_blend_window_fast(const uint8_t *guides, const uint8_t *styles, int N,
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Sec. 3.4, quality improvement ("accurate mode"), for output frame i: the NNFs of  */
+/* all pairs (j -> i) of the truncated window are computed together.  At the        */
+/* beginning of every iteration the mean remapped frame                              */
+/*   Tbar_i = (k^2 S_i + sum_j V(S_j through F_j)) / (k^2 c_i)    (rounded half up)    */
+/* is refreshed from the current fields and every pair's incumbent is re-evaluated    */
+/* under L_j(x) = alpha ||G_j[F_j(x)] - G_i[x]||^2 + ||S_j[F_j(x)] - Tbar_i[x]||^2;    */
+/* then each pair takes one Jacobi step (same order, streams, strict acceptance as    */
+/* fbref_nnf).  The output is Eq. 2 of the final fields.  One level.                  */
+/* ------------------------------------------------------------------------------ */
+int fbref_blend_frame_accurate(const uint8_t *guides, const uint8_t *styles, int N, int H,
+                               int W, int window, const fbref_params *p, uint32_t alpha, int i,
+                               float *out, uint8_t *tbar_out, int32_t *nnf_out)
+{
+    if (!params_ok(p, H, W) || p->levels != 1 || alpha > 255 || N < 1 || N > 65535 ||
+        window < 1 || (window & 1) == 0 || i < 0 || i >= N)
+        return -1;
+    const int k = p->patch, M = (window - 1) / 2, h = H, w = W;
+    size_t npx = (size_t)H * W, fsz = npx * 3;
+    int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
+    const int c_i = hi - lo + 1, np = c_i - 1;
+    const uint8_t *Gi = guides + (size_t)i * fsz, *Si = styles + (size_t)i * fsz;
+    int32_t *F = (int32_t *)malloc((size_t)(np > 0 ? np : 1) * npx * 2 * sizeof(int32_t));
+    int32_t *Fn = (int32_t *)malloc((size_t)(np > 0 ? np : 1) * npx * 2 * sizeof(int32_t));
+    uint32_t *E = (uint32_t *)malloc((size_t)(np > 0 ? np : 1) * npx * sizeof(uint32_t));
+    uint32_t *En = (uint32_t *)malloc((size_t)(np > 0 ? np : 1) * npx * sizeof(uint32_t));
+    uint32_t *acc = (uint32_t *)malloc(fsz * sizeof(uint32_t));
+    uint32_t *V = (uint32_t *)malloc(fsz * sizeof(uint32_t));
+    uint8_t *tbar = (uint8_t *)malloc(fsz);
+    int js[65535];
+    int q = 0;
+    for (int j = lo; j <= hi; ++j)
+        if (j != i) js[q++] = j;
+    for (int m = 0; m < np; ++m)
+        for (int r = 0; r < h; ++r)
+            for (int c = 0; c < w; ++c) {
+                size_t x = (size_t)r * w + c;
+                random_match(p->seed, (uint32_t)x, fbref_pair_tag(js[m], i), 0, h, w,
+                             &F[((size_t)m * npx + x) * 2], &F[((size_t)m * npx + x) * 2 + 1]);
+            }
+    const int r0 = p->r0 > 0 ? p->r0 : (h > w ? h : w);
+    static const int dirs[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    const uint32_t kk = (uint32_t)(k * k), den_t = kk * (uint32_t)c_i;
+    for (int it = 0; it < p->iters; ++it) {
+        /* the beginning of the iteration: Tbar_i from the current fields */
+        for (size_t t = 0; t < fsz; ++t) acc[t] = kk * Si[t];
+        for (int m = 0; m < np; ++m) {
+            fbref_remap_sum(styles + (size_t)js[m] * fsz, F + (size_t)m * npx * 2, h, w, k, V);
+            for (size_t t = 0; t < fsz; ++t) acc[t] += V[t];
+        }
+        for (size_t t = 0; t < fsz; ++t) tbar[t] = (uint8_t)((acc[t] + den_t / 2) / den_t);
+        for (int m = 0; m < np; ++m) {
+            const uint8_t *Gj = guides + (size_t)js[m] * fsz, *Sj = styles + (size_t)js[m] * fsz;
+            const int32_t *Fm = F + (size_t)m * npx * 2;
+            int32_t *Fnm = Fn + (size_t)m * npx * 2;
+            uint32_t *Em = E + (size_t)m * npx, *Enm = En + (size_t)m * npx;
+            const uint32_t tag = fbref_pair_tag(js[m], i);
+#pragma omp parallel for schedule(static)
+            for (int r = 0; r < h; ++r)
+                for (int c = 0; c < w; ++c) {
+                    size_t x = (size_t)r * w + c;
+                    Em[x] = balanced_loss(Gj, Gi, Sj, tbar, h, w, k, alpha, Fm[2 * x], Fm[2 * x + 1], r, c);
+                }
+#pragma omp parallel for schedule(static)
+            for (int r = 0; r < h; ++r) {
+                for (int c = 0; c < w; ++c) {
+                    size_t x = (size_t)r * w + c;
+                    int32_t br = Fm[2 * x], bc = Fm[2 * x + 1];
+                    uint32_t be = Em[x];
+                    for (int d = 0; d < 4; ++d) {
+                        int nr = r + dirs[d][0], nc = c + dirs[d][1];
+                        if (nr < 0 || nr >= h || nc < 0 || nc >= w) continue;
+                        size_t n = (size_t)nr * w + nc;
+                        int cr = clampi(Fm[2 * n] - dirs[d][0], 0, h - 1);
+                        int cc = clampi(Fm[2 * n + 1] - dirs[d][1], 0, w - 1);
+                        uint32_t e = balanced_loss(Gj, Gi, Sj, tbar, h, w, k, alpha, cr, cc, r, c);
+                        if (e < be) { be = e; br = cr; bc = cc; }
+                    }
+                    for (int t = 0; (r0 >> t) >= 1; ++t) {
+                        int rad = r0 >> t;
+                        int32_t dr, dc;
+                        fbref_rs_offset(p->seed, (uint32_t)x, tag, 0, it, t, rad, &dr, &dc);
+                        int cr = clampi(br + dr, 0, h - 1);
+                        int cc = clampi(bc + dc, 0, w - 1);
+                        uint32_t e = balanced_loss(Gj, Gi, Sj, tbar, h, w, k, alpha, cr, cc, r, c);
+                        if (e < be) { be = e; br = cr; bc = cc; }
+                    }
+                    Fnm[2 * x] = br; Fnm[2 * x + 1] = bc; Enm[x] = be;
+                }
+            }
+        }
+        int32_t *tf = F; F = Fn; Fn = tf;
+        uint32_t *te = E; E = En; En = te;
+    }
+    /* Eq. 2 of the final fields */
+    for (size_t t = 0; t < fsz; ++t) acc[t] = kk * Si[t];
+    for (int m = 0; m < np; ++m) {
+        fbref_remap_sum(styles + (size_t)js[m] * fsz, F + (size_t)m * npx * 2, h, w, k, V);
+        for (size_t t = 0; t < fsz; ++t) acc[t] += V[t];
+    }
+    float den = (float)(255 * k * k * c_i);
+    for (size_t t = 0; t < fsz; ++t) out[t] = (float)acc[t] / den;
+    if (tbar_out && p->iters > 0) memcpy(tbar_out, tbar, fsz);   /* Tbar of the last iteration */
+    if (nnf_out && np > 0) memcpy(nnf_out, F, (size_t)np * npx * 2 * sizeof(int32_t));  /* j ascending */
+    free(F); free(Fn); free(E); free(En); free(acc); free(V); free(tbar);
+    return 0;
+}
+
+int fbref_blend_window_accurate(const uint8_t *guides, const uint8_t *styles, int N, int H,
+                                int W, int window, const fbref_params *p, uint32_t alpha,
+                                float *out)
+{
+    size_t fsz = (size_t)H * W * 3;
+    for (int i = 0; i < N; ++i) {
+        int rc = fbref_blend_frame_accurate(guides, styles, N, H, W, window, p, alpha, i,
+                                            out + (size_t)i * fsz, NULL, NULL);
+        if (rc) return rc;
+    }
+    return 0;
+}

@@ -94,6 +94,14 @@ int fbref_interpolate_frame(const uint8_t *guides, int N, int H, int W, const in
  * Philox counter. */
 uint32_t fbref_pair_tag(int j, int i);
 
+/* Sec. 3.4 quality improvement ("accurate mode"), one level: see fbref.c. */
+int fbref_blend_frame_accurate(const uint8_t *guides, const uint8_t *styles, int N, int H,
+                               int W, int window, const fbref_params *p, uint32_t alpha, int i,
+                               float *out, uint8_t *tbar_out, int32_t *nnf_out);
+int fbref_blend_window_accurate(const uint8_t *guides, const uint8_t *styles, int N, int H,
+                                int W, int window, const fbref_params *p, uint32_t alpha,
+                                float *out);
+
 /* Sec. 3.4 fast mode (Algs. 3-5 and the split identity): see fbref.c. */
 int fbref_blend_frame_fast(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
                            int window, const fbref_params *p, int i, float *out);

@@ -4,7 +4,8 @@ Each mutant below is a one-place edit of oracle/fbref.c of the kind a restatemen
 the paper can get wrong (a dropped term, a wrong sign, an index of the wrong axis, a
 non-strict acceptance, an off-by-one bound or constant).  It is compiled into a
 temporary directory and the pin suites (tests/test_oracle_pins.py,
-tests/test_oracle_balanced.py, tests/test_oracle_fast.py) are run against it:
+tests/test_oracle_balanced.py, tests/test_oracle_fast.py, tests/test_oracle_accurate.py)
+are run against it:
 every mutant must make at least one pin fail.  The oracle's own source is not touched.
 """
 import os
@@ -40,7 +41,7 @@ MUTANTS = {
                                    "if (e <= be) { be = e; br = cr; bc = cc; }", 1),
     "random_search_skips_largest_radius": ("int rad = r0 >> t;", "int rad = r0 >> (t + 1);", 0),
     "random_search_centred_on_snapshot": ("int cr = clampi(br + dr, 0, h - 1);\n                        int cc = clampi(bc + dc, 0, w - 1);",
-                                          "int cr = clampi(F[2 * x] + dr, 0, h - 1);\n                        int cc = clampi(F[2 * x + 1] + dc, 0, w - 1);", None),
+                                          "int cr = clampi(F[2 * x] + dr, 0, h - 1);\n                        int cc = clampi(F[2 * x + 1] + dc, 0, w - 1);", 0),
     "upsample_drops_parity": ("Fn[2 * x] = clampi(2 * F[2 * xc] + (r & 1), 0, h - 1);",
                               "Fn[2 * x] = clampi(2 * F[2 * xc], 0, h - 1);", None),
     "remap_offset_sign": ("int sr = clampi(fr - (qr - r), 0, H - 1);", "int sr = clampi(fr + (qr - r), 0, H - 1);", 0),
@@ -62,6 +63,12 @@ MUTANTS = {
     "balanced_propagation_row_offset_sign": ("int cr = clampi(F[2 * n] - dirs[d][0], 0, h - 1);",
                                              "int cr = clampi(F[2 * n] + dirs[d][0], 0, h - 1);", 1),
     "balanced_random_search_skips_largest_radius": ("int rad = r0 >> t;", "int rad = r0 >> (t + 1);", 1),
+    "accurate_tbar_rounds_down": ("tbar[t] = (uint8_t)((acc[t] + den_t / 2) / den_t);", "tbar[t] = (uint8_t)(acc[t] / den_t);", None),
+    "accurate_tbar_without_self_term": ("        for (size_t t = 0; t < fsz; ++t) acc[t] = kk * Si[t];\n        for (int m = 0; m < np; ++m) {\n            fbref_remap_sum",
+                                        "        for (size_t t = 0; t < fsz; ++t) acc[t] = 0;\n        for (int m = 0; m < np; ++m) {\n            fbref_remap_sum", None),
+    "accurate_propagation_row_offset_sign": ("int cr = clampi(Fm[2 * n] - dirs[d][0], 0, h - 1);", "int cr = clampi(Fm[2 * n] + dirs[d][0], 0, h - 1);", None),
+    "accurate_random_search_skips_largest_radius": ("int rad = r0 >> t;", "int rad = r0 >> (t + 1);", 2),
+    "accurate_pair_stream_reversed": ("const uint32_t tag = fbref_pair_tag(js[m], i);", "const uint32_t tag = fbref_pair_tag(i, js[m]);", None),
     "fast_table_remap_offset_sign": ("int sr = clampi(fr - (qr - r), 0, H - 1);", "int sr = clampi(fr + (qr - r), 0, H - 1);", 1),
     "fast_walk_steps_twice_the_piece": ("        i -= 1 << L;", "        i -= 2 << L;", None),
     "fast_identity_piece_unweighted": ("acc[t] += (uint32_t)(k * k) * B[t];  /* identity remap */",
@@ -106,9 +113,13 @@ def run_mutant(name: str, workdir: str):
     old, new, which = MUTANTS[name]
     with open(SRC) as f:
         src = f.read()
+    try:
+        text = mutate(src, old, new, which)
+    except AssertionError as e:          # a mutation site that is missing or ambiguous
+        return -1, str(e)
     mutant_c = os.path.join(workdir, f"{name}.c")
     with open(mutant_c, "w") as f:
-        f.write(mutate(src, old, new, which))
+        f.write(text)
     lib = os.path.join(workdir, f"lib{name}.so")
     subprocess.run(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", "-fno-fast-math",
                     "-I", os.path.join(ROOT, "oracle"), "-o", lib, mutant_c], check=True)
@@ -116,7 +127,8 @@ def run_mutant(name: str, workdir: str):
     res = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider",
                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                           os.path.join(ROOT, "tests", "test_oracle_balanced.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_fast.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_fast.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_accurate.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     return res.returncode, res.stdout[-1500:]
 
