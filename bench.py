@@ -56,7 +56,7 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=("fastblend", "reference"), default="fastblend")
     ap.add_argument("--workload", default="blend_512",
                     choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512", "initnet_512",
-                                                       "balanced_512", "fast_512"])
+                                                       "balanced_512", "fast_512", "accurate_512"])
     ap.add_argument("--window", type=int, default=0,
                     help="override the blend window of the headline-clip workloads (odd)")
     ap.add_argument("--learned-iters", type=int, default=2,
@@ -193,11 +193,13 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------
 # CPU oracle (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------------
-def oracle_frame_seconds(w: synth.Workload, g, s, frames, alpha=None, fast=False):
+def oracle_frame_seconds(w: synth.Workload, g, s, frames, alpha=None, fast=False, accurate=False):
     import oracle
     t0 = time.perf_counter()
     for i in frames:
-        if w.mode == "blend" and fast:
+        if w.mode == "blend" and accurate:
+            oracle.blend_frame_accurate(g, s, w.window, i, w.patch, w.iters, alpha, seed=w.seed)
+        elif w.mode == "blend" and fast:
             oracle.blend_frame_fast(g, s, w.window, i, w.patch, w.iters, seed=w.seed)
         elif w.mode == "blend" and alpha is not None:
             oracle.blend_frame_balanced(g, s, w.window, i, w.patch, w.iters, alpha, seed=w.seed)
@@ -214,10 +216,10 @@ def sample_frames(w: synth.Workload, n: int):
     return [mid + d for d in range(n)]
 
 
-def cpu_baseline(w: synth.Workload, g, s, n_frames: int, alpha=None, fast=False):
+def cpu_baseline(w: synth.Workload, g, s, n_frames: int, alpha=None, fast=False, accurate=False):
     import oracle
     frames = sample_frames(w, n_frames)
-    secs = oracle_frame_seconds(w, g, s, frames, alpha, fast)
+    secs = oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate)
     return {"value": len(frames) / secs, "unit": "frames/s", "cores": oracle.num_threads(),
             "kind": "oracle",
             "sample": f"{len(frames)} of {w.N} output frames ({frames}) of the same clip, each "
@@ -237,20 +239,22 @@ def run_reference(args):
                            seed=BATCH_SEED)
     else:
         w = synth.WORKLOADS["blend_512" if args.workload in ("balanced_512", "learned_512",
-                                                             "initnet_512", "fast_512")
+                                                             "initnet_512", "fast_512",
+                                                             "accurate_512")
                             else args.workload]
         if args.window and w.mode == "blend":
             import dataclasses
             w = dataclasses.replace(w, window=args.window)
         g, s = make_inputs(w, w.seed)
-    alpha = BALANCED_ALPHA if args.workload == "balanced_512" else None
+    alpha = BALANCED_ALPHA if args.workload in ("balanced_512", "accurate_512") else None
     fast = args.workload == "fast_512"
+    accurate = args.workload == "accurate_512"
     frames = sample_frames(w, 1)
     for _ in range(args.warmup):
-        oracle_frame_seconds(w, g, s, frames, alpha, fast)
+        oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate)
     total = 0.0
     for _ in range(args.steps):
-        total += oracle_frame_seconds(w, g, s, frames, alpha, fast)
+        total += oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate)
     value = args.steps * len(frames) / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
@@ -291,7 +295,8 @@ def run_gpu(args):
     learned = args.workload == "learned_512"
     balanced = args.workload == "balanced_512"
     fast = args.workload == "fast_512"
-    w = synth.WORKLOADS["blend_512" if learned or balanced or fast else args.workload]
+    accurate = args.workload == "accurate_512"
+    w = synth.WORKLOADS["blend_512" if learned or balanced or fast or accurate else args.workload]
     if args.window and w.mode == "blend":
         import dataclasses
         w = dataclasses.replace(w, window=args.window)
@@ -300,6 +305,9 @@ def run_gpu(args):
     params = fbp.Params.make(w.patch, w.iters, w.levels, 0, w.seed)
     if balanced:
         params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_BALANCED,
+                                 alpha=BALANCED_ALPHA)
+    if accurate:
+        params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_ACCURATE,
                                  alpha=BALANCED_ALPHA)
     fast_info = None
     if fast:
@@ -403,7 +411,7 @@ def run_gpu(args):
     iter_ms, iter_n = prof["iter"]
     kernel_total_ms = sum(v[0] for v in prof.values())
     ops = iter_ops_per_launch(w) if w.levels == 1 else None  # same per launch with learned init
-    if ops and balanced:
+    if ops and (balanced or accurate):
         ops *= 2   # each candidate compares a guide patch and a style patch
     if ops and fast:
         ops = ops * fast_info["nnfs"] // w.pairs()   # the fast mode computes fewer NNFs
@@ -428,6 +436,8 @@ def run_gpu(args):
         peak = DP4A_PER_CLK_SM * 4 * SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
         roof = {"bound": "alu", "kernel": ("nnf_iter_balanced (Alg. 1 Jacobi iteration, Sec. 3.4 "
                                            "improved loss)" if balanced else
+                                           "nnf_iter_balanced (Alg. 1 Jacobi iteration, Sec. 3.4 "
+                                           "mean-remap loss)" if accurate else
                                            "nnf_iter (Alg. 1 Jacobi iteration)"),
                 "achieved": achieved, "peak": peak, "unit": "T byte-pair ops/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
@@ -455,7 +465,9 @@ def run_gpu(args):
                                 "balanced blend all-pairs 60x512x512 k5 w15 n6: Sec. 3.4 improved "
                                 f"loss, alpha {BALANCED_ALPHA}" if balanced else
                                 f"fast-mode blend 60x512x512 k5 w{w.window} n6: Sec. 3.4 remapping / "
-                                "blending tables and interval queries (Algs. 3-5)" if fast else w.name),
+                                "blending tables and interval queries (Algs. 3-5)" if fast else
+                                "accurate blend all-pairs 60x512x512 k5 w15 n6: Sec. 3.4 mean-remap "
+                                f"alignment loss, alpha {BALANCED_ALPHA}" if accurate else w.name),
                    "frames": w.N, "height": w.H, "width": w.W,
                    "patch": w.patch, "window": w.window,
                    "iters": w.iters if not learned else args.learned_iters, "levels": w.levels,
@@ -475,7 +487,8 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, g, s, args.cpu_sample_frames,
-                                            BALANCED_ALPHA if balanced else None, fast)
+                                            BALANCED_ALPHA if balanced or accurate else None, fast,
+                                            accurate)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

@@ -92,6 +92,14 @@ typedef struct fb_params {
  * FB_FLAG_BALANCED or FB_FLAG_LEARNED_INIT; all NNFs of the call are held at once
  * (FB_ERR_UNSUPPORTED beyond the pair budget). */
 #define FB_FLAG_FAST 0x8u
+/* FB_FLAG_ACCURATE (fb_blend_window only): the quality improvement of Sec. 3.4 -- the
+ * NNFs of each output frame i are computed together; at the beginning of every
+ * iteration the mean remapped frame Tbar_i = (k^2 S_i + sum_j (S_j -> S_i)) / (k^2 c_i),
+ * rounded half up to 8 bits, is rebuilt from the current fields, and every pair (j -> i)
+ * takes its Jacobi step under alpha ||G_j[F] - G_i||^2 + ||S_j[F] - Tbar_i||^2 (the
+ * incumbent re-evaluated first).  levels must be 1, p->alpha <= 255; not with the other
+ * mode flags. */
+#define FB_FLAG_ACCURATE 0x10u
 
 /* Create a context on CUDA device `device` (made current for the call).  The context
  * allocates scratch lazily and keeps it for reuse until fb_ctx_destroy. */

@@ -210,8 +210,15 @@ int check_params(fb_ctx* ctx, const fb_params* p, int H, int W) {
         return fail(ctx, FB_ERR_ARG, "levels must be in [1, 16], got %d", p->levels);
     if (p->r0 < 0 || p->r0 > (1 << 20))
         return fail(ctx, FB_ERR_ARG, "r0 must be in [0, 2^20], got %d", p->r0);
-    if (p->flags & ~(FB_FLAG_LEARNED_INIT | FB_FLAG_REPORT_ENERGY | FB_FLAG_BALANCED | FB_FLAG_FAST))
+    if (p->flags & ~(FB_FLAG_LEARNED_INIT | FB_FLAG_REPORT_ENERGY | FB_FLAG_BALANCED | FB_FLAG_FAST |
+                     FB_FLAG_ACCURATE))
         return fail(ctx, FB_ERR_ARG, "unknown flags 0x%x", p->flags);
+    if (p->flags & FB_FLAG_ACCURATE) {
+        if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_LEARNED_INIT))
+            return fail(ctx, FB_ERR_ARG, "FB_FLAG_ACCURATE does not combine with the other mode flags");
+        if (p->levels != 1) return fail(ctx, FB_ERR_ARG, "FB_FLAG_ACCURATE requires levels == 1");
+        if (p->alpha > 255) return fail(ctx, FB_ERR_ARG, "alpha must be in [0, 255], got %u", p->alpha);
+    }
     if ((p->flags & FB_FLAG_FAST) && (p->flags & (FB_FLAG_BALANCED | FB_FLAG_LEARNED_INIT)))
         return fail(ctx, FB_ERR_ARG, "FB_FLAG_FAST does not combine with FB_FLAG_BALANCED or FB_FLAG_LEARNED_INIT");
     if (p->flags & FB_FLAG_BALANCED) {
@@ -376,12 +383,41 @@ int run_nnf_balanced(fb_ctx* ctx, const Buffers& b, int H, int W, const fb_param
         FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(k, b.shat_img, n, H, W, b.shat_rec, st));
         if (p->iters == 0) {
             FB_LAUNCH(ctx, st, FB_K_ENERGY, fb::launch_energy_balanced(k, b.pairs, pair0, n, g, b.srec, b.shat_rec,
-                                                                       p->alpha, Fc, Ec, st));
+                                                                       0, 0, p->alpha, Fc, Ec, st));
             break;
         }
         // the iteration kernel re-evaluates the incumbent against the new S^ itself
         FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_nnf_iter_balanced(k, b.pairs, pair0, n, g, b.srec, b.shat_rec,
-                                                                   p->alpha, r0, p->seed, it, Fc, Fo, Eo, st));
+                                                                   0, 0, p->alpha, r0, p->seed, it, Fc, Fo, Eo, st));
+        std::swap(Fc, Fo);
+        std::swap(Ec, Eo);
+    }
+    *F_out = Fc;
+    *E_out = Ec;
+    return FB_OK;
+}
+
+// Accurate mode of Sec. 3.4 for the pairs of output jobs [job0, job0 + n_jobs) (pairs
+// [pair0, pair0 + n_pairs), level 0): at the beginning of every iteration the mean
+// remapped frame Tbar of every output frame is rebuilt from the current fields (rounded,
+// laid out as row patches in the S^ buffers, one slot per job), then every pair takes a
+// Jacobi step under alpha * Eq.1(guides) + Eq.1(source style, Tbar of its output frame).
+int run_nnf_accurate(fb_ctx* ctx, const Buffers& b, int H, int W, const fb_params* p, int job0,
+                     int n_jobs, int target0, int pair0, int n, cudaStream_t st, uint32_t** F_out,
+                     uint32_t** E_out) {
+    const int k = p->patch;
+    const LevelGeom g{H, W, b.rec[0]};
+    uint32_t *Fc = b.FA, *Ec = b.EA, *Fo = b.FB, *Eo = b.EB;
+    FB_LAUNCH(ctx, st, FB_K_INIT, fb::launch_nnf_init(k, b.pairs, pair0, n, g, 0, nullptr, 0, 0, nullptr, p->seed,
+                                                      0, Fc, Ec, st));
+    const int r0 = p->r0 > 0 ? p->r0 : (H > W ? H : W);
+    for (int it = 0; it < p->iters; ++it) {
+        FB_LAUNCH(ctx, st, FB_K_SHAT, fb::launch_tbar(k, b.jobs, job0, n_jobs, b.pairs, pair0, Fc, b.styles, H, W,
+                                                      b.shat_img, st));
+        FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(k, b.shat_img, n_jobs, H, W, b.shat_rec, st));
+        FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_nnf_iter_balanced(k, b.pairs, pair0, n, g, b.srec, b.shat_rec,
+                                                                   1, target0, p->alpha, r0, p->seed, it, Fc, Fo,
+                                                                   Eo, st));
         std::swap(Fc, Fo);
         std::swap(Ec, Eo);
     }
@@ -441,8 +477,10 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
         return fail(ctx, FB_ERR_ARG, "guides, styles and out must all be device or all host memory");
     const bool staging = mg == Mem::Host;
 
-    const bool balanced = (p->flags & FB_FLAG_BALANCED) != 0;
-    // the improved loss keeps each pair's S^ image and row patches next to its F/E
+    const bool accurate = (p->flags & FB_FLAG_ACCURATE) != 0;
+    const bool balanced = (p->flags & FB_FLAG_BALANCED) != 0 || accurate;
+    // the improved loss keeps each pair's S^ image and row patches next to its F/E (the
+    // accurate mode uses the same buffers for the Tbar of each output frame)
     const size_t extra = balanced ? npx0 * 3 + fb::rowpatch_frame_words(k, H, W) * sizeof(uint32_t) : 0;
     std::vector<Chunk> chunks;
     size_t max_pairs = 0;
@@ -521,8 +559,10 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
                 }
                 init = b.init;
             }
-            rc = balanced ? run_nnf_balanced(ctx, b, H, W, p, c.pair0, c.n_pairs, init, st, &F, &E)
-                          : run_nnf(ctx, b, L, p, c.pair0, c.n_pairs, init, st, &F, &E);
+            rc = accurate ? run_nnf_accurate(ctx, b, H, W, p, c.job0, c.n_jobs, jobs[c.job0].out_frame, c.pair0,
+                                             c.n_pairs, st, &F, &E)
+                 : balanced ? run_nnf_balanced(ctx, b, H, W, p, c.pair0, c.n_pairs, init, st, &F, &E)
+                            : run_nnf(ctx, b, L, p, c.pair0, c.n_pairs, init, st, &F, &E);
             if (rc) return rc;
             if (p->flags & FB_FLAG_REPORT_ENERGY) {
                 FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_energy_sum(E, static_cast<size_t>(c.n_pairs) * npx0,
@@ -717,7 +757,7 @@ int check_clips(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     if (!clips || n < 1) return fail(ctx, FB_ERR_ARG, "clips must be a non-empty host array");
     if (!p) return fail(ctx, FB_ERR_ARG, "params is NULL");
     if (p->levels != 1) return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use levels == 1");
-    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST))
+    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_ACCURATE))
         return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use the plain loss and the direct sum");
     for (int c = 0; c < n; ++c) {
         const fb_clip_desc& d = clips[c];
@@ -1377,7 +1417,8 @@ int fb_nnf(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int 
         return fail(ctx, FB_ERR_ARG, "an initial NNF requires levels == 1");
     if (p->flags & FB_FLAG_BALANCED)
         return fail(ctx, FB_ERR_ARG, "the improved loss needs the source style: use fb_nnf_balanced");
-    if (p->flags & FB_FLAG_FAST) return fail(ctx, FB_ERR_ARG, "FB_FLAG_FAST applies to fb_blend_window only");
+    if (p->flags & (FB_FLAG_FAST | FB_FLAG_ACCURATE))
+        return fail(ctx, FB_ERR_ARG, "FB_FLAG_FAST and FB_FLAG_ACCURATE apply to fb_blend_window only");
     DeviceGuard dg(ctx->device);
     for (const void* q : {static_cast<const void*>(src_guide), static_cast<const void*>(tgt_guide),
                           static_cast<const void*>(nnf_out), static_cast<const void*>(init_nnf),
@@ -1546,8 +1587,8 @@ int fb_interpolate(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, cons
     ctx->err.clear();
     int rc = check_params(ctx, p, H, W);
     if (rc) return rc;
-    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST))
-        return fail(ctx, FB_ERR_ARG, "FB_FLAG_BALANCED and FB_FLAG_FAST apply to fb_blend_window only");
+    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_ACCURATE))
+        return fail(ctx, FB_ERR_ARG, "the blending modes apply to fb_blend_window only");
     if (N < 1 || N > 65535) return fail(ctx, FB_ERR_ARG, "N must be in [1, 65535], got %d", N);
     if (!guides || !key_idx || !key_styles || !out)
         return fail(ctx, FB_ERR_ARG, "guides, key_idx, key_styles and out must be non-NULL");

@@ -101,13 +101,22 @@ cudaError_t launch_fast_combine(int k, const FastJob* jobs, int n_jobs, const in
 // Jacobi step under that loss (which evaluates the incumbent's loss itself).  Level 0.
 cudaError_t launch_shat(int k, const PairDesc* pairs, int pair0, int n_pairs, int H, int W,
                        const uint32_t* F, const uint32_t* styles, uint8_t* shat, cudaStream_t st);
+// The style target of a pair is row-patch slot pl (its own S^) or, with slot_by_target,
+// slot pd.tgt - target0 (the mean remapped frame Tbar of its output frame, accurate mode).
 cudaError_t launch_energy_balanced(int k, const PairDesc* pairs, int pair0, int n_pairs,
                                    const LevelGeom& g, const uint32_t* srp, const uint32_t* shat_rp,
-                                   uint32_t alpha, const uint32_t* F, uint32_t* E, cudaStream_t st);
+                                   int slot_by_target, int target0, uint32_t alpha, const uint32_t* F,
+                                   uint32_t* E, cudaStream_t st);
 cudaError_t launch_nnf_iter_balanced(int k, const PairDesc* pairs, int pair0, int n_pairs,
                                      const LevelGeom& g, const uint32_t* srp, const uint32_t* shat_rp,
-                                     uint32_t alpha, int r0, uint64_t seed, int it, const uint32_t* Fp,
-                                     uint32_t* Fn, uint32_t* En, cudaStream_t st);
+                                     int slot_by_target, int target0, uint32_t alpha, int r0,
+                                     uint64_t seed, int it, const uint32_t* Fp, uint32_t* Fn,
+                                     uint32_t* En, cudaStream_t st);
+// Accurate mode: Tbar (8-bit, n_jobs x H x W x 3) of output jobs [job0, job0 + n_jobs)
+// from the chunk's fields (pair-local planes from pair0).
+cudaError_t launch_tbar(int k, const JobDesc* jobs, int job0, int n_jobs, const PairDesc* pairs, int pair0,
+                        const uint32_t* F, const uint32_t* styles, int H, int W, uint8_t* out,
+                        cudaStream_t st);
 cudaError_t launch_combine(int k, const JobDesc* jobs, int job0, int n_jobs,
                            const PairDesc* pairs, int pair0, const uint32_t* F,
                            const uint32_t* styles, int H, int W, float* out, cudaStream_t st);

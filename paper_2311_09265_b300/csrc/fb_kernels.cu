@@ -232,13 +232,45 @@ __global__ void __launch_bounds__(TILE_THREADS)
     o[2] = static_cast<uint8_t>((v2 + kk / 2) / kk);
 }
 
+// Accurate mode of Sec. 3.4: Tbar of output frame job.out_frame = the Eq. 2 numerator of
+// the current fields (k^2 S_self + sum of the pairs' votes) over k^2 c, rounded half up.
+template <int K>
+__global__ void __launch_bounds__(TILE_THREADS)
+    tbar_kernel(const JobDesc* __restrict__ jobs, int job0, const PairDesc* __restrict__ pairs,
+                int pair0, const uint32_t* __restrict__ F, const uint32_t* __restrict__ styles, int H,
+                int W, uint8_t* __restrict__ out) {
+    const TileCoord tc = tile_coord(W);
+    if (tc.r >= H || tc.c >= W) return;
+    const JobDesc job = jobs[job0 + blockIdx.y];
+    const size_t npx = static_cast<size_t>(H) * W;
+    const size_t x = static_cast<size_t>(tc.r) * W + tc.c;
+    constexpr uint32_t kk = static_cast<uint32_t>(K * K);
+    const uint32_t s = __ldg(styles + static_cast<size_t>(job.self_style) * npx + x);
+    uint32_t a0 = kk * (s & 0xFFu), a1 = kk * ((s >> 8) & 0xFFu), a2 = kk * ((s >> 16) & 0xFFu);
+    for (int p = 0; p < job.n_pairs; ++p) {
+        const int gp = job.first_pair + p;
+        const PairDesc pd = pairs[gp];
+        uint32_t v0, v1, v2;
+        remap_votes<K>(F + static_cast<size_t>(gp - pair0) * npx, styles + static_cast<size_t>(pd.style) * npx,
+                       H, W, tc.r, tc.c, v0, v1, v2);
+        a0 += v0;
+        a1 += v1;
+        a2 += v2;
+    }
+    const uint32_t den = job.den / 255u;  // k^2 c
+    uint8_t* o = out + (static_cast<size_t>(blockIdx.y) * npx + x) * 3;
+    o[0] = static_cast<uint8_t>((a0 + den / 2) / den);
+    o[1] = static_cast<uint8_t>((a1 + den / 2) / den);
+    o[2] = static_cast<uint8_t>((a2 + den / 2) / den);
+}
+
 // E(x) = the improved loss of the pair's current match against its current S^.
 template <int K>
 __global__ void __launch_bounds__(TILE_THREADS)
     energy_balanced_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
                            const uint32_t* __restrict__ rp, const uint32_t* __restrict__ srp,
-                           const uint32_t* __restrict__ shat_rp, uint32_t alpha,
-                           const uint32_t* __restrict__ F, uint32_t* __restrict__ E) {
+                           const uint32_t* __restrict__ shat_rp, int slot_by_target, int target0,
+                           uint32_t alpha, const uint32_t* __restrict__ F, uint32_t* __restrict__ E) {
     const TileCoord tc = tile_coord(W);
     if (tc.r >= H || tc.c >= W) return;
     const int pl = blockIdx.y;
@@ -247,7 +279,7 @@ __global__ void __launch_bounds__(TILE_THREADS)
     const size_t npx = static_cast<size_t>(H) * W;
     TargetPatch<K> tg, ts;
     load_target<K>(frame_rows<K>(rp, pd.tgt, H, W), H, W, tc.r, tc.c, tg);
-    load_target<K>(frame_rows<K>(shat_rp, pl, H, W), H, W, tc.r, tc.c, ts);
+    load_target<K>(frame_rows<K>(shat_rp, slot_by_target ? pd.tgt - target0 : pl, H, W), H, W, tc.r, tc.c, ts);
     const uint32_t f = F[static_cast<size_t>(pl) * npx + x];
     uint32_t e = 0;
     balanced_error_below<K>(frame_rows<K>(rp, pd.src, H, W), frame_rows<K>(srp, pd.style, H, W), H, W,
@@ -265,8 +297,8 @@ template <int K>
 __global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
     nnf_iter_balanced_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
                              const uint32_t* __restrict__ rp, const uint32_t* __restrict__ srp,
-                             const uint32_t* __restrict__ shat_rp, uint32_t alpha, int r0,
-                             uint32_t key0, uint32_t key1, uint32_t ctr_word,
+                             const uint32_t* __restrict__ shat_rp, int slot_by_target, int target0,
+                             uint32_t alpha, int r0, uint32_t key0, uint32_t key1, uint32_t ctr_word,
                              const uint32_t* __restrict__ Fp, uint32_t* __restrict__ Fn,
                              uint32_t* __restrict__ En) {
     const TileCoord tc = tile_coord(W);
@@ -275,7 +307,8 @@ __global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
     const PairDesc pd = pairs[pair0 + pl];
     const size_t npx = static_cast<size_t>(H) * W;
     iterate_pixel_balanced<K>(frame_rows<K>(rp, pd.src, H, W), frame_rows<K>(srp, pd.style, H, W),
-                              frame_rows<K>(rp, pd.tgt, H, W), frame_rows<K>(shat_rp, pl, H, W), alpha,
+                              frame_rows<K>(rp, pd.tgt, H, W),
+                              frame_rows<K>(shat_rp, slot_by_target ? pd.tgt - target0 : pl, H, W), alpha,
                               H, W, tc.r, tc.c, pd.tag, r0, key0, key1, ctr_word,
                               Fp + static_cast<size_t>(pl) * npx, Fn + static_cast<size_t>(pl) * npx,
                               En + static_cast<size_t>(pl) * npx);
@@ -515,25 +548,38 @@ cudaError_t launch_shat(int k, const PairDesc* pairs, int pair0, int n_pairs, in
 
 cudaError_t launch_energy_balanced(int k, const PairDesc* pairs, int pair0, int n_pairs,
                                    const LevelGeom& g, const uint32_t* srp, const uint32_t* shat_rp,
-                                   uint32_t alpha, const uint32_t* F, uint32_t* E, cudaStream_t st) {
+                                   int slot_by_target, int target0, uint32_t alpha, const uint32_t* F,
+                                   uint32_t* E, cudaStream_t st) {
     if (n_pairs <= 0) return cudaSuccess;
     const dim3 grid = tile_grid(g.H, g.W, n_pairs);
     const dim3 block(TILE_W, TILE_H);
     FB_DISPATCH_K(k, (energy_balanced_kernel<KK><<<grid, block, 0, st>>>(pairs, pair0, g.H, g.W, g.rp, srp,
-                                                                       shat_rp, alpha, F, E)));
+                                                                       shat_rp, slot_by_target, target0,
+                                                                       alpha, F, E)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tbar(int k, const JobDesc* jobs, int job0, int n_jobs, const PairDesc* pairs, int pair0,
+                        const uint32_t* F, const uint32_t* styles, int H, int W, uint8_t* out,
+                        cudaStream_t st) {
+    if (n_jobs <= 0) return cudaSuccess;
+    const dim3 grid = tile_grid(H, W, n_jobs);
+    const dim3 block(TILE_W, TILE_H);
+    FB_DISPATCH_K(k, (tbar_kernel<KK><<<grid, block, 0, st>>>(jobs, job0, pairs, pair0, F, styles, H, W, out)));
     return cudaGetLastError();
 }
 
 cudaError_t launch_nnf_iter_balanced(int k, const PairDesc* pairs, int pair0, int n_pairs,
                                      const LevelGeom& g, const uint32_t* srp, const uint32_t* shat_rp,
-                                     uint32_t alpha, int r0, uint64_t seed, int it, const uint32_t* Fp,
-                                     uint32_t* Fn, uint32_t* En, cudaStream_t st) {
+                                     int slot_by_target, int target0, uint32_t alpha, int r0,
+                                     uint64_t seed, int it, const uint32_t* Fp, uint32_t* Fn,
+                                     uint32_t* En, cudaStream_t st) {
     if (n_pairs <= 0) return cudaSuccess;
     const dim3 grid = tile_grid(g.H, g.W, n_pairs);
     const dim3 block(TILE_W, TILE_H);
     const uint32_t ctr_word = static_cast<uint32_t>(it + 1) << 8;  // level 0
     FB_DISPATCH_K(k, (nnf_iter_balanced_kernel<KK><<<grid, block, 0, st>>>(
-                         pairs, pair0, g.H, g.W, g.rp, srp, shat_rp, alpha, r0,
+                         pairs, pair0, g.H, g.W, g.rp, srp, shat_rp, slot_by_target, target0, alpha, r0,
                          static_cast<uint32_t>(seed), static_cast<uint32_t>(seed >> 32), ctr_word,
                          Fp, Fn, En)));
     return cudaGetLastError();
