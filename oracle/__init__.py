@@ -95,6 +95,12 @@ def lib() -> ctypes.CDLL:
                                                   ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
                                                   _f32p]
         L.fbref_blend_window_balanced.restype = ctypes.c_int
+        L.fbref_nnf_chain.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int, _P,
+                                      _u32p, _i32p, _i32p, _u32p]
+        L.fbref_nnf_chain.restype = ctypes.c_int
+        L.fbref_interpolate_tracking.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                 _i32p, _u8p, ctypes.c_int, _P, _f32p]
+        L.fbref_interpolate_tracking.restype = ctypes.c_int
         L.fbref_blend_frame_accurate.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
                                                  ctypes.c_int, _f32p, _u8p, _i32p]
@@ -420,4 +426,40 @@ def blend_window_accurate(guides, styles, window: int, patch: int, iters: int, a
                                            ctypes.byref(p), alpha, _ptr(out, _f32p))
     if rc != 0:
         raise ValueError("fbref_blend_window_accurate: bad arguments")
+    return out
+
+
+# ----------------------------------------------------------------------------------
+# Sec. 3.5.1 tracking
+# ----------------------------------------------------------------------------------
+def nnf_chain(src, tgts, patch: int, iters: int, tags, r0: int = 0, seed: int = 0, init=None):
+    """NNFs from `src` to the consecutive frames `tgts` (n, H, W, 3) with tracking;
+    returns (F (n, H, W, 2), E (n, H, W))."""
+    src, tgts = _u8(src), _u8(tgts)
+    n, H, W = tgts.shape[:3]
+    F = np.zeros((n, H, W, 2), np.int32)
+    E = np.zeros((n, H, W), np.uint32)
+    t = np.ascontiguousarray(tags, dtype=np.uint32)
+    p = params(patch, iters, 1, r0, seed)
+    ip = None
+    if init is not None:
+        init = np.ascontiguousarray(init, dtype=np.int32)
+        ip = _ptr(init, _i32p)
+    rc = lib().fbref_nnf_chain(_ptr(src, _u8p), _ptr(tgts, _u8p), n, H, W, ctypes.byref(p),
+                               _ptr(t, _u32p), ip, _ptr(F, _i32p), _ptr(E, _u32p))
+    if rc != 0:
+        raise ValueError("fbref_nnf_chain: bad arguments")
+    return F, E
+
+
+def interpolate_tracking(guides, key_idx, key_styles, patch: int, iters: int, seed: int = 0):
+    g, ks = _u8(guides), _u8(key_styles)
+    N, H, W = g.shape[:3]
+    keys = np.ascontiguousarray(key_idx, dtype=np.int32)
+    out = np.zeros((N, H, W, 3), np.float32)
+    p = params(patch, iters, 1, 0, seed)
+    rc = lib().fbref_interpolate_tracking(_ptr(g, _u8p), N, H, W, _ptr(keys, _i32p), _ptr(ks, _u8p),
+                                          len(keys), ctypes.byref(p), _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_interpolate_tracking: bad arguments")
     return out

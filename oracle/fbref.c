@@ -896,3 +896,145 @@ int fbref_blend_window_accurate(const uint8_t *guides, const uint8_t *styles, in
     }
     return 0;
 }
+
+/* ------------------------------------------------------------------------------ */
+/* Sec. 3.5.1, tracking: the NNFs from one source frame to n consecutive target      */
+/* frames form a chain; in every iteration the updating sequence of NNF(S, T_m) is    */
+/* expanded by the matches of NNF(S, T_{m-1}) and NNF(S, T_{m+1}) at the same pixel    */
+/* (snapshots of the previous iteration), tried after the four propagation            */
+/* candidates and before the random search.  Same streams, order and strict           */
+/* acceptance as fbref_nnf otherwise; one level.  init (nullable): n initial fields.   */
+/* ------------------------------------------------------------------------------ */
+int fbref_nnf_chain(const uint8_t *src, const uint8_t *tgts, int n, int H, int W,
+                    const fbref_params *p, const uint32_t *tags, const int32_t *init,
+                    int32_t *nnf_out, uint32_t *err_out)
+{
+    if (!params_ok(p, H, W) || p->levels != 1 || n < 1 || !src || !tgts || !tags || !nnf_out)
+        return -1;
+    const int k = p->patch, h = H, w = W;
+    size_t npx = (size_t)H * W, fsz = npx * 3;
+    int32_t *F = (int32_t *)malloc((size_t)n * npx * 2 * sizeof(int32_t));
+    int32_t *Fn = (int32_t *)malloc((size_t)n * npx * 2 * sizeof(int32_t));
+    uint32_t *E = (uint32_t *)malloc((size_t)n * npx * sizeof(uint32_t));
+    uint32_t *En = (uint32_t *)malloc((size_t)n * npx * sizeof(uint32_t));
+    for (int m = 0; m < n; ++m) {
+        const uint8_t *T = tgts + (size_t)m * fsz;
+        for (int r = 0; r < h; ++r)
+            for (int c = 0; c < w; ++c) {
+                size_t x = (size_t)r * w + c, o = ((size_t)m * npx + x) * 2;
+                if (init) {
+                    F[o] = clampi(init[o], 0, h - 1);
+                    F[o + 1] = clampi(init[o + 1], 0, w - 1);
+                } else {
+                    random_match(p->seed, (uint32_t)x, tags[m], 0, h, w, &F[o], &F[o + 1]);
+                }
+                E[(size_t)m * npx + x] = fbref_ssd(src, T, h, w, k, F[o], F[o + 1], r, c);
+            }
+    }
+    const int r0 = p->r0 > 0 ? p->r0 : (h > w ? h : w);
+    static const int dirs[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    for (int it = 0; it < p->iters; ++it) {
+        for (int m = 0; m < n; ++m) {
+            const uint8_t *T = tgts + (size_t)m * fsz;
+            const int32_t *Fm = F + (size_t)m * npx * 2;
+#pragma omp parallel for schedule(static)
+            for (int r = 0; r < h; ++r) {
+                for (int c = 0; c < w; ++c) {
+                    size_t x = (size_t)r * w + c;
+                    int32_t br = Fm[2 * x], bc = Fm[2 * x + 1];
+                    uint32_t be = E[(size_t)m * npx + x];
+                    for (int d = 0; d < 4; ++d) {
+                        int nr = r + dirs[d][0], nc = c + dirs[d][1];
+                        if (nr < 0 || nr >= h || nc < 0 || nc >= w) continue;
+                        size_t q = (size_t)nr * w + nc;
+                        int cr = clampi(Fm[2 * q] - dirs[d][0], 0, h - 1);
+                        int cc = clampi(Fm[2 * q + 1] - dirs[d][1], 0, w - 1);
+                        uint32_t e = fbref_ssd(src, T, h, w, k, cr, cc, r, c);
+                        if (e < be) { be = e; br = cr; bc = cc; }
+                    }
+                    for (int nb = m - 1; nb <= m + 1; nb += 2) {   /* tracking: T_{m-1}, T_{m+1} */
+                        if (nb < 0 || nb >= n) continue;
+                        const int32_t *Fb = F + ((size_t)nb * npx + x) * 2;
+                        uint32_t e = fbref_ssd(src, T, h, w, k, Fb[0], Fb[1], r, c);
+                        if (e < be) { be = e; br = Fb[0]; bc = Fb[1]; }
+                    }
+                    for (int t = 0; (r0 >> t) >= 1; ++t) {
+                        int rad = r0 >> t;
+                        int32_t dr, dc;
+                        fbref_rs_offset(p->seed, (uint32_t)x, tags[m], 0, it, t, rad, &dr, &dc);
+                        int cr = clampi(br + dr, 0, h - 1);
+                        int cc = clampi(bc + dc, 0, w - 1);
+                        uint32_t e = fbref_ssd(src, T, h, w, k, cr, cc, r, c);
+                        if (e < be) { be = e; br = cr; bc = cc; }
+                    }
+                    Fn[((size_t)m * npx + x) * 2] = br;
+                    Fn[((size_t)m * npx + x) * 2 + 1] = bc;
+                    En[(size_t)m * npx + x] = be;
+                }
+            }
+        }
+        int32_t *tf = F; F = Fn; Fn = tf;
+        uint32_t *te = E; E = En; En = te;
+    }
+    memcpy(nnf_out, F, (size_t)n * npx * 2 * sizeof(int32_t));
+    if (err_out) memcpy(err_out, E, (size_t)n * npx * sizeof(uint32_t));
+    free(F); free(Fn); free(E); free(En);
+    return 0;
+}
+
+/* Sec. 3.5.2 with tracking: every keyframe's NNFs to the run of frames on each side of it
+ * that it serves are one chain.  Output as fbref_interpolate. */
+int fbref_interpolate_tracking(const uint8_t *guides, int N, int H, int W,
+                               const int32_t *key_idx, const uint8_t *key_styles, int n_keys,
+                               const fbref_params *p, float *out)
+{
+    if (!params_ok(p, H, W) || p->levels != 1 || N < 1 || N > 65535 || n_keys < 1) return -1;
+    for (int m = 0; m < n_keys; ++m) {
+        if (key_idx[m] < 0 || key_idx[m] >= N) return -1;
+        if (m > 0 && key_idx[m] <= key_idx[m - 1]) return -1;
+    }
+    const int k = p->patch;
+    size_t npx = (size_t)H * W, fsz = npx * 3;
+    uint32_t *acc = (uint32_t *)calloc((size_t)N * fsz, sizeof(uint32_t));
+    uint32_t *den = (uint32_t *)calloc((size_t)N, sizeof(uint32_t));
+    uint32_t *V = (uint32_t *)malloc(fsz * sizeof(uint32_t));
+    int rc = 0;
+    for (int m = 0; m < n_keys && rc == 0; ++m) {
+        const int a = key_idx[m];
+        for (size_t t = 0; t < fsz; ++t) acc[(size_t)a * fsz + t] = (uint32_t)(k * k) * key_styles[(size_t)m * fsz + t];
+        den[a] = (uint32_t)(255 * k * k);
+        /* the frames this key serves: left run (after the previous key, or from 0) and
+         * right run (up to the next key, or to N - 1) */
+        const int prev = m > 0 ? key_idx[m - 1] : -1, next = m + 1 < n_keys ? key_idx[m + 1] : N;
+        const int runs[2][2] = {{prev + 1, a - 1}, {a + 1, next - 1}};
+        for (int side = 0; side < 2 && rc == 0; ++side) {
+            const int lo = runs[side][0], hi = runs[side][1];
+            if (lo > hi) continue;
+            const int n = hi - lo + 1;
+            uint32_t *tags = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+            int32_t *F = (int32_t *)malloc((size_t)n * npx * 2 * sizeof(int32_t));
+            for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(a, lo + q);
+            rc = fbref_nnf_chain(guides + (size_t)a * fsz, guides + (size_t)lo * fsz, n, H, W, p, tags,
+                                 NULL, F, NULL);
+            for (int q = 0; q < n && rc == 0; ++q) {
+                const int i = lo + q;
+                /* Eq. 9 weights: (r - i) for the left key, (i - l) for the right key, over
+                 * (r - l); a frame outside the key range takes its one key with weight one */
+                uint32_t wgt, dd;
+                if (side == 1 && next < N) { wgt = (uint32_t)(next - i); dd = (uint32_t)(next - a); }
+                else if (side == 0 && prev >= 0) { wgt = (uint32_t)(i - prev); dd = (uint32_t)(a - prev); }
+                else { wgt = 1u; dd = 1u; }
+                fbref_remap_sum(key_styles + (size_t)m * fsz, F + (size_t)q * npx * 2, H, W, k, V);
+                for (size_t t = 0; t < fsz; ++t) acc[(size_t)i * fsz + t] += wgt * V[t];
+                den[i] = (uint32_t)(255 * k * k) * dd;
+            }
+            free(tags); free(F);
+        }
+    }
+    for (int i = 0; i < N; ++i) {
+        float d = (float)den[i];
+        for (size_t t = 0; t < fsz; ++t) out[(size_t)i * fsz + t] = (float)acc[(size_t)i * fsz + t] / d;
+    }
+    free(acc); free(den); free(V);
+    return rc;
+}

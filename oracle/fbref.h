@@ -94,6 +94,14 @@ int fbref_interpolate_frame(const uint8_t *guides, int N, int H, int W, const in
  * Philox counter. */
 uint32_t fbref_pair_tag(int j, int i);
 
+/* Sec. 3.5.1 tracking (one level): see fbref.c. */
+int fbref_nnf_chain(const uint8_t *src, const uint8_t *tgts, int n, int H, int W,
+                    const fbref_params *p, const uint32_t *tags, const int32_t *init,
+                    int32_t *nnf_out, uint32_t *err_out);
+int fbref_interpolate_tracking(const uint8_t *guides, int N, int H, int W,
+                               const int32_t *key_idx, const uint8_t *key_styles, int n_keys,
+                               const fbref_params *p, float *out);
+
 /* Sec. 3.4 quality improvement ("accurate mode"), one level: see fbref.c. */
 int fbref_blend_frame_accurate(const uint8_t *guides, const uint8_t *styles, int N, int H,
                                int W, int window, const fbref_params *p, uint32_t alpha, int i,

@@ -4,8 +4,8 @@ Each mutant below is a one-place edit of oracle/fbref.c of the kind a restatemen
 the paper can get wrong (a dropped term, a wrong sign, an index of the wrong axis, a
 non-strict acceptance, an off-by-one bound or constant).  It is compiled into a
 temporary directory and the pin suites (tests/test_oracle_pins.py,
-tests/test_oracle_balanced.py, tests/test_oracle_fast.py, tests/test_oracle_accurate.py)
-are run against it:
+tests/test_oracle_balanced.py, tests/test_oracle_fast.py, tests/test_oracle_accurate.py,
+tests/test_oracle_tracking.py) are run against it:
 every mutant must make at least one pin fail.  The oracle's own source is not touched.
 """
 import os
@@ -63,6 +63,12 @@ MUTANTS = {
     "balanced_propagation_row_offset_sign": ("int cr = clampi(F[2 * n] - dirs[d][0], 0, h - 1);",
                                              "int cr = clampi(F[2 * n] + dirs[d][0], 0, h - 1);", 1),
     "balanced_random_search_skips_largest_radius": ("int rad = r0 >> t;", "int rad = r0 >> (t + 1);", 1),
+    "tracking_wrong_neighbours": ("for (int nb = m - 1; nb <= m + 1; nb += 2) {", "for (int nb = m - 2; nb <= m + 2; nb += 4) {", None),
+    "tracking_candidate_offset": ("uint32_t e = fbref_ssd(src, T, h, w, k, Fb[0], Fb[1], r, c);\n                        if (e < be) { be = e; br = Fb[0]; bc = Fb[1]; }",
+                                  "uint32_t e = fbref_ssd(src, T, h, w, k, clampi(Fb[0] + 1, 0, h - 1), Fb[1], r, c);\n                        if (e < be) { be = e; br = clampi(Fb[0] + 1, 0, h - 1); bc = Fb[1]; }", None),
+    "tracking_interpolation_weights_swapped": ("wgt = (uint32_t)(next - i); dd = (uint32_t)(next - a);", "wgt = (uint32_t)(i - a); dd = (uint32_t)(next - a);", None),
+    "tracking_pair_stream_reversed": ("for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(a, lo + q);", "for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(lo + q, a);", None),
+    "tracking_run_includes_the_next_key": ("const int runs[2][2] = {{prev + 1, a - 1}, {a + 1, next - 1}};", "const int runs[2][2] = {{prev + 1, a - 1}, {a + 1, next < N ? next : N - 1}};", None),
     "accurate_tbar_rounds_down": ("tbar[t] = (uint8_t)((acc[t] + den_t / 2) / den_t);", "tbar[t] = (uint8_t)(acc[t] / den_t);", None),
     "accurate_tbar_without_self_term": ("        for (size_t t = 0; t < fsz; ++t) acc[t] = kk * Si[t];\n        for (int m = 0; m < np; ++m) {\n            fbref_remap_sum",
                                         "        for (size_t t = 0; t < fsz; ++t) acc[t] = 0;\n        for (int m = 0; m < np; ++m) {\n            fbref_remap_sum", None),
@@ -128,7 +134,8 @@ def run_mutant(name: str, workdir: str):
                           os.path.join(ROOT, "tests", "test_oracle_pins.py"),
                           os.path.join(ROOT, "tests", "test_oracle_balanced.py"),
                           os.path.join(ROOT, "tests", "test_oracle_fast.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_accurate.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_accurate.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_tracking.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     return res.returncode, res.stdout[-1500:]
 
