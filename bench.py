@@ -56,7 +56,8 @@ def parse_args(argv=None):
     ap.add_argument("--impl", choices=("fastblend", "reference"), default="fastblend")
     ap.add_argument("--workload", default="blend_512",
                     choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512", "initnet_512",
-                                                       "balanced_512", "fast_512", "accurate_512"])
+                                                       "balanced_512", "fast_512", "accurate_512",
+                                                       "tracking_1024x576"])
     ap.add_argument("--window", type=int, default=0,
                     help="override the blend window of the headline-clip workloads (odd)")
     ap.add_argument("--learned-iters", type=int, default=2,
@@ -193,9 +194,23 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------
 # CPU oracle (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------------
-def oracle_frame_seconds(w: synth.Workload, g, s, frames, alpha=None, fast=False, accurate=False):
+def tracking_sample(w: synth.Workload, g, s):
+    """A bounded oracle sample of a tracking workload: the oracle couples every NNF of a
+    chain, so one output frame costs the whole clip; the sample is the clip's first 4
+    frames of the same size with keys 0 and 3 (2 interpolated frames, 4 tracked NNFs in
+    two chains of 2)."""
+    import numpy as np
+    return np.ascontiguousarray(g[:4]), np.ascontiguousarray(np.stack([s[0], s[0]])), [0, 3]
+
+
+def oracle_frame_seconds(w: synth.Workload, g, s, frames, alpha=None, fast=False, accurate=False,
+                         tracking=False):
     import oracle
     t0 = time.perf_counter()
+    if tracking:
+        g4, k4, keys = tracking_sample(w, g, s)
+        oracle.interpolate_tracking(g4, keys, k4, w.patch, w.iters, seed=w.seed)
+        return time.perf_counter() - t0
     for i in frames:
         if w.mode == "blend" and accurate:
             oracle.blend_frame_accurate(g, s, w.window, i, w.patch, w.iters, alpha, seed=w.seed)
@@ -216,8 +231,15 @@ def sample_frames(w: synth.Workload, n: int):
     return [mid + d for d in range(n)]
 
 
-def cpu_baseline(w: synth.Workload, g, s, n_frames: int, alpha=None, fast=False, accurate=False):
+def cpu_baseline(w: synth.Workload, g, s, n_frames: int, alpha=None, fast=False, accurate=False,
+                 tracking=False):
     import oracle
+    if tracking:
+        secs = oracle_frame_seconds(w, g, s, [], tracking=True)
+        return {"value": 2 / secs, "unit": "frames/s", "cores": oracle.num_threads(),
+                "kind": "oracle",
+                "sample": f"the clip's first 4 frames ({w.H}x{w.W}) with keys 0 and 3: 2 "
+                          f"interpolated frames, 4 tracked NNFs; C oracle, OpenMP, {secs:.1f} s"}
     frames = sample_frames(w, n_frames)
     secs = oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate)
     return {"value": len(frames) / secs, "unit": "frames/s", "cores": oracle.num_threads(),
@@ -238,10 +260,7 @@ def run_reference(args):
                            "blend", N, H, W, patch=patch, iters=BATCH_ITERS, window=window,
                            seed=BATCH_SEED)
     else:
-        w = synth.WORKLOADS["blend_512" if args.workload in ("balanced_512", "learned_512",
-                                                             "initnet_512", "fast_512",
-                                                             "accurate_512")
-                            else args.workload]
+        w = synth.WORKLOADS[base_workload(args.workload)]
         if args.window and w.mode == "blend":
             import dataclasses
             w = dataclasses.replace(w, window=args.window)
@@ -249,13 +268,15 @@ def run_reference(args):
     alpha = BALANCED_ALPHA if args.workload in ("balanced_512", "accurate_512") else None
     fast = args.workload == "fast_512"
     accurate = args.workload == "accurate_512"
+    tracking = args.workload == "tracking_1024x576"
     frames = sample_frames(w, 1)
     for _ in range(args.warmup):
-        oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate)
+        oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate, tracking)
     total = 0.0
     for _ in range(args.steps):
-        total += oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate)
-    value = args.steps * len(frames) / total
+        total += oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate, tracking)
+    n_out = 2 if tracking else len(frames)
+    value = args.steps * n_out / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
@@ -266,7 +287,10 @@ def run_reference(args):
                    "step": "one output frame of the clip (bounded CPU sample)"},
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": oracle.num_threads(),
                          "kind": "oracle",
-                         "sample": f"each step blends output frame {frames[0]} of {w.N}"},
+                         "sample": ("each step interpolates frames 1-2 of the clip's first 4 "
+                                    "frames with keys 0 and 3 (tracking couples whole chains)"
+                                    if tracking else
+                                    f"each step blends output frame {frames[0]} of {w.N}")},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
     }
@@ -283,6 +307,28 @@ def iter_ops_per_launch(w: synth.Workload) -> int:
     return w.pairs() * w.H * w.W * (4 + w.random_search_radii()) * 3 * w.patch * w.patch
 
 
+def base_workload(name: str) -> str:
+    """The synthetic clip a mode workload runs on."""
+    if name in ("balanced_512", "learned_512", "initnet_512", "fast_512", "accurate_512"):
+        return "blend_512"
+    if name == "tracking_1024x576":
+        return "interp_1024x576"
+    return name
+
+
+def tracking_neighbour_refs(w: synth.Workload) -> int:
+    """Chain-neighbour candidates per pixel summed over the pairs of an interpolation with
+    tracking: a keyframe's chain of n consecutive target frames has 2 (n - 1)."""
+    keys = list(w.keys)
+    bounds = [-1] + keys + [w.N]
+    refs = 0
+    for a, b in zip(bounds[:-1], bounds[1:]):
+        n = b - a - 1                              # frames strictly between two keys
+        chains = (a >= 0) + (b < w.N)              # served from the left and / or right key
+        refs += chains * 2 * max(n - 1, 0)
+    return refs
+
+
 def run_gpu(args):
     import torch
 
@@ -296,7 +342,8 @@ def run_gpu(args):
     balanced = args.workload == "balanced_512"
     fast = args.workload == "fast_512"
     accurate = args.workload == "accurate_512"
-    w = synth.WORKLOADS["blend_512" if learned or balanced or fast or accurate else args.workload]
+    tracking = args.workload == "tracking_1024x576"
+    w = synth.WORKLOADS[base_workload(args.workload)]
     if args.window and w.mode == "blend":
         import dataclasses
         w = dataclasses.replace(w, window=args.window)
@@ -309,6 +356,8 @@ def run_gpu(args):
     if accurate:
         params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_ACCURATE,
                                  alpha=BALANCED_ALPHA)
+    if tracking:
+        params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_TRACKING)
     fast_info = None
     if fast:
         params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_FAST)
@@ -415,6 +464,8 @@ def run_gpu(args):
         ops *= 2   # each candidate compares a guide patch and a style patch
     if ops and fast:
         ops = ops * fast_info["nnfs"] // w.pairs()   # the fast mode computes fewer NNFs
+    if ops and tracking:
+        ops += tracking_neighbour_refs(w) * w.H * w.W * 3 * w.patch * w.patch
     if fast:
         # context: the direct window sum of the same clip and window, one untimed-by-the-
         # contract measurement with CUDA events
@@ -438,6 +489,8 @@ def run_gpu(args):
                                            "improved loss)" if balanced else
                                            "nnf_iter_balanced (Alg. 1 Jacobi iteration, Sec. 3.4 "
                                            "mean-remap loss)" if accurate else
+                                           "nnf_iter_track (Alg. 1 Jacobi iteration with the "
+                                           "tracking of Sec. 3.5.1)" if tracking else
                                            "nnf_iter (Alg. 1 Jacobi iteration)"),
                 "achieved": achieved, "peak": peak, "unit": "T byte-pair ops/s",
                 "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
@@ -448,6 +501,8 @@ def run_gpu(args):
                 "avg_launch_ms": iter_ms / iter_n, "launches": iter_n,
                 "share_of_kernel_time": iter_ms / kernel_total_ms if kernel_total_ms else None,
                 "candidate_evals_per_s": (w.candidate_evals() * (fast_info["nnfs"] / w.pairs() if fast else 1)
+                                          + (tracking_neighbour_refs(w) * w.H * w.W * w.iters
+                                             if tracking else 0)
                                           if not learned else
                                           w.pairs() * w.H * w.W * (1 + args.learned_iters *
                                                                    (4 + w.random_search_radii())))
@@ -467,12 +522,16 @@ def run_gpu(args):
                                 f"fast-mode blend 60x512x512 k5 w{w.window} n6: Sec. 3.4 remapping / "
                                 "blending tables and interval queries (Algs. 3-5)" if fast else
                                 "accurate blend all-pairs 60x512x512 k5 w15 n6: Sec. 3.4 mean-remap "
-                                f"alignment loss, alpha {BALANCED_ALPHA}" if accurate else w.name),
+                                f"alignment loss, alpha {BALANCED_ALPHA}" if accurate else
+                                "tracking interpolation 48x576x1024 k7 n8 keys 0,47: Sec. 3.5.1 "
+                                "chain-neighbour candidates" if tracking else w.name),
                    "frames": w.N, "height": w.H, "width": w.W,
                    "patch": w.patch, "window": w.window,
                    "iters": w.iters if not learned else args.learned_iters, "levels": w.levels,
                    "nnfs_per_step": fast_info["nnfs"] if fast else w.pairs(),
-                   "candidate_evals_per_step": (w.candidate_evals() if not learned else
+                   "candidate_evals_per_step": (w.candidate_evals()
+                                                + (tracking_neighbour_refs(w) * w.H * w.W * w.iters
+                                                   if tracking else 0) if not learned else
                                                 w.pairs() * w.H * w.W * (1 + args.learned_iters *
                                                                          (4 + w.random_search_radii()))),
                    "learned_init": learned_info,
@@ -488,7 +547,7 @@ def run_gpu(args):
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, g, s, args.cpu_sample_frames,
                                             BALANCED_ALPHA if balanced or accurate else None, fast,
-                                            accurate)
+                                            accurate, tracking)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

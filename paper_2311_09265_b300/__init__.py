@@ -39,6 +39,7 @@ FB_FLAG_REPORT_ENERGY = 0x2
 FB_FLAG_BALANCED = 0x4
 FB_FLAG_FAST = 0x8
 FB_FLAG_ACCURATE = 0x10
+FB_FLAG_TRACKING = 0x20
 
 FB_BATCH_NO_GRAPH = 0x1
 

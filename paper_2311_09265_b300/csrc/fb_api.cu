@@ -211,8 +211,13 @@ int check_params(fb_ctx* ctx, const fb_params* p, int H, int W) {
     if (p->r0 < 0 || p->r0 > (1 << 20))
         return fail(ctx, FB_ERR_ARG, "r0 must be in [0, 2^20], got %d", p->r0);
     if (p->flags & ~(FB_FLAG_LEARNED_INIT | FB_FLAG_REPORT_ENERGY | FB_FLAG_BALANCED | FB_FLAG_FAST |
-                     FB_FLAG_ACCURATE))
+                     FB_FLAG_ACCURATE | FB_FLAG_TRACKING))
         return fail(ctx, FB_ERR_ARG, "unknown flags 0x%x", p->flags);
+    if (p->flags & FB_FLAG_TRACKING) {
+        if (p->levels != 1) return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING requires levels == 1");
+        if (p->flags & FB_FLAG_LEARNED_INIT)
+            return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING does not combine with FB_FLAG_LEARNED_INIT");
+    }
     if (p->flags & FB_FLAG_ACCURATE) {
         if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_LEARNED_INIT))
             return fail(ctx, FB_ERR_ARG, "FB_FLAG_ACCURATE does not combine with the other mode flags");
@@ -351,9 +356,14 @@ int run_nnf(fb_ctx* ctx, const Buffers& b, const Levels& L, const fb_params* p, 
             std::swap(Ec, Eo);
         }
         const int r0 = p->r0 > 0 ? p->r0 : (L.h[l] > L.w[l] ? L.h[l] : L.w[l]);
+        const bool tracking = (p->flags & FB_FLAG_TRACKING) != 0;  // levels == 1
         for (int it = 0; it < p->iters; ++it) {
-            FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_nnf_iter(k, b.pairs, pair0, n, g, r0, p->seed, l, it, Fc, Ec,
-                                               Fo, Eo, st));
+            if (tracking)
+                FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_nnf_iter_track(k, b.pairs, pair0, n, g, r0, p->seed, it, Fc,
+                                                                       Ec, Fo, Eo, st));
+            else
+                FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_nnf_iter(k, b.pairs, pair0, n, g, r0, p->seed, l, it, Fc, Ec,
+                                                   Fo, Eo, st));
             std::swap(Fc, Fo);
             std::swap(Ec, Eo);
         }
@@ -486,6 +496,9 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
     size_t max_pairs = 0;
     int rc = make_chunks(ctx, jobs, npx0, chunks, max_pairs, extra);
     if (rc) return rc;
+    if ((p->flags & FB_FLAG_TRACKING) && chunks.size() > 1)
+        return fail(ctx, FB_ERR_UNSUPPORTED, "tracking keeps all %zu NNFs of the call at once; the pair budget does not",
+                    pairs.size());
 
     const size_t guide_bytes = static_cast<size_t>(N) * npx0 * 3;
     const size_t style_bytes = static_cast<size_t>(n_styles) * npx0 * 3;
@@ -757,7 +770,7 @@ int check_clips(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     if (!clips || n < 1) return fail(ctx, FB_ERR_ARG, "clips must be a non-empty host array");
     if (!p) return fail(ctx, FB_ERR_ARG, "params is NULL");
     if (p->levels != 1) return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use levels == 1");
-    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_ACCURATE))
+    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_ACCURATE | FB_FLAG_TRACKING))
         return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use the plain loss and the direct sum");
     for (int c = 0; c < n; ++c) {
         const fb_clip_desc& d = clips[c];
@@ -1419,6 +1432,7 @@ int fb_nnf(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int 
         return fail(ctx, FB_ERR_ARG, "the improved loss needs the source style: use fb_nnf_balanced");
     if (p->flags & (FB_FLAG_FAST | FB_FLAG_ACCURATE))
         return fail(ctx, FB_ERR_ARG, "FB_FLAG_FAST and FB_FLAG_ACCURATE apply to fb_blend_window only");
+    if (p->flags & FB_FLAG_TRACKING) return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING applies to fb_interpolate only");
     DeviceGuard dg(ctx->device);
     for (const void* q : {static_cast<const void*>(src_guide), static_cast<const void*>(tgt_guide),
                           static_cast<const void*>(nnf_out), static_cast<const void*>(init_nnf),
@@ -1553,6 +1567,7 @@ int fb_blend_window(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles, i
         return fail(ctx, FB_ERR_ARG, "window must be odd and >= 1, got %d", window);
     if (!guides || !styles || !out)
         return fail(ctx, FB_ERR_ARG, "guides, styles and out must be non-NULL");
+    if (p->flags & FB_FLAG_TRACKING) return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING applies to fb_interpolate only");
     const int k = p->patch, M = (window - 1) / 2;
     if (p->flags & FB_FLAG_FAST) {
         const uint64_t k4 = static_cast<uint64_t>(k) * k * k * k;
@@ -1630,6 +1645,17 @@ int fb_interpolate(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, cons
             j.n_pairs = 1;
         }
         jobs[i] = j;
+    }
+    if (p->flags & FB_FLAG_TRACKING) {
+        // Sec. 3.5.1: a pair's chain neighbours are the pairs from the same keyframe to the
+        // frames before and after its target (keys have no pairs, so chains end there).
+        std::map<std::pair<int, int>, int> index;
+        for (size_t q = 0; q < pairs.size(); ++q) index[{pairs[q].src, pairs[q].tgt}] = static_cast<int>(q);
+        for (PairDesc& pd : pairs) {
+            auto a = index.find({pd.src, pd.tgt - 1}), b = index.find({pd.src, pd.tgt + 1});
+            pd.pad[0] = a == index.end() ? -1 : a->second;
+            pd.pad[1] = b == index.end() ? -1 : b->second;
+        }
     }
     DeviceGuard dg(ctx->device);
     return run_pipeline(ctx, guides, N, H, W, key_styles, n_keys, pairs, jobs, p, out,

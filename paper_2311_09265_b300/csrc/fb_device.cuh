@@ -309,14 +309,36 @@ struct BalancedError {
 // (0,1), then random search around the running best with radius r0 >> t; strict
 // improvement only.  A candidate equal to the running best is skipped: its error equals
 // the incumbent's, so it could not win.
+// Extra candidates tried after propagation: none, or (tracking, Sec. 3.5.1) the matches
+// of the chain neighbours at the same pixel.
+struct NoExtra {
+    template <class F>
+    __device__ __forceinline__ void operator()(F&) const {}
+};
+struct TrackNeighbours {
+    const uint32_t* prev;  // snapshot of the pair to target i - 1 at this pixel, or null
+    const uint32_t* next;  // ... to target i + 1
+    template <class F>
+    __device__ __forceinline__ void operator()(F& consider) const {
+        if (prev) {
+            const uint32_t f = *prev;
+            consider(row_of(f), col_of(f));
+        }
+        if (next) {
+            const uint32_t f = *next;
+            consider(row_of(f), col_of(f));
+        }
+    }
+};
+
 // (bf, be): the incumbent match and its error under `err`.
-template <int K, class Err>
+template <int K, class Err, class Extra = NoExtra>
 __device__ __forceinline__ void search_pixel(const Err& err, int H, int W, int r, int c,
                                              uint32_t tag, int r0, uint32_t key0, uint32_t key1,
                                              uint32_t ctr_word, const uint32_t* __restrict__ Fpp,
                                              uint32_t bf, uint32_t be,
                                              uint32_t* __restrict__ Fnp,
-                                             uint32_t* __restrict__ Enp) {
+                                             uint32_t* __restrict__ Enp, const Extra& extra = Extra{}) {
     const size_t x = static_cast<size_t>(r) * W + c;
 
 #ifdef FB_COUNT_EVALS
@@ -352,6 +374,8 @@ __device__ __forceinline__ void search_pixel(const Err& err, int H, int W, int r
         const uint32_t f = Fpp[x + 1];
         consider(row_of(f), max(col_of(f) - 1, 0));
     }
+
+    extra(consider);
 
     // Random search: F'(x) = F(x) + U[-r, r]^2, r = r0 >> t, t = 0, 1, ... while r >= 1.
     uint4 u = make_uint4(0u, 0u, 0u, 0u);
@@ -389,6 +413,22 @@ __device__ __forceinline__ void iterate_pixel(const uint32_t* __restrict__ rps,
     const size_t x = static_cast<size_t>(r) * W + c;
     search_pixel<K>(PlainError<K>{rps, H, W, t}, H, W, r, c, tag, r0, key0, key1, ctr_word, Fpp,
                     Fpp[x], Epp[x], Fnp, Enp);
+}
+
+// Tracking (Sec. 3.5.1): the plain loss with the chain neighbours' matches as candidates.
+template <int K>
+__device__ __forceinline__ void iterate_pixel_tracking(
+    const uint32_t* __restrict__ rps, const uint32_t* __restrict__ rpt, int H, int W, int r, int c,
+    uint32_t tag, int r0, uint32_t key0, uint32_t key1, uint32_t ctr_word,
+    const uint32_t* __restrict__ Fpp, const uint32_t* __restrict__ Epp,
+    const uint32_t* __restrict__ Fprev, const uint32_t* __restrict__ Fnext, uint32_t* __restrict__ Fnp,
+    uint32_t* __restrict__ Enp) {
+    TargetPatch<K> t;
+    load_target<K>(rpt, H, W, r, c, t);
+    const size_t x = static_cast<size_t>(r) * W + c;
+    search_pixel<K>(PlainError<K>{rps, H, W, t}, H, W, r, c, tag, r0, key0, key1, ctr_word, Fpp,
+                    Fpp[x], Epp[x], Fnp, Enp,
+                    TrackNeighbours{Fprev ? Fprev + x : nullptr, Fnext ? Fnext + x : nullptr});
 }
 
 // The improved loss of Sec. 3.4: the pair's S^ (rpshat, refreshed before the iteration)

@@ -36,7 +36,8 @@ struct PairDesc {
     uint32_t tag;      // Philox stream id of the pair
     int32_t style;     // style slot remapped through this pair's NNF
     uint32_t weight;   // integer weight of the remapped style in the output numerator
-    int32_t pad[3];
+    int32_t pad[3];    // tracking kernel only: pad[0] / pad[1] = chain neighbours (pair
+                       // indices of the launch for targets tgt - 1 / tgt + 1, or -1)
 };
 
 // One output frame: out = (self_w * S_self * k^2 / k^2 ... ) see combine kernel.
@@ -77,6 +78,13 @@ cudaError_t launch_nnf_iter(int k, const PairDesc* pairs, int pair0, int n_pairs
 cudaError_t launch_nnf_unpack(const uint32_t* F, const uint32_t* E, size_t npx, int32_t* nnf_out,
                               uint32_t* err_out, cudaStream_t st);
 cudaError_t launch_nnf_pack(const int32_t* nnf, int H, int W, uint32_t* F, cudaStream_t st);
+// Tracking (Sec. 3.5.1), level 0: one Jacobi iteration of the launch's pairs in which a
+// pair's pad[0] / pad[1] (pair indices of the same launch, -1 for none) name its chain
+// neighbours, whose matches at the same pixel are tried after propagation.
+cudaError_t launch_nnf_iter_track(int k, const PairDesc* pairs, int pair0, int n_pairs, const LevelGeom& g,
+                                  int r0, uint64_t seed, int it, const uint32_t* Fp, const uint32_t* Ep,
+                                  uint32_t* Fn, uint32_t* En, cudaStream_t st);
+
 // Fast mode of Sec. 3.4 (Algs. 3-5).  A blending-table entry: the exact sum
 // k^2 S_frame + the Alg. 2 votes of its sources, each source one NNF pair (index into the
 // pair table; the pair's style is the source frame), stored as 16 bytes per pixel.

@@ -206,6 +206,28 @@ __global__ void __launch_bounds__(TILE_THREADS, IterOccupancy<K>::value * 256 / 
                      Fn + static_cast<size_t>(pl) * npx, En + static_cast<size_t>(pl) * npx);
 }
 
+// Tracking (Sec. 3.5.1): as nnf_iter_kernel, plus the matches of the pair's chain
+// neighbours (pairs pad[0] / pad[1] of the launch, -1 for none) at the same pixel.
+template <int K>
+__global__ void __launch_bounds__(TILE_THREADS, IterOccupancy<K>::value)
+    nnf_iter_track_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
+                          const uint32_t* __restrict__ rp, int r0, uint32_t key0, uint32_t key1,
+                          uint32_t ctr_word, const uint32_t* __restrict__ Fp,
+                          const uint32_t* __restrict__ Ep, uint32_t* __restrict__ Fn,
+                          uint32_t* __restrict__ En) {
+    const TileCoord tc = tile_coord(W);
+    if (tc.r >= H || tc.c >= W) return;
+    const int pl = blockIdx.y;
+    const PairDesc pd = pairs[pair0 + pl];
+    const size_t npx = static_cast<size_t>(H) * W;
+    const uint32_t* prev = pd.pad[0] >= 0 ? Fp + static_cast<size_t>(pd.pad[0] - pair0) * npx : nullptr;
+    const uint32_t* next = pd.pad[1] >= 0 ? Fp + static_cast<size_t>(pd.pad[1] - pair0) * npx : nullptr;
+    iterate_pixel_tracking<K>(frame_rows<K>(rp, pd.src, H, W), frame_rows<K>(rp, pd.tgt, H, W), H, W, tc.r,
+                              tc.c, pd.tag, r0, key0, key1, ctr_word, Fp + static_cast<size_t>(pl) * npx,
+                              Ep + static_cast<size_t>(pl) * npx, prev, next,
+                              Fn + static_cast<size_t>(pl) * npx, En + static_cast<size_t>(pl) * npx);
+}
+
 // ---------------------------------------------------------------------------------
 // Improved loss of Sec. 3.4 ("balanced mode").  Per iteration: S^ of every pair from its
 // current field (shat_kernel, then the guide row-patch layout), the incumbent's loss
@@ -604,6 +626,19 @@ cudaError_t launch_fast_combine(int k, const FastJob* jobs, int n_jobs, const in
     const dim3 block(TILE_W, TILE_H);
     FB_DISPATCH_K(k, (fast_combine_kernel<KK><<<grid, block, 0, st>>>(jobs, pieces, F, entries, styles, H, W,
                                                                      out)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nnf_iter_track(int k, const PairDesc* pairs, int pair0, int n_pairs, const LevelGeom& g,
+                                  int r0, uint64_t seed, int it, const uint32_t* Fp, const uint32_t* Ep,
+                                  uint32_t* Fn, uint32_t* En, cudaStream_t st) {
+    if (n_pairs <= 0) return cudaSuccess;
+    const dim3 grid = tile_grid(g.H, g.W, n_pairs);
+    const dim3 block(TILE_W, TILE_H);
+    const uint32_t ctr_word = static_cast<uint32_t>(it + 1) << 8;  // level 0
+    FB_DISPATCH_K(k, (nnf_iter_track_kernel<KK><<<grid, block, 0, st>>>(
+                         pairs, pair0, g.H, g.W, g.rp, r0, static_cast<uint32_t>(seed),
+                         static_cast<uint32_t>(seed >> 32), ctr_word, Fp, Ep, Fn, En)));
     return cudaGetLastError();
 }
 

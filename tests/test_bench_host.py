@@ -1,0 +1,45 @@
+"""Host-side bookkeeping of bench.py that needs no GPU."""
+import dataclasses
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import synth  # noqa: E402
+
+
+def _pairs(N, keys):
+    """Sec. 3.5.2 pair set by brute force: each non-key frame from its nearest key on
+    either side."""
+    out = set()
+    for i in range(N):
+        if i in keys:
+            continue
+        left = [k for k in keys if k < i]
+        right = [k for k in keys if k > i]
+        if left:
+            out.add((max(left), i))
+        if right:
+            out.add((min(right), i))
+    return out
+
+
+@pytest.mark.parametrize("N,keys", [(48, (0, 47)), (10, (2, 5, 7)), (6, (3,)), (5, (0, 1, 2, 3, 4)),
+                                    (9, (0, 2, 4, 6, 8)), (7, (6,))])
+def test_tracking_neighbour_refs_count_chain_neighbours(N, keys):
+    w = dataclasses.replace(synth.WORKLOADS["interp_1024x576"], N=N, keys=keys)
+    pairs = _pairs(N, set(keys))
+    brute = sum(((src, tgt - 1) in pairs) + ((src, tgt + 1) in pairs) for src, tgt in pairs)
+    assert bench.tracking_neighbour_refs(w) == brute
+    assert len(pairs) == w.pairs()
+
+
+def test_mode_workloads_run_on_their_clip():
+    assert bench.base_workload("tracking_1024x576") == "interp_1024x576"
+    for m in ("balanced_512", "fast_512", "accurate_512", "learned_512", "initnet_512"):
+        assert bench.base_workload(m) == "blend_512"
+    assert bench.base_workload("blend_512_16f") == "blend_512_16f"
