@@ -101,6 +101,9 @@ def lib() -> ctypes.CDLL:
         L.fbref_interpolate_tracking.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                                  _i32p, _u8p, ctypes.c_int, _P, _f32p]
         L.fbref_interpolate_tracking.restype = ctypes.c_int
+        L.fbref_blend_window_tracking.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int,
+                                                  ctypes.c_int, ctypes.c_int, _P, _f32p]
+        L.fbref_blend_window_tracking.restype = ctypes.c_int
         L.fbref_blend_frame_accurate.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
                                                  ctypes.c_int, _f32p, _u8p, _i32p]
@@ -462,4 +465,18 @@ def interpolate_tracking(guides, key_idx, key_styles, patch: int, iters: int, se
                                           len(keys), ctypes.byref(p), _ptr(out, _f32p))
     if rc != 0:
         raise ValueError("fbref_interpolate_tracking: bad arguments")
+    return out
+
+
+def blend_window_tracking(guides, styles, window: int, patch: int, iters: int, seed: int = 0):
+    """Eq. 2 blend whose NNFs from each source frame to the targets before / after it are
+    computed as two tracking chains (Sec. 3.5.1, one level)."""
+    g, s = _u8(guides), _u8(styles)
+    N, H, W = g.shape[:3]
+    out = np.zeros((N, H, W, 3), np.float32)
+    p = params(patch, iters, 1, 0, seed)
+    rc = lib().fbref_blend_window_tracking(_ptr(g, _u8p), _ptr(s, _u8p), N, H, W, window,
+                                           ctypes.byref(p), _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_blend_window_tracking: bad arguments")
     return out

@@ -1038,3 +1038,47 @@ int fbref_interpolate_tracking(const uint8_t *guides, int N, int H, int W,
     free(acc); free(den); free(V);
     return rc;
 }
+
+/* Sec. 3.5.1 applied to the Eq. 2 blend (the optional setting the paper mentions): the
+ * NNFs from source frame j to the targets of its window form two chains, the targets
+ * before j and the targets after j (no NNF(G_j, G_j) is computed, so a chain ends next to
+ * its source); each chain is computed with tracking, then every output frame is the Eq. 2
+ * mean over its window exactly as in fbref_blend_frame. */
+int fbref_blend_window_tracking(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                                int window, const fbref_params *p, float *out)
+{
+    if (!params_ok(p, H, W) || p->levels != 1 || N < 1 || N > 65535 || window < 1 || (window & 1) == 0)
+        return -1;
+    const int k = p->patch, M = (window - 1) / 2;
+    size_t npx = (size_t)H * W, fsz = npx * 3;
+    uint32_t *acc = (uint32_t *)calloc((size_t)N * fsz, sizeof(uint32_t));
+    uint32_t *V = (uint32_t *)malloc(fsz * sizeof(uint32_t));
+    for (size_t t = 0; t < (size_t)N * fsz; ++t) acc[t] = (uint32_t)(k * k) * styles[t];
+    int rc = 0;
+    for (int j = 0; j < N && rc == 0; ++j) {
+        const int runs[2][2] = {{j - M < 0 ? 0 : j - M, j - 1}, {j + 1, j + M > N - 1 ? N - 1 : j + M}};
+        for (int side = 0; side < 2 && rc == 0; ++side) {
+            const int lo = runs[side][0], hi = runs[side][1];
+            if (lo > hi) continue;
+            const int n = hi - lo + 1;
+            uint32_t *tags = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+            int32_t *F = (int32_t *)malloc((size_t)n * npx * 2 * sizeof(int32_t));
+            for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(j, lo + q);
+            rc = fbref_nnf_chain(guides + (size_t)j * fsz, guides + (size_t)lo * fsz, n, H, W, p, tags,
+                                 NULL, F, NULL);
+            for (int q = 0; q < n && rc == 0; ++q) {
+                fbref_remap_sum(styles + (size_t)j * fsz, F + (size_t)q * npx * 2, H, W, k, V);
+                uint32_t *a = acc + (size_t)(lo + q) * fsz;
+                for (size_t t = 0; t < fsz; ++t) a[t] += V[t];
+            }
+            free(tags); free(F);
+        }
+    }
+    for (int i = 0; i < N; ++i) {
+        const int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
+        float den = (float)(255 * k * k * (hi - lo + 1));
+        for (size_t t = 0; t < fsz; ++t) out[(size_t)i * fsz + t] = (float)acc[(size_t)i * fsz + t] / den;
+    }
+    free(acc); free(V);
+    return rc;
+}

@@ -101,6 +101,8 @@ int fbref_nnf_chain(const uint8_t *src, const uint8_t *tgts, int n, int H, int W
 int fbref_interpolate_tracking(const uint8_t *guides, int N, int H, int W,
                                const int32_t *key_idx, const uint8_t *key_styles, int n_keys,
                                const fbref_params *p, float *out);
+int fbref_blend_window_tracking(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
+                                int window, const fbref_params *p, float *out);
 
 /* Sec. 3.4 quality improvement ("accurate mode"), one level: see fbref.c. */
 int fbref_blend_frame_accurate(const uint8_t *guides, const uint8_t *styles, int N, int H,

@@ -69,6 +69,13 @@ MUTANTS = {
     "tracking_interpolation_weights_swapped": ("wgt = (uint32_t)(next - i); dd = (uint32_t)(next - a);", "wgt = (uint32_t)(i - a); dd = (uint32_t)(next - a);", None),
     "tracking_pair_stream_reversed": ("for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(a, lo + q);", "for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(lo + q, a);", None),
     "tracking_run_includes_the_next_key": ("const int runs[2][2] = {{prev + 1, a - 1}, {a + 1, next - 1}};", "const int runs[2][2] = {{prev + 1, a - 1}, {a + 1, next < N ? next : N - 1}};", None),
+    "blend_tracking_chain_includes_the_source": ("const int runs[2][2] = {{j - M < 0 ? 0 : j - M, j - 1}, {j + 1, j + M > N - 1 ? N - 1 : j + M}};",
+                                                 "const int runs[2][2] = {{j - M < 0 ? 0 : j - M, j - 1}, {j, j + M > N - 1 ? N - 1 : j + M}};", None),
+    "blend_tracking_one_chain_per_source": ("        for (int side = 0; side < 2 && rc == 0; ++side) {\n            const int lo = runs[side][0], hi = runs[side][1];\n            if (lo > hi) continue;\n            const int n = hi - lo + 1;\n            uint32_t *tags = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));\n            int32_t *F = (int32_t *)malloc((size_t)n * npx * 2 * sizeof(int32_t));\n            for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(j, lo + q);",
+                                            "        for (int side = 1; side < 2 && rc == 0; ++side) {\n            const int lo = runs[side][0], hi = runs[side][1];\n            if (lo > hi) continue;\n            const int n = hi - lo + 1;\n            uint32_t *tags = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));\n            int32_t *F = (int32_t *)malloc((size_t)n * npx * 2 * sizeof(int32_t));\n            for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(j, lo + q);", None),
+    "blend_tracking_pair_stream_reversed": ("for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(j, lo + q);", "for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(lo + q, j);", None),
+    "blend_tracking_window_short_by_one": ("float den = (float)(255 * k * k * (hi - lo + 1));\n        for (size_t t = 0; t < fsz; ++t) out[(size_t)i * fsz + t]",
+                                           "float den = (float)(255 * k * k * (hi - lo + 2));\n        for (size_t t = 0; t < fsz; ++t) out[(size_t)i * fsz + t]", None),
     "accurate_tbar_rounds_down": ("tbar[t] = (uint8_t)((acc[t] + den_t / 2) / den_t);", "tbar[t] = (uint8_t)(acc[t] / den_t);", None),
     "accurate_tbar_without_self_term": ("        for (size_t t = 0; t < fsz; ++t) acc[t] = kk * Si[t];\n        for (int m = 0; m < np; ++m) {\n            fbref_remap_sum",
                                         "        for (size_t t = 0; t < fsz; ++t) acc[t] = 0;\n        for (int m = 0; m < np; ++m) {\n            fbref_remap_sum", None),

@@ -69,3 +69,66 @@ def test_eq9_weights_between_constant_keys_with_tracking():
         else:
             num, den = 9 * (40 if i <= 2 else 180), 255 * 9
         assert (out[i] == np.float32(num) / np.float32(den)).all(), i
+
+
+# ----------------------------------------------------------------------------------
+# Tracking in the Eq. 2 blend (the optional setting of Sec. 3.5.1)
+# ----------------------------------------------------------------------------------
+def test_blend_tracking_at_window_3_is_the_plain_blend():
+    # Window 3: every source's chains hold one target each, so nothing is tracked.
+    g, s = synth.small_clip(6, 19, 22, seed=4, motion="affine")
+    a = oracle.blend_window_tracking(g, s, 3, 5, 2, seed=6)
+    b = oracle.blend_window(g, s, 3, 5, 2, seed=6)
+    assert (a == b).all()
+
+
+def test_blend_tracking_without_iterations_is_the_plain_blend():
+    # Tracking only adds candidates to the iterations: with none, every NNF is its random
+    # initialisation and the blend is the plain Eq. 2 mean of the same window.
+    g, s = synth.small_clip(8, 17, 20, seed=9, motion="shift")
+    for window in (5, 7, 15):
+        a = oracle.blend_window_tracking(g, s, window, 3, 0, seed=2)
+        b = oracle.blend_window(g, s, window, 3, 0, seed=2)
+        assert (a == b).all(), window
+
+
+def test_blend_tracking_constant_frame_styles_give_the_window_mean():
+    # Frame j styled with the constant c_j remaps to c_j under any field, so output frame i
+    # is exactly k^2 sum_j c_j / (255 k^2 n_i) over its truncated window.
+    N, window, k = 7, 5, 5
+    g, _ = synth.small_clip(N, 15, 16, seed=1, motion="affine")
+    c = np.array([10, 70, 200, 35, 140, 255, 0])
+    s = np.stack([np.full(g.shape[1:], v, np.uint8) for v in c])
+    out = oracle.blend_window_tracking(g, s, window, k, 2, seed=5)
+    for i in range(N):
+        lo, hi = max(0, i - 2), min(N - 1, i + 2)
+        num, den = k * k * int(c[lo:hi + 1].sum()), 255 * k * k * (hi - lo + 1)
+        assert (out[i] == np.float32(num) / np.float32(den)).all(), i
+
+
+def test_blend_tracking_chains_are_the_targets_on_each_side_of_the_source():
+    # Composition check: output frame i is the Eq. 2 mean of S_i and, for every source j of
+    # its window, the remap of S_j by the tracked chain of j's targets on i's side of j.
+    N, window, k, iters, seed = 7, 5, 5, 2, 11
+    g, s = synth.small_clip(N, 16, 19, seed=3, motion="affine")
+    out = oracle.blend_window_tracking(g, s, window, k, iters, seed=seed)
+    M = window // 2
+    fields = {}
+    for j in range(N):
+        for lo, hi in ((max(0, j - M), j - 1), (j + 1, min(N - 1, j + M))):
+            if lo > hi:
+                continue
+            tags = [oracle.pair_tag(j, t) for t in range(lo, hi + 1)]
+            F, _ = oracle.nnf_chain(g[j], g[lo:hi + 1], k, iters, tags, seed=seed)
+            for q, t in enumerate(range(lo, hi + 1)):
+                fields[(j, t)] = F[q]
+    for i in range(N):
+        lo, hi = max(0, i - M), min(N - 1, i + M)
+        acc = k * k * s[i].astype(np.uint64)
+        for j in range(lo, hi + 1):
+            if j != i:
+                acc += oracle.remap_sum(s[j], fields[(j, i)], k).astype(np.uint64)
+        ref = acc.astype(np.float32) / np.float32(255 * k * k * (hi - lo + 1))
+        assert (out[i] == ref).all(), i
+    # and the chains do track: the result differs from the independent NNFs
+    assert not (out == oracle.blend_window(g, s, window, k, iters, seed=seed)).all()
