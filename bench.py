@@ -57,7 +57,7 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="blend_512",
                     choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512", "initnet_512",
                                                        "balanced_512", "fast_512", "accurate_512",
-                                                       "tracking_1024x576"])
+                                                       "tracking_1024x576", "tracking_512"])
     ap.add_argument("--window", type=int, default=0,
                     help="override the blend window of the headline-clip workloads (odd)")
     ap.add_argument("--learned-iters", type=int, default=2,
@@ -194,13 +194,23 @@ class ClockSampler:
 # ----------------------------------------------------------------------------------
 # CPU oracle (cpu_baseline and the reference arm)
 # ----------------------------------------------------------------------------------
+TRACKING_BLEND_SAMPLE_FRAMES = 5
+
+
 def tracking_sample(w: synth.Workload, g, s):
     """A bounded oracle sample of a tracking workload: the oracle couples every NNF of a
-    chain, so one output frame costs the whole clip; the sample is the clip's first 4
+    chain, so one output frame costs the whole clip.  Interpolation: the clip's first 4
     frames of the same size with keys 0 and 3 (2 interpolated frames, 4 tracked NNFs in
-    two chains of 2)."""
+    two chains of 2).  Blend: the clip's first 5 frames (all 20 pairs of the window)."""
     import numpy as np
+    if w.mode == "blend":
+        n = TRACKING_BLEND_SAMPLE_FRAMES
+        return np.ascontiguousarray(g[:n]), np.ascontiguousarray(s[:n]), None
     return np.ascontiguousarray(g[:4]), np.ascontiguousarray(np.stack([s[0], s[0]])), [0, 3]
+
+
+def tracking_sample_outputs(w: synth.Workload) -> int:
+    return TRACKING_BLEND_SAMPLE_FRAMES if w.mode == "blend" else 2
 
 
 def oracle_frame_seconds(w: synth.Workload, g, s, frames, alpha=None, fast=False, accurate=False,
@@ -209,7 +219,10 @@ def oracle_frame_seconds(w: synth.Workload, g, s, frames, alpha=None, fast=False
     t0 = time.perf_counter()
     if tracking:
         g4, k4, keys = tracking_sample(w, g, s)
-        oracle.interpolate_tracking(g4, keys, k4, w.patch, w.iters, seed=w.seed)
+        if w.mode == "blend":
+            oracle.blend_window_tracking(g4, k4, w.window, w.patch, w.iters, seed=w.seed)
+        else:
+            oracle.interpolate_tracking(g4, keys, k4, w.patch, w.iters, seed=w.seed)
         return time.perf_counter() - t0
     for i in frames:
         if w.mode == "blend" and accurate:
@@ -236,10 +249,16 @@ def cpu_baseline(w: synth.Workload, g, s, n_frames: int, alpha=None, fast=False,
     import oracle
     if tracking:
         secs = oracle_frame_seconds(w, g, s, [], tracking=True)
-        return {"value": 2 / secs, "unit": "frames/s", "cores": oracle.num_threads(),
-                "kind": "oracle",
-                "sample": f"the clip's first 4 frames ({w.H}x{w.W}) with keys 0 and 3: 2 "
-                          f"interpolated frames, 4 tracked NNFs; C oracle, OpenMP, {secs:.1f} s"}
+        return {"value": tracking_sample_outputs(w) / secs, "unit": "frames/s",
+                "cores": oracle.num_threads(), "kind": "oracle",
+                "sample": (f"the clip's first {TRACKING_BLEND_SAMPLE_FRAMES} frames ({w.H}x{w.W}), "
+                           f"window {w.window}: all {TRACKING_BLEND_SAMPLE_FRAMES} output frames, "
+                           f"{TRACKING_BLEND_SAMPLE_FRAMES * (TRACKING_BLEND_SAMPLE_FRAMES - 1)} "
+                           f"tracked NNFs (windows truncated by the sample's length)"
+                           if w.mode == "blend" else
+                           f"the clip's first 4 frames ({w.H}x{w.W}) with keys 0 and 3: 2 "
+                           f"interpolated frames, 4 tracked NNFs")
+                          + f"; C oracle, OpenMP, {secs:.1f} s"}
     frames = sample_frames(w, n_frames)
     secs = oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate)
     return {"value": len(frames) / secs, "unit": "frames/s", "cores": oracle.num_threads(),
@@ -268,14 +287,14 @@ def run_reference(args):
     alpha = BALANCED_ALPHA if args.workload in ("balanced_512", "accurate_512") else None
     fast = args.workload == "fast_512"
     accurate = args.workload == "accurate_512"
-    tracking = args.workload == "tracking_1024x576"
+    tracking = args.workload in ("tracking_1024x576", "tracking_512")
     frames = sample_frames(w, 1)
     for _ in range(args.warmup):
         oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate, tracking)
     total = 0.0
     for _ in range(args.steps):
         total += oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate, tracking)
-    n_out = 2 if tracking else len(frames)
+    n_out = tracking_sample_outputs(w) if tracking else len(frames)
     value = args.steps * n_out / total
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s",
@@ -289,7 +308,9 @@ def run_reference(args):
                          "kind": "oracle",
                          "sample": ("each step interpolates frames 1-2 of the clip's first 4 "
                                     "frames with keys 0 and 3 (tracking couples whole chains)"
-                                    if tracking else
+                                    if tracking and w.mode != "blend" else
+                                    f"each step blends the clip's first {TRACKING_BLEND_SAMPLE_FRAMES} "
+                                    "frames (tracking couples whole chains)" if tracking else
                                     f"each step blends output frame {frames[0]} of {w.N}")},
         "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0,
                 "d2h_bytes_per_step": 0},
@@ -309,7 +330,8 @@ def iter_ops_per_launch(w: synth.Workload) -> int:
 
 def base_workload(name: str) -> str:
     """The synthetic clip a mode workload runs on."""
-    if name in ("balanced_512", "learned_512", "initnet_512", "fast_512", "accurate_512"):
+    if name in ("balanced_512", "learned_512", "initnet_512", "fast_512", "accurate_512",
+                "tracking_512"):
         return "blend_512"
     if name == "tracking_1024x576":
         return "interp_1024x576"
@@ -317,8 +339,14 @@ def base_workload(name: str) -> str:
 
 
 def tracking_neighbour_refs(w: synth.Workload) -> int:
-    """Chain-neighbour candidates per pixel summed over the pairs of an interpolation with
-    tracking: a keyframe's chain of n consecutive target frames has 2 (n - 1)."""
+    """Chain-neighbour candidates per pixel summed over the pairs of a call with tracking:
+    a chain of n consecutive target frames from one source has 2 (n - 1)."""
+    if w.mode == "blend":
+        M, refs = w.window // 2, 0
+        for j in range(w.N):
+            for lo, hi in ((max(0, j - M), j - 1), (j + 1, min(w.N - 1, j + M))):
+                refs += 2 * max(hi - lo, 0)
+        return refs
     keys = list(w.keys)
     bounds = [-1] + keys + [w.N]
     refs = 0
@@ -342,7 +370,7 @@ def run_gpu(args):
     balanced = args.workload == "balanced_512"
     fast = args.workload == "fast_512"
     accurate = args.workload == "accurate_512"
-    tracking = args.workload == "tracking_1024x576"
+    tracking = args.workload in ("tracking_1024x576", "tracking_512")
     w = synth.WORKLOADS[base_workload(args.workload)]
     if args.window and w.mode == "blend":
         import dataclasses
@@ -524,6 +552,8 @@ def run_gpu(args):
                                 "accurate blend all-pairs 60x512x512 k5 w15 n6: Sec. 3.4 mean-remap "
                                 f"alignment loss, alpha {BALANCED_ALPHA}" if accurate else
                                 "tracking interpolation 48x576x1024 k7 n8 keys 0,47: Sec. 3.5.1 "
+                                "chain-neighbour candidates" if tracking and w.mode != "blend" else
+                                f"tracking blend all-pairs 60x512x512 k5 w{w.window} n6: Sec. 3.5.1 "
                                 "chain-neighbour candidates" if tracking else w.name),
                    "frames": w.N, "height": w.H, "width": w.W,
                    "patch": w.patch, "window": w.window,

@@ -100,12 +100,14 @@ typedef struct fb_params {
  * incumbent re-evaluated first).  levels must be 1, p->alpha <= 255; not with the other
  * mode flags. */
 #define FB_FLAG_ACCURATE 0x10u
-/* FB_FLAG_TRACKING (fb_interpolate only): the tracking of Sec. 3.5.1 -- the NNFs from a
- * keyframe to the consecutive frames it serves form a chain, and each pair's updating
- * sequence gains, after propagation and before the random search, the matches of the
- * pairs to the previous and next target frame at the same pixel (previous iteration's
- * snapshot).  levels must be 1; all NNFs of the call are held at once (FB_ERR_UNSUPPORTED
- * beyond the pair budget); not with FB_FLAG_LEARNED_INIT. */
+/* FB_FLAG_TRACKING (fb_interpolate, and fb_blend_window with the plain loss): the tracking
+ * of Sec. 3.5.1 -- the NNFs from one source frame (a keyframe; in a blend, a window's
+ * source) to consecutive target frames form a chain, and each pair's updating sequence
+ * gains, after propagation and before the random search, the matches of the pairs to the
+ * previous and next target frame at the same pixel (previous iteration's snapshot).  No
+ * pair maps a frame to itself, so a chain ends next to its source.  levels must be 1; all
+ * NNFs of the call are held at once (FB_ERR_UNSUPPORTED beyond the pair budget); not with
+ * FB_FLAG_LEARNED_INIT, FB_FLAG_BALANCED, FB_FLAG_FAST or FB_FLAG_ACCURATE. */
 #define FB_FLAG_TRACKING 0x20u
 
 /* Create a context on CUDA device `device` (made current for the call).  The context

@@ -217,6 +217,8 @@ int check_params(fb_ctx* ctx, const fb_params* p, int H, int W) {
         if (p->levels != 1) return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING requires levels == 1");
         if (p->flags & FB_FLAG_LEARNED_INIT)
             return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING does not combine with FB_FLAG_LEARNED_INIT");
+        if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_ACCURATE))
+            return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING applies to the plain loss and the direct sum");
     }
     if (p->flags & FB_FLAG_ACCURATE) {
         if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_LEARNED_INIT))
@@ -434,6 +436,20 @@ int run_nnf_accurate(fb_ctx* ctx, const Buffers& b, int H, int W, const fb_param
     *F_out = Fc;
     *E_out = Ec;
     return FB_OK;
+}
+
+// Sec. 3.5.1: a pair's chain neighbours are the pairs from the same source frame to the
+// frames before and after its target.  No pair maps a frame to itself (a keyframe, or the
+// source of a blend window), so chains end next to their source.  The indices are those of
+// the call's pair table, which the tracking kernel sees in one launch.
+void set_chain_neighbours(std::vector<PairDesc>& pairs) {
+    std::map<std::pair<int, int>, int> index;
+    for (size_t q = 0; q < pairs.size(); ++q) index[{pairs[q].src, pairs[q].tgt}] = static_cast<int>(q);
+    for (PairDesc& pd : pairs) {
+        auto a = index.find({pd.src, pd.tgt - 1}), b = index.find({pd.src, pd.tgt + 1});
+        pd.pad[0] = a == index.end() ? -1 : a->second;
+        pd.pad[1] = b == index.end() ? -1 : b->second;
+    }
 }
 
 // Group consecutive output jobs into chunks whose pairs fit the F/E budget.
@@ -1432,7 +1448,7 @@ int fb_nnf(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int 
         return fail(ctx, FB_ERR_ARG, "the improved loss needs the source style: use fb_nnf_balanced");
     if (p->flags & (FB_FLAG_FAST | FB_FLAG_ACCURATE))
         return fail(ctx, FB_ERR_ARG, "FB_FLAG_FAST and FB_FLAG_ACCURATE apply to fb_blend_window only");
-    if (p->flags & FB_FLAG_TRACKING) return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING applies to fb_interpolate only");
+    if (p->flags & FB_FLAG_TRACKING) return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING applies to fb_interpolate and fb_blend_window");
     DeviceGuard dg(ctx->device);
     for (const void* q : {static_cast<const void*>(src_guide), static_cast<const void*>(tgt_guide),
                           static_cast<const void*>(nnf_out), static_cast<const void*>(init_nnf),
@@ -1567,7 +1583,6 @@ int fb_blend_window(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles, i
         return fail(ctx, FB_ERR_ARG, "window must be odd and >= 1, got %d", window);
     if (!guides || !styles || !out)
         return fail(ctx, FB_ERR_ARG, "guides, styles and out must be non-NULL");
-    if (p->flags & FB_FLAG_TRACKING) return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING applies to fb_interpolate only");
     const int k = p->patch, M = (window - 1) / 2;
     if (p->flags & FB_FLAG_FAST) {
         const uint64_t k4 = static_cast<uint64_t>(k) * k * k * k;
@@ -1590,6 +1605,7 @@ int fb_blend_window(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles, i
         for (int j = lo; j <= hi; ++j)
             if (j != i) pairs.push_back(PairDesc{j, i, fb_pair_tag(j, i), j, 1u, {0, 0, 0}});
     }
+    if (p->flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
     DeviceGuard dg(ctx->device);
     return run_pipeline(ctx, guides, N, H, W, styles, N, pairs, jobs, p, out,
                         static_cast<cudaStream_t>(stream));
@@ -1646,17 +1662,7 @@ int fb_interpolate(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, cons
         }
         jobs[i] = j;
     }
-    if (p->flags & FB_FLAG_TRACKING) {
-        // Sec. 3.5.1: a pair's chain neighbours are the pairs from the same keyframe to the
-        // frames before and after its target (keys have no pairs, so chains end there).
-        std::map<std::pair<int, int>, int> index;
-        for (size_t q = 0; q < pairs.size(); ++q) index[{pairs[q].src, pairs[q].tgt}] = static_cast<int>(q);
-        for (PairDesc& pd : pairs) {
-            auto a = index.find({pd.src, pd.tgt - 1}), b = index.find({pd.src, pd.tgt + 1});
-            pd.pad[0] = a == index.end() ? -1 : a->second;
-            pd.pad[1] = b == index.end() ? -1 : b->second;
-        }
-    }
+    if (p->flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
     DeviceGuard dg(ctx->device);
     return run_pipeline(ctx, guides, N, H, W, key_styles, n_keys, pairs, jobs, p, out,
                         static_cast<cudaStream_t>(stream));

@@ -38,8 +38,18 @@ def test_tracking_neighbour_refs_count_chain_neighbours(N, keys):
     assert len(pairs) == w.pairs()
 
 
+@pytest.mark.parametrize("N,window", [(60, 15), (5, 15), (9, 3), (7, 5), (1, 7)])
+def test_tracking_neighbour_refs_of_a_blend(N, window):
+    w = dataclasses.replace(synth.WORKLOADS["blend_512"], N=N, window=window)
+    M = window // 2
+    pairs = {(j, i) for i in range(N) for j in range(max(0, i - M), min(N - 1, i + M) + 1) if j != i}
+    brute = sum(((src, tgt - 1) in pairs) + ((src, tgt + 1) in pairs) for src, tgt in pairs)
+    assert bench.tracking_neighbour_refs(w) == brute
+    assert len(pairs) == w.pairs()
+
+
 def test_mode_workloads_run_on_their_clip():
     assert bench.base_workload("tracking_1024x576") == "interp_1024x576"
-    for m in ("balanced_512", "fast_512", "accurate_512", "learned_512", "initnet_512"):
+    for m in ("balanced_512", "fast_512", "accurate_512", "learned_512", "initnet_512", "tracking_512"):
         assert bench.base_workload(m) == "blend_512"
     assert bench.base_workload("blend_512_16f") == "blend_512_16f"

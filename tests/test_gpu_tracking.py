@@ -1,4 +1,5 @@
-"""Tracking of Sec. 3.5.1 (FB_FLAG_TRACKING of fb_interpolate) on the GPU against the oracle."""
+"""Tracking of Sec. 3.5.1 (FB_FLAG_TRACKING of fb_interpolate and fb_blend_window) on the GPU
+against the oracle."""
 import numpy as np
 import pytest
 
@@ -60,6 +61,52 @@ def test_tracking_changes_the_result_where_chains_exist(fbp, ctx):
     assert not np.array_equal(plain.cpu().numpy(), track.cpu().numpy())
 
 
+BLEND_CASES = [
+    # N, H, W, k, window, iters, motion
+    (7, 40, 44, 5, 5, 2, "affine"),
+    (9, 33, 37, 7, 7, 2, "shift"),
+    (5, 24, 20, 3, 15, 3, "affine"),           # window wider than the clip
+    (6, 21, 26, 9, 3, 2, "affine"),            # chains of one pair
+    (4, 18, 19, 5, 5, 0, "shift"),             # no iterations
+]
+
+
+@pytest.mark.parametrize("N,H,W,k,window,iters,motion", BLEND_CASES)
+def test_tracking_blend_matches_oracle(fbp, ctx, N, H, W, k, window, iters, motion):
+    g, s = synth.small_clip(N, H, W, seed=N * 13 + W, motion=motion)
+    p = fbp.Params.make(k, iters, 1, 0, 17, flags=fbp.FB_FLAG_TRACKING)
+    out = fbp.fb_blend_window(ctx, cuda(g), cuda(s), window, p).cpu().numpy()
+    ref = oracle.blend_window_tracking(g, s, window, k, iters, seed=17)
+    assert np.abs(out - ref).max() <= 0.5 / 255
+    assert (out == ref).all()
+
+
+def test_tracking_blend_through_host_buffers(fbp, ctx):
+    import torch
+    g, s = synth.small_clip(6, 30, 34, seed=2, motion="affine")
+    p = fbp.Params.make(5, 2, 1, 0, 8, flags=fbp.FB_FLAG_TRACKING)
+    out = fbp.fb_blend_window(ctx, torch.from_numpy(g), torch.from_numpy(s), 5, p).numpy()
+    assert (out == oracle.blend_window_tracking(g, s, 5, 5, 2, seed=8)).all()
+
+
+def test_tracking_beyond_the_pair_budget_is_refused(fbp, ctx):
+    # Tracking couples every NNF of the call; a budget that splits the call into chunks
+    # is refused before any launch (the plain search runs it chunk by chunk).
+    g, s = synth.small_clip(8, 96, 96, seed=6, motion="affine")
+    gd, sd = cuda(g), cuda(s)
+    p = fbp.Params.make(5, 1, 1, 0, 2, flags=fbp.FB_FLAG_TRACKING)
+    ctx.set_pair_budget(1 << 20)     # the smallest budget: one output frame's 6 NNFs (864 KiB)
+    try:
+        n0 = ctx.launches
+        with pytest.raises(fbp.FastBlendError) as ei:
+            fbp.fb_blend_window(ctx, gd, sd, 7, p)
+        assert ei.value.status == fbp.FB_ERR_UNSUPPORTED and ctx.launches == n0
+        plain = fbp.fb_blend_window(ctx, gd, sd, 7, fbp.Params.make(5, 1, 1, 0, 2)).cpu().numpy()
+        assert (plain == oracle.blend_window(g, s, 7, 5, 1, seed=2)).all()
+    finally:
+        ctx.set_pair_budget(0)
+
+
 def test_tracking_argument_errors(fbp, ctx):
     import torch
     g = torch.zeros((4, 16, 16, 3), dtype=torch.uint8, device="cuda")
@@ -69,7 +116,12 @@ def test_tracking_argument_errors(fbp, ctx):
         lambda: fbp.fb_interpolate(ctx, g, [0, 3], g[:2], fbp.Params.make(5, 2, 2, flags=T)),
         lambda: fbp.fb_interpolate(ctx, g, [0, 3], g[:2],
                                    fbp.Params.make(5, 2, 1, flags=T | fbp.FB_FLAG_LEARNED_INIT)),
-        lambda: fbp.fb_blend_window(ctx, g, g, 3, fbp.Params.make(5, 2, 1, flags=T)),
+        lambda: fbp.fb_blend_window(ctx, g, g, 3, fbp.Params.make(5, 2, 2, flags=T)),
+        lambda: fbp.fb_blend_window(ctx, g, g, 3, fbp.Params.make(5, 2, 1, flags=T | fbp.FB_FLAG_BALANCED,
+                                                                  alpha=3)),
+        lambda: fbp.fb_blend_window(ctx, g, g, 3, fbp.Params.make(5, 2, 1, flags=T | fbp.FB_FLAG_FAST)),
+        lambda: fbp.fb_blend_window(ctx, g, g, 3, fbp.Params.make(5, 2, 1, flags=T | fbp.FB_FLAG_ACCURATE,
+                                                                  alpha=3)),
         lambda: fbp.fb_nnf(ctx, g[0], g[1], fbp.Params.make(5, 2, 1, flags=T)),
     ]
     for f in bad:
@@ -93,4 +145,17 @@ def test_tracking_interp_1024x576_full_size_sampled_frames(fbp, ctx):
     out = fbp.fb_interpolate(ctx, cuda(g), keys, cuda(ks), p).cpu().numpy()
     ref = oracle.interpolate_tracking(g, keys, ks, w.patch, 2, seed=w.seed)
     assert np.abs(out - ref).max() <= 0.5 / 255
+    assert (out == ref).all()
+
+
+@pytest.mark.slow
+def test_tracking_blend_512_frame_size(fbp, ctx):
+    """The 512x512 frame size of the headline blend at window 15, on a 9-frame clip whose
+    tracked chains the oracle finishes in seconds."""
+    w = synth.WORKLOADS["blend_512"]
+    g, s = synth.make_clip("blend_512")
+    g, s = np.ascontiguousarray(g[:9]), np.ascontiguousarray(s[:9])
+    p = fbp.Params.make(w.patch, 2, 1, 0, w.seed, flags=fbp.FB_FLAG_TRACKING)
+    out = fbp.fb_blend_window(ctx, cuda(g), cuda(s), w.window, p).cpu().numpy()
+    ref = oracle.blend_window_tracking(g, s, w.window, w.patch, 2, seed=w.seed)
     assert (out == ref).all()
