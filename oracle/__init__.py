@@ -104,6 +104,14 @@ def lib() -> ctypes.CDLL:
         L.fbref_blend_window_tracking.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int,
                                                   ctypes.c_int, ctypes.c_int, _P, _f32p]
         L.fbref_blend_window_tracking.restype = ctypes.c_int
+        L.fbref_nnf_segment.argtypes = [_u8p, _u8p, _u8p, _u8p, _u8p, ctypes.c_int, ctypes.c_int,
+                                        ctypes.c_int, _P, ctypes.c_uint32, ctypes.c_int, _u32p,
+                                        _u32p, _i32p, _i32p, _u32p]
+        L.fbref_nnf_segment.restype = ctypes.c_int
+        L.fbref_interpolate_aligned.argtypes = [_u8p, ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                                _i32p, _u8p, ctypes.c_int, _P, ctypes.c_uint32,
+                                                ctypes.c_int, _f32p]
+        L.fbref_interpolate_aligned.restype = ctypes.c_int
         L.fbref_blend_frame_accurate.argtypes = [_u8p, _u8p, ctypes.c_int, ctypes.c_int,
                                                  ctypes.c_int, ctypes.c_int, _P, ctypes.c_uint32,
                                                  ctypes.c_int, _f32p, _u8p, _i32p]
@@ -453,6 +461,45 @@ def nnf_chain(src, tgts, patch: int, iters: int, tags, r0: int = 0, seed: int = 
     if rc != 0:
         raise ValueError("fbref_nnf_chain: bad arguments")
     return F, E
+
+
+def nnf_segment(guide_l, guide_r, style_l, style_r, tgts, patch: int, iters: int, alpha: int,
+                tags_l, tags_r, tracking: bool = False, r0: int = 0, seed: int = 0, init=None):
+    """Coupled NNFs of Eq. 10 from keys l and r to the frames `tgts` (n, H, W, 3) between
+    them; returns (F (2, n, H, W, 2), E (2, n, H, W)), index 0 the left key's fields."""
+    gl, gr, sl, sr, tgts = (_u8(a) for a in (guide_l, guide_r, style_l, style_r, tgts))
+    n, H, W = tgts.shape[:3]
+    F = np.zeros((2, n, H, W, 2), np.int32)
+    E = np.zeros((2, n, H, W), np.uint32)
+    tl = np.ascontiguousarray(tags_l, dtype=np.uint32)
+    tr = np.ascontiguousarray(tags_r, dtype=np.uint32)
+    p = params(patch, iters, 1, r0, seed)
+    ip = None
+    if init is not None:
+        init = np.ascontiguousarray(init, dtype=np.int32)
+        ip = _ptr(init, _i32p)
+    rc = lib().fbref_nnf_segment(_ptr(gl, _u8p), _ptr(gr, _u8p), _ptr(sl, _u8p), _ptr(sr, _u8p),
+                                 _ptr(tgts, _u8p), n, H, W, ctypes.byref(p), alpha, int(tracking),
+                                 _ptr(tl, _u32p), _ptr(tr, _u32p), ip, _ptr(F, _i32p),
+                                 _ptr(E, _u32p))
+    if rc != 0:
+        raise ValueError("fbref_nnf_segment: bad arguments")
+    return F, E
+
+
+def interpolate_aligned(guides, key_idx, key_styles, patch: int, iters: int, alpha: int,
+                        tracking: bool = False, seed: int = 0):
+    g, ks = _u8(guides), _u8(key_styles)
+    N, H, W = g.shape[:3]
+    keys = np.ascontiguousarray(key_idx, dtype=np.int32)
+    out = np.zeros((N, H, W, 3), np.float32)
+    p = params(patch, iters, 1, 0, seed)
+    rc = lib().fbref_interpolate_aligned(_ptr(g, _u8p), N, H, W, _ptr(keys, _i32p),
+                                         _ptr(ks, _u8p), len(keys), ctypes.byref(p), alpha,
+                                         int(tracking), _ptr(out, _f32p))
+    if rc != 0:
+        raise ValueError("fbref_interpolate_aligned: bad arguments")
+    return out
 
 
 def interpolate_tracking(guides, key_idx, key_styles, patch: int, iters: int, seed: int = 0):

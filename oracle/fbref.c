@@ -20,6 +20,17 @@
  *                   closed form on known-shift clips, linearity, window truncation.
  *   Combine (Sec. 3.5.2)  keys copied, endpoint weights, weights sum to one,
  *                   closed form on known-shift clips.
+ *   Improved loss, balanced mode (Sec. 3.4)  alpha / style-term limits reducing to
+ *                   Eq. 1, S^ of identity and shift fields, monotone energy.
+ *   Fast mode (Sec. 3.4, Algs. 3-5)  direct sums on identity-NNF clips, Eq. 6 split
+ *                   identity, table and query structure against brute force.
+ *   Accurate mode (Sec. 3.4)  T^ rounding, self term, reduction cases, monotone energy.
+ *   Tracking (Sec. 3.5.1)  runs of one frame reduce to the plain search, a neighbour's
+ *                   match handed over, monotone energy, Eq. 9 with constant keys, the
+ *                   blend reductions (window 3, no iterations) and its composition.
+ *   Alignment (Sec. 3.5.2, Eq. 10)  constant key styles reduce to the plain (or tracked)
+ *                   search, brute-force initial loss, side symmetry, monotone coupled
+ *                   loss, Eq. 9 with constant keys and its composition.
  * Parity unpinned: none of the functions above; end-to-end visual quality against
  * the paper's human study cannot be pinned (no data).
  */
@@ -1030,6 +1041,196 @@ int fbref_interpolate_tracking(const uint8_t *guides, int N, int H, int W,
             }
             free(tags); free(F);
         }
+    }
+    for (int i = 0; i < N; ++i) {
+        float d = (float)den[i];
+        for (size_t t = 0; t < fsz; ++t) out[(size_t)i * fsz + t] = (float)acc[(size_t)i * fsz + t] / d;
+    }
+    free(acc); free(den); free(V);
+    return rc;
+}
+
+/* ------------------------------------------------------------------------------ */
+/* Sec. 3.5.2, alignment (Eq. 10): between keyframes l < r the NNFs F_l = NNF(l -> i) and */
+/* F_r = NNF(r -> i) of every frame l < i < r are coupled.  The loss of a candidate u  */
+/* of F_l at pixel x is                                                                 */
+/*   alpha * Eq.1(G_l at u, G_i at x) + Eq.1(S_l at u, S_r at F_r(x)),                  */
+/* the second term a patch difference between the two keyframes' styles (the pairwise  */
+/* patch error), and symmetrically for F_r.  F_r(x) is the partner's snapshot of the   */
+/* previous iteration (Jacobi), so the incumbent's loss is re-evaluated at the start of */
+/* every iteration.  With tracking (Sec. 3.5.1) each side's n NNFs also form a chain.   */
+/* Candidate order, random streams (tags_l[m] = tag of (l -> l+1+m), tags_r[m] of      */
+/* (r -> l+1+m)) and strict acceptance as fbref_nnf; one level.  Fields and errors are */
+/* laid out left chain first (index s * n + m).  With iters = 0, err_out holds the      */
+/* coupled loss of the initial fields.                                                  */
+/* ------------------------------------------------------------------------------ */
+static uint32_t aligned_loss(const uint8_t *gs, const uint8_t *gt, const uint8_t *ss,
+                             const uint8_t *so, int H, int W, int k, uint32_t alpha, int ur, int uc,
+                             int xr, int xc, int pr, int pc)
+{
+    return alpha * fbref_ssd(gs, gt, H, W, k, ur, uc, xr, xc) +
+           fbref_ssd(ss, so, H, W, k, ur, uc, pr, pc);
+}
+
+int fbref_nnf_segment(const uint8_t *guide_l, const uint8_t *guide_r, const uint8_t *style_l,
+                      const uint8_t *style_r, const uint8_t *tgts, int n, int H, int W,
+                      const fbref_params *p, uint32_t alpha, int tracking, const uint32_t *tags_l,
+                      const uint32_t *tags_r, const int32_t *init, int32_t *nnf_out,
+                      uint32_t *err_out)
+{
+    if (!params_ok(p, H, W) || p->levels != 1 || n < 1 || alpha > 255 || !guide_l || !guide_r ||
+        !style_l || !style_r || !tgts || !tags_l || !tags_r || !nnf_out)
+        return -1;
+    const int k = p->patch, h = H, w = W;
+    const size_t npx = (size_t)H * W, fsz = npx * 3, nf = (size_t)2 * n;
+    const uint8_t *G[2] = {guide_l, guide_r}, *S[2] = {style_l, style_r};
+    const uint32_t *tags[2] = {tags_l, tags_r};
+    int32_t *F = (int32_t *)malloc(nf * npx * 2 * sizeof(int32_t));
+    int32_t *Fn = (int32_t *)malloc(nf * npx * 2 * sizeof(int32_t));
+    uint32_t *E = (uint32_t *)malloc(nf * npx * sizeof(uint32_t));
+    for (int sd = 0; sd < 2; ++sd)
+        for (int m = 0; m < n; ++m)
+            for (size_t x = 0; x < npx; ++x) {
+                size_t o = (((size_t)sd * n + m) * npx + x) * 2;
+                if (init) {
+                    F[o] = clampi(init[o], 0, h - 1);
+                    F[o + 1] = clampi(init[o + 1], 0, w - 1);
+                } else {
+                    random_match(p->seed, (uint32_t)x, tags[sd][m], 0, h, w, &F[o], &F[o + 1]);
+                }
+            }
+    const int r0 = p->r0 > 0 ? p->r0 : (h > w ? h : w);
+    static const int dirs[4][2] = {{-1, 0}, {1, 0}, {0, -1}, {0, 1}};
+    const int rounds = p->iters > 0 ? p->iters : 1;
+    for (int it = 0; it < rounds; ++it) {
+        for (int sd = 0; sd < 2; ++sd) {
+            const uint8_t *Gs = G[sd], *Ss = S[sd], *So = S[1 - sd];
+            for (int m = 0; m < n; ++m) {
+                const uint8_t *T = tgts + (size_t)m * fsz;
+                const int32_t *Fm = F + ((size_t)sd * n + m) * npx * 2;
+                const int32_t *Fo = F + ((size_t)(1 - sd) * n + m) * npx * 2;   /* the partner */
+                int32_t *Fnm = Fn + ((size_t)sd * n + m) * npx * 2;
+                uint32_t *Em = E + ((size_t)sd * n + m) * npx;
+#pragma omp parallel for schedule(static)
+                for (int r = 0; r < h; ++r) {
+                    for (int c = 0; c < w; ++c) {
+                        size_t x = (size_t)r * w + c;
+                        const int pr = Fo[2 * x], pc = Fo[2 * x + 1];
+                        int32_t br = Fm[2 * x], bc = Fm[2 * x + 1];
+                        uint32_t be = aligned_loss(Gs, T, Ss, So, h, w, k, alpha, br, bc, r, c, pr, pc);
+                        if (p->iters > 0) {
+                            for (int d = 0; d < 4; ++d) {
+                                int nr = r + dirs[d][0], nc = c + dirs[d][1];
+                                if (nr < 0 || nr >= h || nc < 0 || nc >= w) continue;
+                                size_t q = (size_t)nr * w + nc;
+                                int cr = clampi(Fm[2 * q] - dirs[d][0], 0, h - 1);
+                                int cc = clampi(Fm[2 * q + 1] - dirs[d][1], 0, w - 1);
+                                uint32_t e = aligned_loss(Gs, T, Ss, So, h, w, k, alpha, cr, cc, r, c, pr, pc);
+                                if (e < be) { be = e; br = cr; bc = cc; }
+                            }
+                            for (int nb = m - 1; tracking && nb <= m + 1; nb += 2) {
+                                if (nb < 0 || nb >= n) continue;
+                                const int32_t *Fb = F + (((size_t)sd * n + nb) * npx + x) * 2;
+                                uint32_t e = aligned_loss(Gs, T, Ss, So, h, w, k, alpha, Fb[0], Fb[1], r, c, pr, pc);
+                                if (e < be) { be = e; br = Fb[0]; bc = Fb[1]; }
+                            }
+                            for (int t = 0; (r0 >> t) >= 1; ++t) {
+                                int rad = r0 >> t;
+                                int32_t dr, dc;
+                                fbref_rs_offset(p->seed, (uint32_t)x, tags[sd][m], 0, it, t, rad, &dr, &dc);
+                                int cr = clampi(br + dr, 0, h - 1);
+                                int cc = clampi(bc + dc, 0, w - 1);
+                                uint32_t e = aligned_loss(Gs, T, Ss, So, h, w, k, alpha, cr, cc, r, c, pr, pc);
+                                if (e < be) { be = e; br = cr; bc = cc; }
+                            }
+                        }
+                        Fnm[2 * x] = br;
+                        Fnm[2 * x + 1] = bc;
+                        Em[x] = be;
+                    }
+                }
+            }
+        }
+        int32_t *tf = F; F = Fn; Fn = tf;
+    }
+    memcpy(nnf_out, F, nf * npx * 2 * sizeof(int32_t));
+    if (err_out) memcpy(err_out, E, nf * npx * sizeof(uint32_t));
+    free(F); free(Fn); free(E);
+    return 0;
+}
+
+/* Sec. 3.5.2 with the alignment loss of Eq. 10 (alpha the guide weight; tracking
+ * optional): the frames between two keys take fbref_nnf_segment's coupled fields; frames
+ * before the first key or after the last have one key and no partner, and take the
+ * plain loss (fbref_nnf, or a tracked chain).  Output: the Eq. 9 combination exactly as
+ * fbref_interpolate. */
+int fbref_interpolate_aligned(const uint8_t *guides, int N, int H, int W, const int32_t *key_idx,
+                              const uint8_t *key_styles, int n_keys, const fbref_params *p,
+                              uint32_t alpha, int tracking, float *out)
+{
+    if (!params_ok(p, H, W) || p->levels != 1 || alpha > 255 || N < 1 || N > 65535 || n_keys < 1)
+        return -1;
+    for (int m = 0; m < n_keys; ++m) {
+        if (key_idx[m] < 0 || key_idx[m] >= N) return -1;
+        if (m > 0 && key_idx[m] <= key_idx[m - 1]) return -1;
+    }
+    const int k = p->patch;
+    const size_t npx = (size_t)H * W, fsz = npx * 3;
+    uint32_t *acc = (uint32_t *)calloc((size_t)N * fsz, sizeof(uint32_t));
+    uint32_t *den = (uint32_t *)calloc((size_t)N, sizeof(uint32_t));
+    uint32_t *V = (uint32_t *)malloc(fsz * sizeof(uint32_t));
+    int rc = 0;
+    for (int m = 0; m < n_keys; ++m) {
+        const int a = key_idx[m];
+        for (size_t t = 0; t < fsz; ++t) acc[(size_t)a * fsz + t] = (uint32_t)(k * k) * key_styles[(size_t)m * fsz + t];
+        den[a] = (uint32_t)(255 * k * k);
+    }
+    /* runs served by one key: before the first key (served by key 0) and after the last */
+    for (int side = 0; side < 2 && rc == 0; ++side) {
+        const int m = side == 0 ? 0 : n_keys - 1, a = key_idx[m];
+        const int lo = side == 0 ? 0 : a + 1, hi = side == 0 ? a - 1 : N - 1;
+        if (lo > hi) continue;
+        const int n = hi - lo + 1;
+        int32_t *Fs = (int32_t *)malloc((size_t)n * npx * 2 * sizeof(int32_t));
+        uint32_t *tags = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+        for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(a, lo + q);
+        if (tracking)
+            rc = fbref_nnf_chain(guides + (size_t)a * fsz, guides + (size_t)lo * fsz, n, H, W, p, tags, NULL, Fs, NULL);
+        for (int q = 0; q < n && rc == 0; ++q) {
+            if (!tracking)
+                rc = fbref_nnf(guides + (size_t)a * fsz, guides + (size_t)(lo + q) * fsz, H, W, p, tags[q], NULL,
+                               Fs + (size_t)q * npx * 2, NULL);
+            if (rc) break;
+            fbref_remap_sum(key_styles + (size_t)m * fsz, Fs + (size_t)q * npx * 2, H, W, k, V);
+            for (size_t t = 0; t < fsz; ++t) acc[(size_t)(lo + q) * fsz + t] += V[t];
+            den[lo + q] = (uint32_t)(255 * k * k);
+        }
+        free(Fs); free(tags);
+    }
+    /* segments between consecutive keys: coupled fields */
+    for (int m = 0; m + 1 < n_keys && rc == 0; ++m) {
+        const int l = key_idx[m], r = key_idx[m + 1], n = r - l - 1;
+        if (n < 1) continue;
+        int32_t *Fs = (int32_t *)malloc((size_t)2 * n * npx * 2 * sizeof(int32_t));
+        uint32_t *tl = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+        uint32_t *tr = (uint32_t *)malloc((size_t)n * sizeof(uint32_t));
+        for (int q = 0; q < n; ++q) {
+            tl[q] = fbref_pair_tag(l, l + 1 + q);
+            tr[q] = fbref_pair_tag(r, l + 1 + q);
+        }
+        rc = fbref_nnf_segment(guides + (size_t)l * fsz, guides + (size_t)r * fsz,
+                               key_styles + (size_t)m * fsz, key_styles + (size_t)(m + 1) * fsz,
+                               guides + (size_t)(l + 1) * fsz, n, H, W, p, alpha, tracking, tl, tr, NULL,
+                               Fs, NULL);
+        for (int q = 0; q < n && rc == 0; ++q) {
+            const int i = l + 1 + q;
+            fbref_remap_sum(key_styles + (size_t)m * fsz, Fs + (size_t)q * npx * 2, H, W, k, V);
+            for (size_t t = 0; t < fsz; ++t) acc[(size_t)i * fsz + t] += (uint32_t)(r - i) * V[t];
+            fbref_remap_sum(key_styles + (size_t)(m + 1) * fsz, Fs + (size_t)(n + q) * npx * 2, H, W, k, V);
+            for (size_t t = 0; t < fsz; ++t) acc[(size_t)i * fsz + t] += (uint32_t)(i - l) * V[t];
+            den[i] = (uint32_t)(255 * k * k) * (uint32_t)(r - l);
+        }
+        free(Fs); free(tl); free(tr);
     }
     for (int i = 0; i < N; ++i) {
         float d = (float)den[i];

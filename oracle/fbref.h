@@ -101,6 +101,15 @@ int fbref_nnf_chain(const uint8_t *src, const uint8_t *tgts, int n, int H, int W
 int fbref_interpolate_tracking(const uint8_t *guides, int N, int H, int W,
                                const int32_t *key_idx, const uint8_t *key_styles, int n_keys,
                                const fbref_params *p, float *out);
+/* Sec. 3.5.2 alignment (Eq. 10), one level: see fbref.c. */
+int fbref_nnf_segment(const uint8_t *guide_l, const uint8_t *guide_r, const uint8_t *style_l,
+                      const uint8_t *style_r, const uint8_t *tgts, int n, int H, int W,
+                      const fbref_params *p, uint32_t alpha, int tracking, const uint32_t *tags_l,
+                      const uint32_t *tags_r, const int32_t *init, int32_t *nnf_out,
+                      uint32_t *err_out);
+int fbref_interpolate_aligned(const uint8_t *guides, int N, int H, int W, const int32_t *key_idx,
+                              const uint8_t *key_styles, int n_keys, const fbref_params *p,
+                              uint32_t alpha, int tracking, float *out);
 int fbref_blend_window_tracking(const uint8_t *guides, const uint8_t *styles, int N, int H, int W,
                                 int window, const fbref_params *p, float *out);
 

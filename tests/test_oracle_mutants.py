@@ -5,7 +5,7 @@ the paper can get wrong (a dropped term, a wrong sign, an index of the wrong axi
 non-strict acceptance, an off-by-one bound or constant).  It is compiled into a
 temporary directory and the pin suites (tests/test_oracle_pins.py,
 tests/test_oracle_balanced.py, tests/test_oracle_fast.py, tests/test_oracle_accurate.py,
-tests/test_oracle_tracking.py) are run against it:
+tests/test_oracle_tracking.py, tests/test_oracle_alignment.py) are run against it:
 every mutant must make at least one pin fail.  The oracle's own source is not touched.
 """
 import os
@@ -76,6 +76,15 @@ MUTANTS = {
     "blend_tracking_pair_stream_reversed": ("for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(j, lo + q);", "for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(lo + q, j);", None),
     "blend_tracking_window_short_by_one": ("float den = (float)(255 * k * k * (hi - lo + 1));\n        for (size_t t = 0; t < fsz; ++t) out[(size_t)i * fsz + t]",
                                            "float den = (float)(255 * k * k * (hi - lo + 2));\n        for (size_t t = 0; t < fsz; ++t) out[(size_t)i * fsz + t]", None),
+    "align_partner_is_own_field": ("const int32_t *Fo = F + ((size_t)(1 - sd) * n + m) * npx * 2;", "const int32_t *Fo = F + ((size_t)sd * n + m) * npx * 2;", None),
+    "align_pairwise_term_own_style": ("*Ss = S[sd], *So = S[1 - sd];", "*Ss = S[sd], *So = S[sd];", None),
+    "align_guide_weight_dropped": ("    return alpha * fbref_ssd(gs, gt, H, W, k, ur, uc, xr, xc) +\n           fbref_ssd(ss, so, H, W, k, ur, uc, pr, pc);",
+                                   "    return fbref_ssd(gs, gt, H, W, k, ur, uc, xr, xc) +\n           fbref_ssd(ss, so, H, W, k, ur, uc, pr, pc);", None),
+    "align_pairwise_term_at_the_target_pixel": ("fbref_ssd(ss, so, H, W, k, ur, uc, pr, pc);", "fbref_ssd(ss, so, H, W, k, ur, uc, xr, xc);", None),
+    "align_tracking_neighbour_from_partner_side": ("const int32_t *Fb = F + (((size_t)sd * n + nb) * npx + x) * 2;", "const int32_t *Fb = F + (((size_t)(1 - sd) * n + nb) * npx + x) * 2;", None),
+    "align_random_search_partner_stream": ("fbref_rs_offset(p->seed, (uint32_t)x, tags[sd][m], 0, it, t, rad, &dr, &dc);", "fbref_rs_offset(p->seed, (uint32_t)x, tags[1 - sd][m], 0, it, t, rad, &dr, &dc);", None),
+    "align_segment_tags_swapped": ("tr[q] = fbref_pair_tag(r, l + 1 + q);", "tr[q] = fbref_pair_tag(l + 1 + q, r);", None),
+    "align_eq9_weights_swapped": ("acc[(size_t)i * fsz + t] += (uint32_t)(r - i) * V[t];", "acc[(size_t)i * fsz + t] += (uint32_t)(i - l) * V[t];", None),
     "accurate_tbar_rounds_down": ("tbar[t] = (uint8_t)((acc[t] + den_t / 2) / den_t);", "tbar[t] = (uint8_t)(acc[t] / den_t);", None),
     "accurate_tbar_without_self_term": ("        for (size_t t = 0; t < fsz; ++t) acc[t] = kk * Si[t];\n        for (int m = 0; m < np; ++m) {\n            fbref_remap_sum",
                                         "        for (size_t t = 0; t < fsz; ++t) acc[t] = 0;\n        for (int m = 0; m < np; ++m) {\n            fbref_remap_sum", None),
@@ -142,7 +151,8 @@ def run_mutant(name: str, workdir: str):
                           os.path.join(ROOT, "tests", "test_oracle_balanced.py"),
                           os.path.join(ROOT, "tests", "test_oracle_fast.py"),
                           os.path.join(ROOT, "tests", "test_oracle_accurate.py"),
-                          os.path.join(ROOT, "tests", "test_oracle_tracking.py")],
+                          os.path.join(ROOT, "tests", "test_oracle_tracking.py"),
+                          os.path.join(ROOT, "tests", "test_oracle_alignment.py")],
                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
     return res.returncode, res.stdout[-1500:]
 
