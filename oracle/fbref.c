@@ -20,11 +20,13 @@
  *                   closed form on known-shift clips, linearity, window truncation.
  *   Combine (Sec. 3.5.2)  keys copied, endpoint weights, weights sum to one,
  *                   closed form on known-shift clips.
- *   Improved loss, balanced mode (Sec. 3.4)  alpha / style-term limits reducing to
- *                   Eq. 1, S^ of identity and shift fields, monotone energy.
- *   Fast mode (Sec. 3.4, Algs. 3-5)  direct sums on identity-NNF clips, Eq. 6 split
- *                   identity, table and query structure against brute force.
- *   Accurate mode (Sec. 3.4)  T^ rounding, self term, reduction cases, monotone energy.
+ *   Improved loss, balanced mode (Sec. 3.4)  constant styles reduce to Eq. 1 scaled by
+ *                   alpha, true-field fixed point, S^ rounding and refresh, returned
+ *                   error = loss of the returned field, constant blends.
+ *   Fast mode (Sec. 3.4, Algs. 3-5)  constants for every window, window one, linearity
+ *                   in the styles, known-shift closed form.
+ *   Accurate mode (Sec. 3.4)  per-frame constant styles reduce to the plain fields,
+ *                   T-bar rounding and refresh, constant blends.
  *   Tracking (Sec. 3.5.1)  runs of one frame reduce to the plain search, a neighbour's
  *                   match handed over, monotone energy, Eq. 9 with constant keys, the
  *                   blend reductions (window 3, no iterations) and its composition.
