@@ -57,7 +57,8 @@ def parse_args(argv=None):
     ap.add_argument("--workload", default="blend_512",
                     choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512", "initnet_512",
                                                        "balanced_512", "fast_512", "accurate_512",
-                                                       "tracking_1024x576", "tracking_512"])
+                                                       "tracking_1024x576", "tracking_512",
+                                                       "aligned_1024x576"])
     ap.add_argument("--window", type=int, default=0,
                     help="override the blend window of the headline-clip workloads (odd)")
     ap.add_argument("--learned-iters", type=int, default=2,
@@ -197,7 +198,7 @@ class ClockSampler:
 TRACKING_BLEND_SAMPLE_FRAMES = 5
 
 
-def tracking_sample(w: synth.Workload, g, s):
+def tracking_sample(w: synth.Workload, g, s, aligned=False):
     """A bounded oracle sample of a tracking workload: the oracle couples every NNF of a
     chain, so one output frame costs the whole clip.  Interpolation: the clip's first 4
     frames of the same size with keys 0 and 3 (2 interpolated frames, 4 tracked NNFs in
@@ -206,7 +207,8 @@ def tracking_sample(w: synth.Workload, g, s):
     if w.mode == "blend":
         n = TRACKING_BLEND_SAMPLE_FRAMES
         return np.ascontiguousarray(g[:n]), np.ascontiguousarray(s[:n]), None
-    return np.ascontiguousarray(g[:4]), np.ascontiguousarray(np.stack([s[0], s[0]])), [0, 3]
+    return (np.ascontiguousarray(g[:4]),
+            np.ascontiguousarray(np.stack([s[0], s[1 if aligned else 0]])), [0, 3])
 
 
 def tracking_sample_outputs(w: synth.Workload) -> int:
@@ -214,12 +216,15 @@ def tracking_sample_outputs(w: synth.Workload) -> int:
 
 
 def oracle_frame_seconds(w: synth.Workload, g, s, frames, alpha=None, fast=False, accurate=False,
-                         tracking=False):
+                         tracking=False, aligned=False):
     import oracle
     t0 = time.perf_counter()
     if tracking:
-        g4, k4, keys = tracking_sample(w, g, s)
-        if w.mode == "blend":
+        g4, k4, keys = tracking_sample(w, g, s, aligned)
+        if aligned:
+            oracle.interpolate_aligned(g4, keys, k4, w.patch, w.iters, alpha, tracking=True,
+                                       seed=w.seed)
+        elif w.mode == "blend":
             oracle.blend_window_tracking(g4, k4, w.window, w.patch, w.iters, seed=w.seed)
         else:
             oracle.interpolate_tracking(g4, keys, k4, w.patch, w.iters, seed=w.seed)
@@ -245,10 +250,10 @@ def sample_frames(w: synth.Workload, n: int):
 
 
 def cpu_baseline(w: synth.Workload, g, s, n_frames: int, alpha=None, fast=False, accurate=False,
-                 tracking=False):
+                 tracking=False, aligned=False):
     import oracle
     if tracking:
-        secs = oracle_frame_seconds(w, g, s, [], tracking=True)
+        secs = oracle_frame_seconds(w, g, s, [], alpha, tracking=True, aligned=aligned)
         return {"value": tracking_sample_outputs(w) / secs, "unit": "frames/s",
                 "cores": oracle.num_threads(), "kind": "oracle",
                 "sample": (f"the clip's first {TRACKING_BLEND_SAMPLE_FRAMES} frames ({w.H}x{w.W}), "
@@ -257,7 +262,9 @@ def cpu_baseline(w: synth.Workload, g, s, n_frames: int, alpha=None, fast=False,
                            f"tracked NNFs (windows truncated by the sample's length)"
                            if w.mode == "blend" else
                            f"the clip's first 4 frames ({w.H}x{w.W}) with keys 0 and 3: 2 "
-                           f"interpolated frames, 4 tracked NNFs")
+                           f"interpolated frames, 4 tracked NNFs"
+                           + (" coupled by the Eq. 10 alignment loss (the two keys styled with "
+                              "the clip's two key styles)" if aligned else ""))
                           + f"; C oracle, OpenMP, {secs:.1f} s"}
     frames = sample_frames(w, n_frames)
     secs = oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate)
@@ -284,16 +291,18 @@ def run_reference(args):
             import dataclasses
             w = dataclasses.replace(w, window=args.window)
         g, s = make_inputs(w, w.seed)
-    alpha = BALANCED_ALPHA if args.workload in ("balanced_512", "accurate_512") else None
+    alpha = (BALANCED_ALPHA if args.workload in ("balanced_512", "accurate_512", "aligned_1024x576")
+             else None)
     fast = args.workload == "fast_512"
     accurate = args.workload == "accurate_512"
-    tracking = args.workload in ("tracking_1024x576", "tracking_512")
+    aligned = args.workload == "aligned_1024x576"
+    tracking = args.workload in ("tracking_1024x576", "tracking_512") or aligned
     frames = sample_frames(w, 1)
     for _ in range(args.warmup):
-        oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate, tracking)
+        oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate, tracking, aligned)
     total = 0.0
     for _ in range(args.steps):
-        total += oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate, tracking)
+        total += oracle_frame_seconds(w, g, s, frames, alpha, fast, accurate, tracking, aligned)
     n_out = tracking_sample_outputs(w) if tracking else len(frames)
     value = args.steps * n_out / total
     line = {
@@ -307,7 +316,8 @@ def run_reference(args):
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": oracle.num_threads(),
                          "kind": "oracle",
                          "sample": ("each step interpolates frames 1-2 of the clip's first 4 "
-                                    "frames with keys 0 and 3 (tracking couples whole chains)"
+                                    "frames with keys 0 and 3 (tracking couples whole chains"
+                                    + (", alignment couples the two keys' NNFs)" if aligned else ")")
                                     if tracking and w.mode != "blend" else
                                     f"each step blends the clip's first {TRACKING_BLEND_SAMPLE_FRAMES} "
                                     "frames (tracking couples whole chains)" if tracking else
@@ -333,7 +343,7 @@ def base_workload(name: str) -> str:
     if name in ("balanced_512", "learned_512", "initnet_512", "fast_512", "accurate_512",
                 "tracking_512"):
         return "blend_512"
-    if name == "tracking_1024x576":
+    if name in ("tracking_1024x576", "aligned_1024x576"):
         return "interp_1024x576"
     return name
 
@@ -357,6 +367,13 @@ def tracking_neighbour_refs(w: synth.Workload) -> int:
     return refs
 
 
+def aligned_pairs(w: synth.Workload) -> int:
+    """Pairs that carry the Eq. 10 coupled loss: both pairs of every frame strictly
+    between two keys."""
+    keys = list(w.keys)
+    return 2 * sum(b - a - 1 for a, b in zip(keys[:-1], keys[1:]))
+
+
 def run_gpu(args):
     import torch
 
@@ -370,7 +387,8 @@ def run_gpu(args):
     balanced = args.workload == "balanced_512"
     fast = args.workload == "fast_512"
     accurate = args.workload == "accurate_512"
-    tracking = args.workload in ("tracking_1024x576", "tracking_512")
+    aligned = args.workload == "aligned_1024x576"
+    tracking = args.workload in ("tracking_1024x576", "tracking_512") or aligned
     w = synth.WORKLOADS[base_workload(args.workload)]
     if args.window and w.mode == "blend":
         import dataclasses
@@ -385,7 +403,9 @@ def run_gpu(args):
         params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_ACCURATE,
                                  alpha=BALANCED_ALPHA)
     if tracking:
-        params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_TRACKING)
+        params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed,
+                                 flags=fbp.FB_FLAG_TRACKING | (fbp.FB_FLAG_ALIGN if aligned else 0),
+                                 alpha=BALANCED_ALPHA if aligned else 0)
     fast_info = None
     if fast:
         params = fbp.Params.make(w.patch, w.iters, 1, 0, w.seed, flags=fbp.FB_FLAG_FAST)
@@ -494,6 +514,8 @@ def run_gpu(args):
         ops = ops * fast_info["nnfs"] // w.pairs()   # the fast mode computes fewer NNFs
     if ops and tracking:
         ops += tracking_neighbour_refs(w) * w.H * w.W * 3 * w.patch * w.patch
+    if ops and aligned:
+        ops = ops * (2 * aligned_pairs(w) + (w.pairs() - aligned_pairs(w))) // w.pairs()
     if fast:
         # context: the direct window sum of the same clip and window, one untimed-by-the-
         # contract measurement with CUDA events
@@ -517,6 +539,8 @@ def run_gpu(args):
                                            "improved loss)" if balanced else
                                            "nnf_iter_balanced (Alg. 1 Jacobi iteration, Sec. 3.4 "
                                            "mean-remap loss)" if accurate else
+                                           "nnf_iter_align (Alg. 1 Jacobi iteration, Eq. 10 "
+                                           "alignment loss + Sec. 3.5.1 tracking)" if aligned else
                                            "nnf_iter_track (Alg. 1 Jacobi iteration with the "
                                            "tracking of Sec. 3.5.1)" if tracking else
                                            "nnf_iter (Alg. 1 Jacobi iteration)"),
@@ -551,6 +575,9 @@ def run_gpu(args):
                                 "blending tables and interval queries (Algs. 3-5)" if fast else
                                 "accurate blend all-pairs 60x512x512 k5 w15 n6: Sec. 3.4 mean-remap "
                                 f"alignment loss, alpha {BALANCED_ALPHA}" if accurate else
+                                "aligned + tracking interpolation 48x576x1024 k7 n8 keys 0,47: Eq. 10 "
+                                f"alignment loss (alpha {BALANCED_ALPHA}) and Sec. 3.5.1 tracking"
+                                if aligned else
                                 "tracking interpolation 48x576x1024 k7 n8 keys 0,47: Sec. 3.5.1 "
                                 "chain-neighbour candidates" if tracking and w.mode != "blend" else
                                 f"tracking blend all-pairs 60x512x512 k5 w{w.window} n6: Sec. 3.5.1 "
@@ -576,8 +603,8 @@ def run_gpu(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(w, g, s, args.cpu_sample_frames,
-                                            BALANCED_ALPHA if balanced or accurate else None, fast,
-                                            accurate, tracking)
+                                            BALANCED_ALPHA if balanced or accurate or aligned else None,
+                                            fast, accurate, tracking, aligned)
     if rank == 0:
         print(json.dumps(line))
     ctx.close()

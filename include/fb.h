@@ -109,6 +109,16 @@ typedef struct fb_params {
  * NNFs of the call are held at once (FB_ERR_UNSUPPORTED beyond the pair budget); not with
  * FB_FLAG_LEARNED_INIT, FB_FLAG_BALANCED, FB_FLAG_FAST or FB_FLAG_ACCURATE. */
 #define FB_FLAG_TRACKING 0x20u
+/* FB_FLAG_ALIGN (fb_interpolate only): the alignment loss of Sec. 3.5.2 (Eq. 10).  For a
+ * frame i between keys l < i < r the NNFs F_l (key l -> i) and F_r (key r -> i) are
+ * coupled: a candidate u of F_l costs
+ *   alpha * Eq.1(G_l at u, G_i at x) + Eq.1(S_l at u, S_r at F_r(x)),
+ * the second term the pairwise patch error between the two keyframe styles, with F_r(x)
+ * the partner's match of the previous iteration (Jacobi); symmetrically for F_r.  Frames
+ * outside the key range have one key and take the plain loss.  alpha (fb_params.alpha)
+ * in [0, 255]; levels must be 1; combines with FB_FLAG_TRACKING only (not with
+ * FB_FLAG_REPORT_ENERGY: the stored errors mix the two losses). */
+#define FB_FLAG_ALIGN 0x40u
 
 /* Create a context on CUDA device `device` (made current for the call).  The context
  * allocates scratch lazily and keeps it for reuse until fb_ctx_destroy. */

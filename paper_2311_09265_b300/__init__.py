@@ -40,6 +40,7 @@ FB_FLAG_BALANCED = 0x4
 FB_FLAG_FAST = 0x8
 FB_FLAG_ACCURATE = 0x10
 FB_FLAG_TRACKING = 0x20
+FB_FLAG_ALIGN = 0x40
 
 FB_BATCH_NO_GRAPH = 0x1
 

@@ -211,8 +211,15 @@ int check_params(fb_ctx* ctx, const fb_params* p, int H, int W) {
     if (p->r0 < 0 || p->r0 > (1 << 20))
         return fail(ctx, FB_ERR_ARG, "r0 must be in [0, 2^20], got %d", p->r0);
     if (p->flags & ~(FB_FLAG_LEARNED_INIT | FB_FLAG_REPORT_ENERGY | FB_FLAG_BALANCED | FB_FLAG_FAST |
-                     FB_FLAG_ACCURATE | FB_FLAG_TRACKING))
+                     FB_FLAG_ACCURATE | FB_FLAG_TRACKING | FB_FLAG_ALIGN))
         return fail(ctx, FB_ERR_ARG, "unknown flags 0x%x", p->flags);
+    if (p->flags & FB_FLAG_ALIGN) {
+        if (p->levels != 1) return fail(ctx, FB_ERR_ARG, "FB_FLAG_ALIGN requires levels == 1");
+        if (p->alpha > 255) return fail(ctx, FB_ERR_ARG, "alpha must be in [0, 255], got %u", p->alpha);
+        if (p->flags & (FB_FLAG_LEARNED_INIT | FB_FLAG_REPORT_ENERGY | FB_FLAG_BALANCED | FB_FLAG_FAST |
+                        FB_FLAG_ACCURATE))
+            return fail(ctx, FB_ERR_ARG, "FB_FLAG_ALIGN combines with FB_FLAG_TRACKING only");
+    }
     if (p->flags & FB_FLAG_TRACKING) {
         if (p->levels != 1) return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING requires levels == 1");
         if (p->flags & FB_FLAG_LEARNED_INIT)
@@ -276,7 +283,7 @@ struct Buffers {
 void carve(Carver& cv, Buffers& b, const Levels& L, int k, int n_guides, int n_styles,
            size_t chunk_pairs, size_t n_pairs, size_t n_jobs, bool staging, size_t guide_bytes,
            size_t style_bytes, size_t out_floats, bool learned = false,
-           bool balanced = false) {
+           bool balanced = false, bool style_rows = false) {
     for (int l = 0; l < L.n; ++l) {
         const size_t npx = static_cast<size_t>(L.h[l]) * L.w[l];
         if (l > 0) b.raw[l] = cv.take<uint8_t>(static_cast<size_t>(n_guides) * npx * 3);
@@ -289,11 +296,13 @@ void carve(Carver& cv, Buffers& b, const Levels& L, int k, int n_guides, int n_s
     b.EA = cv.take<uint32_t>(chunk_pairs * npx0);
     b.EB = cv.take<uint32_t>(chunk_pairs * npx0);
     if (learned) b.init = cv.take<int32_t>(chunk_pairs * npx0 * 2);
-    if (balanced) {
+    if (balanced || style_rows) {
         const size_t fw = fb::rowpatch_frame_words(k, L.h[0], L.w[0]);
         b.srec = cv.take<uint32_t>(static_cast<size_t>(n_styles) * fw);
-        b.shat_img = cv.take<uint8_t>(chunk_pairs * npx0 * 3);
-        b.shat_rec = cv.take<uint32_t>(chunk_pairs * fw);
+        if (balanced) {
+            b.shat_img = cv.take<uint8_t>(chunk_pairs * npx0 * 3);
+            b.shat_rec = cv.take<uint32_t>(chunk_pairs * fw);
+        }
     }
     b.pairs = cv.take<PairDesc>(n_pairs > 0 ? n_pairs : 1);
     b.jobs = cv.take<JobDesc>(n_jobs > 0 ? n_jobs : 1);
@@ -359,8 +368,13 @@ int run_nnf(fb_ctx* ctx, const Buffers& b, const Levels& L, const fb_params* p, 
         }
         const int r0 = p->r0 > 0 ? p->r0 : (L.h[l] > L.w[l] ? L.h[l] : L.w[l]);
         const bool tracking = (p->flags & FB_FLAG_TRACKING) != 0;  // levels == 1
+        const bool align = (p->flags & FB_FLAG_ALIGN) != 0;        // levels == 1
         for (int it = 0; it < p->iters; ++it) {
-            if (tracking)
+            if (align)
+                FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_nnf_iter_align(k, b.pairs, pair0, n, g, b.srec, p->alpha,
+                                                                       tracking, r0, p->seed, it, Fc, Ec, Fo, Eo,
+                                                                       st));
+            else if (tracking)
                 FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_nnf_iter_track(k, b.pairs, pair0, n, g, r0, p->seed, it, Fc,
                                                                        Ec, Fo, Eo, st));
             else
@@ -530,13 +544,14 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
     }
     Buffers b;
     Carver measure(nullptr);
+    const bool align = (p->flags & FB_FLAG_ALIGN) != 0;
     carve(measure, b, L, k, N, n_styles, max_pairs, pairs.size(), jobs.size(), staging, guide_bytes,
-          style_bytes, out_floats, learned, balanced);
+          style_bytes, out_floats, learned, balanced, align);
     rc = ensure_arena(ctx, measure.off);
     if (rc) return rc;
     Carver cv(ctx->arena);
     carve(cv, b, L, k, N, n_styles, max_pairs, pairs.size(), jobs.size(), staging, guide_bytes,
-          style_bytes, out_floats, learned, balanced);
+          style_bytes, out_floats, learned, balanced, align);
 
     rc = upload_tables(ctx, pairs, jobs, b, st);
     if (rc) return rc;
@@ -554,7 +569,7 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
     rc = prep_guides(ctx, b, L, k, g_dev, N, 0, st);
     if (rc) return rc;
     FB_LAUNCH(ctx, st, FB_K_STYLE, fb::launch_style_rgbx(s_dev, static_cast<size_t>(n_styles) * npx0, b.styles, st));
-    if (balanced)
+    if (balanced || align)
         FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(k, s_dev, n_styles, H, W, b.srec, st));
 
     if (p->flags & FB_FLAG_REPORT_ENERGY) {
@@ -786,7 +801,7 @@ int check_clips(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     if (!clips || n < 1) return fail(ctx, FB_ERR_ARG, "clips must be a non-empty host array");
     if (!p) return fail(ctx, FB_ERR_ARG, "params is NULL");
     if (p->levels != 1) return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use levels == 1");
-    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_ACCURATE | FB_FLAG_TRACKING))
+    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_ACCURATE | FB_FLAG_TRACKING | FB_FLAG_ALIGN))
         return fail(ctx, FB_ERR_UNSUPPORTED, "batched submissions use the plain loss and the direct sum");
     for (int c = 0; c < n; ++c) {
         const fb_clip_desc& d = clips[c];
@@ -1448,7 +1463,8 @@ int fb_nnf(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int 
         return fail(ctx, FB_ERR_ARG, "the improved loss needs the source style: use fb_nnf_balanced");
     if (p->flags & (FB_FLAG_FAST | FB_FLAG_ACCURATE))
         return fail(ctx, FB_ERR_ARG, "FB_FLAG_FAST and FB_FLAG_ACCURATE apply to fb_blend_window only");
-    if (p->flags & FB_FLAG_TRACKING) return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING applies to fb_interpolate and fb_blend_window");
+    if (p->flags & (FB_FLAG_TRACKING | FB_FLAG_ALIGN))
+        return fail(ctx, FB_ERR_ARG, "FB_FLAG_TRACKING and FB_FLAG_ALIGN apply to whole clips");
     DeviceGuard dg(ctx->device);
     for (const void* q : {static_cast<const void*>(src_guide), static_cast<const void*>(tgt_guide),
                           static_cast<const void*>(nnf_out), static_cast<const void*>(init_nnf),
@@ -1583,6 +1599,7 @@ int fb_blend_window(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles, i
         return fail(ctx, FB_ERR_ARG, "window must be odd and >= 1, got %d", window);
     if (!guides || !styles || !out)
         return fail(ctx, FB_ERR_ARG, "guides, styles and out must be non-NULL");
+    if (p->flags & FB_FLAG_ALIGN) return fail(ctx, FB_ERR_ARG, "FB_FLAG_ALIGN applies to fb_interpolate only");
     const int k = p->patch, M = (window - 1) / 2;
     if (p->flags & FB_FLAG_FAST) {
         const uint64_t k4 = static_cast<uint64_t>(k) * k * k * k;
@@ -1663,6 +1680,15 @@ int fb_interpolate(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, cons
         jobs[i] = j;
     }
     if (p->flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
+    if (p->flags & FB_FLAG_ALIGN) {
+        // Eq. 10: the two pairs of a frame between keys are each other's partner.
+        for (PairDesc& pd : pairs) pd.pad[2] = -1;
+        for (const JobDesc& j : jobs)
+            if (j.n_pairs == 2) {
+                pairs[j.first_pair].pad[2] = j.first_pair + 1;
+                pairs[j.first_pair + 1].pad[2] = j.first_pair;
+            }
+    }
     DeviceGuard dg(ctx->device);
     return run_pipeline(ctx, guides, N, H, W, key_styles, n_keys, pairs, jobs, p, out,
                         static_cast<cudaStream_t>(stream));

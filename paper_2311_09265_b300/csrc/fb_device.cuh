@@ -450,6 +450,28 @@ __device__ __forceinline__ void iterate_pixel_balanced(
     search_pixel<K>(err, H, W, r, c, tag, r0, key0, key1, ctr_word, Fpp, bf, be, Fnp, Enp);
 }
 
+// Alignment loss of Sec. 3.5.2 (Eq. 10) for a pair with a partner (the other key's pair
+// to the same frame): alpha * Eq.1(guides) + Eq.1(own key style at u, partner key style at
+// the partner's snapshot match fo of this pixel) -- the pairwise patch error, a patch of
+// one keyframe against a patch of the other.  The incumbent is re-evaluated here against
+// the partner's snapshot.  Extra: tracking candidates, or none.
+template <int K, class Extra>
+__device__ __forceinline__ void iterate_pixel_aligned(
+    const uint32_t* __restrict__ rpg_src, const uint32_t* __restrict__ rps_src,
+    const uint32_t* __restrict__ rpg_tgt, const uint32_t* __restrict__ rps_partner, uint32_t fo,
+    uint32_t alpha, int H, int W, int r, int c, uint32_t tag, int r0, uint32_t key0, uint32_t key1,
+    uint32_t ctr_word, const uint32_t* __restrict__ Fpp, uint32_t* __restrict__ Fnp,
+    uint32_t* __restrict__ Enp, const Extra& extra) {
+    TargetPatch<K> tg, ts;
+    load_target<K>(rpg_tgt, H, W, r, c, tg);
+    load_target<K>(rps_partner, H, W, row_of(fo), col_of(fo), ts);
+    const BalancedError<K> err{rpg_src, rps_src, H, W, tg, ts, alpha};
+    const uint32_t bf = Fpp[static_cast<size_t>(r) * W + c];
+    uint32_t be = 0;
+    err(row_of(bf), col_of(bf), 0xFFFFFFFFu, &be);
+    search_pixel<K>(err, H, W, r, c, tag, r0, key0, key1, ctr_word, Fpp, bf, be, Fnp, Enp, extra);
+}
+
 // Initial field of Alg. 1 for target pixel (r, c) of one pair and its Eq. 1 error.
 // mode 0: Philox random match; 1: the coarse level's match, doubled, plus the pixel's
 // parity; 2: the caller's field (clamped into the image).

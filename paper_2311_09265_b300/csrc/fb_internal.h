@@ -36,8 +36,9 @@ struct PairDesc {
     uint32_t tag;      // Philox stream id of the pair
     int32_t style;     // style slot remapped through this pair's NNF
     uint32_t weight;   // integer weight of the remapped style in the output numerator
-    int32_t pad[3];    // tracking kernel only: pad[0] / pad[1] = chain neighbours (pair
-                       // indices of the launch for targets tgt - 1 / tgt + 1, or -1)
+    int32_t pad[3];    // tracking and alignment kernels only: pad[0] / pad[1] = chain
+                       // neighbours (pair indices for targets tgt - 1 / tgt + 1, or -1);
+                       // pad[2] = the alignment partner (the other key's pair to tgt, or -1)
 };
 
 // One output frame: out = (self_w * S_self * k^2 / k^2 ... ) see combine kernel.
@@ -84,6 +85,12 @@ cudaError_t launch_nnf_pack(const int32_t* nnf, int H, int W, uint32_t* F, cudaS
 cudaError_t launch_nnf_iter_track(int k, const PairDesc* pairs, int pair0, int n_pairs, const LevelGeom& g,
                                   int r0, uint64_t seed, int it, const uint32_t* Fp, const uint32_t* Ep,
                                   uint32_t* Fn, uint32_t* En, cudaStream_t st);
+// Alignment of Sec. 3.5.2 (Eq. 10): pairs with pad[2] >= 0 (the partner pair's index)
+// take the coupled loss, the others the plain one; tracking adds the chain neighbours.
+cudaError_t launch_nnf_iter_align(int k, const PairDesc* pairs, int pair0, int n_pairs, const LevelGeom& g,
+                                  const uint32_t* srp, uint32_t alpha, bool tracking, int r0, uint64_t seed,
+                                  int it, const uint32_t* Fp, const uint32_t* Ep, uint32_t* Fn, uint32_t* En,
+                                  cudaStream_t st);
 
 // Fast mode of Sec. 3.4 (Algs. 3-5).  A blending-table entry: the exact sum
 // k^2 S_frame + the Alg. 2 votes of its sources, each source one NNF pair (index into the

@@ -336,6 +336,43 @@ __global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
                               En + static_cast<size_t>(pl) * npx);
 }
 
+// Alignment of Sec. 3.5.2 (Eq. 10), optionally with tracking: a pair with a partner
+// (pd.pad[2], the other key's pair to the same frame, in this launch) takes the coupled
+// loss against the partner's snapshot; a pair without one (a frame outside the key range)
+// the plain loss.  The branch is uniform per block (one pair per grid row).
+template <int K, bool TRACK>
+__global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
+    nnf_iter_align_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
+                          const uint32_t* __restrict__ rp, const uint32_t* __restrict__ srp,
+                          uint32_t alpha, int r0, uint32_t key0, uint32_t key1, uint32_t ctr_word,
+                          const uint32_t* __restrict__ Fp, const uint32_t* __restrict__ Ep,
+                          uint32_t* __restrict__ Fn, uint32_t* __restrict__ En) {
+    const TileCoord tc = tile_coord(W);
+    if (tc.r >= H || tc.c >= W) return;
+    const int pl = blockIdx.y;
+    const PairDesc pd = pairs[pair0 + pl];
+    const size_t npx = static_cast<size_t>(H) * W;
+    const size_t x = static_cast<size_t>(tc.r) * W + tc.c;
+    const uint32_t* Fpp = Fp + static_cast<size_t>(pl) * npx;
+    const uint32_t* prev = TRACK && pd.pad[0] >= 0 ? Fp + static_cast<size_t>(pd.pad[0] - pair0) * npx + x : nullptr;
+    const uint32_t* next = TRACK && pd.pad[1] >= 0 ? Fp + static_cast<size_t>(pd.pad[1] - pair0) * npx + x : nullptr;
+    const TrackNeighbours extra{prev, next};
+    if (pd.pad[2] < 0) {
+        TargetPatch<K> t;
+        load_target<K>(frame_rows<K>(rp, pd.tgt, H, W), H, W, tc.r, tc.c, t);
+        search_pixel<K>(PlainError<K>{frame_rows<K>(rp, pd.src, H, W), H, W, t}, H, W, tc.r, tc.c, pd.tag, r0,
+                        key0, key1, ctr_word, Fpp, Fpp[x], Ep[static_cast<size_t>(pl) * npx + x],
+                        Fn + static_cast<size_t>(pl) * npx, En + static_cast<size_t>(pl) * npx, extra);
+        return;
+    }
+    const PairDesc po = pairs[pd.pad[2]];
+    const uint32_t fo = Fp[static_cast<size_t>(pd.pad[2] - pair0) * npx + x];
+    iterate_pixel_aligned<K>(frame_rows<K>(rp, pd.src, H, W), frame_rows<K>(srp, pd.style, H, W),
+                             frame_rows<K>(rp, pd.tgt, H, W), frame_rows<K>(srp, po.style, H, W), fo, alpha, H,
+                             W, tc.r, tc.c, pd.tag, r0, key0, key1, ctr_word, Fpp,
+                             Fn + static_cast<size_t>(pl) * npx, En + static_cast<size_t>(pl) * npx, extra);
+}
+
 // ---------------------------------------------------------------------------------
 // Fast mode of Sec. 3.4: blending-table entries (Algs. 3-4) and the interval queries of
 // the output frames (Alg. 5 + the split identity), exact integer sums.
@@ -639,6 +676,25 @@ cudaError_t launch_nnf_iter_track(int k, const PairDesc* pairs, int pair0, int n
     FB_DISPATCH_K(k, (nnf_iter_track_kernel<KK><<<grid, block, 0, st>>>(
                          pairs, pair0, g.H, g.W, g.rp, r0, static_cast<uint32_t>(seed),
                          static_cast<uint32_t>(seed >> 32), ctr_word, Fp, Ep, Fn, En)));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_nnf_iter_align(int k, const PairDesc* pairs, int pair0, int n_pairs, const LevelGeom& g,
+                                  const uint32_t* srp, uint32_t alpha, bool tracking, int r0, uint64_t seed,
+                                  int it, const uint32_t* Fp, const uint32_t* Ep, uint32_t* Fn, uint32_t* En,
+                                  cudaStream_t st) {
+    if (n_pairs <= 0) return cudaSuccess;
+    const dim3 grid = tile_grid(g.H, g.W, n_pairs);
+    const dim3 block(TILE_W, TILE_H);
+    const uint32_t ctr_word = static_cast<uint32_t>(it + 1) << 8;  // level 0
+    const uint32_t key0 = static_cast<uint32_t>(seed), key1 = static_cast<uint32_t>(seed >> 32);
+    if (tracking) {
+        FB_DISPATCH_K(k, (nnf_iter_align_kernel<KK, true><<<grid, block, 0, st>>>(
+                             pairs, pair0, g.H, g.W, g.rp, srp, alpha, r0, key0, key1, ctr_word, Fp, Ep, Fn, En)));
+    } else {
+        FB_DISPATCH_K(k, (nnf_iter_align_kernel<KK, false><<<grid, block, 0, st>>>(
+                             pairs, pair0, g.H, g.W, g.rp, srp, alpha, r0, key0, key1, ctr_word, Fp, Ep, Fn, En)));
+    }
     return cudaGetLastError();
 }
 

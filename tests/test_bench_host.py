@@ -50,6 +50,15 @@ def test_tracking_neighbour_refs_of_a_blend(N, window):
 
 def test_mode_workloads_run_on_their_clip():
     assert bench.base_workload("tracking_1024x576") == "interp_1024x576"
+    assert bench.base_workload("aligned_1024x576") == "interp_1024x576"
     for m in ("balanced_512", "fast_512", "accurate_512", "learned_512", "initnet_512", "tracking_512"):
         assert bench.base_workload(m) == "blend_512"
     assert bench.base_workload("blend_512_16f") == "blend_512_16f"
+
+
+@pytest.mark.parametrize("N,keys,expect", [(48, (0, 47), 92), (10, (2, 5, 7), 6), (6, (3,), 0),
+                                           (5, (0, 1, 2, 3, 4), 0), (9, (0, 4, 8), 12)])
+def test_aligned_pairs_are_the_pairs_between_keys(N, keys, expect):
+    w = dataclasses.replace(synth.WORKLOADS["interp_1024x576"], N=N, keys=keys)
+    between = sum(2 for i in range(N) if i not in keys and keys[0] < i < keys[-1])
+    assert bench.aligned_pairs(w) == between == expect

@@ -17,8 +17,9 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SRC = os.path.join(ROOT, "oracle", "fbref.c")
 
-# name: (original text, replacement, which occurrence (0-based; the plain-mode site
-# precedes the balanced-mode one) or None for a unique site)
+# name: (original text, replacement, which occurrence (0-based, in source order: the
+# plain-mode site precedes the balanced-mode one, which precedes the alignment one) or
+# None for a unique site)
 MUTANTS = {
     "philox_nine_rounds": ("round < 10", "round < 9", None),
     "philox_weyl_constant": ("#define PHILOX_WEYL_B 0xBB67AE85u", "#define PHILOX_WEYL_B 0xBB67AE84u", None),
@@ -56,7 +57,8 @@ MUTANTS = {
     "shat_rounds_down": ("shat[t] = (uint8_t)((v[t] + kk / 2) / kk);", "shat[t] = (uint8_t)(v[t] / kk);", None),
     "balanced_alpha_on_style_term": ("return alpha * fbref_ssd(gs, gt, H, W, k, ur, uc, xr, xc) +\n           fbref_ssd(ss, shat, H, W, k, ur, uc, xr, xc);",
                                      "return fbref_ssd(gs, gt, H, W, k, ur, uc, xr, xc) +\n           alpha * fbref_ssd(ss, shat, H, W, k, ur, uc, xr, xc);", None),
-    "balanced_guide_term_on_style_image": ("return alpha * fbref_ssd(gs, gt,", "return alpha * fbref_ssd(ss, gt,", None),
+    "balanced_guide_term_on_style_image": ("return alpha * fbref_ssd(gs, gt,", "return alpha * fbref_ssd(ss, gt,", 0),
+    "align_guide_term_on_style_image": ("return alpha * fbref_ssd(gs, gt,", "return alpha * fbref_ssd(ss, gt,", 1),
     "balanced_style_term_against_target_guide": ("           fbref_ssd(ss, shat, H, W, k, ur, uc, xr, xc);", "           fbref_ssd(ss, gt, H, W, k, ur, uc, xr, xc);", None),
     "balanced_error_not_reevaluated": ("                E[x] = balanced_loss(", "                if (it == 0) E[x] = balanced_loss(", None),
     "balanced_shat_not_refreshed": ("        fbref_shat(src_style, F, h, w, k, shat);", "        if (it == 0) fbref_shat(src_style, F, h, w, k, shat);", None),
@@ -67,7 +69,8 @@ MUTANTS = {
     "tracking_candidate_offset": ("uint32_t e = fbref_ssd(src, T, h, w, k, Fb[0], Fb[1], r, c);\n                        if (e < be) { be = e; br = Fb[0]; bc = Fb[1]; }",
                                   "uint32_t e = fbref_ssd(src, T, h, w, k, clampi(Fb[0] + 1, 0, h - 1), Fb[1], r, c);\n                        if (e < be) { be = e; br = clampi(Fb[0] + 1, 0, h - 1); bc = Fb[1]; }", None),
     "tracking_interpolation_weights_swapped": ("wgt = (uint32_t)(next - i); dd = (uint32_t)(next - a);", "wgt = (uint32_t)(i - a); dd = (uint32_t)(next - a);", None),
-    "tracking_pair_stream_reversed": ("for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(a, lo + q);", "for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(lo + q, a);", None),
+    "tracking_pair_stream_reversed": ("for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(a, lo + q);", "for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(lo + q, a);", 0),
+    "align_one_key_run_stream_reversed": ("for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(a, lo + q);", "for (int q = 0; q < n; ++q) tags[q] = fbref_pair_tag(lo + q, a);", 1),
     "tracking_run_includes_the_next_key": ("const int runs[2][2] = {{prev + 1, a - 1}, {a + 1, next - 1}};", "const int runs[2][2] = {{prev + 1, a - 1}, {a + 1, next < N ? next : N - 1}};", None),
     "blend_tracking_chain_includes_the_source": ("const int runs[2][2] = {{j - M < 0 ? 0 : j - M, j - 1}, {j + 1, j + M > N - 1 ? N - 1 : j + M}};",
                                                  "const int runs[2][2] = {{j - M < 0 ? 0 : j - M, j - 1}, {j, j + M > N - 1 ? N - 1 : j + M}};", None),
