@@ -223,6 +223,28 @@ int fb_nnf_balanced(fb_ctx *ctx, const uint8_t *src_guide, const uint8_t *tgt_gu
                     const int32_t *init_nnf, int32_t *nnf_out, uint32_t *err_out,
                     uint8_t *shat_out, void *stream);
 
+/* Sec. 3.5.2 alignment (Eq. 10) and Sec. 3.5.1 tracking at the level of the fields: the
+ * NNFs from the two keyframes at the ends of a clip segment to every frame between them,
+ * as fb_interpolate computes them for a pair of consecutive keys.
+ *   guides      (n + 2) x H x W x 3 uint8 (device): key l, the n frames between, key r.
+ *   key_styles  2 x H x W x 3 uint8 (device): S_l, S_r.
+ *   n           frames between the keys, in [1, 32767].
+ *   p           levels must be 1; p->flags: FB_FLAG_ALIGN (coupled loss, p->alpha in
+ *               [0, 255]) and / or FB_FLAG_TRACKING; with neither, the 2n independent
+ *               Alg. 1 fields.  Pair (0 -> q) and (n + 1 -> q), q = 1..n, draw the
+ *               random streams of fb_pair_tag(0, q) and fb_pair_tag(n + 1, q).
+ *   init        2n x H x W x 2 int32 initial fields (device, clamped into the image) or
+ *               NULL for the random initialisation.
+ *   nnf_out     2n x H x W x 2 int32 (device): the fields of key l to frames 1..n, then
+ *               those of key r.
+ *   err_out     2n x H x W uint32 (device) or NULL: the loss each final match was last
+ *               compared under (the coupled loss of Eq. 10 with FB_FLAG_ALIGN, else Eq. 1).
+ *               With FB_FLAG_ALIGN it needs iters >= 1 (FB_ERR_ARG otherwise).
+ * Errors as fb_nnf; the 2n fields are held at once (no pair budget).  Async on `stream`. */
+int fb_nnf_segment(fb_ctx *ctx, const uint8_t *guides, const uint8_t *key_styles, int n, int H,
+                   int W, const fb_params *p, const int32_t *init, int32_t *nnf_out,
+                   uint32_t *err_out, void *stream);
+
 /* Alg. 2 (Sec. 3.3), memory-efficient remap of `src_style` (H x W x 3) through `nnf`
  * (H x W x 2 int32, entries clamped into the image):
  *   out(x) = sum over the k x k neighbours q of x of S(F(q^) - (q^ - x)) / (255 k^2),

@@ -24,7 +24,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_status_string", "fb_ctx_launches", "fb_ctx_scratch_bytes",
                     "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a",
                     "fb_debug_candidates_considered", "fb_pair_tag",
-                    "fb_nnf", "fb_nnf_balanced", "fb_remap", "fb_blend_window", "fb_interpolate",
+                    "fb_nnf", "fb_nnf_balanced", "fb_nnf_segment", "fb_remap", "fb_blend_window", "fb_interpolate",
                     "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan", "fb_fast_plan",
                     "fb_ctx_batch_variant", "fb_ctx_set_pair_budget",
                     "fb_initnet_create", "fb_initnet_destroy", "fb_initnet_last_error",
@@ -120,6 +120,8 @@ def lib() -> ctypes.CDLL:
         L.fb_pair_tag.restype = ctypes.c_uint32
         P = ctypes.POINTER(Params)
         L.fb_nnf.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp, _vp, _vp]
+        L.fb_nnf_segment.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
+                                     _vp, _vp, _vp, _vp]
         L.fb_nnf_balanced.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp,
                                       _vp, _vp, _vp]
         L.fb_fast_plan.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.POINTER(ctypes.c_uint64)] * 3
@@ -348,6 +350,29 @@ def fb_nnf_balanced(ctx: Context, src_guide: torch.Tensor, tgt_guide: torch.Tens
                                _ptr(shat_out, torch.uint8, "shat_out"), _stream_handle(stream, ctx.device))
     ctx.check(rc)
     return nnf_out, err_out, shat_out
+
+
+def fb_nnf_segment(ctx: Context, guides: torch.Tensor, key_styles: torch.Tensor, params: Params,
+                   init: Optional[torch.Tensor] = None, with_err: bool = True, stream=None):
+    """Fields of a clip segment (key l, n frames, key r) under params.flags
+    (FB_FLAG_ALIGN / FB_FLAG_TRACKING).  Returns (nnf (2n,H,W,2) int32, err (2n,H,W)
+    int32 holding uint32 values, or None), the left key's fields first."""
+    n2, H, W = int(guides.shape[0]), int(guides.shape[1]), int(guides.shape[2])
+    n = n2 - 2
+    _shape(guides, (n2, H, W, 3), "guides")
+    _shape(key_styles, (2, H, W, 3), "key_styles")
+    if init is not None:
+        _shape(init, (2 * max(n, 0), H, W, 2), "init")
+    dev = guides.device
+    nnf_out = torch.empty((2 * max(n, 0), H, W, 2), dtype=torch.int32, device=dev)
+    err_out = torch.empty((2 * max(n, 0), H, W), dtype=torch.int32, device=dev) if with_err else None
+    rc = lib().fb_nnf_segment(ctx.handle, _ptr(guides, torch.uint8, "guides"),
+                              _ptr(key_styles, torch.uint8, "key_styles"), n, H, W,
+                              ctypes.byref(params), _ptr(init, torch.int32, "init"),
+                              _ptr(nnf_out, torch.int32, "nnf_out"),
+                              _ptr(err_out, torch.int32, "err_out"), _stream_handle(stream, ctx.device))
+    ctx.check(rc)
+    return nnf_out, err_out
 
 
 def fb_remap(ctx: Context, src_style: torch.Tensor, nnf: torch.Tensor, patch: int,

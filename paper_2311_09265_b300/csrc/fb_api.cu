@@ -1498,6 +1498,65 @@ int fb_nnf(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int 
     return FB_OK;
 }
 
+int fb_nnf_segment(fb_ctx* ctx, const uint8_t* guides, const uint8_t* key_styles, int n, int H, int W,
+                   const fb_params* p, const int32_t* init, int32_t* nnf_out, uint32_t* err_out,
+                   void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->err.clear();
+    int rc = check_params(ctx, p, H, W);
+    if (rc) return rc;
+    if (p->levels != 1) return fail(ctx, FB_ERR_ARG, "fb_nnf_segment requires levels == 1");
+    if (p->flags & ~(FB_FLAG_ALIGN | FB_FLAG_TRACKING))
+        return fail(ctx, FB_ERR_ARG, "fb_nnf_segment takes FB_FLAG_ALIGN and FB_FLAG_TRACKING only");
+    if (n < 1 || n > 32767) return fail(ctx, FB_ERR_ARG, "n must be in [1, 32767], got %d", n);
+    if (!guides || !key_styles || !nnf_out)
+        return fail(ctx, FB_ERR_ARG, "guides, key_styles and nnf_out must be non-NULL");
+    if (err_out && (p->flags & FB_FLAG_ALIGN) && p->iters == 0)
+        return fail(ctx, FB_ERR_ARG, "with FB_FLAG_ALIGN the coupled loss is reported after iters >= 1");
+    DeviceGuard dg(ctx->device);
+    for (const void* q : {static_cast<const void*>(guides), static_cast<const void*>(key_styles),
+                          static_cast<const void*>(init), static_cast<const void*>(nnf_out),
+                          static_cast<const void*>(err_out)})
+        if (q && classify(ctx, q) != Mem::Device)
+            return fail(ctx, FB_ERR_ARG, "fb_nnf_segment takes device pointers of the context's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Levels L = level_dims(H, W, 1);
+    const size_t npx0 = static_cast<size_t>(H) * W;
+    const int k = p->patch;
+
+    // Left key's chain first, then the right key's: pair q - 1 and n + q - 1 target frame q.
+    std::vector<PairDesc> pairs;
+    for (int side = 0; side < 2; ++side) {
+        const int key = side == 0 ? 0 : n + 1;
+        for (int q = 1; q <= n; ++q) pairs.push_back(PairDesc{key, q, fb_pair_tag(key, q), side, 1u, {-1, -1, -1}});
+    }
+    if (p->flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
+    if (p->flags & FB_FLAG_ALIGN)
+        for (int q = 0; q < n; ++q) {
+            pairs[q].pad[2] = n + q;
+            pairs[n + q].pad[2] = q;
+        }
+    const size_t n_pairs = pairs.size();
+
+    Buffers b;
+    Carver measure(nullptr);
+    carve(measure, b, L, k, n + 2, 2, n_pairs, n_pairs, 0, false, 0, 0, 0, false, false, true);
+    rc = ensure_arena(ctx, measure.off);
+    if (rc) return rc;
+    Carver cv(ctx->arena);
+    carve(cv, b, L, k, n + 2, 2, n_pairs, n_pairs, 0, false, 0, 0, 0, false, false, true);
+    rc = upload_tables(ctx, pairs, {}, b, st);
+    if (rc) return rc;
+    rc = prep_guides(ctx, b, L, k, guides, n + 2, 0, st);
+    if (rc) return rc;
+    FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(k, key_styles, 2, H, W, b.srec, st));
+    uint32_t *F = nullptr, *E = nullptr;
+    rc = run_nnf(ctx, b, L, p, 0, static_cast<int>(n_pairs), init, st, &F, &E);
+    if (rc) return rc;
+    FB_LAUNCH(ctx, st, FB_K_UNPACK, fb::launch_nnf_unpack(F, E, n_pairs * npx0, nnf_out, err_out, st));
+    return FB_OK;
+}
+
 int fb_nnf_balanced(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide,
                     const uint8_t* src_style, int H, int W, const fb_params* p,
                     const int32_t* init_nnf, int32_t* nnf_out, uint32_t* err_out, uint8_t* shat_out,

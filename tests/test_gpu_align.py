@@ -53,6 +53,77 @@ def test_aligned_interpolation_matches_oracle(fbp, ctx, N, H, W, k, keys, iters,
     assert (out == ref).all()
 
 
+SEGMENT_CASES = [
+    # n, H, W, k, iters, alpha, align, tracking, with_init
+    (3, 30, 34, 5, 3, 10, True, False, False),
+    (4, 27, 25, 5, 2, 10, True, True, False),
+    (2, 22, 31, 7, 2, 0, True, True, True),
+    (3, 19, 20, 3, 1, 255, True, False, True),
+    (2, 21, 23, 9, 2, 6, True, True, False),
+    (3, 24, 26, 5, 2, 0, False, True, False),     # tracked chains, plain loss
+    (2, 20, 21, 5, 2, 0, False, False, True),     # independent plain fields
+]
+
+
+@pytest.mark.parametrize("n,H,W,k,iters,alpha,align,tracking,with_init", SEGMENT_CASES)
+def test_segment_fields_match_oracle(fbp, ctx, n, H, W, k, iters, alpha, align, tracking, with_init):
+    """Field-level parity: every NNF and loss of a segment, bit-exact."""
+    g, s = synth.small_clip(n + 2, H, W, seed=n * 31 + H, motion="affine")
+    ks = np.ascontiguousarray(s[[0, n + 1]])
+    tl = [oracle.pair_tag(0, q) for q in range(1, n + 1)]
+    tr = [oracle.pair_tag(n + 1, q) for q in range(1, n + 1)]
+    init = None
+    if with_init:
+        rng = np.random.default_rng(n + H)
+        init = np.stack([rng.integers(-3, H + 3, (2 * n, H, W)), rng.integers(-3, W + 3, (2 * n, H, W))],
+                        -1).astype(np.int32)
+    flags = (fbp.FB_FLAG_ALIGN if align else 0) | (fbp.FB_FLAG_TRACKING if tracking else 0)
+    p = fbp.Params.make(k, iters, 1, 0, 19, flags=flags, alpha=alpha)
+    F, E = fbp.fb_nnf_segment(ctx, cuda(g), cuda(ks), p, init=None if init is None else cuda(init))
+    F, E = F.cpu().numpy(), E.cpu().numpy().view(np.uint32)
+    if align:
+        Fo, Eo = oracle.nnf_segment(g[0], g[n + 1], ks[0], ks[1], g[1:n + 1], k, iters, alpha, tl, tr,
+                                    tracking=tracking, seed=19,
+                                    init=None if init is None else init.reshape(2, n, H, W, 2))
+        Fo, Eo = Fo.reshape(2 * n, H, W, 2), Eo.reshape(2 * n, H, W)
+    else:
+        Fs, Es = [], []
+        for side, src in enumerate((0, n + 1)):
+            tags = tl if side == 0 else tr
+            side_init = None if init is None else init[side * n:(side + 1) * n]
+            if tracking:
+                a, b = oracle.nnf_chain(g[src], g[1:n + 1], k, iters, tags, seed=19, init=side_init)
+                Fs.append(a)
+                Es.append(b)
+            else:
+                for q in range(n):
+                    a, b = oracle.nnf(g[src], g[1 + q], k, iters, seed=19, pair_tag=tags[q],
+                                      init=None if side_init is None else side_init[q])
+                    Fs.append(a[None])
+                    Es.append(b[None])
+        Fo, Eo = np.concatenate(Fs), np.concatenate(Es)
+    assert (F == Fo).all()
+    assert (E == Eo).all()
+
+
+def test_segment_argument_errors(fbp, ctx):
+    import torch
+    g = torch.zeros((4, 16, 16, 3), dtype=torch.uint8, device="cuda")
+    A = fbp.FB_FLAG_ALIGN
+    n0 = ctx.launches
+    for p in (fbp.Params.make(5, 0, 1, flags=A, alpha=1),                         # loss needs an iteration
+              fbp.Params.make(5, 2, 2, flags=A, alpha=1),                         # levels
+              fbp.Params.make(5, 2, 1, flags=A | fbp.FB_FLAG_BALANCED, alpha=1),  # other modes
+              fbp.Params.make(5, 2, 1, flags=A, alpha=300)):
+        with pytest.raises(fbp.FastBlendError) as ei:
+            fbp.fb_nnf_segment(ctx, g, g[:2], p)
+        assert ei.value.status == fbp.FB_ERR_ARG
+    with pytest.raises(fbp.FastBlendError) as ei:
+        fbp.fb_nnf_segment(ctx, g[:2], g[:2], fbp.Params.make(5, 2))             # no frame between
+    assert ei.value.status == fbp.FB_ERR_ARG
+    assert ctx.launches == n0
+
+
 def test_aligned_interpolation_through_host_buffers(fbp, ctx):
     import torch
     g, s = synth.small_clip(7, 26, 29, seed=3, motion="affine")
