@@ -43,9 +43,11 @@ SM_MAX_MHZ_NOMINAL = 2032.0
 DP4A_PER_CLK_SM = 64        # integer dot-product (dp4a) issue rate per SM per clock
 # Guide weight of the improved loss (Sec. 3.4) in the balanced workload.
 BALANCED_ALPHA = 10
-# dram__bytes_read.sum + dram__bytes_write.sum of one nnf_iter launch, from an ncu capture
-# of the current kernel, scaled to the workload (see profiles/); None when not captured.
-TRAFFIC_PER_LAUNCH = {"blend_512": 5.73e9}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the workload's iteration
+# kernel, from an ncu capture of the current kernel on a smaller case scaled by the pairs
+# per launch (see profiles/); None when not captured or when the workload is overridden.
+TRAFFIC_PER_LAUNCH = {"blend_512": 5.73e9, "tracking_512": 4.09e9, "balanced_512": 9.12e9,
+                      "aligned_1024x576": 8.24e9}
 
 
 def parse_args(argv=None):
@@ -61,6 +63,9 @@ def parse_args(argv=None):
                                                        "aligned_1024x576"])
     ap.add_argument("--window", type=int, default=0,
                     help="override the blend window of the headline-clip workloads (odd)")
+    ap.add_argument("--frames", type=int, default=0,
+                    help="interpolation workloads: keep the clip's first F frames, keys 0 and "
+                         "F - 1 styled with the clip's two key styles (small profiling cases)")
     ap.add_argument("--learned-iters", type=int, default=2,
                     help="Alg. 1 iterations after the learned initialiser (learned_512)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -116,6 +121,17 @@ def shard_seed(workload_seed: int, rank: int) -> int:
 def aggregate(n_frames_per_rank: int, steps: int, world: int, max_total_ms: float) -> float:
     """Whole-job frames/s: every rank's frames over the slowest rank's time."""
     return world * n_frames_per_rank * steps / (max_total_ms / 1e3)
+
+
+def truncate_interpolation(w: synth.Workload, g, s, frames: int):
+    """The first `frames` frames of a two-key interpolation clip, keys 0 and frames - 1
+    (the key styles unchanged)."""
+    import dataclasses
+    if not frames or w.mode != "interpolate":
+        return w, g, s
+    if len(w.keys) != 2 or not 2 <= frames <= w.N:
+        raise ValueError("--frames needs a two-key interpolation workload and 2 <= F <= N")
+    return dataclasses.replace(w, N=frames, keys=(0, frames - 1)), g[:frames].copy(), s
 
 
 def make_inputs(w: synth.Workload, seed: int):
@@ -291,6 +307,7 @@ def run_reference(args):
             import dataclasses
             w = dataclasses.replace(w, window=args.window)
         g, s = make_inputs(w, w.seed)
+        w, g, s = truncate_interpolation(w, g, s, args.frames)
     alpha = (BALANCED_ALPHA if args.workload in ("balanced_512", "accurate_512", "aligned_1024x576")
              else None)
     fast = args.workload == "fast_512"
@@ -394,6 +411,7 @@ def run_gpu(args):
         import dataclasses
         w = dataclasses.replace(w, window=args.window)
     g, s = make_inputs(w, shard_seed(w.seed, rank))
+    w, g, s = truncate_interpolation(w, g, s, args.frames)
     ctx = fbp.Context(local)
     params = fbp.Params.make(w.patch, w.iters, w.levels, 0, w.seed)
     if balanced:
@@ -545,7 +563,8 @@ def run_gpu(args):
                                            "tracking of Sec. 3.5.1)" if tracking else
                                            "nnf_iter (Alg. 1 Jacobi iteration)"),
                 "achieved": achieved, "peak": peak, "unit": "T byte-pair ops/s",
-                "frac": achieved / peak, "traffic": TRAFFIC_PER_LAUNCH.get(args.workload),
+                "frac": achieved / peak, "traffic": (None if args.window or args.frames
+                                                      else TRAFFIC_PER_LAUNCH.get(args.workload)),
                 "peak_basis": (f"{DP4A_PER_CLK_SM} dp4a/clk/SM x {SM_COUNT_NOMINAL} SMs x "
                                f"{SM_MAX_MHZ_NOMINAL:.0f} MHz x 4 byte pairs (derived; the live "
                                f"register-only probe measured {probe_per_clk:.1f} dp4a/clk/SM)"

@@ -3,6 +3,7 @@ import dataclasses
 import os
 import sys
 
+import numpy as np
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -62,3 +63,16 @@ def test_aligned_pairs_are_the_pairs_between_keys(N, keys, expect):
     w = dataclasses.replace(synth.WORKLOADS["interp_1024x576"], N=N, keys=keys)
     between = sum(2 for i in range(N) if i not in keys and keys[0] < i < keys[-1])
     assert bench.aligned_pairs(w) == between == expect
+
+
+def test_frames_override_truncates_a_two_key_interpolation():
+    w = synth.WORKLOADS["interp_1024x576"]
+    g = np.zeros((w.N, 4, 4, 3), np.uint8)
+    g[:, 0, 0, 0] = np.arange(w.N)
+    s = np.zeros((2, 4, 4, 3), np.uint8)
+    w2, g2, s2 = bench.truncate_interpolation(w, g, s, 12)
+    assert (w2.N, w2.keys) == (12, (0, 11)) and g2.shape[0] == 12 and s2 is s
+    assert (g2[:, 0, 0, 0] == np.arange(12)).all() and w2.pairs() == 20
+    assert bench.truncate_interpolation(w, g, s, 0)[0] is w
+    with pytest.raises(ValueError):
+        bench.truncate_interpolation(w, g, s, 1)
