@@ -327,7 +327,8 @@ def run_reference(args):
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u8", "data": "synthetic",
-        "config": {"workload": w.name, "frames": w.N, "height": w.H, "width": w.W,
+        "config": {"workload": workload_label(args.workload, w, args.learned_iters),
+                   "frames": w.N, "height": w.H, "width": w.W,
                    "patch": w.patch, "window": w.window, "iters": w.iters,
                    "step": "one output frame of the clip (bounded CPU sample)"},
         "cpu_baseline": {"value": value, "unit": "frames/s", "cores": oracle.num_threads(),
@@ -353,6 +354,33 @@ def iter_ops_per_launch(w: synth.Workload) -> int:
     """Algorithmic byte-pair ops of one Jacobi-iteration launch (levels = 1): every
     pair, every pixel, 4 propagation + R random-search candidates, 3k^2 byte pairs."""
     return w.pairs() * w.H * w.W * (4 + w.random_search_radii()) * 3 * w.patch * w.patch
+
+
+def workload_label(name: str, w: synth.Workload, learned_iters: int = 2) -> str:
+    """config.workload: what one step computes, with the sizes it runs at."""
+    dims = f"{w.N}x{w.H}x{w.W} k{w.patch}"
+    dims += f" w{w.window}" if w.mode == "blend" else " keys " + ",".join(map(str, w.keys))
+    it = f" n{w.iters}"
+    labels = {
+        "learned_512": f"learned-init blend all-pairs {dims}: BF16 conv initialiser (tcgen05) + "
+                       f"{learned_iters} Alg. 1 iteration(s)",
+        "balanced_512": f"balanced blend all-pairs {dims}{it}: Sec. 3.4 improved loss, "
+                        f"alpha {BALANCED_ALPHA}",
+        "fast_512": f"fast-mode blend {dims}{it}: Sec. 3.4 remapping / blending tables and "
+                    "interval queries (Algs. 3-5)",
+        "accurate_512": f"accurate blend all-pairs {dims}{it}: Sec. 3.4 mean-remap alignment "
+                        f"loss, alpha {BALANCED_ALPHA}",
+        "tracking_512": f"tracking blend all-pairs {dims}{it}: Sec. 3.5.1 chain-neighbour candidates",
+        "tracking_1024x576": f"tracking interpolation {dims}{it}: Sec. 3.5.1 chain-neighbour "
+                             "candidates",
+        "aligned_1024x576": f"aligned + tracking interpolation {dims}{it}: Eq. 10 alignment loss "
+                            f"(alpha {BALANCED_ALPHA}) and Sec. 3.5.1 tracking",
+    }
+    if name in labels:
+        return labels[name]
+    if name in synth.WORKLOADS and w != synth.WORKLOADS[name]:
+        return f"{w.name}, run at {dims}{it}"
+    return w.name
 
 
 def base_workload(name: str) -> str:
@@ -585,22 +613,7 @@ def run_gpu(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": ("learned-init blend all-pairs 60x512x512 k5 w15: BF16 conv "
-                                f"initialiser (tcgen05) + {args.learned_iters} Alg. 1 iteration(s)"
-                                if learned else
-                                "balanced blend all-pairs 60x512x512 k5 w15 n6: Sec. 3.4 improved "
-                                f"loss, alpha {BALANCED_ALPHA}" if balanced else
-                                f"fast-mode blend 60x512x512 k5 w{w.window} n6: Sec. 3.4 remapping / "
-                                "blending tables and interval queries (Algs. 3-5)" if fast else
-                                "accurate blend all-pairs 60x512x512 k5 w15 n6: Sec. 3.4 mean-remap "
-                                f"alignment loss, alpha {BALANCED_ALPHA}" if accurate else
-                                "aligned + tracking interpolation 48x576x1024 k7 n8 keys 0,47: Eq. 10 "
-                                f"alignment loss (alpha {BALANCED_ALPHA}) and Sec. 3.5.1 tracking"
-                                if aligned else
-                                "tracking interpolation 48x576x1024 k7 n8 keys 0,47: Sec. 3.5.1 "
-                                "chain-neighbour candidates" if tracking and w.mode != "blend" else
-                                f"tracking blend all-pairs 60x512x512 k5 w{w.window} n6: Sec. 3.5.1 "
-                                "chain-neighbour candidates" if tracking else w.name),
+        "config": {"workload": workload_label(args.workload, w, args.learned_iters),
                    "frames": w.N, "height": w.H, "width": w.W,
                    "patch": w.patch, "window": w.window,
                    "iters": w.iters if not learned else args.learned_iters, "levels": w.levels,

@@ -76,3 +76,15 @@ def test_frames_override_truncates_a_two_key_interpolation():
     assert bench.truncate_interpolation(w, g, s, 0)[0] is w
     with pytest.raises(ValueError):
         bench.truncate_interpolation(w, g, s, 1)
+
+
+def test_workload_labels_state_the_sizes_run():
+    w = synth.WORKLOADS["blend_512"]
+    assert bench.workload_label("blend_512", w) == w.name
+    w5 = dataclasses.replace(w, window=5)
+    assert "w5" in bench.workload_label("blend_512", w5) and w.name in bench.workload_label("blend_512", w5)
+    assert "60x512x512 k5 w15 n6" in bench.workload_label("balanced_512", w)
+    wi = synth.WORKLOADS["interp_1024x576"]
+    assert "48x576x1024 k7 keys 0,47 n8" in bench.workload_label("aligned_1024x576", wi)
+    wt = dataclasses.replace(wi, N=12, keys=(0, 11))
+    assert "12x576x1024 k7 keys 0,11 n8" in bench.workload_label("aligned_1024x576", wt)
