@@ -63,6 +63,9 @@ def parse_args(argv=None):
                                                        "aligned_1024x576"])
     ap.add_argument("--window", type=int, default=0,
                     help="override the blend window of the headline-clip workloads (odd)")
+    ap.add_argument("--batch-clips", default="",
+                    help="batch_32: submit only these manifest clips, e.g. 12,13 (small profiling "
+                         "cases)")
     ap.add_argument("--frames", type=int, default=0,
                     help="interpolation workloads: keep the clip's first F frames, keys 0 and "
                          "F - 1 styled with the clip's two key styles (small profiling cases)")
@@ -682,8 +685,11 @@ def run_gpu_batch(args):
     torch.cuda.set_device(local)
     fbp.build()
     manifest = synth.batch_manifest(seed=shard_seed(BATCH_SEED, rank))
+    picked = ([int(i) for i in args.batch_clips.split(",")] if args.batch_clips
+              else list(range(len(manifest))))
+    manifest = [manifest[i] for i in picked]
     clips, host = [], []
-    for n, (N, H, W, window, patch) in enumerate(manifest):
+    for n, (N, H, W, window, patch) in zip(picked, manifest):
         g, s = synth.batch_clip(N, H, W, seed=shard_seed(BATCH_SEED, rank) + n)
         host.append((g, s))
         clips.append((torch.tensor(g, device="cuda"), torch.tensor(s, device="cuda"), window, patch,
@@ -764,8 +770,9 @@ def run_gpu_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": "batched persistent submission of 32 uneven clips "
-                               "(256-1024 px, 16-120 frames, windows 5-31, patch 5/7, n=6)",
+        "config": {"workload": (f"batched persistent submission of {len(manifest)} uneven clips "
+                                "(256-1024 px, 16-120 frames, windows 5-31, patch 5/7, n=6)"
+                                + (f", manifest clips {args.batch_clips}" if args.batch_clips else "")),
                    "frames_per_step": frames, "clips": len(manifest),
                    "nnfs_per_step": sum(sum(min(N - 1, i + (w - 1) // 2) - max(0, i - (w - 1) // 2)
                                             for i in range(N)) for N, H, W, w, k in manifest),
