@@ -311,6 +311,32 @@ typedef struct fb_clip_desc {
 int fb_blend_batch(fb_ctx *ctx, const fb_clip_desc *clips, int n_clips, const fb_params *p,
                    uint32_t flags, void *stream);
 
+/* One NNF of a blend or interpolation call, as the call enumerates it (host-only). */
+typedef struct fb_pair_info {
+    int32_t src;        /* source frame j (blend) or keyframe l / r (interpolation) */
+    int32_t tgt;        /* target frame i: the output frame the NNF is remapped into */
+    uint32_t tag;       /* fb_pair_tag(src, tgt): its random stream */
+    uint32_t weight;    /* integer weight of its remapped style in frame tgt's numerator
+                           (blend: 1; interpolation: Eq. 9's r - i or i - l, or 1) */
+    int32_t prev, next; /* FB_FLAG_TRACKING: the pairs (src -> tgt - 1), (src -> tgt + 1),
+                           or -1 */
+    int32_t partner;    /* FB_FLAG_ALIGN: the other key's pair to tgt, or -1 */
+    int32_t out_frame;  /* = tgt */
+} fb_pair_info;
+
+/* Host-only enumeration of the NNFs of a call (no CUDA calls), in the order the call
+ * computes them: grouped by output frame in increasing order; within a frame, sources in
+ * increasing order (blend) or the left key before the right key (interpolation).
+ *   window > 0: fb_blend_window's pairs (j -> i), 0 < |i - j| <= (window - 1) / 2 inside
+ *               the clip (key_idx NULL, n_keys 0, window odd).
+ *   window = 0: fb_interpolate's pairs for the sorted keys key_idx[0..n_keys).
+ *   flags: FB_FLAG_TRACKING and / or (interpolation) FB_FLAG_ALIGN fill prev / next /
+ *          partner as the tracking and alignment kernels use them.
+ * *n_pairs receives the count; out (capacity cap) may be NULL to query it.  FB_ERR_ARG
+ * for invalid arguments or cap below the count. */
+int fb_pair_plan(int N, int window, const int32_t *key_idx, int n_keys, uint32_t flags,
+                 fb_pair_info *out, size_t cap, size_t *n_pairs);
+
 /* Host-only planning of the fast mode (FB_FLAG_FAST) for N frames and `window`: the
  * number of distinct NNFs it computes, of blending-table entries it builds and of query
  * pieces it remaps (the direct sum of Eq. 2 computes sum_i (window_i - 1) NNFs).  No CUDA

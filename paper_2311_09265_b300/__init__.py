@@ -25,7 +25,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a",
                     "fb_debug_candidates_considered", "fb_pair_tag",
                     "fb_nnf", "fb_nnf_balanced", "fb_nnf_segment", "fb_remap", "fb_blend_window", "fb_interpolate",
-                    "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan", "fb_fast_plan",
+                    "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan", "fb_fast_plan", "fb_pair_plan",
                     "fb_ctx_batch_variant", "fb_ctx_set_pair_budget",
                     "fb_initnet_create", "fb_initnet_destroy", "fb_initnet_last_error",
                     "fb_initnet_param_count", "fb_initnet_get_params", "fb_initnet_set_params",
@@ -66,6 +66,13 @@ class Params(ctypes.Structure):
              pair_tag: int = 0, flags: int = 0, alpha: int = 0) -> "Params":
         return cls(patch, iters, levels, r0, seed & 0xFFFFFFFFFFFFFFFF, pair_tag & 0xFFFFFFFF,
                    flags, alpha)
+
+
+class PairInfo(ctypes.Structure):
+    """fb_pair_info: one NNF of a blend or interpolation call."""
+    _fields_ = [("src", ctypes.c_int32), ("tgt", ctypes.c_int32), ("tag", ctypes.c_uint32),
+                ("weight", ctypes.c_uint32), ("prev", ctypes.c_int32), ("next", ctypes.c_int32),
+                ("partner", ctypes.c_int32), ("out_frame", ctypes.c_int32)]
 
 
 class ClipDesc(ctypes.Structure):
@@ -125,6 +132,9 @@ def lib() -> ctypes.CDLL:
         L.fb_nnf_balanced.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp,
                                       _vp, _vp, _vp]
         L.fb_fast_plan.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.POINTER(ctypes.c_uint64)] * 3
+        L.fb_pair_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
+                                   ctypes.c_uint32, ctypes.POINTER(PairInfo), ctypes.c_size_t,
+                                   ctypes.POINTER(ctypes.c_size_t)]
         L.fb_remap.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, _vp, _vp]
         L.fb_blend_window.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                       ctypes.c_int, P, _vp, _vp]
@@ -191,6 +201,24 @@ def fb_fast_plan(N: int, window: int):
     if rc != FB_OK:
         raise FastBlendError(rc, "fb_fast_plan")
     return int(a.value), int(b.value), int(c.value)
+
+
+def fb_pair_plan(N: int, window: int = 0, keys=None, flags: int = 0):
+    """The NNFs a blend (window > 0) or interpolation (keys) call enumerates, in its order
+    (host only): a list of dicts with src, tgt, tag, weight, prev, next, partner, out_frame."""
+    karr, nk = None, 0
+    if keys is not None:
+        nk = len(keys)
+        karr = (ctypes.c_int32 * max(nk, 1))(*keys)
+    n = ctypes.c_size_t()
+    rc = lib().fb_pair_plan(N, window, karr, nk, flags, None, 0, ctypes.byref(n))
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_pair_plan")
+    out = (PairInfo * max(n.value, 1))()
+    rc = lib().fb_pair_plan(N, window, karr, nk, flags, out, n.value, ctypes.byref(n))
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_pair_plan")
+    return [{f: getattr(out[q], f) for f, _ in PairInfo._fields_} for q in range(n.value)]
 
 
 def fb_debug_candidates_considered(reset: bool = False) -> int:

@@ -466,6 +466,61 @@ void set_chain_neighbours(std::vector<PairDesc>& pairs) {
     }
 }
 
+// Eq. 2 (a1, blending): one job per output frame i; its pairs are (j -> i) for j in the
+// window [i - M, i + M] truncated to the clip, j != i, in increasing j, each weight 1.
+void blend_pairs(int N, int k, int window, uint32_t flags, std::vector<PairDesc>& pairs,
+                 std::vector<JobDesc>& jobs) {
+    const int M = (window - 1) / 2;
+    pairs.clear();
+    jobs.assign(N, JobDesc{});
+    for (int i = 0; i < N; ++i) {
+        const int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
+        jobs[i] = JobDesc{i, i, 1u, static_cast<int32_t>(pairs.size()), hi - lo,
+                          static_cast<uint32_t>(255 * k * k * (hi - lo + 1)), {0, 0}};
+        for (int j = lo; j <= hi; ++j)
+            if (j != i) pairs.push_back(PairDesc{j, i, fb_pair_tag(j, i), j, 1u, {-1, -1, -1}});
+    }
+    if (flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
+}
+
+// Sec. 3.5.2 (a1, interpolation; Eq. 9): keys are copied; a frame between keys l < i < r
+// takes the pairs (l -> i) with weight r - i and (r -> i) with weight i - l over r - l
+// (Eq. 10 partners of each other under FB_FLAG_ALIGN); a frame outside the key range
+// takes its nearest key alone, weight 1.  Key styles are indexed by key number.
+void interp_pairs(int N, int k, const int32_t* key_idx, int n_keys, uint32_t flags,
+                  std::vector<PairDesc>& pairs, std::vector<JobDesc>& jobs) {
+    const uint32_t kk255 = static_cast<uint32_t>(255 * k * k);
+    pairs.clear();
+    jobs.assign(N, JobDesc{});
+    int m_left = -1;  // last key index < i
+    int next = 0;     // first key with frame >= i
+    for (int i = 0; i < N; ++i) {
+        while (next < n_keys && key_idx[next] < i) m_left = next++;
+        const bool is_key = next < n_keys && key_idx[next] == i;
+        const int m_right = is_key ? (next + 1 < n_keys ? next + 1 : -1) : (next < n_keys ? next : -1);
+        JobDesc j{i, -1, 0u, static_cast<int32_t>(pairs.size()), 0, kk255, {0, 0}};
+        if (is_key) {
+            j.self_style = next;
+            j.self_w = 1u;
+        } else if (m_left >= 0 && m_right >= 0) {
+            const int l = key_idx[m_left], r = key_idx[m_right];
+            const int q = static_cast<int>(pairs.size());
+            const int32_t pl = (flags & FB_FLAG_ALIGN) ? q + 1 : -1, pr = (flags & FB_FLAG_ALIGN) ? q : -1;
+            pairs.push_back(PairDesc{l, i, fb_pair_tag(l, i), m_left, static_cast<uint32_t>(r - i), {-1, -1, pl}});
+            pairs.push_back(PairDesc{r, i, fb_pair_tag(r, i), m_right, static_cast<uint32_t>(i - l), {-1, -1, pr}});
+            j.n_pairs = 2;
+            j.den = kk255 * static_cast<uint32_t>(r - l);
+        } else {
+            const int m = m_left >= 0 ? m_left : m_right;
+            const int l = key_idx[m];
+            pairs.push_back(PairDesc{l, i, fb_pair_tag(l, i), m, 1u, {-1, -1, -1}});
+            j.n_pairs = 1;
+        }
+        jobs[i] = j;
+    }
+    if (flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
+}
+
 // Group consecutive output jobs into chunks whose pairs fit the F/E budget.
 struct Chunk {
     int job0, n_jobs, pair0, n_pairs;
@@ -1212,6 +1267,33 @@ void count_launches(fb_ctx* ctx, int n) {
 }
 }  // namespace fb
 
+extern "C" int fb_pair_plan(int N, int window, const int32_t* key_idx, int n_keys, uint32_t flags,
+                            fb_pair_info* out, size_t cap, size_t* n_pairs) {
+    if (N < 1 || N > 65535) return FB_ERR_ARG;
+    if (flags & ~(FB_FLAG_TRACKING | FB_FLAG_ALIGN)) return FB_ERR_ARG;
+    std::vector<PairDesc> pairs;
+    std::vector<JobDesc> jobs;
+    if (window > 0) {
+        if ((window & 1) == 0 || key_idx || n_keys || (flags & FB_FLAG_ALIGN)) return FB_ERR_ARG;
+        blend_pairs(N, 3, window, flags, pairs, jobs);
+    } else {
+        if (window < 0 || !key_idx || n_keys < 1 || n_keys > N) return FB_ERR_ARG;
+        for (int m = 0; m < n_keys; ++m)
+            if (key_idx[m] < 0 || key_idx[m] >= N || (m > 0 && key_idx[m] <= key_idx[m - 1])) return FB_ERR_ARG;
+        interp_pairs(N, 3, key_idx, n_keys, flags, pairs, jobs);
+    }
+    if (n_pairs) *n_pairs = pairs.size();
+    if (!out) return FB_OK;
+    if (cap < pairs.size()) return FB_ERR_ARG;
+    for (const JobDesc& j : jobs)
+        for (int q = 0; q < j.n_pairs; ++q) {
+            const PairDesc& pd = pairs[j.first_pair + q];
+            out[j.first_pair + q] = fb_pair_info{pd.src, pd.tgt, pd.tag, pd.weight, pd.pad[0], pd.pad[1],
+                                                 pd.pad[2], j.out_frame};
+        }
+    return FB_OK;
+}
+
 extern "C" int fb_fast_plan(int N, int window, uint64_t* n_nnfs, uint64_t* n_entries,
                             uint64_t* n_pieces) {
     if (N < 1 || N > 65535 || window < 1 || (window & 1) == 0) return FB_ERR_ARG;
@@ -1659,7 +1741,7 @@ int fb_blend_window(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles, i
     if (!guides || !styles || !out)
         return fail(ctx, FB_ERR_ARG, "guides, styles and out must be non-NULL");
     if (p->flags & FB_FLAG_ALIGN) return fail(ctx, FB_ERR_ARG, "FB_FLAG_ALIGN applies to fb_interpolate only");
-    const int k = p->patch, M = (window - 1) / 2;
+    const int k = p->patch;
     if (p->flags & FB_FLAG_FAST) {
         const uint64_t k4 = static_cast<uint64_t>(k) * k * k * k;
         if (k4 * 255u * static_cast<uint64_t>(window) >= (1ull << 32))
@@ -1670,18 +1752,9 @@ int fb_blend_window(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles, i
         return run_fast_pipeline(ctx, guides, styles, N, H, W, plan, p, out, static_cast<cudaStream_t>(stream));
     }
 
-    // Eq. 2: one job per output frame; its pairs are (j -> i) for j in the truncated
-    // window, j != i, in increasing j.
     std::vector<PairDesc> pairs;
-    std::vector<JobDesc> jobs(N);
-    for (int i = 0; i < N; ++i) {
-        const int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
-        jobs[i] = JobDesc{i, i, 1u, static_cast<int32_t>(pairs.size()), hi - lo,
-                          static_cast<uint32_t>(255 * k * k * (hi - lo + 1)), {0, 0}};
-        for (int j = lo; j <= hi; ++j)
-            if (j != i) pairs.push_back(PairDesc{j, i, fb_pair_tag(j, i), j, 1u, {0, 0, 0}});
-    }
-    if (p->flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
+    std::vector<JobDesc> jobs;
+    blend_pairs(N, k, window, p->flags, pairs, jobs);
     DeviceGuard dg(ctx->device);
     return run_pipeline(ctx, guides, N, H, W, styles, N, pairs, jobs, p, out,
                         static_cast<cudaStream_t>(stream));
@@ -1707,47 +1780,9 @@ int fb_interpolate(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, cons
         if (m > 0 && key_idx[m] <= key_idx[m - 1])
             return fail(ctx, FB_ERR_ARG, "key_idx must be strictly increasing");
     }
-    const int k = p->patch;
-    const uint32_t kk255 = static_cast<uint32_t>(255 * k * k);
-
-    // Sec. 3.5.2: keys are copied; between keys l < i < r the weights are (r - i) for
-    // S_l and (i - l) for S_r over (r - l); outside the key range the nearest key alone.
     std::vector<PairDesc> pairs;
-    std::vector<JobDesc> jobs(N);
-    int m_left = -1;  // last key index < i
-    int next = 0;     // first key with frame >= i
-    for (int i = 0; i < N; ++i) {
-        while (next < n_keys && key_idx[next] < i) m_left = next++;
-        const bool is_key = next < n_keys && key_idx[next] == i;
-        const int m_right = is_key ? (next + 1 < n_keys ? next + 1 : -1) : (next < n_keys ? next : -1);
-        JobDesc j{i, -1, 0u, static_cast<int32_t>(pairs.size()), 0, kk255, {0, 0}};
-        if (is_key) {
-            j.self_style = next;
-            j.self_w = 1u;
-        } else if (m_left >= 0 && m_right >= 0) {
-            const int l = key_idx[m_left], r = key_idx[m_right];
-            pairs.push_back(PairDesc{l, i, fb_pair_tag(l, i), m_left, static_cast<uint32_t>(r - i), {0, 0, 0}});
-            pairs.push_back(PairDesc{r, i, fb_pair_tag(r, i), m_right, static_cast<uint32_t>(i - l), {0, 0, 0}});
-            j.n_pairs = 2;
-            j.den = kk255 * static_cast<uint32_t>(r - l);
-        } else {
-            const int m = m_left >= 0 ? m_left : m_right;
-            const int l = key_idx[m];
-            pairs.push_back(PairDesc{l, i, fb_pair_tag(l, i), m, 1u, {0, 0, 0}});
-            j.n_pairs = 1;
-        }
-        jobs[i] = j;
-    }
-    if (p->flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
-    if (p->flags & FB_FLAG_ALIGN) {
-        // Eq. 10: the two pairs of a frame between keys are each other's partner.
-        for (PairDesc& pd : pairs) pd.pad[2] = -1;
-        for (const JobDesc& j : jobs)
-            if (j.n_pairs == 2) {
-                pairs[j.first_pair].pad[2] = j.first_pair + 1;
-                pairs[j.first_pair + 1].pad[2] = j.first_pair;
-            }
-    }
+    std::vector<JobDesc> jobs;
+    interp_pairs(N, p->patch, key_idx, n_keys, p->flags, pairs, jobs);
     DeviceGuard dg(ctx->device);
     return run_pipeline(ctx, guides, N, H, W, key_styles, n_keys, pairs, jobs, p, out,
                         static_cast<cudaStream_t>(stream));
