@@ -441,6 +441,16 @@ int fb_conv3x3_backward(const uint16_t *x, int n, int H, int W, int Cin, const u
                         int Cout, int stride, const uint16_t *dz, float *dx, float *dw,
                         int *status, void *stream);
 
+/* Operand staging of the forward convolutions (process-wide; for tests and
+ * measurement).  mode 0 (default): stride-1 layers whose output rows tile 128-pixel
+ * blocks stage both operands with tiled TMA loads (the activation box displaced per tap,
+ * zero-filled outside the image, 128-byte swizzle); other layers, and every layer in
+ * mode 1, gather them with cp.async.  Both accumulate the same products in the same
+ * order, so the outputs are identical.  mode -1 leaves the setting; *tma_launches
+ * (nullable) receives the number of TMA-staged launches so far.  FB_ERR_ARG for other
+ * modes. */
+int fb_conv_gemm_path(int mode, uint64_t *tma_launches);
+
 /* Bytes of the fixed device scratch array used by fb_blend_window_noalloc. */
 #define FB_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 

@@ -29,7 +29,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_ctx_batch_variant", "fb_ctx_set_pair_budget",
                     "fb_initnet_create", "fb_initnet_destroy", "fb_initnet_last_error",
                     "fb_initnet_param_count", "fb_initnet_get_params", "fb_initnet_set_params",
-                    "fb_initnet_get_grads", "fb_initnet_forward", "fb_initnet_init_nnf",
+                    "fb_initnet_get_grads", "fb_initnet_forward", "fb_initnet_init_nnf", "fb_conv_gemm_path",
                     "fb_initnet_train_step", "fb_initnet_status", "fb_conv3x3_forward",
                     "fb_conv3x3_backward", "fb_ctx_set_initnet", "fb_ctx_energy",
                     "fb_initnet_targets")
@@ -132,6 +132,7 @@ def lib() -> ctypes.CDLL:
         L.fb_nnf_balanced.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp,
                                       _vp, _vp, _vp]
         L.fb_fast_plan.argtypes = [ctypes.c_int, ctypes.c_int] + [ctypes.POINTER(ctypes.c_uint64)] * 3
+        L.fb_conv_gemm_path.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_uint64)]
         L.fb_pair_plan.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_int32), ctypes.c_int,
                                    ctypes.c_uint32, ctypes.POINTER(PairInfo), ctypes.c_size_t,
                                    ctypes.POINTER(ctypes.c_size_t)]
@@ -219,6 +220,16 @@ def fb_pair_plan(N: int, window: int = 0, keys=None, flags: int = 0):
     if rc != FB_OK:
         raise FastBlendError(rc, "fb_pair_plan")
     return [{f: getattr(out[q], f) for f, _ in PairInfo._fields_} for q in range(n.value)]
+
+
+def fb_conv_gemm_path(mode: int = -1) -> int:
+    """Set the forward convolutions' operand staging (0: TMA where eligible, 1: cp.async
+    gathers; -1: unchanged); returns the number of TMA-staged launches so far."""
+    n = ctypes.c_uint64()
+    rc = lib().fb_conv_gemm_path(mode, ctypes.byref(n))
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_conv_gemm_path")
+    return int(n.value)
 
 
 def fb_debug_candidates_considered(reset: bool = False) -> int:

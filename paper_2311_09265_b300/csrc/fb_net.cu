@@ -16,14 +16,18 @@
 //   d0  [up(d1), e0b] 96->32         (Hq)
 //   head 32->8 (channels 0,1 used): offset = 16 * head, in full-resolution pixels
 // 3x3 kernels, zero padding, ReLU after every layer but the head; 779,592 parameters.
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <string>
 #include <vector>
 
+#include <cudaTypedefs.h>
+
 #include "fb.h"
 #include "fb_internal.h"
 #include "fb_net_ops.cuh"
+#include "fb_tc_tma.cuh"
 
 namespace fb {
 namespace net {
@@ -73,10 +77,96 @@ cudaError_t launch_gemm_async(const G& gth, const E& epi, int M, int N, int K, i
     return cudaGetLastError();
 }
 
+// ---- TMA-staged forward convolution (stride 1) ---------------------------------------
+constexpr int kTmaStages = 4;
+std::atomic<int> g_gemm_path{0};              // 0: TMA where eligible; 1: gathers only
+std::atomic<unsigned long long> g_tma_launches{0};
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+    static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+    }();
+    return fn;
+}
+
+// The TMA path needs whole output rows per 128-pixel tile: W divides 128 and either an
+// image holds a multiple of 128 pixels (R = 128 / W rows) or 128 is a multiple of the
+// image (I images of R = H rows); 16-byte aligned tensors and strides (Cin % 8 == 0).
+bool tma_conv_geom(const ConvGeom& g, const void* X, const void* Wt, tc::TmaConvGeom& t) {
+    if (g.stride != 1 || g.Cin % 8 || g.W < 1 || 128 % g.W || g.Cout > 128) return false;
+    if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Wt)) & 15) return false;
+    const int px = g.H * g.W;
+    int R, I;
+    if (px >= 128) {
+        if (px % 128) return false;
+        R = 128 / g.W;
+        I = 1;
+    } else {
+        if (128 % px) return false;
+        R = g.H;
+        I = 128 / px;
+    }
+    t = tc::TmaConvGeom{g.H, g.W, g.Cin, g.Cout, g.n * px, R, I};
+    return true;
+}
+
+template <int BN>
+cudaError_t launch_conv_tma(const ConvGeom& g, const tc::TmaConvGeom& t, const bf16* X, const bf16* Wt,
+                            const EpiFwd& epi, int* status, cudaStream_t st, bool* used) {
+    *used = false;
+    const auto encode = tensor_map_encoder();
+    if (!encode) return cudaSuccess;
+    alignas(64) CUtensorMap mx, mw;
+    const cuuint64_t xdim[4] = {static_cast<cuuint64_t>(g.Cin), static_cast<cuuint64_t>(g.W),
+                                static_cast<cuuint64_t>(g.H), static_cast<cuuint64_t>(g.n)};
+    const cuuint64_t xstr[3] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(g.W) * g.Cin * 2,
+                                static_cast<cuuint64_t>(g.H) * g.W * g.Cin * 2};
+    const cuuint32_t xbox[4] = {static_cast<cuuint32_t>(tc::BK), static_cast<cuuint32_t>(g.W),
+                                static_cast<cuuint32_t>(t.R), static_cast<cuuint32_t>(t.I)};
+    const cuuint64_t wdim[3] = {static_cast<cuuint64_t>(g.Cin), 9, static_cast<cuuint64_t>(g.Cout)};
+    const cuuint64_t wstr[2] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(9) * g.Cin * 2};
+    const cuuint32_t wbox[3] = {static_cast<cuuint32_t>(tc::BK), 1, static_cast<cuuint32_t>(BN)};
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    if (encode(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), xdim, xstr, xbox, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        encode(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(Wt), wdim, wstr, wbox, ones,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return cudaSuccess;  // not expressible as tensor maps: the gather path runs instead
+    constexpr int smem = tc::conv_tma_smem_bytes<BN, kTmaStages>();
+    auto kern = tc::tc_conv_tma_kernel<BN, kTmaStages, EpiFwd>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((t.M + tc::BM - 1) / tc::BM, (g.Cout + BN - 1) / BN);
+    kern<<<grid, 128, smem, st>>>(mx, mw, epi, t, status);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        *used = true;
+        ++g_tma_launches;
+    }
+    return e;
+}
+
 cudaError_t conv_forward(const ConvGeom& g, const bf16* X, const bf16* Wt, const float* bias,
                          int relu, bf16* Y, float* Yf, int* status, cudaStream_t st) {
     const int M = g.n * g.Ho * g.Wo, K = 9 * g.Cin, ncb = (g.Cin + 63) / 64;
     EpiFwd epi{Y, Yf, bias, g.Cout, relu};
+    tc::TmaConvGeom t;
+    if (g_gemm_path.load() == 0 && tma_conv_geom(g, X, Wt, t)) {
+        bool used = false;
+        cudaError_t e = g.Cout <= 16   ? launch_conv_tma<16>(g, t, X, Wt, epi, status, st, &used)
+                        : g.Cout <= 32 ? launch_conv_tma<32>(g, t, X, Wt, epi, status, st, &used)
+                        : g.Cout <= 64 ? launch_conv_tma<64>(g, t, X, Wt, epi, status, st, &used)
+                                       : launch_conv_tma<128>(g, t, X, Wt, epi, status, st, &used);
+        if (e != cudaSuccess || used) return e;
+    }
     if (g.Cout <= 16) return launch_gemm_async<16>(GatherFwd<16>{X, Wt, g, M, K, ncb}, epi, M, g.Cout, K, status, st);
     if (g.Cout <= 32) return launch_gemm_async<32>(GatherFwd<32>{X, Wt, g, M, K, ncb}, epi, M, g.Cout, K, status, st);
     if (g.Cout <= 64) return launch_gemm_async<64>(GatherFwd<64>{X, Wt, g, M, K, ncb}, epi, M, g.Cout, K, status, st);
@@ -726,6 +816,13 @@ int fb_initnet_status(fb_initnet* net) {
     int s = 0;
     NET_CUDA(net, cudaMemcpy(&s, net->status, 4, cudaMemcpyDeviceToHost));
     return s ? FB_ERR_TIMEOUT : FB_OK;
+}
+
+int fb_conv_gemm_path(int mode, uint64_t* tma_launches) {
+    if (mode < -1 || mode > 1) return FB_ERR_ARG;
+    if (tma_launches) *tma_launches = fb::net::g_tma_launches.load();
+    if (mode >= 0) fb::net::g_gemm_path.store(mode);
+    return FB_OK;
 }
 
 // Single-layer entry points (used by the gradient checks against the CPU oracle).
