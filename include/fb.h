@@ -442,10 +442,10 @@ int fb_conv3x3_backward(const uint16_t *x, int n, int H, int W, int Cin, const u
                         int *status, void *stream);
 
 /* Operand staging of the forward convolutions (process-wide; for tests and
- * measurement).  mode 0 (default): stride-1 layers whose output rows tile 128-pixel
- * blocks stage both operands with tiled TMA loads (the activation box displaced per tap,
- * zero-filled outside the image, 128-byte swizzle); other layers, and every layer in
- * mode 1, gather them with cp.async.  Both accumulate the same products in the same
+ * measurement).  mode 0 (default): layers whose output rows tile 128-pixel blocks stage
+ * both operands with tiled TMA loads (the activation box displaced per tap and traversed
+ * with the layer's stride, zero-filled outside the image, 128-byte swizzle); other
+ * layers, and every layer in mode 1, gather them with cp.async.  Both accumulate the same products in the same
  * order, so the outputs are identical.  mode -1 leaves the setting; *tma_launches
  * (nullable) receives the number of TMA-staged launches so far.  FB_ERR_ARG for other
  * modes. */

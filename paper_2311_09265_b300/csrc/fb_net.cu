@@ -95,24 +95,26 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
     return fn;
 }
 
-// The TMA path needs whole output rows per 128-pixel tile: W divides 128 and either an
-// image holds a multiple of 128 pixels (R = 128 / W rows) or 128 is a multiple of the
-// image (I images of R = H rows); 16-byte aligned tensors and strides (Cin % 8 == 0).
+// The TMA path needs whole output rows per 128-pixel tile: Wo divides 128 and either an
+// image holds a multiple of 128 output pixels (R = 128 / Wo rows) or 128 is a multiple
+// of the image (I images of R = Ho rows); 16-byte aligned tensors and strides
+// (Cin % 8 == 0); the strided box s Wo within the TMA limit of 256.
 bool tma_conv_geom(const ConvGeom& g, const void* X, const void* Wt, tc::TmaConvGeom& t) {
-    if (g.stride != 1 || g.Cin % 8 || g.W < 1 || 128 % g.W || g.Cout > 128) return false;
+    if ((g.stride != 1 && g.stride != 2) || g.Cin % 8 || g.Wo < 1 || 128 % g.Wo || g.Cout > 128) return false;
     if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Wt)) & 15) return false;
-    const int px = g.H * g.W;
+    const int px = g.Ho * g.Wo;
     int R, I;
     if (px >= 128) {
         if (px % 128) return false;
-        R = 128 / g.W;
+        R = 128 / g.Wo;
         I = 1;
     } else {
         if (128 % px) return false;
-        R = g.H;
+        R = g.Ho;
         I = 128 / px;
     }
-    t = tc::TmaConvGeom{g.H, g.W, g.Cin, g.Cout, g.n * px, R, I};
+    if (g.stride * g.Wo > 256 || g.stride * R > 256) return false;
+    t = tc::TmaConvGeom{g.Ho, g.Wo, g.Cin, g.Cout, g.n * px, R, I, g.stride};
     return true;
 }
 
@@ -127,13 +129,14 @@ cudaError_t launch_conv_tma(const ConvGeom& g, const tc::TmaConvGeom& t, const b
                                 static_cast<cuuint64_t>(g.H), static_cast<cuuint64_t>(g.n)};
     const cuuint64_t xstr[3] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(g.W) * g.Cin * 2,
                                 static_cast<cuuint64_t>(g.H) * g.W * g.Cin * 2};
-    const cuuint32_t xbox[4] = {static_cast<cuuint32_t>(tc::BK), static_cast<cuuint32_t>(g.W),
-                                static_cast<cuuint32_t>(t.R), static_cast<cuuint32_t>(t.I)};
+    const cuuint32_t xbox[4] = {static_cast<cuuint32_t>(tc::BK), static_cast<cuuint32_t>(g.stride * g.Wo),
+                                static_cast<cuuint32_t>(g.stride * t.R), static_cast<cuuint32_t>(t.I)};
+    const cuuint32_t xstep[4] = {1, static_cast<cuuint32_t>(g.stride), static_cast<cuuint32_t>(g.stride), 1};
     const cuuint64_t wdim[3] = {static_cast<cuuint64_t>(g.Cin), 9, static_cast<cuuint64_t>(g.Cout)};
     const cuuint64_t wstr[2] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(9) * g.Cin * 2};
     const cuuint32_t wbox[3] = {static_cast<cuuint32_t>(tc::BK), 1, static_cast<cuuint32_t>(BN)};
     const cuuint32_t ones[4] = {1, 1, 1, 1};
-    if (encode(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), xdim, xstr, xbox, ones,
+    if (encode(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), xdim, xstr, xbox, xstep,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
         encode(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(Wt), wdim, wstr, wbox, ones,

@@ -1,15 +1,16 @@
-// fb_tc_tma.cuh -- the stride-1 forward 3x3 convolution of the learned NNF initialiser as
-// a tcgen05 GEMM whose operands the Tensor Memory Accelerator stages:
+// fb_tc_tma.cuh -- the forward 3x3 convolution (stride s = 1 or 2) of the learned NNF
+// initialiser as a tcgen05 GEMM whose operands the Tensor Memory Accelerator stages:
 //
-//   Y[p][co] = sum_{tap, ci} X[p + tap - (1, 1)][ci] W[co][tap][ci]      (M = pixels,
-//   N = Cout, K = 9 Cin, walked tap-major in blocks of 64 input channels)
+//   Y[p][co] = sum_{tap, ci} X[s p + tap - (1, 1)][ci] W[co][tap][ci]    (M = output
+//   pixels, N = Cout, K = 9 Cin, walked tap-major in blocks of 64 input channels)
 //
-// A CTA of 128 threads owns 128 output pixels -- whole rows of the NHWC activation
-// (R rows of one image, or I whole images when an image has fewer than 128 pixels) --
-// by BN output channels.  For K chunk (tap, channel block) one elected thread issues two
-// tiled TMA loads into a stage of shared memory: the activation box {64 channels, W, R,
-// I} displaced by the tap (coordinates -1 and W fall outside the image and are filled
-// with zeros: the convolution's padding, no bounds arithmetic in the kernel) and the
+// A CTA of 128 threads owns 128 output pixels -- whole output rows (R rows of one image,
+// or I whole images when an image has fewer than 128 output pixels) -- by BN output
+// channels.  For K chunk (tap, channel block) one elected thread issues two tiled TMA
+// loads into a stage of shared memory: the activation box {64 channels, s Wo, s R, I}
+// traversed with element stride s along the image axes and displaced by the tap
+// (coordinates -1 and beyond the image are filled with zeros: the convolution's padding,
+// no bounds arithmetic in the kernel), which lands as the 128 x 64 A tile, and the
 // weight box {64 channels, 1 tap, BN}.  Both land in the 128-byte-swizzled K-major
 // layout the tensor core reads (128-byte rows, 8-row atoms 1024 bytes apart), signalled
 // by the stage's "full" mbarrier with the byte count; the same thread waits for it,
@@ -63,13 +64,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-// Geometry of the TMA convolution: output = input size (stride 1); a tile is R rows of
-// one image (I = 1) or I whole images (R = H).
+// Geometry of the TMA convolution: output Ho x Wo; a tile is R output rows of one image
+// (I = 1) or I whole images (R = Ho).
 struct TmaConvGeom {
-    int H, W, Cin;   // activation
+    int Ho, Wo, Cin;  // output size, input channels
     int Cout;
-    int M;           // n * H * W output pixels
-    int R, I;        // box rows and images per 128-pixel tile
+    int M;            // n * Ho * Wo output pixels
+    int R, I;         // output rows and images per 128-pixel tile
+    int stride;
 };
 
 template <int BN, int S, class Epi>
@@ -91,8 +93,8 @@ __global__ void __launch_bounds__(128)
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int ncb = (g.Cin + BK - 1) / BK;
     const int n_chunks = 9 * ncb;
-    const int img0 = m0 / (g.H * g.W);
-    const int y0 = (m0 - img0 * g.H * g.W) / g.W;
+    const int img0 = m0 / (g.Ho * g.Wo);
+    const int y0 = (m0 - img0 * g.Ho * g.Wo) / g.Wo;
     // 1024-byte alignment of every stage (the swizzle atoms) inside the dynamic buffer
     const uint32_t s0 = (smem_u32(smem) + 1023u) & ~1023u;
 
@@ -126,7 +128,7 @@ __global__ void __launch_bounds__(128)
             const int dy = tap / 3, dx = tap - 3 * dy;
             const uint32_t sa = s0 + s * STAGE;
             mbar_expect_tx(&full[s], static_cast<uint32_t>(STAGE));
-            tma_load_4d(sa, &map_x, &full[s], BK * cb, dx - 1, y0 + dy - 1, img0);
+            tma_load_4d(sa, &map_x, &full[s], BK * cb, dx - 1, g.stride * y0 + dy - 1, img0);
             tma_load_3d(sa + A_BYTES, &map_w, &full[s], BK * cb, tap, n0);
             ++issued;
         };

@@ -1,5 +1,6 @@
 """The TMA-staged forward convolution (tiled TMA loads of the activation box displaced per
-tap and of the weight box, 128-byte swizzle, tcgen05 MMAs) against the cp.async gather
+tap and strided by the layer's stride, and of the weight box, 128-byte swizzle, tcgen05
+MMAs) against the cp.async gather
 path of the same GEMM, which accumulates the same products in the same order: the
 outputs must be bit-identical; and against the FP64 CPU oracle."""
 import numpy as np
@@ -35,31 +36,33 @@ def run(fbp, x, w, b, stride, relu, out_f32, mode):
     return (y.float() if not out_f32 else y).cpu().numpy(), fbp.fb_conv_gemm_path(-1) - n0
 
 
-TMA_CASES = [  # n, H, W, Cin, Cout: the initialiser's stride-1 layers at 512x512 / 8 and more
-    (2, 64, 64, 32, 32), (1, 64, 64, 8, 32), (2, 32, 32, 64, 64), (3, 16, 16, 96, 96),
-    (4, 8, 8, 128, 128), (3, 8, 8, 128, 128), (2, 16, 16, 224, 96), (2, 32, 32, 160, 64),
-    (2, 64, 64, 96, 32), (2, 64, 64, 32, 8), (1, 4, 32, 40, 24), (5, 4, 4, 16, 16),
+TMA_CASES = [  # n, H, W, Cin, Cout, stride: the initialiser's layers at 512x512 / 8 and more
+    (2, 64, 64, 32, 32, 1), (1, 64, 64, 8, 32, 1), (2, 32, 32, 64, 64, 1), (3, 16, 16, 96, 96, 1),
+    (4, 8, 8, 128, 128, 1), (3, 8, 8, 128, 128, 1), (2, 16, 16, 224, 96, 1), (2, 32, 32, 160, 64, 1),
+    (2, 64, 64, 96, 32, 1), (2, 64, 64, 32, 8, 1), (1, 4, 32, 40, 24, 1), (5, 4, 4, 16, 16, 1),
+    (2, 64, 64, 32, 64, 2), (2, 32, 32, 64, 96, 2), (3, 16, 16, 96, 128, 2), (1, 16, 15, 32, 32, 2),
+    (3, 8, 8, 64, 32, 2),
 ]
 
 
-@pytest.mark.parametrize("n,H,W,Cin,Cout", TMA_CASES)
-def test_tma_conv_is_bit_identical_to_the_gather_path(fbp, n, H, W, Cin, Cout):
+@pytest.mark.parametrize("n,H,W,Cin,Cout,stride", TMA_CASES)
+def test_tma_conv_is_bit_identical_to_the_gather_path(fbp, n, H, W, Cin, Cout, stride):
     rng = np.random.default_rng(n * 1000 + H * W + Cin + Cout)
     x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
     w = ref.bf16(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin))
     b = rng.normal(size=Cout).astype(np.float32).astype(np.float64)
     for relu, out_f32 in ((False, True), (True, False)):
-        yg, used_g = run(fbp, x, w, b, 1, relu, out_f32, mode=1)
-        yt, used_t = run(fbp, x, w, b, 1, relu, out_f32, mode=0)
+        yg, used_g = run(fbp, x, w, b, stride, relu, out_f32, mode=1)
+        yt, used_t = run(fbp, x, w, b, stride, relu, out_f32, mode=0)
         assert used_g == 0 and used_t == 1
         assert np.array_equal(yt.view(np.uint32) if out_f32 else yt, yg.view(np.uint32) if out_f32 else yg)
-    want = ref.conv3x3(x, w, b, 1)
-    y32, _ = run(fbp, x, w, b, 1, False, True, mode=0)
+    want = ref.conv3x3(x, w, b, stride)
+    y32, _ = run(fbp, x, w, b, stride, False, True, mode=0)
     assert float(np.linalg.norm(y32 - want) / np.linalg.norm(want)) < 1e-5
 
 
 @pytest.mark.parametrize("n,H,W,Cin,Cout,stride", [(2, 17, 23, 32, 64, 1), (2, 24, 24, 32, 32, 1),
-                                                  (2, 64, 64, 32, 64, 2)])
+                                                  (2, 48, 48, 32, 64, 2)])
 def test_layers_the_tma_boxes_cannot_tile_use_the_gathers(fbp, n, H, W, Cin, Cout, stride):
     rng = np.random.default_rng(7)
     x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
