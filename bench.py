@@ -881,8 +881,8 @@ def run_gpu_initnet(args):
                    "pairs_per_step": INITNET_PAIRS, "flops_per_pair": flops // INITNET_PAIRS,
                    "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"{world} independent replica(s), one per GPU"},
-        "roofline": {"bound": "tensor", "kernel": "whole forward (12 tc_gemm convolutions + "
-                     "input and head kernels)", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "tensor", "kernel": "whole forward (12 TMA-fed tcgen05 convolutions + "
+                     "input, concatenation and head kernels)", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
                      "peak_basis": f"bf16 dense, {basis} (cuBLAS burst)"},
         "e2e": None, "gpu_launches": ctx.launches - launches0, "clocks": clk.summary(),

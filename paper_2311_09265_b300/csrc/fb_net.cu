@@ -78,7 +78,10 @@ cudaError_t launch_gemm_async(const G& gth, const E& epi, int M, int N, int K, i
 }
 
 // ---- TMA-staged forward convolution (stride 1) ---------------------------------------
-constexpr int kTmaStages = 4;
+#ifndef FB_TMA_STAGES
+#define FB_TMA_STAGES 3
+#endif
+constexpr int kTmaStages = FB_TMA_STAGES;
 std::atomic<int> g_gemm_path{0};              // 0: TMA where eligible; 1: gathers only
 std::atomic<unsigned long long> g_tma_launches{0};
 
@@ -114,7 +117,7 @@ bool tma_conv_geom(const ConvGeom& g, const void* X, const void* Wt, tc::TmaConv
         I = 128 / px;
     }
     if (g.stride * g.Wo > 256 || g.stride * R > 256) return false;
-    t = tc::TmaConvGeom{g.Ho, g.Wo, g.Cin, g.Cout, g.n * px, R, I, g.stride};
+    t = tc::TmaConvGeom{g.Ho, g.Wo, g.Cin, g.Cout, g.n * px, R, I, g.stride, g.n};
     return true;
 }
 
@@ -125,26 +128,41 @@ cudaError_t launch_conv_tma(const ConvGeom& g, const tc::TmaConvGeom& t, const b
     const auto encode = tensor_map_encoder();
     if (!encode) return cudaSuccess;
     alignas(64) CUtensorMap mx, mw;
+    const bool packed = g.Cin < tc::BK;
     const cuuint64_t xdim[4] = {static_cast<cuuint64_t>(g.Cin), static_cast<cuuint64_t>(g.W),
                                 static_cast<cuuint64_t>(g.H), static_cast<cuuint64_t>(g.n)};
     const cuuint64_t xstr[3] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(g.W) * g.Cin * 2,
                                 static_cast<cuuint64_t>(g.H) * g.W * g.Cin * 2};
-    const cuuint32_t xbox[4] = {static_cast<cuuint32_t>(tc::BK), static_cast<cuuint32_t>(g.stride * g.Wo),
-                                static_cast<cuuint32_t>(g.stride * t.R), static_cast<cuuint32_t>(t.I)};
+    const cuuint32_t xbox[4] = {static_cast<cuuint32_t>(packed ? 8 : tc::BK),
+                                static_cast<cuuint32_t>(g.stride * g.Wo), static_cast<cuuint32_t>(g.stride * t.R),
+                                static_cast<cuuint32_t>(t.I)};
     const cuuint32_t xstep[4] = {1, static_cast<cuuint32_t>(g.stride), static_cast<cuuint32_t>(g.stride), 1};
-    const cuuint64_t wdim[3] = {static_cast<cuuint64_t>(g.Cin), 9, static_cast<cuuint64_t>(g.Cout)};
-    const cuuint64_t wstr[2] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(9) * g.Cin * 2};
-    const cuuint32_t wbox[3] = {static_cast<cuuint32_t>(tc::BK), 1, static_cast<cuuint32_t>(BN)};
     const cuuint32_t ones[4] = {1, 1, 1, 1};
-    if (encode(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), xdim, xstr, xbox, xstep,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
-        encode(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(Wt), wdim, wstr, wbox, ones,
-               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    CUresult rx = encode(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), xdim, xstr, xbox, xstep,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE,
+                         packed ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
+                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    CUresult rw;
+    if (packed) {  // weights as the {9 Cin, Cout} matrix
+        const cuuint64_t wdim[2] = {static_cast<cuuint64_t>(9) * g.Cin, static_cast<cuuint64_t>(g.Cout)};
+        const cuuint64_t wstr[1] = {static_cast<cuuint64_t>(9) * g.Cin * 2};
+        const cuuint32_t wbox[2] = {static_cast<cuuint32_t>(tc::BK), static_cast<cuuint32_t>(BN)};
+        rw = encode(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(Wt), wdim, wstr, wbox, ones,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    } else {       // weights as the {Cin, 9, Cout} tensor
+        const cuuint64_t wdim[3] = {static_cast<cuuint64_t>(g.Cin), 9, static_cast<cuuint64_t>(g.Cout)};
+        const cuuint64_t wstr[2] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(9) * g.Cin * 2};
+        const cuuint32_t wbox[3] = {static_cast<cuuint32_t>(tc::BK), 1, static_cast<cuuint32_t>(BN)};
+        rw = encode(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(Wt), wdim, wstr, wbox, ones,
+                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    }
+    if (rx != CUDA_SUCCESS || rw != CUDA_SUCCESS)
         return cudaSuccess;  // not expressible as tensor maps: the gather path runs instead
     constexpr int smem = tc::conv_tma_smem_bytes<BN, kTmaStages>();
-    auto kern = tc::tc_conv_tma_kernel<BN, kTmaStages, EpiFwd>;
+    auto kern = packed ? tc::tc_conv_tma_kernel<BN, kTmaStages, true, EpiFwd>
+                       : tc::tc_conv_tma_kernel<BN, kTmaStages, false, EpiFwd>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((t.M + tc::BM - 1) / tc::BM, (g.Cout + BN - 1) / BN);

@@ -40,6 +40,13 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
            (static_cast<uint64_t>(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
 }
 
+// ... and of a K-major operand in the no-swizzle layout: 8-row x 16-byte core matrices,
+// lbo bytes between core matrices adjacent in K, sbo bytes between those adjacent in M/N.
+__device__ __forceinline__ uint64_t smem_desc_plain(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+           (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
 __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
     asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
                  "r"(bytes)
@@ -52,6 +59,15 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap* map
         "cp.async.bulk.tensor.4d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, "
         "%5, %6}], [%2];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2), "r"(c3)
+        : "memory");
+}
+
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int c0,
+                                            int c1) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], "
+        "[%2];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1)
         : "memory");
 }
 
@@ -72,9 +88,19 @@ struct TmaConvGeom {
     int M;            // n * Ho * Wo output pixels
     int R, I;         // output rows and images per 128-pixel tile
     int stride;
+    int n;            // images
 };
 
-template <int BN, int S, class Epi>
+// Two operand arrangements.  Wide (Cin >= 64): K chunk = (tap, 64-channel block), one
+// activation box of 64 channels landing in the 128-byte swizzle layout; the weights as a
+// {Cin, 9, Cout} tensor.  Packed (Cin < 64): the K axis is the tap-major sequence of
+// 8-channel columns, eight per chunk; each column is one activation box of 8 channels
+// landing as 128 rows x 16 bytes (the no-swizzle layout: core matrices 128 bytes apart
+// along M, columns 2048 bytes apart along K), so no channels beyond Cin are moved; a
+// column that only pads the chunk's last K = 16 step is a box lying wholly outside the
+// tensor (zeros); the weights as a {9 Cin, Cout} matrix in the 128-byte swizzle layout.
+
+template <int BN, int S, bool PACKED, class Epi>
 __global__ void __launch_bounds__(128)
     tc_conv_tma_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
                        Epi epi, TmaConvGeom g, int* status) {
@@ -92,7 +118,10 @@ __global__ void __launch_bounds__(128)
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
     const int ncb = (g.Cin + BK - 1) / BK;
-    const int n_chunks = 9 * ncb;
+    const int cpt = g.Cin / 8;            // packed: 8-channel columns per tap
+    const int ncols = 9 * cpt;
+    const int n_chunks = PACKED ? (ncols + 7) / 8 : 9 * ncb;
+    constexpr uint32_t COL = BM * 16;     // packed: bytes of one 8-channel column
     const int img0 = m0 / (g.Ho * g.Wo);
     const int y0 = (m0 - img0 * g.Ho * g.Wo) / g.Wo;
     // 1024-byte alignment of every stage (the swizzle atoms) inside the dynamic buffer
@@ -124,12 +153,24 @@ __global__ void __launch_bounds__(128)
         int issued = 0;   // chunks whose loads were issued
         auto issue = [&](int c) {
             const int s = c % S;
-            const int tap = c / ncb, cb = c - tap * ncb;
-            const int dy = tap / 3, dx = tap - 3 * dy;
             const uint32_t sa = s0 + s * STAGE;
-            mbar_expect_tx(&full[s], static_cast<uint32_t>(STAGE));
-            tma_load_4d(sa, &map_x, &full[s], BK * cb, dx - 1, g.stride * y0 + dy - 1, img0);
-            tma_load_3d(sa + A_BYTES, &map_w, &full[s], BK * cb, tap, n0);
+            if constexpr (PACKED) {
+                const int nq = min(8, ncols - 8 * c), nz = nq & 1;
+                mbar_expect_tx(&full[s], static_cast<uint32_t>((nq + nz) * COL + B_BYTES));
+                for (int q = 0; q < nq; ++q) {
+                    const int col = 8 * c + q, tap = col / cpt, ch8 = col - tap * cpt;
+                    const int dy = tap / 3, dx = tap - 3 * dy;
+                    tma_load_4d(sa + q * COL, &map_x, &full[s], 8 * ch8, dx - 1, g.stride * y0 + dy - 1, img0);
+                }
+                if (nz) tma_load_4d(sa + nq * COL, &map_x, &full[s], 0, 0, 0, g.n);  // all outside: zeros
+                tma_load_2d(sa + A_BYTES, &map_w, &full[s], BK * c, n0);
+            } else {
+                const int tap = c / ncb, cb = c - tap * ncb;
+                const int dy = tap / 3, dx = tap - 3 * dy;
+                mbar_expect_tx(&full[s], static_cast<uint32_t>(STAGE));
+                tma_load_4d(sa, &map_x, &full[s], BK * cb, dx - 1, g.stride * y0 + dy - 1, img0);
+                tma_load_3d(sa + A_BYTES, &map_w, &full[s], BK * cb, tap, n0);
+            }
             ++issued;
         };
         for (int c = 0; c < S - 1 && c < n_chunks; ++c) issue(c);
@@ -140,10 +181,17 @@ __global__ void __launch_bounds__(128)
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t sa = s0 + s * STAGE, sb = sa + A_BYTES;
-            const int steps = (min(BK, g.Cin - BK * (i % ncb)) + 15) / 16;
-            for (int j = 0; j < steps; ++j)
-                mma_bf16(tmem, smem_desc_sw128(sa + 32u * j), smem_desc_sw128(sb + 32u * j), idesc,
-                         (i > 0 || j > 0) ? 1u : 0u);
+            if constexpr (PACKED) {
+                const int steps = (min(8, ncols - 8 * i) + 1) / 2;
+                for (int j = 0; j < steps; ++j)
+                    mma_bf16(tmem, smem_desc_plain(sa + 2u * COL * j, COL, 128u), smem_desc_sw128(sb + 32u * j),
+                             idesc, (i > 0 || j > 0) ? 1u : 0u);
+            } else {
+                const int steps = (min(BK, g.Cin - BK * (i % ncb)) + 15) / 16;
+                for (int j = 0; j < steps; ++j)
+                    mma_bf16(tmem, smem_desc_sw128(sa + 32u * j), smem_desc_sw128(sb + 32u * j), idesc,
+                             (i > 0 || j > 0) ? 1u : 0u);
+            }
             mma_commit(&empty[s]);
             ++done;
             const int nxt = i + S - 1;
