@@ -128,41 +128,37 @@ cudaError_t launch_conv_tma(const ConvGeom& g, const tc::TmaConvGeom& t, const b
     const auto encode = tensor_map_encoder();
     if (!encode) return cudaSuccess;
     alignas(64) CUtensorMap mx, mw;
-    const bool packed = g.Cin < tc::BK;
+    // column width: the widest of 64, 32, 16, 8 channels dividing Cin
+    const int cb = g.Cin % 64 == 0 ? 64 : g.Cin % 32 == 0 ? 32 : g.Cin % 16 == 0 ? 16 : 8;
+    const CUtensorMapSwizzle sw = cb == 64   ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : cb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                  : cb == 16 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                             : CU_TENSOR_MAP_SWIZZLE_NONE;
     const cuuint64_t xdim[4] = {static_cast<cuuint64_t>(g.Cin), static_cast<cuuint64_t>(g.W),
                                 static_cast<cuuint64_t>(g.H), static_cast<cuuint64_t>(g.n)};
     const cuuint64_t xstr[3] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(g.W) * g.Cin * 2,
                                 static_cast<cuuint64_t>(g.H) * g.W * g.Cin * 2};
-    const cuuint32_t xbox[4] = {static_cast<cuuint32_t>(packed ? 8 : tc::BK),
-                                static_cast<cuuint32_t>(g.stride * g.Wo), static_cast<cuuint32_t>(g.stride * t.R),
-                                static_cast<cuuint32_t>(t.I)};
+    const cuuint32_t xbox[4] = {static_cast<cuuint32_t>(cb), static_cast<cuuint32_t>(g.stride * g.Wo),
+                                static_cast<cuuint32_t>(g.stride * t.R), static_cast<cuuint32_t>(t.I)};
     const cuuint32_t xstep[4] = {1, static_cast<cuuint32_t>(g.stride), static_cast<cuuint32_t>(g.stride), 1};
-    const cuuint32_t ones[4] = {1, 1, 1, 1};
-    CUresult rx = encode(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), xdim, xstr, xbox, xstep,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE,
-                         packed ? CU_TENSOR_MAP_SWIZZLE_NONE : CU_TENSOR_MAP_SWIZZLE_128B,
-                         CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    CUresult rw;
-    if (packed) {  // weights as the {9 Cin, Cout} matrix
-        const cuuint64_t wdim[2] = {static_cast<cuuint64_t>(9) * g.Cin, static_cast<cuuint64_t>(g.Cout)};
-        const cuuint64_t wstr[1] = {static_cast<cuuint64_t>(9) * g.Cin * 2};
-        const cuuint32_t wbox[2] = {static_cast<cuuint32_t>(tc::BK), static_cast<cuuint32_t>(BN)};
-        rw = encode(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(Wt), wdim, wstr, wbox, ones,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    } else {       // weights as the {Cin, 9, Cout} tensor
-        const cuuint64_t wdim[3] = {static_cast<cuuint64_t>(g.Cin), 9, static_cast<cuuint64_t>(g.Cout)};
-        const cuuint64_t wstr[2] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(9) * g.Cin * 2};
-        const cuuint32_t wbox[3] = {static_cast<cuuint32_t>(tc::BK), 1, static_cast<cuuint32_t>(BN)};
-        rw = encode(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<bf16*>(Wt), wdim, wstr, wbox, ones,
-                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                    CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    }
+    const cuuint32_t ones[2] = {1, 1};
+    const CUresult rx = encode(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), xdim, xstr, xbox,
+                               xstep, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    // weights as the {9 Cin, Cout} matrix (K = tap-major channels)
+    const cuuint64_t wdim[2] = {static_cast<cuuint64_t>(9) * g.Cin, static_cast<cuuint64_t>(g.Cout)};
+    const cuuint64_t wstr[1] = {static_cast<cuuint64_t>(9) * g.Cin * 2};
+    const cuuint32_t wbox[2] = {static_cast<cuuint32_t>(tc::BK), static_cast<cuuint32_t>(BN)};
+    const CUresult rw = encode(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(Wt), wdim, wstr, wbox,
+                               ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (rx != CUDA_SUCCESS || rw != CUDA_SUCCESS)
         return cudaSuccess;  // not expressible as tensor maps: the gather path runs instead
     constexpr int smem = tc::conv_tma_smem_bytes<BN, kTmaStages>();
-    auto kern = packed ? tc::tc_conv_tma_kernel<BN, kTmaStages, true, EpiFwd>
-                       : tc::tc_conv_tma_kernel<BN, kTmaStages, false, EpiFwd>;
+    auto kern = cb == 64   ? tc::tc_conv_tma_kernel<BN, kTmaStages, 64, EpiFwd>
+                : cb == 32 ? tc::tc_conv_tma_kernel<BN, kTmaStages, 32, EpiFwd>
+                : cb == 16 ? tc::tc_conv_tma_kernel<BN, kTmaStages, 16, EpiFwd>
+                           : tc::tc_conv_tma_kernel<BN, kTmaStages, 8, EpiFwd>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((t.M + tc::BM - 1) / tc::BM, (g.Cout + BN - 1) / BN);

@@ -6,19 +6,21 @@
 //
 // A CTA of 128 threads owns 128 output pixels -- whole output rows (R rows of one image,
 // or I whole images when an image has fewer than 128 output pixels) -- by BN output
-// channels.  For K chunk (tap, channel block) one elected thread issues two tiled TMA
-// loads into a stage of shared memory: the activation box {64 channels, s Wo, s R, I}
-// traversed with element stride s along the image axes and displaced by the tap
-// (coordinates -1 and beyond the image are filled with zeros: the convolution's padding,
-// no bounds arithmetic in the kernel), which lands as the 128 x 64 A tile, and the
-// weight box {64 channels, 1 tap, BN}.  Both land in the 128-byte-swizzled K-major
-// layout the tensor core reads (128-byte rows, 8-row atoms 1024 bytes apart), signalled
-// by the stage's "full" mbarrier with the byte count; the same thread waits for it,
-// issues the chunk's K = 16 MMAs into the TMEM accumulator and commits them to the
-// stage's "empty" mbarrier, which gates the stage's next TMA load S - 1 chunks later.
-// The epilogue reads TMEM with tcgen05.ld.  Every wait is bounded: on expiry the kernel
-// records an error, waits (bounded) for its outstanding copies, skips the epilogue and
-// releases TMEM.
+// channels.  The K axis is the tap-major sequence of CB-channel columns (CB = 64, 32, 16
+// or 8, the widest that divides Cin), 64 / CB columns per chunk of K = 64.  For each
+// chunk one elected thread issues tiled TMA loads into a stage of shared memory: per
+// column the activation box {CB channels, s Wo, s R, I}, traversed with element stride s
+// along the image axes and displaced by the column's tap (coordinates -1 and beyond the
+// image are filled with zeros: the convolution's padding, no bounds arithmetic in the
+// kernel), landing as 128 rows of 2 CB bytes in the K-major layout the tensor core reads
+// (swizzled over 2 CB bytes, none for CB = 8); and the weight box {64 of the 9 Cin K
+// elements, BN} in the 128-byte swizzle layout.  Completion is signalled by the stage's
+// "full" mbarrier with the byte count; the same thread waits for it, issues the chunk's
+// K = 16 MMAs into the TMEM accumulator and commits them to the stage's "empty" mbarrier,
+// which gates the stage's next TMA loads S - 1 chunks later.  No channel beyond Cin is
+// moved.  The epilogue reads TMEM with tcgen05.ld.  Every wait is bounded: on expiry the
+// kernel records an error, waits (bounded) for its outstanding MMAs and copies, skips the
+// epilogue and releases TMEM.
 #pragma once
 
 #include <cstdint>
@@ -30,15 +32,19 @@
 namespace fb {
 namespace tc {
 
-// Shared-memory matrix descriptor of a K-major operand in the 128-byte swizzle layout:
-// start >> 4, stride between 8-row atoms (1024 bytes) >> 4 at bit 32, descriptor version
-// 1 at bit 46, layout type 2 (128-byte swizzle) at bit 61; the leading offset is unused
-// for this layout and set to 1.  Stepping K by 16 elements advances the start by 32
-// bytes inside the swizzle atom.
-__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) {
+// Shared-memory matrix descriptor of a K-major operand whose rows of RB = 32, 64 or 128
+// bytes are swizzled over RB: start >> 4, stride between 8-row atoms (8 RB bytes) >> 4 at
+// bit 32, descriptor version 1 at bit 46, layout type at bit 61 (6: 32-byte, 4: 64-byte,
+// 2: 128-byte swizzle); the leading offset is unused for these layouts and set to 1.
+// Stepping K by 16 elements inside a row advances the start by 32 bytes.
+template <int RB>
+__device__ __forceinline__ uint64_t smem_desc_sw(uint32_t saddr) {
+    static_assert(RB == 32 || RB == 64 || RB == 128, "swizzle width");
+    constexpr uint64_t layout = RB == 128 ? 2 : RB == 64 ? 4 : 6;
     return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (1ull << 16) |
-           (static_cast<uint64_t>(1024 >> 4) << 32) | (1ull << 46) | (2ull << 61);
+           (static_cast<uint64_t>((8 * RB) >> 4) << 32) | (1ull << 46) | (layout << 61);
 }
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t saddr) { return smem_desc_sw<128>(saddr); }
 
 // ... and of a K-major operand in the no-swizzle layout: 8-row x 16-byte core matrices,
 // lbo bytes between core matrices adjacent in K, sbo bytes between those adjacent in M/N.
@@ -71,15 +77,6 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
         : "memory");
 }
 
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, uint64_t* bar, int c0,
-                                            int c1, int c2) {
-    asm volatile(
-        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4, "
-        "%5}], [%2];" ::"r"(dst),
-        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(c0), "r"(c1), "r"(c2)
-        : "memory");
-}
-
 // Geometry of the TMA convolution: output Ho x Wo; a tile is R output rows of one image
 // (I = 1) or I whole images (R = Ho).
 struct TmaConvGeom {
@@ -91,21 +88,13 @@ struct TmaConvGeom {
     int n;            // images
 };
 
-// Two operand arrangements.  Wide (Cin >= 64): K chunk = (tap, 64-channel block), one
-// activation box of 64 channels landing in the 128-byte swizzle layout; the weights as a
-// {Cin, 9, Cout} tensor.  Packed (Cin < 64): the K axis is the tap-major sequence of
-// 8-channel columns, eight per chunk; each column is one activation box of 8 channels
-// landing as 128 rows x 16 bytes (the no-swizzle layout: core matrices 128 bytes apart
-// along M, columns 2048 bytes apart along K), so no channels beyond Cin are moved; a
-// column that only pads the chunk's last K = 16 step is a box lying wholly outside the
-// tensor (zeros); the weights as a {9 Cin, Cout} matrix in the 128-byte swizzle layout.
-
-template <int BN, int S, bool PACKED, class Epi>
+template <int BN, int S, int CB, class Epi>
 __global__ void __launch_bounds__(128)
     tc_conv_tma_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
                        Epi epi, TmaConvGeom g, int* status) {
     static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tile N");
     static_assert(S >= 2 && S <= 8, "stages");
+    static_assert(CB == 8 || CB == 16 || CB == 32 || CB == 64, "column width");
     constexpr int A_BYTES = BM * BK * 2;   // 16 KB: 128 rows of 128 bytes
     constexpr int B_BYTES = BN * BK * 2;   // BN rows of 128 bytes (multiple of 1 KB for BN % 8 == 0)
     constexpr int STAGE = A_BYTES + B_BYTES;
@@ -117,11 +106,12 @@ __global__ void __launch_bounds__(128)
 
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
-    const int ncb = (g.Cin + BK - 1) / BK;
-    const int cpt = g.Cin / 8;            // packed: 8-channel columns per tap
-    const int ncols = 9 * cpt;
-    const int n_chunks = PACKED ? (ncols + 7) / 8 : 9 * ncb;
-    constexpr uint32_t COL = BM * 16;     // packed: bytes of one 8-channel column
+    constexpr int RB = 2 * CB;            // bytes of one row of a column
+    constexpr uint32_t COL = BM * RB;     // bytes of one column (128 rows)
+    constexpr int PER = BK / CB;          // columns per chunk
+    const int cpt = g.Cin / CB;           // columns per tap (Cin % CB == 0)
+    const int ktot = 9 * g.Cin;
+    const int n_chunks = (ktot + BK - 1) / BK;
     const int img0 = m0 / (g.Ho * g.Wo);
     const int y0 = (m0 - img0 * g.Ho * g.Wo) / g.Wo;
     // 1024-byte alignment of every stage (the swizzle atoms) inside the dynamic buffer
@@ -154,23 +144,16 @@ __global__ void __launch_bounds__(128)
         auto issue = [&](int c) {
             const int s = c % S;
             const uint32_t sa = s0 + s * STAGE;
-            if constexpr (PACKED) {
-                const int nq = min(8, ncols - 8 * c), nz = nq & 1;
-                mbar_expect_tx(&full[s], static_cast<uint32_t>((nq + nz) * COL + B_BYTES));
-                for (int q = 0; q < nq; ++q) {
-                    const int col = 8 * c + q, tap = col / cpt, ch8 = col - tap * cpt;
-                    const int dy = tap / 3, dx = tap - 3 * dy;
-                    tma_load_4d(sa + q * COL, &map_x, &full[s], 8 * ch8, dx - 1, g.stride * y0 + dy - 1, img0);
-                }
-                if (nz) tma_load_4d(sa + nq * COL, &map_x, &full[s], 0, 0, 0, g.n);  // all outside: zeros
-                tma_load_2d(sa + A_BYTES, &map_w, &full[s], BK * c, n0);
-            } else {
-                const int tap = c / ncb, cb = c - tap * ncb;
+            const int nq = min(BK, ktot - BK * c) / CB;   // columns of this chunk
+            const int nz = CB == 8 ? (nq & 1) : 0;        // zero column completing a K = 16 step
+            mbar_expect_tx(&full[s], static_cast<uint32_t>((nq + nz) * COL + B_BYTES));
+            for (int q = 0; q < nq; ++q) {
+                const int col = PER * c + q, tap = col / cpt, blk = col - tap * cpt;
                 const int dy = tap / 3, dx = tap - 3 * dy;
-                mbar_expect_tx(&full[s], static_cast<uint32_t>(STAGE));
-                tma_load_4d(sa, &map_x, &full[s], BK * cb, dx - 1, g.stride * y0 + dy - 1, img0);
-                tma_load_3d(sa + A_BYTES, &map_w, &full[s], BK * cb, tap, n0);
+                tma_load_4d(sa + q * COL, &map_x, &full[s], CB * blk, dx - 1, g.stride * y0 + dy - 1, img0);
             }
+            if (nz) tma_load_4d(sa + nq * COL, &map_x, &full[s], 0, 0, 0, g.n);  // wholly outside: zeros
+            tma_load_2d(sa + A_BYTES, &map_w, &full[s], BK * c, n0);
             ++issued;
         };
         for (int c = 0; c < S - 1 && c < n_chunks; ++c) issue(c);
@@ -181,16 +164,14 @@ __global__ void __launch_bounds__(128)
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t sa = s0 + s * STAGE, sb = sa + A_BYTES;
-            if constexpr (PACKED) {
-                const int steps = (min(8, ncols - 8 * i) + 1) / 2;
-                for (int j = 0; j < steps; ++j)
-                    mma_bf16(tmem, smem_desc_plain(sa + 2u * COL * j, COL, 128u), smem_desc_sw128(sb + 32u * j),
-                             idesc, (i > 0 || j > 0) ? 1u : 0u);
-            } else {
-                const int steps = (min(BK, g.Cin - BK * (i % ncb)) + 15) / 16;
-                for (int j = 0; j < steps; ++j)
-                    mma_bf16(tmem, smem_desc_sw128(sa + 32u * j), smem_desc_sw128(sb + 32u * j), idesc,
-                             (i > 0 || j > 0) ? 1u : 0u);
+            const int steps = (min(BK, ktot - BK * i) + 15) / 16;
+            for (int j = 0; j < steps; ++j) {
+                uint64_t da;
+                if constexpr (CB == 8)   // two 16-byte columns per step, 128-byte core-matrix groups
+                    da = smem_desc_plain(sa + 2u * COL * j, COL, 128u);
+                else                     // the step's 32 bytes inside one swizzled row
+                    da = smem_desc_sw<RB>(sa + (16u * j / CB) * COL + (32u * j) % RB);
+                mma_bf16(tmem, da, smem_desc_sw128(sb + 32u * j), idesc, (i > 0 || j > 0) ? 1u : 0u);
             }
             mma_commit(&empty[s]);
             ++done;

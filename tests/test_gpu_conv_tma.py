@@ -42,6 +42,7 @@ TMA_CASES = [  # n, H, W, Cin, Cout, stride: the initialiser's layers at 512x512
     (2, 64, 64, 96, 32, 1), (2, 64, 64, 32, 8, 1), (1, 4, 32, 40, 24, 1), (5, 4, 4, 16, 16, 1),
     (2, 64, 64, 32, 64, 2), (2, 32, 32, 64, 96, 2), (3, 16, 16, 96, 128, 2), (1, 16, 15, 32, 32, 2),
     (3, 8, 8, 64, 32, 2), (2, 32, 32, 16, 32, 1), (2, 16, 16, 56, 64, 2), (1, 8, 16, 48, 16, 1),
+    (2, 16, 16, 24, 32, 1), (2, 8, 8, 192, 64, 1),
 ]
 
 
@@ -51,10 +52,10 @@ def test_tma_conv_is_bit_identical_to_the_gather_path(fbp, n, H, W, Cin, Cout, s
     x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
     w = ref.bf16(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin))
     b = rng.normal(size=Cout).astype(np.float32).astype(np.float64)
-    # The packed arrangement (Cin < 64) pairs 8-channel columns into K = 16 steps; with an
-    # odd number of columns per tap a step spans two taps, where the gather path pads
-    # each tap to 16 channels: same products, other grouping, so equal only to rounding.
-    same_steps = Cin >= 64 or (Cin // 8) % 2 == 0
+    # Columns of 16 or more channels give the gather path's K = 16 steps (16 channels of
+    # one tap); 8-channel columns (Cin an odd multiple of 8) pair two taps in a step,
+    # where the gather path pads each tap to 16: same products, other grouping.
+    same_steps = Cin % 16 == 0
     for relu, out_f32 in ((False, True), (True, False)):
         yg, used_g = run(fbp, x, w, b, stride, relu, out_f32, mode=1)
         yt, used_t = run(fbp, x, w, b, stride, relu, out_f32, mode=0)
