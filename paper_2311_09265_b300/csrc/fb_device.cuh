@@ -62,6 +62,12 @@ __device__ __forceinline__ void load_slot(const uint32_t* __restrict__ p, uint32
                  : "l"(p));
 }
 
+__device__ __forceinline__ void load_half_slot(const uint32_t* __restrict__ p, uint32_t (&w)[4]) {
+    asm volatile("ld.global.nc.v4.b32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(w[0]), "=r"(w[1]), "=r"(w[2]), "=r"(w[3])
+                 : "l"(p));
+}
+
 // Frame f of a guide stack laid out by prep_guides.
 template <int K>
 __device__ __forceinline__ const uint32_t* frame_rows(const uint32_t* rp, int f, int H, int W) {
@@ -155,33 +161,59 @@ __device__ __forceinline__ bool patch_error_below(const uint32_t* __restrict__ r
     uint32_t acc = 0;
     if constexpr (G::PAIRED) {
         // Source rows ur-2 .. ur+2 sit in slots q = ur/2 + L (L = 0, 1, 2), whose halves
-        // are patch rows a = 2L - odd and 2L - odd + 1 (a outside 0..4 is not part of
-        // the patch and contributes zero).  The middle slot, always two patch rows, is
-        // tested first.
+        // are patch rows a = 2L - odd and 2L - odd + 1 (a outside 0..4 is not part of the
+        // patch).  The two slots holding two patch rows are read first -- L = 1, then
+        // L = 0 for even ur or L = 2 for odd ur -- and the slot holding one row last, as a
+        // 16-byte half: the early exit then has four of the five rows after two loads for
+        // either parity.  Addresses and target rows differ by parity through selects, not
+        // branches, so a warp's lanes stay converged.
         const int odd = ur & 1;
         const size_t stride = static_cast<size_t>(W) * 8;
         const uint32_t* base = rps + (static_cast<size_t>(ur >> 1) * W + uc) * 8;
-#pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const int L = i == 0 ? 1 : (i == 1 ? 0 : 2);
+        {   // L = 1: rows a = 2, 3 (even) or 1, 2 (odd)
             uint32_t s[8];
-            load_slot(base + L * stride, s);
+            load_slot(base + stride, s);
             uint32_t dot = 0, ss = 0, te = 0;
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int a_ev = 2 * L + half;      // patch row of this half for even ur
-                const int a_od = 2 * L + half - 1;  // ... for odd ur
-                const bool v_ev = a_ev <= 4, v_od = a_od >= 0;
-                const bool valid = odd ? v_od : v_ev;
-                const int ae = v_ev ? a_ev : 0, ao = v_od ? a_od : 0;
+            for (int half = 0; half < 2; ++half)
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                    const uint32_t tw = valid ? (odd ? t.w[ao][w] : t.w[ae][w]) : 0u;
-                    const uint32_t sw = valid ? s[4 * half + w] : 0u;
+                    const uint32_t tw = odd ? t.w[1 + half][w] : t.w[2 + half][w];
+                    const uint32_t sw = s[4 * half + w];
                     dot = __dp4a(sw, tw, dot);
                     ss = __dp4a(sw, sw, ss);
                     te = __dp4a(tw, tw, te);  // |t|^2 recomputed: five fewer live registers
                 }
+            acc += ss + te - 2u * dot;
+            if (acc >= bound) return false;
+        }
+        {   // L = 0 (even: rows 0, 1) or L = 2 (odd: rows 3, 4)
+            uint32_t s[8];
+            load_slot(base + (odd ? 2 * stride : 0), s);
+            uint32_t dot = 0, ss = 0, te = 0;
+#pragma unroll
+            for (int half = 0; half < 2; ++half)
+#pragma unroll
+                for (int w = 0; w < 4; ++w) {
+                    const uint32_t tw = odd ? t.w[3 + half][w] : t.w[half][w];
+                    const uint32_t sw = s[4 * half + w];
+                    dot = __dp4a(sw, tw, dot);
+                    ss = __dp4a(sw, sw, ss);
+                    te = __dp4a(tw, tw, te);
+                }
+            acc += ss + te - 2u * dot;
+            if (acc >= bound) return false;
+        }
+        {   // the remaining row: L = 2 first half (even: row 4) or L = 0 second half (odd: row 0)
+            uint32_t s[4];
+            load_half_slot(base + (odd ? 4 : 2 * stride), s);
+            uint32_t dot = 0, ss = 0, te = 0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t tw = odd ? t.w[0][w] : t.w[4][w];
+                dot = __dp4a(s[w], tw, dot);
+                ss = __dp4a(s[w], s[w], ss);
+                te = __dp4a(tw, tw, te);
             }
             acc += ss + te - 2u * dot;
             if (acc >= bound) return false;
