@@ -255,28 +255,28 @@ __device__ __forceinline__ bool balanced_error_below(const uint32_t* __restrict_
     using G = Geo<K>;
     uint32_t acc = 0;
     if constexpr (G::PAIRED) {
+        // Slot order and row selection as patch_error_below: the two two-row slots first
+        // (L = 1, then L = 0 for even ur or L = 2 for odd ur), the one-row slot last as
+        // 16-byte halves; the guide and style loads of a slot are issued together.
         const int odd = ur & 1;
         const size_t stride = static_cast<size_t>(W) * 8;
         const size_t off = (static_cast<size_t>(ur >> 1) * W + uc) * 8;
 #pragma unroll
-        for (int i = 0; i < 3; ++i) {
-            const int L = i == 0 ? 1 : (i == 1 ? 0 : 2);
+        for (int i = 0; i < 2; ++i) {
+            const size_t so = off + (i == 0 ? stride : (odd ? 2 * stride : 0));
             uint32_t sg[8], sst[8];
-            load_slot(rpg + off + L * stride, sg);
-            load_slot(rpss + off + L * stride, sst);
+            load_slot(rpg + so, sg);
+            load_slot(rpss + so, sst);
             uint32_t gd = 0, gs = 0, gt = 0, sd = 0, ss = 0, st = 0;
 #pragma unroll
-            for (int half = 0; half < 2; ++half) {
-                const int a_ev = 2 * L + half, a_od = 2 * L + half - 1;
-                const bool v_ev = a_ev <= 4, v_od = a_od >= 0;
-                const bool valid = odd ? v_od : v_ev;
-                const int ae = v_ev ? a_ev : 0, ao = v_od ? a_od : 0;
+            for (int half = 0; half < 2; ++half)
 #pragma unroll
                 for (int w = 0; w < 4; ++w) {
-                    const uint32_t tgw = valid ? (odd ? tg.w[ao][w] : tg.w[ae][w]) : 0u;
-                    const uint32_t tsw = valid ? (odd ? ts.w[ao][w] : ts.w[ae][w]) : 0u;
-                    const uint32_t a = valid ? sg[4 * half + w] : 0u;
-                    const uint32_t b = valid ? sst[4 * half + w] : 0u;
+                    // i = 0: rows 2, 3 (even) / 1, 2 (odd); i = 1: rows 0, 1 / 3, 4
+                    const int ae = i == 0 ? 2 + half : half, ao = i == 0 ? 1 + half : 3 + half;
+                    const uint32_t tgw = odd ? tg.w[ao][w] : tg.w[ae][w];
+                    const uint32_t tsw = odd ? ts.w[ao][w] : ts.w[ae][w];
+                    const uint32_t a = sg[4 * half + w], b = sst[4 * half + w];
                     gd = __dp4a(a, tgw, gd);
                     gs = __dp4a(a, a, gs);
                     gt = __dp4a(tgw, tgw, gt);
@@ -284,6 +284,25 @@ __device__ __forceinline__ bool balanced_error_below(const uint32_t* __restrict_
                     ss = __dp4a(b, b, ss);
                     st = __dp4a(tsw, tsw, st);
                 }
+            acc += alpha * (gs + gt - 2u * gd) + (ss + st - 2u * sd);
+            if (acc >= bound) return false;
+        }
+        {   // the remaining row: L = 2 first half (even: row 4) or L = 0 second half (odd: row 0)
+            const size_t so = off + (odd ? 4 : 2 * stride);
+            uint32_t sg[4], sst[4];
+            load_half_slot(rpg + so, sg);
+            load_half_slot(rpss + so, sst);
+            uint32_t gd = 0, gs = 0, gt = 0, sd = 0, ss = 0, st = 0;
+#pragma unroll
+            for (int w = 0; w < 4; ++w) {
+                const uint32_t tgw = odd ? tg.w[0][w] : tg.w[4][w];
+                const uint32_t tsw = odd ? ts.w[0][w] : ts.w[4][w];
+                gd = __dp4a(sg[w], tgw, gd);
+                gs = __dp4a(sg[w], sg[w], gs);
+                gt = __dp4a(tgw, tgw, gt);
+                sd = __dp4a(sst[w], tsw, sd);
+                ss = __dp4a(sst[w], sst[w], ss);
+                st = __dp4a(tsw, tsw, st);
             }
             acc += alpha * (gs + gt - 2u * gd) + (ss + st - 2u * sd);
             if (acc >= bound) return false;
