@@ -22,6 +22,10 @@ struct fb_ctx {
     size_t pinned_cap = 0;
     cudaEvent_t upload_done = nullptr;
     bool upload_pending = false;
+    // Host-buffer calls: a copy stream that moves the styles in and the blended frames out
+    // while the main stream computes, and the events that order the two.
+    cudaStream_t copy_stream = nullptr;
+    std::vector<cudaEvent_t> xfer_ev;
     uint64_t launches = 0;
     int* dev_status = nullptr;      // device-side error word written by bounded waits
     std::string err;
@@ -521,6 +525,18 @@ void interp_pairs(int N, int k, const int32_t* key_idx, int n_keys, uint32_t fla
     if (flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
 }
 
+// The copy stream and at least n ordering events (created on first use).
+int ensure_xfer(fb_ctx* ctx, size_t n) {
+    if (!ctx->copy_stream)
+        FB_CUDA(ctx, cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    while (ctx->xfer_ev.size() < n) {
+        cudaEvent_t e = nullptr;
+        FB_CUDA(ctx, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        ctx->xfer_ev.push_back(e);
+    }
+    return FB_OK;
+}
+
 // Group consecutive output jobs into chunks whose pairs fit the F/E budget.
 struct Chunk {
     int job0, n_jobs, pair0, n_pairs;
@@ -613,17 +629,48 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
     const uint8_t* g_dev = guides;
     const uint8_t* s_dev = styles;
     float* o_dev = out;
+    // Host buffers: the guides come in on the main stream (the search needs them first);
+    // the styles on the copy stream, after the main stream's earlier work on the arena,
+    // while the guides are prepared and (plain search) the NNFs computed; the blended
+    // frames go out on the copy stream in groups, each as soon as its combine is done.
+    constexpr int kOutGroups = 4;
+    const bool styles_late = staging && !balanced && !align;  // only the combine reads them
+    bool frames_in_order = true;  // output frame of job j is j: a group's frames are contiguous
+    for (size_t j = 0; j < jobs.size(); ++j) frames_in_order = frames_in_order && jobs[j].out_frame == static_cast<int>(j);
+    size_t ev = 0;  // next ordering event
+    if (ctx->copy_stream) {  // a failed earlier call may have left copies of the arena in flight
+        rc = ensure_xfer(ctx, 1);
+        if (rc) return rc;
+        FB_CUDA(ctx, cudaEventRecord(ctx->xfer_ev[0], ctx->copy_stream));
+        FB_CUDA(ctx, cudaStreamWaitEvent(st, ctx->xfer_ev[0], 0));
+    }
     if (staging) {
+        rc = ensure_xfer(ctx, 2 + kOutGroups * chunks.size() + 1);
+        if (rc) return rc;
         FB_CUDA(ctx, cudaMemcpyAsync(b.in_guides, guides, guide_bytes, cudaMemcpyHostToDevice, st));
-        FB_CUDA(ctx, cudaMemcpyAsync(b.in_styles, styles, style_bytes, cudaMemcpyHostToDevice, st));
+        FB_CUDA(ctx, cudaEventRecord(ctx->xfer_ev[ev], st));
+        FB_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->xfer_ev[ev++], 0));
+        FB_CUDA(ctx, cudaMemcpyAsync(b.in_styles, styles, style_bytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+        FB_CUDA(ctx, cudaEventRecord(ctx->xfer_ev[ev], ctx->copy_stream));
         g_dev = b.in_guides;
         s_dev = b.in_styles;
         o_dev = b.in_out;
     }
+    const size_t styles_in = ev++;
+    auto convert_styles = [&]() -> int {
+        if (staging) FB_CUDA(ctx, cudaStreamWaitEvent(st, ctx->xfer_ev[styles_in], 0));
+        FB_LAUNCH(ctx, st, FB_K_STYLE,
+                  fb::launch_style_rgbx(s_dev, static_cast<size_t>(n_styles) * npx0, b.styles, st));
+        return FB_OK;
+    };
 
     rc = prep_guides(ctx, b, L, k, g_dev, N, 0, st);
     if (rc) return rc;
-    FB_LAUNCH(ctx, st, FB_K_STYLE, fb::launch_style_rgbx(s_dev, static_cast<size_t>(n_styles) * npx0, b.styles, st));
+    if (!styles_late) {
+        rc = convert_styles();
+        if (rc) return rc;
+    }
+    bool styles_ready = !styles_late;
     if (balanced || align)
         FB_LAUNCH(ctx, st, FB_K_PREP, fb::launch_prep_guides(k, s_dev, n_styles, H, W, b.srec, st));
 
@@ -669,13 +716,36 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
                 ctx->energy_count += static_cast<uint64_t>(c.n_pairs) * npx0;
             }
         }
-        FB_LAUNCH(ctx, st, FB_K_COMBINE, fb::launch_combine(k, b.jobs, c.job0, c.n_jobs, b.pairs, c.pair0, F,
-                                          b.styles, H, W, o_dev, st));
+        if (!styles_ready) {
+            rc = convert_styles();
+            if (rc) return rc;
+            styles_ready = true;
+        }
+        if (!staging || !frames_in_order) {
+            FB_LAUNCH(ctx, st, FB_K_COMBINE, fb::launch_combine(k, b.jobs, c.job0, c.n_jobs, b.pairs, c.pair0, F,
+                                                               b.styles, H, W, o_dev, st));
+            continue;
+        }
+        // Output frames = job indices; each group's frames leave while the next combines.
+        const int per = (c.n_jobs + kOutGroups - 1) / kOutGroups;
+        for (int j0 = c.job0; j0 < c.job0 + c.n_jobs; j0 += per) {
+            const int nj = std::min(per, c.job0 + c.n_jobs - j0);
+            FB_LAUNCH(ctx, st, FB_K_COMBINE, fb::launch_combine(k, b.jobs, j0, nj, b.pairs, c.pair0, F, b.styles, H,
+                                                               W, o_dev, st));
+            FB_CUDA(ctx, cudaEventRecord(ctx->xfer_ev[ev], st));
+            FB_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->xfer_ev[ev++], 0));
+            const size_t f0 = static_cast<size_t>(jobs[j0].out_frame) * npx0 * 3;
+            FB_CUDA(ctx, cudaMemcpyAsync(out + f0, o_dev + f0, static_cast<size_t>(nj) * npx0 * 3 * sizeof(float),
+                                         cudaMemcpyDeviceToHost, ctx->copy_stream));
+        }
     }
 
     if (staging) {
-        FB_CUDA(ctx, cudaMemcpyAsync(out, o_dev, out_floats * sizeof(float), cudaMemcpyDeviceToHost,
-                                     st));
+        if (!styles_ready) FB_CUDA(ctx, cudaStreamWaitEvent(st, ctx->xfer_ev[styles_in], 0));
+        if (!frames_in_order)
+            FB_CUDA(ctx, cudaMemcpyAsync(out, o_dev, out_floats * sizeof(float), cudaMemcpyDeviceToHost, st));
+        FB_CUDA(ctx, cudaEventRecord(ctx->xfer_ev[ev], ctx->copy_stream));
+        FB_CUDA(ctx, cudaStreamWaitEvent(st, ctx->xfer_ev[ev++], 0));
         FB_CUDA(ctx, cudaStreamSynchronize(st));
     }
     return FB_OK;
@@ -1425,6 +1495,8 @@ int fb_ctx_destroy(fb_ctx* ctx) {
     if (ctx->dev_status) cudaFree(ctx->dev_status);
     if (ctx->energy) cudaFree(ctx->energy);
     for (cudaEvent_t e : ctx->ev_pool) cudaEventDestroy(e);
+    for (cudaEvent_t e : ctx->xfer_ev) cudaEventDestroy(e);
+    if (ctx->copy_stream) cudaStreamDestroy(ctx->copy_stream);
     for (fb_ctx::BatchEntry* be : ctx->batch_cache) {
         if (be->exec) cudaGraphExecDestroy(be->exec);
         if (be->dev) cudaFree(be->dev);

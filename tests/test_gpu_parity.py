@@ -147,6 +147,32 @@ def test_blend_window_host_buffers_equal_device_buffers(fbp, ctx):
                                 p).numpy() == dev).all()
 
 
+def test_host_buffers_in_chunks_and_modes_equal_device_buffers(fbp, ctx):
+    """Host buffers move through a copy stream (styles in while the search runs, frames out
+    in groups as their combine finishes): the results equal the device-buffer call for
+    several chunks, for interpolation and for a mode that reads the styles early."""
+    import torch
+    g, s = synth.small_clip(8, 96, 96, seed=21)
+    gh, sh = torch.from_numpy(g).pin_memory(), torch.from_numpy(s).pin_memory()
+    p = fbp.Params.make(5, 2, 1, 0, 13)
+    ctx.set_pair_budget(1 << 20)   # one to two output frames of 96x96 pairs per chunk
+    try:
+        dev = host(fbp.fb_blend_window(ctx, cuda(g), cuda(s), 7, p))
+        hst = fbp.fb_blend_window(ctx, gh, sh, 7, p).numpy()
+    finally:
+        ctx.set_pair_budget(0)
+    assert (dev == hst).all()
+    assert (dev == oracle.blend_window(g, s, 7, 5, 2, seed=13)).all()
+    ks = np.ascontiguousarray(s[[0, 7]])
+    a = host(fbp.fb_interpolate(ctx, cuda(g), [0, 7], cuda(ks), p))
+    b = fbp.fb_interpolate(ctx, gh, [0, 7], torch.from_numpy(ks).pin_memory(), p).numpy()
+    assert (a == b).all()
+    pb = fbp.Params.make(5, 2, 1, 0, 13, flags=fbp.FB_FLAG_BALANCED, alpha=10)
+    a = host(fbp.fb_blend_window(ctx, cuda(g), cuda(s), 5, pb))
+    b = fbp.fb_blend_window(ctx, gh, sh, 5, pb).numpy()
+    assert (a == b).all()
+
+
 def test_blend_window_is_deterministic_and_counts_launches(fbp, ctx):
     g, s = synth.small_clip(5, 32, 32, seed=2)
     p = fbp.Params.make(5, 3, 1, 0, 3)
