@@ -393,6 +393,11 @@ int fb_initnet_get_params(fb_initnet *net, float *host_out);
 int fb_initnet_set_params(fb_initnet *net, const float *host_in);
 /* Gradient of the last train step, same layout, to a HOST array. */
 int fb_initnet_get_grads(fb_initnet *net, float *host_out);
+/* Adam state, for checkpoint / resume: the first and second moment estimates (HOST arrays
+ * of fb_initnet_param_count floats, parameter layout) and the number of updates taken.
+ * Set after fb_initnet_set_params, which resets them.  FB_ERR_ARG for NULL arrays. */
+int fb_initnet_get_optimizer(fb_initnet *net, float *m_out, float *v_out, uint64_t *step_out);
+int fb_initnet_set_optimizer(fb_initnet *net, const float *m_in, const float *v_in, uint64_t step);
 
 /* Forward pass for n pairs: src, tgt are n x H x W x 3 uint8 stacks (pair p = source
  * frame src[p] -> target frame tgt[p]).  head_out (nullable): n x Hq x Wq x 8 float,

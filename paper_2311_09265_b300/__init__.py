@@ -30,6 +30,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_initnet_create", "fb_initnet_destroy", "fb_initnet_last_error",
                     "fb_initnet_param_count", "fb_initnet_get_params", "fb_initnet_set_params",
                     "fb_initnet_get_grads", "fb_initnet_forward", "fb_initnet_init_nnf", "fb_conv_gemm_path",
+                    "fb_initnet_get_optimizer", "fb_initnet_set_optimizer",
                     "fb_initnet_train_step", "fb_initnet_status", "fb_conv3x3_forward",
                     "fb_conv3x3_backward", "fb_ctx_set_initnet", "fb_ctx_energy",
                     "fb_initnet_targets")
@@ -160,6 +161,8 @@ def lib() -> ctypes.CDLL:
         L.fb_initnet_param_count.restype = ctypes.c_size_t
         for f in ("fb_initnet_get_params", "fb_initnet_set_params", "fb_initnet_get_grads"):
             getattr(L, f).argtypes = [_vp, _vp]
+        L.fb_initnet_get_optimizer.argtypes = [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_uint64)]
+        L.fb_initnet_set_optimizer.argtypes = [_vp, _vp, _vp, ctypes.c_uint64]
         L.fb_initnet_forward.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp]
         L.fb_initnet_init_nnf.argtypes = [_vp, ctypes.c_int, _vp, _vp]
         L.fb_initnet_train_step.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_float,
@@ -174,6 +177,7 @@ def lib() -> ctypes.CDLL:
         for f in ("fb_initnet_create", "fb_initnet_destroy", "fb_initnet_get_params",
                   "fb_initnet_set_params", "fb_initnet_get_grads", "fb_initnet_forward",
                   "fb_initnet_init_nnf", "fb_initnet_train_step", "fb_initnet_status",
+                  "fb_initnet_get_optimizer", "fb_initnet_set_optimizer",
                   "fb_conv3x3_forward", "fb_conv3x3_backward"):
             getattr(L, f).restype = ctypes.c_int
         L.fb_ctx_set_initnet.argtypes = [_vp, _vp]
@@ -568,6 +572,23 @@ class InitNet:
         out = np.zeros(self.n_params, np.float32)
         self._check(lib().fb_initnet_get_grads(self._h, out.ctypes.data))
         return out
+
+    def get_optimizer(self):
+        """(first moments, second moments, updates taken) of the Adam state."""
+        import numpy as np
+        m = np.zeros(self.n_params, np.float32)
+        v = np.zeros(self.n_params, np.float32)
+        step = ctypes.c_uint64()
+        self._check(lib().fb_initnet_get_optimizer(self._h, m.ctypes.data, v.ctypes.data, ctypes.byref(step)))
+        return m, v, int(step.value)
+
+    def set_optimizer(self, m, v, step: int) -> None:
+        import numpy as np
+        m = np.ascontiguousarray(m, np.float32)
+        v = np.ascontiguousarray(v, np.float32)
+        if m.size != self.n_params or v.size != self.n_params:
+            raise ValueError("optimizer state must have n_params entries")
+        self._check(lib().fb_initnet_set_optimizer(self._h, m.ctypes.data, v.ctypes.data, int(step)))
 
     def forward(self, src: torch.Tensor, tgt: torch.Tensor, stream=None) -> torch.Tensor:
         n = int(src.shape[0])

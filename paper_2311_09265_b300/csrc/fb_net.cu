@@ -736,6 +736,22 @@ int fb_initnet_set_params(fb_initnet* net, const float* host_in) {
     return refresh_bf16(net, nullptr);
 }
 
+int fb_initnet_get_optimizer(fb_initnet* net, float* m_out, float* v_out, uint64_t* step_out) {
+    if (!net || !m_out || !v_out || !step_out) return FB_ERR_ARG;
+    NET_CUDA(net, cudaMemcpy(m_out, net->adam_m, net->n_params * 4, cudaMemcpyDeviceToHost));
+    NET_CUDA(net, cudaMemcpy(v_out, net->adam_v, net->n_params * 4, cudaMemcpyDeviceToHost));
+    *step_out = net->step;
+    return FB_OK;
+}
+
+int fb_initnet_set_optimizer(fb_initnet* net, const float* m_in, const float* v_in, uint64_t step) {
+    if (!net || !m_in || !v_in) return FB_ERR_ARG;
+    NET_CUDA(net, cudaMemcpy(net->adam_m, m_in, net->n_params * 4, cudaMemcpyHostToDevice));
+    NET_CUDA(net, cudaMemcpy(net->adam_v, v_in, net->n_params * 4, cudaMemcpyHostToDevice));
+    net->step = step;
+    return FB_OK;
+}
+
 int fb_initnet_forward(fb_initnet* net, const uint8_t* src, const uint8_t* tgt, int n,
                        float* head_out, void* stream) {
     if (!net || !src || !tgt || n < 1 || n > net->max_pairs) return FB_ERR_ARG;

@@ -78,15 +78,18 @@ def initial_params(n_params: int, seed: int) -> np.ndarray:
 
 
 def train(net: InitNet, ts: TrainingSet, steps: int = 1500, batch_size: int = 8, lr: float = 1e-3,
-          warmup: int = 200, seed: int = 0, log_every: int = 100):
+          warmup: int = 200, seed: int = 0, log_every: int = 100, start: int = 0, stop: int = None,
+          rng: np.random.Generator = None):
     """Adam with a linear warm-up over `warmup` steps, then a cosine-decayed step size;
     returns the loss history (every log_every).  Without the warm-up the first few
-    hundred steps swing widely and a run can stall on a plateau."""
-    rng = np.random.default_rng(seed)
+    hundred steps swing widely and a run can stall on a plateau.  Steps [start, stop) of
+    the `steps`-step schedule run (a resumed run passes the checkpoint's step and batch
+    sampler `rng`)."""
+    rng = np.random.default_rng(seed) if rng is None else rng
     hist = []
     loss = torch.zeros(1, dtype=torch.float32, device="cuda")
     t0 = time.perf_counter()
-    for s in range(steps):
+    for s in range(start, steps if stop is None else stop):
         idx = rng.choice(len(ts.pairs), size=batch_size, replace=False)
         src, tgt, target, weight = batch(ts, idx)
         wsum = max(float(weight.sum()), 1.0)
@@ -100,12 +103,32 @@ def train(net: InitNet, ts: TrainingSet, steps: int = 1500, batch_size: int = 8,
 
 
 def save(net: InitNet, path: str) -> None:
-    """Checkpoint: the FP32 parameters (the Adam state is not kept)."""
+    """The FP32 parameters only (what an evaluation needs)."""
     np.save(path, net.get_params())
 
 
 def load(net: InitNet, path: str) -> None:
     net.set_params(np.load(path))
+
+
+def save_checkpoint(net: InitNet, path: str, step: int, rng: np.random.Generator) -> None:
+    """Everything a resumed run needs: parameters, Adam moments and update count, the
+    schedule step and the batch sampler's state (a host .npz file)."""
+    import json
+    m, v, updates = net.get_optimizer()
+    np.savez(path, params=net.get_params(), adam_m=m, adam_v=v, updates=np.uint64(updates),
+             step=np.int64(step), rng=np.array(json.dumps(rng.bit_generator.state)))
+
+
+def load_checkpoint(net: InitNet, path: str):
+    """Restores a save_checkpoint file into `net`; returns (schedule step, batch sampler)."""
+    import json
+    z = np.load(path)
+    net.set_params(z["params"])
+    net.set_optimizer(z["adam_m"], z["adam_v"], int(z["updates"]))
+    rng = np.random.default_rng()
+    rng.bit_generator.state = json.loads(str(z["rng"]))
+    return int(z["step"]), rng
 
 
 def train_default(ctx: Context, H: int, W: int, max_pairs: int = 256, steps: int = 2500,
