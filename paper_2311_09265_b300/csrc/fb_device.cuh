@@ -565,7 +565,9 @@ __device__ __forceinline__ void remap_votes(const uint32_t* __restrict__ Fq,
                                             const uint32_t* __restrict__ S, int H, int W, int r,
                                             int c, uint32_t& v0, uint32_t& v1, uint32_t& v2) {
     constexpr int P = K / 2;
-    v0 = v1 = v2 = 0;
+    // Channels summed two to a register in 16-bit lanes (R and B; G and the pad byte):
+    // a lane holds at most k^2 * 255 <= 20655 for k <= 9, so no lane carries over.
+    uint32_t rb = 0, gx = 0;
 #pragma unroll
     for (int a = -P; a <= P; ++a) {
         const int qr = clampi(r + a, 0, H - 1);
@@ -576,11 +578,13 @@ __device__ __forceinline__ void remap_votes(const uint32_t* __restrict__ Fq,
             const int sr = clampi(row_of(f) - (qr - r), 0, H - 1);
             const int sc = clampi(col_of(f) - (qc - c), 0, W - 1);
             const uint32_t s = __ldg(S + static_cast<size_t>(sr) * W + sc);
-            v0 += s & 0xFFu;
-            v1 += (s >> 8) & 0xFFu;
-            v2 += (s >> 16) & 0xFFu;
+            rb += s & 0x00FF00FFu;
+            gx += (s >> 8) & 0x00FF00FFu;
         }
     }
+    v0 = rb & 0xFFFFu;
+    v1 = gx & 0xFFFFu;
+    v2 = rb >> 16;
 }
 
 // Alg. 2 vote sums of a fast-mode table entry (three uint32 sums per 16-byte pixel).
