@@ -185,3 +185,21 @@ def test_aligned_tracking_interp_1024x576_frame_size(fbp, ctx):
     out = fbp.fb_interpolate(ctx, cuda(g), keys, cuda(ks), p).cpu().numpy()
     ref = oracle.interpolate_aligned(g, keys, ks, w.patch, 2, 10, tracking=True, seed=w.seed)
     assert (out == ref).all()
+
+
+@pytest.mark.parametrize("H,W", [(9, 32767), (32767, 9)])
+def test_segment_at_the_largest_image_side(fbp, ctx, H, W):
+    """Coupled and tracked fields with packed (row << 16 | col) entries at the largest
+    supported side: every field and loss bit-exact."""
+    g = np.stack([synth.noise_pair(H, W, seed=31 + q)[0] for q in range(4)])
+    ks = np.stack([synth.noise_pair(H, W, seed=71)[1], synth.noise_pair(H, W, seed=72)[1]])
+    n = 2
+    p = fbp.Params.make(5, 1, 1, 0, 9, flags=fbp.FB_FLAG_ALIGN | fbp.FB_FLAG_TRACKING, alpha=10)
+    F, E = fbp.fb_nnf_segment(ctx, cuda(g), cuda(ks), p)
+    F, E = F.cpu().numpy(), E.cpu().numpy().view(np.uint32)
+    tl = [oracle.pair_tag(0, q) for q in range(1, n + 1)]
+    tr = [oracle.pair_tag(n + 1, q) for q in range(1, n + 1)]
+    Fo, Eo = oracle.nnf_segment(g[0], g[n + 1], ks[0], ks[1], g[1:n + 1], 5, 1, 10, tl, tr,
+                                tracking=True, seed=9)
+    assert (F == Fo.reshape(2 * n, H, W, 2)).all() and (E == Eo.reshape(2 * n, H, W)).all()
+    assert F[..., 0].max() <= H - 1 and F[..., 1].max() <= W - 1

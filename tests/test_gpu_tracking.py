@@ -159,3 +159,12 @@ def test_tracking_blend_512_frame_size(fbp, ctx):
     out = fbp.fb_blend_window(ctx, cuda(g), cuda(s), w.window, p).cpu().numpy()
     ref = oracle.blend_window_tracking(g, s, w.window, w.patch, 2, seed=w.seed)
     assert (out == ref).all()
+
+
+@pytest.mark.parametrize("H,W", [(9, 32767), (32767, 9)])
+def test_tracking_blend_at_the_largest_image_side(fbp, ctx, H, W):
+    g = np.stack([synth.noise_pair(H, W, seed=51 + q)[0] for q in range(3)])
+    s = np.stack([synth.noise_pair(H, W, seed=61 + q)[1] for q in range(3)])
+    p = fbp.Params.make(5, 1, 1, 0, 4, flags=fbp.FB_FLAG_TRACKING)
+    out = fbp.fb_blend_window(ctx, cuda(g), cuda(s), 5, p).cpu().numpy()
+    assert (out == oracle.blend_window_tracking(g, s, 5, 5, 1, seed=4)).all()
