@@ -61,3 +61,12 @@ def test_accurate_blend_512_full_size_sampled_frame(fbp, ctx):
     out = fbp.fb_blend_window(ctx, cuda(g), cuda(s), w.window, p)
     ref, _, _ = oracle.blend_frame_accurate(g, s, w.window, 31, w.patch, w.iters, ACCURATE_ALPHA, seed=w.seed)
     assert (out[31].cpu().numpy() == ref).all()
+
+
+@pytest.mark.parametrize("H,W", [(9, 32767), (32767, 9)])
+def test_accurate_mode_at_the_largest_image_side(fbp, ctx, H, W):
+    g = np.stack([synth.noise_pair(H, W, seed=11 + q)[0] for q in range(3)])
+    s = np.stack([synth.noise_pair(H, W, seed=21 + q)[1] for q in range(3)])
+    p = fbp.Params.make(5, 1, 1, 0, 2, flags=fbp.FB_FLAG_ACCURATE, alpha=10)
+    out = fbp.fb_blend_window(ctx, cuda(g), cuda(s), 3, p).cpu().numpy()
+    assert (out == oracle.blend_window_accurate(g, s, 3, 5, 1, 10, seed=2)).all()

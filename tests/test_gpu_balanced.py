@@ -107,3 +107,21 @@ def test_balanced_blend_512_full_size_sampled_frame(fbp, ctx):
     i = 31
     ref = oracle.blend_frame_balanced(g, s, w.window, i, w.patch, w.iters, BALANCED_ALPHA, seed=w.seed)
     assert (out[i].cpu().numpy() == ref).all()
+
+
+@pytest.mark.parametrize("H,W", [(9, 32767), (32767, 9)])
+def test_balanced_at_the_largest_image_side(fbp, ctx, H, W):
+    """Improved loss with packed field entries at the largest supported side: fields,
+    losses and S^ of one pair, and a short blend, bit-exact."""
+    g0, g1 = synth.noise_pair(H, W, seed=5)
+    s0 = synth.noise_pair(H, W, seed=6)[0]
+    p = fbp.Params.make(5, 1, 1, 0, 3, pair_tag=17, alpha=10)
+    F, E, S = fbp.fb_nnf_balanced(ctx, cuda(g0), cuda(g1), cuda(s0), p)
+    Fo, Eo, So = oracle.nnf_balanced(g0, g1, s0, 5, 1, 10, seed=3, pair_tag=17)
+    assert (F.cpu().numpy() == Fo).all() and (E.cpu().numpy().view(np.uint32) == Eo).all()
+    assert (S.cpu().numpy() == So).all()
+    g = np.stack([g0, g1, synth.noise_pair(H, W, seed=7)[0]])
+    s = np.stack([s0, synth.noise_pair(H, W, seed=8)[0], synth.noise_pair(H, W, seed=9)[0]])
+    pb = fbp.Params.make(5, 1, 1, 0, 3, flags=fbp.FB_FLAG_BALANCED, alpha=10)
+    out = fbp.fb_blend_window(ctx, cuda(g), cuda(s), 3, pb).cpu().numpy()
+    assert (out == oracle.blend_window_balanced(g, s, 3, 5, 1, 10, seed=3)).all()

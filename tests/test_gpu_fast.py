@@ -94,3 +94,12 @@ def test_fast_blend_512_full_size_sampled_frame(fbp, ctx):
     out = fbp.fb_blend_window(ctx, cuda(g), cuda(s), w.window, p)
     ref = oracle.blend_frame_fast(g, s, w.window, 31, w.patch, w.iters, seed=w.seed)
     assert (out[31].cpu().numpy() == ref).all()
+
+
+@pytest.mark.parametrize("H,W", [(9, 32767), (32767, 9)])
+def test_fast_mode_at_the_largest_image_side(fbp, ctx, H, W):
+    g = np.stack([synth.noise_pair(H, W, seed=81 + q)[0] for q in range(5)])
+    s = np.stack([synth.noise_pair(H, W, seed=91 + q)[1] for q in range(5)])
+    p = fbp.Params.make(5, 1, 1, 0, 6, flags=fbp.FB_FLAG_FAST)
+    out = fbp.fb_blend_window(ctx, cuda(g), cuda(s), 5, p).cpu().numpy()
+    assert (out == oracle.blend_window_fast(g, s, 5, 5, 1, seed=6)).all()
