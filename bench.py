@@ -46,6 +46,10 @@ BALANCED_ALPHA = 10
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the workload's iteration
 # kernel, from an ncu capture of the current kernel on a smaller case scaled by the pairs
 # per launch (see profiles/); None when not captured or when the workload is overridden.
+# What the ncu captures of the iteration kernels show bounds them (see profiles/): the dp4a
+# ALU peak above is the arithmetic roofline, not the limit these gathers reach.
+LIMITER = {"k5": "L1TEX pipe 84-88 % of peak on scattered candidate loads (ncu); DRAM 2-4 %",
+           "k7": "L1TEX pipe 90-92 % of peak on scattered candidate loads (ncu); DRAM 2 %"}
 TRAFFIC_PER_LAUNCH = {"blend_512": 5.73e9, "tracking_512": 4.08e9, "balanced_512": 9.11e9,
                       "aligned_1024x576": 8.24e9, "interp_1024x576": 2.40e9}
 
@@ -596,6 +600,7 @@ def run_gpu(args):
                 "achieved": achieved, "peak": peak, "unit": "T byte-pair ops/s",
                 "frac": achieved / peak, "traffic": (None if args.window or args.frames
                                                       else TRAFFIC_PER_LAUNCH.get(args.workload)),
+                "observed_limiter": LIMITER.get("k7" if w.patch == 7 else "k5"),
                 "peak_basis": (f"{DP4A_PER_CLK_SM} dp4a/clk/SM x {SM_COUNT_NOMINAL} SMs x "
                                f"{SM_MAX_MHZ_NOMINAL:.0f} MHz x 4 byte pairs (derived; the live "
                                f"register-only probe measured {probe_per_clk:.1f} dp4a/clk/SM)"
