@@ -43,13 +43,13 @@ SM_MAX_MHZ_NOMINAL = 2032.0
 DP4A_PER_CLK_SM = 64        # integer dot-product (dp4a) issue rate per SM per clock
 # Guide weight of the improved loss (Sec. 3.4) in the balanced workload.
 BALANCED_ALPHA = 10
-# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the workload's iteration
-# kernel, from an ncu capture of the current kernel on a smaller case scaled by the pairs
-# per launch (see profiles/); None when not captured or when the workload is overridden.
 # What the ncu captures of the iteration kernels show bounds them (see profiles/): the dp4a
 # ALU peak above is the arithmetic roofline, not the limit these gathers reach.
 LIMITER = {"k5": "L1TEX pipe 84-88 % of peak on scattered candidate loads (ncu); DRAM 2-4 %",
            "k7": "L1TEX pipe 90-92 % of peak on scattered candidate loads (ncu); DRAM 2 %"}
+# dram__bytes_read.sum + dram__bytes_write.sum of one launch of the workload's iteration
+# kernel, from an ncu capture of the current kernel on a smaller case scaled by the pairs
+# per launch (see profiles/); None when not captured or when the workload is overridden.
 TRAFFIC_PER_LAUNCH = {"blend_512": 5.73e9, "tracking_512": 4.08e9, "balanced_512": 9.11e9,
                       "aligned_1024x576": 8.24e9, "interp_1024x576": 2.40e9}
 
