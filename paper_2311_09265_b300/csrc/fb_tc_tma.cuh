@@ -2,7 +2,7 @@
 // initialiser as a tcgen05 GEMM whose operands the Tensor Memory Accelerator stages:
 //
 //   Y[p][co] = sum_{tap, ci} X[s p + tap - (1, 1)][ci] W[co][tap][ci]    (M = output
-//   pixels, N = Cout, K = 9 Cin, walked tap-major in blocks of 64 input channels)
+//   pixels, N = Cout, K = 9 Cin, walked tap-major in chunks of K = 64)
 //
 // A CTA of 128 threads owns 128 output pixels -- whole output rows (R rows of one image,
 // or I whole images when an image has fewer than 128 output pixels) -- by BN output
