@@ -864,16 +864,33 @@ int run_fast_pipeline(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles,
     const uint8_t* g_dev = guides;
     const uint8_t* s_dev = styles;
     float* o_dev = out;
+    // Host buffers as in run_pipeline: styles in on the copy stream while the NNFs are
+    // computed (only the tables read them), frames out in groups as their queries finish.
+    constexpr int kOutGroups = 4;
+    bool frames_in_order = true;
+    for (size_t j = 0; j < plan.jobs.size(); ++j)
+        frames_in_order = frames_in_order && plan.jobs[j].frame == static_cast<int>(j);
+    if (ctx->copy_stream) {  // a failed earlier call may have left copies of the arena in flight
+        rc = ensure_xfer(ctx, 1);
+        if (rc) return rc;
+        FB_CUDA(ctx, cudaEventRecord(ctx->xfer_ev[0], ctx->copy_stream));
+        FB_CUDA(ctx, cudaStreamWaitEvent(st, ctx->xfer_ev[0], 0));
+    }
+    size_t ev = 0;
     if (staging) {
+        rc = ensure_xfer(ctx, 2 + kOutGroups + 1);
+        if (rc) return rc;
         FB_CUDA(ctx, cudaMemcpyAsync(b.in_guides, guides, fbytes, cudaMemcpyHostToDevice, st));
-        FB_CUDA(ctx, cudaMemcpyAsync(b.in_styles, styles, fbytes, cudaMemcpyHostToDevice, st));
+        FB_CUDA(ctx, cudaEventRecord(ctx->xfer_ev[ev], st));
+        FB_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->xfer_ev[ev++], 0));
+        FB_CUDA(ctx, cudaMemcpyAsync(b.in_styles, styles, fbytes, cudaMemcpyHostToDevice, ctx->copy_stream));
+        FB_CUDA(ctx, cudaEventRecord(ctx->xfer_ev[ev++], ctx->copy_stream));
         g_dev = b.in_guides;
         s_dev = b.in_styles;
         o_dev = b.in_out;
     }
     rc = prep_guides(ctx, b, L, k, g_dev, N, 0, st);
     if (rc) return rc;
-    FB_LAUNCH(ctx, st, FB_K_STYLE, fb::launch_style_rgbx(s_dev, static_cast<size_t>(N) * npx0, b.styles, st));
     if (p->flags & FB_FLAG_REPORT_ENERGY) {
         FB_CUDA(ctx, cudaMemsetAsync(ctx->energy, 0, sizeof(double), st));
         ctx->energy_count = 0;
@@ -887,12 +904,31 @@ int run_fast_pipeline(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles,
             ctx->energy_count += static_cast<uint64_t>(n_pairs) * npx0;
         }
     }
+    if (staging) FB_CUDA(ctx, cudaStreamWaitEvent(st, ctx->xfer_ev[1], 0));  // the styles are in
+    FB_LAUNCH(ctx, st, FB_K_STYLE, fb::launch_style_rgbx(s_dev, static_cast<size_t>(N) * npx0, b.styles, st));
     FB_LAUNCH(ctx, st, FB_K_TABLE, fb::launch_fast_table(k, d_entries, static_cast<int>(n_entries), d_src, b.pairs,
                                                          F, b.styles, H, W, d_table, st));
-    FB_LAUNCH(ctx, st, FB_K_COMBINE, fb::launch_fast_combine(k, d_jobs, static_cast<int>(plan.jobs.size()),
-                                                             d_pieces, F, d_table, b.styles, H, W, o_dev, st));
+    const int n_jobs = static_cast<int>(plan.jobs.size());
+    if (!staging || !frames_in_order) {
+        FB_LAUNCH(ctx, st, FB_K_COMBINE, fb::launch_fast_combine(k, d_jobs, n_jobs, d_pieces, F, d_table, b.styles,
+                                                                 H, W, o_dev, st));
+        if (staging) FB_CUDA(ctx, cudaMemcpyAsync(out, o_dev, fbytes * sizeof(float), cudaMemcpyDeviceToHost, st));
+    } else {
+        const int per = (n_jobs + kOutGroups - 1) / kOutGroups;
+        for (int j0 = 0; j0 < n_jobs; j0 += per) {
+            const int nj = std::min(per, n_jobs - j0);
+            FB_LAUNCH(ctx, st, FB_K_COMBINE, fb::launch_fast_combine(k, d_jobs + j0, nj, d_pieces, F, d_table,
+                                                                     b.styles, H, W, o_dev, st));
+            FB_CUDA(ctx, cudaEventRecord(ctx->xfer_ev[ev], st));
+            FB_CUDA(ctx, cudaStreamWaitEvent(ctx->copy_stream, ctx->xfer_ev[ev++], 0));
+            const size_t f0 = static_cast<size_t>(j0) * npx0 * 3;
+            FB_CUDA(ctx, cudaMemcpyAsync(out + f0, o_dev + f0, static_cast<size_t>(nj) * npx0 * 3 * sizeof(float),
+                                         cudaMemcpyDeviceToHost, ctx->copy_stream));
+        }
+    }
     if (staging) {
-        FB_CUDA(ctx, cudaMemcpyAsync(out, o_dev, fbytes * sizeof(float), cudaMemcpyDeviceToHost, st));
+        FB_CUDA(ctx, cudaEventRecord(ctx->xfer_ev[ev], ctx->copy_stream));
+        FB_CUDA(ctx, cudaStreamWaitEvent(st, ctx->xfer_ev[ev++], 0));
         FB_CUDA(ctx, cudaStreamSynchronize(st));
     }
     return FB_OK;
