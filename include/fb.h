@@ -277,6 +277,49 @@ int fb_interpolate(fb_ctx *ctx, const uint8_t *guides, int N, int H, int W,
                    const int32_t *key_idx, const uint8_t *key_styles, int n_keys,
                    const fb_params *p, float *out, void *stream);
 
+/* Output-frame ranges of one clip, for splitting a clip across GPUs (one process per GPU,
+ * each blending its own range; no data exchange between them).  Every output frame of
+ * Eq. 2 depends only on the frames of its window [i - M, i + M] (Sec. 3.4), so a range of
+ * output frames [a, b) needs only the input frames [a - M, b + M) (clipped to the clip):
+ * the range plus an M-frame halo on either side.  Each NNF keeps the random stream of its
+ * clip frames, fb_pair_tag(j, i), so the range's output frames are bit-identical to the
+ * same frames of fb_blend_window over the whole clip.
+ *   n_total     frames in the whole clip (the windows are truncated at its ends).
+ *   frame_base  clip index of guides[0] / styles[0]; the call holds n_in frames,
+ *               clip frames [frame_base, frame_base + n_in).
+ *   out_first, n_out  the output frames [out_first, out_first + n_out) (clip indices);
+ *               out holds n_out frames, n_out x H x W x 3 float32.
+ * FB_ERR_ARG when an output frame's window reaches outside the held input frames.
+ * Modes: plain, FB_FLAG_BALANCED, FB_FLAG_ACCURATE (its mean frame couples only the NNFs
+ * of one output frame), FB_FLAG_LEARNED_INIT, FB_FLAG_REPORT_ENERGY.  FB_FLAG_FAST and
+ * FB_FLAG_TRACKING couple output frames across the clip: FB_ERR_UNSUPPORTED.  Memory
+ * rules and everything else as fb_blend_window. */
+int fb_blend_window_range(fb_ctx *ctx, const uint8_t *guides, const uint8_t *styles, int n_in,
+                          int H, int W, int window, const fb_params *p, int n_total,
+                          int frame_base, int out_first, int n_out, float *out, void *stream);
+
+/* The output frames [out_first, out_first + n_out) of fb_interpolate over the whole
+ * N-frame clip (Sec. 3.5.2: every frame depends only on its keys), bit-identical to those
+ * frames of the whole-clip call.  guides holds all N frames (the keys are the sources);
+ * out holds n_out frames.  FB_FLAG_ALIGN is supported (its two coupled NNFs belong to
+ * the same output frame); FB_FLAG_TRACKING is not (FB_ERR_UNSUPPORTED).  Other arguments
+ * as fb_interpolate. */
+int fb_interpolate_range(fb_ctx *ctx, const uint8_t *guides, int N, int H, int W,
+                         const int32_t *key_idx, const uint8_t *key_styles, int n_keys,
+                         const fb_params *p, int out_first, int n_out, float *out, void *stream);
+
+/* Host-only split of an N-frame clip into n_shards contiguous ranges of output frames of
+ * about equal work (blend, window > 0: an output frame's work is its NNFs plus its
+ * combine; interpolation, window = 0: one unit per frame), for shard `shard` in
+ * [0, n_shards): the output range [*out_first, *out_first + *n_out) (never empty) and
+ * the input frames [*frame_base, *frame_base + *n_in) that fb_blend_window_range needs
+ * for it (the range plus the (window - 1) / 2 halo, clipped; interpolation: the whole
+ * clip).  The shards cover every output frame exactly once.  No CUDA calls; FB_ERR_ARG
+ * for N outside [1, 65535], an even or negative window, n_shards outside [1, N] or shard
+ * outside [0, n_shards). */
+int fb_shard_plan(int N, int window, int n_shards, int shard, int *frame_base, int *n_in,
+                  int *out_first, int *n_out);
+
 /* One clip of a batched submission (fb_blend_batch).  All pointers are device
  * pointers of the context's device, owned by the caller. */
 typedef struct fb_clip_desc {
@@ -336,6 +379,16 @@ typedef struct fb_pair_info {
  * for invalid arguments or cap below the count. */
 int fb_pair_plan(int N, int window, const int32_t *key_idx, int n_keys, uint32_t flags,
                  fb_pair_info *out, size_t cap, size_t *n_pairs);
+
+/* The NNFs of fb_blend_window_range / fb_interpolate_range for the output frames
+ * [out_first, out_first + n_out) of an N-frame clip, in their order, with clip frame
+ * indices (src, tgt and out_frame) as fb_pair_plan gives them: exactly the entries of
+ * fb_pair_plan over the whole clip whose out_frame lies in the range, except that
+ * `partner` indexes this list (prev / next are -1: tracking has no range form).  flags: 0 or
+ * (interpolation) FB_FLAG_ALIGN.  Host only; errors as fb_pair_plan, and FB_ERR_ARG for a
+ * range outside the clip. */
+int fb_pair_plan_range(int N, int window, const int32_t *key_idx, int n_keys, uint32_t flags,
+                       int out_first, int n_out, fb_pair_info *out, size_t cap, size_t *n_pairs);
 
 /* Host-only planning of the fast mode (FB_FLAG_FAST) for N frames and `window`: the
  * number of distinct NNFs it computes, of blending-table entries it builds and of query

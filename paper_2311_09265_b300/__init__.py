@@ -25,6 +25,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a",
                     "fb_debug_candidates_considered", "fb_pair_tag",
                     "fb_nnf", "fb_nnf_balanced", "fb_nnf_segment", "fb_remap", "fb_blend_window", "fb_interpolate",
+                    "fb_blend_window_range", "fb_interpolate_range", "fb_shard_plan", "fb_pair_plan_range",
                     "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan", "fb_fast_plan", "fb_pair_plan",
                     "fb_ctx_batch_variant", "fb_ctx_set_pair_budget",
                     "fb_initnet_create", "fb_initnet_destroy", "fb_initnet_last_error",
@@ -144,6 +145,17 @@ def lib() -> ctypes.CDLL:
                                      _vp, ctypes.c_int, P, _vp, _vp]
         L.fb_blend_window_noalloc.argtypes = [_vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                               ctypes.c_int, P, _vp, _vp]
+        ci = ctypes.c_int
+        L.fb_blend_window_range.argtypes = [_vp, _vp, _vp, ci, ci, ci, ci, P, ci, ci, ci, ci, _vp, _vp]
+        L.fb_blend_window_range.restype = ctypes.c_int
+        L.fb_interpolate_range.argtypes = [_vp, _vp, ci, ci, ci, _vp, _vp, ci, P, ci, ci, _vp, _vp]
+        L.fb_interpolate_range.restype = ctypes.c_int
+        L.fb_shard_plan.argtypes = [ci, ci, ci, ci] + [ctypes.POINTER(ci)] * 4
+        L.fb_shard_plan.restype = ctypes.c_int
+        L.fb_pair_plan_range.argtypes = [ci, ci, ctypes.POINTER(ctypes.c_int32), ci, ctypes.c_uint32, ci, ci,
+                                         ctypes.POINTER(PairInfo), ctypes.c_size_t,
+                                         ctypes.POINTER(ctypes.c_size_t)]
+        L.fb_pair_plan_range.restype = ctypes.c_int
         L.fb_blend_window_noalloc.restype = ctypes.c_int
         CP = ctypes.POINTER(ClipDesc)
         L.fb_blend_batch.argtypes = [_vp, CP, ctypes.c_int, P, ctypes.c_uint32, _vp]
@@ -224,6 +236,35 @@ def fb_pair_plan(N: int, window: int = 0, keys=None, flags: int = 0):
     if rc != FB_OK:
         raise FastBlendError(rc, "fb_pair_plan")
     return [{f: getattr(out[q], f) for f, _ in PairInfo._fields_} for q in range(n.value)]
+
+
+def fb_pair_plan_range(N: int, out_first: int, n_out: int, window: int = 0, keys=None,
+                       flags: int = 0):
+    """The NNFs of a range call over output frames [out_first, out_first + n_out) of an
+    N-frame clip (host only), as fb_pair_plan lists them (clip frame indices)."""
+    karr, nk = None, 0
+    if keys is not None:
+        nk = len(keys)
+        karr = (ctypes.c_int32 * max(nk, 1))(*keys)
+    n = ctypes.c_size_t()
+    rc = lib().fb_pair_plan_range(N, window, karr, nk, flags, out_first, n_out, None, 0, ctypes.byref(n))
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_pair_plan_range")
+    out = (PairInfo * max(n.value, 1))()
+    rc = lib().fb_pair_plan_range(N, window, karr, nk, flags, out_first, n_out, out, n.value, ctypes.byref(n))
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_pair_plan_range")
+    return [{f: getattr(out[q], f) for f, _ in PairInfo._fields_} for q in range(n.value)]
+
+
+def fb_shard_plan(N: int, window: int, n_shards: int, shard: int) -> dict:
+    """Shard `shard` of an N-frame clip split over n_shards GPUs (host only): its output
+    frames [out_first, out_first + n_out) and input frames [frame_base, frame_base + n_in)."""
+    v = [ctypes.c_int() for _ in range(4)]
+    rc = lib().fb_shard_plan(N, window, n_shards, shard, *[ctypes.byref(x) for x in v])
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_shard_plan")
+    return dict(zip(("frame_base", "n_in", "out_first", "n_out"), (int(x.value) for x in v)))
 
 
 def fb_conv_gemm_path(mode: int = -1) -> int:
@@ -452,6 +493,28 @@ def fb_blend_window(ctx: Context, guides: torch.Tensor, styles: torch.Tensor, wi
     return out
 
 
+def fb_blend_window_range(ctx: Context, guides: torch.Tensor, styles: torch.Tensor, window: int,
+                          params: Params, n_total: int, frame_base: int, out_first: int, n_out: int,
+                          out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Output frames [out_first, out_first + n_out) of the Eq. 2 blend of an n_total-frame
+    clip, from its frames [frame_base, frame_base + len(guides)) (CUDA or CPU tensors, as
+    fb_blend_window).  Returns (n_out,H,W,3) float32, equal to those frames of the
+    whole-clip blend."""
+    n_in, H, W = (int(s) for s in guides.shape[:3])
+    _shape(guides, (n_in, H, W, 3), "guides")
+    _shape(styles, (n_in, H, W, 3), "styles")
+    if out is None:
+        out = torch.empty((n_out, H, W, 3), dtype=torch.float32, device=guides.device,
+                          pin_memory=(not guides.is_cuda))
+    _shape(out, (n_out, H, W, 3), "out")
+    rc = lib().fb_blend_window_range(ctx.handle, _ptr(guides, torch.uint8, "guides"),
+                                     _ptr(styles, torch.uint8, "styles"), n_in, H, W, window,
+                                     ctypes.byref(params), n_total, frame_base, out_first, n_out,
+                                     _ptr(out, torch.float32, "out"), _stream_handle(stream, ctx.device))
+    ctx.check(rc)
+    return out
+
+
 def fb_interpolate(ctx: Context, guides: torch.Tensor, key_idx: Sequence[int],
                    key_styles: torch.Tensor, params: Params, out: Optional[torch.Tensor] = None,
                    stream=None) -> torch.Tensor:
@@ -468,6 +531,27 @@ def fb_interpolate(ctx: Context, guides: torch.Tensor, key_idx: Sequence[int],
                               ctypes.cast(keys, _vp), _ptr(key_styles, torch.uint8, "key_styles"),
                               len(key_idx), ctypes.byref(params), _ptr(out, torch.float32, "out"),
                               _stream_handle(stream, ctx.device))
+    ctx.check(rc)
+    return out
+
+
+def fb_interpolate_range(ctx: Context, guides: torch.Tensor, key_idx: Sequence[int],
+                         key_styles: torch.Tensor, params: Params, out_first: int, n_out: int,
+                         out: Optional[torch.Tensor] = None, stream=None) -> torch.Tensor:
+    """Output frames [out_first, out_first + n_out) of fb_interpolate over the whole clip
+    (guides: all N frames).  Returns (n_out,H,W,3) float32."""
+    N, H, W = (int(s) for s in guides.shape[:3])
+    _shape(guides, (N, H, W, 3), "guides")
+    keys = (ctypes.c_int32 * len(key_idx))(*[int(k) for k in key_idx])
+    _shape(key_styles, (len(key_idx), H, W, 3), "key_styles")
+    if out is None:
+        out = torch.empty((n_out, H, W, 3), dtype=torch.float32, device=guides.device,
+                          pin_memory=(not guides.is_cuda))
+    _shape(out, (n_out, H, W, 3), "out")
+    rc = lib().fb_interpolate_range(ctx.handle, _ptr(guides, torch.uint8, "guides"), N, H, W,
+                                    ctypes.cast(keys, _vp), _ptr(key_styles, torch.uint8, "key_styles"),
+                                    len(key_idx), ctypes.byref(params), out_first, n_out,
+                                    _ptr(out, torch.float32, "out"), _stream_handle(stream, ctx.device))
     ctx.check(rc)
     return out
 

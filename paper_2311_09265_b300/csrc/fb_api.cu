@@ -471,18 +471,25 @@ void set_chain_neighbours(std::vector<PairDesc>& pairs) {
 }
 
 // Eq. 2 (a1, blending): one job per output frame i; its pairs are (j -> i) for j in the
-// window [i - M, i + M] truncated to the clip, j != i, in increasing j, each weight 1.
+// window [i - M, i + M] truncated to the clip [0, N), j != i, in increasing j, each weight 1.
+// Output frames [i0, i1) of the clip (default: all); job q writes output slot q = i - i0.
+// Guide and style slots are clip frames minus `base` (the clip frame held in slot 0), while
+// every pair keeps the Philox stream of its clip frames, fb_pair_tag(j, i): a call over a
+// range of output frames with the input frames their windows need (Sec. 3.4's sliding
+// window makes that range plus M frames on either side) computes the very NNFs, and so the
+// very output frames, that the whole-clip call does.
 void blend_pairs(int N, int k, int window, uint32_t flags, std::vector<PairDesc>& pairs,
-                 std::vector<JobDesc>& jobs) {
+                 std::vector<JobDesc>& jobs, int i0 = 0, int i1 = -1, int base = 0) {
     const int M = (window - 1) / 2;
+    if (i1 < 0) i1 = N;
     pairs.clear();
-    jobs.assign(N, JobDesc{});
-    for (int i = 0; i < N; ++i) {
+    jobs.assign(i1 - i0, JobDesc{});
+    for (int i = i0; i < i1; ++i) {
         const int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
-        jobs[i] = JobDesc{i, i, 1u, static_cast<int32_t>(pairs.size()), hi - lo,
-                          static_cast<uint32_t>(255 * k * k * (hi - lo + 1)), {0, 0}};
+        jobs[i - i0] = JobDesc{i - i0, i - base, 1u, static_cast<int32_t>(pairs.size()), hi - lo,
+                               static_cast<uint32_t>(255 * k * k * (hi - lo + 1)), {0, 0}};
         for (int j = lo; j <= hi; ++j)
-            if (j != i) pairs.push_back(PairDesc{j, i, fb_pair_tag(j, i), j, 1u, {-1, -1, -1}});
+            if (j != i) pairs.push_back(PairDesc{j - base, i - base, fb_pair_tag(j, i), j - base, 1u, {-1, -1, -1}});
     }
     if (flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
 }
@@ -490,19 +497,23 @@ void blend_pairs(int N, int k, int window, uint32_t flags, std::vector<PairDesc>
 // Sec. 3.5.2 (a1, interpolation; Eq. 9): keys are copied; a frame between keys l < i < r
 // takes the pairs (l -> i) with weight r - i and (r -> i) with weight i - l over r - l
 // (Eq. 10 partners of each other under FB_FLAG_ALIGN); a frame outside the key range
-// takes its nearest key alone, weight 1.  Key styles are indexed by key number.
+// takes its nearest key alone, weight 1.  Key styles are indexed by key number.  Output
+// frames [i0, i1) of the clip (default: all), job q writing output slot q = i - i0; guide
+// slots are clip frames (the call holds every guide frame).
 void interp_pairs(int N, int k, const int32_t* key_idx, int n_keys, uint32_t flags,
-                  std::vector<PairDesc>& pairs, std::vector<JobDesc>& jobs) {
+                  std::vector<PairDesc>& pairs, std::vector<JobDesc>& jobs, int i0 = 0, int i1 = -1) {
     const uint32_t kk255 = static_cast<uint32_t>(255 * k * k);
+    if (i1 < 0) i1 = N;
     pairs.clear();
-    jobs.assign(N, JobDesc{});
+    jobs.assign(i1 - i0, JobDesc{});
     int m_left = -1;  // last key index < i
     int next = 0;     // first key with frame >= i
-    for (int i = 0; i < N; ++i) {
+    for (int i = 0; i < i1; ++i) {
         while (next < n_keys && key_idx[next] < i) m_left = next++;
+        if (i < i0) continue;
         const bool is_key = next < n_keys && key_idx[next] == i;
         const int m_right = is_key ? (next + 1 < n_keys ? next + 1 : -1) : (next < n_keys ? next : -1);
-        JobDesc j{i, -1, 0u, static_cast<int32_t>(pairs.size()), 0, kk255, {0, 0}};
+        JobDesc j{i - i0, -1, 0u, static_cast<int32_t>(pairs.size()), 0, kk255, {0, 0}};
         if (is_key) {
             j.self_style = next;
             j.self_w = 1u;
@@ -520,7 +531,7 @@ void interp_pairs(int N, int k, const int32_t* key_idx, int n_keys, uint32_t fla
             pairs.push_back(PairDesc{l, i, fb_pair_tag(l, i), m, 1u, {-1, -1, -1}});
             j.n_pairs = 1;
         }
-        jobs[i] = j;
+        jobs[i - i0] = j;
     }
     if (flags & FB_FLAG_TRACKING) set_chain_neighbours(pairs);
 }
@@ -572,8 +583,9 @@ int make_chunks(fb_ctx* ctx, const std::vector<JobDesc>& jobs, size_t npx0,
     return FB_OK;
 }
 
-// Shared driver of fb_blend_window and fb_interpolate: N guide frames, a style stack,
-// a pair table and one job per output frame.
+// Shared driver of fb_blend_window and fb_interpolate (and their range forms): N guide
+// frames, a style stack, a pair table and one job per output frame (out holds
+// jobs.size() frames).
 int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const uint8_t* styles,
                  int n_styles, const std::vector<PairDesc>& pairs, const std::vector<JobDesc>& jobs,
                  const fb_params* p, float* out, cudaStream_t st) {
@@ -603,7 +615,7 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
 
     const size_t guide_bytes = static_cast<size_t>(N) * npx0 * 3;
     const size_t style_bytes = static_cast<size_t>(n_styles) * npx0 * 3;
-    const size_t out_floats = static_cast<size_t>(N) * npx0 * 3;
+    const size_t out_floats = jobs.size() * npx0 * 3;  // one output frame per job
     const bool learned = (p->flags & FB_FLAG_LEARNED_INIT) != 0;
     if (learned) {
         if (!ctx->init_net) return fail(ctx, FB_ERR_ARG, "FB_FLAG_LEARNED_INIT without fb_ctx_set_initnet");
@@ -705,7 +717,7 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
                 }
                 init = b.init;
             }
-            rc = accurate ? run_nnf_accurate(ctx, b, H, W, p, c.job0, c.n_jobs, jobs[c.job0].out_frame, c.pair0,
+            rc = accurate ? run_nnf_accurate(ctx, b, H, W, p, c.job0, c.n_jobs, jobs[c.job0].self_style, c.pair0,
                                              c.n_pairs, st, &F, &E)
                  : balanced ? run_nnf_balanced(ctx, b, H, W, p, c.pair0, c.n_pairs, init, st, &F, &E)
                             : run_nnf(ctx, b, L, p, c.pair0, c.n_pairs, init, st, &F, &E);
@@ -1400,6 +1412,73 @@ extern "C" int fb_pair_plan(int N, int window, const int32_t* key_idx, int n_key
     return FB_OK;
 }
 
+extern "C" int fb_pair_plan_range(int N, int window, const int32_t* key_idx, int n_keys, uint32_t flags,
+                                  int out_first, int n_out, fb_pair_info* out, size_t cap, size_t* n_pairs) {
+    if (N < 1 || N > 65535 || n_out < 1 || out_first < 0 || out_first + n_out > N) return FB_ERR_ARG;
+    if (flags & ~FB_FLAG_ALIGN) return FB_ERR_ARG;  // tracking has no range form
+    std::vector<PairDesc> pairs;
+    std::vector<JobDesc> jobs;
+    if (window > 0) {
+        if ((window & 1) == 0 || key_idx || n_keys || (flags & FB_FLAG_ALIGN)) return FB_ERR_ARG;
+        blend_pairs(N, 3, window, flags, pairs, jobs, out_first, out_first + n_out, 0);
+    } else {
+        if (window < 0 || !key_idx || n_keys < 1 || n_keys > N) return FB_ERR_ARG;
+        for (int m = 0; m < n_keys; ++m)
+            if (key_idx[m] < 0 || key_idx[m] >= N || (m > 0 && key_idx[m] <= key_idx[m - 1])) return FB_ERR_ARG;
+        interp_pairs(N, 3, key_idx, n_keys, flags, pairs, jobs, out_first, out_first + n_out);
+    }
+    if (n_pairs) *n_pairs = pairs.size();
+    if (!out) return FB_OK;
+    if (cap < pairs.size()) return FB_ERR_ARG;
+    for (const JobDesc& j : jobs)
+        for (int q = 0; q < j.n_pairs; ++q) {
+            const PairDesc& pd = pairs[j.first_pair + q];
+            out[j.first_pair + q] = fb_pair_info{pd.src, pd.tgt, pd.tag, pd.weight, pd.pad[0], pd.pad[1],
+                                                 pd.pad[2], out_first + j.out_frame};
+        }
+    return FB_OK;
+}
+
+extern "C" int fb_shard_plan(int N, int window, int n_shards, int shard, int* frame_base, int* n_in,
+                             int* out_first, int* n_out) {
+    if (N < 1 || N > 65535 || window < 0 || (window > 0 && (window & 1) == 0)) return FB_ERR_ARG;
+    if (n_shards < 1 || n_shards > N || shard < 0 || shard >= n_shards) return FB_ERR_ARG;
+    // Work per output frame: its NNFs (blend: the truncated window's other frames), or one
+    // unit per frame for interpolation.  Shard s takes the output frames whose cumulative
+    // work before them lies in [s T / n, (s + 1) T / n) (T the total), so the shards are
+    // contiguous, cover the clip once and carry about equal work; each keeps at least one
+    // frame (n_shards <= N).
+    const int M = window > 0 ? (window - 1) / 2 : 0;
+    auto work = [&](int i) -> uint64_t {
+        if (window == 0) return 1;
+        const int lo = i - M < 0 ? 0 : i - M, hi = i + M > N - 1 ? N - 1 : i + M;
+        return static_cast<uint64_t>(hi - lo) + 1;  // + 1: the frame's own combine
+    };
+    uint64_t total = 0;
+    for (int i = 0; i < N; ++i) total += work(i);
+    std::vector<int> start(n_shards + 1, N);
+    start[0] = 0;
+    uint64_t acc = 0;
+    int s = 1;
+    for (int i = 0; i < N && s < n_shards; ++i) {
+        // frame i opens shard s once the work before it reaches s/n of the total
+        while (s < n_shards && acc * n_shards >= total * static_cast<uint64_t>(s)) start[s++] = i;
+        acc += work(i);
+    }
+    for (int q = 1; q <= n_shards; ++q) {  // at least one frame per shard
+        const int lo = start[q - 1] + 1, hi = N - (n_shards - q);
+        if (q < n_shards) start[q] = start[q] < lo ? lo : start[q] > hi ? hi : start[q];
+    }
+    const int a = start[shard], b = start[shard + 1];
+    const int in_lo = window > 0 ? (a - M < 0 ? 0 : a - M) : 0;
+    const int in_hi = window > 0 ? (b + M > N ? N : b + M) : N;
+    if (frame_base) *frame_base = in_lo;
+    if (n_in) *n_in = in_hi - in_lo;
+    if (out_first) *out_first = a;
+    if (n_out) *n_out = b - a;
+    return FB_OK;
+}
+
 extern "C" int fb_fast_plan(int N, int window, uint64_t* n_nnfs, uint64_t* n_entries,
                             uint64_t* n_pieces) {
     if (N < 1 || N > 65535 || window < 1 || (window & 1) == 0) return FB_ERR_ARG;
@@ -1891,6 +1970,86 @@ int fb_interpolate(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, cons
     std::vector<PairDesc> pairs;
     std::vector<JobDesc> jobs;
     interp_pairs(N, p->patch, key_idx, n_keys, p->flags, pairs, jobs);
+    DeviceGuard dg(ctx->device);
+    return run_pipeline(ctx, guides, N, H, W, key_styles, n_keys, pairs, jobs, p, out,
+                        static_cast<cudaStream_t>(stream));
+}
+
+// Modes whose pairs couple output frames across the whole clip cannot be cut into
+// output-frame ranges: the fast mode's tables span the clip (Algs. 3-5) and tracking's
+// chains run through the targets of one source (Sec. 3.5.1).
+static int check_range_flags(fb_ctx* ctx, const fb_params* p) {
+    if (p->flags & (FB_FLAG_FAST | FB_FLAG_TRACKING))
+        return fail(ctx, FB_ERR_UNSUPPORTED,
+                    "FB_FLAG_FAST and FB_FLAG_TRACKING couple output frames across the clip; "
+                    "a range call cannot reproduce them");
+    return FB_OK;
+}
+
+int fb_blend_window_range(fb_ctx* ctx, const uint8_t* guides, const uint8_t* styles, int n_in, int H, int W,
+                          int window, const fb_params* p, int n_total, int frame_base, int out_first, int n_out,
+                          float* out, void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->err.clear();
+    int rc = check_params(ctx, p, H, W);
+    if (rc) return rc;
+    if (n_total < 1 || n_total > 65535) return fail(ctx, FB_ERR_ARG, "n_total must be in [1, 65535], got %d", n_total);
+    if (window < 1 || (window & 1) == 0)
+        return fail(ctx, FB_ERR_ARG, "window must be odd and >= 1, got %d", window);
+    if (!guides || !styles || !out)
+        return fail(ctx, FB_ERR_ARG, "guides, styles and out must be non-NULL");
+    if (p->flags & FB_FLAG_ALIGN) return fail(ctx, FB_ERR_ARG, "FB_FLAG_ALIGN applies to fb_interpolate only");
+    if (frame_base < 0 || n_in < 1 || frame_base + n_in > n_total)
+        return fail(ctx, FB_ERR_ARG, "input frames [%d, %d) are not inside the clip [0, %d)", frame_base,
+                    frame_base + n_in, n_total);
+    if (n_out < 1 || out_first < 0 || out_first + n_out > n_total)
+        return fail(ctx, FB_ERR_ARG, "output frames [%d, %d) are not inside the clip [0, %d)", out_first,
+                    out_first + n_out, n_total);
+    const int M = (window - 1) / 2;
+    const int need_lo = out_first - M < 0 ? 0 : out_first - M;
+    const int need_hi = out_first + n_out + M > n_total ? n_total : out_first + n_out + M;
+    if (need_lo < frame_base || need_hi > frame_base + n_in)
+        return fail(ctx, FB_ERR_ARG,
+                    "output frames [%d, %d) with window %d need input frames [%d, %d); the call holds [%d, %d)",
+                    out_first, out_first + n_out, window, need_lo, need_hi, frame_base, frame_base + n_in);
+    rc = check_range_flags(ctx, p);
+    if (rc) return rc;
+    std::vector<PairDesc> pairs;
+    std::vector<JobDesc> jobs;
+    blend_pairs(n_total, p->patch, window, p->flags, pairs, jobs, out_first, out_first + n_out, frame_base);
+    DeviceGuard dg(ctx->device);
+    return run_pipeline(ctx, guides, n_in, H, W, styles, n_in, pairs, jobs, p, out,
+                        static_cast<cudaStream_t>(stream));
+}
+
+int fb_interpolate_range(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const int32_t* key_idx,
+                         const uint8_t* key_styles, int n_keys, const fb_params* p, int out_first, int n_out,
+                         float* out, void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->err.clear();
+    int rc = check_params(ctx, p, H, W);
+    if (rc) return rc;
+    if (p->flags & (FB_FLAG_BALANCED | FB_FLAG_FAST | FB_FLAG_ACCURATE))
+        return fail(ctx, FB_ERR_ARG, "the blending modes apply to fb_blend_window only");
+    if (N < 1 || N > 65535) return fail(ctx, FB_ERR_ARG, "N must be in [1, 65535], got %d", N);
+    if (!guides || !key_idx || !key_styles || !out)
+        return fail(ctx, FB_ERR_ARG, "guides, key_idx, key_styles and out must be non-NULL");
+    if (n_keys < 1 || n_keys > N)
+        return fail(ctx, FB_ERR_ARG, "n_keys must be in [1, N], got %d", n_keys);
+    for (int m = 0; m < n_keys; ++m) {
+        if (key_idx[m] < 0 || key_idx[m] >= N)
+            return fail(ctx, FB_ERR_ARG, "key_idx[%d] = %d outside [0, %d)", m, key_idx[m], N);
+        if (m > 0 && key_idx[m] <= key_idx[m - 1])
+            return fail(ctx, FB_ERR_ARG, "key_idx must be strictly increasing");
+    }
+    if (n_out < 1 || out_first < 0 || out_first + n_out > N)
+        return fail(ctx, FB_ERR_ARG, "output frames [%d, %d) are not inside the clip [0, %d)", out_first,
+                    out_first + n_out, N);
+    rc = check_range_flags(ctx, p);
+    if (rc) return rc;
+    std::vector<PairDesc> pairs;
+    std::vector<JobDesc> jobs;
+    interp_pairs(N, p->patch, key_idx, n_keys, p->flags, pairs, jobs, out_first, out_first + n_out);
     DeviceGuard dg(ctx->device);
     return run_pipeline(ctx, guides, N, H, W, key_styles, n_keys, pairs, jobs, p, out,
                         static_cast<cudaStream_t>(stream));
