@@ -14,8 +14,12 @@ Prints ONE JSON line (rank 0):
   cpu_baseline  the CPU oracle on a bounded sample of the same workload
 
 --impl reference times the CPU oracle (the only reference: the paper ships no code).
-Multi-GPU (torchrun): every rank blends its own clip (weak scaling, no data-path
-collective); a gloo barrier and a max-reduce bracket the timed region.
+Multi-GPU (torchrun), no data-path collective; a gloo barrier and a max-reduce bracket the
+timed region.  --shard frames (default): one clip of N x 60 frames is split by output
+frame (fb_shard_plan), each rank blending its range from its frames plus the window's
+halo (fb_blend_window_range) -- weak scaling, 60 output frames per GPU; modes whose NNFs
+couple frames across the clip (fast, tracking) and the learned and interpolation
+workloads fall back to replicas.  --shard replicas: every rank blends its own clip.
 """
 from __future__ import annotations
 
@@ -75,6 +79,9 @@ def parse_args(argv=None):
                          "F - 1 styled with the clip's two key styles (small profiling cases)")
     ap.add_argument("--learned-iters", type=int, default=2,
                     help="Alg. 1 iterations after the learned initialiser (learned_512)")
+    ap.add_argument("--shard", choices=("frames", "replicas"), default="frames",
+                    help="N > 1: split one clip by output frame (frames) or give every rank "
+                         "its own clip (replicas)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--cpu-sample-frames", type=int, default=5)
@@ -112,6 +119,15 @@ class RankGroup:
         import torch.distributed as dist
         t = torch.tensor([x], dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum(self, x: float) -> float:
+        if self.world == 1:
+            return x
+        import torch
+        import torch.distributed as dist
+        t = torch.tensor([x], dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
         return float(t.item())
 
     def close(self):
@@ -357,10 +373,25 @@ def run_reference(args):
 # ----------------------------------------------------------------------------------
 # GPU arm
 # ----------------------------------------------------------------------------------
-def iter_ops_per_launch(w: synth.Workload) -> int:
+def iter_ops_per_launch(w: synth.Workload, pairs=None) -> int:
     """Algorithmic byte-pair ops of one Jacobi-iteration launch (levels = 1): every
-    pair, every pixel, 4 propagation + R random-search candidates, 3k^2 byte pairs."""
-    return w.pairs() * w.H * w.W * (4 + w.random_search_radii()) * 3 * w.patch * w.patch
+    pair (all of the workload's, or `pairs`), every pixel, 4 propagation + R
+    random-search candidates, 3k^2 byte pairs."""
+    n = w.pairs() if pairs is None else pairs
+    return n * w.H * w.W * (4 + w.random_search_radii()) * 3 * w.patch * w.patch
+
+
+def shard_inputs(w: synth.Workload, n_total: int, first: int, last: int):
+    """Frames [first, last) of the n_total-frame clip that a frame-sharded run splits:
+    the workload's motion model drawn for the whole clip (same seed on every rank), and
+    styles drawn per frame index, so every rank sees the same clip wherever it is cut."""
+    import numpy as np
+    if w.motion == "shift":   # small clips: draw the whole clip, keep the range
+        g, _ = synth.shift_clip(n_total, w.H, w.W, w.seed)
+        s = synth.colour_matrix_styles(g, w.seed)
+        return np.ascontiguousarray(g[first:last]), np.ascontiguousarray(s[first:last])
+    g, _ = synth.affine_clip(n_total, w.H, w.W, w.seed, frames=(first, last))
+    return g, synth.lut_styles_indexed(g, w.seed, first)
 
 
 def workload_label(name: str, w: synth.Workload, learned_iters: int = 2) -> str:
@@ -445,8 +476,24 @@ def run_gpu(args):
     if args.window and w.mode == "blend":
         import dataclasses
         w = dataclasses.replace(w, window=args.window)
-    g, s = make_inputs(w, shard_seed(w.seed, rank))
-    w, g, s = truncate_interpolation(w, g, s, args.frames)
+    # --shard frames: one clip of world x N frames split by output frame; each rank holds
+    # its range plus the window's halo and blends the range with fb_blend_window_range.
+    shard = None
+    if (world > 1 and args.shard == "frames" and w.mode == "blend"
+            and not (fast or tracking or learned)):
+        import dataclasses
+        n_total = w.N * world
+        shard = fbp.fb_shard_plan(n_total, w.window, world, rank)
+        shard["n_total"] = n_total
+        shard["pairs"] = len(fbp.fb_pair_plan_range(n_total, shard["out_first"], shard["n_out"],
+                                                    window=w.window))
+        g, s = shard_inputs(w, n_total, shard["frame_base"], shard["frame_base"] + shard["n_in"])
+        w_job = dataclasses.replace(w, N=n_total)       # what the whole job computes
+    else:
+        g, s = make_inputs(w, shard_seed(w.seed, rank))
+        w, g, s = truncate_interpolation(w, g, s, args.frames)
+        w_job = None
+    n_out = shard["n_out"] if shard else w.N
     ctx = fbp.Context(local)
     params = fbp.Params.make(w.patch, w.iters, w.levels, 0, w.seed)
     if balanced:
@@ -480,10 +527,13 @@ def run_gpu(args):
                         "net_params": net.n_params, "downscale": net.ds}
     g_d = torch.tensor(g, device="cuda")
     s_d = torch.tensor(s, device="cuda")
-    out = torch.empty((w.N, w.H, w.W, 3), dtype=torch.float32, device="cuda")
+    out = torch.empty((n_out, w.H, w.W, 3), dtype=torch.float32, device="cuda")
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device="cuda")
 
     def step(gg, ss, oo):
+        if shard:
+            return fbp.fb_blend_window_range(ctx, gg, ss, w.window, params, shard["n_total"],
+                                             shard["frame_base"], shard["out_first"], n_out, out=oo)
         if w.mode == "blend":
             return fbp.fb_blend_window(ctx, gg, ss, w.window, params, out=oo)
         return fbp.fb_interpolate(ctx, gg, list(w.keys), ss, params, out=oo)
@@ -512,6 +562,8 @@ def run_gpu(args):
     ctx.profile(False)
     step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
     total_ms = grp.max(sum(step_ms))
+    # whole-job frames/s: every rank's output frames over the slowest rank's time (a
+    # frame-sharded job outputs its world x N-frame clip once per step)
     value = aggregate(w.N, args.steps, world, total_ms)
     clocks = clk.summary()
 
@@ -520,7 +572,7 @@ def run_gpu(args):
     if not args.no_e2e:
         g_h = torch.tensor(g).pin_memory()
         s_h = torch.tensor(s).pin_memory()
-        o_h = torch.empty((w.N, w.H, w.W, 3), dtype=torch.float32).pin_memory()
+        o_h = torch.empty((n_out, w.H, w.W, 3), dtype=torch.float32).pin_memory()
         step(g_h, s_h, o_h)                     # warm (staging buffers)
         grp.barrier()
         torch.cuda.synchronize()
@@ -528,9 +580,10 @@ def run_gpu(args):
         for _ in range(args.steps):
             step(g_h, s_h, o_h)                 # synchronous: returns with o_h filled
         t_e2e = grp.max(time.perf_counter() - t0)
+        # copies of the whole job: every rank's inputs in and its output frames out
         e2e = {"value": world * w.N * args.steps / t_e2e, "unit": "frames/s",
-               "h2d_bytes_per_step": int(g_h.numel() + s_h.numel()),
-               "d2h_bytes_per_step": int(o_h.numel() * 4)}
+               "h2d_bytes_per_step": int(grp.sum(g_h.numel() + s_h.numel())),
+               "d2h_bytes_per_step": int(grp.sum(o_h.numel() * 4))}
 
     if learned:
         # NNF energy (mean Eq. 1 error of all 784 final fields) against the plain search.
@@ -560,7 +613,9 @@ def run_gpu(args):
     rate, _ = ctx.probe_dp4a()
     iter_ms, iter_n = prof["iter"]
     kernel_total_ms = sum(v[0] for v in prof.values())
-    ops = iter_ops_per_launch(w) if w.levels == 1 else None  # same per launch with learned init
+    # per launch of this rank (a frame shard launches its own range's pairs)
+    ops = (iter_ops_per_launch(w, shard["pairs"] if shard else None)
+           if w.levels == 1 else None)  # same per launch with learned init
     if ops and (balanced or accurate):
         ops *= 2   # each candidate compares a guide patch and a style patch
     if ops and fast:
@@ -607,7 +662,8 @@ def run_gpu(args):
                                if probe_per_clk else "derived"),
                 "avg_launch_ms": iter_ms / iter_n, "launches": iter_n,
                 "share_of_kernel_time": iter_ms / kernel_total_ms if kernel_total_ms else None,
-                "candidate_evals_per_s": (w.candidate_evals() * (fast_info["nnfs"] / w.pairs() if fast else 1)
+                "candidate_evals_per_s": (w_job.candidate_evals() / world if shard else
+                                          w.candidate_evals() * (fast_info["nnfs"] / w.pairs() if fast else 1)
                                           + (tracking_neighbour_refs(w) * w.H * w.W * w.iters
                                              if tracking else 0)
                                           if not learned else
@@ -622,11 +678,13 @@ def run_gpu(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
         "config": {"workload": workload_label(args.workload, w, args.learned_iters),
-                   "frames": w.N, "height": w.H, "width": w.W,
+                   "frames": w_job.N if shard else w.N, "height": w.H, "width": w.W,
                    "patch": w.patch, "window": w.window,
                    "iters": w.iters if not learned else args.learned_iters, "levels": w.levels,
-                   "nnfs_per_step": fast_info["nnfs"] if fast else w.pairs(),
-                   "candidate_evals_per_step": (w.candidate_evals()
+                   "nnfs_per_step": (w_job.pairs() if shard else
+                                     fast_info["nnfs"] if fast else w.pairs()),
+                   "candidate_evals_per_step": (w_job.candidate_evals() if shard else
+                                                w.candidate_evals()
                                                 + (tracking_neighbour_refs(w) * w.H * w.W * w.iters
                                                    if tracking else 0) if not learned else
                                                 w.pairs() * w.H * w.W * (1 + args.learned_iters *
@@ -634,7 +692,10 @@ def run_gpu(args):
                    "learned_init": learned_info,
                    "fast_mode": fast_info,
                    "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
-                   "parallelism": f"{world} independent clip(s), one per GPU"},
+                   "parallelism": (f"one {w_job.N}-frame clip split by output frame over {world} "
+                                   f"GPUs ({w.N} per GPU, {w.window // 2}-frame input halo, "
+                                   "fb_blend_window_range; no data-path collective)" if shard
+                                   else f"{world} independent clip(s), one per GPU")},
         "roofline": roof,
         "e2e": e2e,
         "gpu_launches": launches,

@@ -125,8 +125,14 @@ def affine_motion(N: int, rng: np.random.Generator, max_rot_step: float = 2.0,
     return AffineMotion(th, sh)
 
 
-def affine_clip(N: int, H: int, W: int, seed: int):
-    """Guides (N,H,W,3) uint8 under smooth random affine motion, and the motion."""
+def affine_clip(N: int, H: int, W: int, seed: int, frames=None):
+    """Guides (N,H,W,3) uint8 under smooth random affine motion, and the motion.
+    frames=(a, b): only clip frames [a, b) of the same N-frame clip, bit-identical to
+    those frames of the whole clip (the motion and texture are drawn for the whole clip
+    first), returned as (b - a,H,W,3)."""
+    a, b = (0, N) if frames is None else frames
+    if not 0 <= a < b <= N:
+        raise ValueError(f"frames {frames} outside [0, {N})")
     rng = np.random.default_rng(seed)
     mot = affine_motion(N, rng)
     half_diag = 0.5 * math.hypot(H, W)
@@ -135,10 +141,10 @@ def affine_clip(N: int, H: int, W: int, seed: int):
     tex = noise_texture(TH, TW, rng, periods=(48.0, 20.0, 9.0, 4.0), jitter=5)
     yy, xx = np.meshgrid(np.arange(H, dtype=np.float64) - (H - 1) / 2.0,
                          np.arange(W, dtype=np.float64) - (W - 1) / 2.0, indexing="ij")
-    g = np.empty((N, H, W, 3), np.uint8)
-    for t in range(N):
-        a = math.radians(mot.theta_deg[t])
-        ca, sa = math.cos(a), math.sin(a)
+    g = np.empty((b - a, H, W, 3), np.uint8)
+    for t in range(a, b):
+        ang = math.radians(mot.theta_deg[t])
+        ca, sa = math.cos(ang), math.sin(ang)
         sy = ca * yy - sa * xx + mot.shift[t, 0] + (TH - 1) / 2.0
         sx = sa * yy + ca * xx + mot.shift[t, 1] + (TW - 1) / 2.0
         y0 = np.clip(np.floor(sy).astype(np.int64), 0, TH - 2)
@@ -147,7 +153,7 @@ def affine_clip(N: int, H: int, W: int, seed: int):
         fx = np.clip(sx - x0, 0.0, 1.0)[..., None].astype(np.float32)
         v = (tex[y0, x0] * (1 - fy) * (1 - fx) + tex[y0, x0 + 1] * (1 - fy) * fx
              + tex[y0 + 1, x0] * fy * (1 - fx) + tex[y0 + 1, x0 + 1] * fy * fx)
-        g[t] = np.clip(np.rint(v), 0, 255).astype(np.uint8)
+        g[t - a] = np.clip(np.rint(v), 0, 255).astype(np.uint8)
     mot.margin = m
     return g, mot
 
@@ -181,6 +187,21 @@ def lut_styles(guides: np.ndarray, seed: int, sigma: float = 6.0) -> np.ndarray:
     rng = np.random.default_rng(seed ^ 0x1C7)
     out = np.empty_like(guides)
     for t in range(guides.shape[0]):
+        v = np.empty(guides.shape[1:], np.float32)
+        for ch in range(3):
+            v[..., ch] = random_lut(rng)[guides[t, ..., ch]]
+        v += rng.normal(0.0, sigma, size=v.shape).astype(np.float32)
+        out[t] = np.clip(np.rint(v), 0, 255).astype(np.uint8)
+    return out
+
+
+def lut_styles_indexed(guides: np.ndarray, seed: int, first: int = 0, sigma: float = 6.0) -> np.ndarray:
+    """The LUT style recipe with one generator per clip frame index (first + t): any range
+    of frames of a long clip is styled on its own, identically wherever it is cut (a clip
+    split over several processes)."""
+    out = np.empty_like(guides)
+    for t in range(guides.shape[0]):
+        rng = np.random.default_rng([seed ^ 0x1C7, first + t])
         v = np.empty(guides.shape[1:], np.float32)
         for ch in range(3):
             v[..., ch] = random_lut(rng)[guides[t, ..., ch]]

@@ -1,9 +1,10 @@
 """The N > 1 bench path on CPU: two gloo ranks (world size 2, 127.0.0.1).
 
-The hot path shards by clip (every rank blends its own clips, no data-path exchange), so
-what runs across ranks is the bench's own plumbing: the barriers around the timed region,
-the max-over-ranks timing, the whole-job aggregate, per-rank inputs, and the reference arm
-that only rank 0 runs.
+The hot path shards by output frame of one clip (each rank blends its range from its
+frames plus the window's halo) or by clip (replicas); neither exchanges data, so what runs
+across ranks is the bench's own plumbing: the barriers around the timed region, the
+max-over-ranks timing, the whole-job aggregate, per-rank inputs (the same clip wherever it
+is cut), and the reference arm that only rank 0 runs.
 """
 import json
 import os
@@ -90,3 +91,43 @@ def test_window_override_keeps_the_named_clip():
     g0, s0 = bench.make_inputs(w, w.seed)
     g1, s1 = bench.make_inputs(dataclasses.replace(w, window=5), w.seed)
     assert np.array_equal(g0, g1) and np.array_equal(s0, s1)
+
+
+def _shard_rank_main(rank, world, port, out_dir):
+    import dataclasses
+    import json
+
+    import paper_2311_09265_b300 as fbp
+    os.environ.update({"RANK": str(rank), "WORLD_SIZE": str(world), "LOCAL_RANK": str(rank),
+                       "MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
+    grp = bench.RankGroup()
+    w = dataclasses.replace(synth.WORKLOADS["blend_512"], N=8, H=48, W=64)
+    n_total = w.N * world
+    pl = fbp.fb_shard_plan(n_total, w.window, world, rank)
+    g, s = bench.shard_inputs(w, n_total, pl["frame_base"], pl["frame_base"] + pl["n_in"])
+    total_in = grp.sum(g.nbytes + s.nbytes)
+    grp.barrier()
+    grp.close()
+    np.savez(os.path.join(out_dir, f"shard{rank}.npz"), g=g, s=s, total_in=total_in)
+    with open(os.path.join(out_dir, f"shard{rank}.json"), "w") as f:
+        json.dump(pl, f)
+
+
+def test_frame_shards_see_one_clip(tmp_path):
+    """bench.py --shard frames: two gloo ranks plan their output ranges of one 16-frame
+    clip (window 15) and draw only their own input frames, halo included; the frames both
+    ranks hold are identical, and every rank's frames are those of the whole clip."""
+    import dataclasses
+    import json
+    world = 2
+    mp.start_processes(_shard_rank_main, args=(world, free_port(), str(tmp_path)), nprocs=world,
+                       join=True, start_method="spawn")
+    pl = [json.load(open(tmp_path / f"shard{r}.json")) for r in range(world)]
+    d = [np.load(tmp_path / f"shard{r}.npz") for r in range(world)]
+    w = dataclasses.replace(synth.WORKLOADS["blend_512"], N=8, H=48, W=64)
+    g_all, s_all = bench.shard_inputs(w, 16, 0, 16)
+    for r in range(world):
+        a, n = pl[r]["frame_base"], pl[r]["n_in"]
+        assert np.array_equal(d[r]["g"], g_all[a:a + n]) and np.array_equal(d[r]["s"], s_all[a:a + n])
+    assert pl[0]["out_first"] + pl[0]["n_out"] == pl[1]["out_first"]
+    assert float(d[0]["total_in"]) == d[0]["g"].nbytes + d[0]["s"].nbytes + d[1]["g"].nbytes + d[1]["s"].nbytes
