@@ -481,8 +481,21 @@ int fb_ctx_set_initnet(fb_ctx *ctx, fb_initnet *net);
 int fb_initnet_targets(const int32_t *nnf, int n, int H, int W, int downscale, float *target,
                        float *weight, void *stream);
 
-/* FB_ERR_TIMEOUT if a tensor-core kernel of this net hit its bounded wait. */
+/* FB_ERR_TIMEOUT if a tensor-core kernel of this net hit its bounded wait since the last
+ * call (the flag is then cleared), else FB_OK.  Synchronous.  Outputs of the pass that
+ * timed out are undefined; the net stays usable. */
 int fb_initnet_status(fb_initnet *net);
+
+/* Diagnostics (failure detection): the number of polls a tensor-core kernel's progress
+ * wait (operands landed, a pipeline stage free, the accumulator complete) makes on the
+ * current device before the CTA gives up, drains the MMAs it committed and the copies it
+ * issued (those waits keep the full limit), skips its epilogue, releases its tensor memory
+ * and raises the net's timeout flag (fb_initnet_status).  polls = 0 makes every progress
+ * wait give up at once, so a forward or training pass reports FB_ERR_TIMEOUT without any
+ * fault; polls < 0 restores the default (2^26, far beyond any real wait).  Waits for the
+ * device before and after; call it with no other work of this library in flight.  Not
+ * part of the method. */
+int fb_debug_set_wait_limit(int64_t polls);
 
 /* Single 3x3 convolution layer (zero padding 1) on the tensor cores, for tests:
  *   x   n x H x W x Cin bf16 (uint16 storage), w Cout x 3 x 3 x Cin bf16, bias Cout f32,
@@ -527,9 +540,10 @@ int fb_conv_gemm_path(int mode, uint64_t *tma_launches);
  *   pyramid level, four H x W words per NNF, the pair tables) exceeds the array is
  *   rejected with FB_ERR_ARG and a message giving both sizes; so is one with more than
  *   65535 NNFs.  Errors are reported through fb_last_error(NULL).
- *   Set-up: the first call on each device looks up the array's device address
- *   (cudaGetSymbolAddress) with that device current; make that first call before any
- *   stream capture.
+ *   Set-up: every call looks up the array's device address on the current device
+ *   (cudaGetSymbolAddress; a host-side lookup, so the address is never stale, even after
+ *   a device reset); the first call on a device also loads the library's device code
+ *   there, so make that first call before any stream capture.
  *   Sharing: every call on a device uses the same array and leaves its contents
  *   behind; nothing in it needs to start at zero (every word is written before it is
  *   read).  Calls whose work overlaps on the GPU (different streams, or host threads

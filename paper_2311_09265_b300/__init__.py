@@ -34,7 +34,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_initnet_get_optimizer", "fb_initnet_set_optimizer",
                     "fb_initnet_train_step", "fb_initnet_status", "fb_conv3x3_forward",
                     "fb_conv3x3_backward", "fb_ctx_set_initnet", "fb_ctx_energy",
-                    "fb_initnet_targets")
+                    "fb_initnet_targets", "fb_debug_set_wait_limit")
 
 FB_FLAG_LEARNED_INIT = 0x1
 FB_FLAG_REPORT_ENERGY = 0x2
@@ -180,6 +180,8 @@ def lib() -> ctypes.CDLL:
         L.fb_initnet_train_step.argtypes = [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_float,
                                             ctypes.c_float, _vp, _vp]
         L.fb_initnet_status.argtypes = [_vp]
+        L.fb_debug_set_wait_limit.argtypes = [ctypes.c_int64]
+        L.fb_debug_set_wait_limit.restype = ctypes.c_int
         L.fb_conv3x3_forward.argtypes = [_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, _vp, _vp, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, _vp, _vp, _vp, _vp]
@@ -285,6 +287,14 @@ def fb_debug_candidates_considered(reset: bool = False) -> int:
     if rc != FB_OK:
         raise FastBlendError(rc, "fb_debug_candidates_considered")
     return int(v.value)
+
+
+def fb_debug_set_wait_limit(polls: int) -> None:
+    """Polls of the tensor-core kernels' progress waits on the current device (0: give up
+    at once; < 0: the default); for exercising the timeout path."""
+    rc = lib().fb_debug_set_wait_limit(int(polls))
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_debug_set_wait_limit")
 
 
 def fb_pair_tag(j: int, i: int) -> int:

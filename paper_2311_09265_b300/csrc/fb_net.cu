@@ -848,7 +848,15 @@ int fb_initnet_status(fb_initnet* net) {
     if (!net) return FB_ERR_ARG;
     int s = 0;
     NET_CUDA(net, cudaMemcpy(&s, net->status, 4, cudaMemcpyDeviceToHost));
+    if (s) NET_CUDA(net, cudaMemset(net->status, 0, 4));  // reported once, then cleared
     return s ? FB_ERR_TIMEOUT : FB_OK;
+}
+
+int fb_debug_set_wait_limit(int64_t polls) {
+    const long v = polls >= 0 ? static_cast<long>(polls) : fb::tc::kWaitLimit;
+    if (cudaDeviceSynchronize() != cudaSuccess) return FB_ERR_CUDA;
+    if (cudaMemcpyToSymbol(fb::tc::g_progress_wait_limit, &v, sizeof(v)) != cudaSuccess) return FB_ERR_CUDA;
+    return cudaDeviceSynchronize() == cudaSuccess ? FB_OK : FB_ERR_CUDA;
 }
 
 int fb_conv_gemm_path(int mode, uint64_t* tma_launches) {

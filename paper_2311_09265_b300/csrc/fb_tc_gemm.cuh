@@ -27,6 +27,12 @@ constexpr int BK = 64;              // K per stage: 8 core-matrix columns, 4 MMA
 constexpr int LBO = 128;            // bytes between core matrices along K
 constexpr int SBO = 1024;           // bytes between 8-row groups (BK / 8 * 128)
 constexpr long kWaitLimit = 1L << 26;
+// Polls a PROGRESS wait (one that gates further work: operands landed, a stage free, the
+// accumulator complete) makes before the kernel gives up and reports a timeout.  Host code
+// may lower it (fb_debug_set_wait_limit) to exercise the timeout path; DRAIN waits (for
+// MMAs already committed and copies already issued, before the CTA releases TMEM and
+// shared memory) always use kWaitLimit.
+static __device__ long g_progress_wait_limit = kWaitLimit;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -55,9 +61,9 @@ __device__ __forceinline__ void mbar_init(uint64_t* bar) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(bar)));
 }
 
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long limit = kWaitLimit) {
     uint32_t done = 0;
-    for (long it = 0; it < kWaitLimit && !done; ++it) {
+    for (long it = 0; it < limit && !done; ++it) {
         asm volatile(
             "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
             "selp.u32 %0, 1, 0, p;\n}"
@@ -65,6 +71,10 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
             : "r"(smem_u32(bar)), "r"(parity));
     }
     return done != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait_progress(uint64_t* bar, uint32_t parity) {
+    return mbar_wait(bar, parity, *static_cast<volatile long*>(&g_progress_wait_limit));
 }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
@@ -141,12 +151,13 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(Gather gather, Epi epi, in
 
     bool ok = true;
     int issued = 0;
+    int last_commit = -1;  // thread 0: last chunk (relative) whose MMAs it committed
     for (int c = c_begin; c < c_end; ++c) {
         const int s = (c - c_begin) & 1;
         const int use = (c - c_begin) >> 1;  // how many times stage s was used before
         unsigned char* sa = smem + s * STAGE;
         unsigned char* sb = sa + A_BYTES;
-        if (use > 0 && ok) ok = mbar_wait(&bars[s], (use - 1) & 1);  // MMAs of that stage done
+        if (use > 0 && ok) ok = mbar_wait_progress(&bars[s], (use - 1) & 1);  // MMAs of that stage done
         gather.load(sa, sb, c * BK, m0, n0);
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
@@ -158,14 +169,19 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(Gather gather, Epi epi, in
                          idesc, (c > c_begin || j > 0) ? 1u : 0u);
             }
             mma_commit(&bars[s]);
+            last_commit = c - c_begin;
         }
         ++issued;
     }
     if (issued > 0 && ok) {
         const int last = issued - 1;
-        ok = mbar_wait(&bars[last & 1], (last >> 1) & 1);
+        ok = mbar_wait_progress(&bars[last & 1], (last >> 1) & 1);
     }
     if (!ok && lane == 0) atomicExch(status, 1);
+    // After a timeout, let the MMAs already committed finish before TMEM is released (they
+    // complete in issue order, so the last commit's phase covers them all).
+    if (!ok && threadIdx.x == 0 && last_commit >= 0)
+        mbar_wait(&bars[last_commit & 1], (last_commit >> 1) & 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok && issued > 0) {
         const int row = m0 + warp * 32 + lane;
@@ -258,6 +274,7 @@ __global__ void __launch_bounds__(128) tc_gemm_async_kernel(Gather gather, Epi e
         cp_async_commit();
     }
     bool ok = true;
+    int last_commit = -1;  // thread 0: last chunk whose MMAs it committed
     for (int i = 0; i < n_chunks; ++i) {
         const int s = i % S;
         cp_async_wait<LA - 1>();  // this thread's copies of chunk i have landed
@@ -271,11 +288,12 @@ __global__ void __launch_bounds__(128) tc_gemm_async_kernel(Gather gather, Epi e
                 mma_bf16(tmem, smem_desc(sa + j * 2 * LBO), smem_desc(sb + j * 2 * LBO), idesc,
                          (i > 0 || j > 0) ? 1u : 0u);
             mma_commit(&bars[s]);
+            last_commit = i;
         }
         const int nxt = i + LA;
         const int prev = nxt - S;  // the chunk that last used nxt's stage
         if (nxt < n_chunks) {
-            if (prev >= 0 && ok) ok = mbar_wait(&bars[prev % S], (prev / S) & 1);
+            if (prev >= 0 && ok) ok = mbar_wait_progress(&bars[prev % S], (prev / S) & 1);
             if (ok) {
                 const uint32_t sa = s0 + (nxt % S) * STAGE;
                 gather.load_async(gst, sa, sa + A_BYTES, nxt, n0);
@@ -283,9 +301,12 @@ __global__ void __launch_bounds__(128) tc_gemm_async_kernel(Gather gather, Epi e
         }
         cp_async_commit();
     }
-    cp_async_wait<0>();
-    if (n_chunks > 0 && ok) ok = mbar_wait(&bars[(n_chunks - 1) % S], ((n_chunks - 1) / S) & 1);
+    cp_async_wait<0>();   // no copy of this thread is in flight past this point
+    if (n_chunks > 0 && ok) ok = mbar_wait_progress(&bars[(n_chunks - 1) % S], ((n_chunks - 1) / S) & 1);
     if (!ok && lane == 0) atomicExch(status, 1);
+    // After a timeout, let the MMAs already committed finish before TMEM is released.
+    if (!ok && threadIdx.x == 0 && last_commit >= 0)
+        mbar_wait(&bars[last_commit % S], (last_commit / S) & 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (ok && n_chunks > 0) {
         const int row = m0 + warp * 32 + lane;
