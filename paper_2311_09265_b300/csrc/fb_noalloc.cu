@@ -1,5 +1,5 @@
-// fb_noalloc.cu -- fb_blend_window_noalloc: the Eq. 2 window blend for callers that
-// cannot allocate device memory themselves.
+// fb_noalloc.cu -- fb_blend_window_noalloc: fb_blend_window without a context or any
+// device allocation, for callers that cannot allocate device memory themselves.
 //
 // Some callers may not call cudaMalloc (or any allocator) at the point where they
 // blend: code running inside a host callback or a stream-ordered pipeline that must
@@ -10,7 +10,6 @@
 // library holds until the process exits.  The caller still passes its own inputs and
 // outputs.
 #include <cstdio>
-#include <mutex>
 
 #include "fb.h"
 #include "fb_internal.h"
@@ -32,10 +31,6 @@ static_assert(kStaticScratchBytes == FB_NOALLOC_SCRATCH_BYTES, "header and file 
 // array; its device address comes from cudaGetSymbolAddress (scratch_address below).
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
-constexpr int kMaxDevices = 128;
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {};
-
 int report(int status, const char* fmt, long long a = 0, long long b = 0) {
     char buf[256];
     std::snprintf(buf, sizeof buf, fmt, a, b);
@@ -43,22 +38,19 @@ int report(int status, const char* fmt, long long a = 0, long long b = 0) {
     return status;
 }
 
-// Set-up, once per device, with that device current: the device address of the
-// static scratch array.
-int scratch_address(int device, unsigned char** out) {
-    if (device < 0 || device >= kMaxDevices) return report(FB_ERR_UNSUPPORTED, "device %lld", device);
-    std::lock_guard<std::mutex> lock(g_setup_mu);
-    if (!g_scratch_addr[device]) {
-        void* p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
-        if (e != cudaSuccess || p == nullptr) {
-            cudaGetLastError();
-            return report(FB_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed (%lld)",
-                          static_cast<long long>(e));
-        }
-        g_scratch_addr[device] = p;
+// The device address of the static scratch array on the current device, looked up on
+// every call: a host-side lookup once the library's device code is loaded on the device
+// (the first call on a device loads it), and never stale, even after the device's
+// primary context was reset and the array moved.
+int scratch_address(unsigned char** out) {
+    void* p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_static_scratch);
+    if (e != cudaSuccess || p == nullptr) {
+        cudaGetLastError();
+        return report(FB_ERR_CUDA, "cudaGetSymbolAddress of the static scratch failed (%lld)",
+                      static_cast<long long>(e));
     }
-    *out = static_cast<unsigned char*>(g_scratch_addr[device]);
+    *out = static_cast<unsigned char*>(p);
     return FB_OK;
 }
 
@@ -90,7 +82,7 @@ __global__ void blend_tables_kernel(int N, int M, int k, PairDesc* __restrict__ 
         pd.tag = (static_cast<uint32_t>(j) << 16) | static_cast<uint32_t>(i);
         pd.style = j;
         pd.weight = 1u;
-        pd.pad[0] = pd.pad[1] = pd.pad[2] = 0;
+        pd.pad[0] = pd.pad[1] = pd.pad[2] = -1;  // no chain neighbours, no partner
         pairs[n++] = pd;
     }
 }
@@ -111,6 +103,7 @@ bool on_device(const void* p, int device) {
 extern "C" int fb_blend_window_noalloc(const uint8_t* guides, const uint8_t* styles, int N, int H,
                                        int W, int window, const fb_params* p, float* out,
                                        void* stream) {
+    fb::set_null_ctx_error("");  // a success leaves no message behind
     if (!p) return report(FB_ERR_ARG, "params is NULL");
     if (p->patch < 3 || p->patch > 9 || (p->patch & 1) == 0)
         return report(FB_ERR_ARG, "patch must be odd in [3, 9], got %lld", p->patch);
@@ -165,7 +158,7 @@ extern "C" int fb_blend_window_noalloc(const uint8_t* guides, const uint8_t* sty
                       static_cast<long long>(off), static_cast<long long>(kStaticScratchBytes));
 
     unsigned char* base = nullptr;
-    int rc = scratch_address(device, &base);
+    int rc = scratch_address(&base);
     if (rc) return rc;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     auto u32 = [&](size_t o) { return reinterpret_cast<uint32_t*>(base + o); };
