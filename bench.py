@@ -611,6 +611,8 @@ def run_gpu(args):
 
     # ---- roofline of the dominant kernel ----
     rate, _ = ctx.probe_dp4a()
+    # the ALU roofline of the instruction sequence the kernels actually issue (live probe)
+    mix_rate = ctx.probe_ssd_mix(w.patch)[0] if w.patch in (5, 7) else None
     iter_ms, iter_n = prof["iter"]
     kernel_total_ms = sum(v[0] for v in prof.values())
     # per launch of this rank (a frame shard launches its own range's pairs)
@@ -660,6 +662,13 @@ def run_gpu(args):
                                f"{SM_MAX_MHZ_NOMINAL:.0f} MHz x 4 byte pairs (derived; the live "
                                f"register-only probe measured {probe_per_clk:.1f} dp4a/clk/SM)"
                                if probe_per_clk else "derived"),
+                "peak_chosen_mix": mix_rate / 1e12 if mix_rate else None,
+                "frac_chosen_mix": achieved / (mix_rate / 1e12) if mix_rate else None,
+                "chosen_mix_basis": (f"register-only probe of the k = {w.patch} kernels' Eq. 1 "
+                                     "sequence (" + ("3 dp4a per word, 20 words" if w.patch == 5 else
+                                                     "2 dp4a per word, |t|^2 held, 42 words") +
+                                     " per candidate, accumulate + early-exit compare per slot), "
+                                     "measured live" if mix_rate else None),
                 "avg_launch_ms": iter_ms / iter_n, "launches": iter_n,
                 "share_of_kernel_time": iter_ms / kernel_total_ms if kernel_total_ms else None,
                 "candidate_evals_per_s": (w_job.candidate_evals() / world if shard else

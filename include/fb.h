@@ -178,6 +178,17 @@ int fb_ctx_profile_read(fb_ctx *ctx, double *ms, uint64_t *launches);
  * kernel's duration.  Synchronous.  Not part of the method. */
 int fb_probe_dp4a(fb_ctx *ctx, double *dp4a_per_s, double *ms);
 
+/* Diagnostics: measures the device's throughput of the instruction sequence the
+ * patch-match kernels evaluate Eq. 1 with, on register operands (no memory traffic) on
+ * every SM: for patch = 5 the five 15-byte patch rows as two 32-byte slots and one 16-byte
+ * half, three dp4a per 4-byte word (<s, t>, |s|^2, |t|^2); for patch = 7 seven 24-byte
+ * rows, two dp4a per word with |t|^2 held; per slot or row the accumulate and the
+ * early-exit compare.  Writes Eq. 1 byte pairs per second (3k^2 per candidate) and the
+ * kernel's duration.  This is the ALU roofline of the chosen sequence, below the dp4a-only
+ * bound of fb_probe_dp4a (k = 5: 60 dp4a for 75 byte pairs instead of 19).  FB_ERR_ARG for
+ * other patch sizes.  Synchronous.  Not part of the method. */
+int fb_probe_ssd_mix(fb_ctx *ctx, int patch, double *byte_pairs_per_s, double *ms);
+
 /* Diagnostics of debug builds: libfb_debug.so (compiled with FB_COUNT_EVALS) counts,
  * in a device-global counter, every candidate the per-call NNF kernels consider -- one
  * per pixel and level for the initial match, then per pixel and iteration one per

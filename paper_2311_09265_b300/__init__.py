@@ -22,7 +22,7 @@ FB_OK, FB_ERR_ARG, FB_ERR_CUDA, FB_ERR_OOM, FB_ERR_TIMEOUT, FB_ERR_UNSUPPORTED =
 
 HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_error",
                     "fb_status_string", "fb_ctx_launches", "fb_ctx_scratch_bytes",
-                    "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a",
+                    "fb_ctx_profile", "fb_ctx_profile_read", "fb_probe_dp4a", "fb_probe_ssd_mix",
                     "fb_debug_candidates_considered", "fb_pair_tag",
                     "fb_nnf", "fb_nnf_balanced", "fb_nnf_segment", "fb_remap", "fb_blend_window", "fb_interpolate",
                     "fb_blend_window_range", "fb_interpolate_range", "fb_shard_plan", "fb_pair_plan_range",
@@ -123,6 +123,9 @@ def lib() -> ctypes.CDLL:
         L.fb_probe_dp4a.argtypes = [_vp, ctypes.POINTER(ctypes.c_double),
                                     ctypes.POINTER(ctypes.c_double)]
         L.fb_probe_dp4a.restype = ctypes.c_int
+        L.fb_probe_ssd_mix.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
+                                       ctypes.POINTER(ctypes.c_double)]
+        L.fb_probe_ssd_mix.restype = ctypes.c_int
         L.fb_debug_candidates_considered.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
         L.fb_debug_candidates_considered.restype = ctypes.c_int
         L.fb_pair_tag.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -355,6 +358,13 @@ class Context:
         """(dp4a instructions per second, kernel ms) of a register-only probe."""
         rate, ms = ctypes.c_double(), ctypes.c_double()
         self.check(lib().fb_probe_dp4a(self._h, ctypes.byref(rate), ctypes.byref(ms)))
+        return rate.value, ms.value
+
+    def probe_ssd_mix(self, patch: int = 5):
+        """(Eq. 1 byte pairs per second, kernel ms) of a register-only probe of the patch-k
+        kernels' per-candidate instruction sequence (k = 5 or 7)."""
+        rate, ms = ctypes.c_double(), ctypes.c_double()
+        self.check(lib().fb_probe_ssd_mix(self._h, patch, ctypes.byref(rate), ctypes.byref(ms)))
         return rate.value, ms.value
 
     def set_initnet(self, net) -> None:

@@ -1713,6 +1713,36 @@ int fb_probe_dp4a(fb_ctx* ctx, double* dp4a_per_s, double* ms) {
     return FB_OK;
 }
 
+int fb_probe_ssd_mix(fb_ctx* ctx, int patch, double* byte_pairs_per_s, double* ms) {
+    if (!ctx || !byte_pairs_per_s || !ms) return fail(ctx, FB_ERR_ARG, "NULL argument");
+    if (patch != 5 && patch != 7) return fail(ctx, FB_ERR_ARG, "patch must be 5 or 7, got %d", patch);
+    DeviceGuard dg(ctx->device);
+    int sms = 0;
+    FB_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int blocks = sms * 8, iters = 1 << 12;
+    Carver measure(nullptr);
+    measure.take<uint32_t>(blocks);
+    int rc = ensure_arena(ctx, measure.off);
+    if (rc) return rc;
+    cudaEvent_t a = nullptr, b = nullptr;
+    FB_CUDA(ctx, cudaEventCreate(&a));
+    FB_CUDA(ctx, cudaEventCreate(&b));
+    uint32_t* sink = reinterpret_cast<uint32_t*>(ctx->arena);
+    FB_CUDA(ctx, fb::launch_ssd_mix_probe(patch, blocks, iters / 16, sink, nullptr));  // warm-up
+    FB_CUDA(ctx, cudaEventRecord(a, nullptr));
+    FB_CUDA(ctx, fb::launch_ssd_mix_probe(patch, blocks, iters, sink, nullptr));
+    FB_CUDA(ctx, cudaEventRecord(b, nullptr));
+    FB_CUDA(ctx, cudaEventSynchronize(b));
+    float t = 0.f;
+    FB_CUDA(ctx, cudaEventElapsedTime(&t, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->launches += 2;
+    *ms = t;
+    *byte_pairs_per_s = static_cast<double>(blocks) * 256.0 * iters * 3.0 * patch * patch / (t * 1e-3);
+    return FB_OK;
+}
+
 uint32_t fb_pair_tag(int j, int i) {
     return (static_cast<uint32_t>(j) << 16) | static_cast<uint32_t>(i & 0xFFFF);
 }

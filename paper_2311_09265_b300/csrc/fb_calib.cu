@@ -25,7 +25,86 @@ __global__ void __launch_bounds__(256) dp4a_probe_kernel(uint32_t seed, int iter
     if (r == 0x12345678u) sink[blockIdx.x] = r;  // practically never taken; defeats DCE
 }
 
+// The instruction sequences the patch-match kernels evaluate Eq. 1 with, on register
+// operands.  k = 5 (paired rows): per candidate two 8-word slots and one 4-word half slot
+// (the five 15-byte patch rows, zero padded), each word with three dp4a (<s, t>, |s|^2,
+// |t|^2), each slot closed by acc += |s|^2 + |t|^2 - 2 <s, t> and the early-exit compare
+// against the incumbent's error.  k = 7: seven 6-word rows, two dp4a per word (<s, t>,
+// |s|^2) and |t_a|^2 held, each row closed the same way.  The compare is never taken
+// here (the bound is the kernel argument); dp4a is issued through volatile asm so that no
+// product is hoisted or folded: every candidate pays the whole sequence, as in the
+// kernels.  3k^2 byte pairs of Eq. 1 per candidate.
+__device__ __forceinline__ uint32_t dp4a_kept(uint32_t a, uint32_t b, uint32_t c) {
+    uint32_t d;
+    asm volatile("dp4a.u32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+
+template <int K>
+__global__ void __launch_bounds__(256) ssd_mix_probe_kernel(uint32_t seed, uint32_t bound, int iters,
+                                                            uint32_t* __restrict__ sink) {
+    constexpr int NWORDS = K == 5 ? 20 : 42;
+    uint32_t t[NWORDS], s[NWORDS];
+#pragma unroll
+    for (int w = 0; w < NWORDS; ++w) {
+        t[w] = (seed * static_cast<uint32_t>(w + 1)) ^ (threadIdx.x * 0x9E3779B9u) ^ blockIdx.x;
+        s[w] = t[w] + 0x01010101u * static_cast<uint32_t>(w & 3);
+    }
+    uint32_t row_e[7];
+    if constexpr (K == 7) {
+#pragma unroll
+        for (int a = 0; a < 7; ++a) {
+            row_e[a] = 0;
+#pragma unroll
+            for (int w = 0; w < 6; ++w) row_e[a] = __dp4a(t[6 * a + w], t[6 * a + w], row_e[a]);
+        }
+    }
+    uint32_t total = 0;
+    for (int i = 0; i < iters; ++i) {
+        uint32_t acc = 0;
+        if constexpr (K == 5) {
+#pragma unroll
+            for (int slot = 0; slot < 3; ++slot) {
+                const int w0 = 8 * slot, nw = slot < 2 ? 8 : 4;
+                uint32_t dot = 0, ss = 0, te = 0;
+#pragma unroll
+                for (int w = 0; w < nw; ++w) {
+                    dot = dp4a_kept(s[w0 + w], t[w0 + w], dot);
+                    ss = dp4a_kept(s[w0 + w], s[w0 + w], ss);
+                    te = dp4a_kept(t[w0 + w], t[w0 + w], te);
+                }
+                acc += ss + te - 2u * dot;
+                if (acc >= bound) break;
+            }
+        } else {
+#pragma unroll
+            for (int a = 0; a < 7; ++a) {
+                uint32_t dot = 0, ss = 0;
+#pragma unroll
+                for (int w = 0; w < 6; ++w) {
+                    dot = dp4a_kept(s[6 * a + w], t[6 * a + w], dot);
+                    ss = dp4a_kept(s[6 * a + w], s[6 * a + w], ss);
+                }
+                acc += ss + row_e[a] - 2u * dot;
+                if (acc >= bound) break;
+            }
+        }
+        total += acc;
+    }
+    if (total == 0x12345678u) sink[blockIdx.x] = total;  // practically never taken; defeats DCE
+}
+
 }  // namespace
+
+cudaError_t launch_ssd_mix_probe(int k, int blocks, int iters, uint32_t* sink, cudaStream_t st) {
+    if (k == 5)
+        ssd_mix_probe_kernel<5><<<blocks, 256, 0, st>>>(0xC0FFEEu, 0xFFFFFFFFu, iters, sink);
+    else if (k == 7)
+        ssd_mix_probe_kernel<7><<<blocks, 256, 0, st>>>(0xC0FFEEu, 0xFFFFFFFFu, iters, sink);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
 
 cudaError_t launch_dp4a_probe(int blocks, int iters, uint32_t* sink, cudaStream_t st) {
     dp4a_probe_kernel<<<blocks, 256, 0, st>>>(0xC0FFEEu, iters, sink);
