@@ -1,6 +1,9 @@
 """The learned initialiser's tensor-core kernels against the FP64 CPU oracle: single
-conv layers (forward, input and weight gradients) and the whole training step's
-parameter gradient (relative L2 error <= 1e-2 at BF16)."""
+conv layers (forward, input and weight gradients: relative L2 error < 1e-5 in fp32) and
+the whole training step's parameter gradient, at the downscales 4 and 8 (8 is the one the
+library trains and runs by default).  For the whole network the asserted bound is a
+relative L2 error of at most max(1e-2, twice the measured BF16 noise floor of the
+oracle's own gradient), a cosine similarity above 0.995, and 1e-2 on the head layer."""
 import numpy as np
 import pytest
 
@@ -67,36 +70,38 @@ def test_conv_backward_matches_oracle(fbp, n, H, W, Cin, Cout, stride):
     assert rel_l2(dw.cpu().numpy(), dw_ref) < 1e-5
 
 
-def _oracle_grads(params, src, tgt, target, nudge=0.0):
+def _oracle_grads(params, src, tgt, target, nudge=0.0, ds=4):
     p = params.astype(np.float64)
     if nudge:
         p = p * (1.0 + nudge * np.random.default_rng(9).normal(size=p.shape))
-    head, cache = ref.forward(p, src, tgt)
+    head, cache = ref.forward(p, src, tgt, ds)
     n, hq, wq = head.shape[:3]
     _, dhead = ref.loss_and_grad_head(head, target.astype(np.float64), None, float(n * hq * wq))
     return ref.backward(cache, dhead), head
 
 
-def test_training_step_gradient_matches_oracle(fbp):
+@pytest.mark.parametrize("ds", [4, 8])
+def test_training_step_gradient_matches_oracle(fbp, ds):
     """A BF16 network's gradient is chaotic at the per-cent level: nudging the weights by
     1e-6 (far below BF16 resolution) moves the oracle's own gradient by about 2 %,
-    through rounding flips at ReLU boundaries and BF16 stores.  The GPU gradient must lie
-    within twice that measured noise floor of the oracle (and the head layer, where no
-    flip can intervene, within 1 %)."""
+    through rounding flips at ReLU boundaries and BF16 stores.  Asserted: the GPU
+    gradient's relative L2 distance from the oracle's is at most max(1e-2, twice that
+    measured noise floor) -- about 4 % --, its cosine similarity above 0.995, and the head
+    layer, where no flip can intervene, within 1 %."""
     import torch
     rng = np.random.default_rng(5)
-    n, H, W = 2, 64, 64
+    n, H, W = 2, 16 * ds, 16 * ds      # a 16 x 16 grid at either downscale
     src = rng.integers(0, 256, size=(n, H, W, 3)).astype(np.uint8)
     tgt = rng.integers(0, 256, size=(n, H, W, 3)).astype(np.uint8)
     params = ref.init_params(11).astype(np.float32)
     params[-8 * 9 * 32 - 8:-6 * 9 * 32 - 8] = rng.normal(0, 0.05, size=2 * 9 * 32)   # live head rows 0,1
-    target = rng.normal(0, 4, size=(n, H // 4, W // 4, 2)).astype(np.float32)
-    g_ref, head = _oracle_grads(params, src, tgt, target)
-    g_nudged, head_nudged = _oracle_grads(params, src, tgt, target, nudge=1e-6)
+    target = rng.normal(0, 4, size=(n, H // ds, W // ds, 2)).astype(np.float32)
+    g_ref, head = _oracle_grads(params, src, tgt, target, ds=ds)
+    g_nudged, head_nudged = _oracle_grads(params, src, tgt, target, nudge=1e-6, ds=ds)
     noise = rel_l2(g_nudged, g_ref)
     head_noise = rel_l2(head_nudged[..., :2], head[..., :2])
     ctx = fbp.Context(0)
-    net = fbp.InitNet(ctx, n, H, W, downscale=4)
+    net = fbp.InitNet(ctx, n, H, W, downscale=ds)
     net.set_params(params)
     g_src = torch.tensor(src, device="cuda")
     g_tgt = torch.tensor(tgt, device="cuda")
