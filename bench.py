@@ -95,6 +95,16 @@ def dist_env():
     return rank, world, local
 
 
+def rank_device(local: int) -> int:
+    """The GPU of local rank `local`: one per rank; ranks beyond the visible devices share
+    them round-robin (a functional run of the multi-rank path on fewer GPUs -- its kernels
+    never wait on another rank's, so sharing is safe, but its timings are not scaling
+    numbers)."""
+    import torch
+    n = torch.cuda.device_count()
+    return local % n if n else local
+
+
 class RankGroup:
     """The ranks of one bench run.  With more than one rank a gloo group carries the
     barriers around the timed region and the max-over-ranks reduction of the timings;
@@ -464,6 +474,7 @@ def run_gpu(args):
 
     grp = RankGroup()
     rank, world, local = grp.rank, grp.world, grp.local
+    local = rank_device(local)
     torch.cuda.set_device(local)
     fbp.build()
     learned = args.workload == "learned_512"
@@ -521,7 +532,10 @@ def run_gpu(args):
         ctx.set_initnet(net)
         params = fbp.Params.make(w.patch, args.learned_iters, 1, 0, w.seed)
         params.flags = fbp.FB_FLAG_LEARNED_INIT
-        learned_info = {"training_set_s": t_data, "training_s": t_train,
+        learned_info = {"timing": "the initialiser is trained once before the timed region "
+                                  "(training_set_s + training_s, not in ms_per_step); each timed "
+                                  "step runs its forward pass and the refinement iterations",
+                        "training_set_s": t_data, "training_s": t_train,
                         "training_steps": hist[-1][0] + 1, "loss_first": hist[0][1],
                         "loss_last": hist[-1][1], "refinement_iters": args.learned_iters,
                         "net_params": net.n_params, "downscale": net.ds}
@@ -757,6 +771,7 @@ def run_gpu_batch(args):
 
     grp = RankGroup()
     rank, world, local = grp.rank, grp.world, grp.local
+    local = rank_device(local)
     torch.cuda.set_device(local)
     fbp.build()
     manifest = synth.batch_manifest(seed=shard_seed(BATCH_SEED, rank))
@@ -798,6 +813,8 @@ def run_gpu_batch(args):
     value = aggregate(frames, args.steps, world, total_ms)
     clocks = clk.summary()
 
+    modes = {k: ("per-clip launches" if fbp.fb_ctx_batch_mode(ctx, k) == 1 else "persistent")
+             for k in (5, 7)}
     # Kernel breakdown: one untimed submission with direct launches and event timing.
     ctx.profile(True)
     fbp.fb_blend_batch(ctx, clips, params, flags=fbp.FB_BATCH_NO_GRAPH)
@@ -807,7 +824,9 @@ def run_gpu_batch(args):
     kernel_total_ms = sum(v[0] for v in prof.values())
     peak = DP4A_PER_CLK_SM * 4 * SM_COUNT_NOMINAL * SM_MAX_MHZ_NOMINAL * 1e6 / 1e12
     achieved = batch_iter_ops(manifest) / (iter_ms / 1e3) / 1e12 if iter_ms else None
-    roof = {"bound": "alu", "kernel": "batch_iter (persistent Alg. 1 Jacobi iteration)",
+    roof = {"bound": "alu", "kernel": ("Alg. 1 Jacobi iterations of the batch: "
+                                       + ", ".join(f"k={k} {'nnf_iter per clip' if m != 'persistent' else 'persistent batch_iter'}"
+                                                   for k, m in modes.items())),
             "achieved": achieved, "peak": peak, "unit": "T byte-pair ops/s",
             "frac": achieved / peak if achieved else None, "traffic": None,
             "peak_basis": f"{DP4A_PER_CLK_SM} dp4a/clk/SM x {SM_COUNT_NOMINAL} SMs x "
@@ -817,6 +836,22 @@ def run_gpu_batch(args):
             "candidate_evals_per_s": batch_candidate_evals(manifest) * args.steps * world
             / (total_ms / 1e3)}
     variants = {k: fbp.batch_variant_name(fbp.fb_ctx_batch_variant(ctx, k)) for k in (5, 7)}
+    claims = {k: fbp.fb_ctx_batch_claim(ctx, k) for k in (5, 7)}
+
+    # The same clips through one fb_blend_window call each, in the same run (one warm-up
+    # loop so the per-call scratch exists, then one timed loop, L2 flushed first).
+    def per_clip_loop():
+        for g, s, window, patch, o in clips:
+            fbp.fb_blend_window(ctx, g, s, window, fbp.Params.make(patch, BATCH_ITERS, 1, 0, BATCH_SEED), out=o)
+    per_clip_loop()
+    torch.cuda.synchronize()
+    flush.zero_()
+    la, lb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    la.record()
+    per_clip_loop()
+    lb.record()
+    torch.cuda.synchronize()
+    loop_ms = la.elapsed_time(lb)
 
     e2e = None
     if not args.no_e2e:
@@ -852,7 +887,10 @@ def run_gpu_batch(args):
                    "nnfs_per_step": sum(sum(min(N - 1, i + (w - 1) // 2) - max(0, i - (w - 1) // 2)
                                             for i in range(N)) for N, H, W, w, k in manifest),
                    "candidate_evals_per_step": batch_candidate_evals(manifest),
-                   "tuned_variants": variants, "first_call_s": t_build,
+                   "tuned_modes": modes, "tuned_variants": variants, "tuned_tiles_per_claim": claims,
+                   "first_call_s": t_build,
+                   "per_clip_loop_ms": loop_ms,
+                   "speedup_vs_per_clip_loop": loop_ms / (total_ms / args.steps),
                    "l2": f"flushed between steps ({FLUSH_BYTES >> 20} MiB write)",
                    "parallelism": f"{world} independent batch(es), one per GPU"},
         "roofline": roof, "e2e": e2e, "gpu_launches": launches,
@@ -912,6 +950,7 @@ def run_gpu_initnet(args):
 
     grp = RankGroup()
     rank, world, local = grp.rank, grp.world, grp.local
+    local = rank_device(local)
     torch.cuda.set_device(local)
     fbp.build()
     w = synth.WORKLOADS["blend_512"]
@@ -945,6 +984,29 @@ def run_gpu_initnet(args):
     flops = initnet_flops_per_pair(w.H, w.W, 8) * INITNET_PAIRS
     peak, basis = measured_peak("bf16_tflops", 1800.0)
     achieved = flops / (statistics.median(step_ms) / 1e3) / 1e12
+
+    # One training step on the same pairs (forward, smooth-L1 loss, backward, Adam): the
+    # twelve weight gradients and the input gradients of layers 1-11 cost a forward each,
+    # 3 F - F(layer 0) FLOPs in all.  Context for the forward line, timed the same way.
+    target = torch.zeros((INITNET_PAIRS, w.H // 8, w.W // 8, 2), dtype=torch.float32, device="cuda")
+    for _ in range(max(args.warmup, 1)):
+        net.train_step(src, tgt, target, lr=1e-6)
+    torch.cuda.synchronize()
+    from paper_2311_09265_b300.initnet_layout import LAYERS
+    f0 = 2 * (w.H // 8) * (w.W // 8) * LAYERS[0][1] * 9 * LAYERS[0][0] * INITNET_PAIRS
+    train_flops = 3 * flops - f0
+    tms = []
+    for _ in range(max(args.steps, 1)):
+        flush.zero_()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        net.train_step(src, tgt, target, lr=1e-6)
+        b.record()
+        torch.cuda.synchronize()
+        tms.append(a.elapsed_time(b))
+    assert net.status() == fbp.FB_OK
+    train_ms = statistics.median(tms)
+    train_tflops = train_flops / (train_ms / 1e3) / 1e12
     line = {
         "metric": "learned-initialiser forward: NNF pairs/s at 512x512 (64x64 grid)",
         "value": world * INITNET_PAIRS * args.steps / (total_ms / 1e3), "unit": "pairs/s",
@@ -959,7 +1021,12 @@ def run_gpu_initnet(args):
         "roofline": {"bound": "tensor", "kernel": "whole forward (12 TMA-fed tcgen05 convolutions + "
                      "input, concatenation and head kernels)", "achieved": achieved, "peak": peak,
                      "unit": "TFLOP/s", "frac": achieved / peak, "traffic": None,
-                     "peak_basis": f"bf16 dense, {basis} (cuBLAS burst)"},
+                     "peak_basis": f"bf16 dense, {basis} (cuBLAS burst)",
+                     "train_step": {"ms": train_ms, "flops": train_flops, "achieved": train_tflops,
+                                    "frac": train_tflops / peak,
+                                    "what": "forward + loss + backward (12 weight gradients, input "
+                                            "gradients of layers 1-11) + Adam, 256 pairs, median of "
+                                            f"{len(tms)}"}},
         "e2e": None, "gpu_launches": ctx.launches - launches0, "clocks": clk.summary(),
     }
     if rank == 0:

@@ -345,6 +345,9 @@ typedef struct fb_clip_desc {
 
 #define FB_BATCH_NO_GRAPH 0x1u            /* launch directly, do not capture/replay */
 #define FB_BATCH_VARIANT(v) (((uint32_t)(v) + 1u) << 8)  /* force tile variant v (0..3) */
+#define FB_BATCH_CLAIM(c) ((uint32_t)(c) << 16)  /* force c tiles per iteration claim (1..64) */
+#define FB_BATCH_PERSISTENT (1u << 24)  /* force the persistent kernels for every patch size */
+#define FB_BATCH_PER_CLIP (2u << 24)    /* force per-clip launches for every patch size       */
 
 /* Eq. 2 window blends of n_clips clips of uneven size, window and patch in one
  * submission.  This batched, persistent form is not in the paper; the paper only
@@ -360,7 +363,15 @@ typedef struct fb_clip_desc {
  * tunes the tile shape / occupancy per patch size on a few iterations of the size's
  * first chunk (all variants give identical results), then captures the whole
  * submission into a CUDA graph that later submissions with the same manifest replay
- * (FB_BATCH_NO_GRAPH: direct launches).  The context keeps the tables, scratch and graph of the two most recent
+ * (FB_BATCH_NO_GRAPH: direct launches).  The tuner chooses, per patch size, the tile
+ * shape / occupancy variant and the number of consecutive tiles one claim of the
+ * iteration kernel covers (1, 2, 4 or 8), timing every combination on a prefix of the
+ * size's first chunk, and then the launch mode: those persistent kernels, or per-clip
+ * launches of the kernels fb_blend_window uses (one clip segment after another, spread
+ * over three branches of the graph so that one clip's launch tails overlap the next clip's
+ * work), whichever ran the same prefix faster.  FB_BATCH_VARIANT / FB_BATCH_CLAIM force
+ * the persistent kernels with that variant / claim; FB_BATCH_PERSISTENT /
+ * FB_BATCH_PER_CLIP force the mode.  The context keeps the tables, scratch and graph of the two most recent
  * manifests.  Async on `stream`; do not call it while `stream` is being captured. */
 int fb_blend_batch(fb_ctx *ctx, const fb_clip_desc *clips, int n_clips, const fb_params *p,
                    uint32_t flags, void *stream);
@@ -424,6 +435,13 @@ int fb_ctx_energy(fb_ctx *ctx, double *sum, uint64_t *count);
 
 /* Tile variant the autotuner chose for patch size k in this context, or -1. */
 int fb_ctx_batch_variant(const fb_ctx *ctx, int patch);
+
+/* Tiles per iteration claim the autotuner chose for patch size k in this context, or -1. */
+int fb_ctx_batch_claim(const fb_ctx *ctx, int patch);
+
+/* Launch mode the autotuner chose for patch size k in this context: 0 persistent kernels,
+ * 1 per-clip launches, -1 not tuned. */
+int fb_ctx_batch_mode(const fb_ctx *ctx, int patch);
 
 /* ---------------------------------------------------------------------------------
  * Learned NNF initialiser.  Not in the paper (its method is model-free and needs no

@@ -27,7 +27,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_nnf", "fb_nnf_balanced", "fb_nnf_segment", "fb_remap", "fb_blend_window", "fb_interpolate",
                     "fb_blend_window_range", "fb_interpolate_range", "fb_shard_plan", "fb_pair_plan_range",
                     "fb_blend_window_noalloc", "fb_blend_batch", "fb_batch_plan", "fb_fast_plan", "fb_pair_plan",
-                    "fb_ctx_batch_variant", "fb_ctx_set_pair_budget",
+                    "fb_ctx_batch_variant", "fb_ctx_batch_claim", "fb_ctx_batch_mode", "fb_ctx_set_pair_budget",
                     "fb_initnet_create", "fb_initnet_destroy", "fb_initnet_last_error",
                     "fb_initnet_param_count", "fb_initnet_get_params", "fb_initnet_set_params",
                     "fb_initnet_get_grads", "fb_initnet_forward", "fb_initnet_init_nnf", "fb_conv_gemm_path",
@@ -45,6 +45,10 @@ FB_FLAG_TRACKING = 0x20
 FB_FLAG_ALIGN = 0x40
 
 FB_BATCH_NO_GRAPH = 0x1
+
+
+def FB_BATCH_CLAIM(c: int) -> int:
+    return (int(c) & 0xFF) << 16
 
 
 def FB_BATCH_VARIANT(v: int) -> int:
@@ -208,6 +212,10 @@ def lib() -> ctypes.CDLL:
         L.fb_ctx_set_pair_budget.restype = ctypes.c_int
         L.fb_ctx_batch_variant.argtypes = [_vp, ctypes.c_int]
         L.fb_ctx_batch_variant.restype = ctypes.c_int
+        L.fb_ctx_batch_claim.argtypes = [_vp, ctypes.c_int]
+        L.fb_ctx_batch_claim.restype = ctypes.c_int
+        L.fb_ctx_batch_mode.argtypes = [_vp, ctypes.c_int]
+        L.fb_ctx_batch_mode.restype = ctypes.c_int
         for f in ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_ctx_profile",
                   "fb_ctx_profile_read", "fb_nnf", "fb_remap",
                   "fb_blend_window", "fb_interpolate"):
@@ -615,6 +623,20 @@ def fb_batch_plan(shapes, params: Params, budget_bytes: int = 0):
 
 def fb_ctx_batch_variant(ctx: Context, patch: int) -> int:
     return int(lib().fb_ctx_batch_variant(ctx.handle, patch))
+
+
+FB_BATCH_PERSISTENT = 1 << 24
+FB_BATCH_PER_CLIP = 2 << 24
+
+
+def fb_ctx_batch_mode(ctx: Context, patch: int) -> int:
+    """Launch mode the batch autotuner chose for patch size k: 0 persistent, 1 per-clip, -1 none."""
+    return int(lib().fb_ctx_batch_mode(ctx.handle, patch))
+
+
+def fb_ctx_batch_claim(ctx: Context, patch: int) -> int:
+    """Tiles per iteration claim the batch autotuner chose for patch size k (-1: none)."""
+    return int(lib().fb_ctx_batch_claim(ctx.handle, patch))
 
 
 BATCH_VARIANT_NAMES = ("tile 32x8, 5 blocks/SM", "tile 32x4, 10 blocks/SM",

@@ -40,6 +40,8 @@ struct fb_ctx {
     std::vector<Rec> recs;
     // Batched submissions: tuned tile variant per patch size, and the cached manifests.
     int tuned_variant[10] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};
+    int tuned_claim[10] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};  // tiles per iteration claim
+    int tuned_mode[10] = {-1, -1, -1, -1, -1, -1, -1, -1, -1, -1};   // persistent or per-clip
     size_t pair_budget = 0;  // bytes of NNF scratch per chunk; 0 = kPairBudgetBytes
     fb_initnet* init_net = nullptr;  // learned initialiser for FB_FLAG_LEARNED_INIT
     double* energy = nullptr;        // device: sum of final errors (FB_FLAG_REPORT_ENERGY)
@@ -57,6 +59,10 @@ struct fb_ctx::BatchEntry {
     uint64_t launches_per_run = 0;
     std::vector<std::function<cudaError_t(cudaStream_t)>> steps;  // the submission's launches
     std::vector<int> step_kind;
+    // Per-clip launch mode: the streams the clip segments of a chunk are spread over
+    // (graph branches) and the events that fork them from and join them to the caller's.
+    std::vector<cudaStream_t> side;
+    std::vector<cudaEvent_t> ev;
 };
 
 namespace {
@@ -1099,12 +1105,65 @@ std::vector<uint8_t> manifest_key(const fb_clip_desc* clips, int n, const fb_par
 void drop_entry(fb_ctx::BatchEntry* be) {
     if (be->exec) cudaGraphExecDestroy(be->exec);
     if (be->dev) cudaFree(be->dev);
+    for (cudaStream_t x : be->side) cudaStreamDestroy(x);
+    for (cudaEvent_t x : be->ev) cudaEventDestroy(x);
     delete be;
+}
+
+// Launch modes of a patch size in a batch: the persistent kernels over the flattened work
+// list, or per-clip launches of the kernels fb_blend_window uses, one clip segment (the
+// consecutive output frames of one clip in a chunk) after another on a few graph branches.
+constexpr int kModePersistent = 0, kModePerClip = 1;
+constexpr int kPerClipBranches = 3;
+
+// FB_BATCH_MODE(m): launch mode forced to m - 1 (0: tuned).
+int forced_mode(uint32_t flags) {
+    const uint32_t m = (flags >> 24) & 0x3u;
+    return m == 0 ? -1 : static_cast<int>(m) - 1;
+}
+
+// A chunk's clip segments: [job0, job0 + nj) of one clip with pairs [pair0, pair0 + np),
+// each within the per-call kernels' grid limit (65535 pairs, 65535 jobs).
+struct ClipSeg {
+    int clip, job0, nj, pair0, np;
+};
+std::vector<ClipSeg> clip_segments(const HostChunk& ch) {
+    std::vector<ClipSeg> out;
+    for (size_t j = 0; j < ch.jobs.size(); ++j) {
+        const BatchJob& bj = ch.jobs[j];
+        if (out.empty() || out.back().clip != bj.clip || out.back().np + bj.n_pairs > kMaxChunkPairs ||
+            out.back().nj + 1 > kMaxChunkPairs)
+            out.push_back(ClipSeg{bj.clip, static_cast<int>(j), 0, bj.first_pair, 0});
+        out.back().nj += 1;
+        out.back().np += bj.n_pairs;
+    }
+    return out;
 }
 
 int forced_variant(uint32_t flags) {
     const uint32_t v = (flags >> 8) & 0xFFu;
     return v == 0 ? -1 : static_cast<int>(v) - 1;
+}
+
+// FB_BATCH_CLAIM(c): tiles per claim of the iteration kernel forced to c (0: tuned).
+int forced_claim(uint32_t flags) {
+    const uint32_t c = (flags >> 16) & 0xFFu;
+    return c == 0 ? -1 : static_cast<int>(c);
+}
+
+// The first pairs of a chunk, enough for about `waves` rounds of tiles over the GPU: the
+// autotuner times its candidates on this prefix so that tuning costs a few milliseconds
+// whatever the chunk's size.
+HostChunk tuning_prefix(const HostChunk& ch, const fb_clip_desc* clips, size_t tiles_wanted) {
+    HostChunk t;
+    t.k = ch.k;
+    size_t tiles = 0;
+    for (const BatchPair& bp : ch.pairs) {
+        if (tiles >= tiles_wanted) break;
+        t.pairs.push_back(bp);
+        tiles += tiles_of(clips[bp.clip].H, clips[bp.clip].W, 8);
+    }
+    return t;
 }
 
 // Builds a cache entry: device tables and scratch, tuning, the list of launches and,
@@ -1123,7 +1182,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
     size_t n_counters = 2;  // tuning launches
     for (const HostChunk& ch : chunks) n_counters += 2 + static_cast<size_t>(p->iters);
     auto layout = [&](Carver& c, BatchClip** d_clips, std::vector<ClipBufs>& cb,
-                      uint32_t** fe, std::vector<std::array<void*, 8>>& tabs, int** counters) {
+                      uint32_t** fe, std::vector<std::array<void*, 10>>& tabs, int** counters) {
         *counters = c.take<int>(n_counters);
         *d_clips = c.take<BatchClip>(n);
         cb.assign(n, ClipBufs{});
@@ -1151,12 +1210,15 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
             tabs[ci][5] = c.take<int32_t>(std::max<size_t>(job_items, 1));
             tabs[ci][6] = c.take<int32_t>(std::max<size_t>(max_items, 1));  // init units
             tabs[ci][7] = c.take<int32_t>(std::max<size_t>(max_items, 1));
+            // the per-call kernels' pair and job tables of the chunk (per-clip mode)
+            tabs[ci][8] = c.take<PairDesc>(std::max<size_t>(ch.pairs.size(), 1));
+            tabs[ci][9] = c.take<JobDesc>(std::max<size_t>(ch.jobs.size(), 1));
         }
     };
     BatchClip* d_clips = nullptr;
     std::vector<ClipBufs> cb;
     uint32_t* fe[4] = {};
-    std::vector<std::array<void*, 8>> tabs;
+    std::vector<std::array<void*, 10>> tabs;
     int* counters = nullptr;
     layout(cv, &d_clips, cb, fe, tabs, &counters);
     be->bytes = align_up(cv.off, 1 << 20);
@@ -1189,6 +1251,21 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         job_units[ci] = static_cast<int>(m0.size());
         FB_CUDA(ctx, cudaMemcpy(tabs[ci][4], m0.data(), sizeof(int32_t) * m0.size(), cudaMemcpyHostToDevice));
         FB_CUDA(ctx, cudaMemcpy(tabs[ci][5], m1.data(), sizeof(int32_t) * m1.size(), cudaMemcpyHostToDevice));
+        // The same NNFs in the per-call kernels' tables: what blend_pairs builds for the clip
+        // (frame slots of the clip, the clip-frame streams), pair indices of the chunk.
+        std::vector<PairDesc> pd(ch.pairs.size());
+        for (size_t q = 0; q < ch.pairs.size(); ++q) {
+            const BatchPair& bp = ch.pairs[q];
+            pd[q] = PairDesc{bp.src, bp.tgt, bp.tag, bp.style, bp.weight, {-1, -1, -1}};
+        }
+        std::vector<JobDesc> jd(ch.jobs.size());
+        for (size_t q = 0; q < ch.jobs.size(); ++q) {
+            const BatchJob& bj = ch.jobs[q];
+            jd[q] = JobDesc{bj.frame, bj.frame, 1u, bj.first_pair, bj.n_pairs, bj.den, {0, 0}};
+        }
+        if (!pd.empty())
+            FB_CUDA(ctx, cudaMemcpy(tabs[ci][8], pd.data(), sizeof(PairDesc) * pd.size(), cudaMemcpyHostToDevice));
+        FB_CUDA(ctx, cudaMemcpy(tabs[ci][9], jd.data(), sizeof(JobDesc) * jd.size(), cudaMemcpyHostToDevice));
     }
 
     // ---- the launches of one submission ----
@@ -1209,14 +1286,32 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         });
         be->step_kind.push_back(FB_K_STYLE);
     }
-    // Tile variant per patch size: forced, tuned earlier in this context, or tuned now on
-    // iterations 1-2 of the size's first chunk (after an untimed iteration 0).
-    int variant_of[10];
-    for (int k = 0; k < 10; ++k) variant_of[k] = forced_variant(flags) >= 0 ? forced_variant(flags) : ctx->tuned_variant[k];
+    // Tile variant and iteration claim size per patch size: forced, tuned earlier in this
+    // context, or tuned now.  Every (variant, claim) candidate -- the ones not forced -- runs
+    // iterations 1-2 (after an untimed iteration 0) over a prefix of the size's first chunk
+    // (about 32 rounds of 32x8 tiles over the GPU); the fastest is kept.  All candidates give
+    // the same results.
+    int variant_of[10], claim_of[10], mode_of[10];
+    for (int k = 0; k < 10; ++k) {
+        variant_of[k] = forced_variant(flags) >= 0 ? forced_variant(flags) : ctx->tuned_variant[k];
+        claim_of[k] = forced_claim(flags) >= 0 ? forced_claim(flags) : ctx->tuned_claim[k];
+        mode_of[k] = forced_mode(flags) >= 0 ? forced_mode(flags) : ctx->tuned_mode[k];
+        if (forced_variant(flags) >= 0 || forced_claim(flags) >= 0)
+            mode_of[k] = forced_mode(flags) >= 0 ? forced_mode(flags) : kModePersistent;
+        if (forced_variant(flags) < 0 && forced_claim(flags) >= 0 && ctx->tuned_variant[k] >= 0 &&
+            ctx->tuned_claim[k] != forced_claim(flags))
+            variant_of[k] = -1;   // the variant was tuned for another claim size: tune again
+        if (forced_claim(flags) < 0 && forced_variant(flags) >= 0 && ctx->tuned_claim[k] >= 0 &&
+            ctx->tuned_variant[k] != forced_variant(flags))
+            claim_of[k] = -1;
+    }
     bool prepped = false;
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
-        const HostChunk& ch = chunks[ci];
-        if (variant_of[ch.k] >= 0 || ch.pairs.empty()) continue;
+        const HostChunk& full_ch = chunks[ci];
+        if ((variant_of[full_ch.k] >= 0 && claim_of[full_ch.k] >= 0 && mode_of[full_ch.k] >= 0) ||
+            full_ch.pairs.empty())
+            continue;
+        const HostChunk ch = tuning_prefix(full_ch, clips, static_cast<size_t>(sms) * 8 * 32);
         if (!prepped) {
             for (size_t q = 0; q < 1 + 2 * static_cast<size_t>(n); ++q) FB_CUDA(ctx, be->steps[q](st));
             prepped = true;
@@ -1228,12 +1323,17 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
         int32_t* d_it0 = static_cast<int32_t*>(tabs[ci][7]);
         std::vector<int32_t> u0, u1;
         float best = 0.f;
-        int best_v = 0;
+        int best_v = -1, best_c = -1;
         cudaEvent_t a = nullptr, b = nullptr;
         FB_CUDA(ctx, cudaEventCreate(&a));
         FB_CUDA(ctx, cudaEventCreate(&b));
-        for (int v = 0; v < fb::kBatchVariants; ++v) {
-            item_maps(ch, clips, fb::batch_variant_tile_h(v), fb::kIterTilesPerClaim, m0, m1);
+        std::vector<int> claim_list(fb::kIterClaimChoices, fb::kIterClaimChoices + fb::kIterClaimCount);
+        if (claim_of[ch.k] >= 0) claim_list.assign(1, claim_of[ch.k]);
+        for (int cand = 0; cand < fb::kBatchVariants * static_cast<int>(claim_list.size()); ++cand) {
+            const int v = cand / static_cast<int>(claim_list.size());
+            const int claim = claim_list[cand % claim_list.size()];
+            if (variant_of[ch.k] >= 0 && v != variant_of[ch.k]) continue;
+            item_maps(ch, clips, fb::batch_variant_tile_h(v), claim, m0, m1);
             item_maps(ch, clips, fb::batch_variant_tile_h(v), fb::kInitTilesPerClaim, u0, u1);
             FB_CUDA(ctx, cudaMemcpyAsync(d_ip, m0.data(), sizeof(int32_t) * m0.size(), cudaMemcpyHostToDevice, st));
             FB_CUDA(ctx, cudaMemcpyAsync(d_it, m1.data(), sizeof(int32_t) * m1.size(), cudaMemcpyHostToDevice, st));
@@ -1249,7 +1349,7 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
                 const int s0 = (it & 1) ? 2 : 0, s1 = (it & 1) ? 0 : 2;
                 FB_CUDA(ctx, cudaMemsetAsync(counters + 1, 0, sizeof(int), st));
                 FB_CUDA(ctx, fb::launch_batch_iter(ch.k, v, d_pairs, d_clips, d_ip, d_it, static_cast<int>(m0.size()),
-                                                   counters + 1, p->seed, it, fe[s0], fe[s0 + 1], fe[s1],
+                                                   claim, counters + 1, p->seed, it, fe[s0], fe[s0 + 1], fe[s1],
                                                    fe[s1 + 1], grid, st));
             }
             FB_CUDA(ctx, cudaEventRecord(b, st));
@@ -1257,22 +1357,153 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
             float ms = 0.f;
             FB_CUDA(ctx, cudaEventElapsedTime(&ms, a, b));
             ctx->launches += 4;
-            if (v == 0 || ms < best) {
+            if (best_v < 0 || ms < best) {
                 best = ms;
                 best_v = v;
+                best_c = claim;
             }
+        }
+        // The per-clip mode on the same prefix: the per-call kernels over each run of one
+        // clip's pairs, the same untimed iteration and two timed ones.
+        float per_clip_ms = -1.f;
+        if (mode_of[ch.k] < 0) {
+            const PairDesc* d_pd = static_cast<const PairDesc*>(tabs[ci][8]);
+            std::vector<std::array<int, 3>> runs;  // clip, first pair, pairs
+            for (size_t q = 0; q < ch.pairs.size(); ++q) {
+                if (runs.empty() || runs.back()[0] != ch.pairs[q].clip)
+                    runs.push_back({ch.pairs[q].clip, static_cast<int>(q), 0});
+                runs.back()[2] += 1;
+            }
+            for (int it = -1; it < 3; ++it) {
+                if (it == 1) FB_CUDA(ctx, cudaEventRecord(a, st));
+                for (const auto& rn : runs) {
+                    const fb_clip_desc& d = clips[rn[0]];
+                    const LevelGeom g{d.H, d.W, cb[rn[0]].rp};
+                    const size_t off = ch.pairs[rn[1]].fe_off;
+                    const int r0 = p->r0 > 0 ? p->r0 : std::max(d.H, d.W);
+                    if (it < 0) {
+                        FB_CUDA(ctx, fb::launch_nnf_init(ch.k, d_pd, rn[1], rn[2], g, 0, nullptr, 0, 0, nullptr,
+                                                         p->seed, 0, fe[0] + off, fe[1] + off, st));
+                    } else {
+                        const int s0 = (it & 1) ? 2 : 0, s1 = (it & 1) ? 0 : 2;
+                        FB_CUDA(ctx, fb::launch_nnf_iter(ch.k, d_pd, rn[1], rn[2], g, r0, p->seed, 0, it,
+                                                         fe[s0] + off, fe[s0 + 1] + off, fe[s1] + off,
+                                                         fe[s1 + 1] + off, st));
+                    }
+                }
+            }
+            FB_CUDA(ctx, cudaEventRecord(b, st));
+            FB_CUDA(ctx, cudaEventSynchronize(b));
+            FB_CUDA(ctx, cudaEventElapsedTime(&per_clip_ms, a, b));
+            ctx->launches += 4 * runs.size();
         }
         cudaEventDestroy(a);
         cudaEventDestroy(b);
         variant_of[ch.k] = best_v;
-        if (forced_variant(flags) < 0) ctx->tuned_variant[ch.k] = best_v;
+        claim_of[ch.k] = best_c;
+        if (mode_of[ch.k] < 0) mode_of[ch.k] = per_clip_ms >= 0.f && per_clip_ms < best ? kModePerClip : kModePersistent;
+        if (forced_variant(flags) < 0 && forced_claim(flags) < 0 && forced_mode(flags) < 0) {
+            ctx->tuned_variant[ch.k] = best_v;   // a free choice: remember it
+            ctx->tuned_claim[ch.k] = best_c;
+            ctx->tuned_mode[ch.k] = mode_of[ch.k];
+        }
     }
     int* next_counter = counters + 2;
+    // Per-clip chunks spread their clip segments over side streams (graph branches) when the
+    // submission is captured; launched directly, they run on the caller's stream.
+    const bool branches = !(flags & FB_BATCH_NO_GRAPH);
+    bool any_per_clip = false;
+    for (const HostChunk& ch : chunks) any_per_clip = any_per_clip || mode_of[ch.k] == kModePerClip;
+    if (branches && any_per_clip) {
+        for (int q = 0; q < kPerClipBranches; ++q) {
+            cudaStream_t x = nullptr;
+            FB_CUDA(ctx, cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+            be->side.push_back(x);
+        }
+    }
     for (size_t ci = 0; ci < chunks.size(); ++ci) {
         const HostChunk& ch = chunks[ci];
+        if (mode_of[ch.k] == kModePerClip) {
+            // The kernels and tables fb_blend_window uses, segment by segment (bit-identical
+            // results: the same pairs, streams and schedule).
+            const int k = ch.k;
+            const uint64_t seed = p->seed;
+            const int iters = p->iters;
+            const PairDesc* d_pd = static_cast<const PairDesc*>(tabs[ci][8]);
+            const JobDesc* d_jd = static_cast<const JobDesc*>(tabs[ci][9]);
+            cudaEvent_t fork = nullptr;
+            std::vector<cudaEvent_t> joins;
+            if (branches) {
+                FB_CUDA(ctx, cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+                be->ev.push_back(fork);
+                for (size_t b = 0; b < be->side.size(); ++b) {
+                    cudaEvent_t e2 = nullptr;
+                    FB_CUDA(ctx, cudaEventCreateWithFlags(&e2, cudaEventDisableTiming));
+                    be->ev.push_back(e2);
+                    joins.push_back(e2);
+                }
+                const std::vector<cudaStream_t> side = be->side;
+                be->steps.push_back([fork, side](cudaStream_t s) {
+                    cudaError_t e2 = cudaEventRecord(fork, s);
+                    for (cudaStream_t x : side)
+                        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(x, fork, 0);
+                    return e2;
+                });
+                be->step_kind.push_back(-1);
+            }
+            const std::vector<ClipSeg> segs = clip_segments(ch);
+            for (size_t q = 0; q < segs.size(); ++q) {
+                const ClipSeg sg = segs[q];
+                if (sg.np <= 0 && sg.nj <= 0) continue;
+                const fb_clip_desc d = clips[sg.clip];
+                const LevelGeom g{d.H, d.W, cb[sg.clip].rp};
+                const uint32_t* sty = cb[sg.clip].sty;
+                const int r0 = p->r0 > 0 ? p->r0 : std::max(d.H, d.W);
+                const size_t off = sg.np > 0 ? ch.pairs[sg.pair0].fe_off : 0;
+                cudaStream_t side = branches ? be->side[q % be->side.size()] : nullptr;
+                auto on = [side](cudaStream_t s) { return side ? side : s; };
+                uint32_t *Fc = fe[0] + off, *Ec = fe[1] + off, *Fo = fe[2] + off, *Eo = fe[3] + off;
+                if (sg.np > 0) {
+                    be->steps.push_back([=](cudaStream_t s) {
+                        return fb::launch_nnf_init(k, d_pd, sg.pair0, sg.np, g, 0, nullptr, 0, 0, nullptr, seed, 0, Fc,
+                                                   Ec, on(s));
+                    });
+                    be->step_kind.push_back(FB_K_INIT);
+                    for (int it = 0; it < iters; ++it) {
+                        uint32_t *a = Fc, *ea = Ec, *b = Fo, *eb = Eo;
+                        be->steps.push_back([=](cudaStream_t s) {
+                            return fb::launch_nnf_iter(k, d_pd, sg.pair0, sg.np, g, r0, seed, 0, it, a, ea, b, eb, on(s));
+                        });
+                        be->step_kind.push_back(FB_K_ITER);
+                        std::swap(Fc, Fo);
+                        std::swap(Ec, Eo);
+                    }
+                }
+                const uint32_t* Ffin = Fc;
+                float* out = d.out;
+                be->steps.push_back([=](cudaStream_t s) {
+                    return fb::launch_combine(k, d_jd, sg.job0, sg.nj, d_pd, sg.pair0, Ffin, sty, d.H, d.W, out, on(s));
+                });
+                be->step_kind.push_back(FB_K_COMBINE);
+            }
+            if (branches) {
+                const std::vector<cudaStream_t> side = be->side;
+                be->steps.push_back([joins, side](cudaStream_t s) {
+                    cudaError_t e2 = cudaSuccess;
+                    for (size_t b = 0; b < side.size() && e2 == cudaSuccess; ++b) {
+                        e2 = cudaEventRecord(joins[b], side[b]);
+                        if (e2 == cudaSuccess) e2 = cudaStreamWaitEvent(s, joins[b], 0);
+                    }
+                    return e2;
+                });
+                be->step_kind.push_back(-1);
+            }
+            continue;
+        }
         const int v = variant_of[ch.k] >= 0 ? variant_of[ch.k] : 0;
+        const int claim = claim_of[ch.k] >= 0 ? claim_of[ch.k] : fb::kIterTilesPerClaim;
         std::vector<int32_t> u0, u1;
-        item_maps(ch, clips, fb::batch_variant_tile_h(v), fb::kIterTilesPerClaim, m0, m1);
+        item_maps(ch, clips, fb::batch_variant_tile_h(v), claim, m0, m1);
         item_maps(ch, clips, fb::batch_variant_tile_h(v), fb::kInitTilesPerClaim, u0, u1);
         if (!m0.empty()) {
             FB_CUDA(ctx, cudaMemcpyAsync(tabs[ci][1], m0.data(), sizeof(int32_t) * m0.size(), cudaMemcpyHostToDevice, st));
@@ -1307,7 +1538,8 @@ int build_entry(fb_ctx* ctx, const fb_clip_desc* clips, int n, const fb_params* 
                 uint32_t *a = Fc, *ea = Ec, *b = Fo, *eb = Eo;
                 int* cnt_it = next_counter++;
                 be->steps.push_back([=](cudaStream_t s) {
-                    return fb::launch_batch_iter(k, v, d_pairs, d_clips, d_ip, d_it, n_items, cnt_it, seed, it, a, ea, b, eb, grid, s);
+                    return fb::launch_batch_iter(k, v, d_pairs, d_clips, d_ip, d_it, n_items, claim, cnt_it, seed, it, a,
+                                                 ea, b, eb, grid, s);
                 });
                 be->step_kind.push_back(FB_K_ITER);
                 std::swap(Fc, Fo);
@@ -1512,6 +1744,16 @@ extern "C" int fb_ctx_set_pair_budget(fb_ctx* ctx, size_t bytes) {
     return FB_OK;
 }
 
+extern "C" int fb_ctx_batch_mode(const fb_ctx* ctx, int patch) {
+    if (!ctx || patch < 0 || patch > 9) return -1;
+    return ctx->tuned_mode[patch];
+}
+
+extern "C" int fb_ctx_batch_claim(const fb_ctx* ctx, int patch) {
+    if (!ctx || patch < 0 || patch > 9) return -1;
+    return ctx->tuned_claim[patch];
+}
+
 extern "C" int fb_ctx_batch_variant(const fb_ctx* ctx, int patch) {
     if (!ctx || patch < 0 || patch > 9) return -1;
     return ctx->tuned_variant[patch];
@@ -1521,9 +1763,14 @@ extern "C" int fb_blend_batch(fb_ctx* ctx, const fb_clip_desc* clips, int n_clip
                               const fb_params* p, uint32_t flags, void* stream) {
     if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
     ctx->err.clear();
-    if (flags & ~(FB_BATCH_NO_GRAPH | 0xFF00u)) return fail(ctx, FB_ERR_ARG, "unknown flags 0x%x", flags);
+    if (flags & ~(FB_BATCH_NO_GRAPH | 0xFF00u | 0xFF0000u | 0x3000000u))
+        return fail(ctx, FB_ERR_ARG, "unknown flags 0x%x", flags);
+    if (forced_mode(flags) > kModePerClip) return fail(ctx, FB_ERR_ARG, "launch mode %d outside [0, 1]", forced_mode(flags));
+    if (forced_mode(flags) == kModePerClip && (forced_variant(flags) >= 0 || forced_claim(flags) >= 0))
+        return fail(ctx, FB_ERR_ARG, "a tile variant or claim size applies to the persistent mode only");
     if (forced_variant(flags) >= fb::kBatchVariants)
         return fail(ctx, FB_ERR_ARG, "tile variant %d outside [0, %d)", forced_variant(flags), fb::kBatchVariants);
+    if (forced_claim(flags) > 64) return fail(ctx, FB_ERR_ARG, "claim of %d tiles outside [1, 64]", forced_claim(flags));
     DeviceGuard dg(ctx->device);
     int rc = check_clips(ctx, clips, n_clips, p, true);
     if (rc) return rc;

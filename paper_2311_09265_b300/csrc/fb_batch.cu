@@ -79,8 +79,8 @@ template <int K, int V>
 __global__ void __launch_bounds__(32 * Variant<V>::TH, BatchOcc<K, V>::value)
     batch_iter_kernel(const BatchPair* __restrict__ pairs, const BatchClip* __restrict__ clips,
                       const int32_t* __restrict__ item_pair, const int32_t* __restrict__ item_tile,
-                      int n_items, int* __restrict__ counter, uint32_t key0, uint32_t key1,
-                      uint32_t ctr_word, const uint32_t* __restrict__ Fp,
+                      int n_items, int per_claim, int* __restrict__ counter, uint32_t key0,
+                      uint32_t key1, uint32_t ctr_word, const uint32_t* __restrict__ Fp,
                       const uint32_t* __restrict__ Ep, uint32_t* __restrict__ Fn,
                       uint32_t* __restrict__ En) {
     using G = Geo<K>;
@@ -94,7 +94,7 @@ __global__ void __launch_bounds__(32 * Variant<V>::TH, BatchOcc<K, V>::value)
         int t1;
         {
             const int4 cg = ld_uniform(clips + ld_uniform(pairs + ip).x);  // H, W, N, r0
-            t1 = min(t0 + kIterTilesPerClaim, ((cg.y + 31) / 32) * ((cg.x + TH - 1) / TH));
+            t1 = min(t0 + per_claim, ((cg.y + 31) / 32) * ((cg.x + TH - 1) / TH));
         }
         // No barrier inside the unit: each thread runs through its pixels of the unit's
         // tiles and rejoins the block at q.next().
@@ -198,11 +198,11 @@ __global__ void __launch_bounds__(256)
 
 template <int K, int V>
 cudaError_t launch_iter_kv(const BatchPair* pairs, const BatchClip* clips, const int32_t* ip,
-                           const int32_t* it_, int n, int* counter, uint32_t k0, uint32_t k1,
-                           uint32_t cw, const uint32_t* Fp, const uint32_t* Ep, uint32_t* Fn,
-                           uint32_t* En, int grid, cudaStream_t st) {
-    batch_iter_kernel<K, V><<<grid, dim3(32, Variant<V>::TH), 0, st>>>(pairs, clips, ip, it_, n, counter,
-                                                                       k0, k1, cw, Fp, Ep, Fn, En);
+                           const int32_t* it_, int n, int per_claim, int* counter, uint32_t k0,
+                           uint32_t k1, uint32_t cw, const uint32_t* Fp, const uint32_t* Ep,
+                           uint32_t* Fn, uint32_t* En, int grid, cudaStream_t st) {
+    batch_iter_kernel<K, V><<<grid, dim3(32, Variant<V>::TH), 0, st>>>(pairs, clips, ip, it_, n, per_claim,
+                                                                       counter, k0, k1, cw, Fp, Ep, Fn, En);
     return cudaGetLastError();
 }
 
@@ -282,14 +282,16 @@ int batch_iter_blocks_per_sm(int k, int variant) {
 
 cudaError_t launch_batch_iter(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
                               const int32_t* item_pair, const int32_t* item_tile, int n_items,
-                              int* counter, uint64_t seed, int it, const uint32_t* Fp,
+                              int per_claim, int* counter, uint64_t seed, int it, const uint32_t* Fp,
                               const uint32_t* Ep, uint32_t* Fn, uint32_t* En, int grid,
                               cudaStream_t st) {
     if (n_items <= 0) return cudaSuccess;
+    if (per_claim < 1) return cudaErrorInvalidValue;
     const uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
     const uint32_t cw = static_cast<uint32_t>(it + 1) << 8;  // level 0
     FB_BATCH_DISPATCH(k, variant, (launch_iter_kv<KK, VV>(pairs, clips, item_pair, item_tile, n_items,
-                                                         counter, k0, k1, cw, Fp, Ep, Fn, En, grid, st)));
+                                                         per_claim, counter, k0, k1, cw, Fp, Ep, Fn, En,
+                                                         grid, st)));
 }
 
 cudaError_t launch_batch_init(int k, int variant, const BatchPair* pairs, const BatchClip* clips,

@@ -178,16 +178,18 @@ static_assert(sizeof(BatchJob) == 32, "BatchJob layout");
 constexpr int kBatchVariants = 4;
 // Consecutive tiles of one pair (or output frame) that one claim of a persistent batch
 // kernel covers: the claim's descriptor loads and block barrier are paid once per claim
-// instead of once per tile.  The remap reads F and styles around each pixel, so its
-// units stay one tile (neighbouring tiles then run side by side and share L1/L2 lines).  Work unit u of a launch is (unit_pair[u], first tile
-// unit_tile[u]) and covers tiles [first, min(first + per_claim, tiles of the pair)).
-#ifndef FB_ITER_TILES_PER_CLAIM
-#define FB_ITER_TILES_PER_CLAIM 4
-#endif
+// instead of once per tile.  The iteration kernel's claim size is chosen by the batch
+// autotuner among kIterClaimChoices (kIterTilesPerClaim when it is forced or not tuned);
+// the remap reads F and styles around each pixel, so its units stay one tile (neighbouring
+// tiles then run side by side and share L1/L2 lines).  Work unit u of a launch is
+// (unit_pair[u], first tile unit_tile[u]) and covers tiles
+// [first, min(first + per_claim, tiles of the pair)).
 #ifndef FB_COMBINE_TILES_PER_CLAIM
 #define FB_COMBINE_TILES_PER_CLAIM 1
 #endif
-constexpr int kIterTilesPerClaim = FB_ITER_TILES_PER_CLAIM;
+constexpr int kIterTilesPerClaim = 4;
+constexpr int kIterClaimChoices[] = {1, 2, 4, 8};
+constexpr int kIterClaimCount = 4;
 constexpr int kInitTilesPerClaim = 16;
 constexpr int kCombineTilesPerClaim = FB_COMBINE_TILES_PER_CLAIM;
 const char* batch_variant_name(int v);
@@ -200,7 +202,7 @@ cudaError_t launch_batch_init(int k, int variant, const BatchPair* pairs, const 
                               cudaStream_t st);
 cudaError_t launch_batch_iter(int k, int variant, const BatchPair* pairs, const BatchClip* clips,
                               const int32_t* item_pair, const int32_t* item_tile, int n_items,
-                              int* counter, uint64_t seed, int it, const uint32_t* Fp,
+                              int per_claim, int* counter, uint64_t seed, int it, const uint32_t* Fp,
                               const uint32_t* Ep, uint32_t* Fn, uint32_t* En, int grid,
                               cudaStream_t st);
 cudaError_t launch_batch_combine(int k, const BatchJob* jobs, const BatchPair* pairs,

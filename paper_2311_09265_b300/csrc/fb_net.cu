@@ -121,9 +121,9 @@ bool tma_conv_geom(const ConvGeom& g, const void* X, const void* Wt, tc::TmaConv
     return true;
 }
 
-template <int BN>
+template <int BN, class Epi = EpiFwd, bool FLIP = false>
 cudaError_t launch_conv_tma(const ConvGeom& g, const tc::TmaConvGeom& t, const bf16* X, const bf16* Wt,
-                            const EpiFwd& epi, int* status, cudaStream_t st, bool* used) {
+                            const Epi& epi, int* status, cudaStream_t st, bool* used) {
     *used = false;
     const auto encode = tensor_map_encoder();
     if (!encode) return cudaSuccess;
@@ -155,10 +155,10 @@ cudaError_t launch_conv_tma(const ConvGeom& g, const tc::TmaConvGeom& t, const b
     if (rx != CUDA_SUCCESS || rw != CUDA_SUCCESS)
         return cudaSuccess;  // not expressible as tensor maps: the gather path runs instead
     constexpr int smem = tc::conv_tma_smem_bytes<BN, kTmaStages>();
-    auto kern = cb == 64   ? tc::tc_conv_tma_kernel<BN, kTmaStages, 64, EpiFwd>
-                : cb == 32 ? tc::tc_conv_tma_kernel<BN, kTmaStages, 32, EpiFwd>
-                : cb == 16 ? tc::tc_conv_tma_kernel<BN, kTmaStages, 16, EpiFwd>
-                           : tc::tc_conv_tma_kernel<BN, kTmaStages, 8, EpiFwd>;
+    auto kern = cb == 64   ? tc::tc_conv_tma_kernel<BN, kTmaStages, 64, Epi, FLIP>
+                : cb == 32 ? tc::tc_conv_tma_kernel<BN, kTmaStages, 32, Epi, FLIP>
+                : cb == 16 ? tc::tc_conv_tma_kernel<BN, kTmaStages, 16, Epi, FLIP>
+                           : tc::tc_conv_tma_kernel<BN, kTmaStages, 8, Epi, FLIP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((t.M + tc::BM - 1) / tc::BM, (g.Cout + BN - 1) / BN);
@@ -194,6 +194,18 @@ cudaError_t conv_dgrad(const ConvGeom& g, const bf16* dZ, const bf16* WT, float*
                        int* status, cudaStream_t st) {
     const int M = g.n * g.H * g.W, K = 9 * g.Cout, ncb = (g.Cout + 63) / 64;
     EpiDgrad epi{dX, g.Cin, accumulate};
+    // Stride 1: the input gradient is the 3x3 convolution of dZ with the tap-mirrored
+    // transposed weights, staged by TMA like the forward layers (FLIP), where the boxes tile.
+    tc::TmaConvGeom t;
+    const ConvGeom gd{g.n, g.Ho, g.Wo, g.Cout, g.H, g.W, g.Cin, 1};
+    if (g.stride == 1 && g_gemm_path.load() == 0 && tma_conv_geom(gd, dZ, WT, t)) {
+        bool used = false;
+        cudaError_t e = gd.Cout <= 16   ? launch_conv_tma<16, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
+                        : gd.Cout <= 32 ? launch_conv_tma<32, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
+                        : gd.Cout <= 64 ? launch_conv_tma<64, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
+                                        : launch_conv_tma<128, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used);
+        if (e != cudaSuccess || used) return e;
+    }
     if (g.Cin <= 16) return launch_gemm_async<16>(GatherDgrad<16>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
     if (g.Cin <= 32) return launch_gemm_async<32>(GatherDgrad<32>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
     if (g.Cin <= 64) return launch_gemm_async<64>(GatherDgrad<64>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
@@ -214,9 +226,69 @@ cudaError_t conv_wgrad(const ConvGeom& g, const bf16* dZ, const bf16* X, float* 
 // ---------------------------------------------------------------------------------
 inline unsigned blocks(size_t n, unsigned per = 256) { return static_cast<unsigned>((n + per - 1) / per); }
 
-// Network input: DS x DS box means of both guides, scaled to [-0.5, 0.5], 8 channels.
+// Channel sums of the DS pixels (3 DS bytes, DS = 4 or 8) starting at p, read as 4- or
+// 8-byte words (3 DS is a multiple of 12 and p = 3 DS (W qx + ...) keeps them aligned).
+template <int DS>
+__device__ __forceinline__ void row_channel_sums(const uint8_t* __restrict__ p, uint32_t (&s)[3]) {
+    constexpr int WORDS = 3 * DS / 4;
+    const uint32_t* q = reinterpret_cast<const uint32_t*>(p);
+    uint32_t w[WORDS];
+    if constexpr (DS == 8) {
+#pragma unroll
+        for (int k = 0; k < WORDS / 2; ++k) {
+            const uint2 v = __ldg(reinterpret_cast<const uint2*>(q) + k);
+            w[2 * k] = v.x;
+            w[2 * k + 1] = v.y;
+        }
+    } else {
+#pragma unroll
+        for (int k = 0; k < WORDS; ++k) w[k] = __ldg(q + k);
+    }
+#pragma unroll
+    for (int b = 0; b < 3 * DS; ++b) s[b % 3] += (w[b >> 2] >> (8 * (b & 3))) & 0xFFu;
+}
+
+// Network input: DS x DS box means of both guides, scaled to [-0.5, 0.5], 8 channels.  The
+// block sums are exact integers, so the result does not depend on the summation order.
+template <int DS>
+__device__ __forceinline__ void box_means(const uint8_t* __restrict__ src, const uint8_t* __restrict__ tgt,
+                                         int W, int qy, int qx, bf16* __restrict__ o) {
+    uint32_t a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    for (int dy = 0; dy < DS; ++dy) {
+        const size_t p = (static_cast<size_t>(DS * qy + dy) * W + DS * qx) * 3;
+        row_channel_sums<DS>(src + p, a);
+        row_channel_sums<DS>(tgt + p, b);
+    }
+    const float scale = 1.f / (static_cast<float>(DS * DS) * 255.f);
+    for (int ch = 0; ch < 3; ++ch) {
+        o[ch] = __float2bfloat16_rn(static_cast<float>(a[ch]) * scale - 0.5f);
+        o[3 + ch] = __float2bfloat16_rn(static_cast<float>(b[ch]) * scale - 0.5f);
+    }
+    o[6] = o[7] = __float2bfloat16_rn(0.f);
+}
+
+// The same sums read byte by byte, for caller stacks that are not 8-byte aligned.
+__device__ __forceinline__ void box_means_bytes(const uint8_t* __restrict__ src, const uint8_t* __restrict__ tgt,
+                                                int W, int DS, int qy, int qx, bf16* __restrict__ o) {
+    uint32_t a[3] = {0, 0, 0}, b[3] = {0, 0, 0};
+    for (int dy = 0; dy < DS; ++dy)
+        for (int dx = 0; dx < DS; ++dx) {
+            const size_t p = (static_cast<size_t>(DS * qy + dy) * W + DS * qx + dx) * 3;
+            for (int ch = 0; ch < 3; ++ch) {
+                a[ch] += src[p + ch];
+                b[ch] += tgt[p + ch];
+            }
+        }
+    const float scale = 1.f / (static_cast<float>(DS * DS) * 255.f);
+    for (int ch = 0; ch < 3; ++ch) {
+        o[ch] = __float2bfloat16_rn(static_cast<float>(a[ch]) * scale - 0.5f);
+        o[3 + ch] = __float2bfloat16_rn(static_cast<float>(b[ch]) * scale - 0.5f);
+    }
+    o[6] = o[7] = __float2bfloat16_rn(0.f);
+}
+
 __global__ void prep_input_kernel(const uint8_t* __restrict__ src, const uint8_t* __restrict__ tgt,
-                                  int n, int H, int W, int DS, bf16* __restrict__ out) {
+                                  int n, int H, int W, int DS, int aligned, bf16* __restrict__ out) {
     const int Hq = H / DS, Wq = W / DS;
     const size_t total = static_cast<size_t>(n) * Hq * Wq;
     const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -224,25 +296,19 @@ __global__ void prep_input_kernel(const uint8_t* __restrict__ src, const uint8_t
     const int img = static_cast<int>(i / (static_cast<size_t>(Hq) * Wq));
     const int rem = static_cast<int>(i - static_cast<size_t>(img) * Hq * Wq);
     const int qy = rem / Wq, qx = rem % Wq;
-    float s[6] = {0, 0, 0, 0, 0, 0};
-    for (int dy = 0; dy < DS; ++dy)
-        for (int dx = 0; dx < DS; ++dx) {
-            const size_t p = ((static_cast<size_t>(img) * H + DS * qy + dy) * W + DS * qx + dx) * 3;
-            for (int ch = 0; ch < 3; ++ch) {
-                s[ch] += src[p + ch];
-                s[3 + ch] += tgt[p + ch];
-            }
-        }
-    bf16* o = out + i * 8;
-    const float scale = 1.f / (static_cast<float>(DS * DS) * 255.f);
-    for (int ch = 0; ch < 6; ++ch) o[ch] = __float2bfloat16_rn(s[ch] * scale - 0.5f);
-    o[6] = o[7] = __float2bfloat16_rn(0.f);
+    const size_t fsz = static_cast<size_t>(H) * W * 3;
+    if (!aligned)
+        box_means_bytes(src + img * fsz, tgt + img * fsz, W, DS, qy, qx, out + i * 8);
+    else if (DS == 8)
+        box_means<8>(src + img * fsz, tgt + img * fsz, W, qy, qx, out + i * 8);
+    else
+        box_means<4>(src + img * fsz, tgt + img * fsz, W, qy, qx, out + i * 8);
 }
 
 // The same input built from a guide stack and pairs [first, first + n) of a pair table.
 __global__ void prep_input_pairs_kernel(const uint8_t* __restrict__ guides,
                                         const fb::PairDesc* __restrict__ pairs, int first, int n,
-                                        int H, int W, int DS, bf16* __restrict__ out) {
+                                        int H, int W, int DS, int aligned, bf16* __restrict__ out) {
     const int Hq = H / DS, Wq = W / DS;
     const size_t total = static_cast<size_t>(n) * Hq * Wq;
     const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -254,19 +320,12 @@ __global__ void prep_input_pairs_kernel(const uint8_t* __restrict__ guides,
     const size_t fsz = static_cast<size_t>(H) * W * 3;
     const uint8_t* src = guides + static_cast<size_t>(pd.src) * fsz;
     const uint8_t* tgt = guides + static_cast<size_t>(pd.tgt) * fsz;
-    float s[6] = {0, 0, 0, 0, 0, 0};
-    for (int dy = 0; dy < DS; ++dy)
-        for (int dx = 0; dx < DS; ++dx) {
-            const size_t p = (static_cast<size_t>(DS * qy + dy) * W + DS * qx + dx) * 3;
-            for (int ch = 0; ch < 3; ++ch) {
-                s[ch] += src[p + ch];
-                s[3 + ch] += tgt[p + ch];
-            }
-        }
-    bf16* o = out + i * 8;
-    const float scale = 1.f / (static_cast<float>(DS * DS) * 255.f);
-    for (int ch = 0; ch < 6; ++ch) o[ch] = __float2bfloat16_rn(s[ch] * scale - 0.5f);
-    o[6] = o[7] = __float2bfloat16_rn(0.f);
+    if (!aligned)
+        box_means_bytes(src, tgt, W, DS, qy, qx, out + i * 8);
+    else if (DS == 8)
+        box_means<8>(src, tgt, W, qy, qx, out + i * 8);
+    else
+        box_means<4>(src, tgt, W, qy, qx, out + i * 8);
 }
 
 // Training targets from Alg. 1 fields: the mean offset F(x) - x over each DS x DS block,
@@ -560,7 +619,9 @@ int net_layers(fb_initnet* net, int n, cudaStream_t st);
 int net_forward(fb_initnet* net, const uint8_t* src, const uint8_t* tgt, int n, cudaStream_t st) {
     using namespace fb::net;
     const size_t Pq = static_cast<size_t>(n) * (net->H / net->ds) * (net->W / net->ds);
-    prep_input_kernel<<<blocks(Pq), 256, 0, st>>>(src, tgt, n, net->H, net->W, net->ds, net->act[0]);
+    // 8-byte aligned stacks (every frame then is: W is a multiple of 64) take vector loads
+    const int aligned = ((reinterpret_cast<uintptr_t>(src) | reinterpret_cast<uintptr_t>(tgt)) & 7) == 0;
+    prep_input_kernel<<<blocks(Pq), 256, 0, st>>>(src, tgt, n, net->H, net->W, net->ds, aligned, net->act[0]);
     NET_CUDA(net, cudaGetLastError());
     return net_layers(net, n, st);
 }
@@ -610,7 +671,7 @@ int initnet_init_pairs(::fb_initnet* net, const uint8_t* guides, const PairDesc*
     if (n < 1 || n > net->max_pairs) return FB_ERR_ARG;
     const size_t Pq = static_cast<size_t>(n) * (net->H / net->ds) * (net->W / net->ds);
     prep_input_pairs_kernel<<<blocks(Pq), 256, 0, st>>>(guides, pairs, first, n, net->H, net->W,
-                                                        net->ds, net->act[0]);
+                                                        net->ds, (reinterpret_cast<uintptr_t>(guides) & 7) == 0, net->act[0]);
     NET_CUDA(net, cudaGetLastError());
     int rc = net_layers(net, n, st);
     if (rc) return rc;

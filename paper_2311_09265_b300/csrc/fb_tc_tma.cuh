@@ -88,7 +88,10 @@ struct TmaConvGeom {
     int n;            // images
 };
 
-template <int BN, int S, int CB, class Epi>
+// FLIP = true mirrors every tap's displacement ((dy, dx) -> (2 - dy, 2 - dx)): the
+// stride-1 input gradient dX[p][ci] = sum_{tap, co} dZ[p + (1, 1) - tap][co] WT[ci][tap][co]
+// is this same GEMM over dZ with the transposed weights WT as the {9 Cout, Cin} matrix.
+template <int BN, int S, int CB, class Epi, bool FLIP = false>
 __global__ void __launch_bounds__(128)
     tc_conv_tma_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
                        Epi epi, TmaConvGeom g, int* status) {
@@ -149,7 +152,7 @@ __global__ void __launch_bounds__(128)
             mbar_expect_tx(&full[s], static_cast<uint32_t>((nq + nz) * COL + B_BYTES));
             for (int q = 0; q < nq; ++q) {
                 const int col = PER * c + q, tap = col / cpt, blk = col - tap * cpt;
-                const int dy = tap / 3, dx = tap - 3 * dy;
+                const int dy = FLIP ? 2 - tap / 3 : tap / 3, dx = FLIP ? 2 - (tap - 3 * (tap / 3)) : tap - 3 * dy;
                 tma_load_4d(sa + q * COL, &map_x, &full[s], CB * blk, dx - 1, g.stride * y0 + dy - 1, img0);
             }
             if (nz) tma_load_4d(sa + nq * COL, &map_x, &full[s], 0, 0, 0, g.n);  // wholly outside: zeros

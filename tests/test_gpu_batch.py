@@ -50,6 +50,8 @@ def test_batch_matches_per_clip_blend_and_oracle(fbp, clips):
     assert (got[0] == ref).all()
     for k in (3, 5, 7):
         assert 0 <= fbp.fb_ctx_batch_variant(ctx, k) < 4
+        assert fbp.fb_ctx_batch_claim(ctx, k) in (1, 2, 4, 8)
+        assert fbp.fb_ctx_batch_mode(ctx, k) in (0, 1)
     ctx.close()
 
 
@@ -86,6 +88,36 @@ def test_every_tile_variant_gives_identical_results(fbp, clips, variant):
     ctx.close()
 
 
+@pytest.mark.parametrize("claim", [1, 2, 3, 8, 64])
+def test_every_claim_size_gives_identical_results(fbp, clips, claim):
+    """The tuner's other knob, the tiles one claim of the persistent iteration kernel
+    covers, changes only the schedule (alone or with a forced variant)."""
+    ctx = fbp.Context(0)
+    params = fbp.Params.make(5, 2, 1, 0, 98)
+    want = per_clip(fbp, ctx, clips, params)
+    for flags in (fbp.FB_BATCH_CLAIM(claim), fbp.FB_BATCH_CLAIM(claim) | fbp.FB_BATCH_VARIANT(claim % 4)):
+        got = [o.cpu().numpy() for o in fbp.fb_blend_batch(ctx, clips, params, flags=flags)]
+        assert all((a == b).all() for a, b in zip(want, got))
+    assert fbp.fb_ctx_batch_claim(ctx, 5) == -1       # forced runs are not remembered as tuned
+    ctx.close()
+
+
+def test_per_clip_mode_gives_identical_results(fbp, clips):
+    """The tuner's launch-mode knob: per-clip launches of the per-call kernels (three graph
+    branches, or the caller's stream without a graph, and in many chunks) against the
+    persistent kernels and the per-clip loop."""
+    ctx = fbp.Context(0)
+    params = fbp.Params.make(5, 2, 1, 0, 97)
+    want = per_clip(fbp, ctx, clips, params)
+    for flags in (fbp.FB_BATCH_PER_CLIP, fbp.FB_BATCH_PER_CLIP | fbp.FB_BATCH_NO_GRAPH, fbp.FB_BATCH_PERSISTENT):
+        got = [o.cpu().numpy() for o in fbp.fb_blend_batch(ctx, clips, params, flags=flags)]
+        assert all((a == b).all() for a, b in zip(want, got)), flags
+    ctx.set_pair_budget(1 << 20)                 # segments cut at chunk boundaries
+    got = [o.cpu().numpy() for o in fbp.fb_blend_batch(ctx, clips, params, flags=fbp.FB_BATCH_PER_CLIP)]
+    assert all((a == b).all() for a, b in zip(want, got))
+    ctx.close()
+
+
 def test_chunked_batch_equals_single_chunk(fbp, clips):
     ctx = fbp.Context(0)
     params = fbp.Params.make(5, 2, 1, 0, 5)
@@ -103,6 +135,10 @@ def test_batch_argument_errors(fbp, clips):
     import torch
     ctx = fbp.Context(0)
     g, s, _, _ = clips[0]
+    for bad in (fbp.FB_BATCH_CLAIM(65), fbp.FB_BATCH_PER_CLIP | fbp.FB_BATCH_VARIANT(0), 3 << 24):
+        with pytest.raises(fbp.FastBlendError) as e:
+            fbp.fb_blend_batch(ctx, [(g, s, 3, 5)], fbp.Params.make(5, 2), flags=bad)
+        assert e.value.status == fbp.FB_ERR_ARG
     with pytest.raises(fbp.FastBlendError) as e:
         fbp.fb_blend_batch(ctx, [(g, s, 4, 5)], fbp.Params.make(5, 2))
     assert e.value.status == fbp.FB_ERR_ARG

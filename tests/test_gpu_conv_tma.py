@@ -85,3 +85,40 @@ def test_layers_the_tma_boxes_cannot_tile_use_the_gathers(fbp, n, H, W, Cin, Cou
 def test_gemm_path_argument_errors(fbp):
     with pytest.raises(fbp.FastBlendError):
         fbp.fb_conv_gemm_path(2)
+
+
+DGRAD_CASES = [  # n, H, W, Cin, Cout of stride-1 layers: the input gradient's boxes tile
+    (2, 64, 64, 8, 32), (2, 64, 64, 32, 32), (2, 32, 32, 64, 64), (3, 16, 16, 96, 96),
+    (4, 8, 8, 128, 128), (2, 64, 64, 96, 32), (2, 64, 64, 32, 8), (2, 32, 32, 40, 24),
+]
+
+
+@pytest.mark.parametrize("n,H,W,Cin,Cout", DGRAD_CASES)
+def test_tma_input_gradient_is_bit_identical_to_the_gather_path(fbp, n, H, W, Cin, Cout):
+    """Stride 1: the input gradient is the convolution of dZ with the tap-mirrored
+    transposed weights, staged by TMA (boxes displaced by the mirrored taps); it must
+    equal the cp.async gather path (same products, same order when Cout is a multiple of
+    16) and the FP64 oracle."""
+    import torch
+    rng = np.random.default_rng(n * 7 + H + Cin * 3 + Cout)
+    x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
+    w = ref.bf16(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin))
+    dz = ref.bf16(rng.normal(size=(n, H, W, Cout)))
+    wt = np.ascontiguousarray(np.transpose(w, (3, 1, 2, 0)))
+    out = {}
+    for mode in (1, 0):
+        fbp.fb_conv_gemm_path(mode)
+        n0 = fbp.fb_conv_gemm_path(-1)
+        dx, _, st = fbp.conv3x3_backward(to_bf16_tensor(x), to_bf16_tensor(wt), to_bf16_tensor(dz), 1)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        out[mode] = (dx.cpu().numpy(), fbp.fb_conv_gemm_path(-1) - n0)
+    fbp.fb_conv_gemm_path(0)
+    (dxg, used_g), (dxt, used_t) = out[1], out[0]
+    assert used_g == 0 and used_t == 1
+    if Cout % 16 == 0:
+        assert np.array_equal(dxt.view(np.uint32), dxg.view(np.uint32))
+    else:
+        assert float(np.linalg.norm(dxt - dxg) / np.linalg.norm(dxg)) < 1e-6
+    dx_ref, _, _ = ref.conv3x3_backward(x, w, dz, 1)
+    assert float(np.linalg.norm(dxt - dx_ref) / np.linalg.norm(dx_ref)) < 1e-5
