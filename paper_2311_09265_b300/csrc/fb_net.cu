@@ -181,6 +181,7 @@ cudaError_t conv_forward(const ConvGeom& g, const bf16* X, const bf16* Wt, const
         cudaError_t e = g.Cout <= 16   ? launch_conv_tma<16>(g, t, X, Wt, epi, status, st, &used)
                         : g.Cout <= 32 ? launch_conv_tma<32>(g, t, X, Wt, epi, status, st, &used)
                         : g.Cout <= 64 ? launch_conv_tma<64>(g, t, X, Wt, epi, status, st, &used)
+                        : g.Cout == 96 ? launch_conv_tma<96>(g, t, X, Wt, epi, status, st, &used)
                                        : launch_conv_tma<128>(g, t, X, Wt, epi, status, st, &used);
         if (e != cudaSuccess || used) return e;
     }
@@ -203,6 +204,7 @@ cudaError_t conv_dgrad(const ConvGeom& g, const bf16* dZ, const bf16* WT, float*
         cudaError_t e = gd.Cout <= 16   ? launch_conv_tma<16, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
                         : gd.Cout <= 32 ? launch_conv_tma<32, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
                         : gd.Cout <= 64 ? launch_conv_tma<64, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
+                        : gd.Cout == 96 ? launch_conv_tma<96, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
                                         : launch_conv_tma<128, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used);
         if (e != cudaSuccess || used) return e;
     }
@@ -423,18 +425,36 @@ __global__ void relu_bwd_kernel(const float* __restrict__ dA, const bf16* __rest
 }
 
 // db[c] += sum_p dZ[p][c]
-__global__ void bias_grad_kernel(const bf16* __restrict__ dZ, size_t P, int C, float* __restrict__ db) {
-    const int c = blockIdx.x;
-    float s = 0.f;
-    for (size_t p = threadIdx.x; p < P; p += blockDim.x) s += __bfloat162float(dZ[p * C + c]);
-    __shared__ float red[256];
-    red[threadIdx.x] = s;
-    __syncthreads();
-    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
-        if (static_cast<int>(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
-        __syncthreads();
+// db[c] += sum over the P pixels of dZ[p][c] (C a multiple of 8, at most 128).  Coalesced:
+// a pixel row's C / 8 threads each read 8 channels as one 16-byte load, a 256-thread block
+// walks 256 / (C / 8) rows at a time over a grid-strided range of pixels, reduces its rows in
+// shared memory and adds one partial sum per channel (fp32 atomics, like the weight
+// gradient's split sums: equal to the sequential sum up to rounding order).
+__global__ void __launch_bounds__(256) bias_grad_kernel(const bf16* __restrict__ dZ, size_t P, int C,
+                                                        float* __restrict__ db) {
+    __shared__ float part[256 * 8];
+    const int tpp = C / 8, rows = 256 / tpp;
+    const int t = static_cast<int>(threadIdx.x), r = t / tpp, u = t - r * tpp;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    if (r < rows) {
+        for (size_t p = static_cast<size_t>(blockIdx.x) * rows + r; p < P; p += static_cast<size_t>(gridDim.x) * rows) {
+            const uint4 v = __ldg(reinterpret_cast<const uint4*>(dZ + p * C + 8 * u));
+            const uint32_t w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                s[2 * j] += __uint_as_float(w[j] << 16);             // low bf16
+                s[2 * j + 1] += __uint_as_float(w[j] & 0xFFFF0000u);  // high bf16
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) part[r * C + 8 * u + j] = s[j];
     }
-    if (threadIdx.x == 0) db[c] += red[0];
+    __syncthreads();
+    if (t < C) {
+        float acc = 0.f;
+        for (int q = 0; q < rows; ++q) acc += part[q * C + t];
+        atomicAdd(db + t, acc);
+    }
 }
 
 // Smooth-L1 (Huber, delta 1 pixel) between 16 * head[..., 0:2] and the target offsets,
@@ -862,7 +882,11 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
         relu_bwd_kernel<<<blocks(out_elems), 256, 0, st>>>(dA, A ? A : net->act[0], out_elems,
                                                            kLayers[l].relu, net->dz);
         NET_CUDA(net, cudaGetLastError());
-        bias_grad_kernel<<<g.Cout, 256, 0, st>>>(net->dz, static_cast<size_t>(g.n) * g.Ho * g.Wo, g.Cout,
+        const size_t P = static_cast<size_t>(g.n) * g.Ho * g.Wo;
+        const size_t bg_rows = 256 / (g.Cout / 8);
+        const size_t bg_blocks = (P + bg_rows - 1) / bg_rows;
+        const unsigned bg_grid = static_cast<unsigned>(bg_blocks < 2048 ? bg_blocks : 2048);
+        bias_grad_kernel<<<bg_grid, 256, 0, st>>>(net->dz, P, g.Cout,
                                                  net->grads + net->b_off[l]);
         NET_CUDA(net, cudaGetLastError());
         NET_CUDA(net, conv_wgrad(g, net->dz, net->act[kIn[l]], net->grads + net->w_off[l], net->sms,

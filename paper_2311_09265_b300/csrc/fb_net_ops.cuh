@@ -255,17 +255,31 @@ struct GatherDgrad {
     }
 };
 
-// fp32 input gradient [M][Cin], written or added.
+// fp32 input gradient [M][Cin], written or added; 16-byte vectors where the 16 columns lie
+// inside the row (Cin % 8 == 0 keeps them aligned).
 struct EpiDgrad {
     float* dX;
     int Cin;
     int accumulate;
     __device__ __forceinline__ void store(int row, int col0, const float (&v)[16]) const {
+        float* d = dX + static_cast<size_t>(row) * Cin + col0;
+        if (col0 + 16 <= Cin && (Cin & 3) == 0) {
+            float4* d4 = reinterpret_cast<float4*>(d);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                float4 o = make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]);
+                if (accumulate) {
+                    const float4 a = d4[q];
+                    o = make_float4(a.x + o.x, a.y + o.y, a.z + o.z, a.w + o.w);
+                }
+                d4[q] = o;
+            }
+            return;
+        }
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
             if (col0 + j >= Cin) break;
-            float* d = dX + static_cast<size_t>(row) * Cin + col0 + j;
-            *d = accumulate ? *d + v[j] : v[j];
+            d[j] = accumulate ? d[j] + v[j] : v[j];
         }
     }
 };

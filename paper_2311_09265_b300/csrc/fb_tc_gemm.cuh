@@ -73,9 +73,8 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, long l
     return done != 0;
 }
 
-__device__ __forceinline__ bool mbar_wait_progress(uint64_t* bar, uint32_t parity) {
-    return mbar_wait(bar, parity, *static_cast<volatile long*>(&g_progress_wait_limit));
-}
+// The progress-wait limit, read once by a kernel (the host sets it between launches).
+__device__ __forceinline__ long progress_limit() { return g_progress_wait_limit; }
 
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t da, uint64_t db, uint32_t idesc,
                                          uint32_t accumulate) {
@@ -152,12 +151,13 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(Gather gather, Epi epi, in
     bool ok = true;
     int issued = 0;
     int last_commit = -1;  // thread 0: last chunk (relative) whose MMAs it committed
+    const long lim = progress_limit();
     for (int c = c_begin; c < c_end; ++c) {
         const int s = (c - c_begin) & 1;
         const int use = (c - c_begin) >> 1;  // how many times stage s was used before
         unsigned char* sa = smem + s * STAGE;
         unsigned char* sb = sa + A_BYTES;
-        if (use > 0 && ok) ok = mbar_wait_progress(&bars[s], (use - 1) & 1);  // MMAs of that stage done
+        if (use > 0 && ok) ok = mbar_wait(&bars[s], (use - 1) & 1, lim);  // MMAs of that stage done
         gather.load(sa, sb, c * BK, m0, n0);
         asm volatile("fence.proxy.async.shared::cta;");
         __syncthreads();
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(128) tc_gemm_kernel(Gather gather, Epi epi, in
     }
     if (issued > 0 && ok) {
         const int last = issued - 1;
-        ok = mbar_wait_progress(&bars[last & 1], (last >> 1) & 1);
+        ok = mbar_wait(&bars[last & 1], (last >> 1) & 1, lim);
     }
     if (!ok && lane == 0) atomicExch(status, 1);
     // After a timeout, let the MMAs already committed finish before TMEM is released (they
@@ -275,6 +275,7 @@ __global__ void __launch_bounds__(128) tc_gemm_async_kernel(Gather gather, Epi e
     }
     bool ok = true;
     int last_commit = -1;  // thread 0: last chunk whose MMAs it committed
+    const long lim = progress_limit();
     for (int i = 0; i < n_chunks; ++i) {
         const int s = i % S;
         cp_async_wait<LA - 1>();  // this thread's copies of chunk i have landed
@@ -293,7 +294,7 @@ __global__ void __launch_bounds__(128) tc_gemm_async_kernel(Gather gather, Epi e
         const int nxt = i + LA;
         const int prev = nxt - S;  // the chunk that last used nxt's stage
         if (nxt < n_chunks) {
-            if (prev >= 0 && ok) ok = mbar_wait_progress(&bars[prev % S], (prev / S) & 1);
+            if (prev >= 0 && ok) ok = mbar_wait(&bars[prev % S], (prev / S) & 1, lim);
             if (ok) {
                 const uint32_t sa = s0 + (nxt % S) * STAGE;
                 gather.load_async(gst, sa, sa + A_BYTES, nxt, n0);
@@ -302,7 +303,7 @@ __global__ void __launch_bounds__(128) tc_gemm_async_kernel(Gather gather, Epi e
         cp_async_commit();
     }
     cp_async_wait<0>();   // no copy of this thread is in flight past this point
-    if (n_chunks > 0 && ok) ok = mbar_wait_progress(&bars[(n_chunks - 1) % S], ((n_chunks - 1) / S) & 1);
+    if (n_chunks > 0 && ok) ok = mbar_wait(&bars[(n_chunks - 1) % S], ((n_chunks - 1) / S) & 1, lim);
     if (!ok && lane == 0) atomicExch(status, 1);
     // After a timeout, let the MMAs already committed finish before TMEM is released.
     if (!ok && threadIdx.x == 0 && last_commit >= 0)

@@ -144,6 +144,7 @@ __global__ void __launch_bounds__(128)
     if (threadIdx.x == 0) {
         bool ok = true;
         int issued = 0;   // chunks whose loads were issued
+        const long lim = progress_limit();
         auto issue = [&](int c) {
             const int s = c % S;
             const uint32_t sa = s0 + s * STAGE;
@@ -163,7 +164,7 @@ __global__ void __launch_bounds__(128)
         int done = 0;     // chunks whose MMAs were committed
         for (int i = 0; i < n_chunks && ok; ++i) {
             const int s = i % S;
-            ok = mbar_wait_progress(&full[s], (i / S) & 1);
+            ok = mbar_wait(&full[s], (i / S) & 1, lim);
             if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;");
             const uint32_t sa = s0 + s * STAGE, sb = sa + A_BYTES;
@@ -181,11 +182,11 @@ __global__ void __launch_bounds__(128)
             const int nxt = i + S - 1;
             if (nxt < n_chunks) {
                 const int prev = nxt - S;   // the chunk that last used nxt's stage
-                if (prev >= 0) ok = mbar_wait_progress(&empty[prev % S], (prev / S) & 1);
+                if (prev >= 0) ok = mbar_wait(&empty[prev % S], (prev / S) & 1, lim);
                 if (ok) issue(nxt);
             }
         }
-        if (ok && done > 0) ok = mbar_wait_progress(&empty[(done - 1) % S], ((done - 1) / S) & 1);
+        if (ok && done > 0) ok = mbar_wait(&empty[(done - 1) % S], ((done - 1) / S) & 1, lim);
         if (!ok) {
             // Let the MMAs already committed finish and the copies already issued land
             // before TMEM and the CTA's shared memory go away (each wait bounded).
