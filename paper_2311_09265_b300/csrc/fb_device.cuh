@@ -78,6 +78,15 @@ template <int K>
 __device__ __forceinline__ void load_row(const uint32_t* __restrict__ p,
                                          uint32_t (&out)[Geo<K>::NW]) {
     constexpr int NW = Geo<K>::NW;
+    if constexpr (Geo<K>::RPW == 8 && NW > 4) {
+        // k = 7, 9: the row sits in a 32-byte slot; one 256-bit load is one L1 request
+        // (a 16- plus an 8- or 16-byte load would be two for the same sector).
+        uint32_t w[8];
+        load_slot(p, w);
+#pragma unroll
+        for (int i = 0; i < NW; ++i) out[i] = w[i];
+        return;
+    }
     const uint4* q = reinterpret_cast<const uint4*>(p);
 #pragma unroll
     for (int v = 0; v < NW / 4; ++v) {
