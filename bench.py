@@ -55,7 +55,7 @@ LIMITER = {"k5": "L1TEX pipe 84-88 % of peak on scattered candidate loads (ncu);
 # kernel, from an ncu capture of the current kernel on a smaller case scaled by the pairs
 # per launch (see profiles/); None when not captured or when the workload is overridden.
 TRAFFIC_PER_LAUNCH = {"blend_512": 5.73e9, "tracking_512": 4.08e9, "balanced_512": 9.11e9,
-                      "aligned_1024x576": 8.24e9, "interp_1024x576": 2.40e9}
+                      "aligned_1024x576": 8.25e9, "interp_1024x576": 2.40e9}
 
 
 def parse_args(argv=None):

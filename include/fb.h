@@ -198,6 +198,41 @@ int fb_probe_ssd_mix(fb_ctx *ctx, int patch, double *byte_pairs_per_s, double *m
  * context.  The product libfb.so returns FB_ERR_UNSUPPORTED. */
 int fb_debug_candidates_considered(uint64_t *count, int reset);
 
+/* Checked builds: libfb_checked.so (compiled with FB_CHECKED) tests, on the device, the
+ * index and data invariants the NNF kernels rely on, at the sites below.  A failed check
+ * never traps: it records the first failure, counts it, and skips the access or the
+ * candidate it guards (a remap match is clamped as in every build), so the kernel runs to
+ * its end.  The sites:
+ *   FB_CHECK_CANDIDATE  a candidate match outside the image       (a = row, b = column)
+ *   FB_CHECK_SNAPSHOT   a stored match -- snapshot, coarser level, chain neighbour or
+ *                       partner -- outside its image              (a = row, b = column)
+ *   FB_CHECK_ENERGY     a stored error that is not the loss of its stored match (the
+ *                       Jacobi snapshot invariant E = L(F); a race or a stale buffer
+ *                       breaks it)                                (a = stored, b = loss)
+ *   FB_CHECK_SLOT       a paired row-patch slot row past the frame (a = slot row,
+ *                                                                  b = slot rows)
+ *   FB_CHECK_TABLE      a chain-neighbour or partner pair outside the launch
+ *                                                                 (a = pair, b = index)
+ *   FB_CHECK_REMAP      a match the remap (Alg. 2) reads outside the image
+ *                                                                 (a = row, b = column) */
+#define FB_CHECK_CANDIDATE 1u
+#define FB_CHECK_SNAPSHOT 2u
+#define FB_CHECK_ENERGY 3u
+#define FB_CHECK_SLOT 4u
+#define FB_CHECK_TABLE 5u
+#define FB_CHECK_REMAP 6u
+
+/* State of the device-side checks of a checked build on the current device, summed over
+ * the per-call and the batched kernels:
+ *   first      0, or the first failed check as (site << 56) | (a << 28) | b, with a and b
+ *              the low 28 bits of the site's two values (nullable)
+ *   failed     failed checks (nullable)
+ *   evaluated  pixel visits that ran the checks: one per pixel per NNF kernel launch and
+ *              one per remapped pixel per pair (nullable)
+ * reset != 0 zeroes all three after reading.  Synchronous; synchronise the streams of the
+ * checked calls first.  The product libfb.so returns FB_ERR_UNSUPPORTED. */
+int fb_check_status(uint64_t *first, uint64_t *failed, uint64_t *evaluated, int reset);
+
 /* Philox stream id of the ordered pair (source frame j -> target frame i), as used
  * by fb_blend_window and fb_interpolate: (j << 16) | i. */
 uint32_t fb_pair_tag(int j, int i);
@@ -216,6 +251,24 @@ uint32_t fb_pair_tag(int j, int i);
 int fb_nnf(fb_ctx *ctx, const uint8_t *src_guide, const uint8_t *tgt_guide, int H, int W,
            const fb_params *p, const int32_t *init_nnf, int32_t *nnf_out, uint32_t *err_out,
            void *stream);
+
+/* One Jacobi iteration of Alg. 1 (Sec. 3.2 parallel update) from a caller's snapshot:
+ * the step fb_nnf takes as its iteration `it` (0-based) at the finest level, on the same
+ * candidates, random stream (p->seed, p->pair_tag, it) and strict acceptance.
+ *   nnf_in   H x W x 2 int32 snapshot field (device); entries are clamped into the image.
+ *   err_in   H x W uint32 (device): the incumbents' errors, taken as given.  Only with
+ *            err_in = Eq. 1 of the (clamped) nnf_in is the step Alg. 1's; with that, the
+ *            output after iteration it - 1 of fb_nnf (levels = 1) stepped with `it` is
+ *            bit-identical to fb_nnf's output after iteration it.  Checked builds
+ *            (libfb_checked.so) verify the identity per pixel (FB_CHECK_ENERGY).
+ *   nnf_out, err_out  H x W x 2 int32 and H x W uint32 (device, written; may be nnf_in
+ *            and err_in: the snapshot is copied before the step).
+ *   p        patch, r0, seed and pair_tag are used; levels must be 1 and flags 0 (plain
+ *            loss), FB_ERR_ARG otherwise; iters is ignored.  it in [0, 65534].
+ * Async on `stream`. */
+int fb_nnf_step(fb_ctx *ctx, const uint8_t *src_guide, const uint8_t *tgt_guide, int H, int W,
+                const fb_params *p, int it, const int32_t *nnf_in, const uint32_t *err_in,
+                int32_t *nnf_out, uint32_t *err_out, void *stream);
 
 /* Alg. 1 under the improved loss of Sec. 3.4 ("balanced mode") for one pair:
  *   L(x) = alpha ||G_src[F(x)] - G_tgt[x]||^2 + ||S_src[F(x)] - S^[x]||^2

@@ -34,7 +34,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_initnet_get_optimizer", "fb_initnet_set_optimizer",
                     "fb_initnet_train_step", "fb_initnet_status", "fb_conv3x3_forward",
                     "fb_conv3x3_backward", "fb_ctx_set_initnet", "fb_ctx_energy",
-                    "fb_initnet_targets", "fb_debug_set_wait_limit")
+                    "fb_initnet_targets", "fb_debug_set_wait_limit", "fb_nnf_step", "fb_check_status")
 
 FB_FLAG_LEARNED_INIT = 0x1
 FB_FLAG_REPORT_ENERGY = 0x2
@@ -45,6 +45,9 @@ FB_FLAG_TRACKING = 0x20
 FB_FLAG_ALIGN = 0x40
 
 FB_BATCH_NO_GRAPH = 0x1
+
+# Device-side check sites of the checked build (fb_check_status).
+FB_CHECK_CANDIDATE, FB_CHECK_SNAPSHOT, FB_CHECK_ENERGY, FB_CHECK_SLOT, FB_CHECK_TABLE, FB_CHECK_REMAP = range(1, 7)
 
 
 def FB_BATCH_CLAIM(c: int) -> int:
@@ -136,6 +139,11 @@ def lib() -> ctypes.CDLL:
         L.fb_pair_tag.restype = ctypes.c_uint32
         P = ctypes.POINTER(Params)
         L.fb_nnf.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp, _vp, _vp]
+        L.fb_nnf_step.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, ctypes.c_int, _vp, _vp,
+                                  _vp, _vp, _vp]
+        L.fb_nnf_step.restype = ctypes.c_int
+        L.fb_check_status.argtypes = [ctypes.POINTER(ctypes.c_uint64)] * 3 + [ctypes.c_int]
+        L.fb_check_status.restype = ctypes.c_int
         L.fb_nnf_segment.argtypes = [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, ctypes.c_int, P,
                                      _vp, _vp, _vp, _vp]
         L.fb_nnf_balanced.argtypes = [_vp, _vp, _vp, _vp, ctypes.c_int, ctypes.c_int, P, _vp, _vp,
@@ -300,6 +308,18 @@ def fb_debug_candidates_considered(reset: bool = False) -> int:
     return int(v.value)
 
 
+def fb_check_status(reset: bool = False):
+    """(first failure word, failed checks, visits) of the device-side checks of a checked
+    build (libfb_checked.so); the first failure word is (site << 56) | (a << 28) | b, 0 if
+    none.  The product library raises FB_ERR_UNSUPPORTED."""
+    first, failed, evaluated = ctypes.c_uint64(), ctypes.c_uint64(), ctypes.c_uint64()
+    rc = lib().fb_check_status(ctypes.byref(first), ctypes.byref(failed), ctypes.byref(evaluated),
+                               1 if reset else 0)
+    if rc != FB_OK:
+        raise FastBlendError(rc, "fb_check_status")
+    return int(first.value), int(failed.value), int(evaluated.value)
+
+
 def fb_debug_set_wait_limit(polls: int) -> None:
     """Polls of the tensor-core kernels' progress waits on the current device (0: give up
     at once; < 0: the default); for exercising the timeout path."""
@@ -434,6 +454,27 @@ def fb_nnf(ctx: Context, src_guide: torch.Tensor, tgt_guide: torch.Tensor, param
                       _ptr(init_nnf, torch.int32, "init_nnf"),
                       _ptr(nnf_out, torch.int32, "nnf_out"), _ptr(err_out, torch.int32, "err_out"),
                       _stream_handle(stream, ctx.device))
+    ctx.check(rc)
+    return nnf_out, err_out
+
+
+def fb_nnf_step(ctx: Context, src_guide: torch.Tensor, tgt_guide: torch.Tensor, params: Params,
+                it: int, nnf_in: torch.Tensor, err_in: torch.Tensor, stream=None):
+    """One Jacobi iteration (index it) of Alg. 1 from the snapshot (nnf_in (H,W,2) int32,
+    err_in (H,W) int32 holding uint32 errors).  Returns (nnf, err) after the step."""
+    H, W = int(src_guide.shape[0]), int(src_guide.shape[1])
+    _shape(src_guide, (H, W, 3), "src_guide")
+    _shape(tgt_guide, (H, W, 3), "tgt_guide")
+    _shape(nnf_in, (H, W, 2), "nnf_in")
+    _shape(err_in, (H, W), "err_in")
+    dev = src_guide.device
+    nnf_out = torch.empty((H, W, 2), dtype=torch.int32, device=dev)
+    err_out = torch.empty((H, W), dtype=torch.int32, device=dev)
+    rc = lib().fb_nnf_step(ctx.handle, _ptr(src_guide, torch.uint8, "src_guide"),
+                           _ptr(tgt_guide, torch.uint8, "tgt_guide"), H, W, ctypes.byref(params), int(it),
+                           _ptr(nnf_in, torch.int32, "nnf_in"), _ptr(err_in, torch.int32, "err_in"),
+                           _ptr(nnf_out, torch.int32, "nnf_out"), _ptr(err_out, torch.int32, "err_out"),
+                           _stream_handle(stream, ctx.device))
     ctx.check(rc)
     return nnf_out, err_out
 

@@ -72,6 +72,17 @@ def build_debug(force: bool = False, verbose: bool = False) -> str:
     return _compile(DEBUG_LIB_PATH, defines=("FB_COUNT_EVALS",), verbose=verbose)
 
 
+CHECKED_LIB_PATH = os.path.join(PKG, "libfb_checked.so")
+
+
+def build_checked(force: bool = False, verbose: bool = False) -> str:
+    """libfb_checked.so: the same sources with FB_CHECKED (device-side invariant checks
+    that record failures in a status word instead of faulting; fb_check_status)."""
+    if not force and not _stale(CHECKED_LIB_PATH):
+        return CHECKED_LIB_PATH
+    return _compile(CHECKED_LIB_PATH, defines=("FB_CHECKED",), verbose=verbose)
+
+
 if __name__ == "__main__":
     build(force="--force" in sys.argv, verbose=True, ptxas_info="--ptxas" in sys.argv)
     print(LIB_PATH)

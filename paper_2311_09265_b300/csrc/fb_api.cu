@@ -1722,6 +1722,28 @@ extern "C" int fb_fast_plan(int N, int window, uint64_t* n_nnfs, uint64_t* n_ent
     return FB_OK;
 }
 
+// Checked builds: the device-side check words of the per-call and the batched kernels
+// (fb_check.cuh), combined; the product build reports FB_ERR_UNSUPPORTED.
+extern "C" int fb_check_status(uint64_t* first, uint64_t* failed, uint64_t* evaluated, int reset) {
+#ifdef FB_CHECKED
+    unsigned long long a[3] = {}, b[3] = {};
+    if (fb::check_read_kernels(a, reset != 0) != cudaSuccess || fb::check_read_batch(b, reset != 0) != cudaSuccess) {
+        cudaGetLastError();
+        return FB_ERR_CUDA;
+    }
+    if (first) *first = a[0] ? a[0] : b[0];
+    if (failed) *failed = a[1] + b[1];
+    if (evaluated) *evaluated = a[2] + b[2];
+    return FB_OK;
+#else
+    (void)first;
+    (void)failed;
+    (void)evaluated;
+    (void)reset;
+    return FB_ERR_UNSUPPORTED;
+#endif
+}
+
 extern "C" int fb_ctx_set_initnet(fb_ctx* ctx, fb_initnet* net) {
     if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
     ctx->init_net = net;
@@ -2041,6 +2063,54 @@ int fb_nnf(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int 
     rc = run_nnf(ctx, b, L, p, 0, 1, init_nnf, st, &F, &E);
     if (rc) return rc;
     FB_LAUNCH(ctx, st, FB_K_UNPACK, fb::launch_nnf_unpack(F, E, npx0, nnf_out, err_out, st));
+    return FB_OK;
+}
+
+int fb_nnf_step(fb_ctx* ctx, const uint8_t* src_guide, const uint8_t* tgt_guide, int H, int W,
+                const fb_params* p, int it, const int32_t* nnf_in, const uint32_t* err_in,
+                int32_t* nnf_out, uint32_t* err_out, void* stream) {
+    if (!ctx) return fail(nullptr, FB_ERR_ARG, "ctx is NULL");
+    ctx->err.clear();
+    int rc = check_params(ctx, p, H, W);
+    if (rc) return rc;
+    if (p->levels != 1) return fail(ctx, FB_ERR_ARG, "fb_nnf_step works on one level: levels must be 1");
+    if (p->flags != 0) return fail(ctx, FB_ERR_ARG, "fb_nnf_step takes the plain loss only: flags must be 0");
+    if (it < 0 || it > 65534) return fail(ctx, FB_ERR_ARG, "it must be in [0, 65534], got %d", it);
+    if (!src_guide || !tgt_guide || !nnf_in || !err_in || !nnf_out || !err_out)
+        return fail(ctx, FB_ERR_ARG, "fb_nnf_step takes six non-NULL arrays");
+    DeviceGuard dg(ctx->device);
+    for (const void* q : {static_cast<const void*>(src_guide), static_cast<const void*>(tgt_guide),
+                          static_cast<const void*>(nnf_in), static_cast<const void*>(err_in),
+                          static_cast<const void*>(nnf_out), static_cast<const void*>(err_out)})
+        if (classify(ctx, q) != Mem::Device)
+            return fail(ctx, FB_ERR_ARG, "fb_nnf_step takes device pointers of the context's device");
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const Levels L = level_dims(H, W, 1);
+    const size_t npx = static_cast<size_t>(H) * W;
+
+    Buffers b;
+    Carver measure(nullptr);
+    carve(measure, b, L, p->patch, 2, 0, 1, 1, 0, false, 0, 0, 0);
+    rc = ensure_arena(ctx, measure.off);
+    if (rc) return rc;
+    Carver cv(ctx->arena);
+    carve(cv, b, L, p->patch, 2, 0, 1, 1, 0, false, 0, 0, 0);
+
+    std::vector<PairDesc> pairs(1);
+    pairs[0] = PairDesc{0, 1, p->pair_tag, 0, 1u, {0, 0, 0}};
+    rc = upload_tables(ctx, pairs, {}, b, st);
+    if (rc) return rc;
+    rc = prep_guides(ctx, b, L, p->patch, src_guide, 1, 0, st);
+    if (rc) return rc;
+    rc = prep_guides(ctx, b, L, p->patch, tgt_guide, 1, 1, st);
+    if (rc) return rc;
+    FB_LAUNCH(ctx, st, FB_K_PACK, fb::launch_nnf_pack(nnf_in, H, W, b.FA, st));
+    FB_CUDA(ctx, cudaMemcpyAsync(b.EA, err_in, npx * sizeof(uint32_t), cudaMemcpyDeviceToDevice, st));
+    const LevelGeom g{H, W, b.rec[0]};
+    const int r0 = p->r0 > 0 ? p->r0 : (H > W ? H : W);
+    FB_LAUNCH(ctx, st, FB_K_ITER, fb::launch_nnf_iter(p->patch, b.pairs, 0, 1, g, r0, p->seed, 0, it, b.FA, b.EA,
+                                                      b.FB, b.EB, st));
+    FB_LAUNCH(ctx, st, FB_K_UNPACK, fb::launch_nnf_unpack(b.FB, b.EB, npx, nnf_out, err_out, st));
     return FB_OK;
 }
 

@@ -320,4 +320,10 @@ cudaError_t launch_batch_combine(int k, const BatchJob* jobs, const BatchPair* p
     return cudaGetLastError();
 }
 
+#ifdef FB_CHECKED
+cudaError_t check_read_batch(unsigned long long out[3], bool reset) {
+    return dev::check_read_unit(out, reset);
+}
+#endif
+
 }  // namespace fb

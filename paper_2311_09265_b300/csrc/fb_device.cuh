@@ -4,6 +4,7 @@
 
 #include <cstdint>
 
+#include "fb_check.cuh"
 #include "fb_internal.h"
 
 namespace fb {
@@ -51,6 +52,18 @@ struct Geo {
     static constexpr int RPW = (NW + 3) / 4 * 4;  // row-patch slot stride: 16-byte aligned
     static constexpr bool PAIRED = rowpatch_paired(K);  // k = 5: two rows per 32-byte slot
 };
+
+// Checked builds: the slots the patch at (r, c) reads lie inside the guide frame -- for
+// the paired layout slot rows r/2 .. r/2 + 2 of rowpatch_pair_rows(H), otherwise column c
+// of the (clamped) rows.  Always true in product builds.
+template <int K>
+__device__ __forceinline__ bool slots_inside(int r, int c, int H, int W) {
+    if constexpr (Geo<K>::PAIRED)
+        return FB_CHECK(r >= 0 && c >= 0 && c < W && (r >> 1) + 2 < rowpatch_pair_rows(H), FB_CHECK_SLOT,
+                        (r >> 1) + 2, rowpatch_pair_rows(H));
+    else
+        return FB_CHECK(c >= 0 && c < W, FB_CHECK_SLOT, c, W);
+}
 
 // One 32-byte slot of the paired layout (two row patches of 4 words).  A 256-bit load
 // is one request, like a 16-byte one, so the pair costs what one row did.  volatile:
@@ -121,6 +134,15 @@ template <int K>
 __device__ __forceinline__ void load_target(const uint32_t* __restrict__ rpt, int H, int W,
                                             int r, int c, TargetPatch<K>& t) {
     using G = Geo<K>;
+    if (!slots_inside<K>(r, c, H, W)) {  // checked builds only: an all-zero patch instead
+#pragma unroll
+        for (int a = 0; a < K; ++a) {
+#pragma unroll
+            for (int w = 0; w < G::NW; ++w) t.w[a][w] = 0;
+            t.row_e[a] = 0;
+        }
+        return;
+    }
     if constexpr (G::PAIRED) {
         // Rows r-2 .. r+2 are the clamped rows 2q-2 .. 2q-1 of slots q = r/2 + 0, 1, 2:
         // for even r they are halves 0..4 of the three slots, for odd r halves 1..5.
@@ -167,6 +189,7 @@ __device__ __forceinline__ bool patch_error_below(const uint32_t* __restrict__ r
                                                   int ur, int uc, const TargetPatch<K>& t,
                                                   uint32_t bound, uint32_t* e) {
     using G = Geo<K>;
+    if (!slots_inside<K>(ur, uc, H, W)) return false;
     uint32_t acc = 0;
     if constexpr (G::PAIRED) {
         // Source rows ur-2 .. ur+2 sit in slots q = ur/2 + L (L = 0, 1, 2), whose halves
@@ -262,6 +285,7 @@ __device__ __forceinline__ bool balanced_error_below(const uint32_t* __restrict_
                                                      const TargetPatch<K>& ts, uint32_t alpha,
                                                      uint32_t bound, uint32_t* e) {
     using G = Geo<K>;
+    if (!slots_inside<K>(ur, uc, H, W)) return false;
     uint32_t acc = 0;
     if constexpr (G::PAIRED) {
         // Slot order and row selection as patch_error_below: the two two-row slots first
@@ -408,6 +432,7 @@ __device__ __forceinline__ void search_pixel(const Err& err, int H, int W, int r
 #ifdef FB_COUNT_EVALS
         ++n_considered;
 #endif
+        if (!FB_CHECK(cr >= 0 && cr < H && cc >= 0 && cc < W, FB_CHECK_CANDIDATE, cr, cc)) return;
         const uint32_t f = pack_rc(cr, cc);
         if (f == bf) return;
         uint32_t e;
@@ -417,22 +442,36 @@ __device__ __forceinline__ void search_pixel(const Err& err, int H, int W, int r
         }
     };
 
+#ifdef FB_CHECKED
+    // The snapshot invariant: the incumbent lies in the image and be is its loss.
+    if (FB_CHECK(match_inside(bf, H, W), FB_CHECK_SNAPSHOT, row_of(bf), col_of(bf))) {
+        uint32_t e = 0;
+        err(row_of(bf), col_of(bf), 0xFFFFFFFFu, &e);
+        (void)FB_CHECK(e == be, FB_CHECK_ENERGY, be, e);
+    }
+    FB_CHECK_TALLY(1);
+#endif
+    // A neighbour's snapshot match outside the image (checked builds) is no candidate.
+    auto inside = [&](uint32_t f) {
+        return FB_CHECK(match_inside(f, H, W), FB_CHECK_SNAPSHOT, row_of(f), col_of(f));
+    };
+
     // Propagation: F'(x) = F(x + d) - d.
     if (r > 0) {
         const uint32_t f = Fpp[x - W];
-        consider(min(row_of(f) + 1, H - 1), col_of(f));
+        if (inside(f)) consider(min(row_of(f) + 1, H - 1), col_of(f));
     }
     if (r < H - 1) {
         const uint32_t f = Fpp[x + W];
-        consider(max(row_of(f) - 1, 0), col_of(f));
+        if (inside(f)) consider(max(row_of(f) - 1, 0), col_of(f));
     }
     if (c > 0) {
         const uint32_t f = Fpp[x - 1];
-        consider(row_of(f), min(col_of(f) + 1, W - 1));
+        if (inside(f)) consider(row_of(f), min(col_of(f) + 1, W - 1));
     }
     if (c < W - 1) {
         const uint32_t f = Fpp[x + 1];
-        consider(row_of(f), max(col_of(f) - 1, 0));
+        if (inside(f)) consider(row_of(f), max(col_of(f) - 1, 0));
     }
 
     extra(consider);
@@ -551,7 +590,8 @@ __device__ __forceinline__ void init_pixel(const uint32_t* __restrict__ rps,
         ur = static_cast<int>(__umulhi(u.x, static_cast<uint32_t>(H)));
         uc = static_cast<int>(__umulhi(u.y, static_cast<uint32_t>(W)));
     } else if (mode == 1) {
-        const uint32_t fc = coarse_Fp[static_cast<size_t>(r >> 1) * Wc + (c >> 1)];
+        uint32_t fc = coarse_Fp[static_cast<size_t>(r >> 1) * Wc + (c >> 1)];
+        if (!FB_CHECK(match_inside(fc, Hc, Wc), FB_CHECK_SNAPSHOT, row_of(fc), col_of(fc))) fc = 0u;
         ur = clampi(2 * row_of(fc) + (r & 1), 0, H - 1);
         uc = clampi(2 * col_of(fc) + (c & 1), 0, W - 1);
     } else {
@@ -565,6 +605,7 @@ __device__ __forceinline__ void init_pixel(const uint32_t* __restrict__ rps,
     Fp[x] = pack_rc(ur, uc);
     Ep[x] = e;
     FB_COUNT_CANDIDATES(1);
+    FB_CHECK_TALLY(1);
 }
 
 // Alg. 2 remap of one pair's style through its NNF at output pixel (r, c): the k^2
@@ -584,6 +625,7 @@ __device__ __forceinline__ void remap_votes(const uint32_t* __restrict__ Fq,
         for (int b = -P; b <= P; ++b) {
             const int qc = clampi(c + b, 0, W - 1);
             const uint32_t f = __ldg(Fq + static_cast<size_t>(qr) * W + qc);
+            (void)FB_CHECK(match_inside(f, H, W), FB_CHECK_REMAP, row_of(f), col_of(f));
             const int sr = clampi(row_of(f) - (qr - r), 0, H - 1);
             const int sc = clampi(col_of(f) - (qc - c), 0, W - 1);
             const uint32_t s = __ldg(S + static_cast<size_t>(sr) * W + sc);
@@ -594,6 +636,7 @@ __device__ __forceinline__ void remap_votes(const uint32_t* __restrict__ Fq,
     v0 = rb & 0xFFFFu;
     v1 = gx & 0xFFFFu;
     v2 = rb >> 16;
+    FB_CHECK_TALLY(1);
 }
 
 // Alg. 2 vote sums of a fast-mode table entry (three uint32 sums per 16-byte pixel).
@@ -610,6 +653,7 @@ __device__ __forceinline__ void remap_votes_u4(const uint32_t* __restrict__ Fq,
         for (int b = -P; b <= P; ++b) {
             const int qc = clampi(c + b, 0, W - 1);
             const uint32_t f = __ldg(Fq + static_cast<size_t>(qr) * W + qc);
+            (void)FB_CHECK(match_inside(f, H, W), FB_CHECK_REMAP, row_of(f), col_of(f));
             const int sr = clampi(row_of(f) - (qr - r), 0, H - 1);
             const int sc = clampi(col_of(f) - (qc - c), 0, W - 1);
             const uint4 s = __ldg(T + static_cast<size_t>(sr) * W + sc);
@@ -618,6 +662,7 @@ __device__ __forceinline__ void remap_votes_u4(const uint32_t* __restrict__ Fq,
             v2 += s.z;
         }
     }
+    FB_CHECK_TALLY(1);
 }
 
 // Fast-mode output: num / den per channel, one IEEE double division rounded once to float.

@@ -221,4 +221,12 @@ cudaError_t launch_dp4a_probe(int blocks, int iters, uint32_t* sink, cudaStream_
 // the patch-k kernels' per-candidate dp4a sequence (k = 5 or 7), 3k^2 byte pairs each.
 cudaError_t launch_ssd_mix_probe(int k, int blocks, int iters, uint32_t* sink, cudaStream_t st);
 
+#ifdef FB_CHECKED
+// Checked builds: the device-side check words (fb_check.cuh) of the per-call kernels
+// (fb_kernels.cu) and of the batched kernels (fb_batch.cu): first failure, failures,
+// visits; zeroed after reading if reset.
+cudaError_t check_read_kernels(unsigned long long out[3], bool reset);
+cudaError_t check_read_batch(unsigned long long out[3], bool reset);
+#endif
+
 }  // namespace fb

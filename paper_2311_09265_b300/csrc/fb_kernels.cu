@@ -139,6 +139,12 @@ __global__ void __launch_bounds__(256) style_rgbx_kernel(const uint8_t* __restri
 struct TileCoord {
     int r, c;
 };
+// Checked builds: pair index q (relative to the launch's first pair) of a chain neighbour
+// or partner of launch pair pl is one of the launch's gridDim.y pairs.
+__device__ __forceinline__ bool in_launch(int q, int pl) {
+    return FB_CHECK(q >= 0 && q < static_cast<int>(gridDim.y), FB_CHECK_TABLE, pl, q);
+}
+
 __device__ __forceinline__ TileCoord tile_coord(int W) {
     const int tiles_x = (W + TILE_W - 1) / TILE_W;
     TileCoord t;
@@ -220,8 +226,10 @@ __global__ void __launch_bounds__(TILE_THREADS, IterOccupancy<K>::value)
     const int pl = blockIdx.y;
     const PairDesc pd = pairs[pair0 + pl];
     const size_t npx = static_cast<size_t>(H) * W;
-    const uint32_t* prev = pd.pad[0] >= 0 ? Fp + static_cast<size_t>(pd.pad[0] - pair0) * npx : nullptr;
-    const uint32_t* next = pd.pad[1] >= 0 ? Fp + static_cast<size_t>(pd.pad[1] - pair0) * npx : nullptr;
+    const uint32_t* prev = pd.pad[0] >= 0 && in_launch(pd.pad[0] - pair0, pl)
+                               ? Fp + static_cast<size_t>(pd.pad[0] - pair0) * npx : nullptr;
+    const uint32_t* next = pd.pad[1] >= 0 && in_launch(pd.pad[1] - pair0, pl)
+                               ? Fp + static_cast<size_t>(pd.pad[1] - pair0) * npx : nullptr;
     iterate_pixel_tracking<K>(frame_rows<K>(rp, pd.src, H, W), frame_rows<K>(rp, pd.tgt, H, W), H, W, tc.r,
                               tc.c, pd.tag, r0, key0, key1, ctr_word, Fp + static_cast<size_t>(pl) * npx,
                               Ep + static_cast<size_t>(pl) * npx, prev, next,
@@ -354,10 +362,12 @@ __global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
     const size_t npx = static_cast<size_t>(H) * W;
     const size_t x = static_cast<size_t>(tc.r) * W + tc.c;
     const uint32_t* Fpp = Fp + static_cast<size_t>(pl) * npx;
-    const uint32_t* prev = TRACK && pd.pad[0] >= 0 ? Fp + static_cast<size_t>(pd.pad[0] - pair0) * npx + x : nullptr;
-    const uint32_t* next = TRACK && pd.pad[1] >= 0 ? Fp + static_cast<size_t>(pd.pad[1] - pair0) * npx + x : nullptr;
+    const uint32_t* prev = TRACK && pd.pad[0] >= 0 && in_launch(pd.pad[0] - pair0, pl)
+                               ? Fp + static_cast<size_t>(pd.pad[0] - pair0) * npx + x : nullptr;
+    const uint32_t* next = TRACK && pd.pad[1] >= 0 && in_launch(pd.pad[1] - pair0, pl)
+                               ? Fp + static_cast<size_t>(pd.pad[1] - pair0) * npx + x : nullptr;
     const TrackNeighbours extra{prev, next};
-    if (pd.pad[2] < 0) {
+    if (pd.pad[2] < 0 || !in_launch(pd.pad[2] - pair0, pl)) {
         TargetPatch<K> t;
         load_target<K>(frame_rows<K>(rp, pd.tgt, H, W), H, W, tc.r, tc.c, t);
         search_pixel<K>(PlainError<K>{frame_rows<K>(rp, pd.src, H, W), H, W, t}, H, W, tc.r, tc.c, pd.tag, r0,
@@ -366,7 +376,8 @@ __global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
         return;
     }
     const PairDesc po = pairs[pd.pad[2]];
-    const uint32_t fo = Fp[static_cast<size_t>(pd.pad[2] - pair0) * npx + x];
+    uint32_t fo = Fp[static_cast<size_t>(pd.pad[2] - pair0) * npx + x];
+    if (!FB_CHECK(match_inside(fo, H, W), FB_CHECK_SNAPSHOT, row_of(fo), col_of(fo))) fo = 0u;
     iterate_pixel_aligned<K>(frame_rows<K>(rp, pd.src, H, W), frame_rows<K>(srp, pd.style, H, W),
                              frame_rows<K>(rp, pd.tgt, H, W), frame_rows<K>(srp, po.style, H, W), fo, alpha, H,
                              W, tc.r, tc.c, pd.tag, r0, key0, key1, ctr_word, Fpp,
@@ -727,6 +738,14 @@ cudaError_t launch_combine(int k, const JobDesc* jobs, int job0, int n_jobs,
 }
 
 }  // namespace fb
+
+#ifdef FB_CHECKED
+namespace fb {
+cudaError_t check_read_kernels(unsigned long long out[3], bool reset) {
+    return dev::check_read_unit(out, reset);
+}
+}  // namespace fb
+#endif
 
 // Debug counter of considered candidates (see fb_device.cuh); the product build reports
 // FB_ERR_UNSUPPORTED.

@@ -40,6 +40,27 @@ def test_library_exports_every_declared_symbol(libfb):
     assert not missing, missing
 
 
+@pytest.mark.parametrize("variant", ["build_debug", "build_checked"])
+def test_diagnostic_variants_export_every_declared_symbol(variant):
+    """libfb_debug.so (candidate counter) and libfb_checked.so (device-side checks) are
+    the same sources under a define: same ABI."""
+    path = getattr(_build, variant)()
+    lib = ctypes.CDLL(path)
+    missing = [n for n in declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_product_library_reports_no_checks_without_touching_the_device(libfb):
+    v = ctypes.c_uint64()
+    assert libfb.fb_check_status(ctypes.byref(v), ctypes.byref(v), ctypes.byref(v), 0) == fbp.FB_ERR_UNSUPPORTED
+
+
+def test_nnf_step_rejects_a_null_context(libfb):
+    p = fbp.Params.make(5, 1)
+    rc = libfb.fb_nnf_step(None, None, None, 16, 16, ctypes.byref(p), 0, None, None, None, None, None)
+    assert rc == fbp.FB_ERR_ARG and b"ctx" in libfb.fb_last_error(None)
+
+
 def test_library_is_built_for_sm_103a_only():
     out = os.popen(f"cuobjdump --list-elf {_build.LIB_PATH} 2>/dev/null").read()
     if not out:

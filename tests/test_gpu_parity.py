@@ -86,6 +86,36 @@ def test_nnf_bit_exact_with_user_init(fbp, ctx):
     assert (Fg == Fo).all() and (Eg == Eo).all()
 
 
+@pytest.mark.parametrize("H,W,k,iters,r0", [(37, 53, 3, 3, 0), (61, 77, 5, 3, 0), (41, 45, 7, 2, 0),
+                                            (30, 33, 9, 2, 5), (5, 300, 5, 2, 0)])
+def test_nnf_step_chain_reproduces_the_oracle_iterations(fbp, ctx, H, W, k, iters, r0):
+    """fb_nnf_step from the oracle's initial field, stepped `iters` times, gives the
+    oracle's field and errors after each iteration (Sec. 3.2 Jacobi schedule, one
+    launch per step)."""
+    g, _ = synth.small_clip(2, H, W, seed=H + 7 * W + k, motion="affine")
+    tag = oracle.pair_tag(1, 0)
+    F, E = oracle.nnf(g[1], g[0], k, 0, r0=r0, seed=77, pair_tag=tag)
+    src, tgt = cuda(g[1]), cuda(g[0])
+    p = fbp.Params.make(k, 0, 1, r0, 77, tag)
+    Fd, Ed = cuda(F), cuda(E.view(np.int32))
+    for it in range(iters):
+        Fd, Ed = fbp.fb_nnf_step(ctx, src, tgt, p, it, Fd, Ed)
+        Fo, Eo = oracle.nnf(g[1], g[0], k, it + 1, r0=r0, seed=77, pair_tag=tag)
+        assert (host(Fd) == Fo).all() and (host(Ed).view(np.uint32) == Eo).all(), it
+
+
+def test_nnf_step_rejects_what_it_does_not_compute(fbp, ctx):
+    g, _ = synth.small_clip(2, 24, 24, seed=1)
+    src, tgt = cuda(g[1]), cuda(g[0])
+    F = cuda(np.zeros((24, 24, 2), np.int32))
+    E = cuda(np.zeros((24, 24), np.int32))
+    for p, it in [(fbp.Params.make(5, 1, 2), 0), (fbp.Params.make(5, 1, flags=fbp.FB_FLAG_TRACKING), 0),
+                  (fbp.Params.make(5, 1), -1), (fbp.Params.make(5, 1), 65535)]:
+        with pytest.raises(fbp.FastBlendError) as e:
+            fbp.fb_nnf_step(ctx, src, tgt, p, it, F, E)
+        assert e.value.status == fbp.FB_ERR_ARG
+
+
 def test_nnf_seed_and_tag_change_the_stream(fbp, ctx):
     g, _ = synth.small_clip(2, 32, 32, seed=3)
     a = gpu_nnf(fbp, ctx, g[0], g[1], 5, 1, seed=1, tag=1)[0]
