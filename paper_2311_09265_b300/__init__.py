@@ -826,19 +826,22 @@ def conv3x3_forward(x: torch.Tensor, w: torch.Tensor, bias: torch.Tensor, stride
     return y, status
 
 
-def conv3x3_backward(x: torch.Tensor, wt: torch.Tensor, dz: torch.Tensor, stride: int,
-                     status: Optional[torch.Tensor] = None):
-    """(dx f32, dw f32) of one conv layer; wt = weights transposed to [Cin,3,3,Cout] bf16."""
+def conv3x3_backward(x: torch.Tensor, wt: Optional[torch.Tensor], dz: torch.Tensor, stride: int,
+                     status: Optional[torch.Tensor] = None, input_grad: bool = True,
+                     weight_grad: bool = True):
+    """(dx f32 or None, dw f32 or None) of one conv layer; wt = weights transposed to
+    [Cin,3,3,Cout] bf16 (needed for dx only); input_grad / weight_grad select the two."""
     n, H, W, Cin = (int(v) for v in x.shape)
     Cout = int(dz.shape[-1])
     if status is None:
         status = torch.zeros(1, dtype=torch.int32, device=x.device)
-    dx = torch.empty((n, H, W, Cin), dtype=torch.float32, device=x.device)
-    dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device=x.device)
+    dx = torch.empty((n, H, W, Cin), dtype=torch.float32, device=x.device) if input_grad else None
+    dw = torch.zeros((Cout, 3, 3, Cin), dtype=torch.float32, device=x.device) if weight_grad else None
     rc = lib().fb_conv3x3_backward(_ptr(x, torch.bfloat16, "x"), n, H, W, Cin,
-                                   _ptr(wt, torch.bfloat16, "wt"), Cout, stride,
-                                   _ptr(dz, torch.bfloat16, "dz"), dx.data_ptr(), dw.data_ptr(),
-                                   status.data_ptr(), torch.cuda.current_stream().cuda_stream)
+                                   _ptr(wt, torch.bfloat16, "wt") if input_grad else None, Cout, stride,
+                                   _ptr(dz, torch.bfloat16, "dz"), dx.data_ptr() if input_grad else None,
+                                   dw.data_ptr() if weight_grad else None, status.data_ptr(),
+                                   torch.cuda.current_stream().cuda_stream)
     if rc != FB_OK:
         raise FastBlendError(rc, "fb_conv3x3_backward")
     return dx, dw, status

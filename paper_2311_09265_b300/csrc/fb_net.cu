@@ -101,9 +101,11 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // The TMA path needs whole output rows per 128-pixel tile: Wo divides 128 and either an
 // image holds a multiple of 128 output pixels (R = 128 / Wo rows) or 128 is a multiple
 // of the image (I images of R = Ho rows); 16-byte aligned tensors and strides
-// (Cin % 8 == 0); the strided box s Wo within the TMA limit of 256.
+// (Cin % 8 == 0); the strided box s Wo within the TMA limit of 256.  Output channels
+// beyond 128 take further tiles along grid.y (the input gradients of the concatenated
+// decoder layers: 160 and 224 channels).
 bool tma_conv_geom(const ConvGeom& g, const void* X, const void* Wt, tc::TmaConvGeom& t) {
-    if ((g.stride != 1 && g.stride != 2) || g.Cin % 8 || g.Wo < 1 || 128 % g.Wo || g.Cout > 128) return false;
+    if ((g.stride != 1 && g.stride != 2) || g.Cin % 8 || g.Wo < 1 || 128 % g.Wo) return false;
     if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(Wt)) & 15) return false;
     const int px = g.Ho * g.Wo;
     int R, I;
@@ -214,8 +216,93 @@ cudaError_t conv_dgrad(const ConvGeom& g, const bf16* dZ, const bf16* WT, float*
     return launch_gemm_async<128>(GatherDgrad<128>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
 }
 
+// The TMA-fed weight gradient (tc_wgrad_tma_kernel): both operands MN-major in 32-channel
+// boxes (channel counts padded to 32 by the boxes' zero fill; Cin and Cout multiples of 8
+// for 16-byte strides, Cout <= 128); the pixel chunks are the forward's 128-pixel tiles of
+// whole output rows or whole images.
+bool tma_wgrad_geom(const ConvGeom& g, const void* X, const void* dZ, int* R, int* I) {
+    if ((g.stride != 1 && g.stride != 2) || g.Cin % 8 || g.Cout % 8 || g.Cout > 128 || g.Wo < 1 || 128 % g.Wo)
+        return false;
+    if ((reinterpret_cast<uintptr_t>(X) | reinterpret_cast<uintptr_t>(dZ)) & 15) return false;
+    const int px = g.Ho * g.Wo;
+    if (px >= 128) {
+        if (px % 128) return false;
+        *R = 128 / g.Wo;
+        *I = 1;
+    } else {
+        if (128 % px) return false;
+        *R = g.Ho;
+        *I = 128 / px;
+    }
+    return g.stride * g.Wo <= 256 && g.stride * *R <= 256;
+}
+
+template <int NB>
+cudaError_t launch_wgrad_tma(const ConvGeom& g, int R, int I, const bf16* dZ, const bf16* X, float* dW, int sms,
+                             int* status, cudaStream_t st, bool* used) {
+    constexpr int S = NB <= 2 ? 4 : 3;
+    *used = false;
+    const auto encode = tensor_map_encoder();
+    if (!encode) return cudaSuccess;
+    alignas(64) CUtensorMap mx, mz;
+    const cuuint64_t xdim[4] = {static_cast<cuuint64_t>(g.Cin), static_cast<cuuint64_t>(g.W),
+                                static_cast<cuuint64_t>(g.H), static_cast<cuuint64_t>(g.n)};
+    const cuuint64_t xstr[3] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(g.W) * g.Cin * 2,
+                                static_cast<cuuint64_t>(g.H) * g.W * g.Cin * 2};
+    const cuuint32_t xbox[4] = {32u, static_cast<cuuint32_t>(g.stride * g.Wo), static_cast<cuuint32_t>(g.stride * R),
+                                static_cast<cuuint32_t>(I)};
+    const cuuint32_t xstep[4] = {1, static_cast<cuuint32_t>(g.stride), static_cast<cuuint32_t>(g.stride), 1};
+    const CUresult rx = encode(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), xdim, xstr, xbox,
+                               xstep, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const long long P = static_cast<long long>(g.n) * g.Ho * g.Wo;
+    const cuuint64_t zdim[2] = {static_cast<cuuint64_t>(g.Cout), static_cast<cuuint64_t>(P)};
+    const cuuint64_t zstr[1] = {static_cast<cuuint64_t>(g.Cout) * 2};
+    const cuuint32_t zbox[2] = {32u, 128u};
+    const cuuint32_t ones[2] = {1, 1};
+    const CUresult rz = encode(&mz, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(dZ), zdim, zstr, zbox,
+                               ones, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                               CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (rx != CUDA_SUCCESS || rz != CUDA_SUCCESS) return cudaSuccess;  // the gathered kernel runs instead
+    tc::TmaWgradGeom t{};
+    t.Cin = g.Cin;
+    t.Cp = (g.Cin + 31) / 32 * 32;
+    t.Cout = g.Cout;
+    t.rows = 9 * g.Cin;
+    t.HoWo = g.Ho * g.Wo;
+    t.Wo = g.Wo;
+    t.stride = g.stride;
+    t.chunks = static_cast<int>((P + 127) / 128);
+    // one CTA per SM (the stages fill most of its shared memory): at most one wave
+    const int mt = (9 * t.Cp + tc::BM - 1) / tc::BM;
+    const int splits_max = sms / mt > 0 ? sms / mt : 1;
+    t.per_split = (t.chunks + splits_max - 1) / splits_max;
+    const int splits = (t.chunks + t.per_split - 1) / t.per_split;
+    constexpr int smem = tc::wgrad_tma_smem_bytes<NB, S>();
+    auto kern = tc::tc_wgrad_tma_kernel<NB, S>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    kern<<<dim3(mt, splits), 128, smem, st>>>(mx, mz, dW, t, status);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        *used = true;
+        ++g_tma_launches;
+    }
+    return e;
+}
+
 cudaError_t conv_wgrad(const ConvGeom& g, const bf16* dZ, const bf16* X, float* dW, int sms,
                        int* status, cudaStream_t st) {
+    int R = 0, I = 0;
+    if (g_gemm_path.load() == 0 && tma_wgrad_geom(g, X, dZ, &R, &I)) {
+        bool used = false;
+        const int nb = (g.Cout + 31) / 32;
+        cudaError_t e = nb == 1   ? launch_wgrad_tma<1>(g, R, I, dZ, X, dW, sms, status, st, &used)
+                        : nb == 2 ? launch_wgrad_tma<2>(g, R, I, dZ, X, dW, sms, status, st, &used)
+                        : nb == 3 ? launch_wgrad_tma<3>(g, R, I, dZ, X, dW, sms, status, st, &used)
+                                  : launch_wgrad_tma<4>(g, R, I, dZ, X, dW, sms, status, st, &used);
+        if (e != cudaSuccess || used) return e;
+    }
     const int P = g.n * g.Ho * g.Wo, N = 9 * g.Cin;
     const int ntiles = (N + 127) / 128;
     const int splits = (2 * sms + ntiles - 1) / ntiles;

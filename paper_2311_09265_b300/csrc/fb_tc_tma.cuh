@@ -220,5 +220,174 @@ constexpr int conv_tma_smem_bytes() {
     return S * (BM * BK * 2 + BN * BK * 2) + 1024;
 }
 
+// ---------------------------------------------------------------------------------
+// Weight gradient of the 3x3 convolution, with both operands MN-major:
+//
+//   dW[co][tap][ci] = sum_p X[s p + tap - (1, 1)][ci] dZ[p][co]
+//
+// as the GEMM D[r][co] = sum_p A[r][p] B[co][p] with r = tap Cp + ci (M = 9 Cp rows,
+// tap-major, Cp = Cin rounded up to 32), N = 32 NB >= Cout and K = the output pixels p.
+// Neither operand is transposed: for a chunk of 128 consecutive output pixels (whole output
+// rows, as in the forward) the activation box {32 channels, s Wo, s R, I} of one tap --
+// displaced by the tap, zeros outside the image and past the last channel -- lands as 128
+// rows of 64 bytes, pixel-major, i.e. K rows of 32 contiguous M elements: the MN-major
+// layout in the 64-byte swizzle (8 K rows x 64 bytes per atom, atoms along K 512 bytes
+// apart).  A 128-row M tile is four such boxes (32-channel blocks of one or two taps), 8 KB
+// apart; the output gradient's box {32 channels, 128 pixels} of the [P][Cout] matrix (zeros
+// past Cout) is the same layout for B, NB boxes.  Rows of padding channels and columns past
+// Cout are computed as zeros and not stored.  Per chunk the elected thread issues eight K = 16 MMAs (start + 1 KB each) into
+// the 128 x Cout fp32 accumulator.  CTAs split the pixel axis (grid.y) and add their
+// partial sums to dW with fp32 atomics (dW is accumulated, as by the gathered kernel).
+// Waits, drains and the timeout report are those of the forward kernel.
+// ---------------------------------------------------------------------------------
+
+// Shared-memory matrix descriptor of an MN-major operand in the 64-byte swizzle layout:
+// atoms of 8 K rows x 64 bytes (32 MN elements); lbo bytes between atoms adjacent along
+// MN, sbo bytes between atoms adjacent along K; version 1 at bit 46, layout type 4.
+__device__ __forceinline__ uint64_t smem_desc_mn_sw64(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+    return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+           (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46) | (4ull << 61);
+}
+
+// Instruction descriptor of kind::f16 with both operands MN-major (bits 15 and 16).
+__host__ __device__ constexpr uint32_t instr_desc_mn(int n) { return instr_desc(n) | (1u << 15) | (1u << 16); }
+
+struct TmaWgradGeom {
+    int Cin, Cp;     // input channels, and rounded up to 32
+    int Cout;        // output channels (<= 32 NB)
+    int rows;        // 9 Cin: columns of dW
+    int HoWo, Wo;    // output pixels per image, output width
+    int stride;
+    int chunks;      // pixel chunks of 128 (the last may run past the last image: zeros)
+    int per_split;   // chunks per CTA along grid.y
+};
+
+constexpr int kWgradChunk = 128 * 64;          // bytes of one 32-wide box of 128 K rows
+constexpr int kWgradSlack = 16 * 1024;         // dynamic shared memory past the last stage
+
+template <int NB, int S>
+constexpr int wgrad_tma_smem_bytes() {
+    return S * (4 + NB) * kWgradChunk + 1024 + kWgradSlack;
+}
+
+template <int NB, int S>
+__global__ void __launch_bounds__(128)
+    tc_wgrad_tma_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_dz,
+                        float* __restrict__ dW, TmaWgradGeom g, int* status) {
+    static_assert(NB >= 1 && NB <= 4, "Cout = 32 NB");
+    static_assert(S >= 2 && S <= 4, "stages");
+    constexpr int BN = 32 * NB;
+    constexpr int A_BYTES = 4 * kWgradChunk;
+    constexpr int STAGE = A_BYTES + NB * kWgradChunk;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[S];
+    __shared__ __align__(8) uint64_t empty[S];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM;
+    const int c_begin = blockIdx.y * g.per_split;
+    const int c_end = min(g.chunks, c_begin + g.per_split);
+    if (c_begin >= c_end) return;                      // uniform over the CTA
+    const int n_local = c_end - c_begin;
+    const int na = min(4, (9 * g.Cp - m0) / 32);       // 32-row blocks of this M tile
+    const uint32_t s0 = (smem_u32(smem) + 1023u) & ~1023u;
+
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s]);
+            mbar_init(&empty[s]);
+        }
+        s_ok = 1;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TmemCols<BN>::value));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = instr_desc_mn(BN);
+
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        int issued = 0;   // local chunks whose loads were issued
+        const long lim = progress_limit();
+        auto issue = [&](int i) {
+            const int s = i % S;
+            const uint32_t sa = s0 + s * STAGE;
+            const int p0 = 128 * (c_begin + i);
+            const int img0 = p0 / g.HoWo;
+            const int y0 = (p0 - img0 * g.HoWo) / g.Wo;
+            mbar_expect_tx(&full[s], static_cast<uint32_t>((na + NB) * kWgradChunk));
+            for (int q = 0; q < na; ++q) {
+                const int r0 = m0 + 32 * q, tap = r0 / g.Cp, ci0 = r0 - tap * g.Cp;
+                const int dy = tap / 3, dx = tap - 3 * dy;
+                tma_load_4d(sa + q * kWgradChunk, &map_x, &full[s], ci0, dx - 1, g.stride * y0 + dy - 1, img0);
+            }
+#pragma unroll
+            for (int b = 0; b < NB; ++b)
+                tma_load_2d(sa + A_BYTES + b * kWgradChunk, &map_dz, &full[s], 32 * b, p0);
+            ++issued;
+        };
+        for (int i = 0; i < S - 1 && i < n_local; ++i) issue(i);
+        int done = 0;     // local chunks whose MMAs were committed
+        for (int i = 0; i < n_local && ok; ++i) {
+            const int s = i % S;
+            ok = mbar_wait(&full[s], (i / S) & 1, lim);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = s0 + s * STAGE, sb = sa + A_BYTES;
+#pragma unroll
+            for (int j = 0; j < 8; ++j)   // K rows 16 j .. 16 j + 15: two atoms along K
+                mma_bf16(tmem, smem_desc_mn_sw64(sa + 1024u * j, kWgradChunk, 512u),
+                         smem_desc_mn_sw64(sb + 1024u * j, kWgradChunk, 512u), idesc, (i > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+            ++done;
+            const int nxt = i + S - 1;
+            if (nxt < n_local) {
+                const int prev = nxt - S;   // the chunk that last used nxt's stage
+                if (prev >= 0) ok = mbar_wait(&empty[prev % S], (prev / S) & 1, lim);
+                if (ok) issue(nxt);
+            }
+        }
+        if (ok && done > 0) ok = mbar_wait(&empty[(done - 1) % S], ((done - 1) / S) & 1, lim);
+        if (!ok) {
+            if (done > 0) mbar_wait(&empty[(done - 1) % S], ((done - 1) / S) & 1);
+            for (int c = done; c < issued; ++c) mbar_wait(&full[c % S], (c / S) & 1);
+            s_ok = 0;
+            atomicExch(status, 1);
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (s_ok) {
+        const int rp = m0 + warp * 32 + lane, tap = rp / g.Cp, ci = rp - tap * g.Cp;
+        const bool real = rp < 9 * g.Cp && ci < g.Cin;   // not a padding channel
+        const int row = tap * g.Cin + ci;                 // column of dW
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+            if (real) {
+#pragma unroll
+                for (int j = 0; j < 16; ++j)
+                    if (c0 + j < g.Cout) atomicAdd(dW + static_cast<size_t>(c0 + j) * g.rows + row, v[j]);
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TmemCols<BN>::value));
+}
+
 }  // namespace tc
 }  // namespace fb

@@ -1,8 +1,9 @@
-"""The TMA-staged forward convolution (tiled TMA loads of the activation box displaced per
-tap and strided by the layer's stride, and of the weight box, 128-byte swizzle, tcgen05
-MMAs) against the cp.async gather
-path of the same GEMM, which accumulates the same products in the same order: the
-outputs must be bit-identical; and against the FP64 CPU oracle."""
+"""The TMA-staged convolutions against the gathered kernels of the same GEMMs and the
+FP64 CPU oracle.  Forward (tiled TMA loads of the activation box displaced per tap and
+strided by the layer's stride, and of the weight box, tcgen05 MMAs) and stride-1 input
+gradient: the same products in the same order as the gather path, so bit-identical.
+Weight gradient (both operands MN-major): the same products in another order, so equal to
+fp32 rounding.  Layers whose boxes do not tile run the gathered kernels."""
 import numpy as np
 import pytest
 
@@ -90,6 +91,7 @@ def test_gemm_path_argument_errors(fbp):
 DGRAD_CASES = [  # n, H, W, Cin, Cout of stride-1 layers: the input gradient's boxes tile
     (2, 64, 64, 8, 32), (2, 64, 64, 32, 32), (2, 32, 32, 64, 64), (3, 16, 16, 96, 96),
     (4, 8, 8, 128, 128), (2, 64, 64, 96, 32), (2, 64, 64, 32, 8), (2, 32, 32, 40, 24),
+    (2, 32, 32, 160, 64), (2, 16, 16, 224, 96),   # concatenated decoder inputs: two N tiles
 ]
 
 
@@ -109,7 +111,8 @@ def test_tma_input_gradient_is_bit_identical_to_the_gather_path(fbp, n, H, W, Ci
     for mode in (1, 0):
         fbp.fb_conv_gemm_path(mode)
         n0 = fbp.fb_conv_gemm_path(-1)
-        dx, _, st = fbp.conv3x3_backward(to_bf16_tensor(x), to_bf16_tensor(wt), to_bf16_tensor(dz), 1)
+        dx, _, st = fbp.conv3x3_backward(to_bf16_tensor(x), to_bf16_tensor(wt), to_bf16_tensor(dz), 1,
+                                         weight_grad=False)
         torch.cuda.synchronize()
         assert int(st.item()) == 0
         out[mode] = (dx.cpu().numpy(), fbp.fb_conv_gemm_path(-1) - n0)
@@ -122,3 +125,54 @@ def test_tma_input_gradient_is_bit_identical_to_the_gather_path(fbp, n, H, W, Ci
         assert float(np.linalg.norm(dxt - dxg) / np.linalg.norm(dxg)) < 1e-6
     dx_ref, _, _ = ref.conv3x3_backward(x, w, dz, 1)
     assert float(np.linalg.norm(dxt - dx_ref) / np.linalg.norm(dx_ref)) < 1e-5
+
+
+WGRAD_CASES = [  # n, H, W, Cin, Cout, stride: whole-row pixel chunks; channels padded to 32
+    (2, 64, 64, 32, 32, 1), (2, 64, 64, 96, 32, 1), (2, 32, 32, 64, 64, 1), (3, 16, 16, 96, 96, 1),
+    (4, 8, 8, 128, 128, 1), (2, 16, 16, 224, 96, 1), (2, 32, 32, 160, 64, 1), (2, 64, 64, 32, 64, 2),
+    (2, 32, 32, 64, 96, 2), (3, 16, 16, 96, 128, 2), (2, 64, 64, 8, 32, 1), (2, 64, 64, 32, 8, 1),
+    (2, 32, 32, 40, 24, 1), (1, 4, 32, 48, 16, 1), (3, 16, 16, 24, 8, 2),
+]
+
+
+@pytest.mark.parametrize("n,H,W,Cin,Cout,stride", WGRAD_CASES)
+def test_tma_weight_gradient_matches_the_gather_path_and_the_oracle(fbp, n, H, W, Cin, Cout, stride):
+    """The weight gradient with both operands MN-major, staged by TMA: the same products
+    as the gathered kernel, summed in another order (tensor-core K steps, pixel splits
+    added with fp32 atomics), so equal to it up to fp32 rounding, and to the FP64 oracle."""
+    import torch
+    rng = np.random.default_rng(n * 5 + H + Cin + 7 * Cout + stride)
+    x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
+    w = ref.bf16(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin))
+    Ho, Wo = ref.out_size(H, stride), ref.out_size(W, stride)
+    dz = ref.bf16(rng.normal(size=(n, Ho, Wo, Cout)))
+    out = {}
+    for mode in (1, 0):
+        fbp.fb_conv_gemm_path(mode)
+        n0 = fbp.fb_conv_gemm_path(-1)
+        _, dw, st = fbp.conv3x3_backward(to_bf16_tensor(x), None, to_bf16_tensor(dz), stride, input_grad=False)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        out[mode] = (dw.cpu().numpy(), fbp.fb_conv_gemm_path(-1) - n0)
+    fbp.fb_conv_gemm_path(0)
+    (dwg, used_g), (dwt, used_t) = out[1], out[0]
+    assert used_g == 0 and used_t == 1
+    assert float(np.linalg.norm(dwt - dwg) / np.linalg.norm(dwg)) < 2e-6
+    _, dw_ref, _ = ref.conv3x3_backward(x, w, dz, stride)
+    assert float(np.linalg.norm(dwt - dw_ref) / np.linalg.norm(dw_ref)) < 1e-5
+
+
+@pytest.mark.parametrize("n,H,W,Cin,Cout,stride", [(3, 9, 11, 32, 8, 1), (2, 17, 23, 32, 64, 2)])
+def test_weight_gradients_the_tma_boxes_cannot_tile_use_the_gathers(fbp, n, H, W, Cin, Cout, stride):
+    import torch
+    rng = np.random.default_rng(3)
+    x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
+    Ho, Wo = ref.out_size(H, stride), ref.out_size(W, stride)
+    dz = ref.bf16(rng.normal(size=(n, Ho, Wo, Cout)))
+    n0 = fbp.fb_conv_gemm_path(-1)
+    _, dw, st = fbp.conv3x3_backward(to_bf16_tensor(x), None, to_bf16_tensor(dz), stride, input_grad=False)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and fbp.fb_conv_gemm_path(-1) == n0
+    w = np.zeros((Cout, 3, 3, Cin))
+    _, dw_ref, _ = ref.conv3x3_backward(x, w, dz, stride)
+    assert float(np.linalg.norm(dw.cpu().numpy() - dw_ref) / np.linalg.norm(dw_ref)) < 1e-5

@@ -5,8 +5,8 @@ progress wait (operands landed, a stage free, the accumulator complete) gives up
 lets the MMAs it committed and the copies it issued finish (those drain waits keep the
 full limit), skips its epilogue, releases its tensor memory and raises the timeout flag.
 Here the progress limit is set to zero polls, so every such wait gives up at once:
-each kernel family (the TMA-fed forward, the cp.async-gathered forward and input
-gradient, the synchronous weight gradient, and a whole forward pass of the network)
+each kernel family (the TMA-fed forward and gradients, the cp.async-gathered forward and
+input gradient, the synchronous weight gradient, and a whole forward pass of the network)
 must report the timeout, the device must stay usable, and once the limit is restored
 the same calls must give the results they gave before.
 """
@@ -70,26 +70,35 @@ def test_forward_layer_times_out_then_recovers(fbp, expire, path):
         fbp.fb_conv_gemm_path(0)
 
 
-def test_backward_layer_times_out_then_recovers(fbp, expire):
-    """The input gradient (cp.async-gathered) and the weight gradient (synchronous)."""
+@pytest.mark.parametrize("path", [0, 1])   # 0: TMA-fed gradients, 1: gathered
+def test_backward_layer_times_out_then_recovers(fbp, expire, path):
+    """The input gradient and the weight gradient: the weight gradient alone, then both."""
     import torch
     x, w, _ = _layer(21, 2, 16, 16, 32, 64)
     wt = w.permute(3, 1, 2, 0).contiguous()
     g = torch.Generator().manual_seed(5)
     dz = torch.randn((2, 16, 16, 64), generator=g).to(torch.bfloat16).cuda()
-    dx0, dw0, st = fbp.conv3x3_backward(x, wt, dz, 1)
-    torch.cuda.synchronize()
-    assert int(st.item()) == 0
-    with expire():
-        _, _, st = fbp.conv3x3_backward(x, wt, dz, 1)
+    old = fbp.fb_conv_gemm_path(path)
+    try:
+        dx0, dw0, st = fbp.conv3x3_backward(x, wt, dz, 1)
         torch.cuda.synchronize()
-    assert int(st.item()) == 1
-    dx1, dw1, st = fbp.conv3x3_backward(x, wt, dz, 1)
-    torch.cuda.synchronize()
-    assert int(st.item()) == 0
-    assert torch.equal(dx1, dx0)
-    # the weight gradient sums K splits with fp32 atomics: equal up to their rounding
-    assert float((dw1 - dw0).abs().max()) <= 1e-5 * float(dw0.abs().max())
+        assert int(st.item()) == 0
+        for input_grad in (False, True):
+            tma0 = fbp.fb_conv_gemm_path(-1)
+            with expire():
+                _, _, st = fbp.conv3x3_backward(x, wt, dz, 1, input_grad=input_grad)
+                torch.cuda.synchronize()
+            assert int(st.item()) == 1
+            if path == 0:
+                assert fbp.fb_conv_gemm_path(-1) > tma0   # the TMA-fed kernels are the ones that ran
+        dx1, dw1, st = fbp.conv3x3_backward(x, wt, dz, 1)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        assert torch.equal(dx1, dx0)
+        # the weight gradient sums pixel splits with fp32 atomics: equal up to their rounding
+        assert float((dw1 - dw0).abs().max()) <= 1e-5 * float(dw0.abs().max())
+    finally:
+        fbp.fb_conv_gemm_path(0)
 
 
 def test_network_forward_reports_timeout_then_recovers(fbp, expire):
