@@ -475,8 +475,10 @@ __global__ void concat_up_kernel(const bf16* __restrict__ lo, int C1, const bf16
 }
 
 // Gradient of concat_up: dlo[n][h][w][C1] += sum over the 2x2 block, dskip += its part.
+// acc_lo / acc_skip: add to the gradient already in dlo / dskip, or write it (first writer).
 __global__ void concat_up_bwd_kernel(const float* __restrict__ dout, int C1, int C2, int n, int H2,
-                                     int W2, float* __restrict__ dlo, float* __restrict__ dskip) {
+                                     int W2, float* __restrict__ dlo, float* __restrict__ dskip, int acc_lo,
+                                     int acc_skip) {
     const int C = C1 + C2;
     const int H = H2 / 2, W = W2 / 2;
     const size_t lo_total = static_cast<size_t>(n) * H * W * C1;
@@ -492,12 +494,12 @@ __global__ void concat_up_bwd_kernel(const float* __restrict__ dout, int C1, int
         for (int dy = 0; dy < 2; ++dy)
             for (int dx = 0; dx < 2; ++dx)
                 s += dout[((static_cast<size_t>(img) * H2 + 2 * y + dy) * W2 + 2 * x + dx) * C + c];
-        dlo[i] += s;
+        dlo[i] = acc_lo ? dlo[i] + s : s;
     } else if (i < lo_total + sk_total) {
         const size_t j = i - lo_total;
         const int c = static_cast<int>(j % C2);
         const size_t p = j / C2;
-        dskip[j] += dout[p * C + C1 + c];
+        dskip[j] = acc_skip ? dskip[j] + dout[p * C + C1 + c] : dout[p * C + C1 + c];
     }
 }
 
@@ -956,8 +958,11 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
     const size_t Pq = static_cast<size_t>(n) * (net->H / net->ds) * (net->W / net->ds);
     NET_CUDA(net, cudaMemsetAsync(net->loss, 0, 4, st));
     NET_CUDA(net, cudaMemsetAsync(net->grads, 0, net->n_params * 4, st));
-    for (int t = 0; t < 15; ++t)
-        NET_CUDA(net, cudaMemsetAsync(net->dact[t], 0, tens_elems(net, t, n) * 4, st));
+    // Activation gradients need no clearing: the first kernel to reach a tensor writes it
+    // and later ones add (only the skip tensors of the stride-2 encoder layers receive two
+    // contributions, from the concatenation split and from the next layer's input gradient).
+    bool written[16] = {};
+    written[15] = true;   // the head's gradient, written by the loss kernel
     offset_loss_kernel<<<blocks(Pq), 256, 0, st>>>(net->head, target, weight, Pq, 1.f / weight_sum,
                                                    net->dact[15], net->loss);
     NET_CUDA(net, cudaGetLastError());
@@ -966,6 +971,7 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
         const size_t out_elems = static_cast<size_t>(g.n) * g.Ho * g.Wo * g.Cout;
         const float* dA = kOut[l] < 0 ? net->dact[15] : net->dact[kOut[l]];
         const bf16* A = kOut[l] < 0 ? nullptr : net->act[kOut[l]];
+        if (!written[kOut[l] < 0 ? 15 : kOut[l]]) return FB_ERR_CUDA;  // unreachable: every gradient is written first
         relu_bwd_kernel<<<blocks(out_elems), 256, 0, st>>>(dA, A ? A : net->act[0], out_elems,
                                                            kLayers[l].relu, net->dz);
         NET_CUDA(net, cudaGetLastError());
@@ -978,9 +984,11 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
         NET_CUDA(net, cudaGetLastError());
         NET_CUDA(net, conv_wgrad(g, net->dz, net->act[kIn[l]], net->grads + net->w_off[l], net->sms,
                                  net->status, st));
-        if (l > 0)
-            NET_CUDA(net, conv_dgrad(g, net->dz, net->wt + net->w_off[l], net->dact[kIn[l]], 1,
-                                     net->status, st));
+        if (l > 0) {
+            NET_CUDA(net, conv_dgrad(g, net->dz, net->wt + net->w_off[l], net->dact[kIn[l]],
+                                     written[kIn[l]] ? 1 : 0, net->status, st));
+            written[kIn[l]] = true;
+        }
         if (l == 8 || l == 9 || l == 10) {  // split the concatenated input's gradient
             const int lo = l == 8 ? 8 : (l == 9 ? 10 : 12);
             const int skip = l == 8 ? 6 : (l == 9 ? 4 : 2);
@@ -988,8 +996,10 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
             const int H2 = (net->H / net->ds) / kTens[cat].div, W2 = (net->W / net->ds) / kTens[cat].div;
             const size_t tot = tens_elems(net, lo, n) + tens_elems(net, skip, n);
             concat_up_bwd_kernel<<<blocks(tot), 256, 0, st>>>(net->dact[cat], kTens[lo].ch, kTens[skip].ch, n,
-                                                              H2, W2, net->dact[lo], net->dact[skip]);
+                                                              H2, W2, net->dact[lo], net->dact[skip],
+                                                              written[lo] ? 1 : 0, written[skip] ? 1 : 0);
             NET_CUDA(net, cudaGetLastError());
+            written[lo] = written[skip] = true;
         }
     }
     if (lr > 0.f) {
