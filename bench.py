@@ -56,6 +56,14 @@ LIMITER = {"k5": "L1TEX pipe 84-88 % of peak on scattered candidate loads (ncu);
 # per launch (see profiles/); None when not captured or when the workload is overridden.
 TRAFFIC_PER_LAUNCH = {"blend_512": 5.73e9, "tracking_512": 4.08e9, "balanced_512": 9.11e9,
                       "aligned_1024x576": 8.25e9, "interp_1024x576": 2.40e9}
+# 32-byte L1 sectors the plain iteration kernel loads per pixel of each pair and launch:
+# ncu l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum of the captured launch divided by its
+# pairs x pixels (k = 5: 1185.3 M / (168 x 512 x 512); k = 7: 729.1 M / (20 x 576 x 1024);
+# see profiles/).  A CPU replay of the k = 5 load sequence (slot order, early exit) gives
+# 26.5.  The L1 data pipe moves one such sector per wavefront, so sectors per second
+# against a live probe of scattered 32-byte loads is the gather roofline of these kernels.
+SECTORS_PER_PIXEL_ITER = {5: 26.92, 7: 61.81}
+GATHER_PROBE_BYTES = {"l1_resident": 64 * 1024, "l2_resident": 4 * 1024 * 1024}
 
 
 def parse_args(argv=None):
@@ -627,6 +635,9 @@ def run_gpu(args):
     rate, _ = ctx.probe_dp4a()
     # the ALU roofline of the instruction sequence the kernels actually issue (live probe)
     mix_rate = ctx.probe_ssd_mix(w.patch)[0] if w.patch in (5, 7) else None
+    plain_iter = not (balanced or accurate or tracking or aligned or fast or learned)
+    gather_rates = ({k: ctx.probe_gather(b)[0] for k, b in GATHER_PROBE_BYTES.items()}
+                    if plain_iter and w.patch in SECTORS_PER_PIXEL_ITER else None)
     iter_ms, iter_n = prof["iter"]
     kernel_total_ms = sum(v[0] for v in prof.values())
     # per launch of this rank (a frame shard launches its own range's pairs)
@@ -694,6 +705,21 @@ def run_gpu(args):
                                                                    (4 + w.random_search_radii())))
                 * args.steps * world / (total_ms / 1e3),
                 "probe_dp4a_per_s": rate}
+        if gather_rates and w.levels == 1:
+            pairs_launch = shard["pairs"] if shard else w.pairs()
+            sectors = SECTORS_PER_PIXEL_ITER[w.patch] * pairs_launch * w.H * w.W
+            got = sectors / avg_s
+            roof["gather"] = {
+                "sectors_per_pixel_iter": SECTORS_PER_PIXEL_ITER[w.patch],
+                "achieved_sectors_per_s": got,
+                "peak_l1_resident": gather_rates["l1_resident"],
+                "frac_l1_resident": got / gather_rates["l1_resident"],
+                "peak_l2_resident": gather_rates["l2_resident"],
+                "frac_l2_resident": got / gather_rates["l2_resident"],
+                "basis": ("32-byte L1 sectors per launch (ncu count of the captured launch, per pair "
+                          "and pixel) / the live launch time, against fb_probe_gather: independent "
+                          "scattered 256-bit loads at the kernel's occupancy over a 64 KiB "
+                          "(L1-resident) and a 4 MiB (L2-resident) buffer, measured live")}
 
     line = {
         "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": world,

@@ -189,6 +189,17 @@ int fb_probe_dp4a(fb_ctx *ctx, double *dp4a_per_s, double *ms);
  * other patch sizes.  Synchronous.  Not part of the method. */
 int fb_probe_ssd_mix(fb_ctx *ctx, int patch, double *byte_pairs_per_s, double *ms);
 
+/* Diagnostics: measures the device's rate of scattered 32-byte loads, the traffic of the
+ * patch-match kernels (every candidate patch row is a 256-bit load of a 32-byte row-patch
+ * slot at a data-dependent address): 5 resident 256-thread blocks per SM (the k = 5
+ * iteration kernel's occupancy), each thread issuing independent 256-bit loads of
+ * pseudo-randomly chosen slots of a `bytes`-sized buffer in the context's scratch.  A
+ * buffer that fits L1 measures the L1 data pipe (one 32-byte sector per wavefront); a
+ * larger one adds the L2.  Writes 32-byte sectors per second and the kernel's duration.
+ * bytes: a power of two in [1 KiB, 1 GiB] (FB_ERR_ARG otherwise).  Synchronous.  Not part
+ * of the method. */
+int fb_probe_gather(fb_ctx *ctx, size_t bytes, double *sectors_per_s, double *ms);
+
 /* Diagnostics of debug builds: libfb_debug.so (compiled with FB_COUNT_EVALS) counts,
  * in a device-global counter, every candidate the per-call NNF kernels consider -- one
  * per pixel and level for the initial match, then per pixel and iteration one per

@@ -34,7 +34,7 @@ HEADER_FUNCTIONS = ("fb_ctx_create", "fb_ctx_destroy", "fb_ctx_sync", "fb_last_e
                     "fb_initnet_get_optimizer", "fb_initnet_set_optimizer",
                     "fb_initnet_train_step", "fb_initnet_status", "fb_conv3x3_forward",
                     "fb_conv3x3_backward", "fb_ctx_set_initnet", "fb_ctx_energy",
-                    "fb_initnet_targets", "fb_debug_set_wait_limit", "fb_nnf_step", "fb_check_status")
+                    "fb_initnet_targets", "fb_debug_set_wait_limit", "fb_nnf_step", "fb_check_status", "fb_probe_gather")
 
 FB_FLAG_LEARNED_INIT = 0x1
 FB_FLAG_REPORT_ENERGY = 0x2
@@ -133,6 +133,9 @@ def lib() -> ctypes.CDLL:
         L.fb_probe_ssd_mix.argtypes = [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_double),
                                        ctypes.POINTER(ctypes.c_double)]
         L.fb_probe_ssd_mix.restype = ctypes.c_int
+        L.fb_probe_gather.argtypes = [_vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double),
+                                      ctypes.POINTER(ctypes.c_double)]
+        L.fb_probe_gather.restype = ctypes.c_int
         L.fb_debug_candidates_considered.argtypes = [ctypes.POINTER(ctypes.c_uint64), ctypes.c_int]
         L.fb_debug_candidates_considered.restype = ctypes.c_int
         L.fb_pair_tag.argtypes = [ctypes.c_int, ctypes.c_int]
@@ -393,6 +396,12 @@ class Context:
         kernels' per-candidate instruction sequence (k = 5 or 7)."""
         rate, ms = ctypes.c_double(), ctypes.c_double()
         self.check(lib().fb_probe_ssd_mix(self._h, patch, ctypes.byref(rate), ctypes.byref(ms)))
+        return rate.value, ms.value
+
+    def probe_gather(self, nbytes: int):
+        """(32-byte sectors/s, ms) of scattered 256-bit loads over an nbytes buffer."""
+        rate, ms = ctypes.c_double(), ctypes.c_double()
+        self.check(lib().fb_probe_gather(self._h, int(nbytes), ctypes.byref(rate), ctypes.byref(ms)))
         return rate.value, ms.value
 
     def set_initnet(self, net) -> None:

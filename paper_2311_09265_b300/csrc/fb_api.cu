@@ -2012,6 +2012,42 @@ int fb_probe_ssd_mix(fb_ctx* ctx, int patch, double* byte_pairs_per_s, double* m
     return FB_OK;
 }
 
+int fb_probe_gather(fb_ctx* ctx, size_t bytes, double* sectors_per_s, double* ms) {
+    if (!ctx || !sectors_per_s || !ms) return fail(ctx, FB_ERR_ARG, "NULL argument");
+    if (bytes < 1024 || bytes > (size_t(1) << 30) || (bytes & (bytes - 1)) != 0)
+        return fail(ctx, FB_ERR_ARG, "bytes must be a power of two in [1 KiB, 1 GiB], got %zu", bytes);
+    DeviceGuard dg(ctx->device);
+    int sms = 0;
+    FB_CUDA(ctx, cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, ctx->device));
+    const int blocks = sms * fb::kIterProbeBlocksPerSm, iters = 1 << 11;
+    Carver measure(nullptr);
+    measure.take<uint32_t>(bytes / 4);
+    measure.take<uint32_t>(blocks);
+    int rc = ensure_arena(ctx, measure.off);
+    if (rc) return rc;
+    Carver cv(ctx->arena);
+    uint32_t* buf = cv.take<uint32_t>(bytes / 4);
+    uint32_t* sink = cv.take<uint32_t>(blocks);
+    cudaEvent_t a = nullptr, b = nullptr;
+    FB_CUDA(ctx, cudaEventCreate(&a));
+    FB_CUDA(ctx, cudaEventCreate(&b));
+    FB_CUDA(ctx, cudaMemsetAsync(buf, 0x5A, bytes, nullptr));
+    const uint32_t slots = static_cast<uint32_t>(bytes / 32);
+    FB_CUDA(ctx, fb::launch_gather_probe(buf, slots, blocks, iters / 16, sink, nullptr));  // warm-up
+    FB_CUDA(ctx, cudaEventRecord(a, nullptr));
+    FB_CUDA(ctx, fb::launch_gather_probe(buf, slots, blocks, iters, sink, nullptr));
+    FB_CUDA(ctx, cudaEventRecord(b, nullptr));
+    FB_CUDA(ctx, cudaEventSynchronize(b));
+    float t = 0.f;
+    FB_CUDA(ctx, cudaEventElapsedTime(&t, a, b));
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    ctx->launches += 2;
+    *ms = t;
+    *sectors_per_s = static_cast<double>(blocks) * 256.0 * iters * 4.0 / (t * 1e-3);
+    return FB_OK;
+}
+
 uint32_t fb_pair_tag(int j, int i) {
     return (static_cast<uint32_t>(j) << 16) | static_cast<uint32_t>(i & 0xFFFF);
 }

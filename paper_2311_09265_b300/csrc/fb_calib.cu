@@ -94,6 +94,31 @@ __global__ void __launch_bounds__(256) ssd_mix_probe_kernel(uint32_t seed, uint3
     if (total == 0x12345678u) sink[blockIdx.x] = total;  // practically never taken; defeats DCE
 }
 
+
+// Scattered 32-byte loads, the L1 traffic of the patch-match kernels: per round every
+// thread issues four independent 256-bit loads of pseudo-randomly chosen 32-byte slots of
+// a buffer of mask + 1 slots (indices masked into it), so the loads' latency overlaps and
+// the rate of the L1 data pipe (or, for buffers beyond L1, of L2) is what is measured.
+__global__ void __launch_bounds__(256) gather_probe_kernel(const uint32_t* __restrict__ buf, uint32_t mask,
+                                                           int iters, uint32_t* __restrict__ sink) {
+    uint32_t x = (blockIdx.x * blockDim.x + threadIdx.x) * 2654435761u + 12345u;
+    uint32_t acc = 0;
+    for (int i = 0; i < iters; ++i) {
+        uint32_t w[4][8];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            x = x * 1664525u + 1013904223u;
+            const uint32_t* p = buf + static_cast<size_t>((x >> 7) & mask) * 8;
+            asm volatile("ld.global.nc.v8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                         : "=r"(w[q][0]), "=r"(w[q][1]), "=r"(w[q][2]), "=r"(w[q][3]), "=r"(w[q][4]),
+                           "=r"(w[q][5]), "=r"(w[q][6]), "=r"(w[q][7])
+                         : "l"(p));
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc ^= w[q][0] ^ w[q][3] ^ w[q][7];
+    }
+    if (acc == 0x12345678u) sink[blockIdx.x] = acc;  // practically never taken; keeps the loads
+}
 }  // namespace
 
 cudaError_t launch_ssd_mix_probe(int k, int blocks, int iters, uint32_t* sink, cudaStream_t st) {
@@ -108,6 +133,13 @@ cudaError_t launch_ssd_mix_probe(int k, int blocks, int iters, uint32_t* sink, c
 
 cudaError_t launch_dp4a_probe(int blocks, int iters, uint32_t* sink, cudaStream_t st) {
     dp4a_probe_kernel<<<blocks, 256, 0, st>>>(0xC0FFEEu, iters, sink);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_gather_probe(const uint32_t* buf, uint32_t slots, int blocks, int iters, uint32_t* sink,
+                                cudaStream_t st) {
+    if (slots == 0 || (slots & (slots - 1)) != 0) return cudaErrorInvalidValue;
+    gather_probe_kernel<<<blocks, 256, 0, st>>>(buf, slots - 1, iters, sink);
     return cudaGetLastError();
 }
 

@@ -216,10 +216,15 @@ int batch_iter_blocks_per_sm(int k, int variant);
 
 // dp4a throughput probe (fb_calib.cu): blocks x 256 threads x iters x chains dp4a.
 constexpr int kDp4aProbeChains = 32;
+// Resident 256-thread blocks per SM of the gather probe: those of the k = 5 iteration kernel.
+constexpr int kIterProbeBlocksPerSm = 5;
 cudaError_t launch_dp4a_probe(int blocks, int iters, uint32_t* sink, cudaStream_t st);
 // Eq. 1 instruction-sequence probe (fb_calib.cu): blocks x 256 threads x iters candidates of
 // the patch-k kernels' per-candidate dp4a sequence (k = 5 or 7), 3k^2 byte pairs each.
 cudaError_t launch_ssd_mix_probe(int k, int blocks, int iters, uint32_t* sink, cudaStream_t st);
+// Scattered 256-bit loads of a buffer of `slots` (a power of two) 32-byte slots.
+cudaError_t launch_gather_probe(const uint32_t* buf, uint32_t slots, int blocks, int iters, uint32_t* sink,
+                                cudaStream_t st);
 
 #ifdef FB_CHECKED
 // Checked builds: the device-side check words (fb_check.cuh) of the per-call kernels
