@@ -619,7 +619,8 @@ int fb_conv_gemm_path(int mode, uint64_t *tma_launches);
 #define FB_NOALLOC_SCRATCH_BYTES ((size_t)64 << 20)
 
 /* fb_blend_window without a context or any device allocation, for callers that cannot
- * allocate device memory.  The paper has no counterpart to this entry point.  Some callers are not allowed to call cudaMalloc or any allocator where they
+ * allocate device memory.  The paper has no counterpart to this entry point.  Some
+ * callers are not allowed to call cudaMalloc or any allocator where they
  * blend (a host callback or stream-ordered pipeline that must not synchronise the
  * device, a plug-in whose host application owns all device memory, a process held to
  * a device-memory budget fixed at start-up), and every other entry point here needs a

@@ -347,15 +347,19 @@ __device__ __forceinline__ bool balanced_error_below(const uint32_t* __restrict_
             uint32_t sg[G::NW], sst[G::NW];
             load_row<K>(rpg + (static_cast<size_t>(rr) * W + uc) * G::RPW, sg);
             load_row<K>(rpss + (static_cast<size_t>(rr) * W + uc) * G::RPW, sst);
-            uint32_t gd = 0, gs = 0, sd = 0, ss = 0;
+            // |t|^2 of both target rows recomputed per candidate: two held row energies per
+            // row would cost 2k registers, which the two target patches cannot spare.
+            uint32_t gd = 0, gs = 0, gt = 0, sd = 0, ss = 0, st = 0;
 #pragma unroll
             for (int w = 0; w < G::NW; ++w) {
                 gd = __dp4a(sg[w], tg.w[a][w], gd);
                 gs = __dp4a(sg[w], sg[w], gs);
+                gt = __dp4a(tg.w[a][w], tg.w[a][w], gt);
                 sd = __dp4a(sst[w], ts.w[a][w], sd);
                 ss = __dp4a(sst[w], sst[w], ss);
+                st = __dp4a(ts.w[a][w], ts.w[a][w], st);
             }
-            acc += alpha * (gs + tg.row_e[a] - 2u * gd) + (ss + ts.row_e[a] - 2u * sd);
+            acc += alpha * (gs + gt - 2u * gd) + (ss + st - 2u * sd);
             if (acc >= bound) return false;
         }
     }

@@ -54,7 +54,7 @@ int scratch_address(unsigned char** out) {
     return FB_OK;
 }
 
-// Pair and job tables of Eq. 2, built on the device (no host staging buffer): output
+// Pair and job tables of the window blend, built on the device (no host staging buffer): output
 // frame i owns the pairs (j -> i), j in [max(0, i-M), min(N-1, i+M)], j != i, in
 // increasing j, after the pairs of frames 0 .. i-1.
 __global__ void blend_tables_kernel(int N, int M, int k, PairDesc* __restrict__ pairs,
