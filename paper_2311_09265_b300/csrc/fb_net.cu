@@ -193,27 +193,32 @@ cudaError_t conv_forward(const ConvGeom& g, const bf16* X, const bf16* Wt, const
     return launch_gemm_async<128>(GatherFwd<128>{X, Wt, g, M, K, ncb}, epi, M, g.Cout, K, status, st);
 }
 
-cudaError_t conv_dgrad(const ConvGeom& g, const bf16* dZ, const bf16* WT, float* dX, int accumulate,
-                       int* status, cudaStream_t st) {
+template <class Epi>
+cudaError_t conv_dgrad_epi(const ConvGeom& g, const bf16* dZ, const bf16* WT, const Epi& epi, int* status,
+                           cudaStream_t st) {
     const int M = g.n * g.H * g.W, K = 9 * g.Cout, ncb = (g.Cout + 63) / 64;
-    EpiDgrad epi{dX, g.Cin, accumulate};
     // Stride 1: the input gradient is the 3x3 convolution of dZ with the tap-mirrored
     // transposed weights, staged by TMA like the forward layers (FLIP), where the boxes tile.
     tc::TmaConvGeom t;
     const ConvGeom gd{g.n, g.Ho, g.Wo, g.Cout, g.H, g.W, g.Cin, 1};
     if (g.stride == 1 && g_gemm_path.load() == 0 && tma_conv_geom(gd, dZ, WT, t)) {
         bool used = false;
-        cudaError_t e = gd.Cout <= 16   ? launch_conv_tma<16, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
-                        : gd.Cout <= 32 ? launch_conv_tma<32, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
-                        : gd.Cout <= 64 ? launch_conv_tma<64, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
-                        : gd.Cout == 96 ? launch_conv_tma<96, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used)
-                                        : launch_conv_tma<128, EpiDgrad, true>(gd, t, dZ, WT, epi, status, st, &used);
+        cudaError_t e = gd.Cout <= 16   ? launch_conv_tma<16, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
+                        : gd.Cout <= 32 ? launch_conv_tma<32, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
+                        : gd.Cout <= 64 ? launch_conv_tma<64, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
+                        : gd.Cout == 96 ? launch_conv_tma<96, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
+                                        : launch_conv_tma<128, Epi, true>(gd, t, dZ, WT, epi, status, st, &used);
         if (e != cudaSuccess || used) return e;
     }
     if (g.Cin <= 16) return launch_gemm_async<16>(GatherDgrad<16>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
     if (g.Cin <= 32) return launch_gemm_async<32>(GatherDgrad<32>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
     if (g.Cin <= 64) return launch_gemm_async<64>(GatherDgrad<64>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
     return launch_gemm_async<128>(GatherDgrad<128>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
+}
+
+cudaError_t conv_dgrad(const ConvGeom& g, const bf16* dZ, const bf16* WT, float* dX, int accumulate,
+                       int* status, cudaStream_t st) {
+    return conv_dgrad_epi(g, dZ, WT, EpiDgrad{dX, g.Cin, accumulate}, status, st);
 }
 
 // The TMA-fed weight gradient (tc_wgrad_tma_kernel): both operands MN-major in 32-channel
@@ -662,6 +667,7 @@ struct fb_initnet {
     bf16* act[16] = {};
     float* dact[16] = {};
     bf16* dz = nullptr;                     // scratch: bf16 dZ of the largest layer
+    bf16* dz2 = nullptr;                    // ... and a second one (fused ReLU backward)
     float* head = nullptr;                  // fp32 head output [P][8]
     float* loss = nullptr;
     int* status = nullptr;
@@ -851,7 +857,8 @@ int fb_initnet_create(fb_ctx* ctx, fb_initnet** out, int max_pairs, int H, int W
         o_dact[t] = take(e * 4);
     }
     const size_t Pq = static_cast<size_t>(max_pairs) * (H / downscale) * (W / downscale);
-    const size_t o_dz = take(max_t * 2), o_head = take(Pq * 8 * 4), o_dhead = take(Pq * 8 * 4);
+    const size_t o_dz = take(max_t * 2), o_dz2 = take(max_t * 2), o_head = take(Pq * 8 * 4),
+                 o_dhead = take(Pq * 8 * 4);
     const size_t o_loss = take(4), o_status = take(4);
     if (cudaMalloc(reinterpret_cast<void**>(&net->arena), bytes) != cudaSuccess) {
         cudaGetLastError();
@@ -872,6 +879,7 @@ int fb_initnet_create(fb_ctx* ctx, fb_initnet** out, int max_pairs, int H, int W
     }
     net->dact[15] = reinterpret_cast<float*>(a + o_dhead);  // gradient of the head output
     net->dz = reinterpret_cast<bf16*>(a + o_dz);
+    net->dz2 = reinterpret_cast<bf16*>(a + o_dz2);
     net->head = reinterpret_cast<float*>(a + o_head);
     net->loss = reinterpret_cast<float*>(a + o_loss);
     net->status = reinterpret_cast<int*>(a + o_status);
@@ -966,28 +974,47 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
     offset_loss_kernel<<<blocks(Pq), 256, 0, st>>>(net->head, target, weight, Pq, 1.f / weight_sum,
                                                    net->dact[15], net->loss);
     NET_CUDA(net, cudaGetLastError());
+    // The bf16 operand dZ of a layer's gradients comes from its ReLU backward, or -- when
+    // the next layer's input gradient is the only writer of this layer's output gradient
+    // (a plain chain link: no concatenation reads or writes it) -- straight from that
+    // input gradient's epilogue, into the other of two dZ buffers.
+    bf16* dzb[2] = {net->dz, net->dz2};
+    int cur = 0;
+    bool dz_ready = false;
+    auto in_concat = [](int t) { return t == 2 || t == 4 || t == 6 || t == 8 || t == 10 || t == 12; };
     for (int l = kNumLayers - 1; l >= 0; --l) {
         const ConvGeom g = geom(net, l, n);
-        const size_t out_elems = static_cast<size_t>(g.n) * g.Ho * g.Wo * g.Cout;
-        const float* dA = kOut[l] < 0 ? net->dact[15] : net->dact[kOut[l]];
-        const bf16* A = kOut[l] < 0 ? nullptr : net->act[kOut[l]];
-        if (!written[kOut[l] < 0 ? 15 : kOut[l]]) return FB_ERR_CUDA;  // unreachable: every gradient is written first
-        relu_bwd_kernel<<<blocks(out_elems), 256, 0, st>>>(dA, A ? A : net->act[0], out_elems,
-                                                           kLayers[l].relu, net->dz);
-        NET_CUDA(net, cudaGetLastError());
+        bf16* dz = dzb[cur];
+        if (!dz_ready) {
+            const size_t out_elems = static_cast<size_t>(g.n) * g.Ho * g.Wo * g.Cout;
+            const float* dA = kOut[l] < 0 ? net->dact[15] : net->dact[kOut[l]];
+            const bf16* A = kOut[l] < 0 ? nullptr : net->act[kOut[l]];
+            if (!written[kOut[l] < 0 ? 15 : kOut[l]]) return FB_ERR_CUDA;  // unreachable: every gradient is written first
+            relu_bwd_kernel<<<blocks(out_elems), 256, 0, st>>>(dA, A ? A : net->act[0], out_elems,
+                                                               kLayers[l].relu, dz);
+            NET_CUDA(net, cudaGetLastError());
+        }
+        dz_ready = false;
         const size_t P = static_cast<size_t>(g.n) * g.Ho * g.Wo;
         const size_t bg_rows = 256 / (g.Cout / 8);
         const size_t bg_blocks = (P + bg_rows - 1) / bg_rows;
         const unsigned bg_grid = static_cast<unsigned>(bg_blocks < 2048 ? bg_blocks : 2048);
-        bias_grad_kernel<<<bg_grid, 256, 0, st>>>(net->dz, P, g.Cout,
-                                                 net->grads + net->b_off[l]);
+        bias_grad_kernel<<<bg_grid, 256, 0, st>>>(dz, P, g.Cout, net->grads + net->b_off[l]);
         NET_CUDA(net, cudaGetLastError());
-        NET_CUDA(net, conv_wgrad(g, net->dz, net->act[kIn[l]], net->grads + net->w_off[l], net->sms,
+        NET_CUDA(net, conv_wgrad(g, dz, net->act[kIn[l]], net->grads + net->w_off[l], net->sms,
                                  net->status, st));
         if (l > 0) {
-            NET_CUDA(net, conv_dgrad(g, net->dz, net->wt + net->w_off[l], net->dact[kIn[l]],
-                                     written[kIn[l]] ? 1 : 0, net->status, st));
-            written[kIn[l]] = true;
+            const int t = kIn[l];
+            if (!written[t] && kOut[l - 1] == t && !in_concat(t)) {
+                const EpiDgradRelu epi{dzb[cur ^ 1], net->act[t], kTens[t].ch, kLayers[l - 1].relu};
+                NET_CUDA(net, conv_dgrad_epi(g, dz, net->wt + net->w_off[l], epi, net->status, st));
+                cur ^= 1;
+                dz_ready = true;
+            } else {
+                NET_CUDA(net, conv_dgrad(g, dz, net->wt + net->w_off[l], net->dact[t], written[t] ? 1 : 0,
+                                         net->status, st));
+            }
+            written[t] = true;
         }
         if (l == 8 || l == 9 || l == 10) {  // split the concatenated input's gradient
             const int lo = l == 8 ? 8 : (l == 9 ? 10 : 12);

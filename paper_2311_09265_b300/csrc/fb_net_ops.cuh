@@ -284,6 +284,37 @@ struct EpiDgrad {
     }
 };
 
+// Input gradient fused with the ReLU backward of the layer whose output it is: the kernel
+// is the only writer of that gradient, so its value v goes straight to the bf16 operand of
+// that layer's own gradients, dZ = bf16(relu && !(A > 0) ? 0 : v) -- the relu_bwd_kernel
+// result -- and the fp32 gradient is never stored.
+struct EpiDgradRelu {
+    bf16* dZ;        // [rows][C]
+    const bf16* A;   // the layer's output activation [rows][C]
+    int C;
+    int relu;
+    __device__ __forceinline__ void store(int row, int col0, const float (&v)[16]) const {
+        const size_t o = static_cast<size_t>(row) * C + col0;
+        if (col0 + 16 <= C && (C & 7) == 0) {
+            __align__(16) bf16 a[16], z[16];
+            *reinterpret_cast<uint4*>(&a[0]) = __ldg(reinterpret_cast<const uint4*>(A + o));
+            *reinterpret_cast<uint4*>(&a[8]) = __ldg(reinterpret_cast<const uint4*>(A + o + 8));
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                z[j] = __float2bfloat16_rn(relu && !(__bfloat162float(a[j]) > 0.f) ? 0.f : v[j]);
+            uint4* d = reinterpret_cast<uint4*>(dZ + o);
+            d[0] = *reinterpret_cast<const uint4*>(&z[0]);
+            d[1] = *reinterpret_cast<const uint4*>(&z[8]);
+            return;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (col0 + j >= C) break;
+            dZ[o + j] = __float2bfloat16_rn(relu && !(__bfloat162float(A[o + j]) > 0.f) ? 0.f : v[j]);
+        }
+    }
+};
+
 // ---- weight gradient ---------------------------------------------------------------
 template <int BN>
 struct GatherWgrad {
