@@ -27,7 +27,10 @@ using namespace dev;
 #define FB_TILE_H 8
 #endif
 
-constexpr int TILE_W = 32;
+#ifndef FB_TILE_W
+#define FB_TILE_W 32
+#endif
+constexpr int TILE_W = FB_TILE_W;
 constexpr int TILE_H = FB_TILE_H;
 constexpr int TILE_THREADS = TILE_W * TILE_H;
 
