@@ -10,6 +10,7 @@ also against the CPU oracle; between the two calls neither the device's free mem
 torch's allocations may change.  It lives in a file of its own that pytest collects last.
 """
 import ctypes
+import gc
 
 import numpy as np
 import pytest
@@ -53,12 +54,19 @@ def test_noalloc_blend_matches_context_blend_on_two_calls_in_a_row():
     outs = [torch.full(g.shape, -1.0, dtype=torch.float32, device="cuda") for (g, _), _, _ in cases]
     torch.cuda.synchronize()
     got = []
-    for q, ((g, s), window, params) in enumerate(cases):
-        got.append(_noalloc(fbp, dev[q][0], dev[q][1], window, params, outs[q]))
-        torch.cuda.synchronize()
-        if q == 0:   # the library's device code and its static array are in place now
-            free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
-    assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == alloc0
+    # Tensors left by earlier tests may be collected at any time and lower torch's count:
+    # collect them first and keep the collector off while the counts are compared.
+    gc.collect()
+    gc.disable()
+    try:
+        for q, ((g, s), window, params) in enumerate(cases):
+            got.append(_noalloc(fbp, dev[q][0], dev[q][1], window, params, outs[q]))
+            torch.cuda.synchronize()
+            if q == 0:   # the library's device code and its static array are in place now
+                free0, alloc0 = torch.cuda.mem_get_info()[0], torch.cuda.memory_allocated()
+        assert torch.cuda.mem_get_info()[0] == free0 and torch.cuda.memory_allocated() == alloc0
+    finally:
+        gc.enable()
     for q, ((g, s), window, params) in enumerate(cases):
         o = got[q].cpu().numpy()
         assert np.abs(o - want[q]).max() <= TOL
