@@ -605,14 +605,18 @@ int fb_conv3x3_backward(const uint16_t *x, int n, int H, int W, int Cin, const u
                         int Cout, int stride, const uint16_t *dz, float *dx, float *dw,
                         int *status, void *stream);
 
-/* Operand staging of the forward convolutions (process-wide; for tests and
- * measurement).  mode 0 (default): layers whose output rows tile 128-pixel blocks stage
- * both operands with tiled TMA loads (the activation box displaced per tap and traversed
- * with the layer's stride, zero-filled outside the image, 128-byte swizzle); other
- * layers, and every layer in mode 1, gather them with cp.async.  Both accumulate the same products in the same
- * order, so the outputs are identical.  mode -1 leaves the setting; *tma_launches
- * (nullable) receives the number of TMA-staged launches so far.  FB_ERR_ARG for other
- * modes. */
+/* Operand staging of the initialiser's convolutions (process-wide; for tests and
+ * measurement).  Layers whose output rows tile 128-pixel blocks stage both operands with
+ * tiled TMA loads (the activation box displaced per tap and traversed with the layer's
+ * stride, zero-filled outside the image, swizzled rows); other layers gather them with
+ * cp.async.  mode 0 (default): the TMA-fed forward and stride-1 input gradients whose
+ * tiles are whole rows of one image with a width divisible by 8 and Cin % 32 == 0 load one
+ * halo box of R + 2 rows per tap column and channel block and take the three row taps as
+ * views into it (the same products in another order: equal to fp32 rounding); the TMA-fed
+ * weight gradients run.  mode 2: every TMA-fed convolution loads one box per tap, which
+ * accumulates the same products in the same order as the gathers (identical outputs).
+ * mode 1: gathers only.  mode -1 leaves the setting; *tma_launches (nullable) receives the
+ * number of TMA-staged launches so far.  FB_ERR_ARG for other modes. */
 int fb_conv_gemm_path(int mode, uint64_t *tma_launches);
 
 /* Bytes of the fixed device scratch array used by fb_blend_window_noalloc. */

@@ -82,7 +82,8 @@ cudaError_t launch_gemm_async(const G& gth, const E& epi, int M, int N, int K, i
 #define FB_TMA_STAGES 3
 #endif
 constexpr int kTmaStages = FB_TMA_STAGES;
-std::atomic<int> g_gemm_path{0};              // 0: TMA where eligible; 1: gathers only
+std::atomic<int> g_gemm_path{0};  // 0: TMA where eligible, row reuse where eligible; 1: gathers only;
+                                  // 2: TMA without row reuse
 std::atomic<unsigned long long> g_tma_launches{0};
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
@@ -173,18 +174,85 @@ cudaError_t launch_conv_tma(const ConvGeom& g, const tc::TmaConvGeom& t, const b
     return e;
 }
 
+// The row-reuse form of the TMA convolution (tc_conv_tma_rows_kernel): stride 1, tiles of
+// R whole rows of one image (I == 1), Wo a multiple of 8 (the row views start on swizzle
+// atoms), Cin a multiple of 32 (channel blocks of 64 or 32).  Padding 8-channel inputs to
+// 32-wide blocks with the boxes' zero fill was measured and is slower (the 8 -> 32 input
+// layer 86 -> ~250 us): the per-column kernel moves 8-channel columns as they are.
+bool tma_rows_geom(const ConvGeom& g, const tc::TmaConvGeom& t) {
+    return g.stride == 1 && t.I == 1 && g.Wo % 8 == 0 && g.Cin % 32 == 0 && t.R + 2 <= 256 && g.Wo <= 256;
+}
+
+template <int BN, class Epi, bool FLIP>
+cudaError_t launch_conv_tma_rows(const ConvGeom& g, const tc::TmaConvGeom& t, const bf16* X, const bf16* Wt,
+                                 const Epi& epi, int* status, cudaStream_t st, bool* used) {
+    *used = false;
+    const auto encode = tensor_map_encoder();
+    if (!encode) return cudaSuccess;
+    const int cb = g.Cin % 64 == 0 ? 64 : 32;
+    const CUtensorMapSwizzle sw = cb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    alignas(64) CUtensorMap mx, mw;
+    const cuuint64_t xdim[4] = {static_cast<cuuint64_t>(g.Cin), static_cast<cuuint64_t>(g.W),
+                                static_cast<cuuint64_t>(g.H), static_cast<cuuint64_t>(g.n)};
+    const cuuint64_t xstr[3] = {static_cast<cuuint64_t>(g.Cin) * 2, static_cast<cuuint64_t>(g.W) * g.Cin * 2,
+                                static_cast<cuuint64_t>(g.H) * g.W * g.Cin * 2};
+    const cuuint32_t xbox[4] = {static_cast<cuuint32_t>(cb), static_cast<cuuint32_t>(g.Wo),
+                                static_cast<cuuint32_t>(t.R + 2), 1u};
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    const CUresult rx = encode(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(X), xdim, xstr, xbox,
+                               ones, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    // weights as the {9 Cin, Cout} matrix; one box per tap and channel block
+    const cuuint64_t wdim[2] = {static_cast<cuuint64_t>(9) * g.Cin, static_cast<cuuint64_t>(g.Cout)};
+    const cuuint64_t wstr[1] = {static_cast<cuuint64_t>(9) * g.Cin * 2};
+    const cuuint32_t wbox[2] = {static_cast<cuuint32_t>(cb), static_cast<cuuint32_t>(BN)};
+    const CUresult rw = encode(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(Wt), wdim, wstr, wbox,
+                               ones, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (rx != CUDA_SUCCESS || rw != CUDA_SUCCESS) return cudaSuccess;
+    // Three stages or none: with two the row reuse lost to the per-column kernel (the
+    // 160-channel input gradient of the 32x32 decoder layer: 202 against 180 us).
+    const int stage = tc::conv_rows_stage_bytes(BN, cb, g.Wo);
+    const int smem = 3 * stage + 1024;
+    if (smem > 200 * 1024) return cudaSuccess;   // the column kernel runs instead
+    auto kern = cb == 64 ? tc::tc_conv_tma_rows_kernel<BN, 3, 64, Epi, FLIP>
+                         : tc::tc_conv_tma_rows_kernel<BN, 3, 32, Epi, FLIP>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((t.M + tc::BM - 1) / tc::BM, (g.Cout + BN - 1) / BN);
+    kern<<<grid, 128, smem, st>>>(mx, mw, epi, t, status);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        *used = true;
+        ++g_tma_launches;
+    }
+    return e;
+}
+
+// TMA-fed convolution of output-channel tile BN: the row-reuse kernel where its geometry
+// holds (path 0), else the per-column kernel.
+template <int BN, class Epi, bool FLIP>
+cudaError_t launch_conv_any(const ConvGeom& g, const tc::TmaConvGeom& t, const bf16* X, const bf16* Wt,
+                            const Epi& epi, int* status, cudaStream_t st, bool* used) {
+    if (g_gemm_path.load() == 0 && tma_rows_geom(g, t)) {
+        cudaError_t e = launch_conv_tma_rows<BN, Epi, FLIP>(g, t, X, Wt, epi, status, st, used);
+        if (e != cudaSuccess || *used) return e;
+    }
+    return launch_conv_tma<BN, Epi, FLIP>(g, t, X, Wt, epi, status, st, used);
+}
+
 cudaError_t conv_forward(const ConvGeom& g, const bf16* X, const bf16* Wt, const float* bias,
                          int relu, bf16* Y, float* Yf, int* status, cudaStream_t st) {
     const int M = g.n * g.Ho * g.Wo, K = 9 * g.Cin, ncb = (g.Cin + 63) / 64;
     EpiFwd epi{Y, Yf, bias, g.Cout, relu};
     tc::TmaConvGeom t;
-    if (g_gemm_path.load() == 0 && tma_conv_geom(g, X, Wt, t)) {
+    if (g_gemm_path.load() != 1 && tma_conv_geom(g, X, Wt, t)) {
         bool used = false;
-        cudaError_t e = g.Cout <= 16   ? launch_conv_tma<16>(g, t, X, Wt, epi, status, st, &used)
-                        : g.Cout <= 32 ? launch_conv_tma<32>(g, t, X, Wt, epi, status, st, &used)
-                        : g.Cout <= 64 ? launch_conv_tma<64>(g, t, X, Wt, epi, status, st, &used)
-                        : g.Cout == 96 ? launch_conv_tma<96>(g, t, X, Wt, epi, status, st, &used)
-                                       : launch_conv_tma<128>(g, t, X, Wt, epi, status, st, &used);
+        cudaError_t e = g.Cout <= 16   ? launch_conv_any<16, EpiFwd, false>(g, t, X, Wt, epi, status, st, &used)
+                        : g.Cout <= 32 ? launch_conv_any<32, EpiFwd, false>(g, t, X, Wt, epi, status, st, &used)
+                        : g.Cout <= 64 ? launch_conv_any<64, EpiFwd, false>(g, t, X, Wt, epi, status, st, &used)
+                        : g.Cout == 96 ? launch_conv_any<96, EpiFwd, false>(g, t, X, Wt, epi, status, st, &used)
+                                       : launch_conv_any<128, EpiFwd, false>(g, t, X, Wt, epi, status, st, &used);
         if (e != cudaSuccess || used) return e;
     }
     if (g.Cout <= 16) return launch_gemm_async<16>(GatherFwd<16>{X, Wt, g, M, K, ncb}, epi, M, g.Cout, K, status, st);
@@ -201,13 +269,13 @@ cudaError_t conv_dgrad_epi(const ConvGeom& g, const bf16* dZ, const bf16* WT, co
     // transposed weights, staged by TMA like the forward layers (FLIP), where the boxes tile.
     tc::TmaConvGeom t;
     const ConvGeom gd{g.n, g.Ho, g.Wo, g.Cout, g.H, g.W, g.Cin, 1};
-    if (g.stride == 1 && g_gemm_path.load() == 0 && tma_conv_geom(gd, dZ, WT, t)) {
+    if (g.stride == 1 && g_gemm_path.load() != 1 && tma_conv_geom(gd, dZ, WT, t)) {
         bool used = false;
-        cudaError_t e = gd.Cout <= 16   ? launch_conv_tma<16, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
-                        : gd.Cout <= 32 ? launch_conv_tma<32, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
-                        : gd.Cout <= 64 ? launch_conv_tma<64, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
-                        : gd.Cout == 96 ? launch_conv_tma<96, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
-                                        : launch_conv_tma<128, Epi, true>(gd, t, dZ, WT, epi, status, st, &used);
+        cudaError_t e = gd.Cout <= 16   ? launch_conv_any<16, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
+                        : gd.Cout <= 32 ? launch_conv_any<32, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
+                        : gd.Cout <= 64 ? launch_conv_any<64, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
+                        : gd.Cout == 96 ? launch_conv_any<96, Epi, true>(gd, t, dZ, WT, epi, status, st, &used)
+                                        : launch_conv_any<128, Epi, true>(gd, t, dZ, WT, epi, status, st, &used);
         if (e != cudaSuccess || used) return e;
     }
     if (g.Cin <= 16) return launch_gemm_async<16>(GatherDgrad<16>{dZ, WT, g, M, K, ncb}, epi, M, g.Cin, K, status, st);
@@ -299,7 +367,7 @@ cudaError_t launch_wgrad_tma(const ConvGeom& g, int R, int I, const bf16* dZ, co
 cudaError_t conv_wgrad(const ConvGeom& g, const bf16* dZ, const bf16* X, float* dW, int sms,
                        int* status, cudaStream_t st) {
     int R = 0, I = 0;
-    if (g_gemm_path.load() == 0 && tma_wgrad_geom(g, X, dZ, &R, &I)) {
+    if (g_gemm_path.load() != 1 && tma_wgrad_geom(g, X, dZ, &R, &I)) {
         bool used = false;
         const int nb = (g.Cout + 31) / 32;
         cudaError_t e = nb == 1   ? launch_wgrad_tma<1>(g, R, I, dZ, X, dW, sms, status, st, &used)
@@ -1069,7 +1137,7 @@ int fb_debug_set_wait_limit(int64_t polls) {
 }
 
 int fb_conv_gemm_path(int mode, uint64_t* tma_launches) {
-    if (mode < -1 || mode > 1) return FB_ERR_ARG;
+    if (mode < -1 || mode > 2) return FB_ERR_ARG;
     if (tma_launches) *tma_launches = fb::net::g_tma_launches.load();
     if (mode >= 0) fb::net::g_gemm_path.store(mode);
     return FB_OK;

@@ -221,6 +221,135 @@ constexpr int conv_tma_smem_bytes() {
 }
 
 // ---------------------------------------------------------------------------------
+// The same stride-1 convolution with the three row taps of a tap column sharing one halo
+// box ("row reuse").  A tile is R whole output rows y0 .. y0 + R - 1 of one image; for a
+// column displacement ex in {-1, 0, 1} and a CB-channel block the activation box
+// {CB channels, Wo, R + 2, 1} at (x = ex, y = y0 - 1) holds input rows y0 - 1 .. y0 + R,
+// and the row displacement ey in {-1, 0, 1} is the 128-row view starting (ey + 1) Wo rows
+// into it: a whole number of 8-row swizzle atoms when Wo % 8 == 0, so the view is an
+// ordinary K-major operand.  One stage per (ex, block): the box plus the three taps' weight
+// boxes {CB of the 9 Cin K elements, BN}, then 3 CB / 16 MMAs.  The activation bytes per
+// tile fall from 9 R Wo rows to 3 (R + 2) Wo rows per block; the products are the same,
+// accumulated in (ex, block, ey) order instead of tap-major order.
+// ---------------------------------------------------------------------------------
+template <int BN, int S, int CB, class Epi, bool FLIP = false>
+__global__ void __launch_bounds__(128)
+    tc_conv_tma_rows_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
+                            Epi epi, TmaConvGeom g, int* status) {
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tile N");
+    static_assert(S >= 2 && S <= 4, "stages");
+    static_assert(CB == 32 || CB == 64, "column width");
+    constexpr int RB = 2 * CB;                      // bytes of one activation / weight row
+    constexpr uint32_t WB = static_cast<uint32_t>(BN) * RB;   // one weight box
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[S];
+    __shared__ __align__(8) uint64_t empty[S];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN;
+    const uint32_t a_bytes = static_cast<uint32_t>(BM + 2 * g.Wo) * RB;   // R + 2 rows of Wo pixels
+    const uint32_t stage = (a_bytes + 3 * WB + 1023u) & ~1023u;
+    const int cpt = g.Cin / CB;                     // channel blocks (Cin % CB == 0)
+    const int n_groups = 3 * cpt;
+    const int img0 = m0 / (g.Ho * g.Wo);
+    const int y0 = (m0 - img0 * g.Ho * g.Wo) / g.Wo;
+    const uint32_t s0 = (smem_u32(smem) + 1023u) & ~1023u;
+
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s]);
+            mbar_init(&empty[s]);
+        }
+        s_ok = 1;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TmemCols<BN>::value));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = instr_desc(BN);
+
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        int issued = 0;
+        const long lim = progress_limit();
+        auto issue = [&](int gi) {
+            const int s = gi % S;
+            const uint32_t sa = s0 + s * stage;
+            const int ex = gi / cpt - 1, blk = gi - (ex + 1) * cpt;
+            mbar_expect_tx(&full[s], a_bytes + 3 * WB);
+            tma_load_4d(sa, &map_x, &full[s], CB * blk, ex, y0 - 1, img0);
+#pragma unroll
+            for (int e = 0; e < 3; ++e) {   // row displacement ey = e - 1
+                const int tap = FLIP ? (2 - e) * 3 + (1 - ex) : e * 3 + (ex + 1);
+                tma_load_2d(sa + a_bytes + e * WB, &map_w, &full[s], tap * g.Cin + CB * blk, n0);
+            }
+            ++issued;
+        };
+        for (int c = 0; c < S - 1 && c < n_groups; ++c) issue(c);
+        int done = 0;
+        for (int i = 0; i < n_groups && ok; ++i) {
+            const int s = i % S;
+            ok = mbar_wait(&full[s], (i / S) & 1, lim);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = s0 + s * stage, sb = sa + a_bytes;
+#pragma unroll
+            for (int e = 0; e < 3; ++e)
+#pragma unroll
+                for (int j = 0; j < CB / 16; ++j)
+                    mma_bf16(tmem, smem_desc_sw<RB>(sa + static_cast<uint32_t>(e * g.Wo) * RB + 32u * j),
+                             smem_desc_sw<RB>(sb + e * WB + 32u * j), idesc, (i > 0 || e > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+            ++done;
+            const int nxt = i + S - 1;
+            if (nxt < n_groups) {
+                const int prev = nxt - S;
+                if (prev >= 0) ok = mbar_wait(&empty[prev % S], (prev / S) & 1, lim);
+                if (ok) issue(nxt);
+            }
+        }
+        if (ok && done > 0) ok = mbar_wait(&empty[(done - 1) % S], ((done - 1) / S) & 1, lim);
+        if (!ok) {
+            if (done > 0) mbar_wait(&empty[(done - 1) % S], ((done - 1) / S) & 1);
+            for (int c = done; c < issued; ++c) mbar_wait(&full[c % S], (c / S) & 1);
+            s_ok = 0;
+            atomicExch(status, 1);
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (s_ok) {
+        const int row = m0 + warp * 32 + lane;
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+            if (row < g.M && n0 + c0 < g.Cout) epi.store(row, n0 + c0, v);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TmemCols<BN>::value));
+}
+
+// Bytes of one stage of the row-reuse kernel and the dynamic shared memory of S stages.
+inline int conv_rows_stage_bytes(int BN, int CB, int Wo) {
+    return ((BM + 2 * Wo) * 2 * CB + 3 * BN * 2 * CB + 1023) / 1024 * 1024;
+}
+
+// ---------------------------------------------------------------------------------
 // Weight gradient of the 3x3 convolution, with both operands MN-major:
 //
 //   dW[co][tap][ci] = sum_p X[s p + tap - (1, 1)][ci] dZ[p][co]

@@ -47,8 +47,18 @@ TMA_CASES = [  # n, H, W, Cin, Cout, stride: the initialiser's layers at 512x512
 ]
 
 
+def rows_reuse(H, W, Cin, stride):
+    """Whether the default path may run the row-reuse kernel: stride 1, tiles of whole rows
+    of one image (128 output pixels per tile), a width divisible by 8 (and three stages
+    fitting in shared memory, which these cases do unless the tile is 128 wide with
+    64-channel blocks)."""
+    return stride == 1 and (H * W) % 128 == 0 and 128 % W == 0 and W % 8 == 0 and Cin % 32 == 0
+
+
 @pytest.mark.parametrize("n,H,W,Cin,Cout,stride", TMA_CASES)
 def test_tma_conv_is_bit_identical_to_the_gather_path(fbp, n, H, W, Cin, Cout, stride):
+    """One box per tap (mode 2) against the gathers (mode 1): bit-identical for Cin % 16 == 0.
+    The default (mode 0; row reuse where it applies) against both: fp32 rounding."""
     rng = np.random.default_rng(n * 1000 + H * W + Cin + Cout)
     x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
     w = ref.bf16(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin))
@@ -59,12 +69,19 @@ def test_tma_conv_is_bit_identical_to_the_gather_path(fbp, n, H, W, Cin, Cout, s
     same_steps = Cin % 16 == 0
     for relu, out_f32 in ((False, True), (True, False)):
         yg, used_g = run(fbp, x, w, b, stride, relu, out_f32, mode=1)
-        yt, used_t = run(fbp, x, w, b, stride, relu, out_f32, mode=0)
-        assert used_g == 0 and used_t == 1
+        yt, used_t = run(fbp, x, w, b, stride, relu, out_f32, mode=2)
+        yr, used_r = run(fbp, x, w, b, stride, relu, out_f32, mode=0)
+        assert used_g == 0 and used_t == 1 and used_r == 1
         if same_steps:
             assert np.array_equal(yt.view(np.uint32) if out_f32 else yt, yg.view(np.uint32) if out_f32 else yg)
         elif out_f32:
             assert float(np.linalg.norm(yt - yg) / np.linalg.norm(yg)) < 1e-6
+        if out_f32:
+            assert float(np.linalg.norm(yr - yg) / np.linalg.norm(yg)) < 1e-6
+            if not rows_reuse(H, W, Cin, stride):
+                assert np.array_equal(yr.view(np.uint32), yt.view(np.uint32))
+        else:   # bf16 outputs: at most one rounding step apart
+            assert float(np.abs(yr - yg).max()) <= 2.0 ** -6 * max(1.0, float(np.abs(yg).max()))
     want = ref.conv3x3(x, w, b, stride)
     y32, _ = run(fbp, x, w, b, stride, False, True, mode=0)
     assert float(np.linalg.norm(y32 - want) / np.linalg.norm(want)) < 1e-5
@@ -84,8 +101,9 @@ def test_layers_the_tma_boxes_cannot_tile_use_the_gathers(fbp, n, H, W, Cin, Cou
 
 
 def test_gemm_path_argument_errors(fbp):
-    with pytest.raises(fbp.FastBlendError):
-        fbp.fb_conv_gemm_path(2)
+    for mode in (3, -2):
+        with pytest.raises(fbp.FastBlendError):
+            fbp.fb_conv_gemm_path(mode)
 
 
 DGRAD_CASES = [  # n, H, W, Cin, Cout of stride-1 layers: the input gradient's boxes tile
@@ -108,7 +126,7 @@ def test_tma_input_gradient_is_bit_identical_to_the_gather_path(fbp, n, H, W, Ci
     dz = ref.bf16(rng.normal(size=(n, H, W, Cout)))
     wt = np.ascontiguousarray(np.transpose(w, (3, 1, 2, 0)))
     out = {}
-    for mode in (1, 0):
+    for mode in (1, 2, 0):
         fbp.fb_conv_gemm_path(mode)
         n0 = fbp.fb_conv_gemm_path(-1)
         dx, _, st = fbp.conv3x3_backward(to_bf16_tensor(x), to_bf16_tensor(wt), to_bf16_tensor(dz), 1,
@@ -117,14 +135,19 @@ def test_tma_input_gradient_is_bit_identical_to_the_gather_path(fbp, n, H, W, Ci
         assert int(st.item()) == 0
         out[mode] = (dx.cpu().numpy(), fbp.fb_conv_gemm_path(-1) - n0)
     fbp.fb_conv_gemm_path(0)
-    (dxg, used_g), (dxt, used_t) = out[1], out[0]
-    assert used_g == 0 and used_t == 1
+    (dxg, used_g), (dxt, used_t), (dxr, used_r) = out[1], out[2], out[0]
+    assert used_g == 0 and used_t == 1 and used_r == 1
     if Cout % 16 == 0:
         assert np.array_equal(dxt.view(np.uint32), dxg.view(np.uint32))
     else:
         assert float(np.linalg.norm(dxt - dxg) / np.linalg.norm(dxg)) < 1e-6
+    # the default: the row-reuse kernel where the input gradient's geometry allows it
+    assert float(np.linalg.norm(dxr - dxg) / np.linalg.norm(dxg)) < 1e-6
+    if not rows_reuse(H, W, Cout, 1):
+        assert np.array_equal(dxr.view(np.uint32), dxt.view(np.uint32))
     dx_ref, _, _ = ref.conv3x3_backward(x, w, dz, 1)
     assert float(np.linalg.norm(dxt - dx_ref) / np.linalg.norm(dx_ref)) < 1e-5
+    assert float(np.linalg.norm(dxr - dx_ref) / np.linalg.norm(dx_ref)) < 1e-5
 
 
 WGRAD_CASES = [  # n, H, W, Cin, Cout, stride: whole-row pixel chunks; channels padded to 32
