@@ -1,5 +1,9 @@
-// fb_tc_tma.cuh -- the forward 3x3 convolution (stride s = 1 or 2) of the learned NNF
-// initialiser as a tcgen05 GEMM whose operands the Tensor Memory Accelerator stages:
+// fb_tc_tma.cuh -- the 3x3 convolutions of the learned NNF initialiser as tcgen05 GEMMs
+// whose operands the Tensor Memory Accelerator stages: tc_conv_tma_kernel (forward, stride
+// s = 1 or 2, one box per tap; with FLIP the stride-1 input gradient), described here;
+// tc_conv_tma_rows_kernel (the same with the three row taps of a column sharing one halo
+// box); tc_wgrad_tma_kernel (the weight gradient, both operands MN-major).  Each is
+// described above its definition.
 //
 //   Y[p][co] = sum_{tap, ci} X[s p + tap - (1, 1)][ci] W[co][tap][ci]    (M = output
 //   pixels, N = Cout, K = 9 Cin, walked tap-major in chunks of K = 64)
