@@ -548,40 +548,39 @@ __global__ void concat_up_kernel(const bf16* __restrict__ lo, int C1, const bf16
 }
 
 // Gradient of concat_up: dlo[n][h][w][C1] += sum over the 2x2 block, dskip += its part.
-// acc_lo / acc_skip: add to the gradient already in dlo / dskip, or write it (first writer).
+// Gradient of the upsampled part of a concatenation: dlo[p][c] = the sum of the 2 x 2
+// block of dout's first C1 channels above p, added to dlo (acc_lo) or written (first
+// writer).  The skip part (dout's last C2 channels) is not copied: the ReLU backward of the
+// skip tensor's layer adds it where it reads that tensor's gradient.
 __global__ void concat_up_bwd_kernel(const float* __restrict__ dout, int C1, int C2, int n, int H2,
-                                     int W2, float* __restrict__ dlo, float* __restrict__ dskip, int acc_lo,
-                                     int acc_skip) {
+                                     int W2, float* __restrict__ dlo, int acc_lo) {
     const int C = C1 + C2;
     const int H = H2 / 2, W = W2 / 2;
     const size_t lo_total = static_cast<size_t>(n) * H * W * C1;
-    const size_t sk_total = static_cast<size_t>(n) * H2 * W2 * C2;
     const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i < lo_total) {
-        const int c = static_cast<int>(i % C1);
-        const size_t p = i / C1;
-        const int img = static_cast<int>(p / (static_cast<size_t>(H) * W));
-        const int rem = static_cast<int>(p - static_cast<size_t>(img) * H * W);
-        const int y = rem / W, x = rem % W;
-        float s = 0.f;
-        for (int dy = 0; dy < 2; ++dy)
-            for (int dx = 0; dx < 2; ++dx)
-                s += dout[((static_cast<size_t>(img) * H2 + 2 * y + dy) * W2 + 2 * x + dx) * C + c];
-        dlo[i] = acc_lo ? dlo[i] + s : s;
-    } else if (i < lo_total + sk_total) {
-        const size_t j = i - lo_total;
-        const int c = static_cast<int>(j % C2);
-        const size_t p = j / C2;
-        dskip[j] = acc_skip ? dskip[j] + dout[p * C + C1 + c] : dout[p * C + C1 + c];
-    }
+    if (i >= lo_total) return;
+    const int c = static_cast<int>(i % C1);
+    const size_t p = i / C1;
+    const int img = static_cast<int>(p / (static_cast<size_t>(H) * W));
+    const int rem = static_cast<int>(p - static_cast<size_t>(img) * H * W);
+    const int y = rem / W, x = rem % W;
+    float s = 0.f;
+    for (int dy = 0; dy < 2; ++dy)
+        for (int dx = 0; dx < 2; ++dx)
+            s += dout[((static_cast<size_t>(img) * H2 + 2 * y + dy) * W2 + 2 * x + dx) * C + c];
+    dlo[i] = acc_lo ? dlo[i] + s : s;
 }
 
-// dZ = dA * (A > 0) in bf16 (ReLU backward); relu == 0 passes dA through.
+// dZ = dA * (A > 0) in bf16 (ReLU backward); relu == 0 passes dA through.  With add, the
+// gradient is dA + the skip slice of a concatenation's gradient: add[(i / C) * add_stride +
+// add_off + i % C] (the skip tensor's other consumer).
 __global__ void relu_bwd_kernel(const float* __restrict__ dA, const bf16* __restrict__ A, size_t n,
-                                int relu, bf16* __restrict__ dZ) {
+                                int relu, bf16* __restrict__ dZ, const float* __restrict__ add, int C,
+                                int add_stride, int add_off) {
     const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
     if (i >= n) return;
     float g = dA[i];
+    if (add) g += add[(i / C) * add_stride + add_off + i % C];
     if (relu && !(__bfloat162float(A[i]) > 0.f)) g = 0.f;
     dZ[i] = __float2bfloat16_rn(g);
 }
@@ -1035,10 +1034,14 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
     NET_CUDA(net, cudaMemsetAsync(net->loss, 0, 4, st));
     NET_CUDA(net, cudaMemsetAsync(net->grads, 0, net->n_params * 4, st));
     // Activation gradients need no clearing: the first kernel to reach a tensor writes it
-    // and later ones add (only the skip tensors of the stride-2 encoder layers receive two
-    // contributions, from the concatenation split and from the next layer's input gradient).
+    // and later ones add.  The skip tensors of the stride-2 encoder layers have two
+    // consumers; their gradient is written by the next layer's input gradient, and the
+    // other contribution -- the skip slice of the concatenation's gradient -- is added by
+    // the ReLU backward that reads it (skip_cat: the concatenation, skip_off: its channel).
     bool written[16] = {};
     written[15] = true;   // the head's gradient, written by the loss kernel
+    int skip_cat[16], skip_off[16];
+    for (int t = 0; t < 16; ++t) skip_cat[t] = skip_off[t] = -1;
     offset_loss_kernel<<<blocks(Pq), 256, 0, st>>>(net->head, target, weight, Pq, 1.f / weight_sum,
                                                    net->dact[15], net->loss);
     NET_CUDA(net, cudaGetLastError());
@@ -1057,9 +1060,12 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
             const size_t out_elems = static_cast<size_t>(g.n) * g.Ho * g.Wo * g.Cout;
             const float* dA = kOut[l] < 0 ? net->dact[15] : net->dact[kOut[l]];
             const bf16* A = kOut[l] < 0 ? nullptr : net->act[kOut[l]];
-            if (!written[kOut[l] < 0 ? 15 : kOut[l]]) return FB_ERR_CUDA;  // unreachable: every gradient is written first
-            relu_bwd_kernel<<<blocks(out_elems), 256, 0, st>>>(dA, A ? A : net->act[0], out_elems,
-                                                               kLayers[l].relu, dz);
+            const int to = kOut[l] < 0 ? 15 : kOut[l];
+            if (!written[to]) return FB_ERR_CUDA;  // unreachable: every gradient is written first
+            const int cat = skip_cat[to];
+            relu_bwd_kernel<<<blocks(out_elems), 256, 0, st>>>(
+                dA, A ? A : net->act[0], out_elems, kLayers[l].relu, dz, cat >= 0 ? net->dact[cat] : nullptr,
+                g.Cout, cat >= 0 ? kTens[cat].ch : 0, skip_off[to]);
             NET_CUDA(net, cudaGetLastError());
         }
         dz_ready = false;
@@ -1089,12 +1095,13 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
             const int skip = l == 8 ? 6 : (l == 9 ? 4 : 2);
             const int cat = kIn[l];
             const int H2 = (net->H / net->ds) / kTens[cat].div, W2 = (net->W / net->ds) / kTens[cat].div;
-            const size_t tot = tens_elems(net, lo, n) + tens_elems(net, skip, n);
+            const size_t tot = tens_elems(net, lo, n);
             concat_up_bwd_kernel<<<blocks(tot), 256, 0, st>>>(net->dact[cat], kTens[lo].ch, kTens[skip].ch, n,
-                                                              H2, W2, net->dact[lo], net->dact[skip],
-                                                              written[lo] ? 1 : 0, written[skip] ? 1 : 0);
+                                                              H2, W2, net->dact[lo], written[lo] ? 1 : 0);
             NET_CUDA(net, cudaGetLastError());
-            written[lo] = written[skip] = true;
+            written[lo] = true;
+            skip_cat[skip] = cat;
+            skip_off[skip] = kTens[lo].ch;
         }
     }
     if (lr > 0.f) {
