@@ -313,7 +313,7 @@ bool tma_wgrad_geom(const ConvGeom& g, const void* X, const void* dZ, int* R, in
 template <int NB>
 cudaError_t launch_wgrad_tma(const ConvGeom& g, int R, int I, const bf16* dZ, const bf16* X, float* dW, int sms,
                              int* status, cudaStream_t st, bool* used) {
-    constexpr int S = NB <= 2 ? 4 : 3;
+    constexpr int S = NB == 1 ? 5 : NB == 2 ? 4 : 3;   // as many 40-64 KB stages as fit beside the slack
     *used = false;
     const auto encode = tensor_map_encoder();
     if (!encode) return cudaSuccess;

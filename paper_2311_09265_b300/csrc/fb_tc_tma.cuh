@@ -399,7 +399,7 @@ constexpr int kWgradChunk = 128 * 64;          // bytes of one 32-wide box of 12
 constexpr int kWgradSlack = 16 * 1024;         // dynamic shared memory past the last stage
 
 template <int NB, int S>
-constexpr int wgrad_tma_smem_bytes() {
+__host__ __device__ constexpr int wgrad_tma_smem_bytes() {
     return S * (4 + NB) * kWgradChunk + 1024 + kWgradSlack;
 }
 
@@ -408,7 +408,8 @@ __global__ void __launch_bounds__(128)
     tc_wgrad_tma_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_dz,
                         float* __restrict__ dW, TmaWgradGeom g, int* status) {
     static_assert(NB >= 1 && NB <= 4, "Cout = 32 NB");
-    static_assert(S >= 2 && S <= 4, "stages");
+    static_assert(S >= 2 && S <= 6, "stages");
+    static_assert(wgrad_tma_smem_bytes<NB, S>() <= 227 * 1024 - 1024, "shared memory per CTA");
     constexpr int BN = 32 * NB;
     constexpr int A_BYTES = 4 * kWgradChunk;
     constexpr int STAGE = A_BYTES + NB * kWgradChunk;
