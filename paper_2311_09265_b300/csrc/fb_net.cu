@@ -313,7 +313,13 @@ bool tma_wgrad_geom(const ConvGeom& g, const void* X, const void* dZ, int* R, in
 template <int NB>
 cudaError_t launch_wgrad_tma(const ConvGeom& g, int R, int I, const bf16* dZ, const bf16* X, float* dW, int sms,
                              int* status, cudaStream_t st, bool* used) {
-    constexpr int S = NB == 1 ? 5 : NB == 2 ? 4 : 3;   // as many 40-64 KB stages as fit beside the slack
+#ifndef FB_WGRAD_STAGES1
+#define FB_WGRAD_STAGES1 2
+#endif
+#ifndef FB_WGRAD_STAGES2
+#define FB_WGRAD_STAGES2 4
+#endif
+    constexpr int S = NB == 1 ? FB_WGRAD_STAGES1 : NB == 2 ? FB_WGRAD_STAGES2 : 3;   // 40-64 KB stages
     *used = false;
     const auto encode = tensor_map_encoder();
     if (!encode) return cudaSuccess;
@@ -346,9 +352,10 @@ cudaError_t launch_wgrad_tma(const ConvGeom& g, int R, int I, const bf16* dZ, co
     t.Wo = g.Wo;
     t.stride = g.stride;
     t.chunks = static_cast<int>((P + 127) / 128);
-    // one CTA per SM (the stages fill most of its shared memory): at most one wave
+    // at most one wave of the CTAs that fit on the SMs at once
+    constexpr int per_sm = (228 * 1024) / (tc::wgrad_tma_smem_bytes<NB, S>() + 2048);
     const int mt = (9 * t.Cp + tc::BM - 1) / tc::BM;
-    const int splits_max = sms / mt > 0 ? sms / mt : 1;
+    const int splits_max = per_sm * sms / mt > 0 ? per_sm * sms / mt : 1;
     t.per_split = (t.chunks + splits_max - 1) / splits_max;
     const int splits = (t.chunks + t.per_split - 1) / t.per_split;
     constexpr int smem = tc::wgrad_tma_smem_bytes<NB, S>();

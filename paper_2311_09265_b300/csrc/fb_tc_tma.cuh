@@ -396,7 +396,7 @@ struct TmaWgradGeom {
 };
 
 constexpr int kWgradChunk = 128 * 64;          // bytes of one 32-wide box of 128 K rows
-constexpr int kWgradSlack = 16 * 1024;         // dynamic shared memory past the last stage
+constexpr int kWgradSlack = 8 * 1024;          // dynamic shared memory past the last stage
 
 template <int NB, int S>
 __host__ __device__ constexpr int wgrad_tma_smem_bytes() {
