@@ -212,11 +212,15 @@ cudaError_t launch_conv_tma_rows(const ConvGeom& g, const tc::TmaConvGeom& t, co
     if (rx != CUDA_SUCCESS || rw != CUDA_SUCCESS) return cudaSuccess;
     // Three stages or none: with two the row reuse lost to the per-column kernel (the
     // 160-channel input gradient of the 32x32 decoder layer: 202 against 180 us).
+#ifndef FB_ROWS_STAGES
+#define FB_ROWS_STAGES 3
+#endif
+    constexpr int S = FB_ROWS_STAGES;
     const int stage = tc::conv_rows_stage_bytes(BN, cb, g.Wo);
-    const int smem = 3 * stage + 1024;
-    if (smem > 200 * 1024) return cudaSuccess;   // the column kernel runs instead
-    auto kern = cb == 64 ? tc::tc_conv_tma_rows_kernel<BN, 3, 64, Epi, FLIP>
-                         : tc::tc_conv_tma_rows_kernel<BN, 3, 32, Epi, FLIP>;
+    if (3 * stage + 1024 > 200 * 1024) return cudaSuccess;   // the column kernel runs instead
+    const int smem = S * stage + 1024;
+    auto kern = cb == 64 ? tc::tc_conv_tma_rows_kernel<BN, S, 64, Epi, FLIP>
+                         : tc::tc_conv_tma_rows_kernel<BN, S, 32, Epi, FLIP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((t.M + tc::BM - 1) / tc::BM, (g.Cout + BN - 1) / BN);
