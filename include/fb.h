@@ -51,7 +51,7 @@ typedef enum fb_status {
     FB_ERR_CUDA = 2,         /* a CUDA runtime call or kernel launch failed      */
     FB_ERR_OOM = 3,          /* device or pinned-host scratch allocation failed  */
     FB_ERR_TIMEOUT = 4,      /* a bounded device-side wait expired               */
-    FB_ERR_UNSUPPORTED = 5   /* valid request this build does not implement      */
+    FB_ERR_UNSUPPORTED = 5   /* valid request this library does not implement    */
 } fb_status;
 
 typedef struct fb_ctx fb_ctx;
