@@ -176,7 +176,7 @@ cudaError_t launch_conv_tma(const ConvGeom& g, const tc::TmaConvGeom& t, const b
 
 // The row-reuse form of the TMA convolution (tc_conv_tma_rows_kernel): stride 1, tiles of
 // R whole rows of one image (I == 1), Wo a multiple of 8 (the row views start on swizzle
-// atoms), Cin a multiple of 32 (channel blocks of 64 or 32).  Padding 8-channel inputs to
+// atoms), Cin a multiple of 32 (channel blocks of 32).  Padding 8-channel inputs to
 // 32-wide blocks with the boxes' zero fill was measured and is slower (the 8 -> 32 input
 // layer 86 -> ~250 us): the per-column kernel moves 8-channel columns as they are.
 bool tma_rows_geom(const ConvGeom& g, const tc::TmaConvGeom& t) {
@@ -189,8 +189,10 @@ cudaError_t launch_conv_tma_rows(const ConvGeom& g, const tc::TmaConvGeom& t, co
     *used = false;
     const auto encode = tensor_map_encoder();
     if (!encode) return cudaSuccess;
-    const int cb = g.Cin % 64 == 0 ? 64 : 32;
-    const CUtensorMapSwizzle sw = cb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    // 32-channel blocks even when Cin % 64 == 0: 64-channel ones double the stage, which cost
+    // two of three CTAs per SM (the 64-channel 32x32 layer: 78 us against 56 per tap).
+    constexpr int cb = 32;
+    const CUtensorMapSwizzle sw = CU_TENSOR_MAP_SWIZZLE_64B;
     alignas(64) CUtensorMap mx, mw;
     const cuuint64_t xdim[4] = {static_cast<cuuint64_t>(g.Cin), static_cast<cuuint64_t>(g.W),
                                 static_cast<cuuint64_t>(g.H), static_cast<cuuint64_t>(g.n)};
@@ -219,8 +221,7 @@ cudaError_t launch_conv_tma_rows(const ConvGeom& g, const tc::TmaConvGeom& t, co
     const int stage = tc::conv_rows_stage_bytes(BN, cb, g.Wo);
     if (3 * stage + 1024 > 200 * 1024) return cudaSuccess;   // the column kernel runs instead
     const int smem = S * stage + 1024;
-    auto kern = cb == 64 ? tc::tc_conv_tma_rows_kernel<BN, S, 64, Epi, FLIP>
-                         : tc::tc_conv_tma_rows_kernel<BN, S, 32, Epi, FLIP>;
+    auto kern = tc::tc_conv_tma_rows_kernel<BN, S, cb, Epi, FLIP>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     const dim3 grid((t.M + tc::BM - 1) / tc::BM, (g.Cout + BN - 1) / BN);
