@@ -266,9 +266,85 @@ cudaError_t conv_forward(const ConvGeom& g, const bf16* X, const bf16* Wt, const
     return launch_gemm_async<128>(GatherFwd<128>{X, Wt, g, M, K, ncb}, epi, M, g.Cout, K, status, st);
 }
 
+// Input gradient of a stride-2 layer by output parity (tc_conv_tma_s2grad_kernel): gz is
+// the output gradient's grid as a stride-1 geometry (Cin = the layer's Cout, the GEMM's K
+// channels; Cout = the layer's Cin, its N), t its whole-row tiles.
+template <int BN, class Epi>
+cudaError_t launch_conv_tma_s2grad(const ConvGeom& gz, const tc::TmaConvGeom& t, const bf16* dZ,
+                                   const bf16* WT, const Epi& epi, int* status, cudaStream_t st, bool* used) {
+    *used = false;
+    const auto encode = tensor_map_encoder();
+    if (!encode) return cudaSuccess;
+    const int cb = gz.Cin % 64 == 0 ? 64 : 32;
+    const CUtensorMapSwizzle sw = cb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+    alignas(64) CUtensorMap mx, mw;
+    const cuuint64_t xdim[4] = {static_cast<cuuint64_t>(gz.Cin), static_cast<cuuint64_t>(gz.W),
+                                static_cast<cuuint64_t>(gz.H), static_cast<cuuint64_t>(gz.n)};
+    const cuuint64_t xstr[3] = {static_cast<cuuint64_t>(gz.Cin) * 2, static_cast<cuuint64_t>(gz.W) * gz.Cin * 2,
+                                static_cast<cuuint64_t>(gz.H) * gz.W * gz.Cin * 2};
+    const cuuint32_t xbox[4] = {static_cast<cuuint32_t>(cb), static_cast<cuuint32_t>(gz.Wo),
+                                static_cast<cuuint32_t>(t.R), static_cast<cuuint32_t>(t.I)};
+    const cuuint32_t ones[4] = {1, 1, 1, 1};
+    const CUresult rx = encode(&mx, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16*>(dZ), xdim, xstr, xbox,
+                               ones, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    const cuuint64_t wdim[2] = {static_cast<cuuint64_t>(9) * gz.Cin, static_cast<cuuint64_t>(gz.Cout)};
+    const cuuint64_t wstr[1] = {static_cast<cuuint64_t>(9) * gz.Cin * 2};
+    const cuuint32_t wbox[2] = {static_cast<cuuint32_t>(cb), static_cast<cuuint32_t>(BN)};
+    const CUresult rw = encode(&mw, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16*>(WT), wdim, wstr, wbox,
+                               ones, CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (rx != CUDA_SUCCESS || rw != CUDA_SUCCESS) return cudaSuccess;
+    // tap row options per parity: (tap row, displacement) -- py = 0: (1, 0); py = 1: (0, +1), (2, 0)
+    tc::ParityClasses pc{};
+    for (int cls = 0; cls < 4; ++cls) {
+        const int py = cls >> 1, px = cls & 1;
+        const int ny = py ? 2 : 1, nx = px ? 2 : 1;
+        int k = 0;
+        for (int a = 0; a < ny; ++a)
+            for (int b = 0; b < nx; ++b) {
+                const int ty = py ? (a == 0 ? 0 : 2) : 1, sy = py && a == 0 ? 1 : 0;
+                const int tx = px ? (b == 0 ? 0 : 2) : 1, sx = px && b == 0 ? 1 : 0;
+                pc.tap[cls][k] = ty * 3 + tx;
+                pc.sy[cls][k] = sy;
+                pc.sx[cls][k] = sx;
+                ++k;
+            }
+        pc.ntaps[cls] = k;
+    }
+    constexpr int S = 3;
+    const int stage = (tc::BM * 2 * cb + BN * 2 * cb + 1023) / 1024 * 1024;
+    const int smem = S * stage + 1024;
+    auto kern = cb == 64 ? tc::tc_conv_tma_s2grad_kernel<BN, S, 64, Epi> : tc::tc_conv_tma_s2grad_kernel<BN, S, 32, Epi>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const dim3 grid((t.M + tc::BM - 1) / tc::BM, (gz.Cout + BN - 1) / BN, 4);
+    kern<<<grid, 128, smem, st>>>(mx, mw, epi, t, pc, status);
+    e = cudaGetLastError();
+    if (e == cudaSuccess) {
+        *used = true;
+        ++g_tma_launches;
+    }
+    return e;
+}
+
 template <class Epi>
 cudaError_t conv_dgrad_epi(const ConvGeom& g, const bf16* dZ, const bf16* WT, const Epi& epi, int* status,
                            cudaStream_t st) {
+    // Stride 2 with an even input: by output parity, from TMA-staged boxes of dZ.
+    if (g.stride == 2 && g_gemm_path.load() != 1 && g.H == 2 * g.Ho && g.W == 2 * g.Wo && g.Cout % 32 == 0) {
+        const ConvGeom gz{g.n, g.Ho, g.Wo, g.Cout, g.Ho, g.Wo, g.Cin, 1};
+        tc::TmaConvGeom t;
+        if (tma_conv_geom(gz, dZ, WT, t)) {
+            bool used = false;
+            cudaError_t e = gz.Cout <= 16   ? launch_conv_tma_s2grad<16, Epi>(gz, t, dZ, WT, epi, status, st, &used)
+                            : gz.Cout <= 32 ? launch_conv_tma_s2grad<32, Epi>(gz, t, dZ, WT, epi, status, st, &used)
+                            : gz.Cout <= 64 ? launch_conv_tma_s2grad<64, Epi>(gz, t, dZ, WT, epi, status, st, &used)
+                            : gz.Cout == 96 ? launch_conv_tma_s2grad<96, Epi>(gz, t, dZ, WT, epi, status, st, &used)
+                                            : launch_conv_tma_s2grad<128, Epi>(gz, t, dZ, WT, epi, status, st, &used);
+            if (e != cudaSuccess || used) return e;
+        }
+    }
     const int M = g.n * g.H * g.W, K = 9 * g.Cout, ncb = (g.Cout + 63) / 64;
     // Stride 1: the input gradient is the 3x3 convolution of dZ with the tap-mirrored
     // transposed weights, staged by TMA like the forward layers (FLIP), where the boxes tile.

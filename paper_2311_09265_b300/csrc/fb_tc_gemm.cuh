@@ -1,7 +1,8 @@
 // fb_tc_gemm.cuh -- a BF16 GEMM on the 5th-generation tensor cores (tcgen05) whose
 // operands are gathered by the CTA's threads, used by the 3x3 convolutions of the
 // learned NNF initialiser where the TMA-staged kernels (fb_tc_tma.cuh) do not apply: the
-// stride-2 input gradients, and the layers whose output rows do not tile 128-pixel blocks.
+// layers whose output rows do not tile 128-pixel blocks, and the input gradients of
+// stride-2 layers with odd inputs.
 //
 //   D[M x N] (+)= A[M x K] . B[N x K]^T,  bf16 inputs, fp32 accumulation in TMEM.
 //

@@ -2,8 +2,9 @@
 // whose operands the Tensor Memory Accelerator stages: tc_conv_tma_kernel (forward, stride
 // s = 1 or 2, one box per tap; with FLIP the stride-1 input gradient), described here;
 // tc_conv_tma_rows_kernel (the same with the three row taps of a column sharing one halo
-// box); tc_wgrad_tma_kernel (the weight gradient, both operands MN-major).  Each is
-// described above its definition.
+// box); tc_conv_tma_s2grad_kernel (the stride-2 input gradient by output parity);
+// tc_wgrad_tma_kernel (the weight gradient, both operands MN-major).  Each is described
+// above its definition.
 //
 //   Y[p][co] = sum_{tap, ci} X[s p + tap - (1, 1)][ci] W[co][tap][ci]    (M = output
 //   pixels, N = Cout, K = 9 Cin, walked tap-major in chunks of K = 64)
@@ -339,6 +340,134 @@ __global__ void __launch_bounds__(128)
             float v[16];
             tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
             if (row < g.M && n0 + c0 < g.Cout) epi.store(row, n0 + c0, v);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem),
+                     "r"(TmemCols<BN>::value));
+}
+
+// ---------------------------------------------------------------------------------
+// Input gradient of a stride-2 layer by output parity.  The forward reads input pixel
+// (2 oy + ty - 1, 2 ox + tx - 1) for output (oy, ox) and tap (ty, tx), so an input row
+// 2 m + py receives tap row ty = 1 from output row m (py = 0), or tap rows 0 and 2 from
+// output rows m + 1 and m (py = 1); likewise for columns.  Each of the four parity classes
+// (py, px) of dX is therefore a stride-1 convolution over the output gradient's grid with
+// one, two or four taps at displacements 0 or +1 (past the far edge: the box's zero fill):
+//   dX[2 m + py][2 m' + px][ci] = sum_{class taps, co} dZ[m + sy][m' + sx][co] WT[ci][tap][co].
+// blockIdx.z is the class; a tile is 128 class pixels (the forward's whole-row tiles of the
+// Ho x Wo grid); each K column is one (tap, CB-channel block): the box {CB, Wo, R, I} of dZ
+// at (x = sx, y = y0 + sy) and the weight box {CB of the 9 C K elements, BN}; the epilogue
+// stores row (img, 2 m + py, 2 m' + px) of dX.
+// ---------------------------------------------------------------------------------
+struct ParityClasses {
+    int ntaps[4];
+    int sx[4][4], sy[4][4], tap[4][4];   // per class and tap: displacements, weight tap index
+};
+
+template <int BN, int S, int CB, class Epi>
+__global__ void __launch_bounds__(128)
+    tc_conv_tma_s2grad_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_w,
+                              Epi epi, TmaConvGeom g, ParityClasses pc, int* status) {
+    static_assert(BN % 16 == 0 && BN >= 16 && BN <= 128, "tile N");
+    static_assert(S >= 2 && S <= 4, "stages");
+    static_assert(CB == 32 || CB == 64, "column width");
+    constexpr int RB = 2 * CB;
+    constexpr uint32_t A_BYTES = BM * RB;
+    constexpr uint32_t WB = static_cast<uint32_t>(BN) * RB;
+    constexpr uint32_t STAGE = (A_BYTES + WB + 1023u) & ~1023u;
+    extern __shared__ __align__(1024) unsigned char smem[];
+    __shared__ __align__(8) uint64_t full[S];
+    __shared__ __align__(8) uint64_t empty[S];
+    __shared__ uint32_t tmem_base;
+    __shared__ int s_ok;
+
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * BM, n0 = blockIdx.y * BN, cls = blockIdx.z;
+    const int py = cls >> 1, px = cls & 1;
+    const int cpt = g.Cin / CB;                    // channel blocks of dZ (Cin % CB == 0)
+    const int n_cols = pc.ntaps[cls] * cpt;
+    const int img0 = m0 / (g.Ho * g.Wo);
+    const int y0 = (m0 - img0 * g.Ho * g.Wo) / g.Wo;
+    const uint32_t s0 = (smem_u32(smem) + 1023u) & ~1023u;
+
+    if (threadIdx.x == 0) {
+#pragma unroll
+        for (int s = 0; s < S; ++s) {
+            mbar_init(&full[s]);
+            mbar_init(&empty[s]);
+        }
+        s_ok = 1;
+        asm volatile("fence.mbarrier_init.release.cluster;");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(&tmem_base)),
+                     "r"(TmemCols<BN>::value));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_base;
+    constexpr uint32_t idesc = instr_desc(BN);
+
+    if (threadIdx.x == 0) {
+        bool ok = true;
+        int issued = 0;
+        const long lim = progress_limit();
+        auto issue = [&](int q) {
+            const int s = q % S;
+            const uint32_t sa = s0 + s * STAGE;
+            const int t = q / cpt, blk = q - t * cpt;
+            mbar_expect_tx(&full[s], A_BYTES + WB);
+            tma_load_4d(sa, &map_x, &full[s], CB * blk, pc.sx[cls][t], y0 + pc.sy[cls][t], img0);
+            tma_load_2d(sa + A_BYTES, &map_w, &full[s], pc.tap[cls][t] * g.Cin + CB * blk, n0);
+            ++issued;
+        };
+        for (int c = 0; c < S - 1 && c < n_cols; ++c) issue(c);
+        int done = 0;
+        for (int i = 0; i < n_cols && ok; ++i) {
+            const int s = i % S;
+            ok = mbar_wait(&full[s], (i / S) & 1, lim);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const uint32_t sa = s0 + s * STAGE;
+#pragma unroll
+            for (int j = 0; j < CB / 16; ++j)
+                mma_bf16(tmem, smem_desc_sw<RB>(sa + 32u * j), smem_desc_sw<RB>(sa + A_BYTES + 32u * j), idesc,
+                         (i > 0 || j > 0) ? 1u : 0u);
+            mma_commit(&empty[s]);
+            ++done;
+            const int nxt = i + S - 1;
+            if (nxt < n_cols) {
+                const int prev = nxt - S;
+                if (prev >= 0) ok = mbar_wait(&empty[prev % S], (prev / S) & 1, lim);
+                if (ok) issue(nxt);
+            }
+        }
+        if (ok && done > 0) ok = mbar_wait(&empty[(done - 1) % S], ((done - 1) / S) & 1, lim);
+        if (!ok) {
+            if (done > 0) mbar_wait(&empty[(done - 1) % S], ((done - 1) / S) & 1);
+            for (int c = done; c < issued; ++c) mbar_wait(&full[c % S], (c / S) & 1);
+            s_ok = 0;
+            atomicExch(status, 1);
+        }
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (s_ok) {
+        const int m = m0 + warp * 32 + lane;   // class pixel: (img, oy, ox) of the Ho x Wo grid
+        const int img = m / (g.Ho * g.Wo), rem = m - img * g.Ho * g.Wo;
+        const int oy = rem / g.Wo, ox = rem - oy * g.Wo;
+        const int row = (img * (2 * g.Ho) + 2 * oy + py) * (2 * g.Wo) + 2 * ox + px;   // dX pixel
+#pragma unroll
+        for (int c0 = 0; c0 < BN; c0 += 16) {
+            float v[16];
+            tmem_ld16(tmem + (static_cast<uint32_t>(warp * 32) << 16) + c0, v);
+            if (m < g.M && n0 + c0 < g.Cout) epi.store(row, n0 + c0, v);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");

@@ -199,3 +199,56 @@ def test_weight_gradients_the_tma_boxes_cannot_tile_use_the_gathers(fbp, n, H, W
     w = np.zeros((Cout, 3, 3, Cin))
     _, dw_ref, _ = ref.conv3x3_backward(x, w, dz, stride)
     assert float(np.linalg.norm(dw.cpu().numpy() - dw_ref) / np.linalg.norm(dw_ref)) < 1e-5
+
+
+S2_DGRAD_CASES = [  # n, H, W, Cin, Cout of stride-2 layers with even inputs: output-parity classes
+    (2, 64, 64, 32, 64), (2, 32, 32, 64, 96), (3, 16, 16, 96, 128), (2, 64, 64, 32, 32), (2, 32, 64, 16, 64),
+]
+
+
+@pytest.mark.parametrize("n,H,W,Cin,Cout", S2_DGRAD_CASES)
+def test_stride2_input_gradient_by_output_parity(fbp, n, H, W, Cin, Cout):
+    """Stride 2: every parity class of dX is a stride-1 convolution of dZ with its one, two or
+    four taps at displacements 0 or +1, staged by TMA (mode 0); the gathered path (mode 1)
+    walks all nine taps: the same products in another order, so equal to fp32 rounding, and
+    both equal the FP64 oracle."""
+    import torch
+    rng = np.random.default_rng(n * 11 + H + W + Cin + Cout)
+    x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
+    w = ref.bf16(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin))
+    dz = ref.bf16(rng.normal(size=(n, H // 2, W // 2, Cout)))
+    wt = np.ascontiguousarray(np.transpose(w, (3, 1, 2, 0)))
+    out = {}
+    for mode in (1, 0):
+        fbp.fb_conv_gemm_path(mode)
+        n0 = fbp.fb_conv_gemm_path(-1)
+        dx, _, st = fbp.conv3x3_backward(to_bf16_tensor(x), to_bf16_tensor(wt), to_bf16_tensor(dz), 2,
+                                         weight_grad=False)
+        torch.cuda.synchronize()
+        assert int(st.item()) == 0
+        out[mode] = (dx.cpu().numpy(), fbp.fb_conv_gemm_path(-1) - n0)
+    fbp.fb_conv_gemm_path(0)
+    (dxg, used_g), (dxt, used_t) = out[1], out[0]
+    assert used_g == 0 and used_t == 1
+    assert float(np.linalg.norm(dxt - dxg) / np.linalg.norm(dxg)) < 1e-6
+    dx_ref, _, _ = ref.conv3x3_backward(x, w, dz, 2)
+    assert float(np.linalg.norm(dxt - dx_ref) / np.linalg.norm(dx_ref)) < 1e-5
+
+
+@pytest.mark.parametrize("n,H,W,Cin,Cout", [(2, 32, 32, 32, 24), (2, 34, 34, 32, 64), (2, 33, 32, 32, 64)])
+def test_stride2_input_gradients_the_parity_kernel_cannot_take_use_the_gathers(fbp, n, H, W, Cin, Cout):
+    """Cout not a multiple of 32, a row width that does not tile, or an odd input size."""
+    import torch
+    rng = np.random.default_rng(5)
+    x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
+    w = ref.bf16(rng.normal(size=(Cout, 3, 3, Cin)) / np.sqrt(9 * Cin))
+    Ho, Wo = ref.out_size(H, 2), ref.out_size(W, 2)
+    dz = ref.bf16(rng.normal(size=(n, Ho, Wo, Cout)))
+    wt = np.ascontiguousarray(np.transpose(w, (3, 1, 2, 0)))
+    n0 = fbp.fb_conv_gemm_path(-1)
+    dx, _, st = fbp.conv3x3_backward(to_bf16_tensor(x), to_bf16_tensor(wt), to_bf16_tensor(dz), 2,
+                                     weight_grad=False)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and fbp.fb_conv_gemm_path(-1) == n0
+    dx_ref, _, _ = ref.conv3x3_backward(x, w, dz, 2)
+    assert float(np.linalg.norm(dx.cpu().numpy() - dx_ref) / np.linalg.norm(dx_ref)) < 1e-5

@@ -101,6 +101,26 @@ def test_backward_layer_times_out_then_recovers(fbp, expire, path):
         fbp.fb_conv_gemm_path(0)
 
 
+def test_stride2_input_gradient_times_out_then_recovers(fbp, expire):
+    """The parity-class input gradient of a stride-2 layer (TMA-fed)."""
+    import torch
+    x, w, _ = _layer(31, 2, 32, 32, 32, 64)
+    wt = w.permute(3, 1, 2, 0).contiguous()
+    g = torch.Generator().manual_seed(7)
+    dz = torch.randn((2, 16, 16, 64), generator=g).to(torch.bfloat16).cuda()
+    dx0, _, st = fbp.conv3x3_backward(x, wt, dz, 2, weight_grad=False)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    tma0 = fbp.fb_conv_gemm_path(-1)
+    with expire():
+        _, _, st = fbp.conv3x3_backward(x, wt, dz, 2, weight_grad=False)
+        torch.cuda.synchronize()
+    assert int(st.item()) == 1 and fbp.fb_conv_gemm_path(-1) > tma0
+    dx1, _, st = fbp.conv3x3_backward(x, wt, dz, 2, weight_grad=False)
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0 and torch.equal(dx1, dx0)
+
+
 def test_network_forward_reports_timeout_then_recovers(fbp, expire):
     import torch
 
