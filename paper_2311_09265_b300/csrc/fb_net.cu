@@ -639,38 +639,69 @@ __global__ void concat_up_kernel(const bf16* __restrict__ lo, int C1, const bf16
 // Gradient of the upsampled part of a concatenation: dlo[p][c] = the sum of the 2 x 2
 // block of dout's first C1 channels above p, added to dlo (acc_lo) or written (first
 // writer).  The skip part (dout's last C2 channels) is not copied: the ReLU backward of the
-// skip tensor's layer adds it where it reads that tensor's gradient.
+// skip tensor's layer adds it where it reads that tensor's gradient.  One thread per 8
+// channels of one pixel (C1, C2 multiples of 8), 32-byte accesses; the same sums per value.
 __global__ void concat_up_bwd_kernel(const float* __restrict__ dout, int C1, int C2, int n, int H2,
                                      int W2, float* __restrict__ dlo, int acc_lo) {
     const int C = C1 + C2;
     const int H = H2 / 2, W = W2 / 2;
-    const size_t lo_total = static_cast<size_t>(n) * H * W * C1;
-    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
-    if (i >= lo_total) return;
-    const int c = static_cast<int>(i % C1);
-    const size_t p = i / C1;
+    const size_t units = static_cast<size_t>(n) * H * W * (C1 / 8);
+    const size_t u = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (u >= units) return;
+    const int c = static_cast<int>(u % (C1 / 8)) * 8;
+    const size_t p = u / (C1 / 8);
     const int img = static_cast<int>(p / (static_cast<size_t>(H) * W));
     const int rem = static_cast<int>(p - static_cast<size_t>(img) * H * W);
     const int y = rem / W, x = rem % W;
-    float s = 0.f;
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     for (int dy = 0; dy < 2; ++dy)
-        for (int dx = 0; dx < 2; ++dx)
-            s += dout[((static_cast<size_t>(img) * H2 + 2 * y + dy) * W2 + 2 * x + dx) * C + c];
-    dlo[i] = acc_lo ? dlo[i] + s : s;
+        for (int dx = 0; dx < 2; ++dx) {
+            const float4* q = reinterpret_cast<const float4*>(
+                dout + ((static_cast<size_t>(img) * H2 + 2 * y + dy) * W2 + 2 * x + dx) * C + c);
+            const float4 a = __ldg(q), b = __ldg(q + 1);
+            s[0] += a.x; s[1] += a.y; s[2] += a.z; s[3] += a.w;
+            s[4] += b.x; s[5] += b.y; s[6] += b.z; s[7] += b.w;
+        }
+    float4* d = reinterpret_cast<float4*>(dlo + p * C1 + c);
+    if (acc_lo) {
+        const float4 a = d[0], b = d[1];
+        d[0] = make_float4(a.x + s[0], a.y + s[1], a.z + s[2], a.w + s[3]);
+        d[1] = make_float4(b.x + s[4], b.y + s[5], b.z + s[6], b.w + s[7]);
+    } else {
+        d[0] = make_float4(s[0], s[1], s[2], s[3]);
+        d[1] = make_float4(s[4], s[5], s[6], s[7]);
+    }
 }
 
 // dZ = dA * (A > 0) in bf16 (ReLU backward); relu == 0 passes dA through.  With add, the
 // gradient is dA + the skip slice of a concatenation's gradient: add[(i / C) * add_stride +
-// add_off + i % C] (the skip tensor's other consumer).
+// add_off + i % C] (the skip tensor's other consumer).  One thread per 8 values (C, n,
+// add_stride and add_off multiples of 8), 16- and 32-byte accesses; A is read only with relu.
 __global__ void relu_bwd_kernel(const float* __restrict__ dA, const bf16* __restrict__ A, size_t n,
                                 int relu, bf16* __restrict__ dZ, const float* __restrict__ add, int C,
                                 int add_stride, int add_off) {
-    const size_t i = static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const size_t i = (static_cast<size_t>(blockIdx.x) * blockDim.x + threadIdx.x) * 8;
     if (i >= n) return;
-    float g = dA[i];
-    if (add) g += add[(i / C) * add_stride + add_off + i % C];
-    if (relu && !(__bfloat162float(A[i]) > 0.f)) g = 0.f;
-    dZ[i] = __float2bfloat16_rn(g);
+    const float4 a0 = __ldg(reinterpret_cast<const float4*>(dA + i));
+    const float4 a1 = __ldg(reinterpret_cast<const float4*>(dA + i) + 1);
+    float g[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+    if (add) {
+        const float4* q = reinterpret_cast<const float4*>(add + (i / C) * add_stride + add_off + i % C);
+        const float4 b0 = __ldg(q), b1 = __ldg(q + 1);
+        g[0] += b0.x; g[1] += b0.y; g[2] += b0.z; g[3] += b0.w;
+        g[4] += b1.x; g[5] += b1.y; g[6] += b1.z; g[7] += b1.w;
+    }
+    __align__(16) bf16 z[8];
+    if (relu) {
+        __align__(16) bf16 a[8];
+        *reinterpret_cast<uint4*>(a) = __ldg(reinterpret_cast<const uint4*>(A + i));
+#pragma unroll
+        for (int j = 0; j < 8; ++j) z[j] = __float2bfloat16_rn(!(__bfloat162float(a[j]) > 0.f) ? 0.f : g[j]);
+    } else {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) z[j] = __float2bfloat16_rn(g[j]);
+    }
+    *reinterpret_cast<uint4*>(dZ + i) = *reinterpret_cast<const uint4*>(z);
 }
 
 // db[c] += sum_p dZ[p][c]
@@ -1151,7 +1182,7 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
             const int to = kOut[l] < 0 ? 15 : kOut[l];
             if (!written[to]) return FB_ERR_CUDA;  // unreachable: every gradient is written first
             const int cat = skip_cat[to];
-            relu_bwd_kernel<<<blocks(out_elems), 256, 0, st>>>(
+            relu_bwd_kernel<<<blocks(out_elems / 8), 256, 0, st>>>(
                 dA, A ? A : net->act[0], out_elems, kLayers[l].relu, dz, cat >= 0 ? net->dact[cat] : nullptr,
                 g.Cout, cat >= 0 ? kTens[cat].ch : 0, skip_off[to]);
             NET_CUDA(net, cudaGetLastError());
@@ -1183,7 +1214,7 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
             const int skip = l == 8 ? 6 : (l == 9 ? 4 : 2);
             const int cat = kIn[l];
             const int H2 = (net->H / net->ds) / kTens[cat].div, W2 = (net->W / net->ds) / kTens[cat].div;
-            const size_t tot = tens_elems(net, lo, n);
+            const size_t tot = tens_elems(net, lo, n) / 8;
             concat_up_bwd_kernel<<<blocks(tot), 256, 0, st>>>(net->dact[cat], kTens[lo].ch, kTens[skip].ch, n,
                                                               H2, W2, net->dact[lo], written[lo] ? 1 : 0);
             NET_CUDA(net, cudaGetLastError());
