@@ -73,7 +73,7 @@ def parse_args(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("fastblend", "reference"), default="fastblend")
     ap.add_argument("--workload", default="blend_512",
-                    choices=sorted(synth.WORKLOADS) + ["batch_32", "learned_512", "initnet_512",
+                    choices=sorted(synth.WORKLOADS) + ["batch_32", "batch_small", "learned_512", "initnet_512",
                                                        "balanced_512", "fast_512", "accurate_512",
                                                        "tracking_1024x576", "tracking_512",
                                                        "aligned_1024x576"])
@@ -336,10 +336,10 @@ def run_reference(args):
     if rank != 0:
         return 0
     import oracle
-    if args.workload == "batch_32":
-        N, H, W, window, patch = synth.batch_manifest(seed=BATCH_SEED)[0]
+    if args.workload in BATCH_MANIFESTS:
+        N, H, W, window, patch = batch_manifest(args.workload, BATCH_SEED)[0]
         g, s = synth.batch_clip(N, H, W, seed=BATCH_SEED)
-        w = synth.Workload("batched persistent submission of 32 uneven clips (sample: clip 0)",
+        w = synth.Workload(f"batched submission of the {args.workload} manifest (sample: clip 0)",
                            "blend", N, H, W, patch=patch, iters=BATCH_ITERS, window=window,
                            seed=BATCH_SEED)
     else:
@@ -767,6 +767,21 @@ def run_gpu(args):
 # ----------------------------------------------------------------------------------
 BATCH_SEED = synth.clip_seed(3)
 BATCH_ITERS = 6
+# The batched workloads' manifests: 32 uneven clips of 256-1024 px (per-clip launches
+# already fill the GPU), and 512 small clips of 64-128 px (a serving mix of thumbnails:
+# one clip's launches fill a fraction of the SMs, and launches are many).
+BATCH_MANIFESTS = {
+    "batch_32": dict(n_clips=32, sizes=(256, 1024), frames=(16, 120), windows=(5, 31)),
+    "batch_small": dict(n_clips=512, sizes=(64, 128), frames=(6, 12), windows=(3, 5)),
+}
+BATCH_DESCRIPTIONS = {
+    "batch_32": "32 uneven clips (256-1024 px, 16-120 frames, windows 5-31, patch 5/7, n=6)",
+    "batch_small": "512 small clips (64-128 px, 6-12 frames, windows 3-5, patch 5/7, n=6)",
+}
+
+
+def batch_manifest(workload: str, seed: int):
+    return synth.batch_manifest(seed=seed, **BATCH_MANIFESTS[workload])
 
 
 def batch_iter_ops(manifest) -> int:
@@ -800,7 +815,7 @@ def run_gpu_batch(args):
     local = rank_device(local)
     torch.cuda.set_device(local)
     fbp.build()
-    manifest = synth.batch_manifest(seed=shard_seed(BATCH_SEED, rank))
+    manifest = batch_manifest(args.workload, shard_seed(BATCH_SEED, rank))
     picked = ([int(i) for i in args.batch_clips.split(",")] if args.batch_clips
               else list(range(len(manifest))))
     manifest = [manifest[i] for i in picked]
@@ -906,8 +921,7 @@ def run_gpu_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": total_ms / args.steps,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
         "data": "synthetic",
-        "config": {"workload": (f"batched persistent submission of {len(manifest)} uneven clips "
-                                "(256-1024 px, 16-120 frames, windows 5-31, patch 5/7, n=6)"
+        "config": {"workload": (f"batched persistent submission of {BATCH_DESCRIPTIONS[args.workload]}"
                                 + (f", manifest clips {args.batch_clips}" if args.batch_clips else "")),
                    "frames_per_step": frames, "clips": len(manifest),
                    "nnfs_per_step": sum(sum(min(N - 1, i + (w - 1) // 2) - max(0, i - (w - 1) // 2)
@@ -1068,7 +1082,7 @@ def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
-    if args.workload == "batch_32":
+    if args.workload in BATCH_MANIFESTS:
         return run_gpu_batch(args)
     if args.workload == "initnet_512":
         return run_gpu_initnet(args)
