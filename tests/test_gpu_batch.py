@@ -176,3 +176,33 @@ def test_full_manifest_in_the_bench_launch_configuration(fbp):
         ref = oracle.blend_frame(g, s, window, N // 2, patch, bench.BATCH_ITERS, seed=bench.BATCH_SEED)
         assert (outs[i][N // 2].cpu().numpy() == ref).all(), (i, manifest[i])
     ctx.close()
+
+
+def test_small_clip_manifest_matches_per_clip_calls_and_oracle(fbp):
+    """The first 64 clips of the small-clip manifest bench.py times (64-128 px, 6-12 frames,
+    windows 3-5, patch 5 and 7; tuned, graph-replayed as timed): every clip bit for bit
+    equal to its own fb_blend_window call, and the first clip of each patch size to the
+    oracle over the whole clip."""
+    import torch
+    import bench
+    manifest = bench.batch_manifest("batch_small", bench.BATCH_SEED)[:64]
+    clips, host = [], []
+    for n, (N, H, W, window, patch) in enumerate(manifest):
+        g, s = synth.batch_clip(N, H, W, seed=bench.BATCH_SEED + n)
+        host.append((g, s))
+        clips.append((torch.tensor(g, device="cuda"), torch.tensor(s, device="cuda"), window, patch))
+    ctx = fbp.Context(0)
+    params = fbp.Params.make(5, bench.BATCH_ITERS, 1, 0, bench.BATCH_SEED)
+    fbp.fb_blend_batch(ctx, clips, params)            # tunes and captures
+    outs = fbp.fb_blend_batch(ctx, clips, params)     # graph replay, as timed
+    for i, (N, H, W, window, patch) in enumerate(manifest):
+        want = fbp.fb_blend_window(ctx, clips[i][0], clips[i][1], window,
+                                   fbp.Params.make(patch, bench.BATCH_ITERS, 1, 0, bench.BATCH_SEED))
+        assert torch.equal(outs[i], want), (i, manifest[i])
+    for k in (5, 7):
+        i = next(c for c in range(len(manifest)) if manifest[c][4] == k)
+        N, H, W, window, patch = manifest[i]
+        g, s = host[i]
+        ref = oracle.blend_window(g, s, window, patch, bench.BATCH_ITERS, seed=bench.BATCH_SEED)
+        assert (outs[i].cpu().numpy() == ref).all(), (i, manifest[i])
+    ctx.close()
