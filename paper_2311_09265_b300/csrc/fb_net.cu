@@ -38,14 +38,24 @@ constexpr int kOffsetScale = 16;
 // ---------------------------------------------------------------------------------
 // Conv launchers
 // ---------------------------------------------------------------------------------
-template <int BN, class G, class E>
-cudaError_t launch_gemm(const G& gth, const E& epi, int M, int N, int K, int splits, int* status,
-                        cudaStream_t st) {
+// K chunks per split and the number of splits the gathered GEMM runs for a requested
+// split count: every split gets at least one chunk.
+int gemm_per_split(int K, int splits) {
     const int chunks = (K + tc::BK - 1) / tc::BK;
     if (splits < 1) splits = 1;
     if (splits > chunks) splits = chunks;
-    const int per = (chunks + splits - 1) / splits;
-    splits = (chunks + per - 1) / per;
+    return (chunks + splits - 1) / splits;
+}
+int gemm_splits(int K, int splits) {
+    const int chunks = (K + tc::BK - 1) / tc::BK, per = gemm_per_split(K, splits);
+    return (chunks + per - 1) / per;
+}
+
+template <int BN, class G, class E>
+cudaError_t launch_gemm(const G& gth, const E& epi, int M, int N, int K, int splits, int* status,
+                        cudaStream_t st) {
+    const int per = gemm_per_split(K, splits);
+    splits = gemm_splits(K, splits);
     const dim3 grid((M + tc::BM - 1) / tc::BM, (N + BN - 1) / BN, splits);
     constexpr int smem = tc::gemm_smem_bytes<BN>();
     auto kern = tc::tc_gemm_kernel<BN, G, E>;
@@ -391,16 +401,36 @@ bool tma_wgrad_geom(const ConvGeom& g, const void* X, const void* dZ, int* R, in
     return g.stride * g.Wo <= 256 && g.stride * *R <= 256;
 }
 
-template <int NB>
-cudaError_t launch_wgrad_tma(const ConvGeom& g, int R, int I, const bf16* dZ, const bf16* X, float* dW, int sms,
-                             int* status, cudaStream_t st, bool* used) {
 #ifndef FB_WGRAD_STAGES1
 #define FB_WGRAD_STAGES1 2
 #endif
 #ifndef FB_WGRAD_STAGES2
 #define FB_WGRAD_STAGES2 4
 #endif
-    constexpr int S = NB == 1 ? FB_WGRAD_STAGES1 : NB == 2 ? FB_WGRAD_STAGES2 : 3;   // 40-64 KB stages
+template <int NB>
+constexpr int wgrad_stages() { return NB == 1 ? FB_WGRAD_STAGES1 : NB == 2 ? FB_WGRAD_STAGES2 : 3; }  // 40-64 KB stages
+template <int NB>
+constexpr int wgrad_per_sm() { return (228 * 1024) / (tc::wgrad_tma_smem_bytes<NB, wgrad_stages<NB>()>() + 2048); }
+
+// Pixel splits of the TMA-fed weight gradient: at most one wave of the CTAs that fit on the
+// SMs at once, every split at least one chunk of 128 pixels.
+int wgrad_tma_splits_max(const ConvGeom& g, int nb, int sms) {
+    const int per_sm = nb == 1 ? wgrad_per_sm<1>() : nb == 2 ? wgrad_per_sm<2>()
+                     : nb == 3 ? wgrad_per_sm<3>() : wgrad_per_sm<4>();
+    const int mt = (9 * ((g.Cin + 31) / 32 * 32) + tc::BM - 1) / tc::BM;
+    return per_sm * sms / mt > 0 ? per_sm * sms / mt : 1;
+}
+
+// Split count the gathered weight gradient asks for: two CTAs per SM over its N tiles.
+int wgrad_gather_splits(const ConvGeom& g, int sms) {
+    const int ntiles = (9 * g.Cin + 127) / 128;
+    return (2 * sms + ntiles - 1) / ntiles;
+}
+
+template <int NB>
+cudaError_t launch_wgrad_tma(const ConvGeom& g, int R, int I, const bf16* dZ, const bf16* X, float* part, int sms,
+                             int* status, cudaStream_t st, bool* used, int* splits_out) {
+    constexpr int S = wgrad_stages<NB>();
     *used = false;
     const auto encode = tensor_map_encoder();
     if (!encode) return cudaSuccess;
@@ -433,42 +463,129 @@ cudaError_t launch_wgrad_tma(const ConvGeom& g, int R, int I, const bf16* dZ, co
     t.Wo = g.Wo;
     t.stride = g.stride;
     t.chunks = static_cast<int>((P + 127) / 128);
-    // at most one wave of the CTAs that fit on the SMs at once
-    constexpr int per_sm = (228 * 1024) / (tc::wgrad_tma_smem_bytes<NB, S>() + 2048);
     const int mt = (9 * t.Cp + tc::BM - 1) / tc::BM;
-    const int splits_max = per_sm * sms / mt > 0 ? per_sm * sms / mt : 1;
+    const int splits_max = wgrad_tma_splits_max(g, NB, sms);
     t.per_split = (t.chunks + splits_max - 1) / splits_max;
     const int splits = (t.chunks + t.per_split - 1) / t.per_split;
     constexpr int smem = tc::wgrad_tma_smem_bytes<NB, S>();
     auto kern = tc::tc_wgrad_tma_kernel<NB, S>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
-    kern<<<dim3(mt, splits), 128, smem, st>>>(mx, mz, dW, t, status);
+    kern<<<dim3(mt, splits), 128, smem, st>>>(mx, mz, part, t, status);
     e = cudaGetLastError();
     if (e == cudaSuccess) {
         *used = true;
+        *splits_out = splits;
         ++g_tma_launches;
     }
     return e;
 }
 
-cudaError_t conv_wgrad(const ConvGeom& g, const bf16* dZ, const bf16* X, float* dW, int sms,
-                       int* status, cudaStream_t st) {
+// Floats of the per-split slices conv_wgrad may write for geometry g (either path).
+size_t wgrad_part_floats(const ConvGeom& g, int sms) {
+    const int tma = wgrad_tma_splits_max(g, (g.Cout + 31) / 32, sms), gth = wgrad_gather_splits(g, sms);
+    return static_cast<size_t>(tma > gth ? tma : gth) * g.Cout * 9 * g.Cin;
+}
+
+// Weight gradient of one layer as per-split partial sums: slice s of part (floats
+// [Cout][9 Cin], at least wgrad_part_floats(g, sms) in all) holds split s's sum, *splits
+// receives the split count; split_sum_kernel adds the slices.
+cudaError_t conv_wgrad(const ConvGeom& g, const bf16* dZ, const bf16* X, float* part, int sms,
+                       int* status, cudaStream_t st, int* splits) {
     int R = 0, I = 0;
     if (g_gemm_path.load() != 1 && tma_wgrad_geom(g, X, dZ, &R, &I)) {
         bool used = false;
         const int nb = (g.Cout + 31) / 32;
-        cudaError_t e = nb == 1   ? launch_wgrad_tma<1>(g, R, I, dZ, X, dW, sms, status, st, &used)
-                        : nb == 2 ? launch_wgrad_tma<2>(g, R, I, dZ, X, dW, sms, status, st, &used)
-                        : nb == 3 ? launch_wgrad_tma<3>(g, R, I, dZ, X, dW, sms, status, st, &used)
-                                  : launch_wgrad_tma<4>(g, R, I, dZ, X, dW, sms, status, st, &used);
+        cudaError_t e = nb == 1   ? launch_wgrad_tma<1>(g, R, I, dZ, X, part, sms, status, st, &used, splits)
+                        : nb == 2 ? launch_wgrad_tma<2>(g, R, I, dZ, X, part, sms, status, st, &used, splits)
+                        : nb == 3 ? launch_wgrad_tma<3>(g, R, I, dZ, X, part, sms, status, st, &used, splits)
+                                  : launch_wgrad_tma<4>(g, R, I, dZ, X, part, sms, status, st, &used, splits);
         if (e != cudaSuccess || used) return e;
     }
     const int P = g.n * g.Ho * g.Wo, N = 9 * g.Cin;
-    const int ntiles = (N + 127) / 128;
-    const int splits = (2 * sms + ntiles - 1) / ntiles;
-    return launch_gemm<128>(GatherWgrad<128>{dZ, X, g, P}, EpiWgrad{dW, N}, g.Cout, N, P, splits,
-                            status, st);
+    const int want = wgrad_gather_splits(g, sms);
+    *splits = gemm_splits(P, want);
+    return launch_gemm<128>(GatherWgrad<128>{dZ, X, g, P}, EpiWgrad{part, N, static_cast<size_t>(g.Cout) * N},
+                            g.Cout, N, P, want, status, st);
+}
+
+// One sum of per-split slices: out[i] = (out[i] +) sum over s < splits of part[s n + i]
+// (n a multiple of 4, 16-byte aligned arrays).  A block covers v4 quads of outputs with
+// groups x v4 threads (groups a power of two, groups x v4 <= 512).
+struct SplitSum {
+    const float* part;
+    int splits, n;
+    float* out;
+    int v4, groups;
+};
+
+// Blocks [0, blocks_a) reduce a, the rest b.  Thread (g, v) adds the slices s = g, g +
+// groups, ... of output quad v in increasing s; the groups' sums are then added by a fixed
+// pairwise tree.  A fixed order: the result is the same on every run.
+__global__ void __launch_bounds__(512) split_sum_kernel(SplitSum a, SplitSum b, int blocks_a, int accumulate) {
+    __shared__ float4 red[512];
+    const bool first = static_cast<int>(blockIdx.x) < blocks_a;
+    const SplitSum t = first ? a : b;
+    const int blk = first ? blockIdx.x : blockIdx.x - blocks_a;
+    const int v = static_cast<int>(threadIdx.x) % t.v4, g = static_cast<int>(threadIdx.x) / t.v4;
+    const int n4 = t.n / 4, i4 = blk * t.v4 + v;
+    const bool live = g < t.groups && i4 < n4;
+    float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+    if (live) {
+        const float4* p = reinterpret_cast<const float4*>(t.part) + i4;
+#pragma unroll 4
+        for (int s = g; s < t.splits; s += t.groups) {
+            const float4 x = __ldg(p + static_cast<size_t>(s) * n4);
+            acc.x += x.x;
+            acc.y += x.y;
+            acc.z += x.z;
+            acc.w += x.w;
+        }
+    }
+    if (g < t.groups) red[g * t.v4 + v] = acc;
+    __syncthreads();
+    for (int h = t.groups / 2; h > 0; h >>= 1) {   // uniform over the block
+        if (g < h) {
+            float4& x = red[g * t.v4 + v];
+            const float4 y = red[(g + h) * t.v4 + v];
+            x.x += y.x;
+            x.y += y.y;
+            x.z += y.z;
+            x.w += y.w;
+        }
+        __syncthreads();
+    }
+    if (g == 0 && live) {
+        float4 r = red[v];
+        float4* o = reinterpret_cast<float4*>(t.out) + i4;
+        if (accumulate) {
+            const float4 x = *o;
+            r.x += x.x;
+            r.y += x.y;
+            r.z += x.z;
+            r.w += x.w;
+        }
+        *o = r;
+    }
+}
+
+// The block shape of one sum: up to 32 output quads, and the largest power of two of split
+// groups that fits 512 threads (at most the split count).
+SplitSum split_sum(const float* part, int splits, int n, float* out) {
+    SplitSum t{part, splits, n, out, 1, 1};
+    t.v4 = n / 4 < 32 ? (n / 4 > 0 ? n / 4 : 1) : 32;
+    while (t.groups * 2 * t.v4 <= 512 && t.groups < splits) t.groups *= 2;
+    return t;
+}
+
+cudaError_t launch_split_sum(const SplitSum& a, const SplitSum& b, int accumulate, cudaStream_t st) {
+    for (const SplitSum* t : {&a, &b})
+        if (t->n % 4 || ((reinterpret_cast<uintptr_t>(t->part) | reinterpret_cast<uintptr_t>(t->out)) & 15))
+            return cudaErrorInvalidValue;
+    const int ba = (a.n / 4 + a.v4 - 1) / a.v4, bb = (b.n / 4 + b.v4 - 1) / b.v4;
+    if (ba + bb == 0) return cudaSuccess;
+    split_sum_kernel<<<ba + bb, 512, 0, st>>>(a, b, ba, accumulate);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------
@@ -704,19 +821,39 @@ __global__ void relu_bwd_kernel(const float* __restrict__ dA, const bf16* __rest
     *reinterpret_cast<uint4*>(dZ + i) = *reinterpret_cast<const uint4*>(z);
 }
 
-// db[c] += sum_p dZ[p][c]
-// db[c] += sum over the P pixels of dZ[p][c] (C a multiple of 8, at most 128).  Coalesced:
-// a pixel row's C / 8 threads each read 8 channels as one 16-byte load, a 256-thread block
-// walks 256 / (C / 8) rows at a time over a grid-strided range of pixels, reduces its rows in
-// shared memory and adds one partial sum per channel (fp32 atomics, like the weight
-// gradient's split sums: equal to the sequential sum up to rounding order).
-__global__ void __launch_bounds__(256) bias_grad_kernel(const bf16* __restrict__ dZ, size_t P, int C,
-                                                        float* __restrict__ db) {
-    __shared__ float part[256 * 8];
-    const int tpp = C / 8, rows = 256 / tpp;
+// Partial sums of db[c] = sum over the P pixels of dZ[p][c] (C a multiple of 8, at most
+// 128).  Coalesced: a pixel row's C / 8 threads each read 8 channels as one 16-byte load, a
+// 512-thread block walks `rows` rows at a time (the largest power of two that fits) over a
+// grid-strided range of pixels, adds its rows by a fixed pairwise tree in shared memory
+// and stores one partial sum per channel to part[blockIdx.x][c]; split_sum_kernel adds
+// the blocks' partials.
+constexpr int kBiasBlocks = 512;   // at most
+constexpr int kBiasThreads = 512;
+
+__host__ __device__ constexpr int bias_rows(int C) {
+    int r = 1;
+    while (2 * r * (C / 8) <= kBiasThreads) r *= 2;
+    return r;
+}
+
+// Blocks of bias_grad_kernel for P pixels of C channels: enough to stream dZ, and few
+// enough that the split sum adds at most 8 partials per thread.
+int bias_blocks(size_t P, int C) {
+    const size_t rows = bias_rows(C), need = (P + rows - 1) / rows;
+    int cap = kBiasBlocks, g = 1;
+    while (g * 2 * (C / 4) <= 512) g *= 2;
+    if (8 * g < cap) cap = 8 * g;
+    return static_cast<int>(need < static_cast<size_t>(cap) ? need : cap);
+}
+
+__global__ void __launch_bounds__(kBiasThreads) bias_grad_kernel(const bf16* __restrict__ dZ, size_t P, int C,
+                                                                 float* __restrict__ part) {
+    __shared__ float red[kBiasThreads * 8];
+    const int tpp = C / 8, rows = bias_rows(C);
     const int t = static_cast<int>(threadIdx.x), r = t / tpp, u = t - r * tpp;
     float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
     if (r < rows) {
+#pragma unroll 4
         for (size_t p = static_cast<size_t>(blockIdx.x) * rows + r; p < P; p += static_cast<size_t>(gridDim.x) * rows) {
             const uint4 v = __ldg(reinterpret_cast<const uint4*>(dZ + p * C + 8 * u));
             const uint32_t w[4] = {v.x, v.y, v.z, v.w};
@@ -727,14 +864,17 @@ __global__ void __launch_bounds__(256) bias_grad_kernel(const bf16* __restrict__
             }
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) part[r * C + 8 * u + j] = s[j];
+        for (int j = 0; j < 8; ++j) red[r * C + 8 * u + j] = s[j];
+    }
+    for (int h = rows / 2; h > 0; h >>= 1) {   // uniform over the block
+        __syncthreads();
+        if (r < h) {
+#pragma unroll
+            for (int j = 0; j < 8; ++j) red[r * C + 8 * u + j] += red[(r + h) * C + 8 * u + j];
+        }
     }
     __syncthreads();
-    if (t < C) {
-        float acc = 0.f;
-        for (int q = 0; q < rows; ++q) acc += part[q * C + t];
-        atomicAdd(db + t, acc);
-    }
+    if (t < C) part[static_cast<size_t>(blockIdx.x) * C + t] = red[t];
 }
 
 // Smooth-L1 (Huber, delta 1 pixel) between 16 * head[..., 0:2] and the target offsets,
@@ -854,6 +994,8 @@ struct fb_initnet {
     float* dact[16] = {};
     bf16* dz = nullptr;                     // scratch: bf16 dZ of the largest layer
     bf16* dz2 = nullptr;                    // ... and a second one (fused ReLU backward)
+    float* wpart = nullptr;                 // per-split weight-gradient slices of one layer
+    float* bpart = nullptr;                 // per-block bias-gradient partials of one layer
     float* head = nullptr;                  // fp32 head output [P][8]
     float* loss = nullptr;
     int* status = nullptr;
@@ -1046,6 +1188,12 @@ int fb_initnet_create(fb_ctx* ctx, fb_initnet** out, int max_pairs, int H, int W
     const size_t o_dz = take(max_t * 2), o_dz2 = take(max_t * 2), o_head = take(Pq * 8 * 4),
                  o_dhead = take(Pq * 8 * 4);
     const size_t o_loss = take(4), o_status = take(4);
+    size_t wpart = 0;
+    for (int l = 0; l < kNumLayers; ++l) {
+        const size_t f = fb::net::wgrad_part_floats(geom(net, l, max_pairs), net->sms);
+        wpart = f > wpart ? f : wpart;
+    }
+    const size_t o_wpart = take(wpart * 4), o_bpart = take(static_cast<size_t>(fb::net::kBiasBlocks) * 128 * 4);
     if (cudaMalloc(reinterpret_cast<void**>(&net->arena), bytes) != cudaSuccess) {
         cudaGetLastError();
         delete net;
@@ -1066,6 +1214,8 @@ int fb_initnet_create(fb_ctx* ctx, fb_initnet** out, int max_pairs, int H, int W
     net->dact[15] = reinterpret_cast<float*>(a + o_dhead);  // gradient of the head output
     net->dz = reinterpret_cast<bf16*>(a + o_dz);
     net->dz2 = reinterpret_cast<bf16*>(a + o_dz2);
+    net->wpart = reinterpret_cast<float*>(a + o_wpart);
+    net->bpart = reinterpret_cast<float*>(a + o_bpart);
     net->head = reinterpret_cast<float*>(a + o_head);
     net->loss = reinterpret_cast<float*>(a + o_loss);
     net->status = reinterpret_cast<int*>(a + o_status);
@@ -1151,7 +1301,9 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
     if (rc) return rc;
     const size_t Pq = static_cast<size_t>(n) * (net->H / net->ds) * (net->W / net->ds);
     NET_CUDA(net, cudaMemsetAsync(net->loss, 0, 4, st));
-    NET_CUDA(net, cudaMemsetAsync(net->grads, 0, net->n_params * 4, st));
+    int launches = 1;   // the loss
+    // Every parameter's gradient is written once per step, by the split sum of its layer,
+    // so the gradient buffer needs no clearing and the sums do not depend on timing.
     // Activation gradients need no clearing: the first kernel to reach a tensor writes it
     // and later ones add.  The skip tensors of the stride-2 encoder layers have two
     // consumers; their gradient is written by the next layer's input gradient, and the
@@ -1186,16 +1338,18 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
                 dA, A ? A : net->act[0], out_elems, kLayers[l].relu, dz, cat >= 0 ? net->dact[cat] : nullptr,
                 g.Cout, cat >= 0 ? kTens[cat].ch : 0, skip_off[to]);
             NET_CUDA(net, cudaGetLastError());
+            ++launches;
         }
         dz_ready = false;
         const size_t P = static_cast<size_t>(g.n) * g.Ho * g.Wo;
-        const size_t bg_rows = 256 / (g.Cout / 8);
-        const size_t bg_blocks = (P + bg_rows - 1) / bg_rows;
-        const unsigned bg_grid = static_cast<unsigned>(bg_blocks < 2048 ? bg_blocks : 2048);
-        bias_grad_kernel<<<bg_grid, 256, 0, st>>>(dz, P, g.Cout, net->grads + net->b_off[l]);
+        const int bg_grid = bias_blocks(P, g.Cout);
+        bias_grad_kernel<<<bg_grid, kBiasThreads, 0, st>>>(dz, P, g.Cout, net->bpart);
         NET_CUDA(net, cudaGetLastError());
-        NET_CUDA(net, conv_wgrad(g, dz, net->act[kIn[l]], net->grads + net->w_off[l], net->sms,
-                                 net->status, st));
+        int splits = 0;
+        NET_CUDA(net, conv_wgrad(g, dz, net->act[kIn[l]], net->wpart, net->sms, net->status, st, &splits));
+        NET_CUDA(net, launch_split_sum(split_sum(net->wpart, splits, g.Cout * 9 * g.Cin, net->grads + net->w_off[l]),
+                                       split_sum(net->bpart, bg_grid, g.Cout, net->grads + net->b_off[l]), 0, st));
+        launches += 3;
         if (l > 0) {
             const int t = kIn[l];
             if (!written[t] && kOut[l - 1] == t && !in_concat(t)) {
@@ -1208,6 +1362,7 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
                                          net->status, st));
             }
             written[t] = true;
+            ++launches;
         }
         if (l == 8 || l == 9 || l == 10) {  // split the concatenated input's gradient
             const int lo = l == 8 ? 8 : (l == 9 ? 10 : 12);
@@ -1218,6 +1373,7 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
             concat_up_bwd_kernel<<<blocks(tot), 256, 0, st>>>(net->dact[cat], kTens[lo].ch, kTens[skip].ch, n,
                                                               H2, W2, net->dact[lo], written[lo] ? 1 : 0);
             NET_CUDA(net, cudaGetLastError());
+            ++launches;
             written[lo] = true;
             skip_cat[skip] = cat;
             skip_off[skip] = kTens[lo].ch;
@@ -1235,9 +1391,9 @@ int fb_initnet_train_step(fb_initnet* net, const uint8_t* src, const uint8_t* tg
         if (rc) return rc;
     }
     if (loss_out) NET_CUDA(net, cudaMemcpyAsync(loss_out, net->loss, 4, cudaMemcpyDeviceToDevice, st));
-    // forward 16, loss 1, per layer ReLU/bias/weight gradients (36) and input gradients
-    // (11), 3 concatenation splits; with an update Adam 1 and the bf16 refresh 12.
-    fb::count_launches(net->ctx, 67 + (lr > 0.f ? 13 : 0));
+    // the forward's 16 and the backward's, counted above; with an update Adam 1 and the
+    // bf16 refresh 12.
+    fb::count_launches(net->ctx, 16 + launches + (lr > 0.f ? 13 : 0));
     return FB_OK;
 }
 
@@ -1295,8 +1451,20 @@ int fb_conv3x3_backward(const uint16_t* x, int n, int H, int W, int Cin, const u
     cudaGetDevice(&dev);
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (dw) {
+        using fb::net::SplitSum;
+        float* part = nullptr;
+        if (cudaMallocAsync(reinterpret_cast<void**>(&part), fb::net::wgrad_part_floats(g, sms) * 4, st) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            return FB_ERR_OOM;
+        }
+        int splits = 0;
         cudaError_t e = fb::net::conv_wgrad(g, reinterpret_cast<const bf16*>(dz), reinterpret_cast<const bf16*>(x),
-                                            dw, sms, status, st);
+                                            part, sms, status, st, &splits);
+        if (e == cudaSuccess)
+            e = fb::net::launch_split_sum(fb::net::split_sum(part, splits, Cout * 9 * Cin, dw),
+                                          SplitSum{nullptr, 0, 0, nullptr, 1, 1}, 1, st);
+        cudaFreeAsync(part, st);
         if (e != cudaSuccess) return FB_ERR_CUDA;
     }
     if (dx) {

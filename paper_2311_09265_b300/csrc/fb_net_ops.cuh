@@ -363,13 +363,17 @@ struct GatherWgrad {
     }
 };
 
+// The K split blockIdx.z stores its partial sums to its own slice of part (each slice laid
+// out like dW); a separate reduction adds the slices in split order.
 struct EpiWgrad {
-    float* dW;  // [Cout][9*Cin], accumulated
-    int N;      // 9*Cin
+    float* part;  // [splits][Cout][9*Cin]
+    int N;        // 9*Cin
+    size_t MN;    // Cout * 9*Cin: floats per slice
     __device__ __forceinline__ void store(int row, int col0, const float (&v)[16]) const {
+        float* slice = part + blockIdx.z * MN + static_cast<size_t>(row) * N;
 #pragma unroll
         for (int j = 0; j < 16; ++j)
-            if (col0 + j < N) atomicAdd(dW + static_cast<size_t>(row) * N + col0 + j, v[j]);
+            if (col0 + j < N) slice[col0 + j] = v[j];
     }
 };
 

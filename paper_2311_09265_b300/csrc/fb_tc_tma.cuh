@@ -498,8 +498,10 @@ inline int conv_rows_stage_bytes(int BN, int CB, int Wo) {
 // apart; the output gradient's box {32 channels, 128 pixels} of the [P][Cout] matrix (zeros
 // past Cout) is the same layout for B, NB boxes.  Rows of padding channels and columns past
 // Cout are computed as zeros and not stored.  Per chunk the elected thread issues eight K = 16 MMAs (start + 1 KB each) into
-// the 128 x Cout fp32 accumulator.  CTAs split the pixel axis (grid.y) and add their
-// partial sums to dW with fp32 atomics (dW is accumulated, as by the gathered kernel).
+// the 128 x Cout fp32 accumulator.  CTAs split the pixel axis (grid.y); each stores its
+// partial sums to its own slice part[blockIdx.y] (laid out like dW), and a separate
+// reduction adds the slices in split order, so the sum does not depend on which CTA ends
+// first.
 // Waits, drains and the timeout report are those of the forward kernel.
 // ---------------------------------------------------------------------------------
 
@@ -535,7 +537,7 @@ __host__ __device__ constexpr int wgrad_tma_smem_bytes() {
 template <int NB, int S>
 __global__ void __launch_bounds__(128)
     tc_wgrad_tma_kernel(const __grid_constant__ CUtensorMap map_x, const __grid_constant__ CUtensorMap map_dz,
-                        float* __restrict__ dW, TmaWgradGeom g, int* status) {
+                        float* __restrict__ part, TmaWgradGeom g, int* status) {
     static_assert(NB >= 1 && NB <= 4, "Cout = 32 NB");
     static_assert(S >= 2 && S <= 6, "stages");
     static_assert(wgrad_tma_smem_bytes<NB, S>() <= 227 * 1024 - 1024, "shared memory per CTA");
@@ -634,6 +636,7 @@ __global__ void __launch_bounds__(128)
         const int rp = m0 + warp * 32 + lane, tap = rp / g.Cp, ci = rp - tap * g.Cp;
         const bool real = rp < 9 * g.Cp && ci < g.Cin;   // not a padding channel
         const int row = tap * g.Cin + ci;                 // column of dW
+        float* slice = part + static_cast<size_t>(blockIdx.y) * g.Cout * g.rows;
 #pragma unroll
         for (int c0 = 0; c0 < BN; c0 += 16) {
             float v[16];
@@ -641,7 +644,7 @@ __global__ void __launch_bounds__(128)
             if (real) {
 #pragma unroll
                 for (int j = 0; j < 16; ++j)
-                    if (c0 + j < g.Cout) atomicAdd(dW + static_cast<size_t>(c0 + j) * g.rows + row, v[j]);
+                    if (c0 + j < g.Cout) slice[static_cast<size_t>(c0 + j) * g.rows + row] = v[j];
             }
         }
     }

@@ -161,8 +161,9 @@ WGRAD_CASES = [  # n, H, W, Cin, Cout, stride: whole-row pixel chunks; channels 
 @pytest.mark.parametrize("n,H,W,Cin,Cout,stride", WGRAD_CASES)
 def test_tma_weight_gradient_matches_the_gather_path_and_the_oracle(fbp, n, H, W, Cin, Cout, stride):
     """The weight gradient with both operands MN-major, staged by TMA: the same products
-    as the gathered kernel, summed in another order (tensor-core K steps, pixel splits
-    added with fp32 atomics), so equal to it up to fp32 rounding, and to the FP64 oracle."""
+    as the gathered kernel, summed in another order (tensor-core K steps, another split of
+    the pixels), so equal to it up to fp32 rounding, and to the FP64 oracle.  Each path adds
+    its splits in a fixed order, so a repeated call is bit-identical."""
     import torch
     rng = np.random.default_rng(n * 5 + H + Cin + 7 * Cout + stride)
     x = ref.bf16(rng.normal(size=(n, H, W, Cin)))
@@ -177,6 +178,8 @@ def test_tma_weight_gradient_matches_the_gather_path_and_the_oracle(fbp, n, H, W
         torch.cuda.synchronize()
         assert int(st.item()) == 0
         out[mode] = (dw.cpu().numpy(), fbp.fb_conv_gemm_path(-1) - n0)
+        _, dw2, _ = fbp.conv3x3_backward(to_bf16_tensor(x), None, to_bf16_tensor(dz), stride, input_grad=False)
+        assert np.array_equal(dw2.cpu().numpy(), out[mode][0])
     fbp.fb_conv_gemm_path(0)
     (dwg, used_g), (dwt, used_t) = out[1], out[0]
     assert used_g == 0 and used_t == 1
