@@ -20,11 +20,8 @@ namespace {
 
 using namespace dev;
 
-#ifndef FB_ITER_MIN_BLOCKS
-#define FB_ITER_MIN_BLOCKS 5  // resident 256-thread blocks per SM the k=5 iteration kernel is built for
-#endif
 #ifndef FB_TILE_H
-#define FB_TILE_H 8
+#define FB_TILE_H 4
 #endif
 
 #ifndef FB_TILE_W
@@ -179,11 +176,24 @@ __global__ void __launch_bounds__(TILE_THREADS)
                   level_word, F + static_cast<size_t>(pl) * npx, E + static_cast<size_t>(pl) * npx);
 }
 
-// Resident 256-thread blocks per SM the iteration kernel is compiled for: larger
-// patches hold more target words in registers.
+// Resident warps per SM the iteration kernels are compiled for (launch bounds: that many
+// warps in blocks of TILE_THREADS).  Larger patches hold more target words in registers;
+// a few spilled words cost less than the warps they buy (k = 7: 28 warps at 72 registers
+// beat 24 at 80).
+#ifndef FB_ITER_WARPS5
+#define FB_ITER_WARPS5 40
+#endif
+#ifndef FB_ITER_WARPS7
+#define FB_ITER_WARPS7 28
+#endif
 template <int K>
-struct IterOccupancy {
-    static constexpr int value = K <= 3 ? 6 : K <= 5 ? FB_ITER_MIN_BLOCKS : K <= 7 ? 3 : 2;
+struct IterWarps {
+    static constexpr int value = K <= 3 ? 48 : K <= 5 ? FB_ITER_WARPS5 : K <= 7 ? FB_ITER_WARPS7 : 16;
+};
+// Blocks of TILE_THREADS threads that hold `warps` warps.
+template <int warps>
+struct MinBlocks {
+    static constexpr int value = warps * 32 / TILE_THREADS > 0 ? warps * 32 / TILE_THREADS : 1;
 };
 
 // ---------------------------------------------------------------------------------
@@ -194,7 +204,7 @@ struct IterOccupancy {
 // skipped: its error equals the incumbent's, so it could not win.
 // ---------------------------------------------------------------------------------
 template <int K>
-__global__ void __launch_bounds__(TILE_THREADS, IterOccupancy<K>::value * 256 / TILE_THREADS)
+__global__ void __launch_bounds__(TILE_THREADS, MinBlocks<IterWarps<K>::value>::value)
     nnf_iter_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
                     const uint32_t* __restrict__ rp, int r0,
                     uint32_t key0, uint32_t key1, uint32_t ctr_word,
@@ -218,7 +228,7 @@ __global__ void __launch_bounds__(TILE_THREADS, IterOccupancy<K>::value * 256 / 
 // Tracking (Sec. 3.5.1): as nnf_iter_kernel, plus the matches of the pair's chain
 // neighbours (pairs pad[0] / pad[1] of the launch, -1 for none) at the same pixel.
 template <int K>
-__global__ void __launch_bounds__(TILE_THREADS, IterOccupancy<K>::value)
+__global__ void __launch_bounds__(TILE_THREADS, MinBlocks<IterWarps<K>::value>::value)
     nnf_iter_track_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
                           const uint32_t* __restrict__ rp, int r0, uint32_t key0, uint32_t key1,
                           uint32_t ctr_word, const uint32_t* __restrict__ Fp,
@@ -320,14 +330,20 @@ __global__ void __launch_bounds__(TILE_THREADS)
     E[static_cast<size_t>(pl) * npx + x] = e;
 }
 
-// Two target patches per thread: fewer resident blocks than the plain kernel.
+// Two target patches per thread: fewer resident warps than the plain kernel.
+#ifndef FB_BAL_WARPS5
+#define FB_BAL_WARPS5 24
+#endif
+#ifndef FB_BAL_WARPS7
+#define FB_BAL_WARPS7 16
+#endif
 template <int K>
-struct BalancedOccupancy {
-    static constexpr int value = K <= 3 ? 4 : K <= 5 ? 3 : K <= 7 ? 2 : 1;
+struct BalancedWarps {
+    static constexpr int value = K <= 3 ? 32 : K <= 5 ? FB_BAL_WARPS5 : K <= 7 ? FB_BAL_WARPS7 : 8;
 };
 
 template <int K>
-__global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
+__global__ void __launch_bounds__(TILE_THREADS, MinBlocks<BalancedWarps<K>::value>::value)
     nnf_iter_balanced_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
                              const uint32_t* __restrict__ rp, const uint32_t* __restrict__ srp,
                              const uint32_t* __restrict__ shat_rp, int slot_by_target, int target0,
@@ -352,7 +368,7 @@ __global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
 // loss against the partner's snapshot; a pair without one (a frame outside the key range)
 // the plain loss.  The branch is uniform per block (one pair per grid row).
 template <int K, bool TRACK>
-__global__ void __launch_bounds__(TILE_THREADS, BalancedOccupancy<K>::value)
+__global__ void __launch_bounds__(TILE_THREADS, MinBlocks<BalancedWarps<K>::value>::value)
     nnf_iter_align_kernel(const PairDesc* __restrict__ pairs, int pair0, int H, int W,
                           const uint32_t* __restrict__ rp, const uint32_t* __restrict__ srp,
                           uint32_t alpha, int r0, uint32_t key0, uint32_t key1, uint32_t ctr_word,
