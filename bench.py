@@ -54,8 +54,8 @@ LIMITER = {"k5": "L1TEX pipe 84-88 % of peak on scattered candidate loads (ncu);
 # dram__bytes_read.sum + dram__bytes_write.sum of one launch of the workload's iteration
 # kernel, from an ncu capture of the current kernel on a smaller case scaled by the pairs
 # per launch (see profiles/); None when not captured or when the workload is overridden.
-TRAFFIC_PER_LAUNCH = {"blend_512": 5.73e9, "tracking_512": 4.08e9, "balanced_512": 9.11e9,
-                      "aligned_1024x576": 7.36e9, "interp_1024x576": 2.40e9}
+TRAFFIC_PER_LAUNCH = {"blend_512": 5.71e9, "tracking_512": 4.08e9, "balanced_512": 9.11e9,
+                      "aligned_1024x576": 7.41e9, "interp_1024x576": 2.74e9}
 # 32-byte L1 sectors the plain iteration kernel loads per pixel of each pair and launch:
 # ncu l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum of the captured launch divided by its
 # pairs x pixels (k = 5: 1185.3 M / (168 x 512 x 512); k = 7: 729.1 M / (20 x 576 x 1024);
