@@ -55,7 +55,7 @@ LIMITER = {"k5": "L1TEX pipe 84-88 % of peak on scattered candidate loads (ncu);
 # kernel, from an ncu capture of the current kernel on a smaller case scaled by the pairs
 # per launch (see profiles/); None when not captured or when the workload is overridden.
 TRAFFIC_PER_LAUNCH = {"blend_512": 5.71e9, "tracking_512": 4.08e9, "balanced_512": 9.11e9,
-                      "aligned_1024x576": 7.41e9, "interp_1024x576": 2.74e9}
+                      "aligned_1024x576": 7.41e9, "interp_1024x576": 2.47e9}
 # 32-byte L1 sectors the plain iteration kernel loads per pixel of each pair and launch:
 # ncu l1tex__t_sectors_pipe_lsu_mem_global_op_ld.sum of the captured launch divided by its
 # pairs x pixels (k = 5: 1185.3 M / (168 x 512 x 512); k = 7: 729.1 M / (20 x 576 x 1024);
@@ -690,8 +690,8 @@ def run_gpu(args):
                 "peak_chosen_mix": mix_rate / 1e12 if mix_rate else None,
                 "frac_chosen_mix": achieved / (mix_rate / 1e12) if mix_rate else None,
                 "chosen_mix_basis": (f"register-only probe of the k = {w.patch} kernels' Eq. 1 "
-                                     "sequence (" + ("3 dp4a per word, 20 words" if w.patch == 5 else
-                                                     "2 dp4a per word, |t|^2 held, 42 words") +
+                                     "sequence (3 dp4a per word, " + ("20" if w.patch == 5 else "42") +
+                                     " words" +
                                      " per candidate, accumulate + early-exit compare per slot), "
                                      "measured live" if mix_rate else None),
                 "avg_launch_ms": iter_ms / iter_n, "launches": iter_n,

@@ -182,7 +182,7 @@ int fb_probe_dp4a(fb_ctx *ctx, double *dp4a_per_s, double *ms);
  * patch-match kernels evaluate Eq. 1 with, on register operands (no memory traffic) on
  * every SM: for patch = 5 the five 15-byte patch rows as two 32-byte slots and one 16-byte
  * half, three dp4a per 4-byte word (<s, t>, |s|^2, |t|^2); for patch = 7 seven 24-byte
- * rows, two dp4a per word with |t|^2 held; per slot or row the accumulate and the
+ * rows, three dp4a per word likewise; per slot or row the accumulate and the
  * early-exit compare.  Writes Eq. 1 byte pairs per second (3k^2 per candidate) and the
  * kernel's duration.  This is the ALU roofline of the chosen sequence, below the dp4a-only
  * bound of fb_probe_dp4a (k = 5: 60 dp4a for 75 byte pairs instead of 19).  FB_ERR_ARG for

@@ -29,8 +29,8 @@ __global__ void __launch_bounds__(256) dp4a_probe_kernel(uint32_t seed, int iter
 // operands.  k = 5 (paired rows): per candidate two 8-word slots and one 4-word half slot
 // (the five 15-byte patch rows, zero padded), each word with three dp4a (<s, t>, |s|^2,
 // |t|^2), each slot closed by acc += |s|^2 + |t|^2 - 2 <s, t> and the early-exit compare
-// against the incumbent's error.  k = 7: seven 6-word rows, two dp4a per word (<s, t>,
-// |s|^2) and |t_a|^2 held, each row closed the same way.  The compare is never taken
+// against the incumbent's error.  k = 7: seven 6-word rows, three dp4a per word likewise,
+// each row closed the same way.  The compare is never taken
 // here (the bound is the kernel argument); dp4a is issued through volatile asm so that no
 // product is hoisted or folded: every candidate pays the whole sequence, as in the
 // kernels.  3k^2 byte pairs of Eq. 1 per candidate.
@@ -49,15 +49,6 @@ __global__ void __launch_bounds__(256) ssd_mix_probe_kernel(uint32_t seed, uint3
     for (int w = 0; w < NWORDS; ++w) {
         t[w] = (seed * static_cast<uint32_t>(w + 1)) ^ (threadIdx.x * 0x9E3779B9u) ^ blockIdx.x;
         s[w] = t[w] + 0x01010101u * static_cast<uint32_t>(w & 3);
-    }
-    uint32_t row_e[7];
-    if constexpr (K == 7) {
-#pragma unroll
-        for (int a = 0; a < 7; ++a) {
-            row_e[a] = 0;
-#pragma unroll
-            for (int w = 0; w < 6; ++w) row_e[a] = __dp4a(t[6 * a + w], t[6 * a + w], row_e[a]);
-        }
     }
     uint32_t total = 0;
     for (int i = 0; i < iters; ++i) {
@@ -79,13 +70,14 @@ __global__ void __launch_bounds__(256) ssd_mix_probe_kernel(uint32_t seed, uint3
         } else {
 #pragma unroll
             for (int a = 0; a < 7; ++a) {
-                uint32_t dot = 0, ss = 0;
+                uint32_t dot = 0, ss = 0, te = 0;
 #pragma unroll
                 for (int w = 0; w < 6; ++w) {
                     dot = dp4a_kept(s[6 * a + w], t[6 * a + w], dot);
                     ss = dp4a_kept(s[6 * a + w], s[6 * a + w], ss);
+                    te = dp4a_kept(t[6 * a + w], t[6 * a + w], te);
                 }
-                acc += ss + row_e[a] - 2u * dot;
+                acc += ss + te - 2u * dot;
                 if (acc >= bound) break;
             }
         }

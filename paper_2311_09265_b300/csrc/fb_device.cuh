@@ -124,10 +124,12 @@ __device__ __forceinline__ void load_row(const uint32_t* __restrict__ p,
     }
 }
 
+// The target patch, held in registers for all of a pixel's candidates.  |t_a|^2 of each
+// row is recomputed per candidate row (one dp4a per word) rather than held: the k
+// registers it would take cost more, as spills or as resident warps, than the dp4a issue.
 template <int K>
 struct TargetPatch {
     uint32_t w[K][Geo<K>::NW];  // the k rows of the target patch
-    uint32_t row_e[K];          // sum of squares of each row
 };
 
 template <int K>
@@ -139,7 +141,6 @@ __device__ __forceinline__ void load_target(const uint32_t* __restrict__ rpt, in
         for (int a = 0; a < K; ++a) {
 #pragma unroll
             for (int w = 0; w < G::NW; ++w) t.w[a][w] = 0;
-            t.row_e[a] = 0;
         }
         return;
     }
@@ -166,15 +167,6 @@ __device__ __forceinline__ void load_target(const uint32_t* __restrict__ rpt, in
         for (int a = 0; a < K; ++a) {
             const int rr = clampi(r - G::P + a, 0, H - 1);
             load_row<K>(rpt + (static_cast<size_t>(rr) * W + c) * G::RPW, t.w[a]);
-        }
-    }
-    if constexpr (!G::PAIRED) {  // the paired path recomputes |t_a|^2 per candidate
-#pragma unroll
-        for (int a = 0; a < K; ++a) {
-            uint32_t e = 0;
-#pragma unroll
-            for (int w = 0; w < G::NW; ++w) e = __dp4a(t.w[a][w], t.w[a][w], e);
-            t.row_e[a] = e;
         }
     }
 }
@@ -258,13 +250,14 @@ __device__ __forceinline__ bool patch_error_below(const uint32_t* __restrict__ r
             const int rr = clampi(ur - G::P + a, 0, H - 1);
             uint32_t s[G::NW];
             load_row<K>(rps + (static_cast<size_t>(rr) * W + uc) * G::RPW, s);
-            uint32_t dot = 0, ss = 0;
+            uint32_t dot = 0, ss = 0, te = 0;
 #pragma unroll
             for (int w = 0; w < G::NW; ++w) {
                 dot = __dp4a(s[w], t.w[a][w], dot);
                 ss = __dp4a(s[w], s[w], ss);
+                te = __dp4a(t.w[a][w], t.w[a][w], te);
             }
-            acc += ss + t.row_e[a] - 2u * dot;
+            acc += ss + te - 2u * dot;
             if (acc >= bound) return false;
         }
         *e = acc;

@@ -177,9 +177,9 @@ __global__ void __launch_bounds__(TILE_THREADS)
 }
 
 // Resident warps per SM the iteration kernels are compiled for (launch bounds: that many
-// warps in blocks of TILE_THREADS).  Larger patches hold more target words in registers;
-// a few spilled words cost less than the warps they buy (k = 7: 28 warps at 72 registers
-// beat 24 at 80).
+// warps in blocks of TILE_THREADS).  Larger patches hold more target words in registers
+// (k = 7: 28 warps fit 72 registers without spilling; 24 warps at 80 are slower, 32 at 64
+// spill).
 #ifndef FB_ITER_WARPS5
 #define FB_ITER_WARPS5 40
 #endif
