@@ -68,11 +68,13 @@ __device__ __forceinline__ const uint32_t* as_ptr(int lo, int hi) {
                                              static_cast<uint32_t>(lo));
 }
 
-// Larger patches keep more target words in registers: scale the block count down.
+// Larger patches keep more target words in registers: fewer resident warps (k = 7: 28
+// warps per SM, as the per-call kernel, in as many whole blocks as fit).
 template <int K, int V>
 struct BatchOcc {
     static constexpr int base = Variant<V>::MINB;
-    static constexpr int value = K <= 5 ? base : K <= 7 ? (base * 3 + 4) / 5 : (base * 2 + 4) / 5;
+    static constexpr int k7 = 28 / Variant<V>::TH > 0 ? 28 / Variant<V>::TH : 1;
+    static constexpr int value = K <= 5 ? base : K <= 7 ? k7 : (base * 2 + 4) / 5;
 };
 
 template <int K, int V>
