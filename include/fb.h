@@ -191,8 +191,8 @@ int fb_probe_ssd_mix(fb_ctx *ctx, int patch, double *byte_pairs_per_s, double *m
 
 /* Diagnostics: measures the device's rate of scattered 32-byte loads, the traffic of the
  * patch-match kernels (every candidate patch row is a 256-bit load of a 32-byte row-patch
- * slot at a data-dependent address): 5 resident 256-thread blocks per SM (the k = 5
- * iteration kernel's occupancy), each thread issuing independent 256-bit loads of
+ * slot at a data-dependent address): 5 resident 256-thread blocks per SM (40 warps, the
+ * k = 5 iteration kernel's occupancy), each thread issuing independent 256-bit loads of
  * pseudo-randomly chosen slots of a `bytes`-sized buffer in the context's scratch.  A
  * buffer that fits L1 measures the L1 data pipe (one 32-byte sector per wavefront); a
  * larger one adds the L2.  Writes 32-byte sectors per second and the kernel's duration.

@@ -216,7 +216,8 @@ int batch_iter_blocks_per_sm(int k, int variant);
 
 // dp4a throughput probe (fb_calib.cu): blocks x 256 threads x iters x chains dp4a.
 constexpr int kDp4aProbeChains = 32;
-// Resident 256-thread blocks per SM of the gather probe: those of the k = 5 iteration kernel.
+// Resident 256-thread blocks per SM of the gather probe: 40 warps, the k = 5 iteration
+// kernel's occupancy.
 constexpr int kIterProbeBlocksPerSm = 5;
 cudaError_t launch_dp4a_probe(int blocks, int iters, uint32_t* sink, cudaStream_t st);
 // Eq. 1 instruction-sequence probe (fb_calib.cu): blocks x 256 threads x iters candidates of
