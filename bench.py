@@ -705,6 +705,21 @@ def run_gpu(args):
                                                                    (4 + w.random_search_radii())))
                 * args.steps * world / (total_ms / 1e3),
                 "probe_dp4a_per_s": rate}
+        if roof["traffic"]:
+            # The other side of the roofline: the launch's DRAM bytes (ncu) at the measured
+            # copy bandwidth, against the ops at the measured rate of the kernel's own
+            # instruction sequence; the fraction is the slower of the two over the launch.
+            hbm_peak, hbm_basis = measured_peak("hbm_gbs", 6400.0)
+            t_hbm = roof["traffic"] / (hbm_peak * 1e9)
+            roof["hbm"] = {"traffic_bytes_per_launch": roof["traffic"],
+                           "achieved_gbs": roof["traffic"] / avg_s / 1e9, "peak_gbs": hbm_peak,
+                           "peak_basis": hbm_basis, "frac": roof["traffic"] / avg_s / 1e9 / hbm_peak,
+                           "t_hbm_ms": t_hbm * 1e3}
+            if mix_rate:
+                t_int = ops / mix_rate
+                roof["t_int_ms"] = t_int * 1e3
+                roof["slower_bound"] = "alu" if t_int >= t_hbm else "hbm"
+                roof["frac_max_bound"] = max(t_int, t_hbm) / avg_s
         if gather_rates and w.levels == 1:
             pairs_launch = shard["pairs"] if shard else w.pairs()
             sectors = SECTORS_PER_PIXEL_ITER[w.patch] * pairs_launch * w.H * w.W
