@@ -564,10 +564,12 @@ size_t pair_budget(const fb_ctx* ctx) {
 }
 
 int make_chunks(fb_ctx* ctx, const std::vector<JobDesc>& jobs, size_t npx0,
-                std::vector<Chunk>& chunks, size_t& max_pairs, size_t extra_per_pair = 0) {
+                std::vector<Chunk>& chunks, size_t& max_pairs, size_t extra_per_pair = 0,
+                size_t cap_pairs = 0) {
     const size_t per_pair = npx0 * 4 * sizeof(uint32_t) + extra_per_pair;
     size_t cap = pair_budget(ctx) / per_pair;
     if (cap > static_cast<size_t>(kMaxChunkPairs)) cap = kMaxChunkPairs;
+    if (cap_pairs > 0 && cap_pairs < cap) cap = cap_pairs;
     if (cap < 1) cap = 1;
     max_pairs = 0;
     Chunk cur{0, 0, jobs.empty() ? 0 : jobs[0].first_pair, 0};
@@ -615,6 +617,18 @@ int run_pipeline(fb_ctx* ctx, const uint8_t* guides, int N, int H, int W, const 
     size_t max_pairs = 0;
     int rc = make_chunks(ctx, jobs, npx0, chunks, max_pairs, extra);
     if (rc) return rc;
+    // Host buffers: at least kStagingChunks chunks (each still millions of pixels per
+    // launch), so that a chunk's frames leave on the copy stream while the next chunk's
+    // NNFs are computed.  Tracking chains run through whole clips: one chunk.
+    constexpr size_t kStagingChunks = 4, kStagingChunkPixels = size_t(1) << 21;
+    if (staging && !(p->flags & FB_FLAG_TRACKING) && chunks.size() < kStagingChunks &&
+        pairs.size() * npx0 >= kStagingChunks * kStagingChunkPixels) {
+        size_t cap = (pairs.size() + kStagingChunks - 1) / kStagingChunks, most = 1;
+        for (const JobDesc& j : jobs) most = std::max(most, static_cast<size_t>(j.n_pairs));
+        chunks.clear();
+        rc = make_chunks(ctx, jobs, npx0, chunks, max_pairs, extra, std::max(cap, most));
+        if (rc) return rc;
+    }
     if ((p->flags & FB_FLAG_TRACKING) && chunks.size() > 1)
         return fail(ctx, FB_ERR_UNSUPPORTED, "tracking keeps all %zu NNFs of the call at once; the pair budget does not",
                     pairs.size());
