@@ -177,6 +177,34 @@ def test_blend_window_host_buffers_equal_device_buffers(fbp, ctx):
                                 p).numpy() == dev).all()
 
 
+def test_host_buffer_calls_split_into_chunks_give_the_device_results(fbp, ctx):
+    """A host-buffer call whose pairs hold at least 4 x 2^21 pixels is cut into at least four
+    chunks of output frames, so each chunk's frames leave while the next chunk's NNFs are
+    computed; the device-buffer call of the same clip runs as one chunk.  Same results;
+    more iteration launches for the host call show the cut."""
+    import torch
+    g, s = synth.small_clip(72, 256, 256, seed=31)
+    ks = np.ascontiguousarray(s[[0, 71]])
+    p = fbp.Params.make(5, 2, 1, 0, 17)
+    n0 = ctx.launches
+    a = host(fbp.fb_interpolate(ctx, cuda(g), [0, 71], cuda(ks), p))
+    n_dev = ctx.launches - n0
+    gh = torch.from_numpy(g).pin_memory()
+    n0 = ctx.launches
+    b = fbp.fb_interpolate(ctx, gh, [0, 71], torch.from_numpy(ks).pin_memory(), p).numpy()
+    n_host = ctx.launches - n0
+    assert (a == b).all()
+    # 140 NNFs of 65,536 pixels: one chunk on the device, four from host buffers (2 more
+    # iterations, an init and a combine per extra chunk; the combine split in groups)
+    assert n_host >= n_dev + 3 * (p.iters + 2)
+    assert (a[35] == oracle.interpolate_frame(g, [0, 71], ks, 35, 5, 2, seed=17)).all()
+    g2, s2 = synth.small_clip(20, 256, 256, seed=32)
+    d = host(fbp.fb_blend_window(ctx, cuda(g2), cuda(s2), 9, p))
+    h = fbp.fb_blend_window(ctx, torch.from_numpy(g2).pin_memory(), torch.from_numpy(s2).pin_memory(), 9,
+                            p).numpy()
+    assert (d == h).all()
+
+
 def test_host_buffers_in_chunks_and_modes_equal_device_buffers(fbp, ctx):
     """Host buffers move through a copy stream (styles in while the search runs, frames out
     in groups as their combine finishes): the results equal the device-buffer call for
