@@ -123,3 +123,34 @@ def test_training_step_gradient_matches_oracle(fbp, ds):
         off += nw + cout
     net.close()
     ctx.close()
+
+
+def test_training_is_reproducible_bit_for_bit_at_the_shipped_size(fbp):
+    """The shipped network (512 x 512 guides, downscale 8, batches of 8 pairs): every
+    gradient is a sum in a fixed order -- per-split weight-gradient slices and per-block
+    bias partials added in index order, no atomics -- so the same steps from the same
+    parameters give the same gradients and parameters bit for bit, whatever the order in
+    which the CTAs ran."""
+    import torch
+    from paper_2311_09265_b300 import initnet_train as it
+    rng = np.random.default_rng(23)
+    n, H, W = 8, 512, 512
+    src = torch.tensor(rng.integers(0, 256, size=(n, H, W, 3)).astype(np.uint8), device="cuda")
+    tgt = torch.tensor(rng.integers(0, 256, size=(n, H, W, 3)).astype(np.uint8), device="cuda")
+    target = torch.tensor(rng.normal(0, 4, size=(n, H // 8, W // 8, 2)).astype(np.float32), device="cuda")
+    ctx = fbp.Context(0)
+    runs = []
+    for _ in range(2):
+        net = fbp.InitNet(ctx, n, H, W, downscale=8)
+        net.set_params(it.initial_params(net.n_params, 3))
+        for _ in range(3):
+            net.train_step(src, tgt, target, lr=1e-3)
+        net.train_step(src, tgt, target, lr=0.0)   # gradients of the updated parameters
+        torch.cuda.synchronize()
+        assert net.status() == 0
+        runs.append((net.get_grads(), net.get_params()))
+        net.close()
+    (g0, p0), (g1, p1) = runs
+    assert np.abs(g0).sum() > 0
+    assert np.array_equal(g0, g1) and np.array_equal(p0, p1)
+    ctx.close()
