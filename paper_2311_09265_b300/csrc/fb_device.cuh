@@ -605,60 +605,86 @@ __device__ __forceinline__ void init_pixel(const uint32_t* __restrict__ rps,
     FB_CHECK_TALLY(1);
 }
 
-// Alg. 2 remap of one pair's style through its NNF at output pixel (r, c): the k^2
-// votes S(clamp(F(q^) - (q^ - x))), q^ = clamp(q), summed per channel.
-template <int K>
+// Source pixel of the vote of q^ = clamp(x + d) for target x: clamp(F(q^) - (q^ - x)) per
+// coordinate.  F packs (row, col) in the two 16-bit halves of a word, both inside the image,
+// so for H, W <= 32760 (no half can leave the signed 16-bit range) one per-halfword
+// add-min-max instruction (DPX: max(min(a + b, c), 0)) forms both clamped coordinates, and
+// the linear index row * W + col is t + row * (W - 65536); larger frames take the scalar
+// clamps.  Both give the same pixel.
+__device__ __forceinline__ bool votes_packed(int H, int W) { return H <= 32760 && W <= 32760; }
+
+template <int K, bool PACKED, class Vote>
+__device__ __forceinline__ void remap_walk(const uint32_t* __restrict__ Fq, int H, int W, int r, int c,
+                                           Vote&& vote) {
+    constexpr int P = K / 2;
+    if (PACKED && votes_packed(H, W)) {   // uniform over the grid
+        const uint32_t hi = (static_cast<uint32_t>(H - 1) << 16) | static_cast<uint32_t>(W - 1);
+        const uint32_t wm = static_cast<uint32_t>(W) - 65536u;
+#pragma unroll
+        for (int a = -P; a <= P; ++a) {
+            const int qr = clampi(r + a, 0, H - 1);
+            const uint32_t ndr = static_cast<uint32_t>(r - qr) << 16;   // -(qr - r), high half
+#pragma unroll
+            for (int b = -P; b <= P; ++b) {
+                const int qc = clampi(c + b, 0, W - 1);
+                const uint32_t f = __ldg(Fq + static_cast<size_t>(qr) * W + qc);
+                (void)FB_CHECK(match_inside(f, H, W), FB_CHECK_REMAP, row_of(f), col_of(f));
+                const uint32_t t = __viaddmin_s16x2_relu(f, ndr | (static_cast<uint32_t>(c - qc) & 0xFFFFu), hi);
+                vote(t + (t >> 16) * wm);
+            }
+        }
+    } else {
+#pragma unroll
+        for (int a = -P; a <= P; ++a) {
+            const int qr = clampi(r + a, 0, H - 1);
+#pragma unroll
+            for (int b = -P; b <= P; ++b) {
+                const int qc = clampi(c + b, 0, W - 1);
+                const uint32_t f = __ldg(Fq + static_cast<size_t>(qr) * W + qc);
+                (void)FB_CHECK(match_inside(f, H, W), FB_CHECK_REMAP, row_of(f), col_of(f));
+                const int sr = clampi(row_of(f) - (qr - r), 0, H - 1);
+                const int sc = clampi(col_of(f) - (qc - c), 0, W - 1);
+                vote(static_cast<uint32_t>(sr) * static_cast<uint32_t>(W) + static_cast<uint32_t>(sc));
+            }
+        }
+    }
+}
+
+// Alg. 2 remap of one pair's style through its NNF at output pixel (r, c): the k^2 votes
+// S(clamp(F(q^) - (q^ - x))), q^ = clamp(q), summed per channel.  S: RGBX words of the
+// source style frame.  PACKED: the packed clamps where the frame allows them.
+template <int K, bool PACKED = true>
 __device__ __forceinline__ void remap_votes(const uint32_t* __restrict__ Fq,
                                             const uint32_t* __restrict__ S, int H, int W, int r,
                                             int c, uint32_t& v0, uint32_t& v1, uint32_t& v2) {
-    constexpr int P = K / 2;
     // Channels summed two to a register in 16-bit lanes (R and B; G and the pad byte):
     // a lane holds at most k^2 * 255 <= 20655 for k <= 9, so no lane carries over.
     uint32_t rb = 0, gx = 0;
-#pragma unroll
-    for (int a = -P; a <= P; ++a) {
-        const int qr = clampi(r + a, 0, H - 1);
-#pragma unroll
-        for (int b = -P; b <= P; ++b) {
-            const int qc = clampi(c + b, 0, W - 1);
-            const uint32_t f = __ldg(Fq + static_cast<size_t>(qr) * W + qc);
-            (void)FB_CHECK(match_inside(f, H, W), FB_CHECK_REMAP, row_of(f), col_of(f));
-            const int sr = clampi(row_of(f) - (qr - r), 0, H - 1);
-            const int sc = clampi(col_of(f) - (qc - c), 0, W - 1);
-            const uint32_t s = __ldg(S + static_cast<size_t>(sr) * W + sc);
-            rb += s & 0x00FF00FFu;
-            gx += (s >> 8) & 0x00FF00FFu;
-        }
-    }
+    remap_walk<K, PACKED>(Fq, H, W, r, c, [&](uint32_t idx) {
+        const uint32_t s = __ldg(S + idx);
+        rb += s & 0x00FF00FFu;
+        gx += (s >> 8) & 0x00FF00FFu;
+    });
     v0 = rb & 0xFFFFu;
     v1 = gx & 0xFFFFu;
     v2 = rb >> 16;
     FB_CHECK_TALLY(1);
 }
 
-// Alg. 2 vote sums of a fast-mode table entry (three uint32 sums per 16-byte pixel).
+// Alg. 2 vote sums of a fast-mode table entry (three uint32 sums per 16-byte pixel).  The
+// scalar clamps: with 16-byte votes the packed form's extra live registers cost more than
+// the instructions it saves.
 template <int K>
 __device__ __forceinline__ void remap_votes_u4(const uint32_t* __restrict__ Fq,
                                                const uint4* __restrict__ T, int H, int W, int r,
                                                int c, uint32_t& v0, uint32_t& v1, uint32_t& v2) {
-    constexpr int P = K / 2;
     v0 = v1 = v2 = 0;
-#pragma unroll
-    for (int a = -P; a <= P; ++a) {
-        const int qr = clampi(r + a, 0, H - 1);
-#pragma unroll
-        for (int b = -P; b <= P; ++b) {
-            const int qc = clampi(c + b, 0, W - 1);
-            const uint32_t f = __ldg(Fq + static_cast<size_t>(qr) * W + qc);
-            (void)FB_CHECK(match_inside(f, H, W), FB_CHECK_REMAP, row_of(f), col_of(f));
-            const int sr = clampi(row_of(f) - (qr - r), 0, H - 1);
-            const int sc = clampi(col_of(f) - (qc - c), 0, W - 1);
-            const uint4 s = __ldg(T + static_cast<size_t>(sr) * W + sc);
-            v0 += s.x;
-            v1 += s.y;
-            v2 += s.z;
-        }
-    }
+    remap_walk<K, false>(Fq, H, W, r, c, [&](uint32_t idx) {
+        const uint4 s = __ldg(T + idx);
+        v0 += s.x;
+        v1 += s.y;
+        v2 += s.z;
+    });
     FB_CHECK_TALLY(1);
 }
 

@@ -294,8 +294,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
         const int gp = job.first_pair + p;
         const PairDesc pd = pairs[gp];
         uint32_t v0, v1, v2;
-        remap_votes<K>(F + static_cast<size_t>(gp - pair0) * npx, styles + static_cast<size_t>(pd.style) * npx,
-                       H, W, tc.r, tc.c, v0, v1, v2);
+        remap_votes<K, false>(F + static_cast<size_t>(gp - pair0) * npx, styles + static_cast<size_t>(pd.style) * npx,
+                              H, W, tc.r, tc.c, v0, v1, v2);
         a0 += v0;
         a1 += v1;
         a2 += v2;
@@ -424,8 +424,8 @@ __global__ void __launch_bounds__(TILE_THREADS)
         const int p = src_pairs[e.first_src + q];
         const PairDesc pd = pairs[p];
         uint32_t v0, v1, v2;
-        remap_votes<K>(F + static_cast<size_t>(p) * npx, styles + static_cast<size_t>(pd.style) * npx, H,
-                       W, tc.r, tc.c, v0, v1, v2);
+        remap_votes<K, false>(F + static_cast<size_t>(p) * npx, styles + static_cast<size_t>(pd.style) * npx, H,
+                              W, tc.r, tc.c, v0, v1, v2);
         a0 += v0;
         a1 += v1;
         a2 += v2;
