@@ -138,6 +138,22 @@ def test_remap_bit_exact(fbp, ctx, H, W, k):
     assert (out == ref).all()
 
 
+@pytest.mark.parametrize("H,W,k", [(9, 32760, 9), (32760, 9, 9), (9, 32761, 5), (32761, 9, 5)])
+def test_remap_at_the_packed_clamp_bound(fbp, ctx, H, W, k):
+    """The remap forms both clamped source coordinates of a vote with one per-halfword
+    instruction on the packed field word for frames up to 32760 pixels a side (the largest
+    side at which no half leaves the signed 16-bit range, with the largest patch), and with
+    scalar clamps above that: both sides of the bound, fields running past every edge."""
+    rng = np.random.default_rng(H + 3 * W + k)
+    S = rng.integers(0, 256, (H, W, 3), dtype=np.uint8)
+    F = np.stack([rng.integers(-6, H + 6, (H, W)), rng.integers(-6, W + 6, (H, W))], -1).astype(np.int32)
+    # the fields along the far edges point at the far edges, where the votes' offsets reach
+    F[-2:, :, 0] = H - 1
+    F[:, -2:, 1] = W - 1
+    out = host(fbp.fb_remap(ctx, cuda(S), cuda(F), k))
+    assert (out == oracle.remap(S, F, k)).all()
+
+
 # ----------------------------------------------------------------------------------
 # Eq. 2 window blend
 # ----------------------------------------------------------------------------------
